@@ -1,0 +1,410 @@
+"""Benchmark: samples/s of exact n* at L = 16 over all 127 neighborhoods (seeds 1..256 per rank),
+learned bracket vs plain bracket, on one B300 per rank.
+
+One step = the whole path for one batch: perc_rank of the 256 seeds, the bracket network on the
+32,512 samples (learned arm), and the persistent perc_nstar launch.  Inputs (seeds, sample table,
+network parameters) are resident in HBM when the timed region starts; L2 is flushed between steps
+and the site orders (2 GiB) are larger than L2 anyway.  `e2e` repeats the step through the C ABI
+from pinned host buffers with the host<->device copies inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own seed block (weak scaling, no collective on the data path);
+rank 0 prints one JSON line.  `--impl reference` times the CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L = 16
+NUM_SEEDS = 256
+MASKS = list(range(1, 128))
+METRIC = "samples/sec (exact n*) at L=16 over 127 neighborhoods, learned vs plain bracket"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_for(rank: int, num_seeds: int = NUM_SEEDS):
+    seeds = np.arange(1, num_seeds + 1) + rank * num_seeds
+    return seeds, np.array([(L, m, int(s)) for m in MASKS for s in seeds], dtype=np.int64)
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline); workers are spawned, never forked
+# ------------------------------------------------------------------------------------------------
+def _oracle_seed(seed: int) -> int:
+    import oracle
+    perm, rk = oracle.rank(L, seed)
+    for m in MASKS:
+        oracle.nz(L, m, perm, rk)
+    return len(MASKS)
+
+
+def oracle_rate(seeds, workers: int):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        done = sum(pool.map(_oracle_seed, list(seeds)))
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    cpu_workers = max(1, min(host_cores(), 32))  # oracle workers for cpu_baseline (spawned)
+
+    from paper_2607_18991_b300 import bracket as pbracket
+    from paper_2607_18991_b300 import build as pbuild
+    from paper_2607_18991_b300 import driver, perc
+
+    pbuild.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ws = perc.Workspace(dev)
+    seeds, wl = workload_for(rank, args.num_seeds)
+    num = len(wl)
+
+    # ---- bracket network: trained on plain n* of held-out seeds at L = 8 (zone 1) and L = 16
+    t_train = time.perf_counter()
+    train_seeds = np.arange(1, args.train_seeds + 1) + 1_000_000
+    wl_train = np.concatenate([np.array([(8, 1, s) for s in range(1_000_001, 1_001_001)]),
+                               np.array([(L, m, int(s)) for m in MASKS for s in train_seeds])])
+    ns_train, _ = driver.nstar(wl_train)
+    params, losses = pbracket.train(wl_train[:, 0], wl_train[:, 1], ns_train, steps=args.train_steps,
+                                    lr=args.lr, seed=0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train
+
+    # ---- resident inputs
+    seeds_dev = torch.as_tensor(seeds.astype(np.int64), device=dev)
+    N = L ** 5
+    perm = torch.empty((len(seeds), N), dtype=torch.int32, device=dev)
+    rk = torch.empty((len(seeds), N), dtype=torch.int32, device=dev)
+    rows = np.searchsorted(seeds, wl[:, 2])
+    samples = perc.samples_for(L, wl[:, 1], rows, perm, rk)
+    br = torch.empty((num, 2), dtype=torch.int32, device=dev)
+    ns = torch.empty(num, dtype=torch.int32, device=dev)
+    ps = torch.empty(num, dtype=torch.int32, device=dev)
+    rank_ws_bytes = perc.workspace_bytes(perc.OP_RANK, L, len(seeds))
+    nstar_ws_bytes = perc.workspace_bytes(perc.OP_NSTAR, L, num)
+    ws_buf = torch.empty(max(rank_ws_bytes, nstar_ws_bytes), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    lib = perc.lib()
+    sp = stream.cuda_stream
+
+    def step(learned: bool, ev=None):
+        perc._ok(lib.perc_rank(L, seeds_dev.data_ptr(), len(seeds), perm.data_ptr(), rk.data_ptr(),
+                               ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_rank")
+        if ev is not None:
+            ev[0].record(stream)
+        if learned:
+            perc._ok(lib.perc_bracket(params.data_ptr(), samples.data_ptr(), num, args.margin, br.data_ptr(), sp),
+                     "perc_bracket")
+        if ev is not None:
+            ev[1].record(stream)
+        perc._ok(lib.perc_nstar(samples.data_ptr(), num, L, br.data_ptr() if learned else None, ns.data_ptr(),
+                                ps.data_ptr(), None, ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_nstar")
+        if ev is not None:
+            ev[2].record(stream)
+
+    def timed(learned: bool, K: int, W: int):
+        for _ in range(W):
+            step(learned)
+        torch.cuda.synchronize()
+        tot, t_rank, t_nstar = 0.0, 0.0, 0.0
+        for _ in range(K):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            e[3].record(stream)
+            step(learned, e)
+            torch.cuda.synchronize()
+            tot += e[3].elapsed_time(e[2])
+            t_rank += e[3].elapsed_time(e[0])
+            t_nstar += e[1].elapsed_time(e[2])
+        return tot / K, t_rank / K, t_nstar / K
+
+    gpu_index = torch.cuda.current_device()
+    phys = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    smi_index = int(phys[gpu_index]) if phys and phys[0].strip().isdigit() else gpu_index
+    with ClockSampler(smi_index) as clk:
+        ms_learned, ms_rank, ms_nstar_learned = timed(True, args.steps, args.warmup)
+        ms_plain, _, ms_nstar_plain = timed(False, args.steps, args.warmup)
+    clocks = clk.summary()
+
+    # passes and correctness summary of the last learned / plain runs
+    step(True)
+    passes_learned = perc.u32(ps).astype(np.float64).mean()
+    ns_learned = perc.u32(ns).copy()
+    stats = perc.new_stats()
+    perc._ok(lib.perc_nstar(samples.data_ptr(), num, L, br.data_ptr(), ns.data_ptr(), ps.data_ptr(),
+                            stats.data_ptr(), ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_nstar")
+    st_learned = perc.stats_dict(stats)
+    step(False)
+    passes_plain = perc.u32(ps).astype(np.float64).mean()
+    ns_plain = perc.u32(ns).copy()
+    assert np.array_equal(ns_learned, ns_plain), "learned and plain n* differ"
+    stats = perc.new_stats()
+    perc._ok(lib.perc_nstar(samples.data_ptr(), num, L, None, ns.data_ptr(), ps.data_ptr(),
+                            stats.data_ptr(), ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_nstar")
+    st_plain = perc.stats_dict(stats)
+    rc = lib.perc_check(ws_buf.data_ptr(), sp)
+    assert rc == 0, perc.status_string(rc)
+
+    # ---- e2e through the C ABI from pinned host buffers
+    seeds_host = torch.from_numpy(seeds.astype(np.int64)).pin_memory()
+    samples_host = samples.cpu().pin_memory()
+    params_host = params.cpu().pin_memory()
+    ns_host = torch.empty(num, dtype=torch.int32).pin_memory()
+    seeds_d2 = torch.empty_like(seeds_dev)
+    samples_d2 = torch.empty_like(samples)
+    params_d2 = torch.empty_like(params)
+
+    def e2e_step():
+        seeds_d2.copy_(seeds_host, non_blocking=True)
+        samples_d2.copy_(samples_host, non_blocking=True)
+        params_d2.copy_(params_host, non_blocking=True)
+        perc._ok(lib.perc_rank(L, seeds_d2.data_ptr(), len(seeds), perm.data_ptr(), rk.data_ptr(),
+                               ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_rank")
+        perc._ok(lib.perc_bracket(params_d2.data_ptr(), samples_d2.data_ptr(), num, args.margin, br.data_ptr(), sp),
+                 "perc_bracket")
+        perc._ok(lib.perc_nstar(samples_d2.data_ptr(), num, L, br.data_ptr(), ns.data_ptr(), None, None,
+                                ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_nstar")
+        ns_host.copy_(ns, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    e2e_ms /= args.steps
+    h2d = seeds_host.numel() * 8 + samples_host.numel() * 8 + params_host.numel() * 4
+    d2h = ns_host.numel() * 4
+
+    # ---- max over ranks
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms_learned = max_over_ranks(ms_learned)
+    ms_plain = max_over_ranks(ms_plain)
+    e2e_ms = max_over_ranks(e2e_ms)
+    ms_nstar_learned = max_over_ranks(ms_nstar_learned)
+
+    # ---- roofline of the dominant kernel (k_nstar, learned arm): algorithmic bytes per pass
+    # = N/8 (bitmap write) + N/8 (bitmap read) + 4n (perm prefix) + 8n (labels) + 8 L^4 (faces)
+    #   + 8 E_n, summed over the passes of the launch (E_n = successful hooks)
+    alg_bytes = (st_learned["passes"] * (N / 8 * 2 + 8 * L ** 4) + 12 * st_learned["probe_sites"]
+                 + 8 * st_learned["hooks"])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    achieved = alg_bytes / (ms_nstar_learned * 1e-3) / 1e9
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "k_nstar_traffic.json")))
+        traffic = prof.get("bytes_per_launch")
+    except Exception:
+        pass
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_seeds_cpu = cpu_workers * args.cpu_seeds_per_worker
+        rate, done, dt = oracle_rate(range(1, n_seeds_cpu + 1), cpu_workers)
+        cpu = {"value": rate, "unit": "samples/s", "cores": cpu_workers, "kind": "oracle",
+               "sample": f"L=16, seeds 1..{n_seeds_cpu} x 127 masks ({done} samples) in {dt:.1f} s, "
+                         f"one ranking per seed, {cpu_workers} spawned workers"}
+
+    gpu_launches = (math.ceil(len(seeds) / 64) * 13) + 2  # rank passes + bracket + nstar per step
+    value = world * num / (ms_learned * 1e-3)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic (Philox-keyed site orders, seeds per rank)",
+            "config": {"workload": "all 127 neighborhoods, L=16 (1,048,576 sites), seeds 1..256 per rank, "
+                                   "32,512 samples/rank, one persistent launch",
+                       "L": L, "masks": 127, "seeds_per_rank": int(len(seeds)), "samples_per_rank": num,
+                       "bracket": "learned", "margin": args.margin,
+                       "l2": "flushed (256 MiB write) between timed steps; site orders 2 GiB > L2",
+                       "parallelism": f"dp{world} (seed blocks, no collective)"},
+            "plain": {"value": world * num / (ms_plain * 1e-3), "unit": "samples/s", "ms_per_step": ms_plain,
+                      "nstar_ms": ms_nstar_plain, "passes_per_sample": passes_plain, "stats": st_plain},
+            "learned": {"value": value, "ms_per_step": ms_learned, "nstar_ms": ms_nstar_learned,
+                        "rank_ms": ms_rank, "passes_per_sample": passes_learned, "stats": st_learned,
+                        "train_s": t_train, "train_loss_last": float(losses[-1].item())},
+            "e2e": {"value": world * num / (e2e_ms * 1e-3), "unit": "samples/s", "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "roofline": {"kernel": "k_nstar (learned)", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": alg_bytes, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": gpu_launches,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------------
+# reference arm: the CPU oracle on the same workload
+# ------------------------------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    workers = max(1, min(host_cores(), 32))
+    per_step = workers  # one seed (127 samples) per worker per step
+    for w in range(args.warmup):
+        oracle_rate(range(1, min(per_step, 4) + 1), min(workers, 4))
+    rates, total_dt, total_done = [], 0.0, 0
+    for k in range(args.steps):
+        s0 = 1 + k * per_step
+        rate, done, dt = oracle_rate(range(s0, s0 + per_step), workers)
+        rates.append(rate)
+        total_dt += dt
+        total_done += done
+    value = total_done / total_dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (Philox-keyed site orders)",
+        "config": {"workload": "all 127 neighborhoods, L=16 (1,048,576 sites); each step a bounded sample of "
+                               f"{per_step} seeds x 127 masks", "L": L, "masks": 127},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": workers, "kind": "oracle",
+                         "sample": f"{args.steps} steps x {per_step} seeds x 127 masks at L=16"},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--num-seeds", type=int, default=NUM_SEEDS)
+    ap.add_argument("--train-seeds", type=int, default=64)
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--margin", type=float, default=0.05)
+    ap.add_argument("--cpu-seeds-per-worker", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * perc.h -- C ABI of libperc.so: exact, batched first-spanning search and largest-cluster mass
+ * for random site percolation on the 5D simple cubic lattice with complex neighborhoods
+ * (neighborhood = any non-empty union of coordination zones 1..7, eq. z / eq. zeta, Table I).
+ *
+ * The quantities are those of the paper's Newman--Ziff study (Methods, "Computational methods";
+ * eq. Pmax; Introduction):
+ *   - a sample is a lattice side L, a zone mask and a random site-addition order;
+ *   - n* is the smallest number n of occupied sites (the first n in that order) for which one
+ *     cluster touches both borders x1 = 0 and x1 = L-1 (open boundaries);
+ *   - S_max(n) is the size of the largest cluster with the first n sites occupied.
+ * The order of a sample with seed s sorts the sites ascending by (key_i, i), where key_i is word 0
+ * of Philox4x32-10 with counter (i, 0, 0, 0) and key (s mod 2^32, s >> 32), and
+ * i = (((x1*L + x2)*L + x3)*L + x4)*L + x5.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "device" are caller-owned device memory; "host" pointers are read during
+ *     the call only.  The library never allocates device memory: the caller sizes the workspace
+ *     with perc_workspace_bytes() and passes it in.
+ *   - Every call that takes a stream only enqueues work on it and returns; it is capturable in a
+ *     CUDA graph.  Arguments that the host can check are checked before any launch
+ *     (PERC_EINVAL / PERC_EWORKSPACE).  Errors found on the device (a sample with an invalid L or
+ *     mask, a bounded wait that ran out) are written to a status word in the workspace;
+ *     perc_check() synchronises the stream and returns it.
+ *   - Returns PERC_OK (0) or a negative perc_status.
+ */
+#ifndef PERC_H
+#define PERC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PERC_OK = 0,
+    PERC_EINVAL = -1,     /* bad argument (L, mask, n, sizes, null pointer) */
+    PERC_EWORKSPACE = -2, /* workspace smaller than perc_workspace_bytes() */
+    PERC_ECUDA = -3,      /* a CUDA runtime call failed */
+    PERC_ETIMEOUT = -4,   /* a bounded device-side wait ran out */
+    PERC_EDEVICE = -5     /* a device-side check failed (bad sample found on the device) */
+} perc_status;
+
+/* n* of a sample in which no n spans (e.g. L = 2 with zones 6 and 7 only). */
+#define PERC_NEVER 0xFFFFFFFFu
+
+/* Largest lattice side: L^5 + 2 must stay below 2^31 (union-find node indices keep bit 31 free). */
+#define PERC_MAX_L 73u
+
+/* Operation codes for perc_workspace_bytes(). */
+#define PERC_OP_RANK 1
+#define PERC_OP_NSTAR 2
+#define PERC_OP_MASS 3
+
+/* One sample.  perm/rank are this sample's site order (as written by perc_rank); samples that
+ * share a seed point at the same arrays.  Layout: 24 bytes, 8-byte aligned. */
+typedef struct {
+    uint32_t L;           /* lattice side, 1 <= L <= max_L given to the call */
+    uint32_t zone_mask;   /* bit (i-1) selects coordination zone i; 1..127 */
+    const uint32_t *perm; /* device [L^5]: perm[r] = site added r-th */
+    const uint32_t *rank; /* device [L^5]: rank[perm[r]] = r */
+} perc_sample;
+
+/* Optional counters a call can accumulate into (device, zero them before the call). */
+typedef struct {
+    unsigned long long passes;      /* connected-component passes (bisection probes) */
+    unsigned long long new_sites;   /* sites merged into the union-find over all passes */
+    unsigned long long probe_sites; /* sum over passes of the probe's n */
+    unsigned long long hooks;       /* successful union-find hooks */
+    unsigned long long early_exits; /* passes that stopped as soon as a spanning cluster formed */
+    unsigned long long fallbacks;   /* learned brackets that failed verification */
+    unsigned long long verified;    /* learned brackets that passed verification */
+    unsigned long long reserved;
+} perc_stats;
+
+/*
+ * Workspace bytes that `op` needs for a batch of `num` items (seeds for PERC_OP_RANK, samples
+ * otherwise) whose largest lattice side is max_L.  Returns 0 for invalid arguments.
+ */
+size_t perc_workspace_bytes(int op, uint32_t max_L, uint32_t num);
+
+/*
+ * perc_rank -- the random addition order of the Newman--Ziff method (Methods, "Computational
+ * methods"), one per seed: perm[s][r] = the site with the r-th smallest (key, index) for seed
+ * seeds[s], and rank[s][perm[s][r]] = r.  The order does not depend on the neighborhood, so one
+ * ranking serves all 127 masks.
+ *   L          lattice side, 1..PERC_MAX_L
+ *   seeds      device uint64[num_seeds]
+ *   perm, rank device uint32[num_seeds][L^5] (outputs, row s for seed s)
+ * Errors: PERC_EINVAL (L out of range, num_seeds 0, null pointer), PERC_EWORKSPACE.
+ */
+int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, uint32_t *perm,
+              uint32_t *rank, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * perc_nstar -- exact first spanning n per sample (Introduction: the spanning cluster appears
+ * for the first time at the threshold; Methods: clusters of the first n sites).  Bisection over
+ * n; every probe is one connected-component pass (union-find with hooking and pointer jumping)
+ * over the occupied sites of the probe.
+ *   samples     device perc_sample[num_samples]
+ *   max_L       host bound on every sample's L (sizes the launch and the workspace)
+ *   bracket     device uint32[num_samples][2] = (lo, hi) proposed by a model, or NULL for the plain
+ *               bracket [1, L^5].  A bracket is verified (span(hi) and not span(lo-1)); one that
+ *               fails, or is malformed, falls back to the plain bracket, so n* stays exact.
+ *   nstar       device uint32[num_samples] (output; PERC_NEVER when nothing spans)
+ *   passes      device uint32[num_samples] (output, may be NULL): passes spent on each sample
+ *   stats       device perc_stats (accumulated, may be NULL)
+ * Errors: PERC_EINVAL, PERC_EWORKSPACE, PERC_ECUDA; samples that fail the device check get
+ * n* = PERC_NEVER and set PERC_EDEVICE in the status word.
+ */
+int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+               const uint32_t *bracket, uint32_t *nstar, uint32_t *passes, perc_stats *stats,
+               void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * perc_mass -- largest-cluster size S_max(n) of each sample with its first n[k] sites occupied
+ * (eq. Pmax; eq. M_vs_L uses it at n = p_c L^5).
+ *   n     device uint64[num_samples], 0 <= n[k] <= L^5 (larger n is a device-side error)
+ *   mass  device int64[num_samples] (output)
+ */
+int perc_mass(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+              const uint64_t *n, int64_t *mass, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * perc_check -- synchronise `stream`, read and clear the device status word of `workspace`
+ * (written by perc_nstar / perc_mass), and return it (PERC_OK if nothing went wrong).
+ */
+int perc_check(void *workspace, void *stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Learned bisection bracket.  Not in the paper: a small network maps a sample's zone-mask bits */
+/* and ln L to three quantiles of ln(n* / L^5) (taus 0.01, 0.5, 0.99). Parameters are FP32 in  */
+/* the flat layout W1[64][8], b1[64], W2[64][64], b2[64], W3[3][64], b3[3] (4931 floats);      */
+/* features are rows of 8 floats [bit0..bit6 of the mask, ln L].                               */
+/* ---------------------------------------------------------------------------------------- */
+#define PERC_MLP_NPARAM 4931
+
+/* Q[B][3] = network(X[B][8]).  All pointers device. */
+int perc_mlp_forward(const float *params, const float *X, uint32_t B, float *Q, void *stream);
+
+/* grad[4931] = d/dparams of the mean pinball loss over the batch (overwritten, not accumulated);
+ * loss (device float, may be NULL) = that loss.  y[B] are the targets ln(n* / L^5). */
+int perc_mlp_grad(const float *params, const float *X, const float *y, uint32_t B, float *grad,
+                  float *loss, void *stream);
+
+/* One Adam step (Kingma and Ba) at step count t >= 1 on n parameters, in place. */
+int perc_adam(float *params, const float *grad, float *m, float *v, uint32_t n, uint32_t t,
+              float lr, float beta1, float beta2, float eps, void *stream);
+
+/* `steps` full-batch Adam steps from step count t0 + 1; grad is a device scratch of 4931 floats;
+ * losses (device float[steps], may be NULL) receives the loss before each step. */
+int perc_mlp_train(float *params, float *m, float *v, float *grad, const float *X, const float *y,
+                   uint32_t B, uint32_t t0, uint32_t steps, float lr, float *losses, void *stream);
+
+/* bracket[k] = (lo, hi) for samples[k]: lo = floor(N e^(q0 - margin)), hi = ceil(N e^(q2 + margin)),
+ * N = L^5, clamped to 1 <= lo <= hi <= N. */
+int perc_bracket(const float *params, const perc_sample *samples, uint32_t num_samples,
+                 float margin, uint32_t *bracket, void *stream);
+
+/* Human-readable name of a perc_status value. */
+const char *perc_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PERC_H */

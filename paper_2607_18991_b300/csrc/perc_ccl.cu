@@ -1,0 +1,561 @@
+// perc_ccl.cu -- exact first-spanning n* (bisection over connected-component passes) and
+// largest-cluster mass S_max(n) for 5D site percolation with complex neighborhoods.
+//
+// What is computed (paper: Introduction -- the spanning cluster appears for the first time at the
+// threshold; Methods, "Computational methods" -- clusters of the first n sites of a random
+// addition order; eq. Pmax -- S_max):
+//   span(n) = some cluster of the sites with rank < n touches both x1 = 0 and x1 = L-1,
+//   n*      = min { n : span(n) },  S_max(n) = size of the largest such cluster.
+// span(n) is monotone in n (sites are only added), so n* is found by bisection; every probe is one
+// connected-component pass.
+//
+// Design (one CTA per sample, persistent over a queue of samples):
+//   * occupancy bitmap of the probe's n: 1 bit per site, in shared memory when L^5/8 bytes fit
+//     (L <= 17: 177 KiB), otherwise in a per-CTA global slot; it is updated incrementally from the
+//     rank prefix (set bits for ranks [n_old, n), clear them for [n, n_old));
+//   * union-find in rank space: node r + 2 is the site of rank r, so a probe at n touches only n + 2
+//     nodes; nodes 0 and 1 are the two borders (LO: x1 = 0, HI: x1 = L-1), and span(n) holds iff
+//     node 1 has been hooked (it can only be hooked under node 0, the only smaller index);
+//   * hooking: atomicCAS of the larger root onto the smaller root; pointer jumping: path halving
+//     in every find;
+//   * neighborhood offsets from the compile-time zone table in constant memory, expanded per
+//     sample into (linear delta, 25-bit validity one-hot) pairs in shared memory;
+//   * incremental probes: the union-find of the last non-spanning probe n_b is kept, and a probe
+//     at n > n_b only merges the sites of rank [n_b, n) (each with its occupied neighbors of
+//     smaller rank, the Newman--Ziff rule).  Hooks of roots that existed at n_b are tagged (bit
+//     31) and logged; a spanning probe is undone by resetting the logged roots, a non-spanning
+//     probe is committed by clearing their tags.  Path halving never shortcuts a tagged edge of
+//     an old node, so the committed forest stays valid;
+//   * a spanning probe stops as soon as node 1 is hooked (early exit), since span is decided.
+#include <cstdio>
+#include <cstdlib>
+
+#include "perc_common.cuh"
+
+namespace perc {
+
+constexpr uint32_t kTag = 0x80000000u;
+constexpr uint32_t kSmemBitmapMaxL = 17;
+constexpr size_t kSlotCapBytes = size_t(32) << 30;  // total per-CTA slot memory aimed at
+
+__constant__ ZoneTable c_zones = kZones;
+
+struct WsHeader {
+    int status;
+    uint32_t queue;
+    uint32_t pad[62];
+};
+static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
+
+struct Ctl {
+    uint32_t sample;
+    uint32_t mid;     // probe n
+    uint32_t nb;      // n of the committed (non-spanning) union-find
+    uint32_t bm_n;    // n the bitmap currently holds
+    uint32_t stop;    // early-exit flag of the running pass
+    uint32_t logn;    // undo-log length
+    uint32_t span;    // result of the last pass
+    uint32_t bad;     // sample failed validation
+    uint32_t z;       // offsets of the sample's neighborhood
+    uint32_t gshift;  // log2 of the threads that share one site
+    unsigned long long hooks, new_sites;
+};
+
+// ------------------------------------------------------------------------------------------------
+// union-find on rank-space nodes (global memory, L2-coherent loads)
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_cg(const uint32_t *p) { return __ldcg(p); }
+
+// Root of x with path halving.  Nodes below nold existed at the committed state: their pointer is
+// rewritten only when both skipped edges are untagged (committed edges).
+__device__ __forceinline__ uint32_t uf_find(uint32_t *P, uint32_t x, uint32_t nold)
+{
+    for (;;) {
+        const uint32_t p = ld_cg(P + x);
+        const uint32_t pu = p & ~kTag;
+        if (pu == x) return x;
+        const uint32_t g = ld_cg(P + pu);
+        const uint32_t gu = g & ~kTag;
+        if (gu == pu) return pu;
+        if (x >= nold || ((p | g) & kTag) == 0u) __stcg(P + x, gu);
+        x = gu;
+    }
+}
+
+// Merge the clusters of a and b; returns true if a hook was made.
+__device__ __forceinline__ bool uf_unite(uint32_t *P, uint32_t a, uint32_t b, uint32_t nold,
+                                         uint32_t *logb, uint32_t *logn)
+{
+    a = uf_find(P, a, nold);
+    b = uf_find(P, b, nold);
+    while (a != b) {
+        const uint32_t hi = a > b ? a : b;
+        const uint32_t lo = a > b ? b : a;
+        const bool old = hi < nold;
+        const uint32_t seen = atomicCAS(P + hi, hi, old ? (lo | kTag) : lo);
+        if (seen == hi) {
+            if (old) logb[atomicAdd(logn, 1u)] = hi;
+            return true;
+        }
+        a = uf_find(P, seen & ~kTag, nold);  // hi was hooked meanwhile: continue from its root
+        b = uf_find(P, lo, nold);
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------------------------------------
+// per-sample setup: offsets of the neighborhood for this L
+// ------------------------------------------------------------------------------------------------
+__device__ uint32_t build_offsets(uint32_t mask, uint32_t L, NbrEntry *tab)
+{
+    uint32_t z = 0;
+    for (int zone = 0; zone < kZoneCount; ++zone)
+        if (mask & (1u << zone)) z += c_zones.start[zone + 1] - c_zones.start[zone];
+    for (uint32_t v = threadIdx.x; v < z; v += blockDim.x) {
+        uint32_t k = v;
+        uint32_t packed = 0;
+        for (int zone = 0; zone < kZoneCount; ++zone) {
+            if (!(mask & (1u << zone))) continue;
+            const uint32_t cnt = c_zones.start[zone + 1] - c_zones.start[zone];
+            if (k < cnt) {
+                packed = c_zones.vec[c_zones.start[zone] + k];
+                break;
+            }
+            k -= cnt;
+        }
+        tab[v] = make_nbr_entry(packed, L);
+    }
+    return z;
+}
+
+__device__ __forceinline__ uint32_t site_allowed(const uint32_t x[5], uint32_t L)
+{
+    return allowed_bits(x[0], L) | (allowed_bits(x[1], L) << 5) | (allowed_bits(x[2], L) << 10) |
+           (allowed_bits(x[3], L) << 15) | (allowed_bits(x[4], L) << 20);
+}
+
+template <bool kSmemBm>
+__device__ __forceinline__ uint32_t bm_test(const uint32_t *bm, uint32_t j)
+{
+    const uint32_t w = kSmemBm ? bm[j >> 5] : ld_cg(bm + (j >> 5));
+    return (w >> (j & 31u)) & 1u;
+}
+
+// Bitmap of the first n sites moves from bm_n to n.
+__device__ void bitmap_update(uint32_t *bm, const uint32_t *perm, uint32_t bm_n, uint32_t n)
+{
+    if (n > bm_n) {
+        for (uint32_t r = bm_n + threadIdx.x; r < n; r += blockDim.x) {
+            const uint32_t i = __ldg(perm + r);
+            atomicOr(bm + (i >> 5), 1u << (i & 31u));
+        }
+    } else {
+        for (uint32_t r = n + threadIdx.x; r < bm_n; r += blockDim.x) {
+            const uint32_t i = __ldg(perm + r);
+            atomicAnd(bm + (i >> 5), ~(1u << (i & 31u)));
+        }
+    }
+}
+
+// Merge the sites of rank [r0, r1) with their occupied neighbors of smaller rank.  With kFaces the
+// border nodes take part and the pass stops early once node 1 is hooked.
+template <bool kSmemBm, bool kFaces>
+__device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, const uint32_t *bm,
+                           const NbrEntry *tab, const uint32_t *perm, const uint32_t *rank,
+                           uint32_t L, const FastDiv &fd, uint32_t r0, uint32_t r1, uint32_t nold)
+{
+    const uint32_t gshift = c.gshift;
+    const uint32_t gsize = 1u << gshift;
+    const uint32_t grp = threadIdx.x >> gshift;
+    const uint32_t gl = threadIdx.x & (gsize - 1u);
+    const uint32_t ngrp = blockDim.x >> gshift;
+    const uint32_t z = c.z;
+    uint32_t hooks = 0, iter = 0;
+    for (uint32_t r = r0 + grp; r < r1; r += ngrp) {
+        if (kFaces && *reinterpret_cast<volatile uint32_t *>(&c.stop)) break;
+        const uint32_t i = __ldg(perm + r);
+        uint32_t x[5];
+        site_coords(i, fd, x);
+        const uint32_t allowed = site_allowed(x, L);
+        const uint32_t node = r + 2u;
+        if (kFaces && gl == 0u) {
+            if (x[0] == 0u) hooks += uf_unite(P, node, 0u, nold, logb, &c.logn);
+            if (x[0] == L - 1u) hooks += uf_unite(P, node, 1u, nold, logb, &c.logn);
+        }
+        for (uint32_t v = gl; v < z; v += gsize) {
+            const NbrEntry e = tab[v];
+            if ((e.onehot & ~allowed) != 0u) continue;
+            const uint32_t j = i + static_cast<uint32_t>(e.delta);
+            if (!bm_test<kSmemBm>(bm, j)) continue;
+            const uint32_t rj = __ldg(rank + j);
+            if (rj < r) hooks += uf_unite(P, node, rj + 2u, nold, logb, &c.logn);
+        }
+        if (kFaces && gl == 0u && ((++iter & 3u) == 0u) && ld_cg(P + 1) != 1u)
+            *reinterpret_cast<volatile uint32_t *>(&c.stop) = 1u;
+    }
+    if (hooks) atomicAdd(&c.hooks, static_cast<unsigned long long>(hooks));
+}
+
+__device__ __forceinline__ uint32_t gshift_for(uint32_t z)
+{
+    uint32_t s = 0;
+    while (s < 5u && (2u << s) <= z) ++s;  // largest power of two <= z, at most 32
+    return s;
+}
+
+struct SlotPtrs {
+    uint32_t *P, *logb, *gbm;
+};
+
+__device__ __forceinline__ SlotPtrs slot_ptrs(char *ws, size_t slot_bytes, uint64_t Ncap, bool gbm)
+{
+    char *base = ws + sizeof(WsHeader) + size_t(blockIdx.x) * slot_bytes;
+    const size_t nodes = ((Ncap + 2) * 4 + 255) & ~size_t(255);
+    SlotPtrs s;
+    s.P = reinterpret_cast<uint32_t *>(base);
+    s.logb = reinterpret_cast<uint32_t *>(base + nodes);
+    s.gbm = gbm ? reinterpret_cast<uint32_t *>(base + 2 * nodes) : nullptr;
+    return s;
+}
+
+// One connected-component pass of the bisection at n = c.mid (all threads).  Returns span(mid).
+template <bool kSmemBm>
+__device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, uint32_t *bm, const NbrEntry *tab,
+                          const uint32_t *perm, const uint32_t *rank, uint32_t L, const FastDiv &fd)
+{
+    const uint32_t mid = c.mid, nb = c.nb, bm_n = c.bm_n;
+    bitmap_update(bm, perm, bm_n, mid);
+    for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x) __stcg(P + r + 2u, r + 2u);
+    __syncthreads();
+    union_pass<kSmemBm, true>(c, P, logb, bm, tab, perm, rank, L, fd, nb, mid, nb + 2u);
+    __syncthreads();
+    const uint32_t span = ld_cg(P + 1) != 1u;
+    const uint32_t logn = c.logn;
+    __syncthreads();  // every thread has read span before node 1 may be reset below
+    for (uint32_t k = threadIdx.x; k < logn; k += blockDim.x) {
+        const uint32_t b = logb[k];
+        __stcg(P + b, span ? b : (ld_cg(P + b) & ~kTag));  // undo, or commit the hook
+    }
+    __syncthreads();
+    return span;
+}
+
+__global__ void __launch_bounds__(1024, 1)
+k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L,
+        const uint32_t *__restrict__ bracket, uint32_t *__restrict__ nstar_out,
+        uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    NbrEntry *tab = reinterpret_cast<NbrEntry *>(dyn);
+    uint32_t *sbm = reinterpret_cast<uint32_t *>(dyn + kMaxOffsets * sizeof(NbrEntry));
+    __shared__ Ctl c;
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+    const uint64_t Ncap = num_sites(max_L);
+    const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
+    uint32_t *P = sp.P, *logb = sp.logb;
+    unsigned long long tot_passes = 0, tot_probe = 0, tot_early = 0, tot_fb = 0, tot_ok = 0;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            c.sample = atomicAdd(&hdr->queue, 1u);
+            c.hooks = 0;
+            c.new_sites = 0;
+        }
+        __syncthreads();
+        const uint32_t s = c.sample;
+        if (s >= num) break;
+        const perc_sample smp = samples[s];
+        const uint32_t L = smp.L, mask = smp.zone_mask;
+        if (L < 1u || L > max_L || mask < 1u || mask > 127u || !smp.perm || !smp.rank) {
+            if (threadIdx.x == 0) {
+                nstar_out[s] = PERC_NEVER;
+                if (passes_out) passes_out[s] = 0;
+                set_status(&hdr->status, PERC_EDEVICE);
+            }
+            __syncthreads();
+            continue;
+        }
+        const uint32_t N = static_cast<uint32_t>(num_sites(L));
+        const bool smem_bm = L <= smem_L;
+        uint32_t *bm = smem_bm ? sbm : sp.gbm;
+        const uint32_t words = (N + 31u) >> 5;
+        const uint32_t z = build_offsets(mask, L, tab);
+        for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
+        if (threadIdx.x == 0) {
+            __stcg(P + 0, 0u);
+            __stcg(P + 1, 1u);
+            c.z = z;
+            c.gshift = gshift_for(z);
+        }
+        const FastDiv fd = make_fastdiv(L);
+        __syncthreads();
+
+        // bisection state (every thread keeps the same copy; all decisions are block-uniform)
+        const uint32_t n_top = (L <= 2u) ? N + 1u : N;  // span(N) holds for every mask when L >= 3
+        uint32_t lo = 1, hi = n_top, nb = 0, bm_n = 0, npass = 0;
+        int stage = 2;  // 0: verify lo-1, 1: verify hi, 2: bisect
+        uint32_t blo = 0, bhi = 0;
+        if (bracket) {
+            blo = bracket[2 * size_t(s)];
+            bhi = bracket[2 * size_t(s) + 1];
+            if (blo >= 1u && blo <= bhi && bhi <= N)
+                stage = blo > 1u ? 0 : 1;
+            else
+                ++tot_fb;
+        }
+        for (;;) {
+            uint32_t mid;
+            if (stage == 0)
+                mid = blo - 1u;
+            else if (stage == 1)
+                mid = bhi;
+            else if (lo < hi)
+                mid = lo + (hi - lo) / 2u;
+            else
+                break;
+            if (threadIdx.x == 0) {
+                c.mid = mid;
+                c.nb = nb;
+                c.bm_n = bm_n;
+                c.stop = 0;
+                c.logn = 0;
+                c.new_sites += mid - nb;
+            }
+            __syncthreads();
+            const uint32_t span = smem_bm ? probe<true>(c, P, logb, bm, tab, smp.perm, smp.rank, L, fd)
+                                          : probe<false>(c, P, logb, bm, tab, smp.perm, smp.rank, L, fd);
+            ++npass;
+            tot_probe += mid;
+            if (span && c.stop) ++tot_early;
+            bm_n = mid;
+            if (!span) nb = mid;
+            if (stage == 0) {
+                if (span) { stage = 2; lo = 1; hi = n_top; nb = 0; ++tot_fb; }
+                else stage = 1;
+            } else if (stage == 1) {
+                if (!span) { stage = 2; lo = 1; hi = n_top; nb = 0; ++tot_fb; }
+                else { stage = 2; lo = blo; hi = bhi; ++tot_ok; }
+            } else if (span) {
+                hi = mid;
+            } else {
+                lo = mid + 1u;
+            }
+            __syncthreads();  // c.stop / c.logn are rewritten by thread 0 next round
+        }
+        if (threadIdx.x == 0) {
+            nstar_out[s] = (lo == N + 1u) ? PERC_NEVER : lo;
+            if (passes_out) passes_out[s] = npass;
+            tot_passes += npass;
+            if (stats) {
+                atomicAdd(&stats->hooks, c.hooks);
+                atomicAdd(&stats->new_sites, c.new_sites);
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && stats) {
+        atomicAdd(&stats->passes, tot_passes);
+        atomicAdd(&stats->probe_sites, tot_probe);
+        atomicAdd(&stats->early_exits, tot_early);
+        atomicAdd(&stats->fallbacks, tot_fb);
+        atomicAdd(&stats->verified, tot_ok);
+    }
+}
+
+// S_max(n) per sample: one full pass over the first n sites, then cluster sizes by root counting.
+__global__ void __launch_bounds__(1024, 1)
+k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L,
+       const uint64_t *__restrict__ n_in, int64_t *__restrict__ mass_out, char *ws, size_t slot_bytes)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    NbrEntry *tab = reinterpret_cast<NbrEntry *>(dyn);
+    uint32_t *sbm = reinterpret_cast<uint32_t *>(dyn + kMaxOffsets * sizeof(NbrEntry));
+    __shared__ Ctl c;
+    __shared__ uint32_t red[32];
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+    const uint64_t Ncap = num_sites(max_L);
+    const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
+    uint32_t *P = sp.P, *cnt = sp.logb;
+
+    for (;;) {
+        if (threadIdx.x == 0) c.sample = atomicAdd(&hdr->queue, 1u);
+        __syncthreads();
+        const uint32_t s = c.sample;
+        if (s >= num) break;
+        const perc_sample smp = samples[s];
+        const uint32_t L = smp.L, mask = smp.zone_mask;
+        const uint64_t n64 = n_in[s];
+        if (L < 1u || L > max_L || mask < 1u || mask > 127u || !smp.perm || !smp.rank ||
+            n64 > num_sites(L)) {
+            if (threadIdx.x == 0) {
+                mass_out[s] = -1;
+                set_status(&hdr->status, PERC_EDEVICE);
+            }
+            __syncthreads();
+            continue;
+        }
+        const uint32_t N = static_cast<uint32_t>(num_sites(L));
+        const uint32_t n = static_cast<uint32_t>(n64);
+        const bool smem_bm = L <= smem_L;
+        uint32_t *bm = smem_bm ? sbm : sp.gbm;
+        const uint32_t words = (N + 31u) >> 5;
+        const uint32_t z = build_offsets(mask, L, tab);
+        for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
+        if (threadIdx.x == 0) {
+            c.z = z;
+            c.gshift = gshift_for(z);
+            c.logn = 0;
+            c.stop = 0;
+        }
+        const FastDiv fd = make_fastdiv(L);
+        __syncthreads();
+        bitmap_update(bm, smp.perm, 0u, n);
+        for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) {
+            __stcg(P + r + 2u, r + 2u);
+            __stcg(cnt + r + 2u, 0u);
+        }
+        __syncthreads();
+        if (smem_bm)
+            union_pass<true, false>(c, P, nullptr, bm, tab, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+        else
+            union_pass<false, false>(c, P, nullptr, bm, tab, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+        __syncthreads();
+        for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) atomicAdd(cnt + uf_find(P, r + 2u, 0u), 1u);
+        __syncthreads();
+        uint32_t best = 0;
+        for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) best = max(best, ld_cg(cnt + r + 2u));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t b = 0;
+            for (uint32_t w = 0; w < (blockDim.x >> 5); ++w) b = max(b, red[w]);
+            mass_out[s] = static_cast<int64_t>(b);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// host side: launch configuration and workspace layout
+// ------------------------------------------------------------------------------------------------
+struct LaunchCfg {
+    int threads = 0;
+    size_t smem = 0;
+    uint32_t smem_L = 0;
+    uint32_t grid = 0;
+    size_t slot_bytes = 0;
+};
+
+static int env_int(const char *name, int dflt)
+{
+    const char *v = getenv(name);
+    return v ? atoi(v) : dflt;
+}
+
+static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
+{
+    if (max_L < 1 || max_L > PERC_MAX_L || num == 0) return PERC_EINVAL;
+    const uint64_t Ncap = num_sites(max_L);
+    cfg.smem_L = max_L < kSmemBitmapMaxL ? max_L : kSmemBitmapMaxL;
+    const uint64_t smem_sites = num_sites(cfg.smem_L);
+    cfg.smem = kMaxOffsets * sizeof(NbrEntry) + ((smem_sites + 31) / 32) * 4;
+    int dflt_threads = max_L <= 8 ? 256 : (max_L <= 12 ? 512 : 1024);
+    cfg.threads = env_int("PERC_THREADS", dflt_threads);
+    if (cfg.threads < 32 || cfg.threads > 1024 || (cfg.threads & 31)) return PERC_EINVAL;
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PERC_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PERC_ECUDA;
+    const void *fn = op == PERC_OP_MASS ? reinterpret_cast<const void *>(k_mass)
+                                        : reinterpret_cast<const void *>(k_nstar);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cfg.smem)) != cudaSuccess)
+        return PERC_ECUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, cfg.threads, cfg.smem) != cudaSuccess)
+        return PERC_ECUDA;
+    if (occ < 1) return PERC_EINVAL;
+    const size_t nodes = ((Ncap + 2) * 4 + 255) & ~size_t(255);
+    const size_t gbm = max_L > cfg.smem_L ? ((Ncap / 32 + 2) * 4 + 255) & ~size_t(255) : 0;
+    cfg.slot_bytes = 2 * nodes + gbm;
+    uint64_t grid = uint64_t(sms) * occ;
+    const int cap = env_int("PERC_MAX_CTAS", 0);
+    if (cap > 0 && uint64_t(cap) < grid) grid = cap;
+    if (grid > num) grid = num;
+    const uint64_t mem_cap = kSlotCapBytes / cfg.slot_bytes;
+    if (grid > mem_cap) grid = mem_cap > 0 ? mem_cap : 1;
+    cfg.grid = static_cast<uint32_t>(grid);
+    return PERC_OK;
+}
+
+}  // namespace perc
+
+using namespace perc;
+
+extern "C" size_t perc_workspace_bytes(int op, uint32_t max_L, uint32_t num)
+{
+    if (op == PERC_OP_RANK) {
+        if (max_L < 1 || max_L > PERC_MAX_L || num == 0) return 0;
+        return rank_workspace_bytes(max_L, num);
+    }
+    if (op != PERC_OP_NSTAR && op != PERC_OP_MASS) return 0;
+    LaunchCfg cfg;
+    if (launch_cfg(op, max_L, num, cfg) != PERC_OK) return 0;
+    return sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes;
+}
+
+extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                          const uint32_t *bracket, uint32_t *nstar, uint32_t *passes, perc_stats *stats,
+                          void *workspace, size_t ws_bytes, void *stream_)
+{
+    if (!samples || !nstar || !workspace || num_samples == 0) return PERC_EINVAL;
+    LaunchCfg cfg;
+    int rc = launch_cfg(PERC_OP_NSTAR, max_L, num_samples, cfg);
+    if (rc != PERC_OK) return rc;
+    if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
+    k_nstar<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, bracket,
+                                                         nstar, passes, stats, static_cast<char *>(workspace),
+                                                         cfg.slot_bytes);
+    return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
+}
+
+extern "C" int perc_mass(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                         const uint64_t *n, int64_t *mass, void *workspace, size_t ws_bytes, void *stream_)
+{
+    if (!samples || !n || !mass || !workspace || num_samples == 0) return PERC_EINVAL;
+    LaunchCfg cfg;
+    int rc = launch_cfg(PERC_OP_MASS, max_L, num_samples, cfg);
+    if (rc != PERC_OK) return rc;
+    if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
+    k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, n, mass,
+                                                        static_cast<char *>(workspace), cfg.slot_bytes);
+    return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
+}
+
+extern "C" int perc_check(void *workspace, void *stream_)
+{
+    if (!workspace) return PERC_EINVAL;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return PERC_ECUDA;
+    int status = 0;
+    if (cudaMemcpy(&status, workspace, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PERC_ECUDA;
+    const int zero = 0;
+    if (cudaMemcpy(workspace, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return PERC_ECUDA;
+    return status;
+}
+
+extern "C" const char *perc_status_string(int status)
+{
+    switch (status) {
+    case PERC_OK: return "ok";
+    case PERC_EINVAL: return "invalid argument";
+    case PERC_EWORKSPACE: return "workspace too small";
+    case PERC_ECUDA: return "CUDA runtime error";
+    case PERC_ETIMEOUT: return "bounded device wait ran out";
+    case PERC_EDEVICE: return "device-side check failed (invalid sample)";
+    default: return "unknown status";
+    }
+}

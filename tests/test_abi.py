@@ -1,0 +1,51 @@
+"""The C ABI library builds, loads without a GPU and exports every entry point of include/perc.h."""
+import os
+import re
+import subprocess
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "perc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(perc_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("perc_rank", "perc_nstar", "perc_mass", "perc_workspace_bytes", "perc_check",
+                 "perc_status_string", "perc_bracket", "perc_mlp_train"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2607_18991_b300 import build, perc
+    build.build()
+    lib = perc.lib()
+    out = subprocess.run(["nm", "-D", "--defined-only", perc.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (perc_\w+)$", out, flags=re.M))
+    for name in declared_functions():
+        assert name in exported, name
+        assert getattr(lib, name) is not None
+    assert set(perc.exported_symbols()) <= exported
+
+
+def test_status_strings_without_gpu():
+    from paper_2607_18991_b300 import perc
+    assert perc.status_string(0) == "ok"
+    assert "workspace" in perc.status_string(-2)
+    assert perc.status_string(-99) == "unknown status"
+
+
+def test_host_side_argument_checks_without_gpu():
+    # invalid arguments are rejected before any CUDA call, so this runs on a CPU-only machine
+    from paper_2607_18991_b300 import perc
+    lib = perc.lib()
+    assert lib.perc_rank(0, None, 1, None, None, None, 0, None) == -1
+    assert lib.perc_rank(74, 1, 1, 1, 1, 1, 1 << 30, None) == -1
+    assert lib.perc_nstar(None, 1, 8, None, None, None, None, None, 0, None) == -1
+    assert lib.perc_mass(None, 1, 8, None, None, None, 0, None) == -1
+    assert lib.perc_workspace_bytes(7, 8, 1) == 0
+    assert lib.perc_workspace_bytes(1, 0, 1) == 0
+    assert lib.perc_workspace_bytes(1, 8, 1) > 8 * 8 ** 5
