@@ -43,7 +43,8 @@ def dist_env():
 
 def workload_for(rank: int, num_seeds: int = NUM_SEEDS):
     seeds = np.arange(1, num_seeds + 1) + rank * num_seeds
-    return seeds, np.array([(L, m, int(s)) for m in MASKS for s in seeds], dtype=np.int64)
+    # seed-major: the 127 masks of a seed are adjacent, so CTAs running together share one site order
+    return seeds, np.array([(L, m, int(s)) for s in seeds for m in MASKS], dtype=np.int64)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -198,6 +199,7 @@ def run_ours(args):
         for _ in range(W):
             step(learned)
         torch.cuda.synchronize()
+        torch.cuda.profiler.start()  # an ncu run with --profile-from-start off sees only this region
         tot, t_rank, t_nstar = 0.0, 0.0, 0.0
         for _ in range(K):
             flush.zero_()
@@ -211,7 +213,21 @@ def run_ours(args):
             tot += e[3].elapsed_time(e[2])
             t_rank += e[3].elapsed_time(e[0])
             t_nstar += e[1].elapsed_time(e[2])
+        torch.cuda.profiler.stop()
         return tot / K, t_rank / K, t_nstar / K
+
+    if args.ncu_case:
+        # one learned and one plain launch inside the profiler range, nothing else (for ncu)
+        step(True)
+        step(False)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step(True)
+        step(False)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"ncu_case": True, "samples": num, "seeds": int(len(seeds))}))
+        return
 
     gpu_index = torch.cuda.current_device()
     phys = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
@@ -397,6 +413,8 @@ def main():
     ap.add_argument("--margin", type=float, default=0.05)
     ap.add_argument("--cpu-seeds-per-worker", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="run one learned and one plain step inside a profiler range and exit")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -158,11 +158,16 @@ __device__ void bitmap_update(uint32_t *bm, const uint32_t *perm, uint32_t bm_n,
 }
 
 // Merge the sites of rank [r0, r1) with their occupied neighbors of smaller rank.  With kFaces the
-// border nodes take part and the pass stops early once node 1 is hooked.
+// border nodes take part and the pass stops early once node 1 is hooked.  The threads of a group
+// share one site; each lane tests kUnroll offsets (strided by the group size) with independent
+// shared-memory loads before it handles the hits.
+constexpr int kUnroll = 8;
+
 template <bool kSmemBm, bool kFaces>
 __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, const uint32_t *bm,
-                           const NbrEntry *tab, const uint32_t *perm, const uint32_t *rank,
-                           uint32_t L, const FastDiv &fd, uint32_t r0, uint32_t r1, uint32_t nold)
+                                           const NbrEntry *tab, const uint32_t *perm, const uint32_t *rank,
+                                           uint32_t L, const FastDiv &fd, uint32_t r0, uint32_t r1,
+                                           uint32_t nold)
 {
     const uint32_t gshift = c.gshift;
     const uint32_t gsize = 1u << gshift;
@@ -182,13 +187,25 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, 
             if (x[0] == 0u) hooks += uf_unite(P, node, 0u, nold, logb, &c.logn);
             if (x[0] == L - 1u) hooks += uf_unite(P, node, 1u, nold, logb, &c.logn);
         }
-        for (uint32_t v = gl; v < z; v += gsize) {
-            const NbrEntry e = tab[v];
-            if ((e.onehot & ~allowed) != 0u) continue;
-            const uint32_t j = i + static_cast<uint32_t>(e.delta);
-            if (!bm_test<kSmemBm>(bm, j)) continue;
-            const uint32_t rj = __ldg(rank + j);
-            if (rj < r) hooks += uf_unite(P, node, rj + 2u, nold, logb, &c.logn);
+        for (uint32_t v0 = gl; v0 < z; v0 += gsize * kUnroll) {
+            uint32_t hits = 0;
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const uint32_t v = v0 + u * gsize;
+                if (v < z) {
+                    const NbrEntry e = tab[v];
+                    const bool inside = (e.onehot & ~allowed) == 0u;
+                    const uint32_t j = inside ? i + static_cast<uint32_t>(e.delta) : i;
+                    hits |= (inside ? bm_test<kSmemBm>(bm, j) : 0u) << u;
+                }
+            }
+            while (hits) {
+                const int u = __ffs(hits) - 1;
+                hits &= hits - 1u;
+                const uint32_t j = i + static_cast<uint32_t>(tab[v0 + u * gsize].delta);
+                const uint32_t rj = __ldg(rank + j);
+                if (rj < r) hooks += uf_unite(P, node, rj + 2u, nold, logb, &c.logn);
+            }
         }
         if (kFaces && gl == 0u && ((++iter & 3u) == 0u) && ld_cg(P + 1) != 1u)
             *reinterpret_cast<volatile uint32_t *>(&c.stop) = 1u;

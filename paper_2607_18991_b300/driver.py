@@ -18,7 +18,9 @@ DEFAULT_BUDGET = 24 << 30  # bytes of perm + rank per chunk
 
 def _chunks(workload: np.ndarray, budget: int):
     """Split sample indices so that the distinct (L, seed) orders of a chunk fit in `budget`."""
-    order = np.lexsort((workload[:, 2], -workload[:, 0]))  # largest L first, then by seed
+    # largest L first, then seed-major: the CTAs running at the same time share one site order,
+    # which then stays in L2 while all its masks are processed
+    order = np.lexsort((workload[:, 1], workload[:, 2], -workload[:, 0]))
     chunk, seen, used = [], set(), 0
     for idx in order:
         L, _, seed = (int(v) for v in workload[idx])

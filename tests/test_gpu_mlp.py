@@ -62,8 +62,12 @@ def test_adam_matches_oracle():
     g = rng.normal(size=4931)
     p_t, g_t, m_t, v_t = (t32(a) for a in (th, g, m, v))
     perc.adam(p_t, g_t, m_t, v_t, t=7, lr=1e-3)
+    # the kernel holds beta1, beta2, lr and eps as float32; the oracle takes the same values, so
+    # 1 - beta2 (which magnifies the float32 rounding of beta2 a thousandfold) matches
+    f = lambda a: float(np.float32(a))  # noqa: E731
     th_r, m_r, v_r = omlp.adam_step(th.astype(np.float32).astype(np.float64), g.astype(np.float32).astype(np.float64),
-                                    m.astype(np.float32).astype(np.float64), v.astype(np.float32).astype(np.float64), 7, 1e-3)
+                                    m.astype(np.float32).astype(np.float64), v.astype(np.float32).astype(np.float64), 7,
+                                    f(1e-3), b1=f(0.9), b2=f(0.999), eps=f(1e-8))
     assert np.allclose(p_t.cpu().numpy(), th_r, rtol=1e-6, atol=1e-6)
     assert np.allclose(m_t.cpu().numpy(), m_r, rtol=1e-5, atol=1e-7)
     assert np.allclose(v_t.cpu().numpy(), v_r, rtol=1e-5, atol=1e-9)
