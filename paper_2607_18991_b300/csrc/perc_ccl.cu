@@ -57,7 +57,7 @@ struct Ctl {
     uint32_t span;    // result of the last pass
     uint32_t bad;     // sample failed validation
     uint32_t z;       // offsets of the sample's neighborhood
-    uint32_t gshift;  // log2 of the threads that share one site
+    uint32_t R;       // row entries of the sample's neighborhood
     unsigned long long hooks, new_sites;
 };
 
@@ -104,16 +104,31 @@ __device__ __forceinline__ bool uf_unite(uint32_t *P, uint32_t a, uint32_t b, ui
 }
 
 // ------------------------------------------------------------------------------------------------
-// per-sample setup: offsets of the neighborhood for this L
+// per-sample setup: the neighborhood as "row offsets".  Offsets that share (d1..d4) differ only in
+// d5, i.e. they hit one x5 row of the lattice; one row entry holds the linear offset of that row,
+// the one-hot of d1..d4 (validity against the site's allowed mask) and the 5-bit set of d5 values
+// of the neighborhood.  One funnel-shifted bitmap load then tests all d5 neighbors of a row.
 // ------------------------------------------------------------------------------------------------
-__device__ uint32_t build_offsets(uint32_t mask, uint32_t L, NbrEntry *tab)
+struct __align__(16) RowEntry {
+    int32_t delta;    // ((d1*L + d2)*L + d3)*L + d4) * L
+    uint32_t onehot;  // bit 5k + d_k + 2 for k = 0..3 (x1..x4)
+    uint32_t d5mask;  // bit d5 + 2 for every d5 with (d1..d5) in the neighborhood
+    uint32_t pad;
+};
+constexpr int kRowCand = 625;  // (d1..d4) in {-2..2}^4
+constexpr int kEdgeBuf = 64;   // per-warp buffer of pending unions
+
+// Builds the row table of `mask` for side L (all threads; ends with a barrier); returns the count
+// of rows and writes the number of offsets to *z.
+__device__ uint32_t build_rows(uint32_t mask, uint32_t L, RowEntry *rows, uint32_t *scratch, Ctl &c)
 {
+    for (uint32_t t = threadIdx.x; t < kRowCand; t += blockDim.x) scratch[t] = 0u;
+    __syncthreads();
     uint32_t z = 0;
     for (int zone = 0; zone < kZoneCount; ++zone)
         if (mask & (1u << zone)) z += c_zones.start[zone + 1] - c_zones.start[zone];
     for (uint32_t v = threadIdx.x; v < z; v += blockDim.x) {
-        uint32_t k = v;
-        uint32_t packed = 0;
+        uint32_t k = v, packed = 0;
         for (int zone = 0; zone < kZoneCount; ++zone) {
             if (!(mask & (1u << zone))) continue;
             const uint32_t cnt = c_zones.start[zone + 1] - c_zones.start[zone];
@@ -123,9 +138,46 @@ __device__ uint32_t build_offsets(uint32_t mask, uint32_t L, NbrEntry *tab)
             }
             k -= cnt;
         }
-        tab[v] = make_nbr_entry(packed, L);
+        uint32_t key = 0;
+        for (int d = 0; d < 4; ++d) key = key * 5u + static_cast<uint32_t>(zone_component(packed, d) + 2);
+        atomicOr(scratch + key, 1u << (zone_component(packed, 4) + 2));
     }
-    return z;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const uint32_t lane = threadIdx.x;
+        uint32_t count = 0;
+        for (uint32_t base = 0; base < static_cast<uint32_t>(kRowCand); base += 32) {
+            const uint32_t key = base + lane;
+            const uint32_t m = key < static_cast<uint32_t>(kRowCand) ? scratch[key] : 0u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, m != 0u);
+            if (m) {
+                RowEntry e;
+                uint32_t kk = key, onehot = 0;
+                int32_t delta = 0;
+                int d[4];
+                for (int q = 3; q >= 0; --q) {
+                    d[q] = static_cast<int>(kk % 5u) - 2;
+                    kk /= 5u;
+                }
+                for (int q = 0; q < 4; ++q) {
+                    delta = delta * static_cast<int32_t>(L) + d[q];
+                    onehot |= 1u << (5 * q + d[q] + 2);
+                }
+                e.delta = delta * static_cast<int32_t>(L);
+                e.onehot = onehot;
+                e.d5mask = m;
+                e.pad = 0;
+                rows[count + __popc(bal & ((1u << lane) - 1u))] = e;
+            }
+            count += __popc(bal);
+        }
+        if (lane == 0) {
+            c.R = count;
+            c.z = z;
+        }
+    }
+    __syncthreads();
+    return c.R;
 }
 
 __device__ __forceinline__ uint32_t site_allowed(const uint32_t x[5], uint32_t L)
@@ -134,11 +186,15 @@ __device__ __forceinline__ uint32_t site_allowed(const uint32_t x[5], uint32_t L
            (allowed_bits(x[3], L) << 15) | (allowed_bits(x[4], L) << 20);
 }
 
+// Bitmap layout: bit 64 + i is site i (two zero guard words before, two after), so the 5-bit window
+// of a row starting at i - 2 never reaches below word 0.
+constexpr uint32_t kBmGuard = 64;
+__host__ __device__ inline uint32_t bm_words(uint64_t N) { return static_cast<uint32_t>((N + 2 * kBmGuard) / 32 + 1); }
+
 template <bool kSmemBm>
-__device__ __forceinline__ uint32_t bm_test(const uint32_t *bm, uint32_t j)
+__device__ __forceinline__ uint32_t bm_word(const uint32_t *bm, uint32_t k)
 {
-    const uint32_t w = kSmemBm ? bm[j >> 5] : ld_cg(bm + (j >> 5));
-    return (w >> (j & 31u)) & 1u;
+    return kSmemBm ? bm[k] : ld_cg(bm + k);
 }
 
 // Bitmap of the first n sites moves from bm_n to n.
@@ -146,78 +202,122 @@ __device__ void bitmap_update(uint32_t *bm, const uint32_t *perm, uint32_t bm_n,
 {
     if (n > bm_n) {
         for (uint32_t r = bm_n + threadIdx.x; r < n; r += blockDim.x) {
-            const uint32_t i = __ldg(perm + r);
+            const uint32_t i = __ldg(perm + r) + kBmGuard;
             atomicOr(bm + (i >> 5), 1u << (i & 31u));
         }
     } else {
         for (uint32_t r = n + threadIdx.x; r < bm_n; r += blockDim.x) {
-            const uint32_t i = __ldg(perm + r);
+            const uint32_t i = __ldg(perm + r) + kBmGuard;
             atomicAnd(bm + (i >> 5), ~(1u << (i & 31u)));
         }
     }
 }
 
-// Merge the sites of rank [r0, r1) with their occupied neighbors of smaller rank.  With kFaces the
-// border nodes take part and the pass stops early once node 1 is hooked.  The threads of a group
-// share one site; each lane tests kUnroll offsets (strided by the group size) with independent
-// shared-memory loads before it handles the hits.
-constexpr int kUnroll = 8;
+// Warp-collective: lanes with `keep` append the union (a, b) to the warp's buffer; once 32 are
+// pending, all lanes perform one union each.
+__device__ __forceinline__ void push_edge(bool keep, uint32_t a, uint32_t b, uint2 *buf, uint32_t &cnt,
+                                          uint32_t lane, uint32_t *P, uint32_t nold, uint32_t *logb,
+                                          uint32_t *logn, uint32_t &hooks)
+{
+    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+    if (bal == 0u) return;
+    if (keep) buf[cnt + __popc(bal & ((1u << lane) - 1u))] = make_uint2(a, b);
+    cnt += __popc(bal);
+    __syncwarp();
+    if (cnt >= 32u) {
+        const uint2 e = buf[lane];
+        hooks += uf_unite(P, e.x, e.y, nold, logb, logn);
+        __syncwarp();
+        if (lane + 32u < cnt) buf[lane] = buf[lane + 32u];
+        cnt -= 32u;
+        __syncwarp();
+    }
+}
+
+// log2 of the lanes that share one site in a pass that merges `count` sites: one site per lane
+// when there are enough sites for every lane, otherwise the rows of a site are split over lanes.
+__device__ __forceinline__ uint32_t lanes_shift(uint32_t count, uint32_t R)
+{
+    uint32_t s = 0;
+    while (s < 5u && (count << (s + 1)) <= blockDim.x && (1u << s) < R) ++s;
+    return s;
+}
+
+// Merge the sites of rank [r0, r1) with their occupied neighbors of smaller rank (the
+// Newman--Ziff rule: an edge is merged by its later site).  With kFaces the border nodes take part
+// and the pass stops early once node 1 is hooked.
+constexpr int kRowUnroll = 4;
 
 template <bool kSmemBm, bool kFaces>
 __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, const uint32_t *bm,
-                                           const NbrEntry *tab, const uint32_t *perm, const uint32_t *rank,
-                                           uint32_t L, const FastDiv &fd, uint32_t r0, uint32_t r1,
-                                           uint32_t nold)
+                                           const RowEntry *rows, uint2 *ebuf, const uint32_t *perm,
+                                           const uint32_t *rank, uint32_t L, const FastDiv &fd,
+                                           uint32_t r0, uint32_t r1, uint32_t nold)
 {
-    const uint32_t gshift = c.gshift;
-    const uint32_t gsize = 1u << gshift;
-    const uint32_t grp = threadIdx.x >> gshift;
-    const uint32_t gl = threadIdx.x & (gsize - 1u);
-    const uint32_t ngrp = blockDim.x >> gshift;
-    const uint32_t z = c.z;
-    uint32_t hooks = 0, iter = 0;
-    for (uint32_t r = r0 + grp; r < r1; r += ngrp) {
+    const uint32_t R = c.R;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t gshift = lanes_shift(r1 - r0, R);
+    const uint32_t gl = lane & ((1u << gshift) - 1u), gw = lane >> gshift, spw = 32u >> gshift;
+    const uint32_t niter = (R + (1u << gshift) - 1u) >> gshift;
+    uint2 *buf = ebuf + warp * kEdgeBuf;
+    uint32_t cnt = 0, hooks = 0, batch = 0;
+    for (uint32_t base = r0 + warp * spw; base < r1; base += nwarps * spw) {
         if (kFaces && *reinterpret_cast<volatile uint32_t *>(&c.stop)) break;
-        const uint32_t i = __ldg(perm + r);
+        const uint32_t r = base + gw;
+        const bool act = r < r1;
+        const uint32_t i = act ? __ldg(perm + r) : 0u;
         uint32_t x[5];
         site_coords(i, fd, x);
         const uint32_t allowed = site_allowed(x, L);
+        const uint32_t a5 = allowed >> 20;
         const uint32_t node = r + 2u;
-        if (kFaces && gl == 0u) {
-            if (x[0] == 0u) hooks += uf_unite(P, node, 0u, nold, logb, &c.logn);
-            if (x[0] == L - 1u) hooks += uf_unite(P, node, 1u, nold, logb, &c.logn);
+        if (kFaces) {
+            push_edge(act && gl == 0u && x[0] == 0u, node, 0u, buf, cnt, lane, P, nold, logb, &c.logn, hooks);
+            push_edge(act && gl == 0u && x[0] == L - 1u, node, 1u, buf, cnt, lane, P, nold, logb, &c.logn, hooks);
         }
-        for (uint32_t v0 = gl; v0 < z; v0 += gsize * kUnroll) {
-            uint32_t hits = 0;
+        const uint32_t bit0 = i + kBmGuard - 2u;  // window start of the own row, before the row offset
+        for (uint32_t t = 0; t < niter; t += kRowUnroll) {
+            uint32_t hits[kRowUnroll];
+            int32_t dl[kRowUnroll];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const uint32_t v = v0 + u * gsize;
-                if (v < z) {
-                    const NbrEntry e = tab[v];
-                    const bool inside = (e.onehot & ~allowed) == 0u;
-                    const uint32_t j = inside ? i + static_cast<uint32_t>(e.delta) : i;
-                    hits |= (inside ? bm_test<kSmemBm>(bm, j) : 0u) << u;
+            for (int u = 0; u < kRowUnroll; ++u) {
+                const uint32_t k = gl + ((t + u) << gshift);
+                const bool ok = act && k < R;
+                const RowEntry e = rows[ok ? k : 0u];
+                uint32_t h = 0u;
+                if (ok && (e.onehot & ~allowed) == 0u) {
+                    const uint32_t b = bit0 + static_cast<uint32_t>(e.delta);
+                    const uint32_t w = __funnelshift_r(bm_word<kSmemBm>(bm, b >> 5), bm_word<kSmemBm>(bm, (b >> 5) + 1u),
+                                                       b & 31u);
+                    h = w & e.d5mask & a5;
+                }
+                hits[u] = h;
+                dl[u] = e.delta;
+            }
+#pragma unroll
+            for (int u = 0; u < kRowUnroll; ++u) {
+                uint32_t h = hits[u];
+                while (__any_sync(0xffffffffu, h != 0u)) {
+                    bool keep = false;
+                    uint32_t other = 0u;
+                    if (h) {
+                        const uint32_t tb = __ffs(h) - 1;
+                        h &= h - 1u;
+                        const uint32_t j = i + static_cast<uint32_t>(dl[u]) + tb - 2u;
+                        const uint32_t rj = __ldg(rank + j);
+                        keep = rj < r;
+                        other = rj + 2u;
+                    }
+                    push_edge(keep, node, other, buf, cnt, lane, P, nold, logb, &c.logn, hooks);
                 }
             }
-            while (hits) {
-                const int u = __ffs(hits) - 1;
-                hits &= hits - 1u;
-                const uint32_t j = i + static_cast<uint32_t>(tab[v0 + u * gsize].delta);
-                const uint32_t rj = __ldg(rank + j);
-                if (rj < r) hooks += uf_unite(P, node, rj + 2u, nold, logb, &c.logn);
-            }
         }
-        if (kFaces && gl == 0u && ((++iter & 3u) == 0u) && ld_cg(P + 1) != 1u)
+        if (kFaces && lane == 0u && ((++batch & 1u) == 0u) && ld_cg(P + 1) != 1u)
             *reinterpret_cast<volatile uint32_t *>(&c.stop) = 1u;
     }
+    if (lane < cnt) hooks += uf_unite(P, buf[lane].x, buf[lane].y, nold, logb, &c.logn);
+    __syncwarp();
     if (hooks) atomicAdd(&c.hooks, static_cast<unsigned long long>(hooks));
-}
-
-__device__ __forceinline__ uint32_t gshift_for(uint32_t z)
-{
-    uint32_t s = 0;
-    while (s < 5u && (2u << s) <= z) ++s;  // largest power of two <= z, at most 32
-    return s;
 }
 
 struct SlotPtrs {
@@ -235,16 +335,43 @@ __device__ __forceinline__ SlotPtrs slot_ptrs(char *ws, size_t slot_bytes, uint6
     return s;
 }
 
+// Shared-memory carve-up: [row table][edge buffers (also the row-build scratch)][bitmap].
+struct SmemPtrs {
+    RowEntry *rows;
+    uint2 *ebuf;
+    uint32_t *scratch;
+    uint32_t *sbm;
+};
+
+__host__ __device__ inline size_t smem_fixed_bytes(uint32_t threads)
+{
+    const size_t rows = sizeof(RowEntry) * kRowCand;
+    size_t eb = size_t(threads / 32) * kEdgeBuf * sizeof(uint2);
+    if (eb < kRowCand * sizeof(uint32_t)) eb = kRowCand * sizeof(uint32_t);
+    return rows + ((eb + 15) & ~size_t(15));
+}
+
+__device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn)
+{
+    SmemPtrs p;
+    p.rows = reinterpret_cast<RowEntry *>(dyn);
+    p.ebuf = reinterpret_cast<uint2 *>(dyn + sizeof(RowEntry) * kRowCand);
+    p.scratch = reinterpret_cast<uint32_t *>(p.ebuf);
+    p.sbm = reinterpret_cast<uint32_t *>(dyn + smem_fixed_bytes(blockDim.x));
+    return p;
+}
+
 // One connected-component pass of the bisection at n = c.mid (all threads).  Returns span(mid).
 template <bool kSmemBm>
-__device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, uint32_t *bm, const NbrEntry *tab,
-                          const uint32_t *perm, const uint32_t *rank, uint32_t L, const FastDiv &fd)
+__device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, uint32_t *bm,
+                                          const SmemPtrs &sm, const uint32_t *perm, const uint32_t *rank,
+                                          uint32_t L, const FastDiv &fd)
 {
     const uint32_t mid = c.mid, nb = c.nb, bm_n = c.bm_n;
     bitmap_update(bm, perm, bm_n, mid);
     for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x) __stcg(P + r + 2u, r + 2u);
     __syncthreads();
-    union_pass<kSmemBm, true>(c, P, logb, bm, tab, perm, rank, L, fd, nb, mid, nb + 2u);
+    union_pass<kSmemBm, true>(c, P, logb, bm, sm.rows, sm.ebuf, perm, rank, L, fd, nb, mid, nb + 2u);
     __syncthreads();
     const uint32_t span = ld_cg(P + 1) != 1u;
     const uint32_t logn = c.logn;
@@ -263,8 +390,7 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
         uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
-    NbrEntry *tab = reinterpret_cast<NbrEntry *>(dyn);
-    uint32_t *sbm = reinterpret_cast<uint32_t *>(dyn + kMaxOffsets * sizeof(NbrEntry));
+    const SmemPtrs sm = smem_ptrs(dyn);
     __shared__ Ctl c;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
@@ -294,15 +420,13 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
         }
         const uint32_t N = static_cast<uint32_t>(num_sites(L));
         const bool smem_bm = L <= smem_L;
-        uint32_t *bm = smem_bm ? sbm : sp.gbm;
-        const uint32_t words = (N + 31u) >> 5;
-        const uint32_t z = build_offsets(mask, L, tab);
+        uint32_t *bm = smem_bm ? sm.sbm : sp.gbm;
+        const uint32_t words = bm_words(N);
         for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
+        build_rows(mask, L, sm.rows, sm.scratch, c);
         if (threadIdx.x == 0) {
             __stcg(P + 0, 0u);
             __stcg(P + 1, 1u);
-            c.z = z;
-            c.gshift = gshift_for(z);
         }
         const FastDiv fd = make_fastdiv(L);
         __syncthreads();
@@ -339,8 +463,8 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
                 c.new_sites += mid - nb;
             }
             __syncthreads();
-            const uint32_t span = smem_bm ? probe<true>(c, P, logb, bm, tab, smp.perm, smp.rank, L, fd)
-                                          : probe<false>(c, P, logb, bm, tab, smp.perm, smp.rank, L, fd);
+            const uint32_t span = smem_bm ? probe<true>(c, P, logb, bm, sm, smp.perm, smp.rank, L, fd)
+                                          : probe<false>(c, P, logb, bm, sm, smp.perm, smp.rank, L, fd);
             ++npass;
             tot_probe += mid;
             if (span && c.stop) ++tot_early;
@@ -385,8 +509,7 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
        const uint64_t *__restrict__ n_in, int64_t *__restrict__ mass_out, char *ws, size_t slot_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
-    NbrEntry *tab = reinterpret_cast<NbrEntry *>(dyn);
-    uint32_t *sbm = reinterpret_cast<uint32_t *>(dyn + kMaxOffsets * sizeof(NbrEntry));
+    const SmemPtrs sm = smem_ptrs(dyn);
     __shared__ Ctl c;
     __shared__ uint32_t red[32];
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
@@ -414,13 +537,11 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         const uint32_t N = static_cast<uint32_t>(num_sites(L));
         const uint32_t n = static_cast<uint32_t>(n64);
         const bool smem_bm = L <= smem_L;
-        uint32_t *bm = smem_bm ? sbm : sp.gbm;
-        const uint32_t words = (N + 31u) >> 5;
-        const uint32_t z = build_offsets(mask, L, tab);
+        uint32_t *bm = smem_bm ? sm.sbm : sp.gbm;
+        const uint32_t words = bm_words(N);
         for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
+        build_rows(mask, L, sm.rows, sm.scratch, c);
         if (threadIdx.x == 0) {
-            c.z = z;
-            c.gshift = gshift_for(z);
             c.logn = 0;
             c.stop = 0;
         }
@@ -433,9 +554,9 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         }
         __syncthreads();
         if (smem_bm)
-            union_pass<true, false>(c, P, nullptr, bm, tab, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+            union_pass<true, false>(c, P, nullptr, bm, sm.rows, sm.ebuf, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         else
-            union_pass<false, false>(c, P, nullptr, bm, tab, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+            union_pass<false, false>(c, P, nullptr, bm, sm.rows, sm.ebuf, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         __syncthreads();
         for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) atomicAdd(cnt + uf_find(P, r + 2u, 0u), 1u);
         __syncthreads();
@@ -477,10 +598,10 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
     const uint64_t Ncap = num_sites(max_L);
     cfg.smem_L = max_L < kSmemBitmapMaxL ? max_L : kSmemBitmapMaxL;
     const uint64_t smem_sites = num_sites(cfg.smem_L);
-    cfg.smem = kMaxOffsets * sizeof(NbrEntry) + ((smem_sites + 31) / 32) * 4;
     int dflt_threads = max_L <= 8 ? 256 : (max_L <= 12 ? 512 : 1024);
     cfg.threads = env_int("PERC_THREADS", dflt_threads);
     if (cfg.threads < 32 || cfg.threads > 1024 || (cfg.threads & 31)) return PERC_EINVAL;
+    cfg.smem = smem_fixed_bytes(cfg.threads) + size_t(bm_words(smem_sites)) * 4;
     int dev = 0, sms = 0, occ = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PERC_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PERC_ECUDA;
@@ -492,7 +613,7 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
         return PERC_ECUDA;
     if (occ < 1) return PERC_EINVAL;
     const size_t nodes = ((Ncap + 2) * 4 + 255) & ~size_t(255);
-    const size_t gbm = max_L > cfg.smem_L ? ((Ncap / 32 + 2) * 4 + 255) & ~size_t(255) : 0;
+    const size_t gbm = max_L > cfg.smem_L ? (size_t(bm_words(Ncap)) * 4 + 255) & ~size_t(255) : 0;
     cfg.slot_bytes = 2 * nodes + gbm;
     uint64_t grid = uint64_t(sms) * occ;
     const int cap = env_int("PERC_MAX_CTAS", 0);
