@@ -65,14 +65,20 @@ typedef struct {
 
 /* Optional counters a call can accumulate into (device, zero them before the call). */
 typedef struct {
-    unsigned long long passes;      /* connected-component passes (bisection probes) */
-    unsigned long long new_sites;   /* sites merged into the union-find over all passes */
-    unsigned long long probe_sites; /* sum over passes of the probe's n */
-    unsigned long long hooks;       /* successful union-find hooks */
-    unsigned long long early_exits; /* passes that stopped as soon as a spanning cluster formed */
-    unsigned long long fallbacks;   /* learned brackets that failed verification */
-    unsigned long long verified;    /* learned brackets that passed verification */
-    unsigned long long reserved;
+    unsigned long long passes;       /* connected-component passes (bisection probes) */
+    unsigned long long new_sites;    /* sites a pass had to merge, summed over passes (upper bound) */
+    unsigned long long probe_sites;  /* sum over passes of the probe's n */
+    unsigned long long hooks;        /* successful union-find hooks */
+    unsigned long long early_exits;  /* passes that stopped as soon as a spanning cluster formed */
+    unsigned long long fallbacks;    /* learned brackets that failed verification */
+    unsigned long long verified;     /* learned brackets that passed verification */
+    unsigned long long sites_merged; /* sites actually merged (early exits stop short) */
+    unsigned long long unions;       /* union operations issued (edges of the NZ rule, borders included) */
+    unsigned long long cyc_setup;    /* SM cycles in per-sample setup (bitmap clear, neighborhood table) */
+    unsigned long long cyc_update;   /* SM cycles updating the bitmap and initialising new nodes */
+    unsigned long long cyc_union;    /* SM cycles in the union passes */
+    unsigned long long cyc_commit;   /* SM cycles reading span and undoing / committing hooks */
+    unsigned long long reserved[3];
 } perc_stats;
 
 /*

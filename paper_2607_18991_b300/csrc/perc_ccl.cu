@@ -58,7 +58,7 @@ struct Ctl {
     uint32_t bad;     // sample failed validation
     uint32_t z;       // offsets of the sample's neighborhood
     uint32_t R;       // row entries of the sample's neighborhood
-    unsigned long long hooks, new_sites;
+    unsigned long long hooks, new_sites, sites, unions;
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -260,7 +260,7 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, 
     const uint32_t gl = lane & ((1u << gshift) - 1u), gw = lane >> gshift, spw = 32u >> gshift;
     const uint32_t niter = (R + (1u << gshift) - 1u) >> gshift;
     uint2 *buf = ebuf + warp * kEdgeBuf;
-    uint32_t cnt = 0, hooks = 0, batch = 0;
+    uint32_t cnt = 0, hooks = 0, batch = 0, sites = 0, unions = 0;
     for (uint32_t base = r0 + warp * spw; base < r1; base += nwarps * spw) {
         if (kFaces && *reinterpret_cast<volatile uint32_t *>(&c.stop)) break;
         const uint32_t r = base + gw;
@@ -271,6 +271,7 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, 
         const uint32_t allowed = site_allowed(x, L);
         const uint32_t a5 = allowed >> 20;
         const uint32_t node = r + 2u;
+        sites += (act && gl == 0u) ? 1u : 0u;
         if (kFaces) {
             push_edge(act && gl == 0u && x[0] == 0u, node, 0u, buf, cnt, lane, P, nold, logb, &c.logn, hooks);
             push_edge(act && gl == 0u && x[0] == L - 1u, node, 1u, buf, cnt, lane, P, nold, logb, &c.logn, hooks);
@@ -307,6 +308,7 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, 
                         const uint32_t rj = __ldg(rank + j);
                         keep = rj < r;
                         other = rj + 2u;
+                        unions += keep ? 1u : 0u;
                     }
                     push_edge(keep, node, other, buf, cnt, lane, P, nold, logb, &c.logn, hooks);
                 }
@@ -317,7 +319,14 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, 
     }
     if (lane < cnt) hooks += uf_unite(P, buf[lane].x, buf[lane].y, nold, logb, &c.logn);
     __syncwarp();
-    if (hooks) atomicAdd(&c.hooks, static_cast<unsigned long long>(hooks));
+    hooks = __reduce_add_sync(0xffffffffu, hooks);
+    sites = __reduce_add_sync(0xffffffffu, sites);
+    unions = __reduce_add_sync(0xffffffffu, unions);
+    if (lane == 0u) {
+        if (hooks) atomicAdd(&c.hooks, static_cast<unsigned long long>(hooks));
+        if (sites) atomicAdd(&c.sites, static_cast<unsigned long long>(sites));
+        if (unions) atomicAdd(&c.unions, static_cast<unsigned long long>(unions));
+    }
 }
 
 struct SlotPtrs {
@@ -362,17 +371,26 @@ __device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn)
 }
 
 // One connected-component pass of the bisection at n = c.mid (all threads).  Returns span(mid).
+struct PhaseClock {
+    unsigned long long update = 0, unite = 0, commit = 0, setup = 0;
+};
+
 template <bool kSmemBm>
 __device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, uint32_t *bm,
                                           const SmemPtrs &sm, const uint32_t *perm, const uint32_t *rank,
-                                          uint32_t L, const FastDiv &fd)
+                                          uint32_t L, const FastDiv &fd, PhaseClock &clk)
 {
     const uint32_t mid = c.mid, nb = c.nb, bm_n = c.bm_n;
+    const long long t0 = clock64();
     bitmap_update(bm, perm, bm_n, mid);
     for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x) __stcg(P + r + 2u, r + 2u);
     __syncthreads();
+    const long long t1 = clock64();
     union_pass<kSmemBm, true>(c, P, logb, bm, sm.rows, sm.ebuf, perm, rank, L, fd, nb, mid, nb + 2u);
     __syncthreads();
+    const long long t2 = clock64();
+    clk.update += t1 - t0;
+    clk.unite += t2 - t1;
     const uint32_t span = ld_cg(P + 1) != 1u;
     const uint32_t logn = c.logn;
     __syncthreads();  // every thread has read span before node 1 may be reset below
@@ -381,6 +399,7 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, u
         __stcg(P + b, span ? b : (ld_cg(P + b) & ~kTag));  // undo, or commit the hook
     }
     __syncthreads();
+    clk.commit += clock64() - t2;
     return span;
 }
 
@@ -397,14 +416,18 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
     const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
     uint32_t *P = sp.P, *logb = sp.logb;
     unsigned long long tot_passes = 0, tot_probe = 0, tot_early = 0, tot_fb = 0, tot_ok = 0;
+    PhaseClock clk;
 
     for (;;) {
         if (threadIdx.x == 0) {
             c.sample = atomicAdd(&hdr->queue, 1u);
             c.hooks = 0;
             c.new_sites = 0;
+            c.sites = 0;
+            c.unions = 0;
         }
         __syncthreads();
+        const long long t_setup = clock64();
         const uint32_t s = c.sample;
         if (s >= num) break;
         const perc_sample smp = samples[s];
@@ -430,6 +453,7 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
         }
         const FastDiv fd = make_fastdiv(L);
         __syncthreads();
+        clk.setup += clock64() - t_setup;
 
         // bisection state (every thread keeps the same copy; all decisions are block-uniform)
         const uint32_t n_top = (L <= 2u) ? N + 1u : N;  // span(N) holds for every mask when L >= 3
@@ -463,8 +487,8 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
                 c.new_sites += mid - nb;
             }
             __syncthreads();
-            const uint32_t span = smem_bm ? probe<true>(c, P, logb, bm, sm, smp.perm, smp.rank, L, fd)
-                                          : probe<false>(c, P, logb, bm, sm, smp.perm, smp.rank, L, fd);
+            const uint32_t span = smem_bm ? probe<true>(c, P, logb, bm, sm, smp.perm, smp.rank, L, fd, clk)
+                                          : probe<false>(c, P, logb, bm, sm, smp.perm, smp.rank, L, fd, clk);
             ++npass;
             tot_probe += mid;
             if (span && c.stop) ++tot_early;
@@ -490,6 +514,8 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
             if (stats) {
                 atomicAdd(&stats->hooks, c.hooks);
                 atomicAdd(&stats->new_sites, c.new_sites);
+                atomicAdd(&stats->sites_merged, c.sites);
+                atomicAdd(&stats->unions, c.unions);
             }
         }
         __syncthreads();
@@ -500,6 +526,10 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
         atomicAdd(&stats->early_exits, tot_early);
         atomicAdd(&stats->fallbacks, tot_fb);
         atomicAdd(&stats->verified, tot_ok);
+        atomicAdd(&stats->cyc_setup, clk.setup);
+        atomicAdd(&stats->cyc_update, clk.update);
+        atomicAdd(&stats->cyc_union, clk.unite);
+        atomicAdd(&stats->cyc_commit, clk.commit);
     }
 }
 

@@ -20,7 +20,8 @@ MAX_L = 73
 OP_RANK, OP_NSTAR, OP_MASS = 1, 2, 3
 MLP_NPARAM = 4931
 STATS_FIELDS = ("passes", "new_sites", "probe_sites", "hooks", "early_exits", "fallbacks",
-                "verified", "reserved")
+                "verified", "sites_merged", "unions", "cyc_setup", "cyc_update", "cyc_union",
+                "cyc_commit", "reserved0", "reserved1", "reserved2")
 
 _lib = None
 
@@ -204,7 +205,7 @@ def check(ws: Workspace | None = None, stream=None) -> int:
 
 
 def new_stats() -> torch.Tensor:
-    return torch.zeros(8, dtype=torch.int64, device="cuda")
+    return torch.zeros(len(STATS_FIELDS), dtype=torch.int64, device="cuda")
 
 
 def stats_dict(stats: torch.Tensor) -> dict:
