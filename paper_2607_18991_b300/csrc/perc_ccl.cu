@@ -213,11 +213,30 @@ __device__ void bitmap_update(uint32_t *bm, const uint32_t *perm, uint32_t bm_n,
     }
 }
 
-// Warp-collective: lanes with `keep` append the union (a, b) to the warp's buffer; once 32 are
-// pending, all lanes perform one union each.
+// Warp-collective edge buffer.  An entry (a, b) is either a border union (b = node 0 or 1 with
+// kNodeFlag set) or a neighbor site b of node a, whose rank is looked up when the entry is
+// flushed; the Newman--Ziff rule (merge only neighbors of smaller rank) is applied there.  Once 32
+// entries are pending, all lanes flush one each, so the rank loads and the union-find chains of
+// 32 edges run side by side.
+constexpr uint32_t kNodeFlag = 0x80000000u;
+
+__device__ __forceinline__ uint32_t flush_one(uint2 e, const uint32_t *rank, uint32_t *P, uint32_t nold,
+                                              uint32_t *logb, uint32_t *logn, uint32_t &unions)
+{
+    uint32_t other;
+    if (e.y & kNodeFlag) {
+        other = e.y & ~kNodeFlag;
+    } else {
+        other = __ldg(rank + e.y) + 2u;
+        if (other >= e.x) return 0u;  // the neighbor came later: it merges this edge itself
+    }
+    ++unions;
+    return uf_unite(P, e.x, other, nold, logb, logn) ? 1u : 0u;
+}
+
 __device__ __forceinline__ void push_edge(bool keep, uint32_t a, uint32_t b, uint2 *buf, uint32_t &cnt,
-                                          uint32_t lane, uint32_t *P, uint32_t nold, uint32_t *logb,
-                                          uint32_t *logn, uint32_t &hooks)
+                                          uint32_t lane, const uint32_t *rank, uint32_t *P, uint32_t nold,
+                                          uint32_t *logb, uint32_t *logn, uint32_t &hooks, uint32_t &unions)
 {
     const uint32_t bal = __ballot_sync(0xffffffffu, keep);
     if (bal == 0u) return;
@@ -225,8 +244,7 @@ __device__ __forceinline__ void push_edge(bool keep, uint32_t a, uint32_t b, uin
     cnt += __popc(bal);
     __syncwarp();
     if (cnt >= 32u) {
-        const uint2 e = buf[lane];
-        hooks += uf_unite(P, e.x, e.y, nold, logb, logn);
+        hooks += flush_one(buf[lane], rank, P, nold, logb, logn, unions);
         __syncwarp();
         if (lane + 32u < cnt) buf[lane] = buf[lane + 32u];
         cnt -= 32u;
@@ -273,8 +291,10 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, 
         const uint32_t node = r + 2u;
         sites += (act && gl == 0u) ? 1u : 0u;
         if (kFaces) {
-            push_edge(act && gl == 0u && x[0] == 0u, node, 0u, buf, cnt, lane, P, nold, logb, &c.logn, hooks);
-            push_edge(act && gl == 0u && x[0] == L - 1u, node, 1u, buf, cnt, lane, P, nold, logb, &c.logn, hooks);
+            push_edge(act && gl == 0u && x[0] == 0u, node, kNodeFlag | 0u, buf, cnt, lane, rank, P, nold, logb,
+                      &c.logn, hooks, unions);
+            push_edge(act && gl == 0u && x[0] == L - 1u, node, kNodeFlag | 1u, buf, cnt, lane, rank, P, nold, logb,
+                      &c.logn, hooks, unions);
         }
         const uint32_t bit0 = i + kBmGuard - 2u;  // window start of the own row, before the row offset
         for (uint32_t t = 0; t < niter; t += kRowUnroll) {
@@ -299,25 +319,20 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, 
             for (int u = 0; u < kRowUnroll; ++u) {
                 uint32_t h = hits[u];
                 while (__any_sync(0xffffffffu, h != 0u)) {
-                    bool keep = false;
-                    uint32_t other = 0u;
-                    if (h) {
-                        const uint32_t tb = __ffs(h) - 1;
+                    uint32_t j = 0u;
+                    const bool keep = h != 0u;
+                    if (keep) {
+                        j = i + static_cast<uint32_t>(dl[u]) + (__ffs(h) - 1) - 2u;
                         h &= h - 1u;
-                        const uint32_t j = i + static_cast<uint32_t>(dl[u]) + tb - 2u;
-                        const uint32_t rj = __ldg(rank + j);
-                        keep = rj < r;
-                        other = rj + 2u;
-                        unions += keep ? 1u : 0u;
                     }
-                    push_edge(keep, node, other, buf, cnt, lane, P, nold, logb, &c.logn, hooks);
+                    push_edge(keep, node, j, buf, cnt, lane, rank, P, nold, logb, &c.logn, hooks, unions);
                 }
             }
         }
         if (kFaces && lane == 0u && ((++batch & 1u) == 0u) && ld_cg(P + 1) != 1u)
             *reinterpret_cast<volatile uint32_t *>(&c.stop) = 1u;
     }
-    if (lane < cnt) hooks += uf_unite(P, buf[lane].x, buf[lane].y, nold, logb, &c.logn);
+    if (lane < cnt) hooks += flush_one(buf[lane], rank, P, nold, logb, &c.logn, unions);
     __syncwarp();
     hooks = __reduce_add_sync(0xffffffffu, hooks);
     sites = __reduce_add_sync(0xffffffffu, sites);
@@ -381,6 +396,7 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, u
                                           uint32_t L, const FastDiv &fd, PhaseClock &clk)
 {
     const uint32_t mid = c.mid, nb = c.nb, bm_n = c.bm_n;
+    if (kSmemBm) bm = sm.sbm;  // keep the shared-memory address space visible to the compiler
     const long long t0 = clock64();
     bitmap_update(bm, perm, bm_n, mid);
     for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x) __stcg(P + r + 2u, r + 2u);
@@ -455,27 +471,35 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
         __syncthreads();
         clk.setup += clock64() - t_setup;
 
-        // bisection state (every thread keeps the same copy; all decisions are block-uniform)
+        // bisection state (every thread keeps the same copy; all decisions are block-uniform).
+        // A learned bracket [blo, bhi] is verified lazily: not span(blo - 1) is probed first (its
+        // union-find is the base of every later probe); span(bhi) holds as soon as any bisection
+        // probe spans, and is probed on its own only if none did.
         const uint32_t n_top = (L <= 2u) ? N + 1u : N;  // span(N) holds for every mask when L >= 3
         uint32_t lo = 1, hi = n_top, nb = 0, bm_n = 0, npass = 0;
-        int stage = 2;  // 0: verify lo-1, 1: verify hi, 2: bisect
+        int stage = 2;  // 0: verify not span(blo - 1), 2: bisect
+        bool hi_known = true;  // span(hi) is established (by a probe or, plain, by construction)
         uint32_t blo = 0, bhi = 0;
         if (bracket) {
             blo = bracket[2 * size_t(s)];
             bhi = bracket[2 * size_t(s) + 1];
-            if (blo >= 1u && blo <= bhi && bhi <= N)
-                stage = blo > 1u ? 0 : 1;
-            else
+            if (blo >= 1u && blo <= bhi && bhi <= N) {
+                stage = blo > 1u ? 0 : 2;
+                lo = blo;
+                hi = bhi;
+                hi_known = false;
+            } else {
                 ++tot_fb;
+            }
         }
         for (;;) {
             uint32_t mid;
             if (stage == 0)
                 mid = blo - 1u;
-            else if (stage == 1)
-                mid = bhi;
             else if (lo < hi)
                 mid = lo + (hi - lo) / 2u;
+            else if (!hi_known)
+                mid = hi;  // every probe inside the bracket stayed below: check span(bhi) itself
             else
                 break;
             if (threadIdx.x == 0) {
@@ -495,18 +519,25 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
             bm_n = mid;
             if (!span) nb = mid;
             if (stage == 0) {
-                if (span) { stage = 2; lo = 1; hi = n_top; nb = 0; ++tot_fb; }
-                else stage = 1;
-            } else if (stage == 1) {
-                if (!span) { stage = 2; lo = 1; hi = n_top; nb = 0; ++tot_fb; }
-                else { stage = 2; lo = blo; hi = bhi; ++tot_ok; }
+                if (span) {  // n* < blo: the bracket is wrong, bisect the full range
+                    lo = 1; hi = n_top; nb = 0; hi_known = true; ++tot_fb;
+                }
+                stage = 2;
+            } else if (lo == hi) {  // the lazy check of span(bhi)
+                if (span) {
+                    hi_known = true;
+                } else {  // n* > bhi: the bracket is wrong, bisect the full range
+                    lo = 1; hi = n_top; nb = 0; hi_known = true; ++tot_fb;
+                }
             } else if (span) {
                 hi = mid;
+                hi_known = true;
             } else {
                 lo = mid + 1u;
             }
             __syncthreads();  // c.stop / c.logn are rewritten by thread 0 next round
         }
+        if (bracket && blo >= 1u && blo <= bhi && bhi <= N && lo >= blo && lo <= bhi && npass > 0) ++tot_ok;
         if (threadIdx.x == 0) {
             nstar_out[s] = (lo == N + 1u) ? PERC_NEVER : lo;
             if (passes_out) passes_out[s] = npass;
