@@ -58,6 +58,7 @@ struct Ctl {
     uint32_t bad;     // sample failed validation
     uint32_t z;       // offsets of the sample's neighborhood
     uint32_t R;       // row entries of the sample's neighborhood
+    uint32_t NP;      // plane entries (L = 16 path)
     unsigned long long hooks, new_sites, sites, unions;
 };
 
@@ -344,6 +345,157 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, 
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// L = 16 fast path: "planes".  With 16 sites per x5 row the five rows x4-2..x4+2 of a fixed
+// (x1+d1, x2+d2, x3+d3) are 80 contiguous bits, and every plane offset is a multiple of 256 bits,
+// so the bit shift of a site's 5x5 (d4, d5) block is the same for all planes.  Four word loads and
+// three funnel shifts give the whole block; per-plane masks select the neighborhood's (d4, d5)
+// and per-site masks the in-lattice ones.  Bit t of funnel F (F = 0..2) is site
+// i + delta - 34 + 32F + t.
+// ------------------------------------------------------------------------------------------------
+constexpr uint32_t kPlaneL = 16;
+constexpr int kPlaneCand = 125;  // (d1, d2, d3) in {-2..2}^3
+
+struct __align__(16) PlaneEntry {
+    int32_t dword;   // plane offset / 32 (= ((d1*16 + d2)*16 + d3) * 8)
+    uint32_t oh;     // bits 0..14: one-hot of d1..d3; bits 16..20: neighborhood mask of funnel 2
+    uint32_t pm0;    // funnel 0: d4 = -2 in bits 0..4, d4 = -1 in bits 16..20 (bit d5 + 2)
+    uint32_t pm1;    // funnel 1: d4 = 0 in bits 0..4, d4 = +1 in bits 16..20
+};
+
+// Plane table of `mask` from the row table (rows must be built; ends with a barrier).
+__device__ uint32_t build_planes16(const RowEntry *rows, uint32_t R, PlaneEntry *planes, uint32_t *scratch, Ctl &c)
+{
+    // scratch[key * 5 + (d4 + 2)] = d5 mask, key = base-5 code of (d1, d2, d3)
+    for (uint32_t t = threadIdx.x; t < kPlaneCand * 5; t += blockDim.x) scratch[t] = 0u;
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < R; k += blockDim.x) {
+        const RowEntry e = rows[k];
+        int d[4];
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t oh = (e.onehot >> (5 * q)) & 31u;
+            d[q] = __ffs(oh) - 1 - 2;
+        }
+        const uint32_t key = static_cast<uint32_t>(((d[0] + 2) * 5 + (d[1] + 2)) * 5 + (d[2] + 2));
+        scratch[key * 5 + static_cast<uint32_t>(d[3] + 2)] = e.d5mask;  // one row per (d1..d4)
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const uint32_t lane = threadIdx.x;
+        uint32_t count = 0;
+        for (uint32_t base = 0; base < static_cast<uint32_t>(kPlaneCand); base += 32) {
+            const uint32_t key = base + lane;
+            uint32_t f[5] = {0u, 0u, 0u, 0u, 0u};
+            if (key < static_cast<uint32_t>(kPlaneCand))
+                for (int q = 0; q < 5; ++q) f[q] = scratch[key * 5 + q];
+            const bool any = (f[0] | f[1] | f[2] | f[3] | f[4]) != 0u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, any);
+            if (any) {
+                const int d1 = static_cast<int>(key / 25u) - 2, d2 = static_cast<int>((key / 5u) % 5u) - 2,
+                          d3 = static_cast<int>(key % 5u) - 2;
+                PlaneEntry e;
+                e.dword = ((d1 * 16 + d2) * 16 + d3) * 8;
+                e.oh = (1u << (d1 + 2)) | (1u << (5 + d2 + 2)) | (1u << (10 + d3 + 2)) | (f[4] << 16);
+                e.pm0 = f[0] | (f[1] << 16);
+                e.pm1 = f[2] | (f[3] << 16);
+                planes[count + __popc(bal & ((1u << lane) - 1u))] = e;
+            }
+            count += __popc(bal);
+        }
+        if (lane == 0) c.NP = count;
+    }
+    __syncthreads();
+    return c.NP;
+}
+
+constexpr int kPlaneUnroll = 2;
+
+template <bool kFaces>
+__device__ __forceinline__ void union_pass_planes16(Ctl &c, uint32_t *P, uint32_t *logb, const uint32_t *bm,
+                                                    const PlaneEntry *planes, uint2 *ebuf, const uint32_t *perm,
+                                                    const uint32_t *rank, uint32_t r0, uint32_t r1, uint32_t nold)
+{
+    const uint32_t NP = c.NP;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t gshift = lanes_shift(r1 - r0, NP);
+    const uint32_t gl = lane & ((1u << gshift) - 1u), gw = lane >> gshift, spw = 32u >> gshift;
+    const uint32_t niter = (NP + (1u << gshift) - 1u) >> gshift;
+    uint2 *buf = ebuf + warp * kEdgeBuf;
+    uint32_t cnt = 0, hooks = 0, batch = 0, sites = 0, unions = 0;
+    for (uint32_t base = r0 + warp * spw; base < r1; base += nwarps * spw) {
+        if (kFaces && *reinterpret_cast<volatile uint32_t *>(&c.stop)) break;
+        const uint32_t r = base + gw;
+        const bool act = r < r1;
+        const uint32_t i = act ? __ldg(perm + r) : 0u;
+        const uint32_t x1 = i >> 16, x2 = (i >> 12) & 15u, x3 = (i >> 8) & 15u, x4 = (i >> 4) & 15u,
+                       x5 = i & 15u;
+        const uint32_t a123 = allowed_bits(x1, kPlaneL) | (allowed_bits(x2, kPlaneL) << 5) |
+                              (allowed_bits(x3, kPlaneL) << 10);
+        const uint32_t a4 = allowed_bits(x4, kPlaneL), a5 = allowed_bits(x5, kPlaneL);
+        const uint32_t sm0 = ((a4 & 1u) ? a5 : 0u) | ((a4 & 2u) ? (a5 << 16) : 0u);
+        const uint32_t sm1 = ((a4 & 4u) ? a5 : 0u) | ((a4 & 8u) ? (a5 << 16) : 0u);
+        const uint32_t sm2 = (a4 & 16u) ? a5 : 0u;
+        const uint32_t sh = (i + 30u) & 31u;
+        const uint32_t wbase = (i + 30u) >> 5;  // word of the block start at plane offset 0
+        const uint32_t node = r + 2u;
+        sites += (act && gl == 0u) ? 1u : 0u;
+        if (kFaces) {
+            push_edge(act && gl == 0u && x1 == 0u, node, kNodeFlag | 0u, buf, cnt, lane, rank, P, nold, logb,
+                      &c.logn, hooks, unions);
+            push_edge(act && gl == 0u && x1 == kPlaneL - 1u, node, kNodeFlag | 1u, buf, cnt, lane, rank, P, nold,
+                      logb, &c.logn, hooks, unions);
+        }
+        for (uint32_t t = 0; t < niter; t += kPlaneUnroll) {
+            uint32_t h[kPlaneUnroll][3];
+            int32_t dw[kPlaneUnroll];
+#pragma unroll
+            for (int u = 0; u < kPlaneUnroll; ++u) {
+                const uint32_t k = gl + ((t + u) << gshift);
+                const bool ok = act && k < NP;
+                const PlaneEntry e = planes[ok ? k : 0u];
+                h[u][0] = h[u][1] = h[u][2] = 0u;
+                dw[u] = e.dword;
+                if (ok && (e.oh & 0x7FFFu & ~a123) == 0u) {
+                    const uint32_t *w = bm + (wbase + static_cast<uint32_t>(e.dword));
+                    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3];
+                    h[u][0] = __funnelshift_r(w0, w1, sh) & e.pm0 & sm0;
+                    h[u][1] = __funnelshift_r(w1, w2, sh) & e.pm1 & sm1;
+                    h[u][2] = __funnelshift_r(w2, w3, sh) & (e.oh >> 16) & sm2;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kPlaneUnroll; ++u) {
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    uint32_t hf = h[u][f];
+                    while (__any_sync(0xffffffffu, hf != 0u)) {
+                        uint32_t j = 0u;
+                        const bool keep = hf != 0u;
+                        if (keep) {
+                            j = i + static_cast<uint32_t>(dw[u] * 32) + static_cast<uint32_t>(32 * f) +
+                                static_cast<uint32_t>(__ffs(hf) - 1) - 34u;
+                            hf &= hf - 1u;
+                        }
+                        push_edge(keep, node, j, buf, cnt, lane, rank, P, nold, logb, &c.logn, hooks, unions);
+                    }
+                }
+            }
+        }
+        if (kFaces && lane == 0u && ((++batch & 1u) == 0u) && ld_cg(P + 1) != 1u)
+            *reinterpret_cast<volatile uint32_t *>(&c.stop) = 1u;
+    }
+    if (lane < cnt) hooks += flush_one(buf[lane], rank, P, nold, logb, &c.logn, unions);
+    __syncwarp();
+    hooks = __reduce_add_sync(0xffffffffu, hooks);
+    sites = __reduce_add_sync(0xffffffffu, sites);
+    unions = __reduce_add_sync(0xffffffffu, unions);
+    if (lane == 0u) {
+        if (hooks) atomicAdd(&c.hooks, static_cast<unsigned long long>(hooks));
+        if (sites) atomicAdd(&c.sites, static_cast<unsigned long long>(sites));
+        if (unions) atomicAdd(&c.unions, static_cast<unsigned long long>(unions));
+    }
+}
+
 struct SlotPtrs {
     uint32_t *P, *logb, *gbm;
 };
@@ -362,6 +514,7 @@ __device__ __forceinline__ SlotPtrs slot_ptrs(char *ws, size_t slot_bytes, uint6
 // Shared-memory carve-up: [row table][edge buffers (also the row-build scratch)][bitmap].
 struct SmemPtrs {
     RowEntry *rows;
+    PlaneEntry *planes;
     uint2 *ebuf;
     uint32_t *scratch;
     uint32_t *sbm;
@@ -369,7 +522,7 @@ struct SmemPtrs {
 
 __host__ __device__ inline size_t smem_fixed_bytes(uint32_t threads)
 {
-    const size_t rows = sizeof(RowEntry) * kRowCand;
+    const size_t rows = sizeof(RowEntry) * kRowCand + sizeof(PlaneEntry) * kPlaneCand;
     size_t eb = size_t(threads / 32) * kEdgeBuf * sizeof(uint2);
     if (eb < kRowCand * sizeof(uint32_t)) eb = kRowCand * sizeof(uint32_t);
     return rows + ((eb + 15) & ~size_t(15));
@@ -379,7 +532,8 @@ __device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn)
 {
     SmemPtrs p;
     p.rows = reinterpret_cast<RowEntry *>(dyn);
-    p.ebuf = reinterpret_cast<uint2 *>(dyn + sizeof(RowEntry) * kRowCand);
+    p.planes = reinterpret_cast<PlaneEntry *>(dyn + sizeof(RowEntry) * kRowCand);
+    p.ebuf = reinterpret_cast<uint2 *>(dyn + sizeof(RowEntry) * kRowCand + sizeof(PlaneEntry) * kPlaneCand);
     p.scratch = reinterpret_cast<uint32_t *>(p.ebuf);
     p.sbm = reinterpret_cast<uint32_t *>(dyn + smem_fixed_bytes(blockDim.x));
     return p;
@@ -402,7 +556,10 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, u
     for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x) __stcg(P + r + 2u, r + 2u);
     __syncthreads();
     const long long t1 = clock64();
-    union_pass<kSmemBm, true>(c, P, logb, bm, sm.rows, sm.ebuf, perm, rank, L, fd, nb, mid, nb + 2u);
+    if (kSmemBm && L == kPlaneL)
+        union_pass_planes16<true>(c, P, logb, bm, sm.planes, sm.ebuf, perm, rank, nb, mid, nb + 2u);
+    else
+        union_pass<kSmemBm, true>(c, P, logb, bm, sm.rows, sm.ebuf, perm, rank, L, fd, nb, mid, nb + 2u);
     __syncthreads();
     const long long t2 = clock64();
     clk.update += t1 - t0;
@@ -463,6 +620,7 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
         const uint32_t words = bm_words(N);
         for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
         build_rows(mask, L, sm.rows, sm.scratch, c);
+        if (smem_bm && L == kPlaneL) build_planes16(sm.rows, c.R, sm.planes, sm.scratch, c);
         if (threadIdx.x == 0) {
             __stcg(P + 0, 0u);
             __stcg(P + 1, 1u);
@@ -602,6 +760,7 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         const uint32_t words = bm_words(N);
         for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
         build_rows(mask, L, sm.rows, sm.scratch, c);
+        if (smem_bm && L == kPlaneL) build_planes16(sm.rows, c.R, sm.planes, sm.scratch, c);
         if (threadIdx.x == 0) {
             c.logn = 0;
             c.stop = 0;
@@ -614,8 +773,10 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
             __stcg(cnt + r + 2u, 0u);
         }
         __syncthreads();
-        if (smem_bm)
-            union_pass<true, false>(c, P, nullptr, bm, sm.rows, sm.ebuf, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+        if (smem_bm && L == kPlaneL)
+            union_pass_planes16<false>(c, P, nullptr, sm.sbm, sm.planes, sm.ebuf, smp.perm, smp.rank, 0u, n, 0u);
+        else if (smem_bm)
+            union_pass<true, false>(c, P, nullptr, sm.sbm, sm.rows, sm.ebuf, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         else
             union_pass<false, false>(c, P, nullptr, bm, sm.rows, sm.ebuf, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         __syncthreads();
