@@ -34,7 +34,6 @@
 
 namespace perc {
 
-constexpr uint32_t kTag = 0x80000000u;
 constexpr uint32_t kSmemBitmapMaxL = 17;
 constexpr size_t kSlotCapBytes = size_t(32) << 30;  // total per-CTA slot memory aimed at
 
@@ -63,43 +62,70 @@ struct Ctl {
 };
 
 // ------------------------------------------------------------------------------------------------
-// union-find on rank-space nodes (global memory, L2-coherent loads)
+// union-find on rank-space nodes (global memory, L2-coherent loads).
+//
+// A node is one 64-bit word: the committed parent C (low half) and the overlay parent O of the
+// running probe (high half, kNone when unset).  Its parent is O if set, else C.  Nodes below nold
+// existed at the committed (last non-spanning) state: during a probe their changes go to O only,
+// and the first write of an O is logged.  Undo (a spanning probe) clears the logged O; commit
+// copies them into C.  Nodes at or above nold are new and use C directly.  Because every write of
+// an old node lands in its overlay, path halving may shortcut any edge.
 // ------------------------------------------------------------------------------------------------
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
 __device__ __forceinline__ uint32_t ld_cg(const uint32_t *p) { return __ldcg(p); }
 
-// Root of x with path halving.  Nodes below nold existed at the committed state: their pointer is
-// rewritten only when both skipped edges are untagged (committed edges).
-__device__ __forceinline__ uint32_t uf_find(uint32_t *P, uint32_t x, uint32_t nold)
+__device__ __forceinline__ uint2 ld_node(const uint2 *P, uint32_t x)
+{
+    const unsigned long long v = __ldcg(reinterpret_cast<const unsigned long long *>(P + x));
+    return make_uint2(static_cast<uint32_t>(v), static_cast<uint32_t>(v >> 32));
+}
+
+__device__ __forceinline__ uint32_t node_parent(uint2 n) { return n.y != kNone ? n.y : n.x; }
+
+// Root of x with path halving.
+__device__ __forceinline__ uint32_t uf_find(uint2 *P, uint32_t x, uint32_t nold, uint32_t *logb,
+                                            uint32_t *logn)
 {
     for (;;) {
-        const uint32_t p = ld_cg(P + x);
-        const uint32_t pu = p & ~kTag;
-        if (pu == x) return x;
-        const uint32_t g = ld_cg(P + pu);
-        const uint32_t gu = g & ~kTag;
-        if (gu == pu) return pu;
-        if (x >= nold || ((p | g) & kTag) == 0u) __stcg(P + x, gu);
-        x = gu;
+        const uint2 nx = ld_node(P, x);
+        const uint32_t p = node_parent(nx);
+        if (p == x) return x;
+        const uint2 np = ld_node(P, p);
+        const uint32_t g = node_parent(np);
+        if (g == p) return p;
+        if (x >= nold) {
+            __stcg(&P[x].x, g);                          // new node
+        } else if (nx.y == kNone && np.y == kNone) {
+            __stcg(&P[x].x, g);                          // shortcut of two committed edges
+        } else if (nx.y != kNone) {
+            __stcg(&P[x].y, g);                          // overlay already logged
+        } else if (atomicCAS(&P[x].y, kNone, g) == kNone) {
+            logb[atomicAdd(logn, 1u)] = x;               // first overlay write of x
+        }
+        x = g;
     }
 }
 
-// Merge the clusters of a and b; returns true if a hook was made.
-__device__ __forceinline__ bool uf_unite(uint32_t *P, uint32_t a, uint32_t b, uint32_t nold,
-                                         uint32_t *logb, uint32_t *logn)
+// Merge the clusters of a and b (the larger root goes under the smaller); true if a hook was made.
+__device__ __forceinline__ bool uf_unite(uint2 *P, uint32_t a, uint32_t b, uint32_t nold, uint32_t *logb,
+                                         uint32_t *logn)
 {
-    a = uf_find(P, a, nold);
-    b = uf_find(P, b, nold);
+    a = uf_find(P, a, nold, logb, logn);
+    b = uf_find(P, b, nold, logb, logn);
     while (a != b) {
         const uint32_t hi = a > b ? a : b;
         const uint32_t lo = a > b ? b : a;
-        const bool old = hi < nold;
-        const uint32_t seen = atomicCAS(P + hi, hi, old ? (lo | kTag) : lo);
-        if (seen == hi) {
-            if (old) logb[atomicAdd(logn, 1u)] = hi;
-            return true;
+        bool hooked;
+        if (hi < nold) {
+            hooked = atomicCAS(&P[hi].y, kNone, lo) == kNone;
+            if (hooked) logb[atomicAdd(logn, 1u)] = hi;
+        } else {
+            hooked = atomicCAS(&P[hi].x, hi, lo) == hi;
         }
-        a = uf_find(P, seen & ~kTag, nold);  // hi was hooked meanwhile: continue from its root
-        b = uf_find(P, lo, nold);
+        if (hooked) return true;
+        a = uf_find(P, hi, nold, logb, logn);  // hi was hooked meanwhile: continue from its root
+        b = uf_find(P, lo, nold, logb, logn);
     }
     return false;
 }
@@ -221,7 +247,7 @@ __device__ void bitmap_update(uint32_t *bm, const uint32_t *perm, uint32_t bm_n,
 // 32 edges run side by side.
 constexpr uint32_t kNodeFlag = 0x80000000u;
 
-__device__ __forceinline__ uint32_t flush_one(uint2 e, const uint32_t *rank, uint32_t *P, uint32_t nold,
+__device__ __forceinline__ uint32_t flush_one(uint2 e, const uint32_t *rank, uint2 *P, uint32_t nold,
                                               uint32_t *logb, uint32_t *logn, uint32_t &unions)
 {
     uint32_t other;
@@ -236,7 +262,7 @@ __device__ __forceinline__ uint32_t flush_one(uint2 e, const uint32_t *rank, uin
 }
 
 __device__ __forceinline__ void push_edge(bool keep, uint32_t a, uint32_t b, uint2 *buf, uint32_t &cnt,
-                                          uint32_t lane, const uint32_t *rank, uint32_t *P, uint32_t nold,
+                                          uint32_t lane, const uint32_t *rank, uint2 *P, uint32_t nold,
                                           uint32_t *logb, uint32_t *logn, uint32_t &hooks, uint32_t &unions)
 {
     const uint32_t bal = __ballot_sync(0xffffffffu, keep);
@@ -268,7 +294,7 @@ __device__ __forceinline__ uint32_t lanes_shift(uint32_t count, uint32_t R)
 constexpr int kRowUnroll = 4;
 
 template <bool kSmemBm, bool kFaces>
-__device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, const uint32_t *bm,
+__device__ __forceinline__ void union_pass(Ctl &c, uint2 *P, uint32_t *logb, const uint32_t *bm,
                                            const RowEntry *rows, uint2 *ebuf, const uint32_t *perm,
                                            const uint32_t *rank, uint32_t L, const FastDiv &fd,
                                            uint32_t r0, uint32_t r1, uint32_t nold)
@@ -330,7 +356,7 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, 
                 }
             }
         }
-        if (kFaces && lane == 0u && ((++batch & 1u) == 0u) && ld_cg(P + 1) != 1u)
+        if (kFaces && lane == 0u && ((++batch & 1u) == 0u) && ld_cg(&P[1].y) != kNone)
             *reinterpret_cast<volatile uint32_t *>(&c.stop) = 1u;
     }
     if (lane < cnt) hooks += flush_one(buf[lane], rank, P, nold, logb, &c.logn, unions);
@@ -411,7 +437,7 @@ __device__ uint32_t build_planes16(const RowEntry *rows, uint32_t R, PlaneEntry 
 constexpr int kPlaneUnroll = 2;
 
 template <bool kFaces>
-__device__ __forceinline__ void union_pass_planes16(Ctl &c, uint32_t *P, uint32_t *logb, const uint32_t *bm,
+__device__ __forceinline__ void union_pass_planes16(Ctl &c, uint2 *P, uint32_t *logb, const uint32_t *bm,
                                                     const PlaneEntry *planes, uint2 *ebuf, const uint32_t *perm,
                                                     const uint32_t *rank, uint32_t r0, uint32_t r1, uint32_t nold)
 {
@@ -481,7 +507,7 @@ __device__ __forceinline__ void union_pass_planes16(Ctl &c, uint32_t *P, uint32_
                 }
             }
         }
-        if (kFaces && lane == 0u && ((++batch & 1u) == 0u) && ld_cg(P + 1) != 1u)
+        if (kFaces && lane == 0u && ((++batch & 1u) == 0u) && ld_cg(&P[1].y) != kNone)
             *reinterpret_cast<volatile uint32_t *>(&c.stop) = 1u;
     }
     if (lane < cnt) hooks += flush_one(buf[lane], rank, P, nold, logb, &c.logn, unions);
@@ -497,17 +523,19 @@ __device__ __forceinline__ void union_pass_planes16(Ctl &c, uint32_t *P, uint32_
 }
 
 struct SlotPtrs {
-    uint32_t *P, *logb, *gbm;
+    uint2 *P;
+    uint32_t *logb, *gbm;
 };
 
 __device__ __forceinline__ SlotPtrs slot_ptrs(char *ws, size_t slot_bytes, uint64_t Ncap, bool gbm)
 {
     char *base = ws + sizeof(WsHeader) + size_t(blockIdx.x) * slot_bytes;
-    const size_t nodes = ((Ncap + 2) * 4 + 255) & ~size_t(255);
+    const size_t nodes = ((Ncap + 2) * 8 + 255) & ~size_t(255);
+    const size_t logs = ((Ncap + 2) * 4 + 255) & ~size_t(255);
     SlotPtrs s;
-    s.P = reinterpret_cast<uint32_t *>(base);
+    s.P = reinterpret_cast<uint2 *>(base);
     s.logb = reinterpret_cast<uint32_t *>(base + nodes);
-    s.gbm = gbm ? reinterpret_cast<uint32_t *>(base + 2 * nodes) : nullptr;
+    s.gbm = gbm ? reinterpret_cast<uint32_t *>(base + nodes + logs) : nullptr;
     return s;
 }
 
@@ -545,7 +573,7 @@ struct PhaseClock {
 };
 
 template <bool kSmemBm>
-__device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, uint32_t *bm,
+__device__ __forceinline__ uint32_t probe(Ctl &c, uint2 *P, uint32_t *logb, uint32_t *bm,
                                           const SmemPtrs &sm, const uint32_t *perm, const uint32_t *rank,
                                           uint32_t L, const FastDiv &fd, PhaseClock &clk)
 {
@@ -553,7 +581,8 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, u
     if (kSmemBm) bm = sm.sbm;  // keep the shared-memory address space visible to the compiler
     const long long t0 = clock64();
     bitmap_update(bm, perm, bm_n, mid);
-    for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x) __stcg(P + r + 2u, r + 2u);
+    for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x)
+        __stcg(reinterpret_cast<unsigned long long *>(P + r + 2u), (static_cast<unsigned long long>(kNone) << 32) | (r + 2u));
     __syncthreads();
     const long long t1 = clock64();
     if (kSmemBm && L == kPlaneL)
@@ -564,12 +593,13 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, u
     const long long t2 = clock64();
     clk.update += t1 - t0;
     clk.unite += t2 - t1;
-    const uint32_t span = ld_cg(P + 1) != 1u;
+    const uint32_t span = ld_cg(&P[1].y) != kNone;  // node 1 can only be hooked under node 0
     const uint32_t logn = c.logn;
     __syncthreads();  // every thread has read span before node 1 may be reset below
     for (uint32_t k = threadIdx.x; k < logn; k += blockDim.x) {
         const uint32_t b = logb[k];
-        __stcg(P + b, span ? b : (ld_cg(P + b) & ~kTag));  // undo, or commit the hook
+        if (!span) __stcg(&P[b].x, ld_cg(&P[b].y));  // commit the overlay
+        __stcg(&P[b].y, kNone);
     }
     __syncthreads();
     clk.commit += clock64() - t2;
@@ -587,7 +617,8 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
     const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
-    uint32_t *P = sp.P, *logb = sp.logb;
+    uint2 *P = sp.P;
+    uint32_t *logb = sp.logb;
     unsigned long long tot_passes = 0, tot_probe = 0, tot_early = 0, tot_fb = 0, tot_ok = 0;
     PhaseClock clk;
 
@@ -622,8 +653,8 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
         build_rows(mask, L, sm.rows, sm.scratch, c);
         if (smem_bm && L == kPlaneL) build_planes16(sm.rows, c.R, sm.planes, sm.scratch, c);
         if (threadIdx.x == 0) {
-            __stcg(P + 0, 0u);
-            __stcg(P + 1, 1u);
+            __stcg(reinterpret_cast<unsigned long long *>(P + 0), static_cast<unsigned long long>(kNone) << 32);
+            __stcg(reinterpret_cast<unsigned long long *>(P + 1), (static_cast<unsigned long long>(kNone) << 32) | 1u);
         }
         const FastDiv fd = make_fastdiv(L);
         __syncthreads();
@@ -734,7 +765,8 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
     const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
-    uint32_t *P = sp.P, *cnt = sp.logb;
+    uint2 *P = sp.P;
+    uint32_t *cnt = sp.logb;
 
     for (;;) {
         if (threadIdx.x == 0) c.sample = atomicAdd(&hdr->queue, 1u);
@@ -769,7 +801,7 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         __syncthreads();
         bitmap_update(bm, smp.perm, 0u, n);
         for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) {
-            __stcg(P + r + 2u, r + 2u);
+            __stcg(reinterpret_cast<unsigned long long *>(P + r + 2u), (static_cast<unsigned long long>(kNone) << 32) | (r + 2u));
             __stcg(cnt + r + 2u, 0u);
         }
         __syncthreads();
@@ -780,7 +812,7 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         else
             union_pass<false, false>(c, P, nullptr, bm, sm.rows, sm.ebuf, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         __syncthreads();
-        for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) atomicAdd(cnt + uf_find(P, r + 2u, 0u), 1u);
+        for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) atomicAdd(cnt + uf_find(P, r + 2u, 0u, nullptr, nullptr), 1u);
         __syncthreads();
         uint32_t best = 0;
         for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) best = max(best, ld_cg(cnt + r + 2u));
@@ -834,9 +866,10 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, cfg.threads, cfg.smem) != cudaSuccess)
         return PERC_ECUDA;
     if (occ < 1) return PERC_EINVAL;
-    const size_t nodes = ((Ncap + 2) * 4 + 255) & ~size_t(255);
+    const size_t nodes = ((Ncap + 2) * 8 + 255) & ~size_t(255);
+    const size_t logs = ((Ncap + 2) * 4 + 255) & ~size_t(255);
     const size_t gbm = max_L > cfg.smem_L ? (size_t(bm_words(Ncap)) * 4 + 255) & ~size_t(255) : 0;
-    cfg.slot_bytes = 2 * nodes + gbm;
+    cfg.slot_bytes = nodes + logs + gbm;
     uint64_t grid = uint64_t(sms) * occ;
     const int cap = env_int("PERC_MAX_CTAS", 0);
     if (cap > 0 && uint64_t(cap) < grid) grid = cap;
