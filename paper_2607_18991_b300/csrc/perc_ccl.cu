@@ -75,16 +75,53 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 __device__ __forceinline__ uint32_t ld_cg(const uint32_t *p) { return __ldcg(p); }
 
-__device__ __forceinline__ uint2 ld_node(const uint2 *P, uint32_t x)
+// Nodes below `cap` live in shared memory, the others in the CTA's global slot (same indexing).
+struct Nodes {
+    uint2 *s;
+    uint2 *g;
+    uint32_t cap;
+};
+
+__device__ __forceinline__ uint2 ld_node(const Nodes &P, uint32_t x)
 {
-    const unsigned long long v = __ldcg(reinterpret_cast<const unsigned long long *>(P + x));
+    unsigned long long v;
+    if (x < P.cap)
+        v = *reinterpret_cast<volatile unsigned long long *>(P.s + x);
+    else
+        v = __ldcg(reinterpret_cast<const unsigned long long *>(P.g + x));
     return make_uint2(static_cast<uint32_t>(v), static_cast<uint32_t>(v >> 32));
+}
+
+__device__ __forceinline__ uint32_t *node_c(const Nodes &P, uint32_t x) { return x < P.cap ? &P.s[x].x : &P.g[x].x; }
+__device__ __forceinline__ uint32_t *node_o(const Nodes &P, uint32_t x) { return x < P.cap ? &P.s[x].y : &P.g[x].y; }
+
+__device__ __forceinline__ void st_half(const Nodes &P, uint32_t x, uint32_t *h, uint32_t v)
+{
+    if (x < P.cap)
+        *reinterpret_cast<volatile uint32_t *>(h) = v;
+    else
+        __stcg(h, v);
+}
+
+__device__ __forceinline__ uint32_t ld_half(const Nodes &P, uint32_t x, const uint32_t *h)
+{
+    return x < P.cap ? *reinterpret_cast<const volatile uint32_t *>(h) : __ldcg(h);
+}
+
+// A fresh root: C = x, no overlay.
+__device__ __forceinline__ void init_node(const Nodes &P, uint32_t x)
+{
+    const unsigned long long v = (static_cast<unsigned long long>(kNone) << 32) | x;
+    if (x < P.cap)
+        *reinterpret_cast<volatile unsigned long long *>(P.s + x) = v;
+    else
+        __stcg(reinterpret_cast<unsigned long long *>(P.g + x), v);
 }
 
 __device__ __forceinline__ uint32_t node_parent(uint2 n) { return n.y != kNone ? n.y : n.x; }
 
 // Root of x with path halving.
-__device__ __forceinline__ uint32_t uf_find(uint2 *P, uint32_t x, uint32_t nold, uint32_t *logb,
+__device__ __forceinline__ uint32_t uf_find(const Nodes &P, uint32_t x, uint32_t nold, uint32_t *logb,
                                             uint32_t *logn)
 {
     for (;;) {
@@ -94,13 +131,11 @@ __device__ __forceinline__ uint32_t uf_find(uint2 *P, uint32_t x, uint32_t nold,
         const uint2 np = ld_node(P, p);
         const uint32_t g = node_parent(np);
         if (g == p) return p;
-        if (x >= nold) {
-            __stcg(&P[x].x, g);                          // new node
-        } else if (nx.y == kNone && np.y == kNone) {
-            __stcg(&P[x].x, g);                          // shortcut of two committed edges
+        if (x >= nold || (nx.y == kNone && np.y == kNone)) {
+            st_half(P, x, node_c(P, x), g);              // new node, or shortcut of two committed edges
         } else if (nx.y != kNone) {
-            __stcg(&P[x].y, g);                          // overlay already logged
-        } else if (atomicCAS(&P[x].y, kNone, g) == kNone) {
+            st_half(P, x, node_o(P, x), g);              // overlay already logged
+        } else if (atomicCAS(node_o(P, x), kNone, g) == kNone) {
             logb[atomicAdd(logn, 1u)] = x;               // first overlay write of x
         }
         x = g;
@@ -108,8 +143,9 @@ __device__ __forceinline__ uint32_t uf_find(uint2 *P, uint32_t x, uint32_t nold,
 }
 
 // Merge the clusters of a and b (the larger root goes under the smaller); true if a hook was made.
-__device__ __forceinline__ bool uf_unite(uint2 *P, uint32_t a, uint32_t b, uint32_t nold, uint32_t *logb,
-                                         uint32_t *logn)
+// Hooking node 1 (the x1 = L-1 border) decides the pass: it raises *stop.
+__device__ __forceinline__ bool uf_unite(const Nodes &P, uint32_t a, uint32_t b, uint32_t nold, uint32_t *logb,
+                                         uint32_t *logn, uint32_t *stop)
 {
     a = uf_find(P, a, nold, logb, logn);
     b = uf_find(P, b, nold, logb, logn);
@@ -118,10 +154,13 @@ __device__ __forceinline__ bool uf_unite(uint2 *P, uint32_t a, uint32_t b, uint3
         const uint32_t lo = a > b ? b : a;
         bool hooked;
         if (hi < nold) {
-            hooked = atomicCAS(&P[hi].y, kNone, lo) == kNone;
-            if (hooked) logb[atomicAdd(logn, 1u)] = hi;
+            hooked = atomicCAS(node_o(P, hi), kNone, lo) == kNone;
+            if (hooked) {
+                logb[atomicAdd(logn, 1u)] = hi;
+                if (hi == 1u && stop) *reinterpret_cast<volatile uint32_t *>(stop) = 1u;
+            }
         } else {
-            hooked = atomicCAS(&P[hi].x, hi, lo) == hi;
+            hooked = atomicCAS(node_c(P, hi), hi, lo) == hi;
         }
         if (hooked) return true;
         a = uf_find(P, hi, nold, logb, logn);  // hi was hooked meanwhile: continue from its root
@@ -247,8 +286,8 @@ __device__ void bitmap_update(uint32_t *bm, const uint32_t *perm, uint32_t bm_n,
 // 32 edges run side by side.
 constexpr uint32_t kNodeFlag = 0x80000000u;
 
-__device__ __forceinline__ uint32_t flush_one(uint2 e, const uint32_t *rank, uint2 *P, uint32_t nold,
-                                              uint32_t *logb, uint32_t *logn, uint32_t &unions)
+__device__ __forceinline__ uint32_t flush_one(uint2 e, const uint32_t *rank, const Nodes &P, uint32_t nold,
+                                              uint32_t *logb, uint32_t *logn, uint32_t *stop, uint32_t &unions)
 {
     uint32_t other;
     if (e.y & kNodeFlag) {
@@ -258,12 +297,13 @@ __device__ __forceinline__ uint32_t flush_one(uint2 e, const uint32_t *rank, uin
         if (other >= e.x) return 0u;  // the neighbor came later: it merges this edge itself
     }
     ++unions;
-    return uf_unite(P, e.x, other, nold, logb, logn) ? 1u : 0u;
+    return uf_unite(P, e.x, other, nold, logb, logn, stop) ? 1u : 0u;
 }
 
 __device__ __forceinline__ void push_edge(bool keep, uint32_t a, uint32_t b, uint2 *buf, uint32_t &cnt,
-                                          uint32_t lane, const uint32_t *rank, uint2 *P, uint32_t nold,
-                                          uint32_t *logb, uint32_t *logn, uint32_t &hooks, uint32_t &unions)
+                                          uint32_t lane, const uint32_t *rank, const Nodes &P, uint32_t nold,
+                                          uint32_t *logb, uint32_t *logn, uint32_t *stop, uint32_t &hooks,
+                                          uint32_t &unions)
 {
     const uint32_t bal = __ballot_sync(0xffffffffu, keep);
     if (bal == 0u) return;
@@ -271,7 +311,7 @@ __device__ __forceinline__ void push_edge(bool keep, uint32_t a, uint32_t b, uin
     cnt += __popc(bal);
     __syncwarp();
     if (cnt >= 32u) {
-        hooks += flush_one(buf[lane], rank, P, nold, logb, logn, unions);
+        hooks += flush_one(buf[lane], rank, P, nold, logb, logn, stop, unions);
         __syncwarp();
         if (lane + 32u < cnt) buf[lane] = buf[lane + 32u];
         cnt -= 32u;
@@ -294,7 +334,7 @@ __device__ __forceinline__ uint32_t lanes_shift(uint32_t count, uint32_t R)
 constexpr int kRowUnroll = 4;
 
 template <bool kSmemBm, bool kFaces>
-__device__ __forceinline__ void union_pass(Ctl &c, uint2 *P, uint32_t *logb, const uint32_t *bm,
+__device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *logb, const uint32_t *bm,
                                            const RowEntry *rows, uint2 *ebuf, const uint32_t *perm,
                                            const uint32_t *rank, uint32_t L, const FastDiv &fd,
                                            uint32_t r0, uint32_t r1, uint32_t nold)
@@ -305,7 +345,8 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint2 *P, uint32_t *logb, con
     const uint32_t gl = lane & ((1u << gshift) - 1u), gw = lane >> gshift, spw = 32u >> gshift;
     const uint32_t niter = (R + (1u << gshift) - 1u) >> gshift;
     uint2 *buf = ebuf + warp * kEdgeBuf;
-    uint32_t cnt = 0, hooks = 0, batch = 0, sites = 0, unions = 0;
+    uint32_t *stopp = kFaces ? &c.stop : nullptr;
+    uint32_t cnt = 0, hooks = 0, sites = 0, unions = 0;
     for (uint32_t base = r0 + warp * spw; base < r1; base += nwarps * spw) {
         if (kFaces && *reinterpret_cast<volatile uint32_t *>(&c.stop)) break;
         const uint32_t r = base + gw;
@@ -319,9 +360,9 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint2 *P, uint32_t *logb, con
         sites += (act && gl == 0u) ? 1u : 0u;
         if (kFaces) {
             push_edge(act && gl == 0u && x[0] == 0u, node, kNodeFlag | 0u, buf, cnt, lane, rank, P, nold, logb,
-                      &c.logn, hooks, unions);
+                      &c.logn, stopp, hooks, unions);
             push_edge(act && gl == 0u && x[0] == L - 1u, node, kNodeFlag | 1u, buf, cnt, lane, rank, P, nold, logb,
-                      &c.logn, hooks, unions);
+                      &c.logn, stopp, hooks, unions);
         }
         const uint32_t bit0 = i + kBmGuard - 2u;  // window start of the own row, before the row offset
         for (uint32_t t = 0; t < niter; t += kRowUnroll) {
@@ -352,14 +393,12 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint2 *P, uint32_t *logb, con
                         j = i + static_cast<uint32_t>(dl[u]) + (__ffs(h) - 1) - 2u;
                         h &= h - 1u;
                     }
-                    push_edge(keep, node, j, buf, cnt, lane, rank, P, nold, logb, &c.logn, hooks, unions);
+                    push_edge(keep, node, j, buf, cnt, lane, rank, P, nold, logb, &c.logn, stopp, hooks, unions);
                 }
             }
         }
-        if (kFaces && lane == 0u && ((++batch & 1u) == 0u) && ld_cg(&P[1].y) != kNone)
-            *reinterpret_cast<volatile uint32_t *>(&c.stop) = 1u;
     }
-    if (lane < cnt) hooks += flush_one(buf[lane], rank, P, nold, logb, &c.logn, unions);
+    if (lane < cnt) hooks += flush_one(buf[lane], rank, P, nold, logb, &c.logn, stopp, unions);
     __syncwarp();
     hooks = __reduce_add_sync(0xffffffffu, hooks);
     sites = __reduce_add_sync(0xffffffffu, sites);
@@ -437,7 +476,7 @@ __device__ uint32_t build_planes16(const RowEntry *rows, uint32_t R, PlaneEntry 
 constexpr int kPlaneUnroll = 2;
 
 template <bool kFaces>
-__device__ __forceinline__ void union_pass_planes16(Ctl &c, uint2 *P, uint32_t *logb, const uint32_t *bm,
+__device__ __forceinline__ void union_pass_planes16(Ctl &c, const Nodes &P, uint32_t *logb, const uint32_t *bm,
                                                     const PlaneEntry *planes, uint2 *ebuf, const uint32_t *perm,
                                                     const uint32_t *rank, uint32_t r0, uint32_t r1, uint32_t nold)
 {
@@ -447,7 +486,8 @@ __device__ __forceinline__ void union_pass_planes16(Ctl &c, uint2 *P, uint32_t *
     const uint32_t gl = lane & ((1u << gshift) - 1u), gw = lane >> gshift, spw = 32u >> gshift;
     const uint32_t niter = (NP + (1u << gshift) - 1u) >> gshift;
     uint2 *buf = ebuf + warp * kEdgeBuf;
-    uint32_t cnt = 0, hooks = 0, batch = 0, sites = 0, unions = 0;
+    uint32_t *stopp = kFaces ? &c.stop : nullptr;
+    uint32_t cnt = 0, hooks = 0, sites = 0, unions = 0;
     for (uint32_t base = r0 + warp * spw; base < r1; base += nwarps * spw) {
         if (kFaces && *reinterpret_cast<volatile uint32_t *>(&c.stop)) break;
         const uint32_t r = base + gw;
@@ -467,9 +507,9 @@ __device__ __forceinline__ void union_pass_planes16(Ctl &c, uint2 *P, uint32_t *
         sites += (act && gl == 0u) ? 1u : 0u;
         if (kFaces) {
             push_edge(act && gl == 0u && x1 == 0u, node, kNodeFlag | 0u, buf, cnt, lane, rank, P, nold, logb,
-                      &c.logn, hooks, unions);
+                      &c.logn, stopp, hooks, unions);
             push_edge(act && gl == 0u && x1 == kPlaneL - 1u, node, kNodeFlag | 1u, buf, cnt, lane, rank, P, nold,
-                      logb, &c.logn, hooks, unions);
+                      logb, &c.logn, stopp, hooks, unions);
         }
         for (uint32_t t = 0; t < niter; t += kPlaneUnroll) {
             uint32_t h[kPlaneUnroll][3];
@@ -483,7 +523,8 @@ __device__ __forceinline__ void union_pass_planes16(Ctl &c, uint2 *P, uint32_t *
                 dw[u] = e.dword;
                 if (ok && (e.oh & 0x7FFFu & ~a123) == 0u) {
                     const uint32_t *w = bm + (wbase + static_cast<uint32_t>(e.dword));
-                    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3];
+                    // the fourth word only matters when the 69-bit block starts past bit 27
+                    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = sh > 27u ? w[3] : 0u;
                     h[u][0] = __funnelshift_r(w0, w1, sh) & e.pm0 & sm0;
                     h[u][1] = __funnelshift_r(w1, w2, sh) & e.pm1 & sm1;
                     h[u][2] = __funnelshift_r(w2, w3, sh) & (e.oh >> 16) & sm2;
@@ -502,15 +543,13 @@ __device__ __forceinline__ void union_pass_planes16(Ctl &c, uint2 *P, uint32_t *
                                 static_cast<uint32_t>(__ffs(hf) - 1) - 34u;
                             hf &= hf - 1u;
                         }
-                        push_edge(keep, node, j, buf, cnt, lane, rank, P, nold, logb, &c.logn, hooks, unions);
+                        push_edge(keep, node, j, buf, cnt, lane, rank, P, nold, logb, &c.logn, stopp, hooks, unions);
                     }
                 }
             }
         }
-        if (kFaces && lane == 0u && ((++batch & 1u) == 0u) && ld_cg(&P[1].y) != kNone)
-            *reinterpret_cast<volatile uint32_t *>(&c.stop) = 1u;
     }
-    if (lane < cnt) hooks += flush_one(buf[lane], rank, P, nold, logb, &c.logn, unions);
+    if (lane < cnt) hooks += flush_one(buf[lane], rank, P, nold, logb, &c.logn, stopp, unions);
     __syncwarp();
     hooks = __reduce_add_sync(0xffffffffu, hooks);
     sites = __reduce_add_sync(0xffffffffu, sites);
@@ -546,6 +585,7 @@ struct SmemPtrs {
     uint2 *ebuf;
     uint32_t *scratch;
     uint32_t *sbm;
+    uint2 *nodes;  // the first node_cap union-find nodes
 };
 
 __host__ __device__ inline size_t smem_fixed_bytes(uint32_t threads)
@@ -556,7 +596,12 @@ __host__ __device__ inline size_t smem_fixed_bytes(uint32_t threads)
     return rows + ((eb + 15) & ~size_t(15));
 }
 
-__device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn)
+__host__ __device__ inline size_t smem_bitmap_bytes(uint32_t smem_L)
+{
+    return (size_t(bm_words(num_sites(smem_L))) * 4 + 15) & ~size_t(15);
+}
+
+__device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn, uint32_t smem_L)
 {
     SmemPtrs p;
     p.rows = reinterpret_cast<RowEntry *>(dyn);
@@ -564,6 +609,7 @@ __device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn)
     p.ebuf = reinterpret_cast<uint2 *>(dyn + sizeof(RowEntry) * kRowCand + sizeof(PlaneEntry) * kPlaneCand);
     p.scratch = reinterpret_cast<uint32_t *>(p.ebuf);
     p.sbm = reinterpret_cast<uint32_t *>(dyn + smem_fixed_bytes(blockDim.x));
+    p.nodes = reinterpret_cast<uint2 *>(dyn + smem_fixed_bytes(blockDim.x) + smem_bitmap_bytes(smem_L));
     return p;
 }
 
@@ -573,7 +619,7 @@ struct PhaseClock {
 };
 
 template <bool kSmemBm>
-__device__ __forceinline__ uint32_t probe(Ctl &c, uint2 *P, uint32_t *logb, uint32_t *bm,
+__device__ __forceinline__ uint32_t probe(Ctl &c, const Nodes &P, uint32_t *logb, uint32_t *bm,
                                           const SmemPtrs &sm, const uint32_t *perm, const uint32_t *rank,
                                           uint32_t L, const FastDiv &fd, PhaseClock &clk)
 {
@@ -581,8 +627,7 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, uint2 *P, uint32_t *logb, uint
     if (kSmemBm) bm = sm.sbm;  // keep the shared-memory address space visible to the compiler
     const long long t0 = clock64();
     bitmap_update(bm, perm, bm_n, mid);
-    for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x)
-        __stcg(reinterpret_cast<unsigned long long *>(P + r + 2u), (static_cast<unsigned long long>(kNone) << 32) | (r + 2u));
+    for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x) init_node(P, r + 2u);
     __syncthreads();
     const long long t1 = clock64();
     if (kSmemBm && L == kPlaneL)
@@ -593,13 +638,13 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, uint2 *P, uint32_t *logb, uint
     const long long t2 = clock64();
     clk.update += t1 - t0;
     clk.unite += t2 - t1;
-    const uint32_t span = ld_cg(&P[1].y) != kNone;  // node 1 can only be hooked under node 0
+    const uint32_t span = ld_node(P, 1u).y != kNone;  // node 1 can only be hooked under node 0
     const uint32_t logn = c.logn;
     __syncthreads();  // every thread has read span before node 1 may be reset below
     for (uint32_t k = threadIdx.x; k < logn; k += blockDim.x) {
         const uint32_t b = logb[k];
-        if (!span) __stcg(&P[b].x, ld_cg(&P[b].y));  // commit the overlay
-        __stcg(&P[b].y, kNone);
+        if (!span) st_half(P, b, node_c(P, b), ld_half(P, b, node_o(P, b)));  // commit the overlay
+        st_half(P, b, node_o(P, b), kNone);
     }
     __syncthreads();
     clk.commit += clock64() - t2;
@@ -607,17 +652,17 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, uint2 *P, uint32_t *logb, uint
 }
 
 __global__ void __launch_bounds__(1024, 1)
-k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L,
+k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t node_cap,
         const uint32_t *__restrict__ bracket, uint32_t *__restrict__ nstar_out,
         uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
-    const SmemPtrs sm = smem_ptrs(dyn);
+    const SmemPtrs sm = smem_ptrs(dyn, smem_L);
     __shared__ Ctl c;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
     const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
-    uint2 *P = sp.P;
+    const Nodes P{sm.nodes, sp.P, node_cap};
     uint32_t *logb = sp.logb;
     unsigned long long tot_passes = 0, tot_probe = 0, tot_early = 0, tot_fb = 0, tot_ok = 0;
     PhaseClock clk;
@@ -653,8 +698,8 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
         build_rows(mask, L, sm.rows, sm.scratch, c);
         if (smem_bm && L == kPlaneL) build_planes16(sm.rows, c.R, sm.planes, sm.scratch, c);
         if (threadIdx.x == 0) {
-            __stcg(reinterpret_cast<unsigned long long *>(P + 0), static_cast<unsigned long long>(kNone) << 32);
-            __stcg(reinterpret_cast<unsigned long long *>(P + 1), (static_cast<unsigned long long>(kNone) << 32) | 1u);
+            init_node(P, 0u);
+            init_node(P, 1u);
         }
         const FastDiv fd = make_fastdiv(L);
         __syncthreads();
@@ -755,17 +800,17 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
 
 // S_max(n) per sample: one full pass over the first n sites, then cluster sizes by root counting.
 __global__ void __launch_bounds__(1024, 1)
-k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L,
+k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t node_cap,
        const uint64_t *__restrict__ n_in, int64_t *__restrict__ mass_out, char *ws, size_t slot_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
-    const SmemPtrs sm = smem_ptrs(dyn);
+    const SmemPtrs sm = smem_ptrs(dyn, smem_L);
     __shared__ Ctl c;
     __shared__ uint32_t red[32];
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
     const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
-    uint2 *P = sp.P;
+    const Nodes P{sm.nodes, sp.P, node_cap};
     uint32_t *cnt = sp.logb;
 
     for (;;) {
@@ -801,7 +846,7 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         __syncthreads();
         bitmap_update(bm, smp.perm, 0u, n);
         for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) {
-            __stcg(reinterpret_cast<unsigned long long *>(P + r + 2u), (static_cast<unsigned long long>(kNone) << 32) | (r + 2u));
+            init_node(P, r + 2u);
             __stcg(cnt + r + 2u, 0u);
         }
         __syncthreads();
@@ -836,6 +881,7 @@ struct LaunchCfg {
     int threads = 0;
     size_t smem = 0;
     uint32_t smem_L = 0;
+    uint32_t node_cap = 0;
     uint32_t grid = 0;
     size_t slot_bytes = 0;
 };
@@ -855,10 +901,24 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
     int dflt_threads = max_L <= 8 ? 256 : (max_L <= 12 ? 512 : 1024);
     cfg.threads = env_int("PERC_THREADS", dflt_threads);
     if (cfg.threads < 32 || cfg.threads > 1024 || (cfg.threads & 31)) return PERC_EINVAL;
-    cfg.smem = smem_fixed_bytes(cfg.threads) + size_t(bm_words(smem_sites)) * 4;
-    int dev = 0, sms = 0, occ = 0;
+    int dev = 0, sms = 0, occ = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PERC_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PERC_ECUDA;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return PERC_ECUDA;
+    // shared memory per CTA: the register file allows 65536 / (threads * 64) CTAs per SM (64
+    // registers a thread); every CTA gets an equal share, and what the tables, edge buffers and
+    // bitmap leave holds the first union-find nodes
+    (void)smem_sites;
+    const int ctas = (65536 / (cfg.threads * 64)) > 0 ? 65536 / (cfg.threads * 64) : 1;
+    const size_t share = size_t(optin) / ctas - 1024;  // static shared memory and slack
+    const size_t base = smem_fixed_bytes(cfg.threads) + smem_bitmap_bytes(cfg.smem_L);
+    if (base + 64 * 8 > share) return PERC_EINVAL;
+    size_t cap = (share - base) / 8;
+    const int cap_env = env_int("PERC_SMEM_NODES", -1);
+    if (cap_env >= 0 && size_t(cap_env) < cap) cap = cap_env;
+    cfg.node_cap = static_cast<uint32_t>(cap);
+    cfg.smem = base + cap * 8;
     const void *fn = op == PERC_OP_MASS ? reinterpret_cast<const void *>(k_mass)
                                         : reinterpret_cast<const void *>(k_nstar);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cfg.smem)) != cudaSuccess)
@@ -871,8 +931,8 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
     const size_t gbm = max_L > cfg.smem_L ? (size_t(bm_words(Ncap)) * 4 + 255) & ~size_t(255) : 0;
     cfg.slot_bytes = nodes + logs + gbm;
     uint64_t grid = uint64_t(sms) * occ;
-    const int cap = env_int("PERC_MAX_CTAS", 0);
-    if (cap > 0 && uint64_t(cap) < grid) grid = cap;
+    const int cta_cap = env_int("PERC_MAX_CTAS", 0);
+    if (cta_cap > 0 && uint64_t(cta_cap) < grid) grid = cta_cap;
     if (grid > num) grid = num;
     const uint64_t mem_cap = kSlotCapBytes / cfg.slot_bytes;
     if (grid > mem_cap) grid = mem_cap > 0 ? mem_cap : 1;
@@ -907,7 +967,7 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
     if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
-    k_nstar<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, bracket,
+    k_nstar<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap, bracket,
                                                          nstar, passes, stats, static_cast<char *>(workspace),
                                                          cfg.slot_bytes);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
@@ -923,7 +983,7 @@ extern "C" int perc_mass(const perc_sample *samples, uint32_t num_samples, uint3
     if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
-    k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, n, mass,
+    k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap, n, mass,
                                                         static_cast<char *>(workspace), cfg.slot_bytes);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }
