@@ -34,6 +34,7 @@
 
 namespace perc {
 
+constexpr uint32_t kTag = 0x80000000u;
 constexpr uint32_t kSmemBitmapMaxL = 17;
 constexpr size_t kSlotCapBytes = size_t(32) << 30;  // total per-CTA slot memory aimed at
 
@@ -62,109 +63,45 @@ struct Ctl {
 };
 
 // ------------------------------------------------------------------------------------------------
-// union-find on rank-space nodes (global memory, L2-coherent loads).
-//
-// A node is one 64-bit word: the committed parent C (low half) and the overlay parent O of the
-// running probe (high half, kNone when unset).  Its parent is O if set, else C.  Nodes below nold
-// existed at the committed (last non-spanning) state: during a probe their changes go to O only,
-// and the first write of an O is logged.  Undo (a spanning probe) clears the logged O; commit
-// copies them into C.  Nodes at or above nold are new and use C directly.  Because every write of
-// an old node lands in its overlay, path halving may shortcut any edge.
+// union-find on rank-space nodes (global memory, L2-coherent loads)
 // ------------------------------------------------------------------------------------------------
-constexpr uint32_t kNone = 0xFFFFFFFFu;
-
 __device__ __forceinline__ uint32_t ld_cg(const uint32_t *p) { return __ldcg(p); }
 
-// Nodes below `cap` live in shared memory, the others in the CTA's global slot (same indexing).
-struct Nodes {
-    uint2 *s;
-    uint2 *g;
-    uint32_t cap;
-};
-
-__device__ __forceinline__ uint2 ld_node(const Nodes &P, uint32_t x)
-{
-    unsigned long long v;
-    if (x < P.cap)
-        v = *reinterpret_cast<volatile unsigned long long *>(P.s + x);
-    else
-        v = __ldcg(reinterpret_cast<const unsigned long long *>(P.g + x));
-    return make_uint2(static_cast<uint32_t>(v), static_cast<uint32_t>(v >> 32));
-}
-
-__device__ __forceinline__ uint32_t *node_c(const Nodes &P, uint32_t x) { return x < P.cap ? &P.s[x].x : &P.g[x].x; }
-__device__ __forceinline__ uint32_t *node_o(const Nodes &P, uint32_t x) { return x < P.cap ? &P.s[x].y : &P.g[x].y; }
-
-__device__ __forceinline__ void st_half(const Nodes &P, uint32_t x, uint32_t *h, uint32_t v)
-{
-    if (x < P.cap)
-        *reinterpret_cast<volatile uint32_t *>(h) = v;
-    else
-        __stcg(h, v);
-}
-
-__device__ __forceinline__ uint32_t ld_half(const Nodes &P, uint32_t x, const uint32_t *h)
-{
-    return x < P.cap ? *reinterpret_cast<const volatile uint32_t *>(h) : __ldcg(h);
-}
-
-// A fresh root: C = x, no overlay.
-__device__ __forceinline__ void init_node(const Nodes &P, uint32_t x)
-{
-    const unsigned long long v = (static_cast<unsigned long long>(kNone) << 32) | x;
-    if (x < P.cap)
-        *reinterpret_cast<volatile unsigned long long *>(P.s + x) = v;
-    else
-        __stcg(reinterpret_cast<unsigned long long *>(P.g + x), v);
-}
-
-__device__ __forceinline__ uint32_t node_parent(uint2 n) { return n.y != kNone ? n.y : n.x; }
-
-// Root of x with path halving.
-__device__ __forceinline__ uint32_t uf_find(const Nodes &P, uint32_t x, uint32_t nold, uint32_t *logb,
-                                            uint32_t *logn)
+// Root of x with path halving.  Nodes below nold existed at the committed state: their pointer is
+// rewritten only when both skipped edges are untagged (committed edges).
+__device__ __forceinline__ uint32_t uf_find(uint32_t *P, uint32_t x, uint32_t nold)
 {
     for (;;) {
-        const uint2 nx = ld_node(P, x);
-        const uint32_t p = node_parent(nx);
-        if (p == x) return x;
-        const uint2 np = ld_node(P, p);
-        const uint32_t g = node_parent(np);
-        if (g == p) return p;
-        if (x >= nold || (nx.y == kNone && np.y == kNone)) {
-            st_half(P, x, node_c(P, x), g);              // new node, or shortcut of two committed edges
-        } else if (nx.y != kNone) {
-            st_half(P, x, node_o(P, x), g);              // overlay already logged
-        } else if (atomicCAS(node_o(P, x), kNone, g) == kNone) {
-            logb[atomicAdd(logn, 1u)] = x;               // first overlay write of x
-        }
-        x = g;
+        const uint32_t p = ld_cg(P + x);
+        const uint32_t pu = p & ~kTag;
+        if (pu == x) return x;
+        const uint32_t g = ld_cg(P + pu);
+        const uint32_t gu = g & ~kTag;
+        if (gu == pu) return pu;
+        if (x >= nold || ((p | g) & kTag) == 0u) __stcg(P + x, gu);
+        x = gu;
     }
 }
 
-// Merge the clusters of a and b (the larger root goes under the smaller); true if a hook was made.
-// Hooking node 1 (the x1 = L-1 border) decides the pass: it raises *stop.
-__device__ __forceinline__ bool uf_unite(const Nodes &P, uint32_t a, uint32_t b, uint32_t nold, uint32_t *logb,
-                                         uint32_t *logn, uint32_t *stop)
+// Merge the clusters of a and b; returns true if a hook was made.  Hooking node 1 (the x1 = L-1
+// border, which only node 0 can take) decides the pass: it raises *stop.
+__device__ __forceinline__ bool uf_unite(uint32_t *P, uint32_t a, uint32_t b, uint32_t nold,
+                                         uint32_t *logb, uint32_t *logn, uint32_t *stop)
 {
-    a = uf_find(P, a, nold, logb, logn);
-    b = uf_find(P, b, nold, logb, logn);
+    a = uf_find(P, a, nold);
+    b = uf_find(P, b, nold);
     while (a != b) {
         const uint32_t hi = a > b ? a : b;
         const uint32_t lo = a > b ? b : a;
-        bool hooked;
-        if (hi < nold) {
-            hooked = atomicCAS(node_o(P, hi), kNone, lo) == kNone;
-            if (hooked) {
-                logb[atomicAdd(logn, 1u)] = hi;
-                if (hi == 1u && stop) *reinterpret_cast<volatile uint32_t *>(stop) = 1u;
-            }
-        } else {
-            hooked = atomicCAS(node_c(P, hi), hi, lo) == hi;
+        const bool old = hi < nold;
+        const uint32_t seen = atomicCAS(P + hi, hi, old ? (lo | kTag) : lo);
+        if (seen == hi) {
+            if (old) logb[atomicAdd(logn, 1u)] = hi;
+            if (hi == 1u && stop) *reinterpret_cast<volatile uint32_t *>(stop) = 1u;
+            return true;
         }
-        if (hooked) return true;
-        a = uf_find(P, hi, nold, logb, logn);  // hi was hooked meanwhile: continue from its root
-        b = uf_find(P, lo, nold, logb, logn);
+        a = uf_find(P, seen & ~kTag, nold);  // hi was hooked meanwhile: continue from its root
+        b = uf_find(P, lo, nold);
     }
     return false;
 }
@@ -286,7 +223,7 @@ __device__ void bitmap_update(uint32_t *bm, const uint32_t *perm, uint32_t bm_n,
 // 32 edges run side by side.
 constexpr uint32_t kNodeFlag = 0x80000000u;
 
-__device__ __forceinline__ uint32_t flush_one(uint2 e, const uint32_t *rank, const Nodes &P, uint32_t nold,
+__device__ __forceinline__ uint32_t flush_one(uint2 e, const uint32_t *rank, uint32_t *P, uint32_t nold,
                                               uint32_t *logb, uint32_t *logn, uint32_t *stop, uint32_t &unions)
 {
     uint32_t other;
@@ -301,7 +238,7 @@ __device__ __forceinline__ uint32_t flush_one(uint2 e, const uint32_t *rank, con
 }
 
 __device__ __forceinline__ void push_edge(bool keep, uint32_t a, uint32_t b, uint2 *buf, uint32_t &cnt,
-                                          uint32_t lane, const uint32_t *rank, const Nodes &P, uint32_t nold,
+                                          uint32_t lane, const uint32_t *rank, uint32_t *P, uint32_t nold,
                                           uint32_t *logb, uint32_t *logn, uint32_t *stop, uint32_t &hooks,
                                           uint32_t &unions)
 {
@@ -334,7 +271,7 @@ __device__ __forceinline__ uint32_t lanes_shift(uint32_t count, uint32_t R)
 constexpr int kRowUnroll = 4;
 
 template <bool kSmemBm, bool kFaces>
-__device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *logb, const uint32_t *bm,
+__device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, const uint32_t *bm,
                                            const RowEntry *rows, uint2 *ebuf, const uint32_t *perm,
                                            const uint32_t *rank, uint32_t L, const FastDiv &fd,
                                            uint32_t r0, uint32_t r1, uint32_t nold)
@@ -476,7 +413,7 @@ __device__ uint32_t build_planes16(const RowEntry *rows, uint32_t R, PlaneEntry 
 constexpr int kPlaneUnroll = 2;
 
 template <bool kFaces>
-__device__ __forceinline__ void union_pass_planes16(Ctl &c, const Nodes &P, uint32_t *logb, const uint32_t *bm,
+__device__ __forceinline__ void union_pass_planes16(Ctl &c, uint32_t *P, uint32_t *logb, const uint32_t *bm,
                                                     const PlaneEntry *planes, uint2 *ebuf, const uint32_t *perm,
                                                     const uint32_t *rank, uint32_t r0, uint32_t r1, uint32_t nold)
 {
@@ -562,19 +499,17 @@ __device__ __forceinline__ void union_pass_planes16(Ctl &c, const Nodes &P, uint
 }
 
 struct SlotPtrs {
-    uint2 *P;
-    uint32_t *logb, *gbm;
+    uint32_t *P, *logb, *gbm;
 };
 
 __device__ __forceinline__ SlotPtrs slot_ptrs(char *ws, size_t slot_bytes, uint64_t Ncap, bool gbm)
 {
     char *base = ws + sizeof(WsHeader) + size_t(blockIdx.x) * slot_bytes;
-    const size_t nodes = ((Ncap + 2) * 8 + 255) & ~size_t(255);
-    const size_t logs = ((Ncap + 2) * 4 + 255) & ~size_t(255);
+    const size_t nodes = ((Ncap + 2) * 4 + 255) & ~size_t(255);
     SlotPtrs s;
-    s.P = reinterpret_cast<uint2 *>(base);
+    s.P = reinterpret_cast<uint32_t *>(base);
     s.logb = reinterpret_cast<uint32_t *>(base + nodes);
-    s.gbm = gbm ? reinterpret_cast<uint32_t *>(base + nodes + logs) : nullptr;
+    s.gbm = gbm ? reinterpret_cast<uint32_t *>(base + 2 * nodes) : nullptr;
     return s;
 }
 
@@ -585,7 +520,6 @@ struct SmemPtrs {
     uint2 *ebuf;
     uint32_t *scratch;
     uint32_t *sbm;
-    uint2 *nodes;  // the first node_cap union-find nodes
 };
 
 __host__ __device__ inline size_t smem_fixed_bytes(uint32_t threads)
@@ -596,12 +530,7 @@ __host__ __device__ inline size_t smem_fixed_bytes(uint32_t threads)
     return rows + ((eb + 15) & ~size_t(15));
 }
 
-__host__ __device__ inline size_t smem_bitmap_bytes(uint32_t smem_L)
-{
-    return (size_t(bm_words(num_sites(smem_L))) * 4 + 15) & ~size_t(15);
-}
-
-__device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn, uint32_t smem_L)
+__device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn)
 {
     SmemPtrs p;
     p.rows = reinterpret_cast<RowEntry *>(dyn);
@@ -609,7 +538,6 @@ __device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn, uint32_t smem_
     p.ebuf = reinterpret_cast<uint2 *>(dyn + sizeof(RowEntry) * kRowCand + sizeof(PlaneEntry) * kPlaneCand);
     p.scratch = reinterpret_cast<uint32_t *>(p.ebuf);
     p.sbm = reinterpret_cast<uint32_t *>(dyn + smem_fixed_bytes(blockDim.x));
-    p.nodes = reinterpret_cast<uint2 *>(dyn + smem_fixed_bytes(blockDim.x) + smem_bitmap_bytes(smem_L));
     return p;
 }
 
@@ -619,7 +547,7 @@ struct PhaseClock {
 };
 
 template <bool kSmemBm>
-__device__ __forceinline__ uint32_t probe(Ctl &c, const Nodes &P, uint32_t *logb, uint32_t *bm,
+__device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, uint32_t *bm,
                                           const SmemPtrs &sm, const uint32_t *perm, const uint32_t *rank,
                                           uint32_t L, const FastDiv &fd, PhaseClock &clk)
 {
@@ -627,7 +555,7 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, const Nodes &P, uint32_t *logb
     if (kSmemBm) bm = sm.sbm;  // keep the shared-memory address space visible to the compiler
     const long long t0 = clock64();
     bitmap_update(bm, perm, bm_n, mid);
-    for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x) init_node(P, r + 2u);
+    for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x) __stcg(P + r + 2u, r + 2u);
     __syncthreads();
     const long long t1 = clock64();
     if (kSmemBm && L == kPlaneL)
@@ -638,13 +566,12 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, const Nodes &P, uint32_t *logb
     const long long t2 = clock64();
     clk.update += t1 - t0;
     clk.unite += t2 - t1;
-    const uint32_t span = ld_node(P, 1u).y != kNone;  // node 1 can only be hooked under node 0
+    const uint32_t span = ld_cg(P + 1) != 1u;
     const uint32_t logn = c.logn;
     __syncthreads();  // every thread has read span before node 1 may be reset below
     for (uint32_t k = threadIdx.x; k < logn; k += blockDim.x) {
         const uint32_t b = logb[k];
-        if (!span) st_half(P, b, node_c(P, b), ld_half(P, b, node_o(P, b)));  // commit the overlay
-        st_half(P, b, node_o(P, b), kNone);
+        __stcg(P + b, span ? b : (ld_cg(P + b) & ~kTag));  // undo, or commit the hook
     }
     __syncthreads();
     clk.commit += clock64() - t2;
@@ -652,18 +579,17 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, const Nodes &P, uint32_t *logb
 }
 
 __global__ void __launch_bounds__(1024, 1)
-k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t node_cap,
+k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L,
         const uint32_t *__restrict__ bracket, uint32_t *__restrict__ nstar_out,
         uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
-    const SmemPtrs sm = smem_ptrs(dyn, smem_L);
+    const SmemPtrs sm = smem_ptrs(dyn);
     __shared__ Ctl c;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
     const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
-    const Nodes P{sm.nodes, sp.P, node_cap};
-    uint32_t *logb = sp.logb;
+    uint32_t *P = sp.P, *logb = sp.logb;
     unsigned long long tot_passes = 0, tot_probe = 0, tot_early = 0, tot_fb = 0, tot_ok = 0;
     PhaseClock clk;
 
@@ -698,8 +624,8 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
         build_rows(mask, L, sm.rows, sm.scratch, c);
         if (smem_bm && L == kPlaneL) build_planes16(sm.rows, c.R, sm.planes, sm.scratch, c);
         if (threadIdx.x == 0) {
-            init_node(P, 0u);
-            init_node(P, 1u);
+            __stcg(P + 0, 0u);
+            __stcg(P + 1, 1u);
         }
         const FastDiv fd = make_fastdiv(L);
         __syncthreads();
@@ -800,18 +726,17 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
 
 // S_max(n) per sample: one full pass over the first n sites, then cluster sizes by root counting.
 __global__ void __launch_bounds__(1024, 1)
-k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t node_cap,
+k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L,
        const uint64_t *__restrict__ n_in, int64_t *__restrict__ mass_out, char *ws, size_t slot_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
-    const SmemPtrs sm = smem_ptrs(dyn, smem_L);
+    const SmemPtrs sm = smem_ptrs(dyn);
     __shared__ Ctl c;
     __shared__ uint32_t red[32];
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
     const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
-    const Nodes P{sm.nodes, sp.P, node_cap};
-    uint32_t *cnt = sp.logb;
+    uint32_t *P = sp.P, *cnt = sp.logb;
 
     for (;;) {
         if (threadIdx.x == 0) c.sample = atomicAdd(&hdr->queue, 1u);
@@ -846,7 +771,7 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         __syncthreads();
         bitmap_update(bm, smp.perm, 0u, n);
         for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) {
-            init_node(P, r + 2u);
+            __stcg(P + r + 2u, r + 2u);
             __stcg(cnt + r + 2u, 0u);
         }
         __syncthreads();
@@ -857,7 +782,7 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         else
             union_pass<false, false>(c, P, nullptr, bm, sm.rows, sm.ebuf, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         __syncthreads();
-        for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) atomicAdd(cnt + uf_find(P, r + 2u, 0u, nullptr, nullptr), 1u);
+        for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) atomicAdd(cnt + uf_find(P, r + 2u, 0u), 1u);
         __syncthreads();
         uint32_t best = 0;
         for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) best = max(best, ld_cg(cnt + r + 2u));
@@ -881,7 +806,6 @@ struct LaunchCfg {
     int threads = 0;
     size_t smem = 0;
     uint32_t smem_L = 0;
-    uint32_t node_cap = 0;
     uint32_t grid = 0;
     size_t slot_bytes = 0;
 };
@@ -901,24 +825,10 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
     int dflt_threads = max_L <= 8 ? 256 : (max_L <= 12 ? 512 : 1024);
     cfg.threads = env_int("PERC_THREADS", dflt_threads);
     if (cfg.threads < 32 || cfg.threads > 1024 || (cfg.threads & 31)) return PERC_EINVAL;
-    int dev = 0, sms = 0, occ = 0, optin = 0;
+    cfg.smem = smem_fixed_bytes(cfg.threads) + size_t(bm_words(smem_sites)) * 4;
+    int dev = 0, sms = 0, occ = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PERC_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PERC_ECUDA;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-        return PERC_ECUDA;
-    // shared memory per CTA: the register file allows 65536 / (threads * 64) CTAs per SM (64
-    // registers a thread); every CTA gets an equal share, and what the tables, edge buffers and
-    // bitmap leave holds the first union-find nodes
-    (void)smem_sites;
-    const int ctas = (65536 / (cfg.threads * 64)) > 0 ? 65536 / (cfg.threads * 64) : 1;
-    const size_t share = size_t(optin) / ctas - 1024;  // static shared memory and slack
-    const size_t base = smem_fixed_bytes(cfg.threads) + smem_bitmap_bytes(cfg.smem_L);
-    if (base + 64 * 8 > share) return PERC_EINVAL;
-    size_t cap = (share - base) / 8;
-    const int cap_env = env_int("PERC_SMEM_NODES", -1);
-    if (cap_env >= 0 && size_t(cap_env) < cap) cap = cap_env;
-    cfg.node_cap = static_cast<uint32_t>(cap);
-    cfg.smem = base + cap * 8;
     const void *fn = op == PERC_OP_MASS ? reinterpret_cast<const void *>(k_mass)
                                         : reinterpret_cast<const void *>(k_nstar);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cfg.smem)) != cudaSuccess)
@@ -926,13 +836,12 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, cfg.threads, cfg.smem) != cudaSuccess)
         return PERC_ECUDA;
     if (occ < 1) return PERC_EINVAL;
-    const size_t nodes = ((Ncap + 2) * 8 + 255) & ~size_t(255);
-    const size_t logs = ((Ncap + 2) * 4 + 255) & ~size_t(255);
+    const size_t nodes = ((Ncap + 2) * 4 + 255) & ~size_t(255);
     const size_t gbm = max_L > cfg.smem_L ? (size_t(bm_words(Ncap)) * 4 + 255) & ~size_t(255) : 0;
-    cfg.slot_bytes = nodes + logs + gbm;
+    cfg.slot_bytes = 2 * nodes + gbm;
     uint64_t grid = uint64_t(sms) * occ;
-    const int cta_cap = env_int("PERC_MAX_CTAS", 0);
-    if (cta_cap > 0 && uint64_t(cta_cap) < grid) grid = cta_cap;
+    const int cap = env_int("PERC_MAX_CTAS", 0);
+    if (cap > 0 && uint64_t(cap) < grid) grid = cap;
     if (grid > num) grid = num;
     const uint64_t mem_cap = kSlotCapBytes / cfg.slot_bytes;
     if (grid > mem_cap) grid = mem_cap > 0 ? mem_cap : 1;
@@ -967,7 +876,7 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
     if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
-    k_nstar<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap, bracket,
+    k_nstar<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, bracket,
                                                          nstar, passes, stats, static_cast<char *>(workspace),
                                                          cfg.slot_bytes);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
@@ -983,7 +892,7 @@ extern "C" int perc_mass(const perc_sample *samples, uint32_t num_samples, uint3
     if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
-    k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap, n, mass,
+    k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, n, mass,
                                                         static_cast<char *>(workspace), cfg.slot_bytes);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }
