@@ -59,6 +59,7 @@ struct Ctl {
     uint32_t z;       // offsets of the sample's neighborhood
     uint32_t R;       // row entries of the sample's neighborhood
     uint32_t NP;      // plane entries (L = 16 path)
+    uint32_t ecount[2];  // edge-list fill of the current and the next chunk
     unsigned long long hooks, new_sites, sites, unions;
 };
 
@@ -119,7 +120,6 @@ struct __align__(16) RowEntry {
     uint32_t pad;
 };
 constexpr int kRowCand = 625;  // (d1..d4) in {-2..2}^4
-constexpr int kEdgeBuf = 64;   // per-warp buffer of pending unions
 
 // Builds the row table of `mask` for side L (all threads; ends with a barrier); returns the count
 // of rows and writes the number of offsets to *z.
@@ -216,15 +216,40 @@ __device__ void bitmap_update(uint32_t *bm, const uint32_t *perm, uint32_t bm_n,
     }
 }
 
-// Warp-collective edge buffer.  An entry (a, b) is either a border union (b = node 0 or 1 with
-// kNodeFlag set) or a neighbor site b of node a, whose rank is looked up when the entry is
-// flushed; the Newman--Ziff rule (merge only neighbors of smaller rank) is applied there.  Once 32
-// entries are pending, all lanes flush one each, so the rank loads and the union-find chains of
-// 32 edges run side by side.
+// ------------------------------------------------------------------------------------------------
+// A connected-component pass over the new sites runs in chunks of up to blockDim sites, each in
+// two phases:
+//   scan  -- every thread tests the neighborhood of its site (or a share of it when a chunk has
+//            few sites) against the bitmap and appends each hit as an edge (node, neighbor site) to
+//            the CTA's edge list (shared memory, overflowing into the CTA's global slot);
+//   unite -- every thread takes edges from the list, looks up the neighbor's rank, keeps the edge
+//            if the neighbor came earlier (the Newman--Ziff rule: an edge is merged by its later
+//            site) and merges the two clusters.
+// Border edges (node 0 for x1 = 0, node 1 for x1 = L-1) carry kNodeFlag and skip the lookup.
+// ------------------------------------------------------------------------------------------------
 constexpr uint32_t kNodeFlag = 0x80000000u;
 
-__device__ __forceinline__ uint32_t flush_one(uint2 e, const uint32_t *rank, uint32_t *P, uint32_t nold,
-                                              uint32_t *logb, uint32_t *logn, uint32_t *stop, uint32_t &unions)
+struct EdgeList {
+    uint2 *s;       // shared part
+    uint32_t scap;  // entries in the shared part
+    uint2 *g;       // global overflow (entries scap..)
+};
+
+__device__ __forceinline__ void edge_put(const EdgeList &E, uint32_t k, uint2 v)
+{
+    if (k < E.scap)
+        E.s[k] = v;
+    else
+        E.g[k - E.scap] = v;
+}
+
+__device__ __forceinline__ uint2 edge_get(const EdgeList &E, uint32_t k)
+{
+    return k < E.scap ? E.s[k] : E.g[k - E.scap];
+}
+
+__device__ __forceinline__ uint32_t unite_edge(uint2 e, const uint32_t *rank, uint32_t *P, uint32_t nold,
+                                               uint32_t *logb, uint32_t *logn, uint32_t *stop, uint32_t &unions)
 {
     uint32_t other;
     if (e.y & kNodeFlag) {
@@ -237,114 +262,13 @@ __device__ __forceinline__ uint32_t flush_one(uint2 e, const uint32_t *rank, uin
     return uf_unite(P, e.x, other, nold, logb, logn, stop) ? 1u : 0u;
 }
 
-__device__ __forceinline__ void push_edge(bool keep, uint32_t a, uint32_t b, uint2 *buf, uint32_t &cnt,
-                                          uint32_t lane, const uint32_t *rank, uint32_t *P, uint32_t nold,
-                                          uint32_t *logb, uint32_t *logn, uint32_t *stop, uint32_t &hooks,
-                                          uint32_t &unions)
-{
-    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-    if (bal == 0u) return;
-    if (keep) buf[cnt + __popc(bal & ((1u << lane) - 1u))] = make_uint2(a, b);
-    cnt += __popc(bal);
-    __syncwarp();
-    if (cnt >= 32u) {
-        hooks += flush_one(buf[lane], rank, P, nold, logb, logn, stop, unions);
-        __syncwarp();
-        if (lane + 32u < cnt) buf[lane] = buf[lane + 32u];
-        cnt -= 32u;
-        __syncwarp();
-    }
-}
-
-// log2 of the lanes that share one site in a pass that merges `count` sites: one site per lane
-// when there are enough sites for every lane, otherwise the rows of a site are split over lanes.
+// log2 of the threads that share one site in a chunk of `count` sites: one site per thread when
+// there are enough sites, otherwise the neighborhood of a site is split over threads.
 __device__ __forceinline__ uint32_t lanes_shift(uint32_t count, uint32_t R)
 {
     uint32_t s = 0;
     while (s < 5u && (count << (s + 1)) <= blockDim.x && (1u << s) < R) ++s;
     return s;
-}
-
-// Merge the sites of rank [r0, r1) with their occupied neighbors of smaller rank (the
-// Newman--Ziff rule: an edge is merged by its later site).  With kFaces the border nodes take part
-// and the pass stops early once node 1 is hooked.
-constexpr int kRowUnroll = 4;
-
-template <bool kSmemBm, bool kFaces>
-__device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, const uint32_t *bm,
-                                           const RowEntry *rows, uint2 *ebuf, const uint32_t *perm,
-                                           const uint32_t *rank, uint32_t L, const FastDiv &fd,
-                                           uint32_t r0, uint32_t r1, uint32_t nold)
-{
-    const uint32_t R = c.R;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const uint32_t gshift = lanes_shift(r1 - r0, R);
-    const uint32_t gl = lane & ((1u << gshift) - 1u), gw = lane >> gshift, spw = 32u >> gshift;
-    const uint32_t niter = (R + (1u << gshift) - 1u) >> gshift;
-    uint2 *buf = ebuf + warp * kEdgeBuf;
-    uint32_t *stopp = kFaces ? &c.stop : nullptr;
-    uint32_t cnt = 0, hooks = 0, sites = 0, unions = 0;
-    for (uint32_t base = r0 + warp * spw; base < r1; base += nwarps * spw) {
-        if (kFaces && *reinterpret_cast<volatile uint32_t *>(&c.stop)) break;
-        const uint32_t r = base + gw;
-        const bool act = r < r1;
-        const uint32_t i = act ? __ldg(perm + r) : 0u;
-        uint32_t x[5];
-        site_coords(i, fd, x);
-        const uint32_t allowed = site_allowed(x, L);
-        const uint32_t a5 = allowed >> 20;
-        const uint32_t node = r + 2u;
-        sites += (act && gl == 0u) ? 1u : 0u;
-        if (kFaces) {
-            push_edge(act && gl == 0u && x[0] == 0u, node, kNodeFlag | 0u, buf, cnt, lane, rank, P, nold, logb,
-                      &c.logn, stopp, hooks, unions);
-            push_edge(act && gl == 0u && x[0] == L - 1u, node, kNodeFlag | 1u, buf, cnt, lane, rank, P, nold, logb,
-                      &c.logn, stopp, hooks, unions);
-        }
-        const uint32_t bit0 = i + kBmGuard - 2u;  // window start of the own row, before the row offset
-        for (uint32_t t = 0; t < niter; t += kRowUnroll) {
-            uint32_t hits[kRowUnroll];
-            int32_t dl[kRowUnroll];
-#pragma unroll
-            for (int u = 0; u < kRowUnroll; ++u) {
-                const uint32_t k = gl + ((t + u) << gshift);
-                const bool ok = act && k < R;
-                const RowEntry e = rows[ok ? k : 0u];
-                uint32_t h = 0u;
-                if (ok && (e.onehot & ~allowed) == 0u) {
-                    const uint32_t b = bit0 + static_cast<uint32_t>(e.delta);
-                    const uint32_t w = __funnelshift_r(bm_word<kSmemBm>(bm, b >> 5), bm_word<kSmemBm>(bm, (b >> 5) + 1u),
-                                                       b & 31u);
-                    h = w & e.d5mask & a5;
-                }
-                hits[u] = h;
-                dl[u] = e.delta;
-            }
-#pragma unroll
-            for (int u = 0; u < kRowUnroll; ++u) {
-                uint32_t h = hits[u];
-                while (__any_sync(0xffffffffu, h != 0u)) {
-                    uint32_t j = 0u;
-                    const bool keep = h != 0u;
-                    if (keep) {
-                        j = i + static_cast<uint32_t>(dl[u]) + (__ffs(h) - 1) - 2u;
-                        h &= h - 1u;
-                    }
-                    push_edge(keep, node, j, buf, cnt, lane, rank, P, nold, logb, &c.logn, stopp, hooks, unions);
-                }
-            }
-        }
-    }
-    if (lane < cnt) hooks += flush_one(buf[lane], rank, P, nold, logb, &c.logn, stopp, unions);
-    __syncwarp();
-    hooks = __reduce_add_sync(0xffffffffu, hooks);
-    sites = __reduce_add_sync(0xffffffffu, sites);
-    unions = __reduce_add_sync(0xffffffffu, unions);
-    if (lane == 0u) {
-        if (hooks) atomicAdd(&c.hooks, static_cast<unsigned long long>(hooks));
-        if (sites) atomicAdd(&c.sites, static_cast<unsigned long long>(sites));
-        if (unions) atomicAdd(&c.unions, static_cast<unsigned long long>(unions));
-    }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -410,145 +334,203 @@ __device__ uint32_t build_planes16(const RowEntry *rows, uint32_t R, PlaneEntry 
     return c.NP;
 }
 
-constexpr int kPlaneUnroll = 2;
+// Site geometry for the scan phase.
+struct SiteGeo {
+    uint32_t i;        // site index
+    uint32_t allowed;  // row path: 25-bit in-lattice mask of (d1..d5); plane path: (d1..d3) part
+    uint32_t a5;       // in-lattice d5 values
+    uint32_t sm0, sm1, sm2, sh, wbase;  // plane path only
+    bool low, high;    // on the x1 = 0 / x1 = L-1 border
+};
 
-template <bool kFaces>
-__device__ __forceinline__ void union_pass_planes16(Ctl &c, uint32_t *P, uint32_t *logb, const uint32_t *bm,
-                                                    const PlaneEntry *planes, uint2 *ebuf, const uint32_t *perm,
-                                                    const uint32_t *rank, uint32_t r0, uint32_t r1, uint32_t nold)
+template <bool kPlanes>
+__device__ __forceinline__ SiteGeo site_geo(uint32_t i, uint32_t L, const FastDiv &fd)
 {
-    const uint32_t NP = c.NP;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const uint32_t gshift = lanes_shift(r1 - r0, NP);
-    const uint32_t gl = lane & ((1u << gshift) - 1u), gw = lane >> gshift, spw = 32u >> gshift;
-    const uint32_t niter = (NP + (1u << gshift) - 1u) >> gshift;
-    uint2 *buf = ebuf + warp * kEdgeBuf;
+    SiteGeo s;
+    s.i = i;
+    if (kPlanes) {  // L = 16: coordinates are 4-bit fields of the index
+        const uint32_t x1 = i >> 16, x2 = (i >> 12) & 15u, x3 = (i >> 8) & 15u, x4 = (i >> 4) & 15u, x5 = i & 15u;
+        s.allowed = allowed_bits(x1, kPlaneL) | (allowed_bits(x2, kPlaneL) << 5) | (allowed_bits(x3, kPlaneL) << 10);
+        const uint32_t a4 = allowed_bits(x4, kPlaneL);
+        s.a5 = allowed_bits(x5, kPlaneL);
+        s.sm0 = ((a4 & 1u) ? s.a5 : 0u) | ((a4 & 2u) ? (s.a5 << 16) : 0u);
+        s.sm1 = ((a4 & 4u) ? s.a5 : 0u) | ((a4 & 8u) ? (s.a5 << 16) : 0u);
+        s.sm2 = (a4 & 16u) ? s.a5 : 0u;
+        s.sh = (i + 30u) & 31u;
+        s.wbase = (i + 30u) >> 5;
+        s.low = x1 == 0u;
+        s.high = x1 == kPlaneL - 1u;
+    } else {
+        uint32_t x[5];
+        site_coords(i, fd, x);
+        s.allowed = site_allowed(x, L);
+        s.a5 = s.allowed >> 20;
+        s.sm0 = s.sm1 = s.sm2 = s.sh = s.wbase = 0u;
+        s.low = x[0] == 0u;
+        s.high = x[0] == L - 1u;
+    }
+    return s;
+}
+
+// Hits of neighborhood entry k of a site: up to three 32-bit masks; bit t of mask f is the
+// neighbor site base + 32 f + t.
+template <bool kSmemBm, bool kPlanes>
+__device__ __forceinline__ uint32_t entry_hits(const SiteGeo &g, const uint32_t *bm, const RowEntry *rows,
+                                               const PlaneEntry *planes, uint32_t k, uint32_t h[3])
+{
+    h[0] = h[1] = h[2] = 0u;
+    if (kPlanes) {
+        const PlaneEntry e = planes[k];
+        if ((e.oh & 0x7FFFu & ~g.allowed) != 0u) return 0u;
+        const uint32_t *w = bm + (g.wbase + static_cast<uint32_t>(e.dword));
+        // the fourth word only matters when the 69-bit block starts past bit 27
+        const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = g.sh > 27u ? w[3] : 0u;
+        h[0] = __funnelshift_r(w0, w1, g.sh) & e.pm0 & g.sm0;
+        h[1] = __funnelshift_r(w1, w2, g.sh) & e.pm1 & g.sm1;
+        h[2] = __funnelshift_r(w2, w3, g.sh) & (e.oh >> 16) & g.sm2;
+        return g.i + static_cast<uint32_t>(e.dword) * 32u - 34u;
+    } else {
+        const RowEntry e = rows[k];
+        if ((e.onehot & ~g.allowed) != 0u) return 0u;
+        const uint32_t b = g.i + kBmGuard - 2u + static_cast<uint32_t>(e.delta);
+        const uint32_t w = __funnelshift_r(bm_word<kSmemBm>(bm, b >> 5), bm_word<kSmemBm>(bm, (b >> 5) + 1u), b & 31u);
+        h[0] = w & e.d5mask & g.a5;
+        return g.i + static_cast<uint32_t>(e.delta) - 2u;
+    }
+}
+
+template <bool kSmemBm, bool kFaces, bool kPlanes>
+__device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, const uint32_t *bm,
+                                           const RowEntry *rows, const PlaneEntry *planes, const EdgeList &E,
+                                           const uint32_t *perm, const uint32_t *rank, uint32_t L,
+                                           const FastDiv &fd, uint32_t r0, uint32_t r1, uint32_t nold)
+{
+    const uint32_t R = kPlanes ? c.NP : c.R;
+    const uint32_t gshift = lanes_shift(r1 - r0, R);
+    const uint32_t gsize = 1u << gshift, gl = threadIdx.x & (gsize - 1u), grp = threadIdx.x >> gshift;
+    const uint32_t chunk = blockDim.x >> gshift;
     uint32_t *stopp = kFaces ? &c.stop : nullptr;
-    uint32_t cnt = 0, hooks = 0, sites = 0, unions = 0;
-    for (uint32_t base = r0 + warp * spw; base < r1; base += nwarps * spw) {
-        if (kFaces && *reinterpret_cast<volatile uint32_t *>(&c.stop)) break;
-        const uint32_t r = base + gw;
-        const bool act = r < r1;
-        const uint32_t i = act ? __ldg(perm + r) : 0u;
-        const uint32_t x1 = i >> 16, x2 = (i >> 12) & 15u, x3 = (i >> 8) & 15u, x4 = (i >> 4) & 15u,
-                       x5 = i & 15u;
-        const uint32_t a123 = allowed_bits(x1, kPlaneL) | (allowed_bits(x2, kPlaneL) << 5) |
-                              (allowed_bits(x3, kPlaneL) << 10);
-        const uint32_t a4 = allowed_bits(x4, kPlaneL), a5 = allowed_bits(x5, kPlaneL);
-        const uint32_t sm0 = ((a4 & 1u) ? a5 : 0u) | ((a4 & 2u) ? (a5 << 16) : 0u);
-        const uint32_t sm1 = ((a4 & 4u) ? a5 : 0u) | ((a4 & 8u) ? (a5 << 16) : 0u);
-        const uint32_t sm2 = (a4 & 16u) ? a5 : 0u;
-        const uint32_t sh = (i + 30u) & 31u;
-        const uint32_t wbase = (i + 30u) >> 5;  // word of the block start at plane offset 0
-        const uint32_t node = r + 2u;
-        sites += (act && gl == 0u) ? 1u : 0u;
-        if (kFaces) {
-            push_edge(act && gl == 0u && x1 == 0u, node, kNodeFlag | 0u, buf, cnt, lane, rank, P, nold, logb,
-                      &c.logn, stopp, hooks, unions);
-            push_edge(act && gl == 0u && x1 == kPlaneL - 1u, node, kNodeFlag | 1u, buf, cnt, lane, rank, P, nold,
-                      logb, &c.logn, stopp, hooks, unions);
-        }
-        for (uint32_t t = 0; t < niter; t += kPlaneUnroll) {
-            uint32_t h[kPlaneUnroll][3];
-            int32_t dw[kPlaneUnroll];
-#pragma unroll
-            for (int u = 0; u < kPlaneUnroll; ++u) {
-                const uint32_t k = gl + ((t + u) << gshift);
-                const bool ok = act && k < NP;
-                const PlaneEntry e = planes[ok ? k : 0u];
-                h[u][0] = h[u][1] = h[u][2] = 0u;
-                dw[u] = e.dword;
-                if (ok && (e.oh & 0x7FFFu & ~a123) == 0u) {
-                    const uint32_t *w = bm + (wbase + static_cast<uint32_t>(e.dword));
-                    // the fourth word only matters when the 69-bit block starts past bit 27
-                    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = sh > 27u ? w[3] : 0u;
-                    h[u][0] = __funnelshift_r(w0, w1, sh) & e.pm0 & sm0;
-                    h[u][1] = __funnelshift_r(w1, w2, sh) & e.pm1 & sm1;
-                    h[u][2] = __funnelshift_r(w2, w3, sh) & (e.oh >> 16) & sm2;
+    uint32_t hooks = 0, sites = 0, unions = 0, parity = 0;
+    for (uint32_t base = r0; base < r1; base += chunk, parity ^= 1u) {
+        uint32_t *ecount = &c.ecount[parity];
+        // ---- scan
+        const uint32_t r = base + grp;
+        if (r < r1) {
+            const SiteGeo g = site_geo<kPlanes>(__ldg(perm + r), L, fd);
+            const uint32_t node = r + 2u;
+            if (gl == 0u) {
+                ++sites;
+                if (kFaces && (g.low || g.high)) {
+                    uint32_t k = atomicAdd(ecount, (g.low ? 1u : 0u) + (g.high ? 1u : 0u));
+                    if (g.low) edge_put(E, k++, make_uint2(node, kNodeFlag | 0u));
+                    if (g.high) edge_put(E, k, make_uint2(node, kNodeFlag | 1u));
                 }
             }
-#pragma unroll
-            for (int u = 0; u < kPlaneUnroll; ++u) {
+            for (uint32_t k = gl; k < R; k += gsize) {
+                uint32_t h[3];
+                const uint32_t jb = entry_hits<kSmemBm, kPlanes>(g, bm, rows, planes, k, h);
+                const uint32_t nh = __popc(h[0]) + __popc(h[1]) + __popc(h[2]);
+                if (nh == 0u) continue;
+                uint32_t slot = atomicAdd(ecount, nh);
 #pragma unroll
                 for (int f = 0; f < 3; ++f) {
-                    uint32_t hf = h[u][f];
-                    while (__any_sync(0xffffffffu, hf != 0u)) {
-                        uint32_t j = 0u;
-                        const bool keep = hf != 0u;
-                        if (keep) {
-                            j = i + static_cast<uint32_t>(dw[u] * 32) + static_cast<uint32_t>(32 * f) +
-                                static_cast<uint32_t>(__ffs(hf) - 1) - 34u;
-                            hf &= hf - 1u;
-                        }
-                        push_edge(keep, node, j, buf, cnt, lane, rank, P, nold, logb, &c.logn, stopp, hooks, unions);
+                    uint32_t hf = h[f];
+                    while (hf) {
+                        const uint32_t t = __ffs(hf) - 1;
+                        hf &= hf - 1u;
+                        edge_put(E, slot++, make_uint2(node, jb + 32u * f + t));
                     }
                 }
             }
         }
+        __syncthreads();
+        // ---- unite
+        const uint32_t ne = *ecount;
+        if (threadIdx.x == 0) c.ecount[parity ^ 1u] = 0u;  // the next chunk's counter
+        for (uint32_t e = threadIdx.x, it = 0; e < ne; e += blockDim.x, ++it) {
+            if (kFaces && (it & 7u) == 7u && *reinterpret_cast<volatile uint32_t *>(&c.stop)) break;
+            hooks += unite_edge(edge_get(E, e), rank, P, nold, logb, &c.logn, stopp, unions);
+        }
+        __syncthreads();
+        if (kFaces && *reinterpret_cast<volatile uint32_t *>(&c.stop)) break;  // span(n) is decided
     }
-    if (lane < cnt) hooks += flush_one(buf[lane], rank, P, nold, logb, &c.logn, stopp, unions);
-    __syncwarp();
     hooks = __reduce_add_sync(0xffffffffu, hooks);
     sites = __reduce_add_sync(0xffffffffu, sites);
     unions = __reduce_add_sync(0xffffffffu, unions);
-    if (lane == 0u) {
+    if ((threadIdx.x & 31u) == 0u) {
         if (hooks) atomicAdd(&c.hooks, static_cast<unsigned long long>(hooks));
         if (sites) atomicAdd(&c.sites, static_cast<unsigned long long>(sites));
         if (unions) atomicAdd(&c.unions, static_cast<unsigned long long>(unions));
     }
 }
 
+// Per-CTA global slot: union-find nodes, undo log, the bitmap when it does not fit in shared
+// memory, and the overflow of the edge list (a chunk of blockDim sites with at most 892
+// neighbors and 2 borders each).
+__host__ __device__ inline size_t slot_edge_entries(uint32_t threads) { return size_t(threads) * (kMaxOffsets + 2); }
+
 struct SlotPtrs {
     uint32_t *P, *logb, *gbm;
+    uint2 *gedges;
 };
+
+__host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+__host__ __device__ inline size_t slot_bytes_for(uint64_t Ncap, bool gbm, uint32_t threads)
+{
+    return 2 * align256((Ncap + 2) * 4) + (gbm ? align256(size_t(bm_words(Ncap)) * 4) : 0) +
+           align256(slot_edge_entries(threads) * sizeof(uint2));
+}
 
 __device__ __forceinline__ SlotPtrs slot_ptrs(char *ws, size_t slot_bytes, uint64_t Ncap, bool gbm)
 {
     char *base = ws + sizeof(WsHeader) + size_t(blockIdx.x) * slot_bytes;
-    const size_t nodes = ((Ncap + 2) * 4 + 255) & ~size_t(255);
+    const size_t nodes = align256((Ncap + 2) * 4);
+    const size_t bmb = gbm ? align256(size_t(bm_words(Ncap)) * 4) : 0;
     SlotPtrs s;
     s.P = reinterpret_cast<uint32_t *>(base);
     s.logb = reinterpret_cast<uint32_t *>(base + nodes);
     s.gbm = gbm ? reinterpret_cast<uint32_t *>(base + 2 * nodes) : nullptr;
+    s.gedges = reinterpret_cast<uint2 *>(base + 2 * nodes + bmb);
     return s;
 }
 
-// Shared-memory carve-up: [row table][edge buffers (also the row-build scratch)][bitmap].
+// Shared-memory carve-up: [row table][plane table][bitmap of side smem_L][edge list (the rest)];
+// the table-building scratch uses the start of the edge list.
 struct SmemPtrs {
     RowEntry *rows;
     PlaneEntry *planes;
-    uint2 *ebuf;
-    uint32_t *scratch;
     uint32_t *sbm;
+    uint2 *edges;
+    uint32_t *scratch;
 };
 
-__host__ __device__ inline size_t smem_fixed_bytes(uint32_t threads)
+__host__ __device__ inline size_t smem_tables_bytes() { return sizeof(RowEntry) * kRowCand + sizeof(PlaneEntry) * kPlaneCand; }
+
+__host__ __device__ inline size_t smem_bitmap_bytes(uint32_t smem_L)
 {
-    const size_t rows = sizeof(RowEntry) * kRowCand + sizeof(PlaneEntry) * kPlaneCand;
-    size_t eb = size_t(threads / 32) * kEdgeBuf * sizeof(uint2);
-    if (eb < kRowCand * sizeof(uint32_t)) eb = kRowCand * sizeof(uint32_t);
-    return rows + ((eb + 15) & ~size_t(15));
+    return (size_t(bm_words(num_sites(smem_L))) * 4 + 15) & ~size_t(15);
 }
 
-__device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn)
+__device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn, uint32_t smem_L)
 {
     SmemPtrs p;
     p.rows = reinterpret_cast<RowEntry *>(dyn);
     p.planes = reinterpret_cast<PlaneEntry *>(dyn + sizeof(RowEntry) * kRowCand);
-    p.ebuf = reinterpret_cast<uint2 *>(dyn + sizeof(RowEntry) * kRowCand + sizeof(PlaneEntry) * kPlaneCand);
-    p.scratch = reinterpret_cast<uint32_t *>(p.ebuf);
-    p.sbm = reinterpret_cast<uint32_t *>(dyn + smem_fixed_bytes(blockDim.x));
+    p.sbm = reinterpret_cast<uint32_t *>(dyn + smem_tables_bytes());
+    p.edges = reinterpret_cast<uint2 *>(dyn + smem_tables_bytes() + smem_bitmap_bytes(smem_L));
+    p.scratch = reinterpret_cast<uint32_t *>(p.edges);
     return p;
 }
 
-// One connected-component pass of the bisection at n = c.mid (all threads).  Returns span(mid).
 struct PhaseClock {
     unsigned long long update = 0, unite = 0, commit = 0, setup = 0;
 };
 
 template <bool kSmemBm>
 __device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, uint32_t *bm,
-                                          const SmemPtrs &sm, const uint32_t *perm, const uint32_t *rank,
+                                          const SmemPtrs &sm, const EdgeList &E, const uint32_t *perm,
+                                          const uint32_t *rank,
                                           uint32_t L, const FastDiv &fd, PhaseClock &clk)
 {
     const uint32_t mid = c.mid, nb = c.nb, bm_n = c.bm_n;
@@ -559,9 +541,9 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, u
     __syncthreads();
     const long long t1 = clock64();
     if (kSmemBm && L == kPlaneL)
-        union_pass_planes16<true>(c, P, logb, bm, sm.planes, sm.ebuf, perm, rank, nb, mid, nb + 2u);
+        union_pass<true, true, true>(c, P, logb, sm.sbm, sm.rows, sm.planes, E, perm, rank, L, fd, nb, mid, nb + 2u);
     else
-        union_pass<kSmemBm, true>(c, P, logb, bm, sm.rows, sm.ebuf, perm, rank, L, fd, nb, mid, nb + 2u);
+        union_pass<kSmemBm, true, false>(c, P, logb, bm, sm.rows, sm.planes, E, perm, rank, L, fd, nb, mid, nb + 2u);
     __syncthreads();
     const long long t2 = clock64();
     clk.update += t1 - t0;
@@ -579,16 +561,17 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, u
 }
 
 __global__ void __launch_bounds__(1024, 1)
-k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L,
+k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t edge_scap,
         const uint32_t *__restrict__ bracket, uint32_t *__restrict__ nstar_out,
         uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
-    const SmemPtrs sm = smem_ptrs(dyn);
+    const SmemPtrs sm = smem_ptrs(dyn, smem_L);
     __shared__ Ctl c;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
     const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
+    const EdgeList E{sm.edges, edge_scap, sp.gedges};
     uint32_t *P = sp.P, *logb = sp.logb;
     unsigned long long tot_passes = 0, tot_probe = 0, tot_early = 0, tot_fb = 0, tot_ok = 0;
     PhaseClock clk;
@@ -668,11 +651,12 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
                 c.bm_n = bm_n;
                 c.stop = 0;
                 c.logn = 0;
+                c.ecount[0] = 0;
                 c.new_sites += mid - nb;
             }
             __syncthreads();
-            const uint32_t span = smem_bm ? probe<true>(c, P, logb, bm, sm, smp.perm, smp.rank, L, fd, clk)
-                                          : probe<false>(c, P, logb, bm, sm, smp.perm, smp.rank, L, fd, clk);
+            const uint32_t span = smem_bm ? probe<true>(c, P, logb, bm, sm, E, smp.perm, smp.rank, L, fd, clk)
+                                          : probe<false>(c, P, logb, bm, sm, E, smp.perm, smp.rank, L, fd, clk);
             ++npass;
             tot_probe += mid;
             if (span && c.stop) ++tot_early;
@@ -726,16 +710,17 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
 
 // S_max(n) per sample: one full pass over the first n sites, then cluster sizes by root counting.
 __global__ void __launch_bounds__(1024, 1)
-k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L,
+k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t edge_scap,
        const uint64_t *__restrict__ n_in, int64_t *__restrict__ mass_out, char *ws, size_t slot_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
-    const SmemPtrs sm = smem_ptrs(dyn);
+    const SmemPtrs sm = smem_ptrs(dyn, smem_L);
     __shared__ Ctl c;
     __shared__ uint32_t red[32];
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
     const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
+    const EdgeList E{sm.edges, edge_scap, sp.gedges};
     uint32_t *P = sp.P, *cnt = sp.logb;
 
     for (;;) {
@@ -766,6 +751,7 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         if (threadIdx.x == 0) {
             c.logn = 0;
             c.stop = 0;
+            c.ecount[0] = 0;
         }
         const FastDiv fd = make_fastdiv(L);
         __syncthreads();
@@ -776,11 +762,11 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         }
         __syncthreads();
         if (smem_bm && L == kPlaneL)
-            union_pass_planes16<false>(c, P, nullptr, sm.sbm, sm.planes, sm.ebuf, smp.perm, smp.rank, 0u, n, 0u);
+            union_pass<true, false, true>(c, P, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         else if (smem_bm)
-            union_pass<true, false>(c, P, nullptr, sm.sbm, sm.rows, sm.ebuf, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+            union_pass<true, false, false>(c, P, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         else
-            union_pass<false, false>(c, P, nullptr, bm, sm.rows, sm.ebuf, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+            union_pass<false, false, false>(c, P, nullptr, bm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         __syncthreads();
         for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) atomicAdd(cnt + uf_find(P, r + 2u, 0u), 1u);
         __syncthreads();
@@ -806,6 +792,7 @@ struct LaunchCfg {
     int threads = 0;
     size_t smem = 0;
     uint32_t smem_L = 0;
+    uint32_t edge_scap = 0;
     uint32_t grid = 0;
     size_t slot_bytes = 0;
 };
@@ -821,14 +808,24 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
     if (max_L < 1 || max_L > PERC_MAX_L || num == 0) return PERC_EINVAL;
     const uint64_t Ncap = num_sites(max_L);
     cfg.smem_L = max_L < kSmemBitmapMaxL ? max_L : kSmemBitmapMaxL;
-    const uint64_t smem_sites = num_sites(cfg.smem_L);
     int dflt_threads = max_L <= 8 ? 256 : (max_L <= 12 ? 512 : 1024);
     cfg.threads = env_int("PERC_THREADS", dflt_threads);
     if (cfg.threads < 32 || cfg.threads > 1024 || (cfg.threads & 31)) return PERC_EINVAL;
-    cfg.smem = smem_fixed_bytes(cfg.threads) + size_t(bm_words(smem_sites)) * 4;
-    int dev = 0, sms = 0, occ = 0;
+    int dev = 0, sms = 0, occ = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PERC_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PERC_ECUDA;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return PERC_ECUDA;
+    // Shared memory per CTA: the register file holds 65536 / (threads * 64) CTAs per SM (64
+    // registers a thread); each CTA takes an equal share, and whatever the tables and the bitmap
+    // leave holds the shared part of the edge list.
+    const int ctas = (65536 / (cfg.threads * 64)) > 0 ? 65536 / (cfg.threads * 64) : 1;
+    const size_t share = size_t(optin) / ctas - 1024;  // room for the static shared variables
+    const size_t base = smem_tables_bytes() + smem_bitmap_bytes(cfg.smem_L);
+    const size_t min_edges = size_t(kRowCand) * sizeof(uint32_t);  // table-building scratch
+    if (base + min_edges > share) return PERC_EINVAL;
+    cfg.edge_scap = static_cast<uint32_t>((share - base) / sizeof(uint2));
+    cfg.smem = base + size_t(cfg.edge_scap) * sizeof(uint2);
     const void *fn = op == PERC_OP_MASS ? reinterpret_cast<const void *>(k_mass)
                                         : reinterpret_cast<const void *>(k_nstar);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cfg.smem)) != cudaSuccess)
@@ -836,12 +833,10 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, cfg.threads, cfg.smem) != cudaSuccess)
         return PERC_ECUDA;
     if (occ < 1) return PERC_EINVAL;
-    const size_t nodes = ((Ncap + 2) * 4 + 255) & ~size_t(255);
-    const size_t gbm = max_L > cfg.smem_L ? (size_t(bm_words(Ncap)) * 4 + 255) & ~size_t(255) : 0;
-    cfg.slot_bytes = 2 * nodes + gbm;
+    cfg.slot_bytes = slot_bytes_for(Ncap, max_L > cfg.smem_L, cfg.threads);
     uint64_t grid = uint64_t(sms) * occ;
-    const int cap = env_int("PERC_MAX_CTAS", 0);
-    if (cap > 0 && uint64_t(cap) < grid) grid = cap;
+    const int cta_cap = env_int("PERC_MAX_CTAS", 0);
+    if (cta_cap > 0 && uint64_t(cta_cap) < grid) grid = cta_cap;
     if (grid > num) grid = num;
     const uint64_t mem_cap = kSlotCapBytes / cfg.slot_bytes;
     if (grid > mem_cap) grid = mem_cap > 0 ? mem_cap : 1;
@@ -876,7 +871,7 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
     if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
-    k_nstar<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, bracket,
+    k_nstar<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.edge_scap, bracket,
                                                          nstar, passes, stats, static_cast<char *>(workspace),
                                                          cfg.slot_bytes);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
@@ -892,7 +887,7 @@ extern "C" int perc_mass(const perc_sample *samples, uint32_t num_samples, uint3
     if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
-    k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, n, mass,
+    k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.edge_scap, n, mass,
                                                         static_cast<char *>(workspace), cfg.slot_bytes);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }
