@@ -78,7 +78,9 @@ typedef struct {
     unsigned long long cyc_update;   /* SM cycles updating the bitmap and initialising new nodes */
     unsigned long long cyc_union;    /* SM cycles in the union passes */
     unsigned long long cyc_commit;   /* SM cycles reading span and undoing / committing hooks */
-    unsigned long long reserved[3];
+    unsigned long long cyc_scan;     /* part of cyc_union: scanning neighborhoods into edge lists */
+    unsigned long long cyc_link;     /* part of cyc_union: rank lookups and unions of the edges */
+    unsigned long long reserved;
 } perc_stats;
 
 /*

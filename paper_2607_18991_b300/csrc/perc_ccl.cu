@@ -36,6 +36,7 @@ namespace perc {
 
 constexpr uint32_t kTag = 0x80000000u;
 constexpr uint32_t kSmemBitmapMaxL = 17;
+constexpr size_t kSmemNodes = 16384;  // most union-find nodes a CTA keeps in shared memory
 constexpr size_t kSlotCapBytes = size_t(32) << 30;  // total per-CTA slot memory aimed at
 
 __constant__ ZoneTable c_zones = kZones;
@@ -60,33 +61,78 @@ struct Ctl {
     uint32_t R;       // row entries of the sample's neighborhood
     uint32_t NP;      // plane entries (L = 16 path)
     uint32_t ecount[2];  // edge-list fill of the current and the next chunk
-    unsigned long long hooks, new_sites, sites, unions;
+    unsigned long long hooks, new_sites, sites, unions, cyc_scan, cyc_link;
 };
 
 // ------------------------------------------------------------------------------------------------
-// union-find on rank-space nodes (global memory, L2-coherent loads)
+// union-find on rank-space nodes.  The first `cap` nodes of a sample live in shared memory (the
+// nodes of the earliest sites, which every later site reaches), the rest in the CTA's global slot
+// (L2-coherent loads and stores).  Shared-memory accesses use explicit .shared instructions.
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t ld_cg(const uint32_t *p) { return __ldcg(p); }
 
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v)
+{
+    asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t atoms_cas(uint32_t a, uint32_t cmp, uint32_t val)
+{
+    uint32_t old;
+    asm volatile("atom.shared.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "r"(a), "r"(cmp), "r"(val) : "memory");
+    return old;
+}
+
+struct Nodes {
+    uint32_t *g;     // global nodes (node x at g[x], used for x >= cap)
+    uint32_t sbase;  // shared-window address of node 0
+    uint32_t cap;    // nodes held in shared memory
+};
+
+__device__ __forceinline__ uint32_t nd_ld(const Nodes &P, uint32_t x)
+{
+    return x < P.cap ? lds_u32(P.sbase + 4u * x) : __ldcg(P.g + x);
+}
+
+__device__ __forceinline__ void nd_st(const Nodes &P, uint32_t x, uint32_t v)
+{
+    if (x < P.cap)
+        sts_u32(P.sbase + 4u * x, v);
+    else
+        __stcg(P.g + x, v);
+}
+
+__device__ __forceinline__ uint32_t nd_cas(const Nodes &P, uint32_t x, uint32_t cmp, uint32_t val)
+{
+    return x < P.cap ? atoms_cas(P.sbase + 4u * x, cmp, val) : atomicCAS(P.g + x, cmp, val);
+}
+
 // Root of x with path halving.  Nodes below nold existed at the committed state: their pointer is
 // rewritten only when both skipped edges are untagged (committed edges).
-__device__ __forceinline__ uint32_t uf_find(uint32_t *P, uint32_t x, uint32_t nold)
+__device__ __forceinline__ uint32_t uf_find(const Nodes &P, uint32_t x, uint32_t nold)
 {
     for (;;) {
-        const uint32_t p = ld_cg(P + x);
+        const uint32_t p = nd_ld(P, x);
         const uint32_t pu = p & ~kTag;
         if (pu == x) return x;
-        const uint32_t g = ld_cg(P + pu);
+        const uint32_t g = nd_ld(P, pu);
         const uint32_t gu = g & ~kTag;
         if (gu == pu) return pu;
-        if (x >= nold || ((p | g) & kTag) == 0u) __stcg(P + x, gu);
+        if (x >= nold || ((p | g) & kTag) == 0u) nd_st(P, x, gu);
         x = gu;
     }
 }
 
 // Merge the clusters of a and b; returns true if a hook was made.  Hooking node 1 (the x1 = L-1
 // border, which only node 0 can take) decides the pass: it raises *stop.
-__device__ __forceinline__ bool uf_unite(uint32_t *P, uint32_t a, uint32_t b, uint32_t nold,
+__device__ __forceinline__ bool uf_unite(const Nodes &P, uint32_t a, uint32_t b, uint32_t nold,
                                          uint32_t *logb, uint32_t *logn, uint32_t *stop)
 {
     a = uf_find(P, a, nold);
@@ -95,7 +141,7 @@ __device__ __forceinline__ bool uf_unite(uint32_t *P, uint32_t a, uint32_t b, ui
         const uint32_t hi = a > b ? a : b;
         const uint32_t lo = a > b ? b : a;
         const bool old = hi < nold;
-        const uint32_t seen = atomicCAS(P + hi, hi, old ? (lo | kTag) : lo);
+        const uint32_t seen = nd_cas(P, hi, hi, old ? (lo | kTag) : lo);
         if (seen == hi) {
             if (old) logb[atomicAdd(logn, 1u)] = hi;
             if (hi == 1u && stop) *reinterpret_cast<volatile uint32_t *>(stop) = 1u;
@@ -248,7 +294,7 @@ __device__ __forceinline__ uint2 edge_get(const EdgeList &E, uint32_t k)
     return k < E.scap ? E.s[k] : E.g[k - E.scap];
 }
 
-__device__ __forceinline__ uint32_t unite_edge(uint2 e, const uint32_t *rank, uint32_t *P, uint32_t nold,
+__device__ __forceinline__ uint32_t unite_edge(uint2 e, const uint32_t *rank, const Nodes &P, uint32_t nold,
                                                uint32_t *logb, uint32_t *logn, uint32_t *stop, uint32_t &unions)
 {
     uint32_t other;
@@ -400,7 +446,7 @@ __device__ __forceinline__ uint32_t entry_hits(const SiteGeo &g, const uint32_t 
 }
 
 template <bool kSmemBm, bool kFaces, bool kPlanes>
-__device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, const uint32_t *bm,
+__device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *logb, const uint32_t *bm,
                                            const RowEntry *rows, const PlaneEntry *planes, const EdgeList &E,
                                            const uint32_t *perm, const uint32_t *rank, uint32_t L,
                                            const FastDiv &fd, uint32_t r0, uint32_t r1, uint32_t nold)
@@ -413,6 +459,7 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, 
     uint32_t hooks = 0, sites = 0, unions = 0, parity = 0;
     for (uint32_t base = r0; base < r1; base += chunk, parity ^= 1u) {
         uint32_t *ecount = &c.ecount[parity];
+        const long long t_chunk = clock64();
         // ---- scan
         const uint32_t r = base + grp;
         if (r < r1) {
@@ -444,6 +491,7 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, 
             }
         }
         __syncthreads();
+        const long long t_scan = clock64();
         // ---- unite
         const uint32_t ne = *ecount;
         if (threadIdx.x == 0) c.ecount[parity ^ 1u] = 0u;  // the next chunk's counter
@@ -452,6 +500,11 @@ __device__ __forceinline__ void union_pass(Ctl &c, uint32_t *P, uint32_t *logb, 
             hooks += unite_edge(edge_get(E, e), rank, P, nold, logb, &c.logn, stopp, unions);
         }
         __syncthreads();
+        if (threadIdx.x == 0) {
+            const long long t_link = clock64();
+            c.cyc_scan += static_cast<unsigned long long>(t_scan - t_chunk);
+            c.cyc_link += static_cast<unsigned long long>(t_link - t_scan);
+        }
         if (kFaces && *reinterpret_cast<volatile uint32_t *>(&c.stop)) break;  // span(n) is decided
     }
     hooks = __reduce_add_sync(0xffffffffu, hooks);
@@ -495,12 +548,13 @@ __device__ __forceinline__ SlotPtrs slot_ptrs(char *ws, size_t slot_bytes, uint6
     return s;
 }
 
-// Shared-memory carve-up: [row table][plane table][bitmap of side smem_L][edge list (the rest)];
-// the table-building scratch uses the start of the edge list.
+// Shared-memory carve-up: [row table][plane table][bitmap of side smem_L][node_cap union-find
+// nodes][edge list (the rest)]; the table-building scratch uses the start of the edge list.
 struct SmemPtrs {
     RowEntry *rows;
     PlaneEntry *planes;
     uint32_t *sbm;
+    uint32_t *nodes;
     uint2 *edges;
     uint32_t *scratch;
 };
@@ -512,13 +566,16 @@ __host__ __device__ inline size_t smem_bitmap_bytes(uint32_t smem_L)
     return (size_t(bm_words(num_sites(smem_L))) * 4 + 15) & ~size_t(15);
 }
 
-__device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn, uint32_t smem_L)
+__host__ __device__ inline size_t smem_nodes_bytes(uint32_t node_cap) { return (size_t(node_cap) * 4 + 15) & ~size_t(15); }
+
+__device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn, uint32_t smem_L, uint32_t node_cap)
 {
     SmemPtrs p;
     p.rows = reinterpret_cast<RowEntry *>(dyn);
     p.planes = reinterpret_cast<PlaneEntry *>(dyn + sizeof(RowEntry) * kRowCand);
     p.sbm = reinterpret_cast<uint32_t *>(dyn + smem_tables_bytes());
-    p.edges = reinterpret_cast<uint2 *>(dyn + smem_tables_bytes() + smem_bitmap_bytes(smem_L));
+    p.nodes = reinterpret_cast<uint32_t *>(dyn + smem_tables_bytes() + smem_bitmap_bytes(smem_L));
+    p.edges = reinterpret_cast<uint2 *>(dyn + smem_tables_bytes() + smem_bitmap_bytes(smem_L) + smem_nodes_bytes(node_cap));
     p.scratch = reinterpret_cast<uint32_t *>(p.edges);
     return p;
 }
@@ -528,7 +585,7 @@ struct PhaseClock {
 };
 
 template <bool kSmemBm>
-__device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, uint32_t *bm,
+__device__ __forceinline__ uint32_t probe(Ctl &c, const Nodes &P, uint32_t *logb, uint32_t *bm,
                                           const SmemPtrs &sm, const EdgeList &E, const uint32_t *perm,
                                           const uint32_t *rank,
                                           uint32_t L, const FastDiv &fd, PhaseClock &clk)
@@ -537,7 +594,7 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, u
     if (kSmemBm) bm = sm.sbm;  // keep the shared-memory address space visible to the compiler
     const long long t0 = clock64();
     bitmap_update(bm, perm, bm_n, mid);
-    for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x) __stcg(P + r + 2u, r + 2u);
+    for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x) nd_st(P, r + 2u, r + 2u);
     __syncthreads();
     const long long t1 = clock64();
     if (kSmemBm && L == kPlaneL)
@@ -548,12 +605,12 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, u
     const long long t2 = clock64();
     clk.update += t1 - t0;
     clk.unite += t2 - t1;
-    const uint32_t span = ld_cg(P + 1) != 1u;
+    const uint32_t span = nd_ld(P, 1u) != 1u;
     const uint32_t logn = c.logn;
     __syncthreads();  // every thread has read span before node 1 may be reset below
     for (uint32_t k = threadIdx.x; k < logn; k += blockDim.x) {
         const uint32_t b = logb[k];
-        __stcg(P + b, span ? b : (ld_cg(P + b) & ~kTag));  // undo, or commit the hook
+        nd_st(P, b, span ? b : (nd_ld(P, b) & ~kTag));  // undo, or commit the hook
     }
     __syncthreads();
     clk.commit += clock64() - t2;
@@ -561,18 +618,20 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, uint32_t *P, uint32_t *logb, u
 }
 
 __global__ void __launch_bounds__(1024, 1)
-k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t edge_scap,
+k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t node_cap,
+        uint32_t edge_scap,
         const uint32_t *__restrict__ bracket, uint32_t *__restrict__ nstar_out,
         uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
-    const SmemPtrs sm = smem_ptrs(dyn, smem_L);
+    const SmemPtrs sm = smem_ptrs(dyn, smem_L, node_cap);
     __shared__ Ctl c;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
     const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
     const EdgeList E{sm.edges, edge_scap, sp.gedges};
-    uint32_t *P = sp.P, *logb = sp.logb;
+    const Nodes P{sp.P, static_cast<uint32_t>(__cvta_generic_to_shared(sm.nodes)), node_cap};
+    uint32_t *logb = sp.logb;
     unsigned long long tot_passes = 0, tot_probe = 0, tot_early = 0, tot_fb = 0, tot_ok = 0;
     PhaseClock clk;
 
@@ -583,6 +642,8 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
             c.new_sites = 0;
             c.sites = 0;
             c.unions = 0;
+            c.cyc_scan = 0;
+            c.cyc_link = 0;
         }
         __syncthreads();
         const long long t_setup = clock64();
@@ -607,8 +668,8 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
         build_rows(mask, L, sm.rows, sm.scratch, c);
         if (smem_bm && L == kPlaneL) build_planes16(sm.rows, c.R, sm.planes, sm.scratch, c);
         if (threadIdx.x == 0) {
-            __stcg(P + 0, 0u);
-            __stcg(P + 1, 1u);
+            nd_st(P, 0u, 0u);
+            nd_st(P, 1u, 1u);
         }
         const FastDiv fd = make_fastdiv(L);
         __syncthreads();
@@ -691,6 +752,8 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
                 atomicAdd(&stats->new_sites, c.new_sites);
                 atomicAdd(&stats->sites_merged, c.sites);
                 atomicAdd(&stats->unions, c.unions);
+                atomicAdd(&stats->cyc_scan, c.cyc_scan);
+                atomicAdd(&stats->cyc_link, c.cyc_link);
             }
         }
         __syncthreads();
@@ -710,18 +773,20 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
 
 // S_max(n) per sample: one full pass over the first n sites, then cluster sizes by root counting.
 __global__ void __launch_bounds__(1024, 1)
-k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t edge_scap,
+k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t node_cap,
+        uint32_t edge_scap,
        const uint64_t *__restrict__ n_in, int64_t *__restrict__ mass_out, char *ws, size_t slot_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
-    const SmemPtrs sm = smem_ptrs(dyn, smem_L);
+    const SmemPtrs sm = smem_ptrs(dyn, smem_L, node_cap);
     __shared__ Ctl c;
     __shared__ uint32_t red[32];
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
     const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
     const EdgeList E{sm.edges, edge_scap, sp.gedges};
-    uint32_t *P = sp.P, *cnt = sp.logb;
+    const Nodes P{sp.P, static_cast<uint32_t>(__cvta_generic_to_shared(sm.nodes)), node_cap};
+    uint32_t *cnt = sp.logb;
 
     for (;;) {
         if (threadIdx.x == 0) c.sample = atomicAdd(&hdr->queue, 1u);
@@ -757,7 +822,7 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         __syncthreads();
         bitmap_update(bm, smp.perm, 0u, n);
         for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) {
-            __stcg(P + r + 2u, r + 2u);
+            nd_st(P, r + 2u, r + 2u);
             __stcg(cnt + r + 2u, 0u);
         }
         __syncthreads();
@@ -792,6 +857,7 @@ struct LaunchCfg {
     int threads = 0;
     size_t smem = 0;
     uint32_t smem_L = 0;
+    uint32_t node_cap = 0;
     uint32_t edge_scap = 0;
     uint32_t grid = 0;
     size_t slot_bytes = 0;
@@ -817,15 +883,24 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return PERC_ECUDA;
     // Shared memory per CTA: the register file holds 65536 / (threads * 64) CTAs per SM (64
-    // registers a thread); each CTA takes an equal share, and whatever the tables and the bitmap
-    // leave holds the shared part of the edge list.
+    // registers a thread); each CTA takes an equal share.  What the tables and the bitmap leave
+    // goes to union-find nodes (up to kSmemNodes, keeping room for 512 edges) and then to the
+    // shared part of the edge list.
     const int ctas = (65536 / (cfg.threads * 64)) > 0 ? 65536 / (cfg.threads * 64) : 1;
     const size_t share = size_t(optin) / ctas - 1024;  // room for the static shared variables
     const size_t base = smem_tables_bytes() + smem_bitmap_bytes(cfg.smem_L);
     const size_t min_edges = size_t(kRowCand) * sizeof(uint32_t);  // table-building scratch
     if (base + min_edges > share) return PERC_EINVAL;
-    cfg.edge_scap = static_cast<uint32_t>((share - base) / sizeof(uint2));
-    cfg.smem = base + size_t(cfg.edge_scap) * sizeof(uint2);
+    size_t room = share - base;
+    size_t nodes = room > 512 * sizeof(uint2) ? (room - 512 * sizeof(uint2)) / 4 : 0;
+    if (nodes > kSmemNodes) nodes = kSmemNodes;
+    const int nodes_env = env_int("PERC_SMEM_NODES", -1);
+    if (nodes_env >= 0 && size_t(nodes_env) < nodes) nodes = nodes_env;
+    nodes &= ~size_t(3);
+    cfg.node_cap = static_cast<uint32_t>(nodes);
+    room -= smem_nodes_bytes(cfg.node_cap);
+    cfg.edge_scap = static_cast<uint32_t>(room / sizeof(uint2));
+    cfg.smem = base + smem_nodes_bytes(cfg.node_cap) + size_t(cfg.edge_scap) * sizeof(uint2);
     const void *fn = op == PERC_OP_MASS ? reinterpret_cast<const void *>(k_mass)
                                         : reinterpret_cast<const void *>(k_nstar);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cfg.smem)) != cudaSuccess)
@@ -871,7 +946,7 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
     if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
-    k_nstar<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.edge_scap, bracket,
+    k_nstar<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap, cfg.edge_scap, bracket,
                                                          nstar, passes, stats, static_cast<char *>(workspace),
                                                          cfg.slot_bytes);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
@@ -887,7 +962,7 @@ extern "C" int perc_mass(const perc_sample *samples, uint32_t num_samples, uint3
     if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
-    k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.edge_scap, n, mass,
+    k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap, cfg.edge_scap, n, mass,
                                                         static_cast<char *>(workspace), cfg.slot_bytes);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }

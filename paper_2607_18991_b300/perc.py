@@ -21,7 +21,7 @@ OP_RANK, OP_NSTAR, OP_MASS = 1, 2, 3
 MLP_NPARAM = 4931
 STATS_FIELDS = ("passes", "new_sites", "probe_sites", "hooks", "early_exits", "fallbacks",
                 "verified", "sites_merged", "unions", "cyc_setup", "cyc_update", "cyc_union",
-                "cyc_commit", "reserved0", "reserved1", "reserved2")
+                "cyc_commit", "cyc_scan", "cyc_link", "reserved")
 
 _lib = None
 
