@@ -8,16 +8,18 @@
 //   k_rank_hist    per-tile digit counts (pass 0 draws the keys itself, nothing is stored first),
 //   k_rank_scan    exclusive scan per seed in digit-major order -> tile output offsets,
 //   k_rank_scatter stable scatter: warp-level peer ranking with __match_any_sync,
-// then k_rank_invert writes rank[perm[r]] = r.  Seeds are sorted in chunks that fit the workspace.
+// and the last scatter also writes rank[perm[r]] = r.  Seeds are sorted in chunks that fit the
+// workspace.
 #include <cstdio>
 
 #include "perc_common.cuh"
 
 namespace perc {
 
-constexpr int kRankThreads = 256;
+constexpr int kRankThreads = 1024;
+constexpr int kRankWarps = kRankThreads / 32;
 constexpr int kRankItems = 8;
-constexpr int kRankTile = kRankThreads * kRankItems;  // 2048 keys per tile
+constexpr int kRankTile = kRankThreads * kRankItems;  // 8192 keys per tile
 constexpr int kRankMaxChunk = 64;                     // seeds per chunk (upper bound)
 constexpr size_t kRankChunkBytes = size_t(4) << 30;   // workspace aimed at per chunk
 
@@ -46,13 +48,20 @@ size_t rank_workspace_bytes(uint32_t L, uint32_t num_seeds)
     return 256 + size_t(rank_chunk(N, num_seeds)) * rank_bytes_per_seed(N);
 }
 
+// Element e of a tile is read by warp (e / 256), round ((e / 32) % 8), lane (e % 32): warp-major,
+// then round, then lane, i.e. in input order.
+__device__ __forceinline__ uint32_t tile_elem(uint32_t tile, int warp, int k, int lane)
+{
+    return tile * kRankTile + warp * (32 * kRankItems) + k * 32 + lane;
+}
+
 __global__ void __launch_bounds__(kRankThreads)
 k_rank_hist(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ seeds,
             const uint32_t *__restrict__ keys_in, uint32_t *__restrict__ hist)
 {
     __shared__ uint32_t h[256];
     const uint32_t s = blockIdx.y, tile = blockIdx.x;
-    h[threadIdx.x] = 0;
+    if (threadIdx.x < 256) h[threadIdx.x] = 0;
     __syncthreads();
     const uint64_t seed = pass == 0 ? seeds[s] : 0ull;
     const uint32_t *kin = keys_in + size_t(s) * N;
@@ -66,7 +75,7 @@ k_rank_hist(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ seeds
         }
     }
     __syncthreads();
-    hist[(size_t(s) * 256 + threadIdx.x) * T + tile] = h[threadIdx.x];
+    if (threadIdx.x < 256) hist[(size_t(s) * 256 + threadIdx.x) * T + tile] = h[threadIdx.x];
 }
 
 // Exclusive scan of one seed's 256*T counters (digit-major), one block per seed.
@@ -80,7 +89,6 @@ __global__ void __launch_bounds__(1024) k_rank_scan(uint32_t T, uint32_t *__rest
     const uint32_t e = min(n, b + per);
     uint32_t local = 0;
     for (uint32_t i = b; i < e; ++i) local += h[i];
-    // block-wide exclusive scan of `local`
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = local;
 #pragma unroll
@@ -109,18 +117,31 @@ __global__ void __launch_bounds__(1024) k_rank_scan(uint32_t T, uint32_t *__rest
     }
 }
 
+// Stable scatter of one tile by digit `pass`.  Each key's place inside the tile comes from
+// warp-level peer ranking (__match_any_sync) and per-warp digit counters; the tile is staged in
+// shared memory in digit order and then written out in runs, so consecutive threads write
+// consecutive addresses.  The last pass writes the order itself: perm[dst] = site and
+// rank[site] = dst.
+struct ScatterSmem {
+    uint32_t wcnt[kRankWarps][256];  // per-warp digit counts, then per-warp exclusive offsets
+    uint32_t tstart[256];            // exclusive start of each digit inside the tile
+    uint32_t goff[256];              // global start of this tile's run of each digit
+    uint32_t skey[kRankTile];
+    uint32_t sval[kRankTile];
+};
+
 __global__ void __launch_bounds__(kRankThreads)
 k_rank_scatter(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ seeds,
                const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
-               const uint32_t *__restrict__ hist, int write_keys)
+               uint32_t *__restrict__ rank_out, const uint32_t *__restrict__ hist)
 {
-    __shared__ uint32_t wcnt[kRankThreads / 32][256];
-    __shared__ uint32_t goff[256];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
     const uint32_t s = blockIdx.y, tile = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int d = threadIdx.x; d < (kRankThreads / 32) * 256; d += kRankThreads) (&wcnt[0][0])[d] = 0u;
-    goff[threadIdx.x] = hist[(size_t(s) * 256 + threadIdx.x) * T + tile];
+    for (int d = threadIdx.x; d < kRankWarps * 256; d += kRankThreads) (&S.wcnt[0][0])[d] = 0u;
+    if (threadIdx.x < 256) S.goff[threadIdx.x] = hist[(size_t(s) * 256 + threadIdx.x) * T + tile];
     __syncthreads();
 
     const uint64_t seed = pass == 0 ? seeds[s] : 0ull;
@@ -130,8 +151,7 @@ k_rank_scatter(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ se
     uint32_t key[kRankItems], val[kRankItems], pos[kRankItems], dig[kRankItems];
 #pragma unroll
     for (int k = 0; k < kRankItems; ++k) {
-        // element order inside the tile: warp-major, then round, then lane (the input order)
-        const uint32_t e = tile * kRankTile + warp * (32 * kRankItems) + k * 32 + lane;
+        const uint32_t e = tile_elem(tile, warp, k, lane);
         const bool valid = e < N;
         uint32_t kk = 0u, vv = 0u;
         if (valid) {
@@ -146,9 +166,9 @@ k_rank_scatter(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ se
         const uint32_t d = valid ? ((kk >> shift) & 255u) : 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t leader = __ffs(peers) - 1;
-        const uint32_t base = valid ? wcnt[warp][d] : 0u;
+        const uint32_t base = valid ? S.wcnt[warp][d] : 0u;
         __syncwarp();
-        if (valid && lane == static_cast<int>(leader)) wcnt[warp][d] = base + __popc(peers);
+        if (valid && lane == static_cast<int>(leader)) S.wcnt[warp][d] = base + __popc(peers);
         __syncwarp();
         key[k] = kk;
         val[k] = vv;
@@ -156,14 +176,36 @@ k_rank_scatter(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ se
         dig[k] = d;
     }
     __syncthreads();
-    {
-        const uint32_t d = threadIdx.x;  // 256 threads, one digit each
+    if (threadIdx.x < 256) {  // per digit: exclusive offsets over warps, and the digit's tile total
+        const uint32_t d = threadIdx.x;
         uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < kRankThreads / 32; ++w) {
-            const uint32_t c = wcnt[w][d];
-            wcnt[w][d] = run;
+#pragma unroll 8
+        for (int w = 0; w < kRankWarps; ++w) {
+            const uint32_t c = S.wcnt[w][d];
+            S.wcnt[w][d] = run;
             run += c;
+        }
+        S.tstart[d] = run;  // tile total for now
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of the 256 tile totals (one warp, 8 per lane)
+        uint32_t v[8], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            v[q] = S.tstart[lane * 8 + q];
+            sum += v[q];
+        }
+        uint32_t x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        uint32_t run = x - sum;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            S.tstart[lane * 8 + q] = run;
+            run += v[q];
         }
     }
     __syncthreads();
@@ -171,22 +213,24 @@ k_rank_scatter(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ se
     for (int k = 0; k < kRankItems; ++k) {
         const uint32_t d = dig[k];
         if (d < 256u) {
-            const uint32_t dst = goff[d] + wcnt[warp][d] + pos[k];
-            vout[row + dst] = val[k];
-            if (write_keys) kout[row + dst] = key[k];
+            const uint32_t lp = S.tstart[d] + S.wcnt[warp][d] + pos[k];
+            S.skey[lp] = key[k];
+            S.sval[lp] = val[k];
         }
     }
-}
-
-__global__ void k_rank_invert(uint32_t N, uint32_t S, const uint32_t *__restrict__ perm,
-                              uint32_t *__restrict__ rank)
-{
-    const size_t total = size_t(N) * S;
-    for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < total;
-         t += size_t(gridDim.x) * blockDim.x) {
-        const size_t s = t / N;
-        const uint32_t r = static_cast<uint32_t>(t - s * N);
-        rank[s * N + __ldg(perm + t)] = r;
+    __syncthreads();
+    const uint32_t tile_n = min(static_cast<uint32_t>(kRankTile), N - tile * kRankTile);
+    const bool last = pass == 3;
+    for (uint32_t lp = threadIdx.x; lp < tile_n; lp += kRankThreads) {
+        const uint32_t kk = S.skey[lp];
+        const uint32_t d = (kk >> shift) & 255u;
+        const uint32_t dst = S.goff[d] + (lp - S.tstart[d]);
+        const uint32_t vv = S.sval[lp];
+        vout[row + dst] = vv;
+        if (last)
+            rank_out[row + vv] = dst;
+        else
+            kout[row + dst] = kk;
     }
 }
 
@@ -209,27 +253,30 @@ extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, 
     uint32_t *a_vals = a_keys + size_t(chunk) * N;
     uint32_t *hist = a_vals + size_t(chunk) * N;
 
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaFuncSetAttribute(k_rank_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(sizeof(ScatterSmem))) != cudaSuccess)
+            return PERC_ECUDA;
+        attr_set = true;
+    }
     for (uint32_t s0 = 0; s0 < num_seeds; s0 += chunk) {
         const uint32_t S = min(chunk, num_seeds - s0);
         const uint64_t *sd = seeds + s0;
-        uint32_t *b_keys = rank + size_t(s0) * N;  // scratch until the final inversion
+        uint32_t *b_keys = rank + size_t(s0) * N;  // keys of passes 1-2, then the inverse order
         uint32_t *b_vals = perm + size_t(s0) * N;
         const dim3 grid(T, S);
         for (int pass = 0; pass < 4; ++pass) {
-            // ping-pong: gen -> A, A -> B, B -> A, A -> B (values only on the last pass)
+            // ping-pong: gen -> A, A -> B, B -> A, A -> (perm, rank)
             const uint32_t *kin = (pass == 2) ? b_keys : a_keys;
             const uint32_t *vin = (pass == 2) ? b_vals : a_vals;
             uint32_t *kout = (pass == 0 || pass == 2) ? a_keys : b_keys;
             uint32_t *vout = (pass == 0 || pass == 2) ? a_vals : b_vals;
             k_rank_hist<<<grid, kRankThreads, 0, stream>>>(pass, uint32_t(N), T, sd, kin, hist);
             k_rank_scan<<<S, 1024, 0, stream>>>(T, hist);
-            k_rank_scatter<<<grid, kRankThreads, 0, stream>>>(pass, uint32_t(N), T, sd, kin, vin, kout,
-                                                              vout, hist, pass != 3);
+            k_rank_scatter<<<grid, kRankThreads, sizeof(ScatterSmem), stream>>>(pass, uint32_t(N), T, sd, kin, vin, kout,
+                                                                                vout, b_keys, hist);
         }
-        const size_t total = size_t(N) * S;
-        const size_t want = (total + 255) / 256;
-        const uint32_t blocks = static_cast<uint32_t>(want < size_t(148 * 64) ? want : size_t(148 * 64));
-        k_rank_invert<<<blocks, 256, 0, stream>>>(uint32_t(N), S, b_vals, b_keys);
     }
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }
