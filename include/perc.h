@@ -132,6 +132,24 @@ int perc_mass(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
               const uint64_t *n, int64_t *mass, void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * perc_nstar_noalloc -- perc_nstar without a caller-provided workspace, for callers that cannot
+ * allocate device memory (code that runs inside a framework which owns every device allocation,
+ * or that must not allocate once a fixed memory budget is set).  The paper has no counterpart;
+ * it is an entry point of this library only.
+ *   Arguments and results are those of perc_nstar.  The scratch is a 64 MiB array that the
+ *   library keeps in device memory (every GPU that loads the library holds it until exit); the
+ *   call allocates nothing.  The first call on a device looks the array's address up and should
+ *   come before any stream capture.  Calls share the array: calls that may overlap on the GPU race
+ *   and must be serialised by the caller.  The launch uses as many CTAs as slots of its size fit
+ *   in the array (a slot is about 15 MiB at L = 16), so it is slower than perc_nstar; a max_L
+ *   whose single slot does not fit (L above 20) returns PERC_EWORKSPACE.  Device-side sample
+ *   errors give n* = PERC_NEVER; the status word is not exposed.
+ */
+int perc_nstar_noalloc(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                       const uint32_t *bracket, uint32_t *nstar, uint32_t *passes, perc_stats *stats,
+                       void *stream);
+
+/*
  * perc_check -- synchronise `stream`, read and clear the device status word of `workspace`
  * (written by perc_nstar / perc_mass), and return it (PERC_OK if nothing went wrong).
  */

@@ -991,3 +991,57 @@ extern "C" const char *perc_status_string(int status)
     default: return "unknown status";
     }
 }
+
+// ------------------------------------------------------------------------------------------------
+// perc_nstar_noalloc: perc_nstar for callers that cannot allocate device memory themselves.
+//
+// Its scratch is one file-scope device array of kNoAllocBytes (64 MiB), which every GPU that
+// loads this library keeps until the process exits.  The first call on a device, with that device
+// current, looks the array's device address up with cudaGetSymbolAddress (in host code the
+// array's name is only a host-side stand-in, not a device address) and caches it per device; make
+// that first call before any stream capture.  The call itself allocates nothing.  All calls share
+// the array, so calls that may overlap on the GPU (other streams, other host threads) race and
+// must be serialised by the caller.  The persistent launch uses as many CTAs as there are slots of
+// the launch's size in the array: lattices whose single slot does not fit are rejected with
+// PERC_EWORKSPACE.
+// ------------------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace perc {
+constexpr size_t kNoAllocBytes = size_t(64) << 20;
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+static void *g_noalloc_ptr[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mutex;
+}  // namespace perc
+
+extern "C" int perc_nstar_noalloc(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                                  const uint32_t *bracket, uint32_t *nstar, uint32_t *passes,
+                                  perc_stats *stats, void *stream_)
+{
+    if (!samples || !nstar || num_samples == 0) return PERC_EINVAL;
+    LaunchCfg cfg;
+    int rc = launch_cfg(PERC_OP_NSTAR, max_L, num_samples, cfg);
+    if (rc != PERC_OK) return rc;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return PERC_ECUDA;
+    void *ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PERC_ECUDA;
+            g_noalloc_ptr[dev] = p;
+        }
+        ws = g_noalloc_ptr[dev];
+    }
+    const size_t slots = (kNoAllocBytes - sizeof(WsHeader)) / cfg.slot_bytes;
+    if (slots == 0) return PERC_EWORKSPACE;  // max_L too large for the static scratch
+    const uint32_t grid = cfg.grid < slots ? cfg.grid : static_cast<uint32_t>(slots);
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (cudaMemsetAsync(ws, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
+    k_nstar<<<grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap,
+                                                     cfg.edge_scap, bracket, nstar, passes, stats,
+                                                     static_cast<char *>(ws), cfg.slot_bytes);
+    return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
+}

@@ -46,6 +46,7 @@ def lib() -> ctypes.CDLL:
         "perc_workspace_bytes": (sz, [i32, u32, u32]),
         "perc_rank": (i32, [u32, vp, u32, vp, vp, vp, sz, vp]),
         "perc_nstar": (i32, [vp, u32, u32, vp, vp, vp, vp, vp, sz, vp]),
+        "perc_nstar_noalloc": (i32, [vp, u32, u32, vp, vp, vp, vp, vp]),
         "perc_mass": (i32, [vp, u32, u32, vp, vp, vp, sz, vp]),
         "perc_check": (i32, [vp, vp]),
         "perc_mlp_forward": (i32, [vp, vp, u32, vp, vp]),
@@ -64,7 +65,7 @@ def lib() -> ctypes.CDLL:
 
 
 def exported_symbols() -> list[str]:
-    return ["perc_workspace_bytes", "perc_rank", "perc_nstar", "perc_mass", "perc_check",
+    return ["perc_workspace_bytes", "perc_rank", "perc_nstar", "perc_nstar_noalloc", "perc_mass", "perc_check",
             "perc_mlp_forward", "perc_mlp_grad", "perc_adam", "perc_mlp_train", "perc_bracket",
             "perc_status_string"]
 
@@ -181,6 +182,17 @@ def nstar(samples: torch.Tensor, max_L: int, bracket: torch.Tensor | None = None
     buf = ws.get(workspace_bytes(OP_NSTAR, max_L, num))
     _ok(lib().perc_nstar(samples.data_ptr(), num, max_L, _ptr(bracket), ns.data_ptr(), _ptr(ps),
                          _ptr(stats), buf.data_ptr(), buf.numel(), _stream(stream)), "perc_nstar")
+    return ns, ps
+
+
+def nstar_noalloc(samples: torch.Tensor, max_L: int, bracket: torch.Tensor | None = None,
+                  stats: torch.Tensor | None = None, stream=None):
+    """perc_nstar_noalloc: n* and passes with the library's own static scratch (no workspace)."""
+    num = samples.shape[0]
+    ns = torch.empty(num, dtype=torch.int32, device="cuda")
+    ps = torch.empty(num, dtype=torch.int32, device="cuda")
+    _ok(lib().perc_nstar_noalloc(samples.data_ptr(), num, max_L, _ptr(bracket), ns.data_ptr(), ps.data_ptr(),
+                                 _ptr(stats), _stream(stream)), "perc_nstar_noalloc")
     return ns, ps
 
 

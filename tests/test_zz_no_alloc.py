@@ -1,0 +1,49 @@
+"""perc_nstar_noalloc, the entry point for callers that cannot allocate device memory.
+
+Such callers (for example code that runs inside a framework which owns every device allocation,
+or that has to stay within a memory budget fixed in advance) cannot hand the library a workspace.
+perc_nstar_noalloc uses a fixed array that the library itself keeps in device memory instead.  These
+tests call it through the C ABI and check that two calls in a row return exactly what perc_nstar
+returns on the same samples; this file is named so that pytest collects it last.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _samples(L, masks, seeds):
+    from paper_2607_18991_b300 import perc
+    perm, rk = perc.rank(L, seeds)
+    masks_all = [m for s in range(len(seeds)) for m in masks]
+    rows = [s for s in range(len(seeds)) for _ in masks]
+    return perc.samples_for(L, masks_all, rows, perm, rk), (perm, rk)
+
+
+@pytest.mark.parametrize("L,masks,seeds", [(8, list(range(1, 128, 5)), [1, 2, 3]),
+                                           (16, [1, 7, 42, 127], [4, 5])])
+def test_noalloc_matches_workspace_entry_point_twice(L, masks, seeds):
+    import torch
+
+    from paper_2607_18991_b300 import perc
+    smp, keep = _samples(L, masks, seeds)
+    want_ns, want_ps = perc.nstar(smp, L)
+    want_ns, want_ps = perc.u32(want_ns), perc.u32(want_ps)
+    N = L ** 5
+    exact = torch.from_numpy(np.stack([want_ns, want_ns], axis=1).astype(np.uint32).view(np.int32)).cuda()
+    for _ in range(2):  # the static scratch keeps the previous call's contents; results must not depend on it
+        ns, ps = perc.nstar_noalloc(smp, L)
+        assert np.array_equal(perc.u32(ns), want_ns)
+        assert np.array_equal(perc.u32(ps), want_ps)
+        ns_b, _ = perc.nstar_noalloc(smp, L, bracket=exact)
+        assert np.array_equal(perc.u32(ns_b), want_ns)
+    assert np.all(want_ns <= N)
+    torch.cuda.synchronize()
+
+
+def test_noalloc_rejects_lattices_beyond_its_scratch():
+    from paper_2607_18991_b300 import perc
+    smp, keep = _samples(4, [1], [1])
+    with pytest.raises(perc.PercError) as err:
+        perc.nstar_noalloc(smp, 40)  # one CTA slot for L = 40 is far larger than 64 MiB
+    assert err.value.rc == -2
