@@ -68,6 +68,31 @@ def oracle_rate(seeds, workers: int):
     return done / dt, done, dt
 
 
+def source_sha256() -> str:
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2607_18991_b300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(key: str):
+    """DRAM bytes per launch from profiles/k_nstar_traffic.txt, if taken on the current sources."""
+    try:
+        vals = {}
+        for line in open(os.path.join(ROOT, "profiles", "k_nstar_traffic.txt")):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("source_sha256") != source_sha256():
+            return None
+        return int(vals[key])
+    except Exception:
+        return None
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -319,12 +344,7 @@ def run_ours(args):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     achieved = alg_bytes / (ms_nstar_learned * 1e-3) / 1e9
-    traffic = None
-    try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "k_nstar_traffic.json")))
-        traffic = prof.get("bytes_per_launch")
-    except Exception:
-        pass
+    traffic = measured_traffic("learned_bytes_per_launch")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
