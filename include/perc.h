@@ -150,6 +150,21 @@ int perc_nstar_noalloc(const perc_sample *samples, uint32_t num_samples, uint32_
                        void *stream);
 
 /*
+ * perc_set_launch_option -- process-wide launch parameters of perc_nstar / perc_mass /
+ * perc_workspace_bytes (not in the paper; set by the autotuner).  Query the workspace size again
+ * after changing one.  Environment variables PERC_THREADS, PERC_SMEM_NODES and PERC_MAX_CTAS
+ * override these.
+ *   PERC_OPT_THREADS     threads per CTA, a multiple of 32 in 32..1024; 0 = by lattice size
+ *   PERC_OPT_SMEM_NODES  most union-find nodes kept in shared memory; -1 = as many as fit (<= 16384)
+ *   PERC_OPT_MAX_CTAS    cap on the persistent grid; 0 = SMs x resident CTAs
+ * Returns PERC_EINVAL for an unknown option or value.
+ */
+#define PERC_OPT_THREADS 1
+#define PERC_OPT_SMEM_NODES 2
+#define PERC_OPT_MAX_CTAS 3
+int perc_set_launch_option(int option, int value);
+
+/*
  * perc_check -- synchronise `stream`, read and clear the device status word of `workspace`
  * (written by perc_nstar / perc_mass), and return it (PERC_OK if nothing went wrong).
  */

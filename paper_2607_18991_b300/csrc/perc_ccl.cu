@@ -29,6 +29,7 @@
 //   * a spanning probe stops as soon as node 1 is hooked (early exit), since span is decided.
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 
 #include "perc_common.cuh"
 
@@ -869,12 +870,25 @@ static int env_int(const char *name, int dflt)
     return v ? atoi(v) : dflt;
 }
 
+struct CfgCache {
+    int threads = 0, occ = 0;
+    size_t smem = 0, attr_smem = 0;
+    bool valid = false;
+};
+constexpr int kCfgDevices = 64;
+static CfgCache g_cfg_cache[2][kCfgDevices];
+static std::mutex g_cfg_mutex;
+
+// Launch options set through perc_set_launch_option (0 = automatic).
+static int g_opt_threads = 0, g_opt_smem_nodes = -1, g_opt_max_ctas = 0;
+
 static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
 {
     if (max_L < 1 || max_L > PERC_MAX_L || num == 0) return PERC_EINVAL;
     const uint64_t Ncap = num_sites(max_L);
     cfg.smem_L = max_L < kSmemBitmapMaxL ? max_L : kSmemBitmapMaxL;
     int dflt_threads = max_L <= 8 ? 256 : (max_L <= 12 ? 512 : 1024);
+    if (g_opt_threads > 0) dflt_threads = g_opt_threads;
     cfg.threads = env_int("PERC_THREADS", dflt_threads);
     if (cfg.threads < 32 || cfg.threads > 1024 || (cfg.threads & 31)) return PERC_EINVAL;
     int dev = 0, sms = 0, occ = 0, optin = 0;
@@ -886,31 +900,49 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
     // registers a thread); each CTA takes an equal share.  What the tables and the bitmap leave
     // goes to union-find nodes (up to kSmemNodes, keeping room for 512 edges) and then to the
     // shared part of the edge list.
-    const int ctas = (65536 / (cfg.threads * 64)) > 0 ? 65536 / (cfg.threads * 64) : 1;
-    const size_t share = size_t(optin) / ctas - 1024;  // room for the static shared variables
     const size_t base = smem_tables_bytes() + smem_bitmap_bytes(cfg.smem_L);
     const size_t min_edges = size_t(kRowCand) * sizeof(uint32_t);  // table-building scratch
+    int ctas = (65536 / (cfg.threads * 64)) > 0 ? 65536 / (cfg.threads * 64) : 1;
+    while (ctas > 1 && size_t(optin) / ctas - 1024 < base + min_edges) --ctas;  // fewer, larger CTAs
+    const size_t share = size_t(optin) / ctas - 1024;  // room for the static shared variables
     if (base + min_edges > share) return PERC_EINVAL;
     size_t room = share - base;
     size_t nodes = room > 512 * sizeof(uint2) ? (room - 512 * sizeof(uint2)) / 4 : 0;
     if (nodes > kSmemNodes) nodes = kSmemNodes;
-    const int nodes_env = env_int("PERC_SMEM_NODES", -1);
+    const int nodes_env = env_int("PERC_SMEM_NODES", g_opt_smem_nodes);
     if (nodes_env >= 0 && size_t(nodes_env) < nodes) nodes = nodes_env;
     nodes &= ~size_t(3);
     cfg.node_cap = static_cast<uint32_t>(nodes);
     room -= smem_nodes_bytes(cfg.node_cap);
     cfg.edge_scap = static_cast<uint32_t>(room / sizeof(uint2));
     cfg.smem = base + smem_nodes_bytes(cfg.node_cap) + size_t(cfg.edge_scap) * sizeof(uint2);
-    const void *fn = op == PERC_OP_MASS ? reinterpret_cast<const void *>(k_mass)
-                                        : reinterpret_cast<const void *>(k_nstar);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cfg.smem)) != cudaSuccess)
-        return PERC_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, cfg.threads, cfg.smem) != cudaSuccess)
-        return PERC_ECUDA;
+    // The attribute and the occupancy are queried once per (kernel, device, threads, shared memory)
+    // and cached, so that a call made while a stream is being captured issues no such query.
+    const int k = op == PERC_OP_MASS ? 1 : 0;
+    const void *fn = k ? reinterpret_cast<const void *>(k_mass) : reinterpret_cast<const void *>(k_nstar);
+    {
+        std::lock_guard<std::mutex> lock(g_cfg_mutex);
+        CfgCache &cc = g_cfg_cache[k][dev < kCfgDevices ? dev : 0];
+        if (cc.threads == cfg.threads && cc.smem == cfg.smem && cc.valid) {
+            occ = cc.occ;
+        } else {
+            if (cfg.smem > cc.attr_smem) {
+                if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cfg.smem)) != cudaSuccess)
+                    return PERC_ECUDA;
+                cc.attr_smem = cfg.smem;
+            }
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, cfg.threads, cfg.smem) != cudaSuccess)
+                return PERC_ECUDA;
+            cc.threads = cfg.threads;
+            cc.smem = cfg.smem;
+            cc.occ = occ;
+            cc.valid = true;
+        }
+    }
     if (occ < 1) return PERC_EINVAL;
     cfg.slot_bytes = slot_bytes_for(Ncap, max_L > cfg.smem_L, cfg.threads);
     uint64_t grid = uint64_t(sms) * occ;
-    const int cta_cap = env_int("PERC_MAX_CTAS", 0);
+    const int cta_cap = env_int("PERC_MAX_CTAS", g_opt_max_ctas);
     if (cta_cap > 0 && uint64_t(cta_cap) < grid) grid = cta_cap;
     if (grid > num) grid = num;
     const uint64_t mem_cap = kSlotCapBytes / cfg.slot_bytes;
@@ -965,6 +997,26 @@ extern "C" int perc_mass(const perc_sample *samples, uint32_t num_samples, uint3
     k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap, cfg.edge_scap, n, mass,
                                                         static_cast<char *>(workspace), cfg.slot_bytes);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
+}
+
+extern "C" int perc_set_launch_option(int option, int value)
+{
+    switch (option) {
+    case PERC_OPT_THREADS:
+        if (value != 0 && (value < 32 || value > 1024 || (value & 31))) return PERC_EINVAL;
+        g_opt_threads = value;
+        return PERC_OK;
+    case PERC_OPT_SMEM_NODES:
+        if (value < -1) return PERC_EINVAL;
+        g_opt_smem_nodes = value;
+        return PERC_OK;
+    case PERC_OPT_MAX_CTAS:
+        if (value < 0) return PERC_EINVAL;
+        g_opt_max_ctas = value;
+        return PERC_OK;
+    default:
+        return PERC_EINVAL;
+    }
 }
 
 extern "C" int perc_check(void *workspace, void *stream_)

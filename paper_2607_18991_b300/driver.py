@@ -107,3 +107,104 @@ def mass(workload, n, budget: int = DEFAULT_BUDGET):
     if rc != 0:
         raise perc.PercError(rc, "perc_mass device status")
     return out
+
+
+# ------------------------------------------------------------------------------------------------
+# multi-process sharding: every sample is independent, so ranks take disjoint seed blocks (all
+# masks and all L of a seed stay together and share one ranking) and the results are merged once
+# at the end; there is no exchange on the data path
+# ------------------------------------------------------------------------------------------------
+def shard(workload, rank: int, world: int) -> np.ndarray:
+    """Indices of the rows of `workload` that rank `rank` of `world` processes."""
+    workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
+    keys = np.unique(workload[:, [0, 2]], axis=0)  # distinct (L, seed), sorted
+    owner = np.arange(len(keys)) % world
+    mine = {tuple(k) for k, o in zip(keys.tolist(), owner) if o == rank}
+    return np.array([i for i, (L, _, s) in enumerate(workload.tolist()) if (L, s) in mine], dtype=np.int64)
+
+
+def merge_shards(num: int, parts) -> np.ndarray:
+    """Combine [(indices, values), ...] from all ranks into one array of length num."""
+    parts = list(parts)
+    dtype = np.asarray(parts[0][1]).dtype if parts else np.uint32
+    out = np.zeros(num, dtype=dtype)
+    seen = np.zeros(num, dtype=bool)
+    for idx, vals in parts:
+        idx = np.asarray(idx, dtype=np.int64)
+        if np.any(seen[idx]):
+            raise ValueError("a sample was computed by two ranks")
+        out[idx] = vals
+        seen[idx] = True
+    if not seen.all():
+        raise ValueError("some samples were computed by no rank")
+    return out
+
+
+# ------------------------------------------------------------------------------------------------
+# a fixed-shape step with every buffer allocated up front (for timing and CUDA-graph capture)
+# ------------------------------------------------------------------------------------------------
+class NstarStep:
+    """Rank the seeds, propose brackets and find n* for all (mask, seed) pairs at one L.
+
+    Every device buffer is allocated here, so ``run`` only enqueues library calls on the stream and
+    can be captured in a CUDA graph (``capture``).  Samples are seed-major.
+    """
+
+    def __init__(self, L: int, masks, seeds, params: torch.Tensor | None = None, margin: float = 0.0):
+        self.L = int(L)
+        self.masks = np.asarray(list(masks), dtype=np.int64)
+        self.seeds = np.asarray(list(seeds), dtype=np.int64)
+        self.params = params
+        self.margin = float(margin)
+        N = self.L ** 5
+        S = len(self.seeds)
+        self.workload = np.array([(self.L, m, s) for s in self.seeds for m in self.masks], dtype=np.int64)
+        self.num = len(self.workload)
+        self.seeds_dev = torch.as_tensor(self.seeds, device="cuda")
+        self.perm = torch.empty((S, N), dtype=torch.int32, device="cuda")
+        self.rank = torch.empty((S, N), dtype=torch.int32, device="cuda")
+        rows = np.repeat(np.arange(S), len(self.masks))
+        self.samples = perc.samples_for(self.L, np.tile(self.masks, S), rows, self.perm, self.rank)
+        self.bracket = torch.empty((self.num, 2), dtype=torch.int32, device="cuda")
+        self.nstar = torch.empty(self.num, dtype=torch.int32, device="cuda")
+        self.passes = torch.empty(self.num, dtype=torch.int32, device="cuda")
+        nb = max(perc.workspace_bytes(perc.OP_RANK, self.L, S), perc.workspace_bytes(perc.OP_NSTAR, self.L, self.num))
+        self.ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        self.lib = perc.lib()
+
+    def run_rank(self, stream=None):
+        sp = perc._stream(stream)
+        perc._ok(self.lib.perc_rank(self.L, self.seeds_dev.data_ptr(), len(self.seeds), self.perm.data_ptr(),
+                                    self.rank.data_ptr(), self.ws.data_ptr(), self.ws.numel(), sp), "perc_rank")
+
+    def run_bracket(self, stream=None):
+        perc._ok(self.lib.perc_bracket(self.params.data_ptr(), self.samples.data_ptr(), self.num, self.margin,
+                                       self.bracket.data_ptr(), perc._stream(stream)), "perc_bracket")
+
+    def run_nstar(self, learned: bool, stats: torch.Tensor | None = None, stream=None):
+        br = self.bracket.data_ptr() if learned else None
+        perc._ok(self.lib.perc_nstar(self.samples.data_ptr(), self.num, self.L, br, self.nstar.data_ptr(),
+                                     self.passes.data_ptr(), perc._ptr(stats), self.ws.data_ptr(), self.ws.numel(),
+                                     perc._stream(stream)), "perc_nstar")
+
+    def run(self, learned: bool = True, stats: torch.Tensor | None = None, stream=None):
+        self.run_rank(stream)
+        if learned:
+            self.run_bracket(stream)
+        self.run_nstar(learned, stats, stream)
+
+    def capture(self, learned: bool = True) -> torch.cuda.CUDAGraph:
+        """CUDA graph of one step (warm the library up with ``run`` first)."""
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(g, stream=s):
+            self.run(learned)
+        torch.cuda.current_stream().wait_stream(s)
+        return g
+
+    def result(self):
+        rc = self.lib.perc_check(self.ws.data_ptr(), perc._stream())
+        if rc != 0:
+            raise perc.PercError(rc, "perc_nstar device status")
+        return perc.u32(self.nstar), perc.u32(self.passes)

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libperc.so")
 NEVER = 0xFFFFFFFF
 MAX_L = 73
 OP_RANK, OP_NSTAR, OP_MASS = 1, 2, 3
+OPT_THREADS, OPT_SMEM_NODES, OPT_MAX_CTAS = 1, 2, 3
 MLP_NPARAM = 4931
 STATS_FIELDS = ("passes", "new_sites", "probe_sites", "hooks", "early_exits", "fallbacks",
                 "verified", "sites_merged", "unions", "cyc_setup", "cyc_update", "cyc_union",
@@ -49,6 +50,7 @@ def lib() -> ctypes.CDLL:
         "perc_nstar_noalloc": (i32, [vp, u32, u32, vp, vp, vp, vp, vp]),
         "perc_mass": (i32, [vp, u32, u32, vp, vp, vp, sz, vp]),
         "perc_check": (i32, [vp, vp]),
+        "perc_set_launch_option": (i32, [i32, i32]),
         "perc_mlp_forward": (i32, [vp, vp, u32, vp, vp]),
         "perc_mlp_grad": (i32, [vp, vp, vp, u32, vp, vp, vp]),
         "perc_adam": (i32, [vp, vp, vp, vp, u32, u32, f32, f32, f32, f32, vp]),
@@ -67,7 +69,7 @@ def lib() -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     return ["perc_workspace_bytes", "perc_rank", "perc_nstar", "perc_nstar_noalloc", "perc_mass", "perc_check",
             "perc_mlp_forward", "perc_mlp_grad", "perc_adam", "perc_mlp_train", "perc_bracket",
-            "perc_status_string"]
+            "perc_status_string", "perc_set_launch_option"]
 
 
 def status_string(rc: int) -> str:
@@ -86,6 +88,10 @@ def _stream(stream=None) -> int:
 
 def _ptr(t) -> int | None:
     return None if t is None else t.data_ptr()
+
+
+def set_launch_option(option: int, value: int):
+    _ok(lib().perc_set_launch_option(option, value), "perc_set_launch_option")
 
 
 def workspace_bytes(op: int, max_L: int, num: int) -> int:
