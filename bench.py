@@ -188,37 +188,47 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t_train
 
-    # ---- resident inputs
-    seeds_dev = torch.as_tensor(seeds.astype(np.int64), device=dev)
+    # ---- resident inputs: one preallocated step (seeds, orders, sample table, brackets, outputs)
+    from paper_2607_18991_b300 import autotune
     N = L ** 5
-    perm = torch.empty((len(seeds), N), dtype=torch.int32, device=dev)
-    rk = torch.empty((len(seeds), N), dtype=torch.int32, device=dev)
-    rows = np.searchsorted(seeds, wl[:, 2])
-    samples = perc.samples_for(L, wl[:, 1], rows, perm, rk)
-    br = torch.empty((num, 2), dtype=torch.int32, device=dev)
-    ns = torch.empty(num, dtype=torch.int32, device=dev)
-    ps = torch.empty(num, dtype=torch.int32, device=dev)
-    rank_ws_bytes = perc.workspace_bytes(perc.OP_RANK, L, len(seeds))
-    nstar_ws_bytes = perc.workspace_bytes(perc.OP_NSTAR, L, num)
-    ws_buf = torch.empty(max(rank_ws_bytes, nstar_ws_bytes), dtype=torch.uint8, device=dev)
+    step_obj = driver.NstarStep(L, MASKS, seeds, params=params, margin=args.margin)
+    samples, br, ns, ps = step_obj.samples, step_obj.bracket, step_obj.nstar, step_obj.passes
+    perm, rk, ws_buf = step_obj.perm, step_obj.rank, step_obj.ws
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     lib = perc.lib()
     sp = stream.cuda_stream
 
+    # ---- autotune the launch on a few seeds of the workload (cached per device and L)
+    tuned = None
+    if not args.no_tune:
+        step_obj.run_rank()
+        step_obj.run_bracket()
+        few = np.arange(min(4, len(seeds)) * len(MASKS))
+        sub = samples[torch.as_tensor(few, device=dev)]
+        tuned = autotune.tune(sub, L, bracket=br[torch.as_tensor(few, device=dev)])
+        torch.cuda.synchronize()
+        nb = max(perc.workspace_bytes(perc.OP_RANK, L, len(seeds)), perc.workspace_bytes(perc.OP_NSTAR, L, num))
+        if nb > ws_buf.numel():
+            step_obj.ws = ws_buf = torch.empty(nb, dtype=torch.uint8, device=dev)
+
     def step(learned: bool, ev=None):
-        perc._ok(lib.perc_rank(L, seeds_dev.data_ptr(), len(seeds), perm.data_ptr(), rk.data_ptr(),
-                               ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_rank")
+        step_obj.run_rank()
         if ev is not None:
             ev[0].record(stream)
         if learned:
-            perc._ok(lib.perc_bracket(params.data_ptr(), samples.data_ptr(), num, args.margin, br.data_ptr(), sp),
-                     "perc_bracket")
+            step_obj.run_bracket()
         if ev is not None:
             ev[1].record(stream)
-        perc._ok(lib.perc_nstar(samples.data_ptr(), num, L, br.data_ptr() if learned else None, ns.data_ptr(),
-                                ps.data_ptr(), None, ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_nstar")
+        step_obj.run_nstar(learned)
         if ev is not None:
             ev[2].record(stream)
+
+    graphs = {}
+    if args.graph:
+        for learned in (True, False):
+            step(learned)
+            torch.cuda.synchronize()
+            graphs[learned] = step_obj.capture(learned)
 
     def timed(learned: bool, K: int, W: int):
         for _ in range(W):
@@ -241,6 +251,25 @@ def run_ours(args):
         torch.cuda.profiler.stop()
         return tot / K, t_rank / K, t_nstar / K
 
+    def timed_graph(learned: bool, K: int, W: int):
+        g = graphs[learned]
+        for _ in range(W):
+            g.replay()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(K):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / K
+
     if args.ncu_case:
         # one learned and one plain launch inside the profiler range, nothing else (for ncu)
         step(True)
@@ -260,33 +289,34 @@ def run_ours(args):
     with ClockSampler(smi_index) as clk:
         ms_learned, ms_rank, ms_nstar_learned = timed(True, args.steps, args.warmup)
         ms_plain, _, ms_nstar_plain = timed(False, args.steps, args.warmup)
+        ms_graph = {k: timed_graph(k, args.steps, args.warmup) for k in graphs}
     clocks = clk.summary()
+    # the headline is the faster of the eager and the graph-replayed step (same work)
+    ms_learned_eager, ms_plain_eager = ms_learned, ms_plain
+    if True in ms_graph:
+        ms_learned = min(ms_learned, ms_graph[True])
+        ms_plain = min(ms_plain, ms_graph[False])
 
     # passes and correctness summary of the last learned / plain runs
-    step(True)
-    passes_learned = perc.u32(ps).astype(np.float64).mean()
-    ns_learned = perc.u32(ns).copy()
-    stats = perc.new_stats()
-    perc._ok(lib.perc_nstar(samples.data_ptr(), num, L, br.data_ptr(), ns.data_ptr(), ps.data_ptr(),
-                            stats.data_ptr(), ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_nstar")
-    st_learned = perc.stats_dict(stats)
-    step(False)
-    passes_plain = perc.u32(ps).astype(np.float64).mean()
-    ns_plain = perc.u32(ns).copy()
-    assert np.array_equal(ns_learned, ns_plain), "learned and plain n* differ"
-    stats = perc.new_stats()
-    perc._ok(lib.perc_nstar(samples.data_ptr(), num, L, None, ns.data_ptr(), ps.data_ptr(),
-                            stats.data_ptr(), ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_nstar")
-    st_plain = perc.stats_dict(stats)
-    rc = lib.perc_check(ws_buf.data_ptr(), sp)
-    assert rc == 0, perc.status_string(rc)
+    st = {}
+    out = {}
+    for learned in (True, False):
+        stats = perc.new_stats()
+        step_obj.run(learned, stats=stats)
+        torch.cuda.synchronize()
+        out[learned] = step_obj.result()
+        st[learned] = perc.stats_dict(stats)
+    assert np.array_equal(out[True][0], out[False][0]), "learned and plain n* differ"
+    passes_learned = out[True][1].astype(np.float64).mean()
+    passes_plain = out[False][1].astype(np.float64).mean()
+    st_learned, st_plain = st[True], st[False]
 
     # ---- e2e through the C ABI from pinned host buffers
     seeds_host = torch.from_numpy(seeds.astype(np.int64)).pin_memory()
     samples_host = samples.cpu().pin_memory()
     params_host = params.cpu().pin_memory()
     ns_host = torch.empty(num, dtype=torch.int32).pin_memory()
-    seeds_d2 = torch.empty_like(seeds_dev)
+    seeds_d2 = torch.empty_like(step_obj.seeds_dev)
     samples_d2 = torch.empty_like(samples)
     params_d2 = torch.empty_like(params)
 
@@ -368,9 +398,11 @@ def run_ours(args):
                        "l2": "flushed (256 MiB write) between timed steps; site orders 2 GiB > L2",
                        "parallelism": f"dp{world} (seed blocks, no collective)"},
             "plain": {"value": world * num / (ms_plain * 1e-3), "unit": "samples/s", "ms_per_step": ms_plain,
+                      "ms_per_step_eager": ms_plain_eager, "ms_per_step_graph": ms_graph.get(False),
                       "nstar_ms": ms_nstar_plain, "passes_per_sample": passes_plain, "stats": st_plain},
             "learned": {"value": value, "ms_per_step": ms_learned, "nstar_ms": ms_nstar_learned,
                         "rank_ms": ms_rank, "passes_per_sample": passes_learned, "stats": st_learned,
+                        "ms_per_step_eager": ms_learned_eager, "ms_per_step_graph": ms_graph.get(True),
                         "train_s": t_train, "train_loss_last": float(losses[-1].item())},
             "e2e": {"value": world * num / (e2e_ms * 1e-3), "unit": "samples/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -380,6 +412,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": gpu_launches,
+            "autotune": None if tuned is None else {k: tuned[k] for k in ("threads", "smem_nodes", "ms")},
         }
         print(json.dumps(line))
     if world > 1:
@@ -433,6 +466,8 @@ def main():
     ap.add_argument("--margin", type=float, default=0.05)
     ap.add_argument("--cpu-seeds-per-worker", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
+    ap.add_argument("--no-graph", dest="graph", action="store_false", help="do not time CUDA-graph replays")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one learned and one plain step inside a profiler range and exit")
     args = ap.parse_args()
