@@ -1,0 +1,127 @@
+"""Measured runs of the workloads besides the L = 16 benchmark line.
+
+    python -m paper_2607_18991_b300.experiments mass|L24|L40|mixed|all [--quick]
+
+Each run prints one JSON line:
+
+* ``mass``  -- compact neighborhoods {1..k}, k = 1..7: p_hat(k) = mean n*/16^5 over seeds 1..256 at
+  L = 16, then S_max at n = floor(p_hat L^5 + 1/2) for L in {8, 12, 16, 20, 24, 32}, seeds 1..512,
+  and the d_f least-squares fit (eq. M_vs_L) with its percentage error (eq. delta);
+* ``L24``   -- all 127 neighborhoods at L = 24, seeds 1..128: samples/s and passes with the learned
+  bracket (network trained at L = 8 and 16 only) and with the plain one;
+* ``L40``   -- sc(5)-1,...,7 at L = 40 (102.4M sites), seeds 1..8;
+* ``mixed`` -- 4096 samples with L uniform in {10..40} and random masks, plain and learned.
+
+Times are wall-clock with the device synchronised, ranking included.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import analysis, bracket, driver, perc, workloads
+
+L16 = 16
+
+
+def trained_params(quick: bool = False):
+    """Bracket network trained on plain n* of held-out seeds at L = 8 (zone 1) and L = 16."""
+    n8, n16 = (200, 8) if quick else (1000, 64)
+    wl = np.concatenate([np.array([(8, 1, s) for s in range(1_000_001, 1_000_001 + n8)]),
+                         np.array([(L16, m, s) for m in workloads.ALL_MASKS
+                                   for s in range(1_000_001, 1_000_001 + n16)])])
+    ns, _ = driver.nstar(wl)
+    params, _ = bracket.train(wl[:, 0], wl[:, 1], ns, steps=3000, lr=3e-3)
+    return params
+
+
+def _timed(fn):
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t
+
+
+def run_mass(quick: bool = False) -> dict:
+    seeds16 = range(1, 33 if quick else 257)
+    wl16 = workloads.samples(L16, workloads.COMPACT_MASKS, seeds16)
+    ns16, _ = driver.nstar(wl16)
+    p_hat = {m: analysis.p_hat(L16, ns16[wl16[:, 1] == m]) for m in workloads.COMPACT_MASKS}
+    nseeds = 32 if quick else 512
+    rows, ns = [], []
+    for L in workloads.MASS_LS:
+        for m in workloads.COMPACT_MASKS:
+            for s in range(1, nseeds + 1):
+                rows.append((L, m, s))
+                ns.append(workloads.mass_n(p_hat[m], L))
+    wl = np.array(rows, dtype=np.int64)
+    mass, dt = _timed(lambda: driver.mass(wl, ns))
+    fits = {}
+    for m in workloads.COMPACT_MASKS:
+        mean = [float(mass[(wl[:, 0] == L) & (wl[:, 1] == m)].mean()) for L in workloads.MASS_LS]
+        df, err = analysis.fit_df(workloads.MASS_LS, mean)
+        k = bin(m).count("1")
+        fits[f"1..{k}"] = {"p_hat": p_hat[m], "d_f": df, "err": err, "delta_pct": analysis.delta(df),
+                           "mean_mass": mean}
+    return {"workload": "compact masses", "samples": len(wl), "seconds": dt, "samples_per_s": len(wl) / dt,
+            "L": workloads.MASS_LS, "seeds": nseeds, "fits": fits}
+
+
+def _learned_vs_plain(wl: np.ndarray, params) -> dict:
+    out = {}
+    for name, p in (("learned", params), ("plain", None)):
+        stats = perc.new_stats()
+        (ns, passes), dt = _timed(lambda: driver.nstar(wl, params=p, margin=0.05, stats=stats))
+        st = perc.stats_dict(stats)
+        out[name] = {"seconds": dt, "samples_per_s": len(wl) / dt, "passes_per_sample": float(passes.mean()),
+                     "fallbacks": st["fallbacks"], "verified": st["verified"]}
+        out[name + "_nstar"] = ns
+    assert np.array_equal(out.pop("learned_nstar"), out.pop("plain_nstar")), "learned and plain n* differ"
+    return out
+
+
+def run_L24(params, quick: bool = False) -> dict:
+    wl = workloads.all127_L24(16 if quick else 128)
+    res = _learned_vs_plain(wl, params)
+    return {"workload": "all 127 masks, L=24", "samples": len(wl), **res}
+
+
+def run_L40(params, quick: bool = False) -> dict:
+    wl = workloads.z892_L40(2 if quick else 8)
+    res = _learned_vs_plain(wl, params)
+    return {"workload": "sc(5)-1..7, L=40", "samples": len(wl), **res}
+
+
+def run_mixed(params, quick: bool = False) -> dict:
+    wl = workloads.mixed4096(512 if quick else 4096)
+    res = _learned_vs_plain(wl, params)
+    return {"workload": "mixed L in 10..40, random masks", "samples": len(wl), **res}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("which", choices=["mass", "L24", "L40", "mixed", "all"])
+    ap.add_argument("--quick", action="store_true")
+    args = ap.parse_args()
+    torch.cuda.set_device(0)
+    params = None if args.which == "mass" else trained_params(args.quick)
+    todo = ["mass", "L24", "L40", "mixed"] if args.which == "all" else [args.which]
+    for w in todo:
+        if w == "mass":
+            r = run_mass(args.quick)
+        elif w == "L24":
+            r = run_L24(params, args.quick)
+        elif w == "L40":
+            r = run_L40(params, args.quick)
+        else:
+            r = run_mixed(params, args.quick)
+        print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()

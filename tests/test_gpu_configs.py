@@ -1,0 +1,77 @@
+"""Parity on the other workloads: compact-neighborhood masses, L = 24 with the learned bracket,
+L = 40 (the largest lattice), the mixed-L batch, and the full L = 16 benchmark launch (sampled)."""
+import numpy as np
+import pytest
+
+from gpu_util import orc_mass, orc_nstar
+
+pytestmark = pytest.mark.gpu
+
+# p_c of the compact neighborhoods (Table I / Table II of the paper); they only place n
+PC_COMPACT = {1: 0.14079633, 3: 0.033794, 7: 0.013190, 15: 0.007850, 31: 0.0051575, 63: 0.002981,
+              127: 0.001934}
+
+
+def quick_params():
+    from paper_2607_18991_b300 import bracket, driver
+    wl = np.concatenate([np.array([(8, 1, s) for s in range(500001, 500201)]),
+                         np.array([(16, m, s) for m in range(1, 128) for s in range(500001, 500005)])])
+    ns, _ = driver.nstar(wl)
+    params, _ = bracket.train(wl[:, 0], wl[:, 1], ns, steps=1500, lr=3e-3)
+    return params
+
+
+@pytest.mark.parametrize("L", [8, 12, 16, 20, 24])
+def test_compact_masses(L):
+    from paper_2607_18991_b300 import driver, workloads
+    w = workloads.samples(L, workloads.COMPACT_MASKS, [1, 2])
+    n = np.array([workloads.mass_n(PC_COMPACT[m], L) for _, m, _ in w])
+    assert np.array_equal(driver.mass(w, n), orc_mass(w, n))
+
+
+def test_compact_mass_L32():
+    from paper_2607_18991_b300 import driver, workloads
+    w = np.array([(32, 3, 1)])
+    n = np.array([workloads.mass_n(PC_COMPACT[3], 32)])
+    assert np.array_equal(driver.mass(w, n), orc_mass(w, n))
+
+
+def test_L24_learned_and_plain():
+    from paper_2607_18991_b300 import driver, workloads
+    w = workloads.all127_L24(2)
+    want = orc_nstar(w)
+    ns_plain, _ = driver.nstar(w)
+    ns_learned, _ = driver.nstar(w, params=quick_params(), margin=0.05)
+    assert np.array_equal(ns_plain, want)
+    assert np.array_equal(ns_learned, want)
+
+
+def test_L40_all_zones():
+    from paper_2607_18991_b300 import driver, workloads
+    w = workloads.z892_L40(1)
+    ns, passes = driver.nstar(w)
+    assert np.array_equal(ns, orc_nstar(w))
+    assert passes[0] in (26, 27)  # floor / ceil of log2(40^5)
+
+
+def test_mixed_batch_sampled():
+    from paper_2607_18991_b300 import driver, workloads
+    w = workloads.mixed4096()
+    pick = np.nonzero(w[:, 0] <= 20)[0][:48]
+    sub = w[pick]
+    ns, _ = driver.nstar(sub, params=quick_params(), margin=0.05)
+    assert np.array_equal(ns, orc_nstar(sub))
+
+
+def test_full_size_L16_launch_sampled():
+    # the benchmark's launch: all 127 masks x seeds 1..256 in one persistent launch, learned bracket
+    import torch
+
+    from paper_2607_18991_b300 import driver
+    step = driver.NstarStep(16, range(1, 128), range(1, 257), params=quick_params(), margin=0.05)
+    step.run(True)
+    torch.cuda.synchronize()
+    ns, passes = step.result()
+    sel = np.nonzero(np.isin(step.workload[:, 2], [1, 128, 256]))[0]
+    assert np.array_equal(ns[sel], orc_nstar(step.workload[sel]))
+    assert passes.max() <= 2 * 20 + 1  # a fallback costs at most one failed check plus the plain bisection
