@@ -26,6 +26,8 @@ import torch
 from . import analysis, bracket, driver, perc, workloads
 
 L16 = 16
+# p_c of the compact neighborhoods as the paper lists them (Table II), for the cross-check fit
+PC_TABLE2 = {1: 0.14079633, 3: 0.033794, 7: 0.013190, 15: 0.007850, 31: 0.0051575, 63: 0.002981, 127: 0.001934}
 
 
 def trained_params(quick: bool = False):
@@ -47,18 +49,13 @@ def _timed(fn):
     return out, time.perf_counter() - t
 
 
-def run_mass(quick: bool = False) -> dict:
-    seeds16 = range(1, 33 if quick else 257)
-    wl16 = workloads.samples(L16, workloads.COMPACT_MASKS, seeds16)
-    ns16, _ = driver.nstar(wl16)
-    p_hat = {m: analysis.p_hat(L16, ns16[wl16[:, 1] == m]) for m in workloads.COMPACT_MASKS}
-    nseeds = 32 if quick else 512
+def _mass_fits(p_of_mask: dict, nseeds: int):
     rows, ns = [], []
     for L in workloads.MASS_LS:
         for m in workloads.COMPACT_MASKS:
             for s in range(1, nseeds + 1):
                 rows.append((L, m, s))
-                ns.append(workloads.mass_n(p_hat[m], L))
+                ns.append(workloads.mass_n(p_of_mask[m], L))
     wl = np.array(rows, dtype=np.int64)
     mass, dt = _timed(lambda: driver.mass(wl, ns))
     fits = {}
@@ -66,10 +63,21 @@ def run_mass(quick: bool = False) -> dict:
         mean = [float(mass[(wl[:, 0] == L) & (wl[:, 1] == m)].mean()) for L in workloads.MASS_LS]
         df, err = analysis.fit_df(workloads.MASS_LS, mean)
         k = bin(m).count("1")
-        fits[f"1..{k}"] = {"p_hat": p_hat[m], "d_f": df, "err": err, "delta_pct": analysis.delta(df),
+        fits[f"1..{k}"] = {"p": p_of_mask[m], "d_f": df, "err": err, "delta_pct": analysis.delta(df),
                            "mean_mass": mean}
+    return wl, dt, fits
+
+
+def run_mass(quick: bool = False) -> dict:
+    seeds16 = range(1, 33 if quick else 257)
+    wl16 = workloads.samples(L16, workloads.COMPACT_MASKS, seeds16)
+    ns16, _ = driver.nstar(wl16)
+    p_hat = {m: analysis.p_hat(L16, ns16[wl16[:, 1] == m]) for m in workloads.COMPACT_MASKS}
+    nseeds = 32 if quick else 512
+    wl, dt, fits = _mass_fits(p_hat, nseeds)
+    _, dt2, fits_t2 = _mass_fits(PC_TABLE2, nseeds)  # physics cross-check at the paper's p_c
     return {"workload": "compact masses", "samples": len(wl), "seconds": dt, "samples_per_s": len(wl) / dt,
-            "L": workloads.MASS_LS, "seeds": nseeds, "fits": fits}
+            "L": workloads.MASS_LS, "seeds": nseeds, "fits_at_p_hat_L16": fits, "fits_at_table2_pc": fits_t2}
 
 
 def _learned_vs_plain(wl: np.ndarray, params) -> dict:
