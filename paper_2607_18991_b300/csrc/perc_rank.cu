@@ -7,7 +7,8 @@
 // and every pass is stable, so equal keys stay in index order.  Four 8-bit passes, each
 //   k_rank_hist    per-tile digit counts (pass 0 draws the keys itself, nothing is stored first),
 //   k_rank_scan    exclusive scan per seed in digit-major order -> tile output offsets,
-//   k_rank_scatter stable scatter: warp-level peer ranking with __match_any_sync,
+//   k_rank_scatter stable scatter: warp-level peer ranking (lanes with equal digits found with
+//                  eight ballots), tile staged in shared memory in digit order, written in runs,
 // and the last scatter also writes rank[perm[r]] = r.  Seeds are sorted in chunks that fit the
 // workspace.
 #include <cstdio>
@@ -16,10 +17,10 @@
 
 namespace perc {
 
-constexpr int kRankThreads = 1024;
+constexpr int kRankThreads = 512;
 constexpr int kRankWarps = kRankThreads / 32;
 constexpr int kRankItems = 8;
-constexpr int kRankTile = kRankThreads * kRankItems;  // 8192 keys per tile
+constexpr int kRankTile = kRankThreads * kRankItems;  // 4096 keys per tile
 constexpr int kRankMaxChunk = 64;                     // seeds per chunk (upper bound)
 constexpr size_t kRankChunkBytes = size_t(4) << 30;   // workspace aimed at per chunk
 
@@ -55,7 +56,7 @@ __device__ __forceinline__ uint32_t tile_elem(uint32_t tile, int warp, int k, in
     return tile * kRankTile + warp * (32 * kRankItems) + k * 32 + lane;
 }
 
-__global__ void __launch_bounds__(kRankThreads)
+__global__ void __launch_bounds__(kRankThreads, 2)
 k_rank_hist(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ seeds,
             const uint32_t *__restrict__ keys_in, uint32_t *__restrict__ hist)
 {
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(1024) k_rank_scan(uint32_t T, uint32_t *__rest
 }
 
 // Stable scatter of one tile by digit `pass`.  Each key's place inside the tile comes from
-// warp-level peer ranking (__match_any_sync) and per-warp digit counters; the tile is staged in
+// warp-level peer ranking (ballots over the digit bits) and per-warp digit counters; the tile is staged in
 // shared memory in digit order and then written out in runs, so consecutive threads write
 // consecutive addresses.  The last pass writes the order itself: perm[dst] = site and
 // rank[site] = dst.
@@ -130,7 +131,7 @@ struct ScatterSmem {
     uint32_t sval[kRankTile];
 };
 
-__global__ void __launch_bounds__(kRankThreads)
+__global__ void __launch_bounds__(kRankThreads, 2)
 k_rank_scatter(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ seeds,
                const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
@@ -164,7 +165,14 @@ k_rank_scatter(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ se
             }
         }
         const uint32_t d = valid ? ((kk >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        // lanes with the same digit: AND over the 8 digit bits of (ballot of the bit, or its complement)
+        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+        if (!valid) peers = ~peers;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bb : ~bb;
+        }
         const uint32_t leader = __ffs(peers) - 1;
         const uint32_t base = valid ? S.wcnt[warp][d] : 0u;
         __syncwarp();
