@@ -157,11 +157,17 @@ int perc_nstar_noalloc(const perc_sample *samples, uint32_t num_samples, uint32_
  *   PERC_OPT_THREADS     threads per CTA, a multiple of 32 in 32..1024; 0 = by lattice size
  *   PERC_OPT_SMEM_NODES  most union-find nodes kept in shared memory; -1 = as many as fit (<= 16384)
  *   PERC_OPT_MAX_CTAS    cap on the persistent grid; 0 = SMs x resident CTAs
- * Returns PERC_EINVAL for an unknown option or value.
+ *   PERC_OPT_GROUP       CTAs that share one sample in perc_nstar (a cooperative launch whose
+ *                        bitmap and union-find live in global memory); 0 = automatic (groups for
+ *                        batches of lattices above L = 17 with fewer samples than CTAs), 1 = never,
+ *                        2..64 = that many
+ * Returns PERC_EINVAL for an unknown option or value.  Environment variable PERC_GROUP overrides
+ * PERC_OPT_GROUP.
  */
 #define PERC_OPT_THREADS 1
 #define PERC_OPT_SMEM_NODES 2
 #define PERC_OPT_MAX_CTAS 3
+#define PERC_OPT_GROUP 4
 int perc_set_launch_option(int option, int value);
 
 /*

@@ -446,19 +446,34 @@ __device__ __forceinline__ uint32_t entry_hits(const SiteGeo &g, const uint32_t 
     }
 }
 
-template <bool kSmemBm, bool kFaces, bool kPlanes>
+// The early-exit flag and the undo-log length live in shared memory for a one-CTA sample and in
+// global memory (read L2-coherently) when a group of CTAs works on one sample; CTA `member` of a
+// group of `members` takes every members-th chunk of the new sites.
+template <bool kGroup>
+__device__ __forceinline__ uint32_t read_flag(const uint32_t *f)
+{
+    return kGroup ? __ldcg(f) : *reinterpret_cast<const volatile uint32_t *>(f);
+}
+
+template <bool kSmemBm, bool kFaces, bool kPlanes, bool kGroup = false>
 __device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *logb, const uint32_t *bm,
                                            const RowEntry *rows, const PlaneEntry *planes, const EdgeList &E,
                                            const uint32_t *perm, const uint32_t *rank, uint32_t L,
-                                           const FastDiv &fd, uint32_t r0, uint32_t r1, uint32_t nold)
+                                           const FastDiv &fd, uint32_t r0, uint32_t r1, uint32_t nold,
+                                           uint32_t *stop_flag = nullptr, uint32_t *logn = nullptr,
+                                           uint32_t member = 0, uint32_t members = 1)
 {
     const uint32_t R = kPlanes ? c.NP : c.R;
     const uint32_t gshift = lanes_shift(r1 - r0, R);
     const uint32_t gsize = 1u << gshift, gl = threadIdx.x & (gsize - 1u), grp = threadIdx.x >> gshift;
     const uint32_t chunk = blockDim.x >> gshift;
-    uint32_t *stopp = kFaces ? &c.stop : nullptr;
+    if (!kGroup) {
+        stop_flag = &c.stop;
+        logn = &c.logn;
+    }
+    uint32_t *stopp = kFaces ? stop_flag : nullptr;
     uint32_t hooks = 0, sites = 0, unions = 0, parity = 0;
-    for (uint32_t base = r0; base < r1; base += chunk, parity ^= 1u) {
+    for (uint32_t base = r0 + member * chunk; base < r1; base += members * chunk, parity ^= 1u) {
         uint32_t *ecount = &c.ecount[parity];
         const long long t_chunk = clock64();
         // ---- scan
@@ -497,8 +512,8 @@ __device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *log
         const uint32_t ne = *ecount;
         if (threadIdx.x == 0) c.ecount[parity ^ 1u] = 0u;  // the next chunk's counter
         for (uint32_t e = threadIdx.x, it = 0; e < ne; e += blockDim.x, ++it) {
-            if (kFaces && (it & 7u) == 7u && *reinterpret_cast<volatile uint32_t *>(&c.stop)) break;
-            hooks += unite_edge(edge_get(E, e), rank, P, nold, logb, &c.logn, stopp, unions);
+            if (kFaces && (it & 7u) == 7u && read_flag<kGroup>(stop_flag)) break;
+            hooks += unite_edge(edge_get(E, e), rank, P, nold, logb, logn, stopp, unions);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -506,7 +521,13 @@ __device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *log
             c.cyc_scan += static_cast<unsigned long long>(t_scan - t_chunk);
             c.cyc_link += static_cast<unsigned long long>(t_link - t_scan);
         }
-        if (kFaces && *reinterpret_cast<volatile uint32_t *>(&c.stop)) break;  // span(n) is decided
+        // span(n) is decided: stop.  In a group another CTA may raise the flag at any time, so the
+        // CTA decides together (one barrier with an OR) and leaves the loop as a whole.
+        if (kGroup) {
+            if (kFaces && __syncthreads_or(read_flag<kGroup>(stop_flag) != 0u)) break;
+        } else if (kFaces && read_flag<kGroup>(stop_flag)) {
+            break;
+        }
     }
     hooks = __reduce_add_sync(0xffffffffu, hooks);
     sites = __reduce_add_sync(0xffffffffu, sites);
@@ -772,6 +793,254 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// k_nstar_group: `members` co-resident CTAs (a cooperative launch) share one sample, for lattices
+// whose bitmap lives in global memory and batches too small to give every SM a sample of its own
+// (e.g. L = 40).  The group's union-find, undo log and bitmap are in its global slot; the CTAs
+// split the bitmap update, the chunks of new sites and the commit, and meet at group barriers.
+// Every wait is bounded: a barrier that is not reached within ~kSpinLimit polls sets
+// PERC_ETIMEOUT and an abort flag, and every CTA of the group returns.
+// ------------------------------------------------------------------------------------------------
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+struct GroupState {  // at the start of a group's slot (256 bytes)
+    uint32_t bar_count, bar_gen, abort, sample;
+    uint32_t stop, logn, pad[58];
+};
+static_assert(sizeof(GroupState) == 256, "group state is 256 bytes");
+
+// Returns false if the group aborted (a wait ran out); all threads of the CTA agree.
+__device__ __forceinline__ bool group_sync(GroupState *gs, uint32_t members, int *status, uint32_t *ok_s)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t ok = 1u;
+        const uint32_t gen = __ldcg(&gs->bar_gen);
+        __threadfence();
+        if (atomicAdd(&gs->bar_count, 1u) == members - 1u) {
+            atomicExch(&gs->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&gs->bar_gen, 1u);
+        } else {
+            uint32_t it = 0;
+            while (__ldcg(&gs->bar_gen) == gen) {
+                if (__ldcg(&gs->abort)) {
+                    ok = 0u;
+                    break;
+                }
+                if (++it > kSpinLimit) {
+                    set_status(status, PERC_ETIMEOUT);
+                    atomicExch(&gs->abort, 1u);
+                    ok = 0u;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *reinterpret_cast<volatile uint32_t *>(ok_s) = ok;
+    }
+    __syncthreads();
+    return *reinterpret_cast<volatile uint32_t *>(ok_s) != 0u;
+}
+
+__host__ __device__ inline size_t group_slot_bytes(uint64_t Ncap, uint32_t threads, uint32_t members)
+{
+    return sizeof(GroupState) + 2 * align256((Ncap + 2) * 4) + align256(size_t(bm_words(Ncap)) * 4) +
+           size_t(members) * align256(slot_edge_entries(threads) * sizeof(uint2));
+}
+
+__global__ void __launch_bounds__(1024, 1)
+k_nstar_group(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t members,
+              uint32_t edge_scap, const uint32_t *__restrict__ bracket, uint32_t *__restrict__ nstar_out,
+              uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    // shared memory: [row table][plane table (unused)][edge list]
+    RowEntry *rows = reinterpret_cast<RowEntry *>(dyn);
+    uint2 *sedges = reinterpret_cast<uint2 *>(dyn + smem_tables_bytes());
+    __shared__ Ctl c;
+    __shared__ uint32_t ok_s;
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+    const uint32_t group = blockIdx.x / members, member = blockIdx.x % members;
+    const bool leader = member == 0u;
+    const uint64_t Ncap = num_sites(max_L);
+    char *base = ws + sizeof(WsHeader) + size_t(group) * slot_bytes;
+    GroupState *gs = reinterpret_cast<GroupState *>(base);
+    const size_t nodes_b = align256((Ncap + 2) * 4), bm_b = align256(size_t(bm_words(Ncap)) * 4);
+    uint32_t *gP = reinterpret_cast<uint32_t *>(base + sizeof(GroupState));
+    uint32_t *logb = reinterpret_cast<uint32_t *>(base + sizeof(GroupState) + nodes_b);
+    uint32_t *bm = reinterpret_cast<uint32_t *>(base + sizeof(GroupState) + 2 * nodes_b);
+    uint2 *gedges = reinterpret_cast<uint2 *>(base + sizeof(GroupState) + 2 * nodes_b + bm_b +
+                                              size_t(member) * align256(slot_edge_entries(blockDim.x) * sizeof(uint2)));
+    const EdgeList E{sedges, edge_scap, gedges};
+    const Nodes P{gP, 0u, 0u};
+    const uint32_t gthreads = members * blockDim.x, gtid = member * blockDim.x + threadIdx.x;
+    unsigned long long tot_passes = 0, tot_probe = 0, tot_early = 0, tot_fb = 0, tot_ok = 0;
+    PhaseClock clk;
+    bool alive = true;
+
+    while (alive) {
+        if (threadIdx.x == 0) {
+            c.hooks = 0;
+            c.new_sites = 0;
+            c.sites = 0;
+            c.unions = 0;
+            c.cyc_scan = 0;
+            c.cyc_link = 0;
+            if (leader) atomicExch(&gs->sample, atomicAdd(&hdr->queue, 1u));
+        }
+        if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;
+        const long long t_setup = clock64();
+        const uint32_t s = __ldcg(&gs->sample);
+        if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;  // all have read it
+        if (s >= num) break;
+        const perc_sample smp = samples[s];
+        const uint32_t L = smp.L, mask = smp.zone_mask;
+        if (L < 1u || L > max_L || mask < 1u || mask > 127u || !smp.perm || !smp.rank) {
+            if (leader && threadIdx.x == 0) {
+                nstar_out[s] = PERC_NEVER;
+                if (passes_out) passes_out[s] = 0;
+                set_status(&hdr->status, PERC_EDEVICE);
+            }
+            continue;
+        }
+        const uint32_t N = static_cast<uint32_t>(num_sites(L));
+        const uint32_t words = bm_words(N);
+        for (uint32_t w = gtid; w < words; w += gthreads) __stcg(bm + w, 0u);
+        build_rows(mask, L, rows, reinterpret_cast<uint32_t *>(sedges), c);
+        if (leader && threadIdx.x == 0) {
+            nd_st(P, 0u, 0u);
+            nd_st(P, 1u, 1u);
+        }
+        const FastDiv fd = make_fastdiv(L);
+        if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;
+        clk.setup += clock64() - t_setup;
+
+        const uint32_t n_top = (L <= 2u) ? N + 1u : N;
+        uint32_t lo = 1, hi = n_top, nb = 0, bm_n = 0, npass = 0;
+        int stage = 2;
+        bool hi_known = true;
+        uint32_t blo = 0, bhi = 0;
+        if (bracket) {
+            blo = bracket[2 * size_t(s)];
+            bhi = bracket[2 * size_t(s) + 1];
+            if (blo >= 1u && blo <= bhi && bhi <= N) {
+                stage = blo > 1u ? 0 : 2;
+                lo = blo;
+                hi = bhi;
+                hi_known = false;
+            } else {
+                ++tot_fb;
+            }
+        }
+        for (;;) {
+            uint32_t mid;
+            if (stage == 0)
+                mid = blo - 1u;
+            else if (lo < hi)
+                mid = lo + (hi - lo) / 2u;
+            else if (!hi_known)
+                mid = hi;
+            else
+                break;
+            if (threadIdx.x == 0) {
+                c.ecount[0] = 0;
+                c.new_sites += mid - nb;
+                if (leader) {
+                    atomicExch(&gs->stop, 0u);
+                    atomicExch(&gs->logn, 0u);
+                }
+            }
+            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;
+            const long long t0 = clock64();
+            // bitmap of the first mid sites and fresh nodes for the new ones, split over the group
+            if (mid > bm_n) {
+                for (uint32_t r = bm_n + gtid; r < mid; r += gthreads) {
+                    const uint32_t i = __ldg(smp.perm + r) + kBmGuard;
+                    atomicOr(bm + (i >> 5), 1u << (i & 31u));
+                }
+            } else {
+                for (uint32_t r = mid + gtid; r < bm_n; r += gthreads) {
+                    const uint32_t i = __ldg(smp.perm + r) + kBmGuard;
+                    atomicAnd(bm + (i >> 5), ~(1u << (i & 31u)));
+                }
+            }
+            for (uint32_t r = nb + gtid; r < mid; r += gthreads) nd_st(P, r + 2u, r + 2u);
+            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;
+            const long long t1 = clock64();
+            union_pass<false, true, false, true>(c, P, logb, bm, rows, nullptr, E, smp.perm, smp.rank, L, fd, nb, mid,
+                                                 nb + 2u, &gs->stop, &gs->logn, member, members);
+            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;
+            const long long t2 = clock64();
+            const uint32_t span = nd_ld(P, 1u) != 1u;
+            const uint32_t logn = __ldcg(&gs->logn);
+            const bool stopped = __ldcg(&gs->stop) != 0u;
+            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;  // all have read span
+            for (uint32_t k = gtid; k < logn; k += gthreads) {
+                const uint32_t b = __ldcg(logb + k);
+                nd_st(P, b, span ? b : (nd_ld(P, b) & ~kTag));
+            }
+            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;
+            clk.update += t1 - t0;
+            clk.unite += t2 - t1;
+            clk.commit += clock64() - t2;
+            ++npass;
+            tot_probe += mid;
+            if (span && stopped) ++tot_early;
+            bm_n = mid;
+            if (!span) nb = mid;
+            if (stage == 0) {
+                if (span) {
+                    lo = 1; hi = n_top; nb = 0; hi_known = true; ++tot_fb;
+                }
+                stage = 2;
+            } else if (lo == hi) {
+                if (span) {
+                    hi_known = true;
+                } else {
+                    lo = 1; hi = n_top; nb = 0; hi_known = true; ++tot_fb;
+                }
+            } else if (span) {
+                hi = mid;
+                hi_known = true;
+            } else {
+                lo = mid + 1u;
+            }
+        }
+        if (!alive) break;
+        if (bracket && blo >= 1u && blo <= bhi && bhi <= N && lo >= blo && lo <= bhi && npass > 0) ++tot_ok;
+        if (threadIdx.x == 0) {
+            if (leader) {
+                nstar_out[s] = (lo == N + 1u) ? PERC_NEVER : lo;
+                if (passes_out) passes_out[s] = npass;
+                tot_passes += npass;
+            }
+            if (stats) {
+                atomicAdd(&stats->hooks, c.hooks);
+                if (leader) atomicAdd(&stats->new_sites, c.new_sites);
+                atomicAdd(&stats->sites_merged, c.sites);
+                atomicAdd(&stats->unions, c.unions);
+                atomicAdd(&stats->cyc_scan, c.cyc_scan);
+                atomicAdd(&stats->cyc_link, c.cyc_link);
+            }
+        }
+    }
+    if (threadIdx.x == 0 && stats) {
+        if (leader) {
+            atomicAdd(&stats->passes, tot_passes);
+            atomicAdd(&stats->probe_sites, tot_probe);
+            atomicAdd(&stats->early_exits, tot_early);
+            atomicAdd(&stats->fallbacks, tot_fb);
+            atomicAdd(&stats->verified, tot_ok);
+        }
+        atomicAdd(&stats->cyc_setup, clk.setup);
+        atomicAdd(&stats->cyc_update, clk.update);
+        atomicAdd(&stats->cyc_union, clk.unite);
+        atomicAdd(&stats->cyc_commit, clk.commit);
+    }
+}
+
 // S_max(n) per sample: one full pass over the first n sites, then cluster sizes by root counting.
 __global__ void __launch_bounds__(1024, 1)
 k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t node_cap,
@@ -861,6 +1130,7 @@ struct LaunchCfg {
     uint32_t node_cap = 0;
     uint32_t edge_scap = 0;
     uint32_t grid = 0;
+    uint32_t members = 1;  // CTAs per sample (> 1: the cooperative group kernel)
     size_t slot_bytes = 0;
 };
 
@@ -880,9 +1150,10 @@ static CfgCache g_cfg_cache[2][kCfgDevices];
 static std::mutex g_cfg_mutex;
 
 // Launch options set through perc_set_launch_option (0 = automatic).
-static int g_opt_threads = 0, g_opt_smem_nodes = -1, g_opt_max_ctas = 0;
+static int g_opt_threads = 0, g_opt_smem_nodes = -1, g_opt_max_ctas = 0, g_opt_group = 0;
+static CfgCache g_group_cache[kCfgDevices];
 
-static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
+static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool allow_group = true)
 {
     if (max_L < 1 || max_L > PERC_MAX_L || num == 0) return PERC_EINVAL;
     const uint64_t Ncap = num_sites(max_L);
@@ -944,6 +1215,58 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg)
     uint64_t grid = uint64_t(sms) * occ;
     const int cta_cap = env_int("PERC_MAX_CTAS", g_opt_max_ctas);
     if (cta_cap > 0 && uint64_t(cta_cap) < grid) grid = cta_cap;
+
+    // CTAs per sample: a batch of big lattices (bitmap in global memory) with fewer samples than
+    // SMs runs each sample on a cooperative group of CTAs; PERC_OPT_GROUP forces a size (1: never)
+    if (op == PERC_OP_NSTAR && allow_group) {
+        int members = env_int("PERC_GROUP", g_opt_group);
+        if (members == 0) {
+            members = 1;
+            if (max_L > cfg.smem_L)
+                while (members < 32 && uint64_t(members) * 2 * num <= grid) members *= 2;
+        }
+        if (members > 1) {
+            // the group kernel keeps no bitmap or nodes in shared memory: tables and edges only
+            const size_t gbase = smem_tables_bytes();
+            const size_t gshare = size_t(optin) - 1024;
+            cfg.members = static_cast<uint32_t>(members);
+            cfg.node_cap = 0;
+            cfg.edge_scap = static_cast<uint32_t>((gshare - gbase) / sizeof(uint2));
+            cfg.smem = gbase + size_t(cfg.edge_scap) * sizeof(uint2);
+            int gocc = 0;
+            {
+                std::lock_guard<std::mutex> lock(g_cfg_mutex);
+                CfgCache &cc = g_group_cache[dev < kCfgDevices ? dev : 0];
+                if (cc.valid && cc.threads == cfg.threads && cc.smem == cfg.smem) {
+                    gocc = cc.occ;
+                } else {
+                    if (cfg.smem > cc.attr_smem) {
+                        if (cudaFuncSetAttribute(k_nstar_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 int(cfg.smem)) != cudaSuccess)
+                            return PERC_ECUDA;
+                        cc.attr_smem = cfg.smem;
+                    }
+                    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gocc, k_nstar_group, cfg.threads, cfg.smem) !=
+                        cudaSuccess)
+                        return PERC_ECUDA;
+                    cc.threads = cfg.threads;
+                    cc.smem = cfg.smem;
+                    cc.occ = gocc;
+                    cc.valid = true;
+                }
+            }
+            uint64_t resident = uint64_t(sms) * gocc;  // a cooperative launch must be co-resident
+            if (cta_cap > 0 && uint64_t(cta_cap) < resident) resident = cta_cap;
+            uint64_t groups = resident / members;
+            if (groups < 1) return PERC_EINVAL;
+            if (groups > num) groups = num;
+            cfg.slot_bytes = group_slot_bytes(Ncap, cfg.threads, cfg.members);
+            const uint64_t mem_groups = kSlotCapBytes / cfg.slot_bytes;
+            if (groups > mem_groups) groups = mem_groups > 0 ? mem_groups : 1;
+            cfg.grid = static_cast<uint32_t>(groups * members);
+            return PERC_OK;
+        }
+    }
     if (grid > num) grid = num;
     const uint64_t mem_cap = kSlotCapBytes / cfg.slot_bytes;
     if (grid > mem_cap) grid = mem_cap > 0 ? mem_cap : 1;
@@ -978,6 +1301,22 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
     if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
+    if (cfg.members > 1) {
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(cfg.grid);
+        lc.blockDim = dim3(cfg.threads);
+        lc.dynamicSmemBytes = cfg.smem;
+        lc.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelEx(&lc, k_nstar_group, samples, num_samples, max_L, cfg.members,
+                                                 cfg.edge_scap, bracket, nstar, passes, stats,
+                                                 static_cast<char *>(workspace), cfg.slot_bytes);
+        return e == cudaSuccess ? PERC_OK : PERC_ECUDA;
+    }
     k_nstar<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap, cfg.edge_scap, bracket,
                                                          nstar, passes, stats, static_cast<char *>(workspace),
                                                          cfg.slot_bytes);
@@ -1013,6 +1352,10 @@ extern "C" int perc_set_launch_option(int option, int value)
     case PERC_OPT_MAX_CTAS:
         if (value < 0) return PERC_EINVAL;
         g_opt_max_ctas = value;
+        return PERC_OK;
+    case PERC_OPT_GROUP:
+        if (value < 0 || value > 64) return PERC_EINVAL;
+        g_opt_group = value;
         return PERC_OK;
     default:
         return PERC_EINVAL;
@@ -1073,7 +1416,7 @@ extern "C" int perc_nstar_noalloc(const perc_sample *samples, uint32_t num_sampl
 {
     if (!samples || !nstar || num_samples == 0) return PERC_EINVAL;
     LaunchCfg cfg;
-    int rc = launch_cfg(PERC_OP_NSTAR, max_L, num_samples, cfg);
+    int rc = launch_cfg(PERC_OP_NSTAR, max_L, num_samples, cfg, false);  // one CTA per sample here
     if (rc != PERC_OK) return rc;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return PERC_ECUDA;

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libperc.so")
 NEVER = 0xFFFFFFFF
 MAX_L = 73
 OP_RANK, OP_NSTAR, OP_MASS = 1, 2, 3
-OPT_THREADS, OPT_SMEM_NODES, OPT_MAX_CTAS = 1, 2, 3
+OPT_THREADS, OPT_SMEM_NODES, OPT_MAX_CTAS, OPT_GROUP = 1, 2, 3, 4
 MLP_NPARAM = 4931
 STATS_FIELDS = ("passes", "new_sites", "probe_sites", "hooks", "early_exits", "fallbacks",
                 "verified", "sites_merged", "unions", "cyc_setup", "cyc_update", "cyc_union",

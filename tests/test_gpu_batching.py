@@ -98,3 +98,29 @@ def test_learned_bracket_gains_passes_and_time():
     assert times[True] < 0.5 * times[False], times               # and much less time
     sel = np.arange(0, step.num, 97)
     assert np.array_equal(out[True][0][sel], orc_nstar(step.workload[sel]))
+
+
+@pytest.mark.parametrize("members", [2, 4, 16])
+def test_cooperative_groups_match_oracle(members):
+    # several CTAs per sample (forced here at small L; chosen automatically for big lattices)
+    from paper_2607_18991_b300 import autotune, driver, perc
+    w = np.concatenate([np.array([(L, m, s) for m in (1, 3, 42, 64, 127) for s in (1, 2)]) for L in (2, 5, 8, 16, 20)])
+    want = orc_nstar(w)
+    params = trained_params(8)
+    try:
+        perc.set_launch_option(perc.OPT_GROUP, members)
+        ns, passes = driver.nstar(w)
+        assert np.array_equal(ns, want)
+        ns_l, _ = driver.nstar(w, params=params, margin=0.05)
+        assert np.array_equal(ns_l, want)
+    finally:
+        perc.set_launch_option(perc.OPT_GROUP, 0)
+        autotune.reset()
+
+
+def test_automatic_groups_for_few_big_lattices():
+    from paper_2607_18991_b300 import driver, perc
+    w = np.array([(24, 127, 1), (24, 3, 2), (20, 64, 3)])
+    stats = perc.new_stats()
+    ns, _ = driver.nstar(w, stats=stats)
+    assert np.array_equal(ns, orc_nstar(w))
