@@ -1302,6 +1302,10 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
     if (cfg.members > 1) {
+        // every group's barrier counters, abort flag and shared scalars start at zero
+        if (cudaMemset2DAsync(static_cast<char *>(workspace) + sizeof(WsHeader), cfg.slot_bytes, 0, sizeof(GroupState),
+                              cfg.grid / cfg.members, stream) != cudaSuccess)
+            return PERC_ECUDA;
         cudaLaunchConfig_t lc = {};
         lc.gridDim = dim3(cfg.grid);
         lc.blockDim = dim3(cfg.threads);

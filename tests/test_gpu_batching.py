@@ -124,3 +124,24 @@ def test_automatic_groups_for_few_big_lattices():
     stats = perc.new_stats()
     ns, _ = driver.nstar(w, stats=stats)
     assert np.array_equal(ns, orc_nstar(w))
+
+
+def test_groups_on_a_dirty_workspace():
+    # the group barriers live in the workspace: a reused workspace full of stale bytes must not matter
+    import torch
+
+    from paper_2607_18991_b300 import driver, perc
+    w = np.array([(L, m, s) for L in (5, 16, 20) for m in (1, 127) for s in (1, 2, 3)])
+    want = orc_nstar(w)
+    ws = perc.Workspace()
+    try:
+        perc.set_launch_option(perc.OPT_GROUP, 2)
+        for fill in (0xFF, 0x01, 0x00):
+            p = driver.prepare(w, ws=ws)[0]
+            ws.get(perc.workspace_bytes(perc.OP_NSTAR, p.max_L, len(p.idx))).fill_(fill)
+            ns, _ = perc.nstar(p.samples, p.max_L, ws=ws)
+            assert np.array_equal(perc.u32(ns), want[p.idx]), fill
+            assert perc.check(ws) == 0
+    finally:
+        perc.set_launch_option(perc.OPT_GROUP, 0)
+    torch.cuda.synchronize()
