@@ -61,28 +61,34 @@ class Prepared:
 
 
 def prepare(workload, budget: int = DEFAULT_BUDGET, ws: perc.Workspace | None = None, stream=None):
+    """All chunks of a workload, prepared at once (for workloads whose orders fit in memory)."""
+    return list(iter_prepared(workload, budget, ws, stream))
+
+
+def iter_prepared(workload, budget: int = DEFAULT_BUDGET, ws: perc.Workspace | None = None, stream=None):
+    """Chunks one at a time: each chunk's site orders exist only while the caller holds it."""
     workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
     ws = ws or perc.default_workspace()
-    return [Prepared(workload, idx, ws, stream) for idx in _chunks(workload, budget)]
+    for idx in _chunks(workload, budget):
+        yield Prepared(workload, idx, ws, stream)
 
 
 def run_nstar(preps, num: int, params: torch.Tensor | None = None, margin: float = 0.0,
               stats: torch.Tensor | None = None, ws: perc.Workspace | None = None, stream=None):
-    """n* and passes (numpy uint32 [num]) for prepared chunks, in workload order."""
+    """n* and passes (numpy uint32 [num]) for prepared chunks (a list or a generator), in workload
+    order.  Each chunk's results are read back before the next chunk is prepared."""
     ws = ws or perc.default_workspace()
-    outs = []
+    nstar = np.zeros(num, dtype=np.uint32)
+    passes = np.zeros(num, dtype=np.uint32)
     for p in preps:
         br = perc.bracket(params, p.samples, margin, stream=stream) if params is not None else None
         ns, ps = perc.nstar(p.samples, p.max_L, bracket=br, stats=stats, ws=ws, stream=stream)
-        outs.append((p.idx, ns, ps))
-    nstar = np.zeros(num, dtype=np.uint32)
-    passes = np.zeros(num, dtype=np.uint32)
-    for idx, ns, ps in outs:
-        nstar[idx] = perc.u32(ns)
-        passes[idx] = perc.u32(ps)
-    rc = perc.check(ws, stream)
-    if rc != 0:
-        raise perc.PercError(rc, "perc_nstar device status")
+        nstar[p.idx] = perc.u32(ns)
+        passes[p.idx] = perc.u32(ps)
+        rc = perc.check(ws, stream)
+        if rc != 0:
+            raise perc.PercError(rc, "perc_nstar device status")
+        del p
     return nstar, passes
 
 
@@ -90,8 +96,7 @@ def nstar(workload, params: torch.Tensor | None = None, margin: float = 0.0, sta
           budget: int = DEFAULT_BUDGET):
     """Exact n* for every (L, mask, seed) row of `workload`; returns (nstar, passes)."""
     workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
-    preps = prepare(workload, budget)
-    return run_nstar(preps, len(workload), params, margin, stats)
+    return run_nstar(iter_prepared(workload, budget), len(workload), params, margin, stats)
 
 
 def mass(workload, n, budget: int = DEFAULT_BUDGET):
@@ -100,12 +105,13 @@ def mass(workload, n, budget: int = DEFAULT_BUDGET):
     n = np.asarray(n, dtype=np.int64).reshape(-1)
     ws = perc.default_workspace()
     out = np.zeros(len(workload), dtype=np.int64)
-    for p in prepare(workload, budget, ws):
+    for p in iter_prepared(workload, budget, ws):
         m = perc.mass(p.samples, p.max_L, torch.as_tensor(n[p.idx]), ws=ws)
         out[p.idx] = m.cpu().numpy()
-    rc = perc.check(ws)
-    if rc != 0:
-        raise perc.PercError(rc, "perc_mass device status")
+        rc = perc.check(ws)
+        if rc != 0:
+            raise perc.PercError(rc, "perc_mass device status")
+        del p
     return out
 
 
