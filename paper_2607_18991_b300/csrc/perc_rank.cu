@@ -12,6 +12,7 @@
 // and the last scatter also writes rank[perm[r]] = r.  Seeds are sorted in chunks that fit the
 // workspace.
 #include <cstdio>
+#include <cstdlib>
 
 #include "perc_common.cuh"
 
@@ -23,6 +24,12 @@ constexpr int kRankItems = 8;
 constexpr int kRankTile = kRankThreads * kRankItems;  // 4096 keys per tile
 constexpr int kRankMaxChunk = 64;                     // seeds per chunk (upper bound)
 constexpr size_t kRankChunkBytes = size_t(4) << 30;   // workspace aimed at per chunk
+
+static inline int env_int_rank(const char *name, int dflt)
+{
+    const char *v = getenv(name);
+    return v ? atoi(v) : dflt;
+}
 
 static inline uint32_t rank_tiles(uint64_t N) { return static_cast<uint32_t>((N + kRankTile - 1) / kRankTile); }
 
@@ -242,6 +249,201 @@ k_rank_scatter(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ se
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Persistent scatter for passes 1..3 with bulk-async tile loads.  Each CTA walks the (seed, tile)
+// work list; while it ranks and writes one tile, the copy engine (cp.async.bulk, completion on an
+// mbarrier) already brings the next tile's keys and values into the other shared buffer.  The
+// buffer just ranked also serves as the staging area of the digit-ordered tile.  Needs 16-byte
+// aligned rows (L^5 a multiple of 4); otherwise k_rank_scatter is used.  Waits are bounded: a copy
+// that does not land within kTmaSpinLimit polls sets PERC_ETIMEOUT in the workspace status word
+// and the CTA stops.
+// ------------------------------------------------------------------------------------------------
+constexpr uint32_t kTmaSpinLimit = 1u << 26;
+
+struct TmaScatterSmem {
+    uint32_t key[2][kRankTile];
+    uint32_t val[2][kRankTile];
+    uint32_t wcnt[kRankWarps][256];
+    uint32_t tstart[256];
+    uint32_t goff[256];
+    unsigned long long bar[2];
+    uint32_t stop;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < kTmaSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kRankThreads, 2)
+k_rank_scatter_tma(int pass, uint32_t N, uint32_t T, uint32_t S, const uint32_t *__restrict__ kin,
+                   const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                   uint32_t *__restrict__ rank_out, const uint32_t *__restrict__ hist, int *status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TmaScatterSmem &S_ = *reinterpret_cast<TmaScatterSmem *>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t total = T * S;
+    const uint32_t shift = 8u * pass;
+    const bool last = pass == 3;
+    const uint32_t lanes_below = (1u << lane) - 1u;
+
+    auto issue = [&](uint32_t w, int b) {  // thread 0: bring work item w into buffer b
+        const uint32_t s = w / T, tile = w % T;
+        const uint32_t n = min(static_cast<uint32_t>(kRankTile), N - tile * kRankTile);
+        const size_t off = size_t(s) * N + size_t(tile) * kRankTile;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&S_.bar[b], 2u * n * 4u);
+        bulk_load(S_.key[b], kin + off, n * 4u, &S_.bar[b]);
+        bulk_load(S_.val[b], vin + off, n * 4u, &S_.bar[b]);
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&S_.bar[0], 1u);
+        mbar_init(&S_.bar[1], 1u);
+        S_.stop = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t w = blockIdx.x;
+    if (threadIdx.x == 0 && w < total) issue(w, 0);
+    uint32_t use[2] = {0u, 0u};
+    for (int it = 0; w < total; w += gridDim.x, ++it) {
+        const int b = it & 1;
+        const uint32_t s = w / T, tile = w % T;
+        const uint32_t tile_n = min(static_cast<uint32_t>(kRankTile), N - tile * kRankTile);
+        const size_t row = size_t(s) * N;
+        for (int d = threadIdx.x; d < kRankWarps * 256; d += kRankThreads) (&S_.wcnt[0][0])[d] = 0u;
+        if (threadIdx.x < 256) S_.goff[threadIdx.x] = hist[(size_t(s) * 256 + threadIdx.x) * T + tile];
+        // the other buffer was released by the barrier that ended the previous iteration
+        const bool next = w + gridDim.x < total;
+        if (threadIdx.x == 0 && next) issue(w + gridDim.x, b ^ 1);
+        if (!mbar_wait(&S_.bar[b], use[b] & 1u)) {
+            set_status(status, PERC_ETIMEOUT);
+            S_.stop = 1u;
+        }
+        ++use[b];
+        __syncthreads();
+        if (S_.stop) {
+            // let the copy already issued into the other buffer land before the CTA goes away
+            if (threadIdx.x == 0 && next) mbar_wait(&S_.bar[b ^ 1], use[b ^ 1] & 1u);
+            __syncthreads();
+            break;
+        }
+        uint32_t key[kRankItems], val[kRankItems], pos[kRankItems], dig[kRankItems];
+#pragma unroll
+        for (int k = 0; k < kRankItems; ++k) {
+            const uint32_t e = warp * (32 * kRankItems) + k * 32 + lane;  // element inside the tile
+            const bool valid = e < tile_n;
+            const uint32_t kk = valid ? S_.key[b][e] : 0u;
+            const uint32_t vv = valid ? S_.val[b][e] : 0u;
+            const uint32_t d = valid ? ((kk >> shift) & 255u) : 256u;
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+            if (!valid) peers = ~peers;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const uint32_t bb = __ballot_sync(0xffffffffu, (d >> q) & 1u);
+                peers &= ((d >> q) & 1u) ? bb : ~bb;
+            }
+            const uint32_t leader = __ffs(peers) - 1;
+            const uint32_t base = valid ? S_.wcnt[warp][d] : 0u;
+            __syncwarp();
+            if (valid && lane == static_cast<int>(leader)) S_.wcnt[warp][d] = base + __popc(peers);
+            __syncwarp();
+            key[k] = kk;
+            val[k] = vv;
+            pos[k] = base + __popc(peers & lanes_below);
+            dig[k] = d;
+        }
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            const uint32_t d = threadIdx.x;
+            uint32_t run = 0;
+#pragma unroll 4
+            for (int ww = 0; ww < kRankWarps; ++ww) {
+                const uint32_t cnt = S_.wcnt[ww][d];
+                S_.wcnt[ww][d] = run;
+                run += cnt;
+            }
+            S_.tstart[d] = run;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            uint32_t v[8], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                v[q] = S_.tstart[lane * 8 + q];
+                sum += v[q];
+            }
+            uint32_t x = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            uint32_t run = x - sum;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                S_.tstart[lane * 8 + q] = run;
+                run += v[q];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kRankItems; ++k) {  // stage in digit order, in the buffer just read
+            const uint32_t d = dig[k];
+            if (d < 256u) {
+                const uint32_t lp = S_.tstart[d] + S_.wcnt[warp][d] + pos[k];
+                S_.key[b][lp] = key[k];
+                S_.val[b][lp] = val[k];
+            }
+        }
+        __syncthreads();
+        for (uint32_t lp = threadIdx.x; lp < tile_n; lp += kRankThreads) {
+            const uint32_t kk = S_.key[b][lp];
+            const uint32_t d = (kk >> shift) & 255u;
+            const uint32_t dst = S_.goff[d] + (lp - S_.tstart[d]);
+            const uint32_t vv = S_.val[b][lp];
+            vout[row + dst] = vv;
+            if (last)
+                rank_out[row + vv] = dst;
+            else
+                kout[row + dst] = kk;
+        }
+        __syncthreads();  // buffer b is free for the copy issued in the next iteration
+    }
+    // every copy a CTA issues is for a work item it consumes, so none is in flight at exit
+}
+
 }  // namespace perc
 
 using namespace perc;
@@ -262,12 +464,27 @@ extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, 
     uint32_t *hist = a_vals + size_t(chunk) * N;
 
     static bool attr_set = false;
+    static uint32_t tma_ctas = 0;
     if (!attr_set) {
         if (cudaFuncSetAttribute(k_rank_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(sizeof(ScatterSmem))) != cudaSuccess)
             return PERC_ECUDA;
+        if (cudaFuncSetAttribute(k_rank_scatter_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(sizeof(TmaScatterSmem))) != cudaSuccess)
+            return PERC_ECUDA;
+        int dev = 0, sms = 0, occ = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rank_scatter_tma, kRankThreads,
+                                                          sizeof(TmaScatterSmem)) != cudaSuccess)
+            return PERC_ECUDA;
+        tma_ctas = static_cast<uint32_t>(sms * (occ > 0 ? occ : 1));
         attr_set = true;
     }
+    // bulk-async tile loads need 16-byte aligned rows; the status word is the workspace header
+    const bool use_tma = (N % 4u) == 0u && env_int_rank("PERC_RANK_TMA", 1) != 0;
+    int *status = static_cast<int *>(workspace);
+    if (cudaMemsetAsync(workspace, 0, 256, stream) != cudaSuccess) return PERC_ECUDA;
     for (uint32_t s0 = 0; s0 < num_seeds; s0 += chunk) {
         const uint32_t S = min(chunk, num_seeds - s0);
         const uint64_t *sd = seeds + s0;
@@ -282,8 +499,15 @@ extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, 
             uint32_t *vout = (pass == 0 || pass == 2) ? a_vals : b_vals;
             k_rank_hist<<<grid, kRankThreads, 0, stream>>>(pass, uint32_t(N), T, sd, kin, hist);
             k_rank_scan<<<S, 1024, 0, stream>>>(T, hist);
-            k_rank_scatter<<<grid, kRankThreads, sizeof(ScatterSmem), stream>>>(pass, uint32_t(N), T, sd, kin, vin, kout,
-                                                                                vout, b_keys, hist);
+            if (pass > 0 && use_tma) {
+                const uint32_t work = T * S;
+                const uint32_t g = work < tma_ctas ? work : tma_ctas;
+                k_rank_scatter_tma<<<g, kRankThreads, sizeof(TmaScatterSmem), stream>>>(
+                    pass, uint32_t(N), T, S, kin, vin, kout, vout, b_keys, hist, status);
+            } else {
+                k_rank_scatter<<<grid, kRankThreads, sizeof(ScatterSmem), stream>>>(pass, uint32_t(N), T, sd, kin, vin,
+                                                                                    kout, vout, b_keys, hist);
+            }
         }
     }
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
