@@ -295,20 +295,6 @@ __device__ __forceinline__ uint2 edge_get(const EdgeList &E, uint32_t k)
     return k < E.scap ? E.s[k] : E.g[k - E.scap];
 }
 
-__device__ __forceinline__ uint32_t unite_edge(uint2 e, const uint32_t *rank, const Nodes &P, uint32_t nold,
-                                               uint32_t *logb, uint32_t *logn, uint32_t *stop, uint32_t &unions)
-{
-    uint32_t other;
-    if (e.y & kNodeFlag) {
-        other = e.y & ~kNodeFlag;
-    } else {
-        other = __ldg(rank + e.y) + 2u;
-        if (other >= e.x) return 0u;  // the neighbor came later: it merges this edge itself
-    }
-    ++unions;
-    return uf_unite(P, e.x, other, nold, logb, logn, stop) ? 1u : 0u;
-}
-
 // log2 of the threads that share one site in a chunk of `count` sites: one site per thread when
 // there are enough sites, otherwise the neighborhood of a site is split over threads.
 __device__ __forceinline__ uint32_t lanes_shift(uint32_t count, uint32_t R)
@@ -511,9 +497,25 @@ __device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *log
         // ---- unite
         const uint32_t ne = *ecount;
         if (threadIdx.x == 0) c.ecount[parity ^ 1u] = 0u;  // the next chunk's counter
-        for (uint32_t e = threadIdx.x, it = 0; e < ne; e += blockDim.x, ++it) {
-            if (kFaces && (it & 7u) == 7u && read_flag<kGroup>(stop_flag)) break;
-            hooks += unite_edge(edge_get(E, e), rank, P, nold, logb, logn, stopp, unions);
+        // four edges a round: their rank lookups are issued together, then the unions follow
+        for (uint32_t e0 = threadIdx.x; e0 < ne; e0 += 4u * blockDim.x) {
+            if (kFaces && read_flag<kGroup>(stop_flag)) break;
+            uint2 ed[4];
+            uint32_t other[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t e = e0 + q * blockDim.x;
+                ed[q] = e < ne ? edge_get(E, e) : make_uint2(0u, 0u);
+                other[q] = (e < ne && !(ed[q].y & kNodeFlag)) ? __ldg(rank + ed[q].y) + 2u : (ed[q].y & ~kNodeFlag);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t e = e0 + q * blockDim.x;
+                if (e >= ne) continue;
+                if (!(ed[q].y & kNodeFlag) && other[q] >= ed[q].x) continue;  // the later site merges it
+                ++unions;
+                hooks += uf_unite(P, ed[q].x, other[q], nold, logb, logn, stopp) ? 1u : 0u;
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -610,7 +612,7 @@ template <bool kSmemBm>
 __device__ __forceinline__ uint32_t probe(Ctl &c, const Nodes &P, uint32_t *logb, uint32_t *bm,
                                           const SmemPtrs &sm, const EdgeList &E, const uint32_t *perm,
                                           const uint32_t *rank,
-                                          uint32_t L, const FastDiv &fd, PhaseClock &clk)
+                                          uint32_t L, const FastDiv &fd, PhaseClock &clk, bool &stopped)
 {
     const uint32_t mid = c.mid, nb = c.nb, bm_n = c.bm_n;
     if (kSmemBm) bm = sm.sbm;  // keep the shared-memory address space visible to the compiler
@@ -619,16 +621,17 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, const Nodes &P, uint32_t *logb
     for (uint32_t r = nb + threadIdx.x; r < mid; r += blockDim.x) nd_st(P, r + 2u, r + 2u);
     __syncthreads();
     const long long t1 = clock64();
+    // (the chunk loop of the union pass ends with a block barrier, mid > nb gives at least one chunk)
     if (kSmemBm && L == kPlaneL)
         union_pass<true, true, true>(c, P, logb, sm.sbm, sm.rows, sm.planes, E, perm, rank, L, fd, nb, mid, nb + 2u);
     else
         union_pass<kSmemBm, true, false>(c, P, logb, bm, sm.rows, sm.planes, E, perm, rank, L, fd, nb, mid, nb + 2u);
-    __syncthreads();
     const long long t2 = clock64();
     clk.update += t1 - t0;
     clk.unite += t2 - t1;
     const uint32_t span = nd_ld(P, 1u) != 1u;
     const uint32_t logn = c.logn;
+    stopped = c.stop != 0u;
     __syncthreads();  // every thread has read span before node 1 may be reset below
     for (uint32_t k = threadIdx.x; k < logn; k += blockDim.x) {
         const uint32_t b = logb[k];
@@ -738,11 +741,12 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
                 c.new_sites += mid - nb;
             }
             __syncthreads();
-            const uint32_t span = smem_bm ? probe<true>(c, P, logb, bm, sm, E, smp.perm, smp.rank, L, fd, clk)
-                                          : probe<false>(c, P, logb, bm, sm, E, smp.perm, smp.rank, L, fd, clk);
+            bool stopped = false;
+            const uint32_t span = smem_bm ? probe<true>(c, P, logb, bm, sm, E, smp.perm, smp.rank, L, fd, clk, stopped)
+                                          : probe<false>(c, P, logb, bm, sm, E, smp.perm, smp.rank, L, fd, clk, stopped);
             ++npass;
             tot_probe += mid;
-            if (span && c.stop) ++tot_early;
+            if (span && stopped) ++tot_early;
             bm_n = mid;
             if (!span) nb = mid;
             if (stage == 0) {
@@ -762,7 +766,8 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
             } else {
                 lo = mid + 1u;
             }
-            __syncthreads();  // c.stop / c.logn are rewritten by thread 0 next round
+            // no barrier here: after the probe's last barrier no thread reads the Ctl fields that
+            // thread 0 rewrites for the next probe before that probe's first barrier
         }
         if (bracket && blo >= 1u && blo <= bhi && bhi <= N && lo >= blo && lo <= bhi && npass > 0) ++tot_ok;
         if (threadIdx.x == 0) {
