@@ -15,7 +15,9 @@ Contents and the passages they follow:
   x1 = L-1) and S_max(n) (eq. Pmax).
 * ``bfs`` and ``minimax_nstar`` -- independent brute-force cross-checks (flood fill at fixed n;
   bottleneck-path identity) used only to pin ``nz``.
-* ``binomial_convolve`` -- S_max(n) -> S_max(p) (Methods, "Computational methods").
+* ``smax_prefix`` -- the same sweep stopped after n_stop sites: S_max(n) for n = 0..n_stop.
+* ``binomial_weights`` / ``binomial_convolve`` / ``pmax`` -- S_max(n) -> S_max(p) (Methods,
+  "Computational methods") and P_max(p) = S_max(p) / L^5 (eq. Pmax).
 * ``oracle.mlp`` -- FP64 numpy forward/backward/Adam of the bracket network.
 
 The C part is compiled on first use with gcc into ``oracle/liboracle.so`` (``build()``).
@@ -67,6 +69,10 @@ def lib():
         L.orc_bfs.restype = i32
         L.orc_minimax_nstar.argtypes = [u32, u32, P(u32)]
         L.orc_minimax_nstar.restype = u32
+        L.orc_smax_prefix.argtypes = [u32, u32, P(u32), P(u32), u64, P(i64)]
+        L.orc_smax_prefix.restype = i32
+        L.orc_binomial_weights.argtypes = [u64, ctypes.c_double, P(ctypes.c_double)]
+        L.orc_binomial_weights.restype = i32
         L.orc_binomial_convolve.argtypes = [u64, P(ctypes.c_double), ctypes.c_double]
         L.orc_binomial_convolve.restype = ctypes.c_double
         _lib = L
@@ -144,6 +150,17 @@ def nz(L: int, mask: int, perm: np.ndarray, rk: np.ndarray, nq=(), smax_all: boo
     return nstar.value, smax_at, all_arr
 
 
+def smax_prefix(L: int, mask: int, perm: np.ndarray, rk: np.ndarray, n_stop: int) -> np.ndarray:
+    """S_max(n) for n = 0..n_stop (int64[n_stop + 1]) from the sweep stopped after n_stop sites."""
+    out = np.zeros(n_stop + 1, dtype=np.int64)
+    perm = np.ascontiguousarray(perm, dtype=np.uint32)
+    rk = np.ascontiguousarray(rk, dtype=np.uint32)
+    if lib().orc_smax_prefix(L, mask, _ptr(perm, ctypes.c_uint32), _ptr(rk, ctypes.c_uint32), n_stop,
+                             _ptr(out, ctypes.c_int64)) != 0:
+        raise ValueError(f"orc_smax_prefix failed for L={L} mask={mask} n_stop={n_stop}")
+    return out
+
+
 def bfs(L: int, mask: int, rk: np.ndarray, n: int) -> tuple[bool, int]:
     """Flood fill of the sites with rank < n: (some cluster spans x1, S_max)."""
     sp = ctypes.c_int()
@@ -164,6 +181,21 @@ def binomial_convolve(q_of_n: np.ndarray, p: float) -> float:
     """sum_n C(N,n) p^n (1-p)^(N-n) q(n) for q given at n = 0..N."""
     q = np.ascontiguousarray(q_of_n, dtype=np.float64)
     return float(lib().orc_binomial_convolve(len(q) - 1, _ptr(q, ctypes.c_double), p))
+
+
+def binomial_weights(N: int, p: float) -> np.ndarray:
+    """B(N, n, p) for n = 0..N (float64[N + 1]), built by the ratio recursion and normalised."""
+    w = np.zeros(N + 1, dtype=np.float64)
+    if lib().orc_binomial_weights(N, p, _ptr(w, ctypes.c_double)) != 0:
+        raise ValueError(f"orc_binomial_weights failed for N={N} p={p}")
+    return w
+
+
+def pmax(smax_all: np.ndarray, L: int, p: float) -> float:
+    """P_max(p) = S_max(p) / L^5 from S_max(n), n = 0..N (eq. Pmax with the binomial convolution)."""
+    N = num_sites(L)
+    assert len(smax_all) == N + 1
+    return binomial_convolve(np.asarray(smax_all, dtype=np.float64), p) / N
 
 
 def nstar_batch(L: int, seeds, masks) -> np.ndarray:

@@ -203,20 +203,21 @@ static uint32_t orc_find(uint32_t *parent, uint32_t a)
 }
 
 /*
- * Runs the sweep for one (L, mask) on a given order.  Outputs:
- *   *nstar_out            first spanning n (ORC_NEVER if none);
- *   smax_at[q]            S_max after nq[q] sites (nq[q] in [0, N]); nq may be NULL when nnq = 0;
- *   smax_all (optional)   S_max(n) for n = 0..N (N+1 entries), NULL to skip.
+ * Runs the sweep for one (L, mask) on a given order over the first n_limit sites (n_limit <= N).
+ * Outputs:
+ *   *nstar_out            first spanning n <= n_limit (ORC_NEVER if none);
+ *   smax_at[q]            S_max after nq[q] sites (nq[q] in [0, n_limit]); nq may be NULL when nnq = 0;
+ *   smax_all (optional)   S_max(n) for n = 0..n_limit (n_limit+1 entries), NULL to skip.
  * Returns 0, or -1 on bad input / no memory.
  */
-int orc_nz(uint32_t L, uint32_t mask, const uint32_t *perm, const uint32_t *rank,
-           const uint64_t *nq, uint32_t nnq, int64_t *smax_at, uint32_t *nstar_out,
-           int64_t *smax_all)
+static int orc_sweep(uint32_t L, uint32_t mask, const uint32_t *perm, const uint32_t *rank,
+                     const uint64_t *nq, uint32_t nnq, int64_t *smax_at, uint32_t *nstar_out,
+                     int64_t *smax_all, uint64_t n_limit)
 {
     uint64_t N = orc_num_sites(L);
-    if (L == 0 || N >= 0xFFFFFFFFull || mask < 1 || mask > 127) return -1;
+    if (L == 0 || N >= 0xFFFFFFFFull || mask < 1 || mask > 127 || n_limit > N) return -1;
     for (uint32_t q = 0; q < nnq; ++q)
-        if (nq[q] > N) return -1;
+        if (nq[q] > n_limit) return -1;
 
     int8_t offs[892 * 5];
     int z = orc_mask_offsets((int)mask, offs);
@@ -238,7 +239,7 @@ int orc_nz(uint32_t L, uint32_t mask, const uint32_t *perm, const uint32_t *rank
     }
     if (smax_all) smax_all[0] = 0;
 
-    for (uint64_t r = 0; r < N; ++r) {
+    for (uint64_t r = 0; r < n_limit; ++r) {
         uint32_t i = perm[r];
         int x[5];
         orc_coords(L, i, x);
@@ -267,6 +268,23 @@ int orc_nz(uint32_t L, uint32_t mask, const uint32_t *perm, const uint32_t *rank
     *nstar_out = nstar;
     free(parent); free(size); free(flags);
     return 0;
+}
+
+/* The whole sweep (n = 0..N); arguments as orc_sweep with n_limit = N. */
+int orc_nz(uint32_t L, uint32_t mask, const uint32_t *perm, const uint32_t *rank,
+           const uint64_t *nq, uint32_t nnq, int64_t *smax_at, uint32_t *nstar_out,
+           int64_t *smax_all)
+{
+    return orc_sweep(L, mask, perm, rank, nq, nnq, smax_at, nstar_out, smax_all, orc_num_sites(L));
+}
+
+/* S_max(n) for n = 0..n_stop (n_stop + 1 entries): the sweep stopped after n_stop sites. */
+int orc_smax_prefix(uint32_t L, uint32_t mask, const uint32_t *perm, const uint32_t *rank,
+                    uint64_t n_stop, int64_t *smax_prefix)
+{
+    uint32_t nstar;
+    if (!smax_prefix) return -1;
+    return orc_sweep(L, mask, perm, rank, NULL, 0, NULL, &nstar, smax_prefix, n_stop);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -410,13 +428,14 @@ uint32_t orc_minimax_nstar(uint32_t L, uint32_t mask, const uint32_t *rank)
 /* canonical S_max(n), n = 0..N, becomes S_max(p) = sum_n B(N,n,p) S_max(n), with               */
 /* B(N,n,p) = C(N,n) p^n (1-p)^(N-n).  The weights are built outward from the mode n0 with the  */
 /* ratio B(n+1)/B(n) = (N-n)/(n+1) * p/(1-p), then normalised, which never forms C(N,n) itself.  */
+/* orc_binomial_weights writes the normalised B(N,n,p), n = 0..N; returns -1 for p outside [0,1]. */
 /* ------------------------------------------------------------------------------------------ */
-double orc_binomial_convolve(uint64_t N, const double *q_of_n, double p)
+int orc_binomial_weights(uint64_t N, double p, double *w)
 {
-    if (p <= 0.0) return q_of_n[0];
-    if (p >= 1.0) return q_of_n[N];
-    double *w = (double *)malloc(sizeof(double) * (size_t)(N + 1));
-    if (!w) return NAN;
+    if (!w || !(p >= 0.0 && p <= 1.0)) return -1;
+    for (uint64_t n = 0; n <= N; ++n) w[n] = 0.0;
+    if (p == 0.0) { w[0] = 1.0; return 0; }
+    if (p == 1.0) { w[N] = 1.0; return 0; }
     uint64_t n0 = (uint64_t)floor(p * (double)N);
     if (n0 > N) n0 = N;
     double ratio = p / (1.0 - p);
@@ -425,11 +444,20 @@ double orc_binomial_convolve(uint64_t N, const double *q_of_n, double p)
         w[n + 1] = w[n] * ((double)(N - n) / (double)(n + 1)) * ratio;
     for (uint64_t n = n0; n > 0; --n)
         w[n - 1] = w[n] * ((double)n / (double)(N - n + 1)) / ratio;
-    double norm = 0.0, acc = 0.0;
-    for (uint64_t n = 0; n <= N; ++n) {
-        norm += w[n];
-        acc += w[n] * q_of_n[n];
-    }
+    double norm = 0.0;
+    for (uint64_t n = 0; n <= N; ++n) norm += w[n];
+    for (uint64_t n = 0; n <= N; ++n) w[n] /= norm;
+    return 0;
+}
+
+double orc_binomial_convolve(uint64_t N, const double *q_of_n, double p)
+{
+    if (p <= 0.0) return q_of_n[0];
+    if (p >= 1.0) return q_of_n[N];
+    double *w = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    if (!w || orc_binomial_weights(N, p, w) != 0) { free(w); return NAN; }
+    double acc = 0.0;
+    for (uint64_t n = 0; n <= N; ++n) acc += w[n] * q_of_n[n];
     free(w);
-    return acc / norm;
+    return acc;
 }
