@@ -11,6 +11,10 @@ from pinned host buffers with the host<->device copies inside the timed region.
 
 Under torchrun every rank runs its own seed block (weak scaling, no collective on the data path);
 rank 0 prints one JSON line.  `--impl reference` times the CPU oracle on the same workload.
+
+`--workload pmax` measures the P_max(p) path instead: one step = perc_rank of the seeds, the
+binomial weights of 16 probabilities per neighborhood (p_c of Table I, +-2%), S_max(n) over the
++-12-deviation window of n of every sample, and the convolution to P_max(p) (eq. Pmax).
 """
 from __future__ import annotations
 
@@ -32,6 +36,8 @@ L = 16
 NUM_SEEDS = 256
 MASKS = list(range(1, 128))
 METRIC = "samples/sec (exact n*) at L=16 over 127 neighborhoods, learned vs plain bracket"
+PMAX_METRIC = ("samples/sec of P_max(p) curves (exact S_max(n) over +-12-deviation windows, binomial "
+               "convolution at 16 p per neighborhood) at L=16 over 127 neighborhoods")
 
 
 def dist_env():
@@ -58,12 +64,29 @@ def _oracle_seed(seed: int) -> int:
     return len(MASKS)
 
 
-def oracle_rate(seeds, workers: int):
+def _oracle_pmax_seed(seed: int) -> int:
+    """P_max(p) of every neighborhood for one seed with the oracle: its sweep stopped at the end of
+    the GPU's window of n, its binomial weights over all n, and their product."""
+    import oracle
+    from paper_2607_18991_b300 import workloads
+    N = L ** 5
+    perm, rk = oracle.rank(L, seed)
+    for m in MASKS:
+        ps = workloads.pmax_grid(m)
+        n_stop = int(min(N, math.ceil(N * ps.max() + 12.0 * math.sqrt(N * ps.max() * (1 - ps.max())))))
+        pre = oracle.smax_prefix(L, m, perm, rk, n_stop).astype(np.float64)
+        for q in ps:
+            w = oracle.binomial_weights(N, float(q))
+            float(np.dot(w[: n_stop + 1], pre)) / N
+    return len(MASKS)
+
+
+def oracle_rate(seeds, workers: int, fn=_oracle_seed):
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(workers) as pool:
-        done = sum(pool.map(_oracle_seed, list(seeds)))
+        done = sum(pool.map(fn, list(seeds)))
     dt = time.perf_counter() - t0
     return done / dt, done, dt
 
@@ -421,6 +444,224 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------------------------------------------
+# our arm, P_max(p) workload
+# ------------------------------------------------------------------------------------------------
+def run_pmax_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    cpu_workers = max(1, min(host_cores(), 32))
+
+    from paper_2607_18991_b300 import build as pbuild
+    from paper_2607_18991_b300 import driver, perc, workloads
+
+    pbuild.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    seeds, _ = workload_for(rank, args.num_seeds)
+    st = driver.PmaxStep(L, MASKS, seeds, {m: workloads.pmax_grid(m) for m in MASKS})
+    num, N = st.num, L ** 5
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    lib = perc.lib()
+    sp = stream.cuda_stream
+
+    def step(ev=None):
+        st.run_rank()
+        if ev is not None:
+            ev[0].record(stream)
+        st.run_weights()
+        if ev is not None:
+            ev[1].record(stream)
+        st.run_smax()
+        if ev is not None:
+            ev[2].record(stream)
+        st.run_pmax()
+        if ev is not None:
+            ev[3].record(stream)
+
+    step()
+    torch.cuda.synchronize()
+    graph = st.capture() if args.graph else None
+
+    def timed(K: int, W: int):
+        for _ in range(W):
+            step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        tot = [0.0] * 5
+        for _ in range(K):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            e[4].record(stream)
+            step(e)
+            torch.cuda.synchronize()
+            tot[0] += e[4].elapsed_time(e[3])
+            tot[1] += e[4].elapsed_time(e[0])
+            tot[2] += e[0].elapsed_time(e[1])
+            tot[3] += e[1].elapsed_time(e[2])
+            tot[4] += e[2].elapsed_time(e[3])
+        torch.cuda.profiler.stop()
+        return [t / K for t in tot]
+
+    def timed_graph(K: int, W: int):
+        for _ in range(W):
+            graph.replay()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(K):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            a.record(stream)
+            graph.replay()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / K
+
+    if args.ncu_case:
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"ncu_case": True, "workload": "pmax", "samples": num, "seeds": int(len(seeds))}))
+        return
+
+    gpu_index = torch.cuda.current_device()
+    phys = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    smi_index = int(phys[gpu_index]) if phys and phys[0].strip().isdigit() else gpu_index
+    with ClockSampler(smi_index) as clk:
+        ms_step, ms_rank, ms_weights, ms_smax, ms_pmax = timed(args.steps, args.warmup)
+        ms_graph = timed_graph(args.steps, args.warmup) if graph is not None else None
+    clocks = clk.summary()
+    ms_eager = ms_step
+    if ms_graph is not None:
+        ms_step = min(ms_step, ms_graph)
+
+    # a summary of the result: mean P_max curve of a few neighborhoods over the seeds
+    pm = st.pmax.cpu().numpy()
+    curves = {}
+    for m in (1, 3, 7, 127):
+        rows = st.workload[:, 1] == m
+        curves[str(m)] = {"p": workloads.pmax_grid(m)[[0, 7, 15]].tolist(),
+                          "pmax": pm[rows].mean(axis=0)[[0, 7, 15]].tolist()}
+    n_end = st.sites_per_sample()
+
+    # ---- e2e through the C ABI from pinned host buffers
+    host = {k: getattr(st, k).cpu().pin_memory() for k in ("seeds_dev", "samples", "n_lo", "cnt", "group_dev",
+                                                            "Ng_dev", "lo_dev", "pg_dev")}
+    dev2 = {k: torch.empty_like(getattr(st, k)) for k in host}
+    pm_host = torch.empty_like(st.pmax, device="cpu").pin_memory()
+
+    def e2e_step():
+        for k in host:
+            dev2[k].copy_(host[k], non_blocking=True)
+        perc._ok(lib.perc_rank(L, dev2["seeds_dev"].data_ptr(), len(seeds), st.perm.data_ptr(), st.rank.data_ptr(),
+                               st.ws.data_ptr(), st.ws.numel(), sp), "perc_rank")
+        perc._ok(lib.perc_binomial_weights(dev2["Ng_dev"].data_ptr(), dev2["lo_dev"].data_ptr(), st.G, st.window,
+                                           dev2["pg_dev"].data_ptr(), st.np, st.w.data_ptr(), sp),
+                 "perc_binomial_weights")
+        perc._ok(lib.perc_smax_window(dev2["samples"].data_ptr(), num, L, dev2["n_lo"].data_ptr(),
+                                      dev2["cnt"].data_ptr(), st.window, st.smax.data_ptr(), st.ws.data_ptr(),
+                                      st.ws.numel(), sp), "perc_smax_window")
+        perc._ok(lib.perc_pmax(st.smax.data_ptr(), dev2["group_dev"].data_ptr(), num, st.window, st.w.data_ptr(),
+                               dev2["Ng_dev"].data_ptr(), st.G, st.np, st.pmax.data_ptr(), sp), "perc_pmax")
+        pm_host.copy_(st.pmax, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    e2e_ms /= args.steps
+    assert np.array_equal(pm_host.numpy(), pm), "e2e P_max differs from the resident step's"
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = pm_host.numel() * pm_host.element_size()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms_step = max_over_ranks(ms_step)
+    e2e_ms = max_over_ranks(e2e_ms)
+    ms_smax = max_over_ranks(ms_smax)
+
+    # ---- roofline of the dominant kernel (k_smax): algorithmic bytes per sample = N/4 (bitmap write
+    # and read) + 16 per site up to the window's end (perm and rank reads, forest write and read)
+    # + 4 per S_max entry written
+    alg_bytes = float(num * N / 4 + 16 * n_end.sum() + 4 * st.count[st.group].sum())
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    achieved = alg_bytes / (ms_smax * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_seeds_cpu = cpu_workers
+        rate, done, dt = oracle_rate(range(1, n_seeds_cpu + 1), cpu_workers, _oracle_pmax_seed)
+        cpu = {"value": rate, "unit": "samples/s", "cores": cpu_workers, "kind": "oracle",
+               "sample": f"L=16, seeds 1..{n_seeds_cpu} x 127 masks ({done} samples, 16 p each) in {dt:.1f} s, "
+                         f"one ranking per seed, {cpu_workers} spawned workers"}
+
+    gpu_launches = (math.ceil(len(seeds) / 64) * 13) + 3  # rank passes + weights + S_max + P_max
+    value = world * num / (ms_step * 1e-3)
+    if rank == 0:
+        line = {
+            "metric": PMAX_METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32+f64", "data": "synthetic (Philox-keyed site orders, seeds per rank)",
+            "config": {"workload": "P_max(p) curves, all 127 neighborhoods, L=16 (1,048,576 sites), seeds 1..256 "
+                                   "per rank, 16 p per neighborhood at Table I p_c (1 +- 2%), windows of +-12 "
+                                   "binomial deviations",
+                       "L": L, "masks": 127, "seeds_per_rank": int(len(seeds)), "samples_per_rank": num,
+                       "p_per_sample": int(st.np), "window_max": int(st.window),
+                       "window_mean": float(st.count[st.group].mean()),
+                       "l2": "flushed (256 MiB write) between timed steps; site orders 2 GiB > L2",
+                       "parallelism": f"dp{world} (seed blocks, no collective)"},
+            "phases_ms": {"rank": ms_rank, "weights": ms_weights, "smax": ms_smax, "pmax": ms_pmax,
+                          "step_eager": ms_eager, "step_graph": ms_graph},
+            "curves": curves,
+            "e2e": {"value": world * num / (e2e_ms * 1e-3), "unit": "samples/s", "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "roofline": {"kernel": "k_smax", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "algorithmic_bytes_per_launch": alg_bytes,
+                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": gpu_launches,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------------
 # reference arm: the CPU oracle on the same workload
 # ------------------------------------------------------------------------------------------------
 def run_reference(args):
@@ -429,22 +670,26 @@ def run_reference(args):
         return
     workers = max(1, min(host_cores(), 32))
     per_step = workers  # one seed (127 samples) per worker per step
+    pmax = args.workload == "pmax"
+    fn = _oracle_pmax_seed if pmax else _oracle_seed
     for w in range(args.warmup):
-        oracle_rate(range(1, min(per_step, 4) + 1), min(workers, 4))
+        oracle_rate(range(1, min(per_step, 4) + 1), min(workers, 4), fn)
     rates, total_dt, total_done = [], 0.0, 0
     for k in range(args.steps):
         s0 = 1 + k * per_step
-        rate, done, dt = oracle_rate(range(s0, s0 + per_step), workers)
+        rate, done, dt = oracle_rate(range(s0, s0 + per_step), workers, fn)
         rates.append(rate)
         total_dt += dt
         total_done += done
     value = total_done / total_dt
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+        "impl": "reference", "metric": PMAX_METRIC if pmax else METRIC, "value": value, "unit": "samples/s",
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (Philox-keyed site orders)",
-        "config": {"workload": "all 127 neighborhoods, L=16 (1,048,576 sites); each step a bounded sample of "
+        "config": {"workload": ("P_max(p) curves (16 p at Table I p_c +- 2%), " if pmax else "") +
+                               "all 127 neighborhoods, L=16 (1,048,576 sites); each step a bounded sample of "
                                f"{per_step} seeds x 127 masks", "L": L, "masks": 127},
         "cpu_baseline": {"value": value, "unit": "samples/s", "cores": workers, "kind": "oracle",
                          "sample": f"{args.steps} steps x {per_step} seeds x 127 masks at L=16"},
@@ -468,6 +713,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
     ap.add_argument("--no-graph", dest="graph", action="store_false", help="do not time CUDA-graph replays")
+    ap.add_argument("--workload", default="nstar", choices=["nstar", "pmax"],
+                    help="nstar: the n* samples/s line (default); pmax: the P_max(p) path")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one learned and one plain step inside a profiler range and exit")
     args = ap.parse_args()
@@ -475,6 +722,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "pmax":
+        run_pmax_ours(args)
     else:
         run_ours(args)
 

@@ -53,6 +53,7 @@ typedef enum {
 #define PERC_OP_RANK 1
 #define PERC_OP_NSTAR 2
 #define PERC_OP_MASS 3
+#define PERC_OP_SMAX 4
 
 /* One sample.  perm/rank are this sample's site order (as written by perc_rank); samples that
  * share a seed point at the same arrays.  Layout: 24 bytes, 8-byte aligned. */
@@ -130,6 +131,60 @@ int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
  */
 int perc_mass(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
               const uint64_t *n, int64_t *mass, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * perc_smax_window -- S_max(n) for every n of a window: the largest cluster of each sample with its
+ * first n sites occupied, n = n_lo[k] .. n_lo[k] + window - 1 (eq. Pmax; Methods, "Computational
+ * methods": the Newman--Ziff sweep reads S_max after every added site, and the binomial
+ * convolution of perc_pmax needs it at every n where the weights are not negligible).
+ *   n_lo    device uint64[num_samples]: first n of each sample's window (any value; n > L^5 has no
+ *           S_max and reads 0)
+ *   count   device uint32[num_samples] or NULL: entries sample k computes (min(count[k], window));
+ *           NULL computes all `window` entries of every sample
+ *   window  row length of smax, >= 1; num_samples * window <= 2^40
+ *   smax    device uint32[num_samples][window] (output): smax[k][j] = S_max(n_lo[k] + j) for
+ *           j < count[k]; 0 where j >= count[k] or n_lo[k] + j > L^5; 0xFFFFFFFF in every entry
+ *           of a sample that fails the device-side check (the status word then holds PERC_EDEVICE)
+ *   workspace  perc_workspace_bytes(PERC_OP_SMAX, max_L, num_samples) bytes
+ * Cost: one connected-component pass over the first n_lo sites, then work proportional to the
+ * sites n_lo .. n_lo + count - 2 and their earlier neighbors.
+ */
+int perc_smax_window(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                     const uint64_t *n_lo, const uint32_t *count, uint32_t window, uint32_t *smax,
+                     void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * perc_binomial_weights -- the binomial distribution of the occupied-site count n at occupation
+ * probability p, B(N, n, p) = C(N, n) p^n (1-p)^(N-n), over a window of n (Methods, "Computational
+ * methods": the convolution that takes S_max(n) to S_max(p)).  Evaluated in FP64 as
+ * exp(log B) with log B from Loader's saddle-point form (C. Loader, "Fast and accurate computation
+ * of binomial probabilities", 2000): Stirling-series remainders of N!, n!, (N-n)! and the
+ * deviance terms n log(n/Np) + Np - n computed by their series near the mean, so no factorial or
+ * large power is ever formed; relative error about 1e-13.
+ *   For group g (0 <= g < groups) and probability j (0 <= j < np):
+ *   N      device uint64[groups]: sites L^5 of the group (1 <= N < 2^32)
+ *   n_lo   device uint64[groups]: first n of the group's window
+ *   p      device double[groups][np], each in [0, 1] (otherwise the row is NaN)
+ *   w      device double[groups][np][window] (output): w[g][j][k] = B(N[g], n_lo[g] + k, p[g][j]),
+ *          0 where n_lo[g] + k > N[g]
+ * Returns PERC_EINVAL for null pointers or a zero size.
+ */
+int perc_binomial_weights(const uint64_t *N, const uint64_t *n_lo, uint32_t groups, uint32_t window,
+                          const double *p, uint32_t np, double *w, void *stream);
+
+/*
+ * perc_pmax -- P_max(p) = S_max(p) / L^5 with S_max(p) = sum_n B(N, n, p) S_max(n) over the window
+ * (eq. Pmax and the binomial convolution of Methods, "Computational methods"), for every sample
+ * and probability.  The window must cover the n where the weights matter: the neglected part is
+ * at most 1 - sum_k w[g][j][k] (S_max(n) / N <= 1).
+ *   smax    device uint32[num_samples][window] from perc_smax_window
+ *   group   device uint32[num_samples]: weight group of each sample (< groups, else the row is NaN)
+ *   w       device double[groups][np][window] from perc_binomial_weights
+ *   N       device uint64[groups]: L^5 of each group
+ *   pmax    device double[num_samples][np] (output), FP64 sums
+ */
+int perc_pmax(const uint32_t *smax, const uint32_t *group, uint32_t num_samples, uint32_t window,
+              const double *w, const uint64_t *N, uint32_t groups, uint32_t np, double *pmax, void *stream);
 
 /*
  * perc_nstar_noalloc -- perc_nstar without a caller-provided workspace, for callers that cannot

@@ -592,14 +592,16 @@ __host__ __device__ inline size_t smem_bitmap_bytes(uint32_t smem_L)
 
 __host__ __device__ inline size_t smem_nodes_bytes(uint32_t node_cap) { return (size_t(node_cap) * 4 + 15) & ~size_t(15); }
 
-__device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn, uint32_t smem_L, uint32_t node_cap)
+// `extra` bytes (a multiple of 16) between the bitmap and the nodes belong to the caller.
+__device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn, uint32_t smem_L, uint32_t node_cap, size_t extra = 0)
 {
     SmemPtrs p;
     p.rows = reinterpret_cast<RowEntry *>(dyn);
     p.planes = reinterpret_cast<PlaneEntry *>(dyn + sizeof(RowEntry) * kRowCand);
     p.sbm = reinterpret_cast<uint32_t *>(dyn + smem_tables_bytes());
-    p.nodes = reinterpret_cast<uint32_t *>(dyn + smem_tables_bytes() + smem_bitmap_bytes(smem_L));
-    p.edges = reinterpret_cast<uint2 *>(dyn + smem_tables_bytes() + smem_bitmap_bytes(smem_L) + smem_nodes_bytes(node_cap));
+    const size_t nodes_at = smem_tables_bytes() + smem_bitmap_bytes(smem_L) + extra;
+    p.nodes = reinterpret_cast<uint32_t *>(dyn + nodes_at);
+    p.edges = reinterpret_cast<uint2 *>(dyn + nodes_at + smem_nodes_bytes(node_cap));
     p.scratch = reinterpret_cast<uint32_t *>(p.edges);
     return p;
 }
@@ -1126,6 +1128,352 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
 }
 
 // ------------------------------------------------------------------------------------------------
+// S_max(n) for every n of a window [n_lo, n_lo + W) (eq. Pmax; Methods, "Computational methods":
+// the Newman--Ziff sweep adds one site at a time and reads the largest cluster after each).
+//
+// Per sample, one connected-component pass over the first n0 = min(n_lo, N) sites gives the forest
+// and, by counting, every cluster's size and S_max(n0).  The window's sites then follow in chunks
+// of up to blockDim sites:
+//   scan    -- each chunk site's occupied neighbors (bitmap through the chunk's last site) as edges;
+//   filter  -- an edge is kept when its neighbor came earlier (an edge belongs to its later site)
+//              and counted per site; a prefix sum places each site's records.  A chunk whose
+//              records would pass kRecCap is cut after the last site that fits, and the next chunk
+//              starts there;
+//   resolve -- a neighbor from before the chunk becomes the root of its cluster; every distinct
+//              root gets a local slot (shared-memory hash) that holds its size;
+//   replay  -- one thread adds the chunk's sites in rank order to a union-find over the local slots
+//              (union by size) and records the running maximum after each site: S_max at that n,
+//              since cluster sizes never shrink;
+//   apply   -- the chunk's merges and the new roots' sizes are written back to the forest.
+// ------------------------------------------------------------------------------------------------
+constexpr uint32_t kRecCap = 1536;    // kept edges of a window chunk (> 892: one site always fits)
+constexpr uint32_t kRootHash = 2048;  // local slots of the distinct earlier roots one chunk touches
+constexpr uint32_t kEmptySlot = 0xFFFFFFFFu;
+constexpr uint32_t kRootBit = 0x80000000u;  // local union-find entry of a root: kRootBit | size
+static_assert(kRecCap > kMaxOffsets && kRecCap < kRootHash && (kRootHash & (kRootHash - 1)) == 0,
+              "record and hash capacities");
+
+struct WinPtrs {
+    uint32_t *deg;   // [C] kept edges per chunk site, then the scatter cursor
+    uint32_t *ev;    // [C] S_max after each chunk site
+    uint32_t *lp;    // [C + kRootHash] local union-find: parent slot, or kRootBit | size
+    uint32_t *hkey;  // [kRootHash] forest node of local slot C + h (kEmptySlot: free)
+    uint32_t *rec;   // [kRecCap] the earlier end of each kept edge, as a local slot
+    uint32_t *off;   // [C + 1] first record of each chunk site
+};
+
+__host__ __device__ inline size_t smem_window_bytes(uint32_t threads)
+{
+    return ((size_t(threads) * 4 + 1 + kRecCap + 2 * kRootHash) * 4 + 15) & ~size_t(15);
+}
+
+__device__ __forceinline__ WinPtrs win_ptrs(unsigned char *at, uint32_t C)
+{
+    WinPtrs w;
+    uint32_t *u = reinterpret_cast<uint32_t *>(at);
+    w.deg = u;
+    w.ev = u + C;
+    w.lp = u + 2 * C;
+    w.hkey = w.lp + C + kRootHash;
+    w.rec = w.hkey + kRootHash;
+    w.off = w.rec + kRecCap;
+    return w;
+}
+
+// Exclusive prefix sum of v over the block's threads (blockDim a multiple of 32); `total` gets the
+// block's sum.  Uses wsum[32] and two block barriers.
+__device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t v, uint32_t *wsum, uint32_t &total)
+{
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= static_cast<uint32_t>(o)) x += y;
+    }
+    if (lane == 31u) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0u) {
+        uint32_t t = lane < nw ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= static_cast<uint32_t>(o)) t += y;
+        }
+        if (lane < nw) wsum[lane] = t;
+    }
+    __syncthreads();
+    total = wsum[nw - 1u];
+    return (warp ? wsum[warp - 1u] : 0u) + x - v;
+}
+
+// Root of local slot x (read only).
+__device__ __forceinline__ uint32_t local_root(const uint32_t *lp, uint32_t x)
+{
+    for (;;) {
+        const uint32_t v = lp[x];
+        if (v & kRootBit) return x;
+        x = v;
+    }
+}
+
+// Root of local slot x with path halving (the replay thread only).
+__device__ __forceinline__ uint32_t local_find(uint32_t *lp, uint32_t x)
+{
+    for (;;) {
+        const uint32_t v = lp[x];
+        if (v & kRootBit) return x;
+        const uint32_t g = lp[v];
+        if (g & kRootBit) return v;
+        lp[x] = g;
+        x = g;
+    }
+}
+
+// Local slot of forest root g: linear probing in the chunk's hash; the thread that inserts g also
+// stores its cluster size.  Returns kEmptySlot only if the hash is full, which the capacities rule
+// out (a chunk keeps at most kRecCap < kRootHash records).
+__device__ __forceinline__ uint32_t root_slot(const WinPtrs &wp, const uint32_t *cnt, uint32_t g, uint32_t C)
+{
+    uint32_t h = (g * 2654435761u) >> (32 - 11);
+    static_assert(kRootHash == 2048u, "hash width");
+    for (uint32_t probe = 0; probe < kRootHash; ++probe) {
+        const uint32_t prev = atomicCAS(wp.hkey + h, kEmptySlot, g);
+        if (prev == kEmptySlot) {
+            wp.lp[C + h] = kRootBit | __ldcg(cnt + g);
+            return C + h;
+        }
+        if (prev == g) return C + h;
+        h = (h + 1u) & (kRootHash - 1u);
+    }
+    return kEmptySlot;
+}
+
+// Scan of the window chunk [b, b + count): edges (local index of the site, occupied neighbor).
+template <bool kSmemBm, bool kPlanes>
+__device__ __forceinline__ void window_scan(const Ctl &c, const uint32_t *bm, const RowEntry *rows,
+                                            const PlaneEntry *planes, const EdgeList &E, const uint32_t *perm,
+                                            uint32_t L, const FastDiv &fd, uint32_t b, uint32_t count,
+                                            uint32_t *ecount)
+{
+    const uint32_t R = kPlanes ? c.NP : c.R;
+    const uint32_t gshift = lanes_shift(count, R);
+    const uint32_t gsize = 1u << gshift, gl = threadIdx.x & (gsize - 1u), t = threadIdx.x >> gshift;
+    if (t >= count) return;
+    const SiteGeo g = site_geo<kPlanes>(__ldg(perm + b + t), L, fd);
+    for (uint32_t k = gl; k < R; k += gsize) {
+        uint32_t h[3];
+        const uint32_t jb = entry_hits<kSmemBm, kPlanes>(g, bm, rows, planes, k, h);
+        const uint32_t nh = __popc(h[0]) + __popc(h[1]) + __popc(h[2]);
+        if (nh == 0u) continue;
+        uint32_t slot = atomicAdd(ecount, nh);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            uint32_t hf = h[f];
+            while (hf) {
+                const uint32_t bit = __ffs(hf) - 1;
+                hf &= hf - 1u;
+                edge_put(E, slot++, make_uint2(t, jb + 32u * f + bit));
+            }
+        }
+    }
+}
+
+struct SmaxShared {
+    uint32_t run_max;  // S_max after the last site added
+    uint32_t red[32];
+};
+
+// One sample of k_smax (all threads).  Writes row[k] = S_max(n_lo + k) for n_lo + k <= n_end.
+template <bool kSmemBm, bool kPlanes>
+__device__ void smax_sample(Ctl &c, SmaxShared &x, const Nodes &P, uint32_t *cnt, uint32_t *bm, const SmemPtrs &sm,
+                            const WinPtrs &wp, const EdgeList &E, const perc_sample &smp, uint32_t n0, uint32_t n_end,
+                            uint64_t nlo, uint32_t window, uint32_t *row, int *status)
+{
+    const uint32_t C = blockDim.x, L = smp.L;
+    if (kSmemBm) bm = sm.sbm;
+    const FastDiv fd = make_fastdiv(L);
+    // ---- the forest of the first n0 sites, the cluster sizes and S_max(n0)
+    bitmap_update(bm, smp.perm, 0u, n0);
+    for (uint32_t r = threadIdx.x; r < n0; r += C) {
+        nd_st(P, r + 2u, r + 2u);
+        __stcg(cnt + r + 2u, 0u);
+    }
+    __syncthreads();
+    if (n0 > 0u)
+        union_pass<kSmemBm, false, kPlanes>(c, P, nullptr, bm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u,
+                                            n0, 0u);
+    __syncthreads();
+    for (uint32_t r = threadIdx.x; r < n0; r += C) atomicAdd(cnt + uf_find(P, r + 2u, 0u), 1u);
+    __syncthreads();
+    uint32_t best = 0;
+    for (uint32_t r = threadIdx.x; r < n0; r += C) best = max(best, ld_cg(cnt + r + 2u));
+    best = __reduce_max_sync(0xffffffffu, best);
+    if ((threadIdx.x & 31u) == 0u) x.red[threadIdx.x >> 5] = best;
+    wp.lp[threadIdx.x] = kRootBit | 1u;
+    for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey[h] = kEmptySlot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t bmax = 0;
+        for (uint32_t w = 0; w < (C >> 5); ++w) bmax = max(bmax, x.red[w]);
+        x.run_max = bmax;
+        row[0] = bmax;  // n = n_lo = n0
+    }
+    // ---- the window's sites, a chunk at a time
+    for (uint32_t b = n0; b < n_end;) {
+        const uint32_t count = min(C, n_end - b);
+        bitmap_update(bm, smp.perm, b, b + count);
+        wp.deg[threadIdx.x] = 0u;
+        if (threadIdx.x == 0) c.ecount[0] = 0u;
+        __syncthreads();
+        window_scan<kSmemBm, kPlanes>(c, bm, sm.rows, sm.planes, E, smp.perm, L, fd, b, count, &c.ecount[0]);
+        __syncthreads();
+        const uint32_t ne = c.ecount[0];
+        // filter: keep the edges to earlier sites, count them per site (rank replaces the site)
+        for (uint32_t e = threadIdx.x; e < ne; e += C) {
+            const uint2 ed = edge_get(E, e);
+            const uint32_t rj = __ldg(smp.rank + ed.y);
+            const bool keep = rj < b + ed.x;
+            if (keep) atomicAdd(wp.deg + ed.x, 1u);
+            edge_put(E, e, make_uint2(keep ? ed.x : kEmptySlot, rj));
+        }
+        __syncthreads();
+        const uint32_t d = wp.deg[threadIdx.x];
+        uint32_t total;
+        const uint32_t excl = block_exclusive_sum(d, x.red, total);
+        wp.off[threadIdx.x] = excl;
+        if (threadIdx.x == C - 1u) wp.off[C] = total;
+        const uint32_t tn = __syncthreads_count(threadIdx.x < count && excl + d <= kRecCap);
+        wp.deg[threadIdx.x] = 0u;
+        __syncthreads();
+        // resolve: earlier neighbors to local slots, records in site order
+        for (uint32_t e = threadIdx.x; e < ne; e += C) {
+            const uint2 ed = edge_get(E, e);
+            if (ed.x >= tn) continue;  // dropped, or past the cut
+            const uint32_t pos = wp.off[ed.x] + atomicAdd(wp.deg + ed.x, 1u);
+            wp.rec[pos] = ed.y >= b ? ed.y - b : root_slot(wp, cnt, uf_find(P, ed.y + 2u, 0u), C);
+        }
+        __syncthreads();
+        // replay
+        if (threadIdx.x == 0) {
+            uint32_t smax = x.run_max;
+            for (uint32_t t = 0; t < tn; ++t) {
+                uint32_t ra = t, sa = 1u;  // no earlier record names site t: it starts alone
+                const uint32_t k1 = wp.off[t + 1u];
+                for (uint32_t k = wp.off[t]; k < k1; ++k) {
+                    const uint32_t bs = wp.rec[k];
+                    if (bs >= C + kRootHash) {  // full hash (ruled out by the capacities)
+                        set_status(status, PERC_EDEVICE);
+                        continue;
+                    }
+                    const uint32_t rb = local_find(wp.lp, bs);
+                    if (rb == ra) continue;
+                    const uint32_t sb = wp.lp[rb] & ~kRootBit;
+                    if (sa >= sb) {
+                        wp.lp[rb] = ra;
+                    } else {
+                        wp.lp[ra] = rb;
+                        ra = rb;
+                    }
+                    sa += sb;
+                    wp.lp[ra] = kRootBit | sa;
+                }
+                smax = max(smax, sa);
+                wp.ev[t] = smax;
+            }
+            x.run_max = smax;
+        }
+        __syncthreads();
+        // apply: chunk sites point at their root's forest node, hooked earlier roots likewise
+        if (threadIdx.x < tn) {
+            const uint32_t t = threadIdx.x;
+            const uint32_t rt = local_root(wp.lp, t);
+            nd_st(P, b + t + 2u, rt < C ? b + rt + 2u : wp.hkey[rt - C]);
+            if (rt == t) __stcg(cnt + b + t + 2u, wp.lp[t] & ~kRootBit);
+            const uint64_t k = uint64_t(b) + t + 1u - nlo;
+            if (k < window) row[k] = wp.ev[t];
+        }
+        for (uint32_t h = threadIdx.x; h < kRootHash; h += C) {
+            const uint32_t g = wp.hkey[h];
+            if (g == kEmptySlot) continue;
+            const uint32_t rt = local_root(wp.lp, C + h);
+            if (rt != C + h)
+                nd_st(P, g, rt < C ? b + rt + 2u : wp.hkey[rt - C]);
+            else
+                __stcg(cnt + g, wp.lp[C + h] & ~kRootBit);
+        }
+        __syncthreads();
+        wp.lp[threadIdx.x] = kRootBit | 1u;
+        for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey[h] = kEmptySlot;
+        b += tn;  // the next chunk's first barrier orders these resets before their readers
+    }
+}
+
+__global__ void __launch_bounds__(1024, 1)
+k_smax(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t node_cap,
+       uint32_t edge_scap, const uint64_t *__restrict__ n_lo, const uint32_t *__restrict__ count, uint32_t window,
+       uint32_t *__restrict__ out, char *ws, size_t slot_bytes)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    const uint32_t C = blockDim.x;
+    const SmemPtrs sm = smem_ptrs(dyn, smem_L, node_cap, smem_window_bytes(C));
+    const WinPtrs wp = win_ptrs(dyn + smem_tables_bytes() + smem_bitmap_bytes(smem_L), C);
+    __shared__ Ctl c;
+    __shared__ SmaxShared x;
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+    const uint64_t Ncap = num_sites(max_L);
+    const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
+    const EdgeList E{sm.edges, edge_scap, sp.gedges};
+    const Nodes P{sp.P, static_cast<uint32_t>(__cvta_generic_to_shared(sm.nodes)), node_cap};
+
+    for (;;) {
+        if (threadIdx.x == 0) c.sample = atomicAdd(&hdr->queue, 1u);
+        __syncthreads();
+        const uint32_t s = c.sample;
+        if (s >= num) break;
+        const perc_sample smp = samples[s];
+        const uint32_t L = smp.L, mask = smp.zone_mask;
+        uint32_t *row = out + size_t(s) * window;
+        if (L < 1u || L > max_L || mask < 1u || mask > 127u || !smp.perm || !smp.rank) {
+            for (uint32_t k = threadIdx.x; k < window; k += C) row[k] = kEmptySlot;
+            if (threadIdx.x == 0) set_status(&hdr->status, PERC_EDEVICE);
+            __syncthreads();
+            continue;
+        }
+        const uint32_t N = static_cast<uint32_t>(num_sites(L));
+        const uint64_t nlo = n_lo[s];
+        const uint32_t len = count ? min(count[s], window) : window;  // entries this sample computes
+        for (uint32_t k = threadIdx.x; k < window; k += C)
+            if (k >= len || nlo + k > N) row[k] = 0u;  // not asked for, or no such n
+        if (nlo > N || len == 0u) {
+            __syncthreads();
+            continue;
+        }
+        const uint64_t last = nlo + len - 1u;  // the last n computed
+        const uint32_t n0 = static_cast<uint32_t>(nlo), n_end = last < N ? static_cast<uint32_t>(last) : N;
+        const bool smem_bm = L <= smem_L;
+        uint32_t *bm = smem_bm ? sm.sbm : sp.gbm;
+        const uint32_t words = bm_words(N);
+        for (uint32_t w = threadIdx.x; w < words; w += C) bm[w] = 0u;
+        build_rows(mask, L, sm.rows, sm.scratch, c);
+        if (smem_bm && L == kPlaneL) build_planes16(sm.rows, c.R, sm.planes, sm.scratch, c);
+        if (threadIdx.x == 0) {
+            c.logn = 0;
+            c.stop = 0;
+            c.ecount[0] = 0;
+        }
+        __syncthreads();
+        if (smem_bm && L == kPlaneL)
+            smax_sample<true, true>(c, x, P, sp.logb, bm, sm, wp, E, smp, n0, n_end, nlo, window, row, &hdr->status);
+        else if (smem_bm)
+            smax_sample<true, false>(c, x, P, sp.logb, bm, sm, wp, E, smp, n0, n_end, nlo, window, row, &hdr->status);
+        else
+            smax_sample<false, false>(c, x, P, sp.logb, bm, sm, wp, E, smp, n0, n_end, nlo, window, row, &hdr->status);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // host side: launch configuration and workspace layout
 // ------------------------------------------------------------------------------------------------
 struct LaunchCfg {
@@ -1151,7 +1499,7 @@ struct CfgCache {
     bool valid = false;
 };
 constexpr int kCfgDevices = 64;
-static CfgCache g_cfg_cache[2][kCfgDevices];
+static CfgCache g_cfg_cache[3][kCfgDevices];
 static std::mutex g_cfg_mutex;
 
 // Launch options set through perc_set_launch_option (0 = automatic).
@@ -1176,7 +1524,8 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool
     // registers a thread); each CTA takes an equal share.  What the tables and the bitmap leave
     // goes to union-find nodes (up to kSmemNodes, keeping room for 512 edges) and then to the
     // shared part of the edge list.
-    const size_t base = smem_tables_bytes() + smem_bitmap_bytes(cfg.smem_L);
+    const size_t base = smem_tables_bytes() + smem_bitmap_bytes(cfg.smem_L) +
+                        (op == PERC_OP_SMAX ? smem_window_bytes(cfg.threads) : 0);
     const size_t min_edges = size_t(kRowCand) * sizeof(uint32_t);  // table-building scratch
     int ctas = (65536 / (cfg.threads * 64)) > 0 ? 65536 / (cfg.threads * 64) : 1;
     while (ctas > 1 && size_t(optin) / ctas - 1024 < base + min_edges) --ctas;  // fewer, larger CTAs
@@ -1194,8 +1543,10 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool
     cfg.smem = base + smem_nodes_bytes(cfg.node_cap) + size_t(cfg.edge_scap) * sizeof(uint2);
     // The attribute and the occupancy are queried once per (kernel, device, threads, shared memory)
     // and cached, so that a call made while a stream is being captured issues no such query.
-    const int k = op == PERC_OP_MASS ? 1 : 0;
-    const void *fn = k ? reinterpret_cast<const void *>(k_mass) : reinterpret_cast<const void *>(k_nstar);
+    const int k = op == PERC_OP_MASS ? 1 : (op == PERC_OP_SMAX ? 2 : 0);
+    const void *fn = k == 1   ? reinterpret_cast<const void *>(k_mass)
+                     : k == 2 ? reinterpret_cast<const void *>(k_smax)
+                              : reinterpret_cast<const void *>(k_nstar);
     {
         std::lock_guard<std::mutex> lock(g_cfg_mutex);
         CfgCache &cc = g_cfg_cache[k][dev < kCfgDevices ? dev : 0];
@@ -1289,7 +1640,7 @@ extern "C" size_t perc_workspace_bytes(int op, uint32_t max_L, uint32_t num)
         if (max_L < 1 || max_L > PERC_MAX_L || num == 0) return 0;
         return rank_workspace_bytes(max_L, num);
     }
-    if (op != PERC_OP_NSTAR && op != PERC_OP_MASS) return 0;
+    if (op != PERC_OP_NSTAR && op != PERC_OP_MASS && op != PERC_OP_SMAX) return 0;
     LaunchCfg cfg;
     if (launch_cfg(op, max_L, num, cfg) != PERC_OK) return 0;
     return sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes;
@@ -1343,6 +1694,24 @@ extern "C" int perc_mass(const perc_sample *samples, uint32_t num_samples, uint3
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
     k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap, cfg.edge_scap, n, mass,
+                                                        static_cast<char *>(workspace), cfg.slot_bytes);
+    return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
+}
+
+extern "C" int perc_smax_window(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                                const uint64_t *n_lo, const uint32_t *count, uint32_t window, uint32_t *smax,
+                                void *workspace, size_t ws_bytes, void *stream_)
+{
+    if (!samples || !n_lo || !smax || !workspace || num_samples == 0 || window == 0) return PERC_EINVAL;
+    if (uint64_t(num_samples) * window > (uint64_t(1) << 40)) return PERC_EINVAL;
+    LaunchCfg cfg;
+    int rc = launch_cfg(PERC_OP_SMAX, max_L, num_samples, cfg);
+    if (rc != PERC_OK) return rc;
+    if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
+    k_smax<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap,
+                                                        cfg.edge_scap, n_lo, count, window, smax,
                                                         static_cast<char *>(workspace), cfg.slot_bytes);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }

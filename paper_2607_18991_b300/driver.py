@@ -115,6 +115,79 @@ def mass(workload, n, budget: int = DEFAULT_BUDGET):
     return out
 
 
+def smax_window(workload, n_lo, window: int, budget: int = DEFAULT_BUDGET):
+    """S_max(n_lo[k] + j), j < window, for every row of `workload`: uint32 numpy [num, window]
+    (0 where n_lo[k] + j > L^5)."""
+    workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
+    n_lo = np.asarray(n_lo, dtype=np.int64).reshape(-1)
+    ws = perc.default_workspace()
+    out = np.zeros((len(workload), window), dtype=np.uint32)
+    for p in iter_prepared(workload, budget, ws):
+        sm = perc.smax_window(p.samples, p.max_L, torch.as_tensor(n_lo[p.idx]), window, ws=ws)
+        out[p.idx] = perc.u32(sm).reshape(len(p.idx), window)
+        rc = perc.check(ws)
+        if rc != 0:
+            raise perc.PercError(rc, "perc_smax_window device status")
+        del p
+    return out
+
+
+def pmax_windows(L, p, sigmas: float = 12.0):
+    """Weight groups and windows for P_max at probabilities p[k, :] of samples with sides L[k].
+
+    Samples with the same side and the same row of probabilities form one group; its window of n
+    runs from N p_min - sigmas * s to N p_max + sigmas * s (s the largest binomial standard
+    deviation sqrt(N p (1 - p)) of the row), clipped to [0, N].  Returns (group[k], N[g],
+    n_lo[g], count[g], p[g, :], window): count[g] values of n from n_lo[g], window = max count."""
+    L = np.asarray(L, dtype=np.int64).reshape(-1)
+    p = np.asarray(p, dtype=np.float64).reshape(len(L), -1)
+    keys, group = np.unique(np.hstack([L[:, None].astype(np.float64), p]), axis=0, return_inverse=True)
+    Ng = keys[:, 0].astype(np.int64) ** 5
+    pg = keys[:, 1:]
+    sd = np.sqrt(Ng[:, None] * pg * (1.0 - pg)).max(axis=1)
+    lo = np.clip(np.floor(Ng * pg.min(axis=1) - sigmas * sd), 0, Ng).astype(np.int64)
+    hi = np.clip(np.ceil(Ng * pg.max(axis=1) + sigmas * sd), 0, Ng).astype(np.int64)
+    count = hi - lo + 1
+    return group.astype(np.int64).reshape(-1), Ng, lo, count, pg, int(count.max())
+
+
+class PmaxPlan:
+    """Device inputs of one P_max computation: groups, windows and the binomial weights."""
+
+    def __init__(self, workload, p, sigmas: float = 12.0):
+        self.workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
+        self.p = np.asarray(p, dtype=np.float64).reshape(len(self.workload), -1)
+        self.group, self.Ng, self.lo, self.count, self.pg, self.window = pmax_windows(
+            self.workload[:, 0], self.p, sigmas)
+        self.Ng_t = torch.as_tensor(self.Ng, device="cuda")
+        self.w = perc.binomial_weights(self.Ng_t, torch.as_tensor(self.lo, device="cuda"), self.window,
+                                       torch.as_tensor(self.pg, device="cuda"))
+        # weight mass inside each group's own window (S_max is computed there only)
+        k = torch.arange(self.window, device="cuda")
+        inside = k[None, None, :] < torch.as_tensor(self.count, device="cuda")[:, None, None]
+        self.mass_g = (self.w * inside).sum(dim=2).cpu().numpy()
+
+
+def pmax(workload, p, sigmas: float = 12.0, budget: int = DEFAULT_BUDGET):
+    """P_max(p) = S_max(p) / L^5 (eq. Pmax with the binomial convolution) for every row of
+    `workload` at its probabilities p[k, :].  Returns (pmax float64 [num, np], weight mass of each
+    sample's window float64 [num, np]; 1 - mass bounds the neglected part)."""
+    plan = PmaxPlan(workload, p, sigmas)
+    ws = perc.default_workspace()
+    out = np.zeros(plan.p.shape, dtype=np.float64)
+    for pr in iter_prepared(plan.workload, budget, ws):
+        g = plan.group[pr.idx]
+        sm = perc.smax_window(pr.samples, pr.max_L, torch.as_tensor(plan.lo[g]), plan.window,
+                              count=torch.as_tensor(plan.count[g]), ws=ws)
+        pm = perc.pmax(sm, torch.as_tensor(g, device="cuda"), plan.w, plan.Ng_t)
+        out[pr.idx] = pm.cpu().numpy()
+        rc = perc.check(ws)
+        if rc != 0:
+            raise perc.PercError(rc, "perc_smax_window device status")
+        del pr
+    return out, plan.mass_g[plan.group]
+
+
 # ------------------------------------------------------------------------------------------------
 # multi-process sharding: every sample is independent, so ranks take disjoint seed blocks (all
 # masks and all L of a seed stay together and share one ranking) and the results are merged once
@@ -214,3 +287,82 @@ class NstarStep:
         if rc != 0:
             raise perc.PercError(rc, "perc_nstar device status")
         return perc.u32(self.nstar), perc.u32(self.passes)
+
+
+class PmaxStep:
+    """Rank the seeds, build the binomial weights and compute P_max(p) for all (mask, seed) pairs at
+    one L, each mask with its own row of probabilities (eq. Pmax with the binomial convolution).
+
+    Every device buffer is allocated here, so ``run`` only enqueues library calls on the stream.
+    Samples are seed-major; the weight groups are the masks (one row of p per mask)."""
+
+    def __init__(self, L: int, masks, seeds, p_of_mask: dict, sigmas: float = 12.0):
+        self.L = int(L)
+        self.masks = np.asarray(list(masks), dtype=np.int64)
+        self.seeds = np.asarray(list(seeds), dtype=np.int64)
+        N = self.L ** 5
+        S = len(self.seeds)
+        self.workload = np.array([(self.L, m, s) for s in self.seeds for m in self.masks], dtype=np.int64)
+        self.num = len(self.workload)
+        p = np.array([p_of_mask[int(m)] for m in self.workload[:, 1]], dtype=np.float64)
+        self.group, self.Ng, self.lo, self.count, self.pg, self.window = pmax_windows(
+            self.workload[:, 0], p, sigmas)
+        self.np = self.pg.shape[1]
+        self.G = len(self.Ng)
+        self.seeds_dev = torch.as_tensor(self.seeds, device="cuda")
+        self.perm = torch.empty((S, N), dtype=torch.int32, device="cuda")
+        self.rank = torch.empty((S, N), dtype=torch.int32, device="cuda")
+        rows = np.repeat(np.arange(S), len(self.masks))
+        self.samples = perc.samples_for(self.L, np.tile(self.masks, S), rows, self.perm, self.rank)
+        self.n_lo = torch.as_tensor(self.lo[self.group], device="cuda")
+        self.cnt = torch.as_tensor(self.count[self.group].astype(np.int32), device="cuda")
+        self.group_dev = torch.as_tensor(self.group.astype(np.int32), device="cuda")
+        self.Ng_dev = torch.as_tensor(self.Ng, device="cuda")
+        self.lo_dev = torch.as_tensor(self.lo, device="cuda")
+        self.pg_dev = torch.as_tensor(self.pg, device="cuda")
+        self.w = torch.empty((self.G, self.np, self.window), dtype=torch.float64, device="cuda")
+        self.smax = torch.empty((self.num, self.window), dtype=torch.int32, device="cuda")
+        self.pmax = torch.empty((self.num, self.np), dtype=torch.float64, device="cuda")
+        nb = max(perc.workspace_bytes(perc.OP_RANK, self.L, S), perc.workspace_bytes(perc.OP_SMAX, self.L, self.num))
+        self.ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        self.lib = perc.lib()
+
+    def run_rank(self, stream=None):
+        perc._ok(self.lib.perc_rank(self.L, self.seeds_dev.data_ptr(), len(self.seeds), self.perm.data_ptr(),
+                                    self.rank.data_ptr(), self.ws.data_ptr(), self.ws.numel(), perc._stream(stream)),
+                 "perc_rank")
+
+    def run_weights(self, stream=None):
+        perc._ok(self.lib.perc_binomial_weights(self.Ng_dev.data_ptr(), self.lo_dev.data_ptr(), self.G, self.window,
+                                                self.pg_dev.data_ptr(), self.np, self.w.data_ptr(),
+                                                perc._stream(stream)), "perc_binomial_weights")
+
+    def run_smax(self, stream=None):
+        perc._ok(self.lib.perc_smax_window(self.samples.data_ptr(), self.num, self.L, self.n_lo.data_ptr(),
+                                           self.cnt.data_ptr(), self.window, self.smax.data_ptr(), self.ws.data_ptr(),
+                                           self.ws.numel(), perc._stream(stream)), "perc_smax_window")
+
+    def run_pmax(self, stream=None):
+        perc._ok(self.lib.perc_pmax(self.smax.data_ptr(), self.group_dev.data_ptr(), self.num, self.window,
+                                    self.w.data_ptr(), self.Ng_dev.data_ptr(), self.G, self.np, self.pmax.data_ptr(),
+                                    perc._stream(stream)), "perc_pmax")
+
+    def run(self, stream=None):
+        self.run_rank(stream)
+        self.run_weights(stream)
+        self.run_smax(stream)
+        self.run_pmax(stream)
+
+    def capture(self) -> torch.cuda.CUDAGraph:
+        """CUDA graph of one step (warm the library up with ``run`` first)."""
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(g, stream=s):
+            self.run()
+        torch.cuda.current_stream().wait_stream(s)
+        return g
+
+    def sites_per_sample(self) -> np.ndarray:
+        """Last n each sample's window reaches (the sites its S_max pass adds)."""
+        return np.minimum(self.lo + self.count - 1, self.Ng)[self.group]

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libperc.so")
 NEVER = 0xFFFFFFFF
 MAX_L = 73
-OP_RANK, OP_NSTAR, OP_MASS = 1, 2, 3
+OP_RANK, OP_NSTAR, OP_MASS, OP_SMAX = 1, 2, 3, 4
 OPT_THREADS, OPT_SMEM_NODES, OPT_MAX_CTAS, OPT_GROUP = 1, 2, 3, 4
 MLP_NPARAM = 4931
 STATS_FIELDS = ("passes", "new_sites", "probe_sites", "hooks", "early_exits", "fallbacks",
@@ -49,6 +49,9 @@ def lib() -> ctypes.CDLL:
         "perc_nstar": (i32, [vp, u32, u32, vp, vp, vp, vp, vp, sz, vp]),
         "perc_nstar_noalloc": (i32, [vp, u32, u32, vp, vp, vp, vp, vp]),
         "perc_mass": (i32, [vp, u32, u32, vp, vp, vp, sz, vp]),
+        "perc_smax_window": (i32, [vp, u32, u32, vp, vp, u32, vp, vp, sz, vp]),
+        "perc_binomial_weights": (i32, [vp, vp, u32, u32, vp, u32, vp, vp]),
+        "perc_pmax": (i32, [vp, vp, u32, u32, vp, vp, u32, u32, vp, vp]),
         "perc_check": (i32, [vp, vp]),
         "perc_set_launch_option": (i32, [i32, i32]),
         "perc_mlp_forward": (i32, [vp, vp, u32, vp, vp]),
@@ -67,7 +70,8 @@ def lib() -> ctypes.CDLL:
 
 
 def exported_symbols() -> list[str]:
-    return ["perc_workspace_bytes", "perc_rank", "perc_nstar", "perc_nstar_noalloc", "perc_mass", "perc_check",
+    return ["perc_workspace_bytes", "perc_rank", "perc_nstar", "perc_nstar_noalloc", "perc_mass",
+            "perc_smax_window", "perc_binomial_weights", "perc_pmax", "perc_check",
             "perc_mlp_forward", "perc_mlp_grad", "perc_adam", "perc_mlp_train", "perc_bracket",
             "perc_status_string", "perc_set_launch_option"]
 
@@ -213,6 +217,50 @@ def mass(samples: torch.Tensor, max_L: int, n: torch.Tensor, ws: Workspace | Non
     _ok(lib().perc_mass(samples.data_ptr(), num, max_L, n.data_ptr(), m.data_ptr(), buf.data_ptr(),
                         buf.numel(), _stream(stream)), "perc_mass")
     return m
+
+
+def smax_window(samples: torch.Tensor, max_L: int, n_lo: torch.Tensor, window: int,
+                count: torch.Tensor | None = None, ws: Workspace | None = None, stream=None,
+                out=None) -> torch.Tensor:
+    """S_max(n_lo[k] + j), j < count[k] (all `window` entries when count is None), per sample:
+    int32 tensor [num, window] of uint32 values (0 past count[k] or past L^5)."""
+    num = samples.shape[0]
+    sm = out if out is not None else torch.empty((num, window), dtype=torch.int32, device="cuda")
+    ws = ws or default_workspace()
+    buf = ws.get(workspace_bytes(OP_SMAX, max_L, num))
+    n_lo = n_lo.to(device="cuda", dtype=torch.int64).contiguous()
+    if count is not None:
+        count = count.to(device="cuda", dtype=torch.int32).contiguous()
+    _ok(lib().perc_smax_window(samples.data_ptr(), num, max_L, n_lo.data_ptr(), _ptr(count), window,
+                               sm.data_ptr(), buf.data_ptr(), buf.numel(), _stream(stream)), "perc_smax_window")
+    return sm
+
+
+def binomial_weights(N: torch.Tensor, n_lo: torch.Tensor, window: int, p: torch.Tensor,
+                     stream=None, out=None) -> torch.Tensor:
+    """B(N[g], n_lo[g] + k, p[g, j]) as float64 [groups, np, window]."""
+    N = N.to(device="cuda", dtype=torch.int64).contiguous()
+    n_lo = n_lo.to(device="cuda", dtype=torch.int64).contiguous()
+    p = p.to(device="cuda", dtype=torch.float64).contiguous()
+    G, npr = p.shape
+    w = out if out is not None else torch.empty((G, npr, window), dtype=torch.float64, device="cuda")
+    _ok(lib().perc_binomial_weights(N.data_ptr(), n_lo.data_ptr(), G, window, p.data_ptr(), npr, w.data_ptr(),
+                                    _stream(stream)), "perc_binomial_weights")
+    return w
+
+
+def pmax(smax: torch.Tensor, group: torch.Tensor, w: torch.Tensor, N: torch.Tensor, stream=None,
+         out=None) -> torch.Tensor:
+    """P_max(p) per (sample, p): float64 [num, np] from S_max windows and weight groups."""
+    num, window = smax.shape
+    G, npr, W = w.shape
+    assert W == window
+    group = group.to(device="cuda", dtype=torch.int32).contiguous()
+    N = N.to(device="cuda", dtype=torch.int64).contiguous()
+    pm = out if out is not None else torch.empty((num, npr), dtype=torch.float64, device="cuda")
+    _ok(lib().perc_pmax(smax.data_ptr(), group.data_ptr(), num, window, w.data_ptr(), N.data_ptr(), G, npr,
+                        pm.data_ptr(), _stream(stream)), "perc_pmax")
+    return pm
 
 
 def check(ws: Workspace | None = None, stream=None) -> int:

@@ -14,7 +14,8 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for must in ("perc_rank", "perc_nstar", "perc_mass", "perc_workspace_bytes", "perc_check",
+    for must in ("perc_rank", "perc_nstar", "perc_mass", "perc_smax_window", "perc_binomial_weights", "perc_pmax",
+                 "perc_workspace_bytes", "perc_check",
                  "perc_status_string", "perc_bracket", "perc_mlp_train"):
         assert must in names
 
@@ -46,6 +47,13 @@ def test_host_side_argument_checks_without_gpu():
     assert lib.perc_rank(74, 1, 1, 1, 1, 1, 1 << 30, None) == -1
     assert lib.perc_nstar(None, 1, 8, None, None, None, None, None, 0, None) == -1
     assert lib.perc_mass(None, 1, 8, None, None, None, 0, None) == -1
+    assert lib.perc_smax_window(None, 1, 8, 1, None, 4, 1, 1, 1, None) == -1
+    assert lib.perc_smax_window(1, 1, 8, 1, None, 0, 1, 1, 1, None) == -1  # empty window
+    assert lib.perc_smax_window(1, 1 << 20, 8, 1, None, 1 << 21, 1, 1, 1, None) == -1  # output over 2^40
+    assert lib.perc_binomial_weights(None, 1, 1, 1, 1, 1, 1, None) == -1
+    assert lib.perc_binomial_weights(1, 1, 1, 0, 1, 1, 1, None) == -1
+    assert lib.perc_pmax(1, 1, 0, 1, 1, 1, 1, 1, 1, None) == -1
+    assert lib.perc_pmax(1, None, 1, 1, 1, 1, 1, 1, 1, None) == -1
     assert lib.perc_workspace_bytes(7, 8, 1) == 0
     assert lib.perc_workspace_bytes(1, 0, 1) == 0
     assert lib.perc_workspace_bytes(1, 8, 1) > 8 * 8 ** 5

@@ -92,3 +92,9 @@ def test_zeta_single_zone_closed_form():
     for z in range(1, 8):
         n = len(oracle.zone_offsets(z))
         assert math.isclose(oracle.mask_z_zeta(1 << (z - 1))[1], n * math.sqrt(z))
+
+
+def test_workload_table1_matches_golden():
+    """The p grid of the P_max workload is centred on the same (corrected) Table I p_c."""
+    from paper_2607_18991_b300 import workloads
+    assert {m: pc for (_, m, _, _, pc) in corrected_table1()} == workloads.TABLE1_PC
