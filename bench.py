@@ -14,7 +14,8 @@ rank 0 prints one JSON line.  `--impl reference` times the CPU oracle on the sam
 
 `--workload pmax` measures the P_max(p) path instead: one step = perc_rank of the seeds, the
 binomial weights of 16 probabilities per neighborhood (p_c of Table I, +-2%), S_max(n) over the
-+-12-deviation window of n of every sample, and the convolution to P_max(p) (eq. Pmax).
+window of n outside which each binomial has less than 1e-16 on either side, and the convolution to
+P_max(p) (eq. Pmax).
 """
 from __future__ import annotations
 
@@ -36,8 +37,8 @@ L = 16
 NUM_SEEDS = 256
 MASKS = list(range(1, 128))
 METRIC = "samples/sec (exact n*) at L=16 over 127 neighborhoods, learned vs plain bracket"
-PMAX_METRIC = ("samples/sec of P_max(p) curves (exact S_max(n) over +-12-deviation windows, binomial "
-               "convolution at 16 p per neighborhood) at L=16 over 127 neighborhoods")
+PMAX_METRIC = ("samples/sec of P_max(p) curves (exact S_max(n) over the windows of n holding all but 1e-16 of "
+               "each binomial, convolution at 16 p per neighborhood) at L=16 over 127 neighborhoods")
 
 
 def dist_env():
@@ -73,7 +74,8 @@ def _oracle_pmax_seed(seed: int) -> int:
     perm, rk = oracle.rank(L, seed)
     for m in MASKS:
         ps = workloads.pmax_grid(m)
-        n_stop = int(min(N, math.ceil(N * ps.max() + 12.0 * math.sqrt(N * ps.max() * (1 - ps.max())))))
+        mu, a = N * ps.max(), -math.log(1e-16)  # Bernstein: P(X >= mu + t) <= exp(-t^2 / (2 (mu + t/3)))
+        n_stop = int(min(N, math.ceil(mu + (2 * a / 3 + math.sqrt((2 * a / 3) ** 2 + 8 * a * mu)) / 2)))
         pre = oracle.smax_prefix(L, m, perm, rk, n_stop).astype(np.float64)
         for q in ps:
             w = oracle.binomial_weights(N, float(q))
@@ -560,7 +562,7 @@ def run_pmax_ours(args):
 
     # ---- e2e through the C ABI from pinned host buffers
     host = {k: getattr(st, k).cpu().pin_memory() for k in ("seeds_dev", "samples", "n_lo", "cnt", "group_dev",
-                                                            "Ng_dev", "lo_dev", "pg_dev")}
+                                                            "Ng_dev", "lo_dev", "pg_dev", "count_dev")}
     dev2 = {k: torch.empty_like(getattr(st, k)) for k in host}
     pm_host = torch.empty_like(st.pmax, device="cpu").pin_memory()
 
@@ -569,14 +571,15 @@ def run_pmax_ours(args):
             dev2[k].copy_(host[k], non_blocking=True)
         perc._ok(lib.perc_rank(L, dev2["seeds_dev"].data_ptr(), len(seeds), st.perm.data_ptr(), st.rank.data_ptr(),
                                st.ws.data_ptr(), st.ws.numel(), sp), "perc_rank")
-        perc._ok(lib.perc_binomial_weights(dev2["Ng_dev"].data_ptr(), dev2["lo_dev"].data_ptr(), st.G, st.window,
-                                           dev2["pg_dev"].data_ptr(), st.np, st.w.data_ptr(), sp),
-                 "perc_binomial_weights")
+        perc._ok(lib.perc_binomial_weights(dev2["Ng_dev"].data_ptr(), dev2["lo_dev"].data_ptr(),
+                                           dev2["count_dev"].data_ptr(), st.G, st.window, dev2["pg_dev"].data_ptr(),
+                                           st.np, st.w.data_ptr(), sp), "perc_binomial_weights")
         perc._ok(lib.perc_smax_window(dev2["samples"].data_ptr(), num, L, dev2["n_lo"].data_ptr(),
                                       dev2["cnt"].data_ptr(), st.window, st.smax.data_ptr(), st.ws.data_ptr(),
                                       st.ws.numel(), sp), "perc_smax_window")
         perc._ok(lib.perc_pmax(st.smax.data_ptr(), dev2["group_dev"].data_ptr(), num, st.window, st.w.data_ptr(),
-                               dev2["Ng_dev"].data_ptr(), st.G, st.np, st.pmax.data_ptr(), sp), "perc_pmax")
+                               dev2["Ng_dev"].data_ptr(), dev2["count_dev"].data_ptr(), st.G, st.np,
+                               st.pmax.data_ptr(), sp), "perc_pmax")
         pm_host.copy_(st.pmax, non_blocking=True)
 
     for _ in range(args.warmup):
@@ -636,8 +639,8 @@ def run_pmax_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32+f64", "data": "synthetic (Philox-keyed site orders, seeds per rank)",
             "config": {"workload": "P_max(p) curves, all 127 neighborhoods, L=16 (1,048,576 sites), seeds 1..256 "
-                                   "per rank, 16 p per neighborhood at Table I p_c (1 +- 2%), windows of +-12 "
-                                   "binomial deviations",
+                                   "per rank, 16 p per neighborhood at Table I p_c (1 +- 2%), windows of n "
+                                   "holding all but 1e-16 of each binomial",
                        "L": L, "masks": 127, "seeds_per_rank": int(len(seeds)), "samples_per_rank": num,
                        "p_per_sample": int(st.np), "window_max": int(st.window),
                        "window_mean": float(st.count[st.group].mean()),

@@ -164,13 +164,14 @@ int perc_smax_window(const perc_sample *samples, uint32_t num_samples, uint32_t 
  *   For group g (0 <= g < groups) and probability j (0 <= j < np):
  *   N      device uint64[groups]: sites L^5 of the group (1 <= N < 2^32)
  *   n_lo   device uint64[groups]: first n of the group's window
+ *   count  device uint32[groups] or NULL: entries of the group's window (NULL: all `window`)
  *   p      device double[groups][np], each in [0, 1] (otherwise the row is NaN)
- *   w      device double[groups][np][window] (output): w[g][j][k] = B(N[g], n_lo[g] + k, p[g][j]),
- *          0 where n_lo[g] + k > N[g]
+ *   w      device double[groups][np][window] (output): w[g][j][k] = B(N[g], n_lo[g] + k, p[g][j])
+ *          for k < count[g]; 0 where k >= count[g] or n_lo[g] + k > N[g]
  * Returns PERC_EINVAL for null pointers or a zero size.
  */
-int perc_binomial_weights(const uint64_t *N, const uint64_t *n_lo, uint32_t groups, uint32_t window,
-                          const double *p, uint32_t np, double *w, void *stream);
+int perc_binomial_weights(const uint64_t *N, const uint64_t *n_lo, const uint32_t *count, uint32_t groups,
+                          uint32_t window, const double *p, uint32_t np, double *w, void *stream);
 
 /*
  * perc_pmax -- P_max(p) = S_max(p) / L^5 with S_max(p) = sum_n B(N, n, p) S_max(n) over the window
@@ -181,10 +182,12 @@ int perc_binomial_weights(const uint64_t *N, const uint64_t *n_lo, uint32_t grou
  *   group   device uint32[num_samples]: weight group of each sample (< groups, else the row is NaN)
  *   w       device double[groups][np][window] from perc_binomial_weights
  *   N       device uint64[groups]: L^5 of each group
+ *   count   device uint32[groups] or NULL: entries summed per group (NULL: all `window`)
  *   pmax    device double[num_samples][np] (output), FP64 sums
  */
 int perc_pmax(const uint32_t *smax, const uint32_t *group, uint32_t num_samples, uint32_t window,
-              const double *w, const uint64_t *N, uint32_t groups, uint32_t np, double *pmax, void *stream);
+              const double *w, const uint64_t *N, const uint32_t *count, uint32_t groups, uint32_t np,
+              double *pmax, void *stream);
 
 /*
  * perc_nstar_noalloc -- perc_nstar without a caller-provided workspace, for callers that cannot

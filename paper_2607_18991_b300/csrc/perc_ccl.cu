@@ -1153,18 +1153,22 @@ constexpr uint32_t kRootBit = 0x80000000u;  // local union-find entry of a root:
 static_assert(kRecCap > kMaxOffsets && kRecCap < kRootHash && (kRootHash & (kRootHash - 1)) == 0,
               "record and hash capacities");
 
+constexpr uint32_t kRecSlot = 0xFFFFu;  // a record is (chunk site << 16) | local slot
+
 struct WinPtrs {
-    uint32_t *deg;   // [C] kept edges per chunk site, then the scatter cursor
-    uint32_t *ev;    // [C] S_max after each chunk site
-    uint32_t *lp;    // [C + kRootHash] local union-find: parent slot, or kRootBit | size
+    uint32_t *deg;   // [C] kept edges per chunk site, then the scatter cursor, then the site's component
+    uint32_t *ev;    // [C] size of the site's cluster right after it is added, then S_max after it
+    uint32_t *lp;    // [C + kRootHash] local union-find in time order: parent slot, or kRootBit | size
     uint32_t *hkey;  // [kRootHash] forest node of local slot C + h (kEmptySlot: free)
-    uint32_t *rec;   // [kRecCap] the earlier end of each kept edge, as a local slot
+    uint32_t *rec;   // [kRecCap] kept edges in site order: (chunk site << 16) | earlier end's local slot
     uint32_t *off;   // [C + 1] first record of each chunk site
+    uint32_t *cc;    // [C + kRootHash] components of the chunk's records, then per-component ranges
+    uint32_t *memb;  // [C] chunk sites grouped by component
 };
 
 __host__ __device__ inline size_t smem_window_bytes(uint32_t threads)
 {
-    return ((size_t(threads) * 4 + 1 + kRecCap + 2 * kRootHash) * 4 + 15) & ~size_t(15);
+    return ((size_t(threads) * 6 + 1 + kRecCap + 3 * kRootHash) * 4 + 15) & ~size_t(15);
 }
 
 __device__ __forceinline__ WinPtrs win_ptrs(unsigned char *at, uint32_t C)
@@ -1177,6 +1181,8 @@ __device__ __forceinline__ WinPtrs win_ptrs(unsigned char *at, uint32_t C)
     w.hkey = w.lp + C + kRootHash;
     w.rec = w.hkey + kRootHash;
     w.off = w.rec + kRecCap;
+    w.cc = w.off + C + 1;
+    w.memb = w.cc + C + kRootHash;
     return w;
 }
 
@@ -1207,6 +1213,108 @@ __device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t v, uint32_t *ws
     return (warp ? wsum[warp - 1u] : 0u) + x - v;
 }
 
+// Inclusive running maximum of v over the block's threads; uses wsum[32] and two block barriers.
+__device__ __forceinline__ uint32_t block_inclusive_max(uint32_t v, uint32_t *wsum)
+{
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= static_cast<uint32_t>(o)) x = max(x, y);
+    }
+    if (lane == 31u) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0u) {
+        uint32_t t = lane < nw ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= static_cast<uint32_t>(o)) t = max(t, y);
+        }
+        if (lane < nw) wsum[lane] = t;
+    }
+    __syncthreads();
+    return warp ? max(wsum[warp - 1u], x) : x;
+}
+
+
+// Components of the chunk's records: lock-free union-find on shared memory, the larger root hooked
+// under the smaller, so a component's root is its smallest slot (a chunk site, since earlier roots
+// have slots above C).
+__device__ __forceinline__ uint32_t cc_find(uint32_t *cc, uint32_t x)
+{
+    volatile uint32_t *v = cc;
+    for (;;) {
+        const uint32_t p = v[x];
+        if (p == x) return x;
+        const uint32_t g = v[p];
+        if (g != p) v[x] = g;  // path halving: g is an ancestor of x
+        x = g;
+    }
+}
+
+__device__ __forceinline__ void cc_unite(uint32_t *cc, uint32_t a, uint32_t b)
+{
+    for (;;) {
+        a = cc_find(cc, a);
+        b = cc_find(cc, b);
+        if (a == b) return;
+        if (a > b) {
+            const uint32_t t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(cc + b, b, a) == b) return;
+    }
+}
+
+// Cluster size right after site t is added, for the sites of one local component in rank order
+// (their indices at shared address s_sites): union by size on the local slots from each site's
+// records.  Shared-memory addresses throughout; the next site's indices are loaded ahead.
+__device__ __forceinline__ void replay_sites(uint32_t s_lp, uint32_t s_rec, uint32_t s_off, uint32_t s_ev,
+                                             uint32_t s_sites, uint32_t nsites, uint32_t C, int *status)
+{
+    uint32_t t = nsites ? lds_u32(s_sites) : 0u;
+    for (uint32_t i = 0; i < nsites; ++i) {
+        const uint32_t k0 = lds_u32(s_off + 4u * t), k1 = lds_u32(s_off + 4u * t + 4u);
+        const uint32_t t_next = i + 1u < nsites ? lds_u32(s_sites + 4u * i + 4u) : 0u;
+        uint32_t ra = t, sa = 1u;  // no earlier record names site t: it starts alone
+        for (uint32_t k = k0; k < k1; ++k) {
+            const uint32_t bs = lds_u32(s_rec + 4u * k) & kRecSlot;
+            if (bs >= C + kRootHash) {  // full hash (ruled out by the capacities)
+                set_status(status, PERC_EDEVICE);
+                continue;
+            }
+            // root xr of bs (path halving) and its entry v = kRootBit | size
+            uint32_t xr = bs, v = lds_u32(s_lp + 4u * bs);
+            while (!(v & kRootBit)) {
+                const uint32_t g = lds_u32(s_lp + 4u * v);
+                if (g & kRootBit) {
+                    xr = v;
+                    v = g;
+                    break;
+                }
+                sts_u32(s_lp + 4u * xr, g);
+                xr = g;
+                v = lds_u32(s_lp + 4u * g);
+            }
+            if (xr == ra) continue;
+            const uint32_t sb = v & ~kRootBit;
+            if (sa >= sb) {
+                sts_u32(s_lp + 4u * xr, ra);
+            } else {
+                sts_u32(s_lp + 4u * ra, xr);
+                ra = xr;
+            }
+            sa += sb;
+            sts_u32(s_lp + 4u * ra, kRootBit | sa);
+        }
+        sts_u32(s_ev + 4u * t, sa);
+        t = t_next;
+    }
+}
+
 // Root of local slot x (read only).
 __device__ __forceinline__ uint32_t local_root(const uint32_t *lp, uint32_t x)
 {
@@ -1214,19 +1322,6 @@ __device__ __forceinline__ uint32_t local_root(const uint32_t *lp, uint32_t x)
         const uint32_t v = lp[x];
         if (v & kRootBit) return x;
         x = v;
-    }
-}
-
-// Root of local slot x with path halving (the replay thread only).
-__device__ __forceinline__ uint32_t local_find(uint32_t *lp, uint32_t x)
-{
-    for (;;) {
-        const uint32_t v = lp[x];
-        if (v & kRootBit) return x;
-        const uint32_t g = lp[v];
-        if (g & kRootBit) return v;
-        lp[x] = g;
-        x = g;
     }
 }
 
@@ -1351,37 +1446,62 @@ __device__ void smax_sample(Ctl &c, SmaxShared &x, const Nodes &P, uint32_t *cnt
             const uint2 ed = edge_get(E, e);
             if (ed.x >= tn) continue;  // dropped, or past the cut
             const uint32_t pos = wp.off[ed.x] + atomicAdd(wp.deg + ed.x, 1u);
-            wp.rec[pos] = ed.y >= b ? ed.y - b : root_slot(wp, cnt, uf_find(P, ed.y + 2u, 0u), C);
+            const uint32_t slot = ed.y >= b ? ed.y - b : root_slot(wp, cnt, uf_find(P, ed.y + 2u, 0u), C);
+            wp.rec[pos] = (ed.x << 16) | (slot & kRecSlot);
+        }
+        const uint32_t nrec = wp.off[tn];
+        for (uint32_t y = threadIdx.x; y < C + kRootHash; y += C) wp.cc[y] = y;
+        __syncthreads();
+        // replay: the clusters a chunk builds only interact inside a component of its records, so
+        // every component is replayed on its own (in rank order) and S_max after site t is the
+        // running maximum over the chunk of the sizes reached so far.
+        for (uint32_t k = threadIdx.x; k < nrec; k += C) {
+            const uint32_t r = wp.rec[k], s2 = r & kRecSlot;
+            if (s2 < C + kRootHash) cc_unite(wp.cc, r >> 16, s2);
         }
         __syncthreads();
-        // replay
-        if (threadIdx.x == 0) {
-            uint32_t smax = x.run_max;
-            for (uint32_t t = 0; t < tn; ++t) {
-                uint32_t ra = t, sa = 1u;  // no earlier record names site t: it starts alone
-                const uint32_t k1 = wp.off[t + 1u];
-                for (uint32_t k = wp.off[t]; k < k1; ++k) {
-                    const uint32_t bs = wp.rec[k];
-                    if (bs >= C + kRootHash) {  // full hash (ruled out by the capacities)
-                        set_status(status, PERC_EDEVICE);
-                        continue;
+        const uint32_t comp = threadIdx.x < tn ? cc_find(wp.cc, threadIdx.x) : 0u;
+        __syncthreads();
+        for (uint32_t y = threadIdx.x; y < C + kRootHash; y += C) wp.cc[y] = 0u;
+        __syncthreads();
+        if (threadIdx.x < tn) atomicAdd(wp.cc + comp, 1u);
+        __syncthreads();
+        // ranges of the components (roots are chunk sites, so the first tn counts suffice), then the
+        // sites grouped by component, warp after warp so that each component keeps rank order
+        const uint32_t own = threadIdx.x < tn ? wp.cc[threadIdx.x] : 0u;
+        uint32_t tot;
+        const uint32_t start = block_exclusive_sum(own, x.red, tot);
+        if (threadIdx.x < tn) wp.cc[threadIdx.x] = start;
+        __syncthreads();
+        {
+            const uint32_t lane = threadIdx.x & 31u, key = threadIdx.x < tn ? comp : kEmptySlot;
+            const uint32_t peers = __match_any_sync(0xffffffffu, key);
+            const uint32_t lead = __ffs(peers) - 1u;
+            const uint32_t before = __popc(peers & ((1u << lane) - 1u));
+            for (uint32_t w = 0; w * 32u < tn; ++w) {
+                if ((threadIdx.x >> 5) == w) {
+                    uint32_t base = 0u;
+                    if (lane == lead && key != kEmptySlot) base = wp.cc[key];
+                    base = __shfl_sync(0xffffffffu, base, lead);
+                    if (key != kEmptySlot) {
+                        wp.memb[base + before] = threadIdx.x;
+                        if (lane == lead) wp.cc[key] = base + __popc(peers);
                     }
-                    const uint32_t rb = local_find(wp.lp, bs);
-                    if (rb == ra) continue;
-                    const uint32_t sb = wp.lp[rb] & ~kRootBit;
-                    if (sa >= sb) {
-                        wp.lp[rb] = ra;
-                    } else {
-                        wp.lp[ra] = rb;
-                        ra = rb;
-                    }
-                    sa += sb;
-                    wp.lp[ra] = kRootBit | sa;
                 }
-                smax = max(smax, sa);
-                wp.ev[t] = smax;
+                __syncthreads();
             }
-            x.run_max = smax;
+        }
+        if (threadIdx.x < tn && own > 0u) {  // this site is the root of its component: replay it
+            auto sa = [](const uint32_t *q) { return static_cast<uint32_t>(__cvta_generic_to_shared(q)); };
+            replay_sites(sa(wp.lp), sa(wp.rec), sa(wp.off), sa(wp.ev), sa(wp.memb) + 4u * start, own, C, status);
+        }
+        __syncthreads();
+        {
+            const uint32_t v = threadIdx.x < tn ? wp.ev[threadIdx.x] : 0u;
+            const uint32_t run = max(block_inclusive_max(v, x.red), x.run_max);
+            if (threadIdx.x < tn) wp.ev[threadIdx.x] = run;
+            __syncthreads();  // every thread has read x.run_max
+            if (threadIdx.x == tn - 1u) x.run_max = run;
         }
         __syncthreads();
         // apply: chunk sites point at their root's forest node, hooked earlier roots likewise
@@ -1524,12 +1644,15 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool
     // registers a thread); each CTA takes an equal share.  What the tables and the bitmap leave
     // goes to union-find nodes (up to kSmemNodes, keeping room for 512 edges) and then to the
     // shared part of the edge list.
-    const size_t base = smem_tables_bytes() + smem_bitmap_bytes(cfg.smem_L) +
-                        (op == PERC_OP_SMAX ? smem_window_bytes(cfg.threads) : 0);
+    const size_t extra = op == PERC_OP_SMAX ? smem_window_bytes(cfg.threads) : 0;
+    size_t base = smem_tables_bytes() + smem_bitmap_bytes(cfg.smem_L) + extra;
     const size_t min_edges = size_t(kRowCand) * sizeof(uint32_t);  // table-building scratch
     int ctas = (65536 / (cfg.threads * 64)) > 0 ? 65536 / (cfg.threads * 64) : 1;
     while (ctas > 1 && size_t(optin) / ctas - 1024 < base + min_edges) --ctas;  // fewer, larger CTAs
     const size_t share = size_t(optin) / ctas - 1024;  // room for the static shared variables
+    // a lattice whose bitmap does not fit beside the op's own arrays keeps it in global memory
+    while (cfg.smem_L > 1 && base + min_edges > share)
+        base = smem_tables_bytes() + smem_bitmap_bytes(--cfg.smem_L) + extra;
     if (base + min_edges > share) return PERC_EINVAL;
     size_t room = share - base;
     size_t nodes = room > 512 * sizeof(uint2) ? (room - 512 * sizeof(uint2)) / 4 : 0;

@@ -73,8 +73,8 @@ __device__ double binomial_pmf(double N, double n, double p)
 }
 
 __global__ void k_binomial_weights(const uint64_t *__restrict__ Ng, const uint64_t *__restrict__ n_lo,
-                                   uint32_t groups, uint32_t window, const double *__restrict__ p, uint32_t np,
-                                   double *__restrict__ w)
+                                   const uint32_t *__restrict__ count, uint32_t groups, uint32_t window,
+                                   const double *__restrict__ p, uint32_t np, double *__restrict__ w)
 {
     const uint64_t total = uint64_t(groups) * np * window;
     for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < total;
@@ -83,7 +83,8 @@ __global__ void k_binomial_weights(const uint64_t *__restrict__ Ng, const uint64
         const uint32_t k = static_cast<uint32_t>(i - row * window);
         const uint32_t g = static_cast<uint32_t>(row / np);
         const uint64_t N = Ng[g], n = n_lo[g] + k;
-        w[i] = (N == 0 || n > N) ? 0.0 : binomial_pmf(double(N), double(n), p[row]);
+        const bool skip = N == 0 || n > N || (count && k >= count[g]);
+        w[i] = skip ? 0.0 : binomial_pmf(double(N), double(n), p[row]);
     }
 }
 
@@ -93,8 +94,8 @@ constexpr int kPmaxTile = 8;  // probabilities summed together per pass over a s
 // One block per sample: pmax[s][j] = sum_k w[g][j][k] smax[s][k] / N[g].
 __global__ void __launch_bounds__(kPmaxThreads)
 k_pmax(const uint32_t *__restrict__ smax, const uint32_t *__restrict__ group, uint32_t num, uint32_t window,
-       const double *__restrict__ w, const uint64_t *__restrict__ Ng, uint32_t groups, uint32_t np,
-       double *__restrict__ pmax)
+       const double *__restrict__ w, const uint64_t *__restrict__ Ng, const uint32_t *__restrict__ count,
+       uint32_t groups, uint32_t np, double *__restrict__ pmax)
 {
     __shared__ double red[kPmaxTile][kPmaxThreads / 32];
     for (uint32_t s = blockIdx.x; s < num; s += gridDim.x) {
@@ -106,12 +107,13 @@ k_pmax(const uint32_t *__restrict__ smax, const uint32_t *__restrict__ group, ui
             continue;
         }
         const double invN = 1.0 / double(Ng[g]);
+        const uint32_t len = count ? min(count[g], window) : window;
         for (uint32_t j0 = 0; j0 < np; j0 += kPmaxTile) {
             double acc[kPmaxTile];
 #pragma unroll
             for (int t = 0; t < kPmaxTile; ++t) acc[t] = 0.0;
             const double *wg = w + (size_t(g) * np + j0) * window;
-            for (uint32_t k = threadIdx.x; k < window; k += blockDim.x) {
+            for (uint32_t k = threadIdx.x; k < len; k += blockDim.x) {
                 const double v = double(__ldg(row + k));
 #pragma unroll
                 for (int t = 0; t < kPmaxTile; ++t)
@@ -138,8 +140,8 @@ k_pmax(const uint32_t *__restrict__ smax, const uint32_t *__restrict__ group, ui
 
 using namespace perc;
 
-extern "C" int perc_binomial_weights(const uint64_t *N, const uint64_t *n_lo, uint32_t groups, uint32_t window,
-                                     const double *p, uint32_t np, double *w, void *stream_)
+extern "C" int perc_binomial_weights(const uint64_t *N, const uint64_t *n_lo, const uint32_t *count, uint32_t groups,
+                                     uint32_t window, const double *p, uint32_t np, double *w, void *stream_)
 {
     if (!N || !n_lo || !p || !w || groups == 0 || window == 0 || np == 0) return PERC_EINVAL;
     const uint64_t total = uint64_t(groups) * np * window;
@@ -150,12 +152,13 @@ extern "C" int perc_binomial_weights(const uint64_t *N, const uint64_t *n_lo, ui
     const uint64_t cap = uint64_t(sms) * 8;
     if (blocks > cap) blocks = cap;
     k_binomial_weights<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream_)>>>(
-        N, n_lo, groups, window, p, np, w);
+        N, n_lo, count, groups, window, p, np, w);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }
 
 extern "C" int perc_pmax(const uint32_t *smax, const uint32_t *group, uint32_t num_samples, uint32_t window,
-                         const double *w, const uint64_t *N, uint32_t groups, uint32_t np, double *pmax, void *stream_)
+                         const double *w, const uint64_t *N, const uint32_t *count, uint32_t groups, uint32_t np,
+                         double *pmax, void *stream_)
 {
     if (!smax || !group || !w || !N || !pmax || num_samples == 0 || window == 0 || groups == 0 || np == 0)
         return PERC_EINVAL;
@@ -166,6 +169,6 @@ extern "C" int perc_pmax(const uint32_t *smax, const uint32_t *group, uint32_t n
     const uint32_t cap = static_cast<uint32_t>(sms) * 8u;
     if (blocks > cap) blocks = cap;
     k_pmax<<<blocks, kPmaxThreads, 0, static_cast<cudaStream_t>(stream_)>>>(smax, group, num_samples, window, w, N,
-                                                                            groups, np, pmax);
+                                                                            count, groups, np, pmax);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }

@@ -132,21 +132,35 @@ def smax_window(workload, n_lo, window: int, budget: int = DEFAULT_BUDGET):
     return out
 
 
-def pmax_windows(L, p, sigmas: float = 12.0):
+def binomial_tail_halfwidths(mu, tail: float = 1e-16):
+    """(below, above): distances from the mean mu = N p beyond which Binomial(N, p) puts less than
+    `tail` on each side, from the Chernoff bound P(X <= mu - t) <= exp(-t^2 / (2 mu)) and
+    Bernstein's P(X >= mu + t) <= exp(-t^2 / (2 (mu + t / 3))) (variance below mu)."""
+    mu = np.asarray(mu, dtype=np.float64)
+    a = -np.log(tail)
+    below = np.sqrt(2.0 * a * mu)
+    above = (2.0 * a / 3.0 + np.sqrt((2.0 * a / 3.0) ** 2 + 8.0 * a * mu)) / 2.0
+    return below, above
+
+
+def pmax_windows(L, p, tail: float = 1e-16):
     """Weight groups and windows for P_max at probabilities p[k, :] of samples with sides L[k].
 
     Samples with the same side and the same row of probabilities form one group; its window of n
-    runs from N p_min - sigmas * s to N p_max + sigmas * s (s the largest binomial standard
-    deviation sqrt(N p (1 - p)) of the row), clipped to [0, N].  Returns (group[k], N[g],
-    n_lo[g], count[g], p[g, :], window): count[g] values of n from n_lo[g], window = max count."""
+    runs from the lower tail bound of its smallest p to the upper tail bound of its largest p
+    (`binomial_tail_halfwidths`: less than `tail` of each binomial lies outside), clipped to
+    [0, N].  Returns (group[k], N[g], n_lo[g], count[g], p[g, :], window): count[g] values of n
+    from n_lo[g], window = max count."""
     L = np.asarray(L, dtype=np.int64).reshape(-1)
     p = np.asarray(p, dtype=np.float64).reshape(len(L), -1)
     keys, group = np.unique(np.hstack([L[:, None].astype(np.float64), p]), axis=0, return_inverse=True)
     Ng = keys[:, 0].astype(np.int64) ** 5
     pg = keys[:, 1:]
-    sd = np.sqrt(Ng[:, None] * pg * (1.0 - pg)).max(axis=1)
-    lo = np.clip(np.floor(Ng * pg.min(axis=1) - sigmas * sd), 0, Ng).astype(np.int64)
-    hi = np.clip(np.ceil(Ng * pg.max(axis=1) + sigmas * sd), 0, Ng).astype(np.int64)
+    mu_lo, mu_hi = Ng * pg.min(axis=1), Ng * pg.max(axis=1)
+    below, _ = binomial_tail_halfwidths(mu_lo, tail)
+    _, above = binomial_tail_halfwidths(mu_hi, tail)
+    lo = np.clip(np.floor(mu_lo - below), 0, Ng).astype(np.int64)
+    hi = np.clip(np.ceil(mu_hi + above), 0, Ng).astype(np.int64)
     count = hi - lo + 1
     return group.astype(np.int64).reshape(-1), Ng, lo, count, pg, int(count.max())
 
@@ -154,32 +168,33 @@ def pmax_windows(L, p, sigmas: float = 12.0):
 class PmaxPlan:
     """Device inputs of one P_max computation: groups, windows and the binomial weights."""
 
-    def __init__(self, workload, p, sigmas: float = 12.0):
+    def __init__(self, workload, p, tail: float = 1e-16):
         self.workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
         self.p = np.asarray(p, dtype=np.float64).reshape(len(self.workload), -1)
         self.group, self.Ng, self.lo, self.count, self.pg, self.window = pmax_windows(
-            self.workload[:, 0], self.p, sigmas)
+            self.workload[:, 0], self.p, tail)
         self.Ng_t = torch.as_tensor(self.Ng, device="cuda")
+        self.count_t = torch.as_tensor(self.count.astype(np.int32), device="cuda")
         self.w = perc.binomial_weights(self.Ng_t, torch.as_tensor(self.lo, device="cuda"), self.window,
-                                       torch.as_tensor(self.pg, device="cuda"))
+                                       torch.as_tensor(self.pg, device="cuda"), count=self.count_t)
         # weight mass inside each group's own window (S_max is computed there only)
         k = torch.arange(self.window, device="cuda")
         inside = k[None, None, :] < torch.as_tensor(self.count, device="cuda")[:, None, None]
         self.mass_g = (self.w * inside).sum(dim=2).cpu().numpy()
 
 
-def pmax(workload, p, sigmas: float = 12.0, budget: int = DEFAULT_BUDGET):
+def pmax(workload, p, tail: float = 1e-16, budget: int = DEFAULT_BUDGET):
     """P_max(p) = S_max(p) / L^5 (eq. Pmax with the binomial convolution) for every row of
     `workload` at its probabilities p[k, :].  Returns (pmax float64 [num, np], weight mass of each
     sample's window float64 [num, np]; 1 - mass bounds the neglected part)."""
-    plan = PmaxPlan(workload, p, sigmas)
+    plan = PmaxPlan(workload, p, tail)
     ws = perc.default_workspace()
     out = np.zeros(plan.p.shape, dtype=np.float64)
     for pr in iter_prepared(plan.workload, budget, ws):
         g = plan.group[pr.idx]
         sm = perc.smax_window(pr.samples, pr.max_L, torch.as_tensor(plan.lo[g]), plan.window,
                               count=torch.as_tensor(plan.count[g]), ws=ws)
-        pm = perc.pmax(sm, torch.as_tensor(g, device="cuda"), plan.w, plan.Ng_t)
+        pm = perc.pmax(sm, torch.as_tensor(g, device="cuda"), plan.w, plan.Ng_t, count=plan.count_t)
         out[pr.idx] = pm.cpu().numpy()
         rc = perc.check(ws)
         if rc != 0:
@@ -296,7 +311,7 @@ class PmaxStep:
     Every device buffer is allocated here, so ``run`` only enqueues library calls on the stream.
     Samples are seed-major; the weight groups are the masks (one row of p per mask)."""
 
-    def __init__(self, L: int, masks, seeds, p_of_mask: dict, sigmas: float = 12.0):
+    def __init__(self, L: int, masks, seeds, p_of_mask: dict, tail: float = 1e-16):
         self.L = int(L)
         self.masks = np.asarray(list(masks), dtype=np.int64)
         self.seeds = np.asarray(list(seeds), dtype=np.int64)
@@ -306,7 +321,7 @@ class PmaxStep:
         self.num = len(self.workload)
         p = np.array([p_of_mask[int(m)] for m in self.workload[:, 1]], dtype=np.float64)
         self.group, self.Ng, self.lo, self.count, self.pg, self.window = pmax_windows(
-            self.workload[:, 0], p, sigmas)
+            self.workload[:, 0], p, tail)
         self.np = self.pg.shape[1]
         self.G = len(self.Ng)
         self.seeds_dev = torch.as_tensor(self.seeds, device="cuda")
@@ -317,6 +332,7 @@ class PmaxStep:
         self.n_lo = torch.as_tensor(self.lo[self.group], device="cuda")
         self.cnt = torch.as_tensor(self.count[self.group].astype(np.int32), device="cuda")
         self.group_dev = torch.as_tensor(self.group.astype(np.int32), device="cuda")
+        self.count_dev = torch.as_tensor(self.count.astype(np.int32), device="cuda")
         self.Ng_dev = torch.as_tensor(self.Ng, device="cuda")
         self.lo_dev = torch.as_tensor(self.lo, device="cuda")
         self.pg_dev = torch.as_tensor(self.pg, device="cuda")
@@ -333,9 +349,10 @@ class PmaxStep:
                  "perc_rank")
 
     def run_weights(self, stream=None):
-        perc._ok(self.lib.perc_binomial_weights(self.Ng_dev.data_ptr(), self.lo_dev.data_ptr(), self.G, self.window,
-                                                self.pg_dev.data_ptr(), self.np, self.w.data_ptr(),
-                                                perc._stream(stream)), "perc_binomial_weights")
+        perc._ok(self.lib.perc_binomial_weights(self.Ng_dev.data_ptr(), self.lo_dev.data_ptr(),
+                                                self.count_dev.data_ptr(), self.G, self.window, self.pg_dev.data_ptr(),
+                                                self.np, self.w.data_ptr(), perc._stream(stream)),
+                 "perc_binomial_weights")
 
     def run_smax(self, stream=None):
         perc._ok(self.lib.perc_smax_window(self.samples.data_ptr(), self.num, self.L, self.n_lo.data_ptr(),
@@ -344,8 +361,8 @@ class PmaxStep:
 
     def run_pmax(self, stream=None):
         perc._ok(self.lib.perc_pmax(self.smax.data_ptr(), self.group_dev.data_ptr(), self.num, self.window,
-                                    self.w.data_ptr(), self.Ng_dev.data_ptr(), self.G, self.np, self.pmax.data_ptr(),
-                                    perc._stream(stream)), "perc_pmax")
+                                    self.w.data_ptr(), self.Ng_dev.data_ptr(), self.count_dev.data_ptr(), self.G,
+                                    self.np, self.pmax.data_ptr(), perc._stream(stream)), "perc_pmax")
 
     def run(self, stream=None):
         self.run_rank(stream)

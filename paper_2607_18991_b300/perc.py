@@ -50,8 +50,8 @@ def lib() -> ctypes.CDLL:
         "perc_nstar_noalloc": (i32, [vp, u32, u32, vp, vp, vp, vp, vp]),
         "perc_mass": (i32, [vp, u32, u32, vp, vp, vp, sz, vp]),
         "perc_smax_window": (i32, [vp, u32, u32, vp, vp, u32, vp, vp, sz, vp]),
-        "perc_binomial_weights": (i32, [vp, vp, u32, u32, vp, u32, vp, vp]),
-        "perc_pmax": (i32, [vp, vp, u32, u32, vp, vp, u32, u32, vp, vp]),
+        "perc_binomial_weights": (i32, [vp, vp, vp, u32, u32, vp, u32, vp, vp]),
+        "perc_pmax": (i32, [vp, vp, u32, u32, vp, vp, vp, u32, u32, vp, vp]),
         "perc_check": (i32, [vp, vp]),
         "perc_set_launch_option": (i32, [i32, i32]),
         "perc_mlp_forward": (i32, [vp, vp, u32, vp, vp]),
@@ -237,29 +237,34 @@ def smax_window(samples: torch.Tensor, max_L: int, n_lo: torch.Tensor, window: i
 
 
 def binomial_weights(N: torch.Tensor, n_lo: torch.Tensor, window: int, p: torch.Tensor,
-                     stream=None, out=None) -> torch.Tensor:
-    """B(N[g], n_lo[g] + k, p[g, j]) as float64 [groups, np, window]."""
+                     count: torch.Tensor | None = None, stream=None, out=None) -> torch.Tensor:
+    """B(N[g], n_lo[g] + k, p[g, j]) for k < count[g] (all k < window when count is None), as
+    float64 [groups, np, window] (0 elsewhere)."""
     N = N.to(device="cuda", dtype=torch.int64).contiguous()
     n_lo = n_lo.to(device="cuda", dtype=torch.int64).contiguous()
     p = p.to(device="cuda", dtype=torch.float64).contiguous()
+    if count is not None:
+        count = count.to(device="cuda", dtype=torch.int32).contiguous()
     G, npr = p.shape
     w = out if out is not None else torch.empty((G, npr, window), dtype=torch.float64, device="cuda")
-    _ok(lib().perc_binomial_weights(N.data_ptr(), n_lo.data_ptr(), G, window, p.data_ptr(), npr, w.data_ptr(),
-                                    _stream(stream)), "perc_binomial_weights")
+    _ok(lib().perc_binomial_weights(N.data_ptr(), n_lo.data_ptr(), _ptr(count), G, window, p.data_ptr(), npr,
+                                    w.data_ptr(), _stream(stream)), "perc_binomial_weights")
     return w
 
 
-def pmax(smax: torch.Tensor, group: torch.Tensor, w: torch.Tensor, N: torch.Tensor, stream=None,
-         out=None) -> torch.Tensor:
+def pmax(smax: torch.Tensor, group: torch.Tensor, w: torch.Tensor, N: torch.Tensor,
+         count: torch.Tensor | None = None, stream=None, out=None) -> torch.Tensor:
     """P_max(p) per (sample, p): float64 [num, np] from S_max windows and weight groups."""
     num, window = smax.shape
     G, npr, W = w.shape
     assert W == window
     group = group.to(device="cuda", dtype=torch.int32).contiguous()
     N = N.to(device="cuda", dtype=torch.int64).contiguous()
+    if count is not None:
+        count = count.to(device="cuda", dtype=torch.int32).contiguous()
     pm = out if out is not None else torch.empty((num, npr), dtype=torch.float64, device="cuda")
-    _ok(lib().perc_pmax(smax.data_ptr(), group.data_ptr(), num, window, w.data_ptr(), N.data_ptr(), G, npr,
-                        pm.data_ptr(), _stream(stream)), "perc_pmax")
+    _ok(lib().perc_pmax(smax.data_ptr(), group.data_ptr(), num, window, w.data_ptr(), N.data_ptr(), _ptr(count),
+                        G, npr, pm.data_ptr(), _stream(stream)), "perc_pmax")
     return pm
 
 

@@ -50,10 +50,10 @@ def test_host_side_argument_checks_without_gpu():
     assert lib.perc_smax_window(None, 1, 8, 1, None, 4, 1, 1, 1, None) == -1
     assert lib.perc_smax_window(1, 1, 8, 1, None, 0, 1, 1, 1, None) == -1  # empty window
     assert lib.perc_smax_window(1, 1 << 20, 8, 1, None, 1 << 21, 1, 1, 1, None) == -1  # output over 2^40
-    assert lib.perc_binomial_weights(None, 1, 1, 1, 1, 1, 1, None) == -1
-    assert lib.perc_binomial_weights(1, 1, 1, 0, 1, 1, 1, None) == -1
-    assert lib.perc_pmax(1, 1, 0, 1, 1, 1, 1, 1, 1, None) == -1
-    assert lib.perc_pmax(1, None, 1, 1, 1, 1, 1, 1, 1, None) == -1
+    assert lib.perc_binomial_weights(None, 1, None, 1, 1, 1, 1, 1, None) == -1
+    assert lib.perc_binomial_weights(1, 1, None, 1, 0, 1, 1, 1, None) == -1
+    assert lib.perc_pmax(1, 1, 0, 1, 1, 1, None, 1, 1, 1, None) == -1
+    assert lib.perc_pmax(1, None, 1, 1, 1, 1, None, 1, 1, 1, None) == -1
     assert lib.perc_workspace_bytes(7, 8, 1) == 0
     assert lib.perc_workspace_bytes(1, 0, 1) == 0
     assert lib.perc_workspace_bytes(1, 8, 1) > 8 * 8 ** 5

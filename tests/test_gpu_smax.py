@@ -141,6 +141,12 @@ def test_binomial_weights_edges():
     assert np.array_equal(w[0], [1, 0, 0, 0, 0, 0, 0, 0])
     assert np.array_equal(w[1], [0, 0, 0, 0, 0, 1, 0, 0])
     assert np.all(np.isnan(w[2][:6])) and np.all(np.isnan(w[3][:6]))
+    # count limits a group's entries; the rest of its rows is 0
+    p = torch.tensor([[0.3], [0.6]], dtype=torch.float64)
+    w = perc.binomial_weights(torch.tensor([20, 20]), torch.tensor([2, 5]), 10, p,
+                              count=torch.tensor([4, 10])).cpu().numpy()
+    assert np.all(w[0, 0, 4:] == 0.0) and np.all(w[0, 0, :4] > 0.0) and np.all(w[1, 0] > 0.0)
+    assert np.allclose(w[0, 0, :4], oracle.binomial_weights(20, 0.3)[2:6], rtol=1e-12)
 
 
 @pytest.mark.parametrize("L", [4, 6, 8])
@@ -161,7 +167,7 @@ def test_pmax_against_oracle(L):
 
 
 def test_pmax_full_size_L16_sampled():
-    """L = 16, all 127 neighborhoods, one seed: windows of +-12 binomial deviations around a
+    """L = 16, all 127 neighborhoods, one seed: windows holding all but 1e-16 of the binomials of a
     grid p0 (1 +- 5%), p0 = 1.5 / z of the neighborhood; P_max of a spread of masks checked against
     the oracle."""
     from paper_2607_18991_b300 import driver
