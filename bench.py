@@ -387,11 +387,16 @@ def run_ours(args):
     e2e_ms = max_over_ranks(e2e_ms)
     ms_nstar_learned = max_over_ranks(ms_nstar_learned)
 
-    # ---- roofline of the dominant kernel (k_nstar, learned arm): algorithmic bytes per pass
-    # = N/8 (bitmap write) + N/8 (bitmap read) + 4n (perm prefix) + 8n (labels) + 8 L^4 (faces)
-    #   + 8 E_n, summed over the passes of the launch (E_n = successful hooks)
-    alg_bytes = (st_learned["passes"] * (N / 8 * 2 + 8 * L ** 4) + 12 * st_learned["probe_sites"]
-                 + 8 * st_learned["hooks"])
+    # ---- roofline of the dominant kernel (the n* launch, learned arm).  Bisection: per pass at n,
+    # N/8 (bitmap write) + N/8 (bitmap read) + 4n (perm prefix) + 8n (labels) + 8 L^4 (faces) + 8 E_n,
+    # summed over the launch's passes (E_n = successful hooks).  Sweep: the same for one pass that
+    # reaches n* (each site and label once), per sample
+    sweep = st_learned["chunks"] > 0
+    if sweep:
+        alg_bytes = num * (N / 8 * 2 + 8 * L ** 4) + 12 * st_learned["new_sites"] + 8 * st_learned["hooks"]
+    else:
+        alg_bytes = (st_learned["passes"] * (N / 8 * 2 + 8 * L ** 4) + 12 * st_learned["probe_sites"]
+                     + 8 * st_learned["hooks"])
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -399,7 +404,7 @@ def run_ours(args):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     achieved = alg_bytes / (ms_nstar_learned * 1e-3) / 1e9
-    traffic = measured_traffic("learned_bytes_per_launch")
+    traffic = measured_traffic(("sweep_" if sweep else "") + "learned_bytes_per_launch")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -420,6 +425,7 @@ def run_ours(args):
                                    "32,512 samples/rank, one persistent launch",
                        "L": L, "masks": 127, "seeds_per_rank": int(len(seeds)), "samples_per_rank": num,
                        "bracket": "learned", "margin": args.margin,
+                       "method": "sweep (chunked Newman-Ziff replay)" if sweep else "bisection",
                        "l2": "flushed (256 MiB write) between timed steps; site orders 2 GiB > L2",
                        "parallelism": f"dp{world} (seed blocks, no collective)"},
             "plain": {"value": world * num / (ms_plain * 1e-3), "unit": "samples/s", "ms_per_step": ms_plain,
@@ -431,7 +437,7 @@ def run_ours(args):
                         "train_s": t_train, "train_loss_last": float(losses[-1].item())},
             "e2e": {"value": world * num / (e2e_ms * 1e-3), "unit": "samples/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "roofline": {"kernel": "k_nstar (learned)", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+            "roofline": {"kernel": ("k_nstar_sweep" if sweep else "k_nstar") + " (learned)", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                          "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                          "algorithmic_bytes_per_launch": alg_bytes, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
             "cpu_baseline": cpu,

@@ -75,13 +75,17 @@ typedef struct {
     unsigned long long verified;     /* learned brackets that passed verification */
     unsigned long long sites_merged; /* sites actually merged (early exits stop short) */
     unsigned long long unions;       /* union operations issued (edges of the NZ rule, borders included) */
-    unsigned long long cyc_setup;    /* SM cycles in per-sample setup (bitmap clear, neighborhood table) */
-    unsigned long long cyc_update;   /* SM cycles updating the bitmap and initialising new nodes */
-    unsigned long long cyc_union;    /* SM cycles in the union passes */
-    unsigned long long cyc_commit;   /* SM cycles reading span and undoing / committing hooks */
-    unsigned long long cyc_scan;     /* part of cyc_union: scanning neighborhoods into edge lists */
-    unsigned long long cyc_link;     /* part of cyc_union: rank lookups and unions of the edges */
-    unsigned long long reserved;
+    /* SM cycles (thread 0 of each CTA), bisection / sweep: */
+    unsigned long long cyc_setup;    /* per-sample setup (bitmap clear, neighborhood table) */
+    unsigned long long cyc_update;   /* updating the bitmap, initialising new nodes / the first pass */
+    unsigned long long cyc_union;    /* the union passes / - */
+    unsigned long long cyc_commit;   /* reading span, undoing or committing hooks / per-component
+                                        totals, write-back and replay of the chunks */
+    unsigned long long cyc_scan;     /* part of cyc_union: scanning neighborhoods into edge lists /
+                                        the chunks' bitmap update and scan */
+    unsigned long long cyc_link;     /* part of cyc_union: rank lookups and unions of the edges /
+                                        the chunks' filter, record placement, resolve, components */
+    unsigned long long chunks;       /* sweep method: chunks of sites after the first pass */
 } perc_stats;
 
 /*
@@ -105,16 +109,22 @@ int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, uint32_t *p
 
 /*
  * perc_nstar -- exact first spanning n per sample (Introduction: the spanning cluster appears
- * for the first time at the threshold; Methods: clusters of the first n sites).  Bisection over
- * n; every probe is one connected-component pass (union-find with hooking and pointer jumping)
- * over the occupied sites of the probe.
+ * for the first time at the threshold; Methods: clusters of the first n sites added in the
+ * Newman--Ziff order).  Two methods (PERC_OPT_METHOD), same results:
+ *   bisection  every probe n is one connected-component pass (union-find with hooking and pointer
+ *              jumping) over the first n sites; span(n) is monotone in n;
+ *   sweep      one pass over the sites below a start that does not span, then the sites in rank
+ *              order, in chunks, until the first site whose cluster touches both borders (the
+ *              Newman--Ziff sweep, chunk-parallel).
  *   samples     device perc_sample[num_samples]
  *   max_L       host bound on every sample's L (sizes the launch and the workspace)
  *   bracket     device uint32[num_samples][2] = (lo, hi) proposed by a model, or NULL for the plain
- *               bracket [1, L^5].  A bracket is verified (span(hi) and not span(lo-1)); one that
- *               fails, or is malformed, falls back to the plain bracket, so n* stays exact.
+ *               bracket [1, L^5].  A bracket is verified: bisection checks span(hi) and not
+ *               span(lo-1); the sweep starts at lo-1 after checking not span(lo-1) and needs no hi.
+ *               One that fails, or is malformed, falls back to the plain bracket, so n* stays exact.
  *   nstar       device uint32[num_samples] (output; PERC_NEVER when nothing spans)
  *   passes      device uint32[num_samples] (output, may be NULL): passes spent on each sample
+ *               (bisection probes; for the sweep, the first pass plus the chunks)
  *   stats       device perc_stats (accumulated, may be NULL)
  * Errors: PERC_EINVAL, PERC_EWORKSPACE, PERC_ECUDA; samples that fail the device check get
  * n* = PERC_NEVER and set PERC_EDEVICE in the status word.
@@ -194,7 +204,8 @@ int perc_pmax(const uint32_t *smax, const uint32_t *group, uint32_t num_samples,
  * allocate device memory (code that runs inside a framework which owns every device allocation,
  * or that must not allocate once a fixed memory budget is set).  The paper has no counterpart;
  * it is an entry point of this library only.
- *   Arguments and results are those of perc_nstar.  The scratch is a 64 MiB array that the
+ *   Arguments and results are those of perc_nstar with the bisection method (PERC_OPT_METHOD
+ *   does not apply: n* is the same, `passes` counts bisection probes).  The scratch is a 64 MiB array that the
  *   library keeps in device memory (every GPU that loads the library holds it until exit); the
  *   call allocates nothing.  The first call on a device looks the array's address up and should
  *   come before any stream capture.  Calls share the array: calls that may overlap on the GPU race
@@ -219,13 +230,16 @@ int perc_nstar_noalloc(const perc_sample *samples, uint32_t num_samples, uint32_
  *                        bitmap and union-find live in global memory); 0 = automatic (groups for
  *                        batches of lattices above L = 17 with fewer samples than CTAs), 1 = never,
  *                        2..64 = that many
- * Returns PERC_EINVAL for an unknown option or value.  Environment variable PERC_GROUP overrides
- * PERC_OPT_GROUP.
+ *   PERC_OPT_METHOD      perc_nstar's method: 0 = automatic (the sweep, unless the bisection would
+ *                        run cooperative groups), 1 = bisection, 2 = sweep
+ * Returns PERC_EINVAL for an unknown option or value.  Environment variables PERC_GROUP and
+ * PERC_METHOD override PERC_OPT_GROUP and PERC_OPT_METHOD.
  */
 #define PERC_OPT_THREADS 1
 #define PERC_OPT_SMEM_NODES 2
 #define PERC_OPT_MAX_CTAS 3
 #define PERC_OPT_GROUP 4
+#define PERC_OPT_METHOD 5
 int perc_set_launch_option(int option, int value);
 
 /*

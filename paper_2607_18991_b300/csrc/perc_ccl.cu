@@ -27,6 +27,7 @@
 //     probe is committed by clearing their tags.  Path halving never shortcuts a tagged edge of
 //     an old node, so the committed forest stays valid;
 //   * a spanning probe stops as soon as node 1 is hooked (early exit), since span is decided.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <mutex>
@@ -592,16 +593,17 @@ __host__ __device__ inline size_t smem_bitmap_bytes(uint32_t smem_L)
 
 __host__ __device__ inline size_t smem_nodes_bytes(uint32_t node_cap) { return (size_t(node_cap) * 4 + 15) & ~size_t(15); }
 
-// `extra` bytes (a multiple of 16) between the bitmap and the nodes belong to the caller.
+// `extra` bytes (a multiple of 16) between the nodes and the edge list belong to the caller (the
+// window arrays of k_smax and k_nstar_sweep, which also lend them to the first pass as more nodes).
 __device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn, uint32_t smem_L, uint32_t node_cap, size_t extra = 0)
 {
     SmemPtrs p;
     p.rows = reinterpret_cast<RowEntry *>(dyn);
     p.planes = reinterpret_cast<PlaneEntry *>(dyn + sizeof(RowEntry) * kRowCand);
     p.sbm = reinterpret_cast<uint32_t *>(dyn + smem_tables_bytes());
-    const size_t nodes_at = smem_tables_bytes() + smem_bitmap_bytes(smem_L) + extra;
+    const size_t nodes_at = smem_tables_bytes() + smem_bitmap_bytes(smem_L);
     p.nodes = reinterpret_cast<uint32_t *>(dyn + nodes_at);
-    p.edges = reinterpret_cast<uint2 *>(dyn + nodes_at + smem_nodes_bytes(node_cap));
+    p.edges = reinterpret_cast<uint2 *>(dyn + nodes_at + smem_nodes_bytes(node_cap) + extra);
     p.scratch = reinterpret_cast<uint32_t *>(p.edges);
     return p;
 }
@@ -1129,22 +1131,24 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
 
 // ------------------------------------------------------------------------------------------------
 // S_max(n) for every n of a window [n_lo, n_lo + W) (eq. Pmax; Methods, "Computational methods":
-// the Newman--Ziff sweep adds one site at a time and reads the largest cluster after each).
+// the Newman--Ziff sweep adds one site at a time and reads the largest cluster after each), and the
+// same sweep for n* (k_nstar_sweep, below).
 //
-// Per sample, one connected-component pass over the first n0 = min(n_lo, N) sites gives the forest
-// and, by counting, every cluster's size and S_max(n0).  The window's sites then follow in chunks
-// of up to blockDim sites:
-//   scan    -- each chunk site's occupied neighbors (bitmap through the chunk's last site) as edges;
-//   filter  -- an edge is kept when its neighbor came earlier (an edge belongs to its later site)
-//              and counted per site; a prefix sum places each site's records.  A chunk whose
-//              records would pass kRecCap is cut after the last site that fits, and the next chunk
-//              starts there;
-//   resolve -- a neighbor from before the chunk becomes the root of its cluster; every distinct
-//              root gets a local slot (shared-memory hash) that holds its size;
-//   replay  -- one thread adds the chunk's sites in rank order to a union-find over the local slots
-//              (union by size) and records the running maximum after each site: S_max at that n,
-//              since cluster sizes never shrink;
-//   apply   -- the chunk's merges and the new roots' sizes are written back to the forest.
+// Per sample, one connected-component pass over the first n0 sites gives the forest (and, for
+// S_max, every cluster's size by counting).  The next sites then follow in chunks of up to blockDim:
+//   scan       -- each chunk site's occupied neighbors (bitmap through the chunk) as edges;
+//   filter     -- an edge is kept when its neighbor came earlier (an edge belongs to its later site)
+//                 and counted per site; a prefix sum places each site's records.  A chunk whose
+//                 records would pass kRecCap is cut after the last site that fits;
+//   resolve    -- a neighbor from before the chunk becomes the root of its cluster; every distinct
+//                 root gets a local slot (shared-memory hash);
+//   components -- the records join sites and slots into local components (shared-memory
+//                 union-find); each component's total (size, or border flags) is summed and the
+//                 chunk is written back to the forest at once;
+//   replay     -- only a component that can change the result (S_max: its final size passes the
+//                 running maximum; n*: it touches both borders) is replayed by one thread in rank
+//                 order, union by size on the local slots, which gives the size (or flags) of the
+//                 new site's cluster right after each of its sites.
 // ------------------------------------------------------------------------------------------------
 constexpr uint32_t kRecCap = 1536;    // kept edges of a window chunk (> 892: one site always fits)
 constexpr uint32_t kRootHash = 2048;  // local slots of the distinct earlier roots one chunk touches
@@ -1154,21 +1158,26 @@ static_assert(kRecCap > kMaxOffsets && kRecCap < kRootHash && (kRootHash & (kRoo
               "record and hash capacities");
 
 constexpr uint32_t kRecSlot = 0xFFFFu;  // a record is (chunk site << 16) | local slot
+constexpr uint32_t kFlagLo = 1u, kFlagHi = 2u;  // a cluster touches x1 = 0 / x1 = L-1
 
 struct WinPtrs {
-    uint32_t *deg;   // [C] kept edges per chunk site, then the scatter cursor, then the site's component
-    uint32_t *ev;    // [C] size of the site's cluster right after it is added, then S_max after it
-    uint32_t *lp;    // [C + kRootHash] local union-find in time order: parent slot, or kRootBit | size
+    uint32_t *deg;   // [C] kept edges per chunk site
+    uint32_t *ev;    // [C] cluster size right after each chunk site is added (replayed components)
+    uint32_t *lp;    // [C + kRootHash] local union-find in time order: parent slot, or kRootBit | entry
     uint32_t *hkey;  // [kRootHash] forest node of local slot C + h (kEmptySlot: free)
     uint32_t *rec;   // [kRecCap] kept edges in site order: (chunk site << 16) | earlier end's local slot
     uint32_t *off;   // [C + 1] first record of each chunk site
-    uint32_t *cc;    // [C + kRootHash] components of the chunk's records, then per-component ranges
-    uint32_t *memb;  // [C] chunk sites grouped by component
+    uint32_t *cc;    // [C + kRootHash] components of the chunk's records (union-find, smallest root)
+    uint32_t *memb;  // [C] component of each chunk site
+    uint32_t *fl;    // [C] border flags of each chunk site (n* sweep)
+    uint32_t *gm;    // [C] smallest forest node of each component, then the replay list
+    uint32_t *cur;   // [C] placement cursor of each chunk site's records
+    uint32_t *tot;   // [C] per-component totals: border flags (n* sweep) or cluster size
 };
 
 __host__ __device__ inline size_t smem_window_bytes(uint32_t threads)
 {
-    return ((size_t(threads) * 6 + 1 + kRecCap + 3 * kRootHash) * 4 + 15) & ~size_t(15);
+    return ((size_t(threads) * 10 + 1 + kRecCap + 3 * kRootHash) * 4 + 15) & ~size_t(15);
 }
 
 __device__ __forceinline__ WinPtrs win_ptrs(unsigned char *at, uint32_t C)
@@ -1183,7 +1192,21 @@ __device__ __forceinline__ WinPtrs win_ptrs(unsigned char *at, uint32_t C)
     w.off = w.rec + kRecCap;
     w.cc = w.off + C + 1;
     w.memb = w.cc + C + kRootHash;
+    w.fl = w.memb + C;
+    w.gm = w.fl + C;
+    w.cur = w.gm + C;
+    w.tot = w.cur + C;
     return w;
+}
+
+// The first pass of a sample keeps the nodes below PA.cap (its own nodes plus the window arrays'
+// shared memory, which it does not use) on chip; afterwards the nodes in [P.cap, PA.cap) below
+// n_nodes move to the global slot, where P finds them.  All threads; ends with a block barrier.
+__device__ __forceinline__ void lend_back(const Nodes &P, const Nodes &PA, uint32_t n_nodes)
+{
+    const uint32_t hi = min(PA.cap, n_nodes);
+    for (uint32_t x = P.cap + threadIdx.x; x < hi; x += blockDim.x) __stcg(P.g + x, lds_u32(PA.sbase + 4u * x));
+    __syncthreads();
 }
 
 // Exclusive prefix sum of v over the block's threads (blockDim a multiple of 32); `total` gets the
@@ -1269,65 +1292,13 @@ __device__ __forceinline__ void cc_unite(uint32_t *cc, uint32_t a, uint32_t b)
     }
 }
 
-// Cluster size right after site t is added, for the sites of one local component in rank order
-// (their indices at shared address s_sites): union by size on the local slots from each site's
-// records.  Shared-memory addresses throughout; the next site's indices are loaded ahead.
-__device__ __forceinline__ void replay_sites(uint32_t s_lp, uint32_t s_rec, uint32_t s_off, uint32_t s_ev,
-                                             uint32_t s_sites, uint32_t nsites, uint32_t C, int *status)
-{
-    uint32_t t = nsites ? lds_u32(s_sites) : 0u;
-    for (uint32_t i = 0; i < nsites; ++i) {
-        const uint32_t k0 = lds_u32(s_off + 4u * t), k1 = lds_u32(s_off + 4u * t + 4u);
-        const uint32_t t_next = i + 1u < nsites ? lds_u32(s_sites + 4u * i + 4u) : 0u;
-        uint32_t ra = t, sa = 1u;  // no earlier record names site t: it starts alone
-        for (uint32_t k = k0; k < k1; ++k) {
-            const uint32_t bs = lds_u32(s_rec + 4u * k) & kRecSlot;
-            if (bs >= C + kRootHash) {  // full hash (ruled out by the capacities)
-                set_status(status, PERC_EDEVICE);
-                continue;
-            }
-            // root xr of bs (path halving) and its entry v = kRootBit | size
-            uint32_t xr = bs, v = lds_u32(s_lp + 4u * bs);
-            while (!(v & kRootBit)) {
-                const uint32_t g = lds_u32(s_lp + 4u * v);
-                if (g & kRootBit) {
-                    xr = v;
-                    v = g;
-                    break;
-                }
-                sts_u32(s_lp + 4u * xr, g);
-                xr = g;
-                v = lds_u32(s_lp + 4u * g);
-            }
-            if (xr == ra) continue;
-            const uint32_t sb = v & ~kRootBit;
-            if (sa >= sb) {
-                sts_u32(s_lp + 4u * xr, ra);
-            } else {
-                sts_u32(s_lp + 4u * ra, xr);
-                ra = xr;
-            }
-            sa += sb;
-            sts_u32(s_lp + 4u * ra, kRootBit | sa);
-        }
-        sts_u32(s_ev + 4u * t, sa);
-        t = t_next;
-    }
-}
 
-// Root of local slot x (read only).
-__device__ __forceinline__ uint32_t local_root(const uint32_t *lp, uint32_t x)
-{
-    for (;;) {
-        const uint32_t v = lp[x];
-        if (v & kRootBit) return x;
-        x = v;
-    }
-}
-
-// Local slot of forest root g: linear probing in the chunk's hash; the thread that inserts g also
-// stores its cluster size.  Returns kEmptySlot only if the hash is full, which the capacities rule
-// out (a chunk keeps at most kRecCap < kRootHash records).
+// Local slot of forest root g: linear probing in the chunk's hash.  The thread that inserts g
+// also stores the slot's entry: kRootBit | cluster size (S_max windows), or kRootBit | (1 << 2) |
+// border flags of g's cluster (the n* sweep: root 0 is the x1 = 0 border, root 1 the x1 = L-1
+// border).  Returns kEmptySlot only if the hash is full, which the capacities rule out (a chunk
+// keeps at most kRecCap < kRootHash records).
+template <bool kSpan>
 __device__ __forceinline__ uint32_t root_slot(const WinPtrs &wp, const uint32_t *cnt, uint32_t g, uint32_t C)
 {
     uint32_t h = (g * 2654435761u) >> (32 - 11);
@@ -1335,7 +1306,8 @@ __device__ __forceinline__ uint32_t root_slot(const WinPtrs &wp, const uint32_t 
     for (uint32_t probe = 0; probe < kRootHash; ++probe) {
         const uint32_t prev = atomicCAS(wp.hkey + h, kEmptySlot, g);
         if (prev == kEmptySlot) {
-            wp.lp[C + h] = kRootBit | __ldcg(cnt + g);
+            wp.lp[C + h] = kSpan ? (kRootBit | 4u | (g == 0u ? kFlagLo : g == 1u ? kFlagHi : 0u))
+                                 : (kRootBit | __ldcg(cnt + g));
             return C + h;
         }
         if (prev == g) return C + h;
@@ -1344,18 +1316,25 @@ __device__ __forceinline__ uint32_t root_slot(const WinPtrs &wp, const uint32_t 
     return kEmptySlot;
 }
 
-// Scan of the window chunk [b, b + count): edges (local index of the site, occupied neighbor).
+// Scan of the window chunk [b, b + count): edges (local index of the site, occupied neighbor).  With
+// one site per thread, `site` is the thread's site (loaded by the caller); with fl, each site's
+// border flags go to fl and, for the n* sweep, its local union-find entry to lp.
 template <bool kSmemBm, bool kPlanes>
 __device__ __forceinline__ void window_scan(const Ctl &c, const uint32_t *bm, const RowEntry *rows,
                                             const PlaneEntry *planes, const EdgeList &E, const uint32_t *perm,
                                             uint32_t L, const FastDiv &fd, uint32_t b, uint32_t count,
-                                            uint32_t *ecount)
+                                            uint32_t site, uint32_t *ecount, uint32_t *fl, uint32_t *lp)
 {
     const uint32_t R = kPlanes ? c.NP : c.R;
     const uint32_t gshift = lanes_shift(count, R);
     const uint32_t gsize = 1u << gshift, gl = threadIdx.x & (gsize - 1u), t = threadIdx.x >> gshift;
     if (t >= count) return;
-    const SiteGeo g = site_geo<kPlanes>(__ldg(perm + b + t), L, fd);
+    const SiteGeo g = site_geo<kPlanes>(gshift ? __ldg(perm + b + t) : site, L, fd);
+    if (fl && gl == 0u) {
+        const uint32_t f = (g.low ? kFlagLo : 0u) | (g.high ? kFlagHi : 0u);
+        fl[t] = f;
+        lp[t] = kRootBit | 4u | f;
+    }
     for (uint32_t k = gl; k < R; k += gsize) {
         uint32_t h[3];
         const uint32_t jb = entry_hits<kSmemBm, kPlanes>(g, bm, rows, planes, k, h);
@@ -1376,36 +1355,241 @@ __device__ __forceinline__ void window_scan(const Ctl &c, const uint32_t *bm, co
 
 struct SmaxShared {
     uint32_t run_max;  // S_max after the last site added
+    uint32_t span_t;   // first chunk site whose cluster spans (n* sweep)
     uint32_t red[32];
 };
 
+// The front of a window chunk starting at rank b (all threads): the chunk's per-site arrays reset,
+// bitmap through the chunk, scan, the kept records in site order (a chunk cut where they would pass
+// kRecCap), earlier neighbors resolved to local slots, and the local components of the records.
+// Returns the number of sites taken (>= 1); `comp` gets the component (its smallest site) of the
+// thread's site (< tn).  The previous chunk must have ended with a block barrier after its last
+// reader of the per-site arrays.
+template <bool kSmemBm, bool kPlanes, bool kSpan>
+__device__ __forceinline__ uint32_t chunk_front(Ctl &c, SmaxShared &x, const Nodes &P, const uint32_t *cnt,
+                                                uint32_t *bm, const SmemPtrs &sm, const WinPtrs &wp,
+                                                const EdgeList &E, const perc_sample &smp, const FastDiv &fd,
+                                                uint32_t b, uint32_t n_end, uint32_t &comp)
+{
+    const uint32_t C = blockDim.x;
+    const uint32_t count = min(C, n_end - b);
+    const long long t0 = clock64();
+    wp.deg[threadIdx.x] = 0u;
+    wp.cur[threadIdx.x] = 0u;
+    wp.tot[threadIdx.x] = 0u;
+    wp.gm[threadIdx.x] = kEmptySlot;
+    wp.ev[threadIdx.x] = 0u;
+    if (!kSpan) wp.lp[threadIdx.x] = kRootBit | 1u;
+    for (uint32_t y = threadIdx.x; y < C + kRootHash; y += C) wp.cc[y] = y;
+    if (threadIdx.x == 0) {
+        c.ecount[0] = 0u;
+        x.span_t = kEmptySlot;
+    }
+    uint32_t site = 0u;
+    if (threadIdx.x < count) {  // the chunk's sites join the bitmap
+        site = __ldg(smp.perm + b + threadIdx.x);
+        const uint32_t i = site + kBmGuard;
+        atomicOr(bm + (i >> 5), 1u << (i & 31u));
+    }
+    __syncthreads();
+    window_scan<kSmemBm, kPlanes>(c, bm, sm.rows, sm.planes, E, smp.perm, smp.L, fd, b, count, site, &c.ecount[0],
+                                  kSpan ? wp.fl : nullptr, wp.lp);
+    __syncthreads();
+    const long long t1 = clock64();
+    const uint32_t ne = c.ecount[0];
+    // filter: keep the edges to earlier sites, count them per site (rank replaces the site)
+    for (uint32_t e = threadIdx.x; e < ne; e += C) {
+        const uint2 ed = edge_get(E, e);
+        const uint32_t rj = __ldg(smp.rank + ed.y);
+        const bool keep = rj < b + ed.x;
+        if (keep) atomicAdd(wp.deg + ed.x, 1u);
+        edge_put(E, e, make_uint2(keep ? ed.x : kEmptySlot, rj));
+    }
+    __syncthreads();
+    const uint32_t d = wp.deg[threadIdx.x];
+    uint32_t total;
+    const uint32_t excl = block_exclusive_sum(d, x.red, total);
+    wp.off[threadIdx.x] = excl;
+    if (threadIdx.x == C - 1u) wp.off[C] = total;
+    const uint32_t tn = __syncthreads_count(threadIdx.x < count && excl + d <= kRecCap);
+    // resolve: earlier neighbors to local slots, records in site order
+    for (uint32_t e = threadIdx.x; e < ne; e += C) {
+        const uint2 ed = edge_get(E, e);
+        if (ed.x >= tn) continue;  // dropped, or past the cut
+        const uint32_t pos = wp.off[ed.x] + atomicAdd(wp.cur + ed.x, 1u);
+        const uint32_t slot = ed.y >= b ? ed.y - b : root_slot<kSpan>(wp, cnt, uf_find(P, ed.y + 2u, 0u), C);
+        wp.rec[pos] = (ed.x << 16) | (slot & kRecSlot);
+    }
+    const uint32_t nrec = wp.off[tn];
+    __syncthreads();
+    // the clusters a chunk builds only interact inside a component of its records
+    for (uint32_t k = threadIdx.x; k < nrec; k += C) {
+        const uint32_t r = wp.rec[k], s2 = r & kRecSlot;
+        if (s2 < C + kRootHash) cc_unite(wp.cc, r >> 16, s2);
+    }
+    __syncthreads();
+    comp = threadIdx.x < tn ? cc_find(wp.cc, threadIdx.x) : 0u;
+    if (threadIdx.x == 0) {
+        c.cyc_scan += static_cast<unsigned long long>(t1 - t0);
+        c.cyc_link += static_cast<unsigned long long>(clock64() - t1);
+    }
+    return tn;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const uint32_t *q)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(q));
+}
+
+// After chunk_front (all threads): each component's total -- border flags (n* sweep) or cluster
+// size (S_max windows) -- and its smallest forest node, then (after one block barrier) the chunk
+// written back to the forest, every component under one node: for the sweep node 0 if the
+// component touches x1 = 0, node 1 if it touches x1 = L-1, else its smallest node (so a cluster
+// touching a border keeps that border's node as its root); for S_max windows its smallest node,
+// which takes the component's size.  The caller's next block barrier orders the write-back.
+template <bool kSpan>
+__device__ __forceinline__ void chunk_components(const Nodes &P, uint32_t *cnt, const WinPtrs &wp, uint32_t b,
+                                                 uint32_t tn, uint32_t comp)
+{
+    const uint32_t C = blockDim.x;
+    if (threadIdx.x < tn) {
+        wp.memb[threadIdx.x] = comp;
+        if (kSpan)
+            atomicOr(wp.tot + comp, wp.fl[threadIdx.x]);
+        else
+            atomicAdd(wp.tot + comp, 1u);
+        atomicMin(wp.gm + comp, b + threadIdx.x + 2u);
+    }
+    for (uint32_t h = threadIdx.x; h < kRootHash; h += C) {
+        const uint32_t g = wp.hkey[h];
+        if (g == kEmptySlot) continue;
+        const uint32_t ch = cc_find(wp.cc, C + h);
+        if (kSpan)
+            atomicOr(wp.tot + ch, g == 0u ? kFlagLo : g == 1u ? kFlagHi : 0u);
+        else
+            atomicAdd(wp.tot + ch, wp.lp[C + h] & ~kRootBit);
+        atomicMin(wp.gm + ch, g);
+    }
+    __syncthreads();
+    auto root_of = [&](uint32_t cp) {
+        if (kSpan) {
+            const uint32_t f = wp.tot[cp];
+            if (f & kFlagLo) return 0u;
+            if (f & kFlagHi) return 1u;
+        }
+        return wp.gm[cp];
+    };
+    if (threadIdx.x < tn) {
+        const uint32_t node = b + threadIdx.x + 2u, r = root_of(comp);
+        nd_st(P, node, r);
+        if (!kSpan && r == node) __stcg(cnt + node, wp.tot[comp]);
+    }
+    for (uint32_t h = threadIdx.x; h < kRootHash; h += C) {
+        const uint32_t g = wp.hkey[h];
+        if (g == kEmptySlot) continue;
+        const uint32_t ch = cc_find(wp.cc, C + h), r = root_of(ch);
+        if (r != g)
+            nd_st(P, g, r);
+        else if (!kSpan)
+            __stcg(cnt + g, wp.tot[ch]);
+    }
+}
+
+// The sites of the components to replay (need = this thread's site belongs to one), in rank order,
+// compacted into wp.gm (free after the write-back); returns their number.  All threads; contains
+// block barriers.
+__device__ __forceinline__ uint32_t replay_list(SmaxShared &x, const WinPtrs &wp, bool need)
+{
+    uint32_t tot;
+    const uint32_t at = block_exclusive_sum(need ? 1u : 0u, x.red, tot);
+    if (need) wp.gm[at] = threadIdx.x;
+    __syncthreads();
+    return tot;
+}
+
+// Replay of the component rooted at chunk site t0 (one thread): its sites in rank order (found in
+// the replay list), each merged with the clusters its records name (union by size on the local
+// slots; entries kRootBit | size, or kRootBit | size << 2 | flags for the sweep).  S_max windows:
+// ev[t] = the cluster size right after site t.  Sweep: returns the first site whose cluster carries
+// both border flags, or kEmptySlot.
+template <bool kSpan>
+__device__ __forceinline__ uint32_t replay_component(const WinPtrs &wp, uint32_t t0, uint32_t nlist, uint32_t C,
+                                                     int *status)
+{
+    const uint32_t s_lp = smem_addr(wp.lp);
+    constexpr uint32_t kSz = kSpan ? 2u : 0u;  // shift of the size field
+    for (uint32_t i = 0; i < nlist; ++i) {
+        const uint32_t t = wp.gm[i];
+        if (wp.memb[t] != t0) continue;
+        const uint32_t k0 = wp.off[t], k1 = wp.off[t + 1u];
+        uint32_t ra = t, ea = lds_u32(s_lp + 4u * t);  // no earlier record names site t: a root
+        for (uint32_t k = k0; k < k1; ++k) {
+            const uint32_t bs = wp.rec[k] & kRecSlot;
+            if (bs >= C + kRootHash) {  // full hash (ruled out by the capacities)
+                set_status(status, PERC_EDEVICE);
+                continue;
+            }
+            // root xr of bs (path halving) and its entry v
+            uint32_t xr = bs, v = lds_u32(s_lp + 4u * bs);
+            while (!(v & kRootBit)) {
+                const uint32_t g = lds_u32(s_lp + 4u * v);
+                if (g & kRootBit) {
+                    xr = v;
+                    v = g;
+                    break;
+                }
+                sts_u32(s_lp + 4u * xr, g);
+                xr = g;
+                v = lds_u32(s_lp + 4u * g);
+            }
+            if (xr == ra) continue;
+            const uint32_t sa = (ea & ~kRootBit) >> kSz, sb = (v & ~kRootBit) >> kSz;
+            const uint32_t e = kRootBit | ((sa + sb) << kSz) | (kSpan ? ((ea | v) & 3u) : 0u);
+            if (sa >= sb) {
+                sts_u32(s_lp + 4u * xr, ra);
+            } else {
+                sts_u32(s_lp + 4u * ra, xr);
+                ra = xr;
+            }
+            ea = e;
+            sts_u32(s_lp + 4u * ra, ea);
+        }
+        if (kSpan) {
+            if ((ea & 3u) == (kFlagLo | kFlagHi)) return t;
+        } else {
+            wp.ev[t] = ea & ~kRootBit;
+        }
+    }
+    return kEmptySlot;
+}
+
 // One sample of k_smax (all threads).  Writes row[k] = S_max(n_lo + k) for n_lo + k <= n_end.
 template <bool kSmemBm, bool kPlanes>
-__device__ void smax_sample(Ctl &c, SmaxShared &x, const Nodes &P, uint32_t *cnt, uint32_t *bm, const SmemPtrs &sm,
-                            const WinPtrs &wp, const EdgeList &E, const perc_sample &smp, uint32_t n0, uint32_t n_end,
-                            uint64_t nlo, uint32_t window, uint32_t *row, int *status)
+__device__ void smax_sample(Ctl &c, SmaxShared &x, const Nodes &P, const Nodes &PA, uint32_t *cnt, uint32_t *bm,
+                            const SmemPtrs &sm, const WinPtrs &wp, const EdgeList &E, const perc_sample &smp,
+                            uint32_t n0, uint32_t n_end, uint64_t nlo, uint32_t window, uint32_t *row, int *status)
 {
     const uint32_t C = blockDim.x, L = smp.L;
     if (kSmemBm) bm = sm.sbm;
     const FastDiv fd = make_fastdiv(L);
-    // ---- the forest of the first n0 sites, the cluster sizes and S_max(n0)
+    // ---- the forest of the first n0 sites (nodes PA), the cluster sizes and S_max(n0)
     bitmap_update(bm, smp.perm, 0u, n0);
     for (uint32_t r = threadIdx.x; r < n0; r += C) {
-        nd_st(P, r + 2u, r + 2u);
+        nd_st(PA, r + 2u, r + 2u);
         __stcg(cnt + r + 2u, 0u);
     }
     __syncthreads();
     if (n0 > 0u)
-        union_pass<kSmemBm, false, kPlanes>(c, P, nullptr, bm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u,
+        union_pass<kSmemBm, false, kPlanes>(c, PA, nullptr, bm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u,
                                             n0, 0u);
     __syncthreads();
-    for (uint32_t r = threadIdx.x; r < n0; r += C) atomicAdd(cnt + uf_find(P, r + 2u, 0u), 1u);
+    for (uint32_t r = threadIdx.x; r < n0; r += C) atomicAdd(cnt + uf_find(PA, r + 2u, 0u), 1u);
     __syncthreads();
     uint32_t best = 0;
     for (uint32_t r = threadIdx.x; r < n0; r += C) best = max(best, ld_cg(cnt + r + 2u));
     best = __reduce_max_sync(0xffffffffu, best);
     if ((threadIdx.x & 31u) == 0u) x.red[threadIdx.x >> 5] = best;
-    wp.lp[threadIdx.x] = kRootBit | 1u;
+    lend_back(P, PA, n0 + 2u);
     for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey[h] = kEmptySlot;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1416,117 +1600,66 @@ __device__ void smax_sample(Ctl &c, SmaxShared &x, const Nodes &P, uint32_t *cnt
     }
     // ---- the window's sites, a chunk at a time
     for (uint32_t b = n0; b < n_end;) {
-        const uint32_t count = min(C, n_end - b);
-        bitmap_update(bm, smp.perm, b, b + count);
-        wp.deg[threadIdx.x] = 0u;
-        if (threadIdx.x == 0) c.ecount[0] = 0u;
-        __syncthreads();
-        window_scan<kSmemBm, kPlanes>(c, bm, sm.rows, sm.planes, E, smp.perm, L, fd, b, count, &c.ecount[0]);
-        __syncthreads();
-        const uint32_t ne = c.ecount[0];
-        // filter: keep the edges to earlier sites, count them per site (rank replaces the site)
-        for (uint32_t e = threadIdx.x; e < ne; e += C) {
-            const uint2 ed = edge_get(E, e);
-            const uint32_t rj = __ldg(smp.rank + ed.y);
-            const bool keep = rj < b + ed.x;
-            if (keep) atomicAdd(wp.deg + ed.x, 1u);
-            edge_put(E, e, make_uint2(keep ? ed.x : kEmptySlot, rj));
+        uint32_t comp;
+        const uint32_t tn = chunk_front<kSmemBm, kPlanes, false>(c, x, P, cnt, bm, sm, wp, E, smp, fd, b, n_end, comp);
+        const uint32_t run0 = x.run_max;
+        chunk_components<false>(P, cnt, wp, b, tn, comp);
+        // a component can raise S_max only if its final size passes the running maximum: replay those
+        const bool need = threadIdx.x < tn && wp.tot[comp] > run0;
+        if (__syncthreads_or(need)) {
+            const uint32_t nlist = replay_list(x, wp, need);
+            if (need && comp == threadIdx.x) replay_component<false>(wp, threadIdx.x, nlist, C, status);
+            __syncthreads();
         }
-        __syncthreads();
-        const uint32_t d = wp.deg[threadIdx.x];
-        uint32_t total;
-        const uint32_t excl = block_exclusive_sum(d, x.red, total);
-        wp.off[threadIdx.x] = excl;
-        if (threadIdx.x == C - 1u) wp.off[C] = total;
-        const uint32_t tn = __syncthreads_count(threadIdx.x < count && excl + d <= kRecCap);
-        wp.deg[threadIdx.x] = 0u;
-        __syncthreads();
-        // resolve: earlier neighbors to local slots, records in site order
-        for (uint32_t e = threadIdx.x; e < ne; e += C) {
-            const uint2 ed = edge_get(E, e);
-            if (ed.x >= tn) continue;  // dropped, or past the cut
-            const uint32_t pos = wp.off[ed.x] + atomicAdd(wp.deg + ed.x, 1u);
-            const uint32_t slot = ed.y >= b ? ed.y - b : root_slot(wp, cnt, uf_find(P, ed.y + 2u, 0u), C);
-            wp.rec[pos] = (ed.x << 16) | (slot & kRecSlot);
-        }
-        const uint32_t nrec = wp.off[tn];
-        for (uint32_t y = threadIdx.x; y < C + kRootHash; y += C) wp.cc[y] = y;
-        __syncthreads();
-        // replay: the clusters a chunk builds only interact inside a component of its records, so
-        // every component is replayed on its own (in rank order) and S_max after site t is the
-        // running maximum over the chunk of the sizes reached so far.
-        for (uint32_t k = threadIdx.x; k < nrec; k += C) {
-            const uint32_t r = wp.rec[k], s2 = r & kRecSlot;
-            if (s2 < C + kRootHash) cc_unite(wp.cc, r >> 16, s2);
-        }
-        __syncthreads();
-        const uint32_t comp = threadIdx.x < tn ? cc_find(wp.cc, threadIdx.x) : 0u;
-        __syncthreads();
-        for (uint32_t y = threadIdx.x; y < C + kRootHash; y += C) wp.cc[y] = 0u;
-        __syncthreads();
-        if (threadIdx.x < tn) atomicAdd(wp.cc + comp, 1u);
-        __syncthreads();
-        // ranges of the components (roots are chunk sites, so the first tn counts suffice), then the
-        // sites grouped by component, warp after warp so that each component keeps rank order
-        const uint32_t own = threadIdx.x < tn ? wp.cc[threadIdx.x] : 0u;
-        uint32_t tot;
-        const uint32_t start = block_exclusive_sum(own, x.red, tot);
-        if (threadIdx.x < tn) wp.cc[threadIdx.x] = start;
-        __syncthreads();
-        {
-            const uint32_t lane = threadIdx.x & 31u, key = threadIdx.x < tn ? comp : kEmptySlot;
-            const uint32_t peers = __match_any_sync(0xffffffffu, key);
-            const uint32_t lead = __ffs(peers) - 1u;
-            const uint32_t before = __popc(peers & ((1u << lane) - 1u));
-            for (uint32_t w = 0; w * 32u < tn; ++w) {
-                if ((threadIdx.x >> 5) == w) {
-                    uint32_t base = 0u;
-                    if (lane == lead && key != kEmptySlot) base = wp.cc[key];
-                    base = __shfl_sync(0xffffffffu, base, lead);
-                    if (key != kEmptySlot) {
-                        wp.memb[base + before] = threadIdx.x;
-                        if (lane == lead) wp.cc[key] = base + __popc(peers);
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        if (threadIdx.x < tn && own > 0u) {  // this site is the root of its component: replay it
-            auto sa = [](const uint32_t *q) { return static_cast<uint32_t>(__cvta_generic_to_shared(q)); };
-            replay_sites(sa(wp.lp), sa(wp.rec), sa(wp.off), sa(wp.ev), sa(wp.memb) + 4u * start, own, C, status);
-        }
-        __syncthreads();
-        {
-            const uint32_t v = threadIdx.x < tn ? wp.ev[threadIdx.x] : 0u;
-            const uint32_t run = max(block_inclusive_max(v, x.red), x.run_max);
-            if (threadIdx.x < tn) wp.ev[threadIdx.x] = run;
-            __syncthreads();  // every thread has read x.run_max
-            if (threadIdx.x == tn - 1u) x.run_max = run;
-        }
-        __syncthreads();
-        // apply: chunk sites point at their root's forest node, hooked earlier roots likewise
+        const uint32_t v = threadIdx.x < tn ? wp.ev[threadIdx.x] : 0u;
+        const uint32_t run = max(block_inclusive_max(v, x.red), run0);
         if (threadIdx.x < tn) {
-            const uint32_t t = threadIdx.x;
-            const uint32_t rt = local_root(wp.lp, t);
-            nd_st(P, b + t + 2u, rt < C ? b + rt + 2u : wp.hkey[rt - C]);
-            if (rt == t) __stcg(cnt + b + t + 2u, wp.lp[t] & ~kRootBit);
-            const uint64_t k = uint64_t(b) + t + 1u - nlo;
-            if (k < window) row[k] = wp.ev[t];
+            const uint64_t k = uint64_t(b) + threadIdx.x + 1u - nlo;
+            if (k < window) row[k] = run;
         }
-        for (uint32_t h = threadIdx.x; h < kRootHash; h += C) {
-            const uint32_t g = wp.hkey[h];
-            if (g == kEmptySlot) continue;
-            const uint32_t rt = local_root(wp.lp, C + h);
-            if (rt != C + h)
-                nd_st(P, g, rt < C ? b + rt + 2u : wp.hkey[rt - C]);
-            else
-                __stcg(cnt + g, wp.lp[C + h] & ~kRootBit);
-        }
-        __syncthreads();
-        wp.lp[threadIdx.x] = kRootBit | 1u;
+        if (threadIdx.x == tn - 1u) x.run_max = run;
         for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey[h] = kEmptySlot;
-        b += tn;  // the next chunk's first barrier orders these resets before their readers
+        b += tn;
+        __syncthreads();  // the per-site arrays, the hash and run_max are read again by the next chunk
     }
+}
+
+// The n* sweep of one sample from n_s (all threads; the sites of rank < n_s are merged and do not
+// span).  Returns n*, or PERC_NEVER if no n <= N spans; `chunks` counts the chunks taken.  Only a
+// component that carries both border flags at the end of its chunk is replayed.
+template <bool kSmemBm, bool kPlanes>
+__device__ uint32_t span_sweep(Ctl &c, SmaxShared &x, const Nodes &P, uint32_t *bm, const SmemPtrs &sm,
+                               const WinPtrs &wp, const EdgeList &E, const perc_sample &smp, const FastDiv &fd,
+                               uint32_t N, uint32_t n_s, uint32_t &chunks, unsigned long long &cyc_back, int *status)
+{
+    const uint32_t C = blockDim.x;
+    if (kSmemBm) bm = sm.sbm;
+    for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey[h] = kEmptySlot;
+    for (uint32_t b = n_s; b < N;) {
+        ++chunks;
+        uint32_t comp;
+        const uint32_t tn = chunk_front<kSmemBm, kPlanes, true>(c, x, P, nullptr, bm, sm, wp, E, smp, fd, b, N, comp);
+        const long long t0 = clock64();
+        chunk_components<true>(P, nullptr, wp, b, tn, comp);
+        // only a component that spans at the end of the chunk can hold the first spanning site
+        const bool spans = threadIdx.x < tn && wp.tot[comp] == (kFlagLo | kFlagHi);
+        uint32_t st = kEmptySlot;
+        if (__syncthreads_or(spans)) {
+            const uint32_t nlist = replay_list(x, wp, spans);
+            if (spans && comp == threadIdx.x) {
+                const uint32_t t = replay_component<true>(wp, threadIdx.x, nlist, C, status);
+                if (t != kEmptySlot) atomicMin(&x.span_t, t);
+            }
+            __syncthreads();
+            st = x.span_t;
+        }
+        if (threadIdx.x == 0) cyc_back += static_cast<unsigned long long>(clock64() - t0);
+        for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey[h] = kEmptySlot;
+        if (st != kEmptySlot) return b + st + 1u;
+        b += tn;
+        __syncthreads();  // the per-site arrays and the hash are reset by the next chunk
+    }
+    return PERC_NEVER;
 }
 
 __global__ void __launch_bounds__(1024, 1)
@@ -1537,7 +1670,7 @@ k_smax(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
     extern __shared__ __align__(16) unsigned char dyn[];
     const uint32_t C = blockDim.x;
     const SmemPtrs sm = smem_ptrs(dyn, smem_L, node_cap, smem_window_bytes(C));
-    const WinPtrs wp = win_ptrs(dyn + smem_tables_bytes() + smem_bitmap_bytes(smem_L), C);
+    const WinPtrs wp = win_ptrs(reinterpret_cast<unsigned char *>(sm.nodes) + smem_nodes_bytes(node_cap), C);
     __shared__ Ctl c;
     __shared__ SmaxShared x;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
@@ -1545,6 +1678,7 @@ k_smax(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
     const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
     const EdgeList E{sm.edges, edge_scap, sp.gedges};
     const Nodes P{sp.P, static_cast<uint32_t>(__cvta_generic_to_shared(sm.nodes)), node_cap};
+    const Nodes PA{sp.P, P.sbase, node_cap + static_cast<uint32_t>(smem_window_bytes(C) / 4)};  // first pass
 
     for (;;) {
         if (threadIdx.x == 0) c.sample = atomicAdd(&hdr->queue, 1u);
@@ -1584,12 +1718,168 @@ k_smax(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         }
         __syncthreads();
         if (smem_bm && L == kPlaneL)
-            smax_sample<true, true>(c, x, P, sp.logb, bm, sm, wp, E, smp, n0, n_end, nlo, window, row, &hdr->status);
+            smax_sample<true, true>(c, x, P, PA, sp.logb, bm, sm, wp, E, smp, n0, n_end, nlo, window, row, &hdr->status);
         else if (smem_bm)
-            smax_sample<true, false>(c, x, P, sp.logb, bm, sm, wp, E, smp, n0, n_end, nlo, window, row, &hdr->status);
+            smax_sample<true, false>(c, x, P, PA, sp.logb, bm, sm, wp, E, smp, n0, n_end, nlo, window, row, &hdr->status);
         else
-            smax_sample<false, false>(c, x, P, sp.logb, bm, sm, wp, E, smp, n0, n_end, nlo, window, row, &hdr->status);
+            smax_sample<false, false>(c, x, P, PA, sp.logb, bm, sm, wp, E, smp, n0, n_end, nlo, window, row, &hdr->status);
         __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// k_nstar_sweep: n* by one sweep over the sites in rank order (the Newman--Ziff order), in chunks,
+// instead of bisection.  A start n_s that does not span -- the learned bracket's lower end minus
+// one, checked by one connected-component pass, else 0 -- is reached in one pass; the window
+// chunks then follow with border flags in place of sizes, and only a component that touches both
+// borders at the end of its chunk is replayed: its first site whose cluster carries both flags
+// gives n*.  Between chunks the forest keeps the invariant of the passes: a cluster touching
+// x1 = 0 has root node 0, one touching x1 = L-1 (and not x1 = 0) has root node 1.
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024, 1)
+k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L,
+              uint32_t node_cap, uint32_t edge_scap, const uint32_t *__restrict__ bracket,
+              uint32_t *__restrict__ nstar_out, uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws,
+              size_t slot_bytes)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    const uint32_t C = blockDim.x;
+    const SmemPtrs sm = smem_ptrs(dyn, smem_L, node_cap, smem_window_bytes(C));
+    const WinPtrs wp = win_ptrs(reinterpret_cast<unsigned char *>(sm.nodes) + smem_nodes_bytes(node_cap), C);
+    __shared__ Ctl c;
+    __shared__ SmaxShared x;
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+    const uint64_t Ncap = num_sites(max_L);
+    const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
+    const EdgeList E{sm.edges, edge_scap, sp.gedges};
+    const Nodes P{sp.P, static_cast<uint32_t>(__cvta_generic_to_shared(sm.nodes)), node_cap};
+    const Nodes PA{sp.P, P.sbase, node_cap + static_cast<uint32_t>(smem_window_bytes(C) / 4)};  // first pass
+    unsigned long long tot_passes = 0, tot_probe = 0, tot_fb = 0, tot_ok = 0, tot_chunks = 0;
+    unsigned long long cyc_setup = 0, cyc_first = 0, cyc_back = 0;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            c.sample = atomicAdd(&hdr->queue, 1u);
+            c.hooks = 0;
+            c.new_sites = 0;
+            c.sites = 0;
+            c.unions = 0;
+            c.cyc_scan = 0;
+            c.cyc_link = 0;
+        }
+        __syncthreads();
+        const long long t_setup = clock64();
+        const uint32_t s = c.sample;
+        if (s >= num) break;
+        const perc_sample smp = samples[s];
+        const uint32_t L = smp.L, mask = smp.zone_mask;
+        if (L < 1u || L > max_L || mask < 1u || mask > 127u || !smp.perm || !smp.rank) {
+            if (threadIdx.x == 0) {
+                nstar_out[s] = PERC_NEVER;
+                if (passes_out) passes_out[s] = 0;
+                set_status(&hdr->status, PERC_EDEVICE);
+            }
+            __syncthreads();
+            continue;
+        }
+        const uint32_t N = static_cast<uint32_t>(num_sites(L));
+        const bool smem_bm = L <= smem_L;
+        uint32_t *bm = smem_bm ? sm.sbm : sp.gbm;
+        const uint32_t words = bm_words(N);
+        for (uint32_t w = threadIdx.x; w < words; w += C) bm[w] = 0u;
+        build_rows(mask, L, sm.rows, sm.scratch, c);
+        if (smem_bm && L == kPlaneL) build_planes16(sm.rows, c.R, sm.planes, sm.scratch, c);
+        if (threadIdx.x == 0) {
+            nd_st(PA, 0u, 0u);  // for the first pass
+            nd_st(PA, 1u, 1u);
+            nd_st(P, 0u, 0u);  // for the sweep (the same words when node_cap > 1)
+            nd_st(P, 1u, 1u);
+            c.stop = 0;
+            c.logn = 0;
+            c.ecount[0] = 0;
+        }
+        const FastDiv fd = make_fastdiv(L);
+        __syncthreads();
+        const long long t_first = clock64();
+        cyc_setup += static_cast<unsigned long long>(t_first - t_setup);
+
+        // the start: the bracket's lower end minus one, which must not span
+        uint32_t n_s = 0, blo = 0, bhi = 0, npass = 0;
+        bool have_br = false;
+        if (bracket) {
+            blo = bracket[2 * size_t(s)];
+            bhi = bracket[2 * size_t(s) + 1];
+            if (blo >= 1u && blo <= bhi && bhi <= N) {
+                n_s = blo - 1u;
+                have_br = true;
+            } else {
+                ++tot_fb;
+            }
+        }
+        if (n_s > 0u) {
+            bitmap_update(bm, smp.perm, 0u, n_s);
+            for (uint32_t r = threadIdx.x; r < n_s; r += C) nd_st(PA, r + 2u, r + 2u);
+            __syncthreads();
+            if (smem_bm && L == kPlaneL)
+                union_pass<true, true, true>(c, PA, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd,
+                                             0u, n_s, 0u);
+            else if (smem_bm)
+                union_pass<true, true, false>(c, PA, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm, smp.rank, L,
+                                              fd, 0u, n_s, 0u);
+            else
+                union_pass<false, true, false>(c, PA, nullptr, bm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd,
+                                               0u, n_s, 0u);
+            __syncthreads();
+            ++npass;
+            tot_probe += n_s;
+            const bool span = nd_ld(PA, 1u) != 1u;
+            lend_back(P, PA, n_s + 2u);  // (a barrier: every thread has read node 1)
+            if (span) {                  // n* < the bracket's lower end: sweep from the start
+                ++tot_fb;
+                have_br = false;
+                n_s = 0u;
+                if (threadIdx.x == 0) {
+                    nd_st(P, 0u, 0u);
+                    nd_st(P, 1u, 1u);
+                }
+                __syncthreads();
+            }
+        }
+        uint32_t chunks = 0, ns;
+        cyc_first += static_cast<unsigned long long>(clock64() - t_first);
+        if (smem_bm && L == kPlaneL)
+            ns = span_sweep<true, true>(c, x, P, bm, sm, wp, E, smp, fd, N, n_s, chunks, cyc_back, &hdr->status);
+        else if (smem_bm)
+            ns = span_sweep<true, false>(c, x, P, bm, sm, wp, E, smp, fd, N, n_s, chunks, cyc_back, &hdr->status);
+        else
+            ns = span_sweep<false, false>(c, x, P, bm, sm, wp, E, smp, fd, N, n_s, chunks, cyc_back, &hdr->status);
+        npass += chunks;
+        tot_chunks += chunks;
+        if (have_br && ns >= blo && ns <= bhi) ++tot_ok;
+        if (threadIdx.x == 0) {
+            nstar_out[s] = ns;
+            if (passes_out) passes_out[s] = npass;
+            tot_passes += npass;
+            if (stats) {
+                atomicAdd(&stats->hooks, c.hooks);
+                atomicAdd(&stats->sites_merged, c.sites);
+                atomicAdd(&stats->unions, c.unions);
+                atomicAdd(&stats->new_sites, static_cast<unsigned long long>(ns == PERC_NEVER ? N : ns));
+                atomicAdd(&stats->cyc_scan, c.cyc_scan);
+                atomicAdd(&stats->cyc_link, c.cyc_link);
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && stats) {
+        atomicAdd(&stats->passes, tot_passes);
+        atomicAdd(&stats->probe_sites, tot_probe);
+        atomicAdd(&stats->fallbacks, tot_fb);
+        atomicAdd(&stats->verified, tot_ok);
+        atomicAdd(&stats->chunks, tot_chunks);
+        atomicAdd(&stats->cyc_setup, cyc_setup);
+        atomicAdd(&stats->cyc_update, cyc_first);
+        atomicAdd(&stats->cyc_commit, cyc_back);
     }
 }
 
@@ -1619,11 +1909,12 @@ struct CfgCache {
     bool valid = false;
 };
 constexpr int kCfgDevices = 64;
-static CfgCache g_cfg_cache[3][kCfgDevices];
+static CfgCache g_cfg_cache[4][kCfgDevices];
 static std::mutex g_cfg_mutex;
 
 // Launch options set through perc_set_launch_option (0 = automatic).
-static int g_opt_threads = 0, g_opt_smem_nodes = -1, g_opt_max_ctas = 0, g_opt_group = 0;
+static int g_opt_threads = 0, g_opt_smem_nodes = -1, g_opt_max_ctas = 0, g_opt_group = 0, g_opt_method = 0;
+constexpr int kOpSweep = 100;  // launch configuration of k_nstar_sweep (perc_nstar, sweep method)
 static CfgCache g_group_cache[kCfgDevices];
 
 static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool allow_group = true)
@@ -1644,7 +1935,7 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool
     // registers a thread); each CTA takes an equal share.  What the tables and the bitmap leave
     // goes to union-find nodes (up to kSmemNodes, keeping room for 512 edges) and then to the
     // shared part of the edge list.
-    const size_t extra = op == PERC_OP_SMAX ? smem_window_bytes(cfg.threads) : 0;
+    const size_t extra = (op == PERC_OP_SMAX || op == kOpSweep) ? smem_window_bytes(cfg.threads) : 0;
     size_t base = smem_tables_bytes() + smem_bitmap_bytes(cfg.smem_L) + extra;
     const size_t min_edges = size_t(kRowCand) * sizeof(uint32_t);  // table-building scratch
     int ctas = (65536 / (cfg.threads * 64)) > 0 ? 65536 / (cfg.threads * 64) : 1;
@@ -1666,9 +1957,10 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool
     cfg.smem = base + smem_nodes_bytes(cfg.node_cap) + size_t(cfg.edge_scap) * sizeof(uint2);
     // The attribute and the occupancy are queried once per (kernel, device, threads, shared memory)
     // and cached, so that a call made while a stream is being captured issues no such query.
-    const int k = op == PERC_OP_MASS ? 1 : (op == PERC_OP_SMAX ? 2 : 0);
+    const int k = op == PERC_OP_MASS ? 1 : op == PERC_OP_SMAX ? 2 : op == kOpSweep ? 3 : 0;
     const void *fn = k == 1   ? reinterpret_cast<const void *>(k_mass)
                      : k == 2 ? reinterpret_cast<const void *>(k_smax)
+                     : k == 3 ? reinterpret_cast<const void *>(k_nstar_sweep)
                               : reinterpret_cast<const void *>(k_nstar);
     {
         std::lock_guard<std::mutex> lock(g_cfg_mutex);
@@ -1766,7 +2058,23 @@ extern "C" size_t perc_workspace_bytes(int op, uint32_t max_L, uint32_t num)
     if (op != PERC_OP_NSTAR && op != PERC_OP_MASS && op != PERC_OP_SMAX) return 0;
     LaunchCfg cfg;
     if (launch_cfg(op, max_L, num, cfg) != PERC_OK) return 0;
-    return sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes;
+    size_t bytes = sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes;
+    LaunchCfg sw;  // perc_nstar may run either method: room for both
+    if (op == PERC_OP_NSTAR && launch_cfg(kOpSweep, max_L, num, sw) == PERC_OK)
+        bytes = std::max(bytes, sizeof(WsHeader) + size_t(sw.grid) * sw.slot_bytes);
+    return bytes;
+}
+
+// The method perc_nstar uses: bisection (1) or the sweep (2); a negative status if the sweep was
+// asked for and cannot be configured.  Automatic (0): the sweep, unless the bisection would run
+// cooperative groups (big lattices in small batches) or the sweep's shared-memory arrays do not fit.
+static int nstar_method(uint32_t max_L, uint32_t num, const LaunchCfg &bis, LaunchCfg &sw)
+{
+    const int m = env_int("PERC_METHOD", g_opt_method);
+    if (m == 1) return 1;
+    const int rc = launch_cfg(kOpSweep, max_L, num, sw);
+    if (m == 2) return rc == PERC_OK ? 2 : rc;
+    return (rc == PERC_OK && bis.members == 1) ? 2 : 1;
 }
 
 extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
@@ -1774,11 +2082,21 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
                           void *workspace, size_t ws_bytes, void *stream_)
 {
     if (!samples || !nstar || !workspace || num_samples == 0) return PERC_EINVAL;
-    LaunchCfg cfg;
+    LaunchCfg cfg, sw;
     int rc = launch_cfg(PERC_OP_NSTAR, max_L, num_samples, cfg);
     if (rc != PERC_OK) return rc;
-    if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
+    const int method = nstar_method(max_L, num_samples, cfg, sw);
+    if (method < 0) return method;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (method == 2) {
+        if (ws_bytes < sizeof(WsHeader) + size_t(sw.grid) * sw.slot_bytes) return PERC_EWORKSPACE;
+        if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
+        k_nstar_sweep<<<sw.grid, sw.threads, sw.smem, stream>>>(samples, num_samples, max_L, sw.smem_L, sw.node_cap,
+                                                                sw.edge_scap, bracket, nstar, passes, stats,
+                                                                static_cast<char *>(workspace), sw.slot_bytes);
+        return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
+    }
+    if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
     if (cfg.members > 1) {
         // every group's barrier counters, abort flag and shared scalars start at zero
@@ -1857,6 +2175,10 @@ extern "C" int perc_set_launch_option(int option, int value)
     case PERC_OPT_GROUP:
         if (value < 0 || value > 64) return PERC_EINVAL;
         g_opt_group = value;
+        return PERC_OK;
+    case PERC_OPT_METHOD:
+        if (value < 0 || value > 2) return PERC_EINVAL;
+        g_opt_method = value;
         return PERC_OK;
     default:
         return PERC_EINVAL;

@@ -18,11 +18,12 @@ LIB_PATH = os.path.join(HERE, "libperc.so")
 NEVER = 0xFFFFFFFF
 MAX_L = 73
 OP_RANK, OP_NSTAR, OP_MASS, OP_SMAX = 1, 2, 3, 4
-OPT_THREADS, OPT_SMEM_NODES, OPT_MAX_CTAS, OPT_GROUP = 1, 2, 3, 4
+OPT_THREADS, OPT_SMEM_NODES, OPT_MAX_CTAS, OPT_GROUP, OPT_METHOD = 1, 2, 3, 4, 5
+METHOD_AUTO, METHOD_BISECTION, METHOD_SWEEP = 0, 1, 2
 MLP_NPARAM = 4931
 STATS_FIELDS = ("passes", "new_sites", "probe_sites", "hooks", "early_exits", "fallbacks",
                 "verified", "sites_merged", "unions", "cyc_setup", "cyc_update", "cyc_union",
-                "cyc_commit", "cyc_scan", "cyc_link", "reserved")
+                "cyc_commit", "cyc_scan", "cyc_link", "chunks")
 
 _lib = None
 

@@ -70,7 +70,17 @@ def test_autotuner_picks_a_candidate_and_keeps_nstar(tmp_path, monkeypatch):
         autotune.reset()
 
 
-def test_learned_bracket_gains_passes_and_time():
+@pytest.mark.parametrize("method", ["bisection", "sweep"])
+def test_learned_bracket_gains_passes_and_time(method):
+    from paper_2607_18991_b300 import perc
+    perc.set_launch_option(perc.OPT_METHOD, perc.METHOD_BISECTION if method == "bisection" else perc.METHOD_SWEEP)
+    try:
+        _learned_gain(method)
+    finally:
+        perc.set_launch_option(perc.OPT_METHOD, perc.METHOD_AUTO)
+
+
+def _learned_gain(method):
     import torch
 
     from paper_2607_18991_b300 import driver, perc
@@ -94,8 +104,12 @@ def test_learned_bracket_gains_passes_and_time():
         times[learned] = a.elapsed_time(b)
         out[learned] = step.result()
     assert np.array_equal(out[True][0], out[False][0])
-    assert out[True][1].mean() < out[False][1].mean() - 3       # fewer passes per sample
-    assert times[True] < 0.5 * times[False], times               # and much less time
+    if method == "bisection":
+        assert out[True][1].mean() < out[False][1].mean() - 3   # fewer passes per sample
+        assert times[True] < 0.5 * times[False], times           # and much less time
+    else:  # the sweep starts at the bracket's lower end instead of n = 0: fewer chunks (the time
+        # is not asserted: a chunk costs about as much as the share of the first pass it replaces)
+        assert out[True][1].mean() < out[False][1].mean(), (out[True][1].mean(), out[False][1].mean())
     sel = np.arange(0, step.num, 97)
     assert np.array_equal(out[True][0][sel], orc_nstar(step.workload[sel]))
 

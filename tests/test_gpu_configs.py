@@ -63,15 +63,21 @@ def test_mixed_batch_sampled():
     assert np.array_equal(ns, orc_nstar(sub))
 
 
-def test_full_size_L16_launch_sampled():
+@pytest.mark.parametrize("method", ["bisection", "sweep"])
+def test_full_size_L16_launch_sampled(method):
     # the benchmark's launch: all 127 masks x seeds 1..256 in one persistent launch, learned bracket
     import torch
 
-    from paper_2607_18991_b300 import driver
-    step = driver.NstarStep(16, range(1, 128), range(1, 257), params=quick_params(), margin=0.05)
-    step.run(True)
-    torch.cuda.synchronize()
-    ns, passes = step.result()
+    from paper_2607_18991_b300 import driver, perc
+    perc.set_launch_option(perc.OPT_METHOD, perc.METHOD_BISECTION if method == "bisection" else perc.METHOD_SWEEP)
+    try:
+        step = driver.NstarStep(16, range(1, 128), range(1, 257), params=quick_params(), margin=0.05)
+        step.run(True)
+        torch.cuda.synchronize()
+        ns, passes = step.result()
+    finally:
+        perc.set_launch_option(perc.OPT_METHOD, perc.METHOD_AUTO)
     sel = np.nonzero(np.isin(step.workload[:, 2], [1, 128, 256]))[0]
     assert np.array_equal(ns[sel], orc_nstar(step.workload[sel]))
-    assert passes.max() <= 2 * 20 + 1  # a fallback costs at most one failed check plus the plain bisection
+    if method == "bisection":
+        assert passes.max() <= 2 * 20 + 1  # a fallback costs one failed check plus the plain bisection

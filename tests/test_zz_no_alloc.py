@@ -27,7 +27,11 @@ def test_noalloc_matches_workspace_entry_point_twice(L, masks, seeds):
 
     from paper_2607_18991_b300 import perc
     smp, keep = _samples(L, masks, seeds)
-    want_ns, want_ps = perc.nstar(smp, L)
+    perc.set_launch_option(perc.OPT_METHOD, perc.METHOD_BISECTION)  # the method the no-alloc entry uses
+    try:
+        want_ns, want_ps = perc.nstar(smp, L)
+    finally:
+        perc.set_launch_option(perc.OPT_METHOD, perc.METHOD_AUTO)
     want_ns, want_ps = perc.u32(want_ns), perc.u32(want_ps)
     N = L ** 5
     exact = torch.from_numpy(np.stack([want_ns, want_ns], axis=1).astype(np.uint32).view(np.int32)).cuda()
