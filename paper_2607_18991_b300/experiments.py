@@ -10,7 +10,11 @@ Each run prints one JSON line:
 * ``L24``   -- all 127 neighborhoods at L = 24, seeds 1..128: samples/s and passes with the learned
   bracket (network trained at L = 8 and 16 only) and with the plain one;
 * ``L40``   -- sc(5)-1,...,7 at L = 40 (102.4M sites), seeds 1..8;
-* ``mixed`` -- 4096 samples with L uniform in {10..40} and random masks, plain and learned.
+* ``mixed`` -- 4096 samples with L uniform in {10..40} and random masks, plain and learned;
+* ``universality`` -- p_hat(k, L) = mean n*/L^5 for all 127 neighborhoods at L in {8, 12, 16, 20, 24},
+  extrapolated per neighborhood to L -> infinity (p_hat = p_c + A L^(-1/nu)), compared with Table I,
+  and the universality fits p_c = c/(z+b), p_c = zeta^(-g), p_c = a zeta^(-g) on those values and on
+  Table I (section "Universality of p_c behavior").
 
 Times are wall-clock with the device synchronised, ranking included.
 """
@@ -111,17 +115,57 @@ def run_mixed(params, quick: bool = False) -> dict:
     return {"workload": "mixed L in 10..40, random masks", "samples": len(wl), **res}
 
 
+UNIV_SEEDS = {8: 512, 12: 256, 16: 128, 20: 64, 24: 32}
+
+
+def _fits(z, zeta, pc) -> dict:
+    (b, c), (eb, ec), rss = analysis.fit_rational_z(z, pc)
+    (g,), (eg,), rss_g = analysis.fit_power_zeta(zeta, pc)
+    (a, g2), (ea, eg2), rss_g2 = analysis.fit_power_zeta(zeta, pc, prefactor=True)
+    return {"c_over_z_plus_b": {"b": b, "b_err": eb, "c": c, "c_err": ec, "rss": rss},
+            "zeta_power": {"g": g, "g_err": eg, "rss": rss_g},
+            "zeta_power_prefactor": {"a": a, "a_err": ea, "g": g2, "g_err": eg2, "rss": rss_g2}}
+
+
+def run_universality(quick: bool = False) -> dict:
+    masks = workloads.ALL_MASKS
+    p_hat = {}
+    t0 = time.perf_counter()
+    for L, ns in UNIV_SEEDS.items():
+        wl = workloads.samples(L, masks, range(1, (max(ns // 8, 2) if quick else ns) + 1))
+        nst, _ = driver.nstar(wl)
+        p_hat[L] = np.array([analysis.p_hat(L, nst[wl[:, 1] == m]) for m in masks])
+    dt = time.perf_counter() - t0
+    Ls = sorted(p_hat)
+    ext = [analysis.extrapolate_pc(Ls, [p_hat[L][k] for L in Ls]) for k in range(len(masks))]
+    pc_ext = np.array([e[0] for e in ext])
+    z = np.array([analysis.mask_z_zeta(m)[0] for m in masks], dtype=np.float64)
+    zeta = np.array([analysis.mask_z_zeta(m)[1] for m in masks], dtype=np.float64)
+    pc_t1 = np.array([workloads.TABLE1_PC[m] for m in masks])
+    rel = pc_ext / pc_t1 - 1.0
+    return {"workload": "universality: n* of all 127 neighborhoods at L = " + ", ".join(map(str, Ls)),
+            "seeds": UNIV_SEEDS, "seconds": dt,
+            "p_hat_mean_rel_to_table1": {str(L): float(np.mean(p_hat[L] / pc_t1 - 1.0)) for L in Ls},
+            "extrapolated_vs_table1": {"mean_rel": float(rel.mean()), "rms_rel": float(np.sqrt(np.mean(rel ** 2))),
+                                       "max_abs_rel": float(np.abs(rel).max()),
+                                       "sc5_1": [float(pc_ext[0]), float(ext[0][1])],
+                                       "sc5_1_7": [float(pc_ext[126]), float(ext[126][1])]},
+            "fits_extrapolated": _fits(z, zeta, pc_ext), "fits_table1": _fits(z, zeta, pc_t1)}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["mass", "L24", "L40", "mixed", "all"])
+    ap.add_argument("which", choices=["mass", "L24", "L40", "mixed", "universality", "all"])
     ap.add_argument("--quick", action="store_true")
     args = ap.parse_args()
     torch.cuda.set_device(0)
-    params = None if args.which == "mass" else trained_params(args.quick)
+    params = None if args.which in ("mass", "universality") else trained_params(args.quick)
     todo = ["mass", "L24", "L40", "mixed"] if args.which == "all" else [args.which]
     for w in todo:
         if w == "mass":
             r = run_mass(args.quick)
+        elif w == "universality":
+            r = run_universality(args.quick)
         elif w == "L24":
             r = run_L24(params, args.quick)
         elif w == "L40":

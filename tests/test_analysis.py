@@ -28,3 +28,55 @@ def test_delta_of_table2_rows():
     assert round(abs(analysis.delta(3.5453)), 2) == 0.68
     assert round(abs(analysis.delta(3.5836)), 2) == 1.76
     assert analysis.p_hat(2, [16, 16]) == 0.5
+
+
+def _table1():
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_zones import corrected_table1
+    rows = corrected_table1()
+    z = np.array([r[2] for r in rows], float)
+    zeta = np.array([r[3] for r in rows], float)
+    pc = np.array([r[4] for r in rows], float)
+    return z, zeta, pc
+
+
+def test_universality_fits_reproduce_the_papers_numbers():
+    """On Table I's p_c (five printed decimals), the fits give the values the paper prints
+    (Universality of p_c behavior; Results): p_c = c/(z+b) with b = 1.01(18), c = 1.553(22) and a
+    residual sum of squares 9.40327e-5; p_c = zeta^(-g) with g = 0.8293(24); with a prefactor,
+    g = 0.7913(43) and residual sum 8.1039e-5.  Table I's rounding moves them slightly."""
+    z, zeta, pc = _table1()
+    (b, c), (eb, ec), rss = analysis.fit_rational_z(z, pc)
+    assert abs(b - 1.01) < 0.02 and abs(c - 1.553) < 0.003 and 0.1 < eb < 0.25 and 0.01 < ec < 0.03
+    assert abs(rss - 9.40327e-5) / 9.40327e-5 < 0.02
+    (g,), (eg,), _ = analysis.fit_power_zeta(zeta, pc)
+    assert abs(g - 0.8293) < 0.001 and 0.001 < eg < 0.004
+    (a, g2), (_, eg2), rss2 = analysis.fit_power_zeta(zeta, pc, prefactor=True)
+    assert abs(g2 - 0.7913) < 0.003 and 0.002 < eg2 < 0.006 and abs(rss2 - 8.1039e-5) / 8.1039e-5 < 0.05
+
+
+def test_fits_recover_exact_laws():
+    z = np.linspace(10, 900, 40)
+    (b, c), _, rss = analysis.fit_rational_z(z, 1.7 / (z + 2.5))
+    assert np.allclose([b, c], [2.5, 1.7], rtol=1e-9) and rss < 1e-24
+    zeta = np.linspace(10, 2100, 40)
+    (g,), _, _ = analysis.fit_power_zeta(zeta, zeta ** -0.83)
+    assert abs(g - 0.83) < 1e-10
+    (a, g), _, _ = analysis.fit_power_zeta(zeta, 0.9 * zeta ** -0.79, prefactor=True)
+    assert np.allclose([a, g], [0.9, 0.79], rtol=1e-9)
+
+
+def test_extrapolation_to_infinite_lattice():
+    Ls = np.array([8, 12, 16, 20, 24])
+    pc, err, A = analysis.extrapolate_pc(Ls, 0.1408 + 0.25 * Ls ** (-1 / analysis.NU_5))
+    assert abs(pc - 0.1408) < 1e-12 and abs(A - 0.25) < 1e-10 and err < 1e-10
+
+
+def test_host_z_and_zeta_match_the_oracles_enumeration():
+    import oracle
+    for m in range(1, 128):
+        z, zeta = analysis.mask_z_zeta(m)
+        oz, ozeta = oracle.mask_z_zeta(m)
+        assert z == oz and abs(zeta - ozeta) < 1e-9
