@@ -1624,9 +1624,49 @@ __device__ void smax_sample(Ctl &c, SmaxShared &x, const Nodes &P, const Nodes &
     }
 }
 
+// The first site of a spanning chunk whose cluster carries both border flags (all threads; the chunk
+// spans once all its tn sites are added).  Bisection over m, the number of the chunk's sites added:
+// the records of sites < m (stored in site order, the first off[m] of them) are united into local
+// components (shared-memory union-find, smallest slot as root, so every component of a site has a
+// site as root), each root ORs the border flags of its sites and of the earlier clusters it reaches
+// (forest root 0: x1 = 0, root 1: x1 = L-1), and m spans when a root carries both.  span(0) is
+// false (the earlier clusters do not span) and span(tn) true; the answer is the largest m that does
+// not span.  About log2(tn) rounds of four block barriers, instead of one thread replaying the
+// component site by site.
+__device__ uint32_t first_span_site(const WinPtrs &wp, uint32_t tn)
+{
+    const uint32_t C = blockDim.x;
+    uint32_t lo = 0, hi = tn;
+    while (hi - lo > 1u) {
+        const uint32_t m = (lo + hi) >> 1;
+        for (uint32_t y = threadIdx.x; y < C + kRootHash; y += C) wp.cc[y] = y;
+        wp.ev[threadIdx.x] = 0u;
+        __syncthreads();
+        const uint32_t nr = wp.off[m];
+        for (uint32_t k = threadIdx.x; k < nr; k += C) {
+            const uint32_t r = wp.rec[k], s2 = r & kRecSlot;
+            if (s2 < C + kRootHash) cc_unite(wp.cc, r >> 16, s2);
+        }
+        __syncthreads();
+        if (threadIdx.x < m) atomicOr(wp.ev + cc_find(wp.cc, threadIdx.x), wp.fl[threadIdx.x]);
+        for (uint32_t h = threadIdx.x; h < kRootHash; h += C) {
+            const uint32_t g = wp.hkey[h];
+            if (g > 1u) continue;  // free slot (kEmptySlot) or a root that touches no border
+            const uint32_t rt = cc_find(wp.cc, C + h);
+            if (rt < C) atomicOr(wp.ev + rt, g == 0u ? kFlagLo : kFlagHi);  // reached by a site below m
+        }
+        __syncthreads();
+        if (__syncthreads_or(threadIdx.x < m && wp.ev[threadIdx.x] == (kFlagLo | kFlagHi)))
+            hi = m;
+        else
+            lo = m;
+    }
+    return hi - 1u;
+}
+
 // The n* sweep of one sample from n_s (all threads; the sites of rank < n_s are merged and do not
 // span).  Returns n*, or PERC_NEVER if no n <= N spans; `chunks` counts the chunks taken.  Only a
-// component that carries both border flags at the end of its chunk is replayed.
+// chunk whose components touch both borders at its end is searched for the first spanning site.
 template <bool kSmemBm, bool kPlanes>
 __device__ uint32_t span_sweep(Ctl &c, SmaxShared &x, const Nodes &P, uint32_t *bm, const SmemPtrs &sm,
                                const WinPtrs &wp, const EdgeList &E, const perc_sample &smp, const FastDiv &fd,
@@ -1644,15 +1684,7 @@ __device__ uint32_t span_sweep(Ctl &c, SmaxShared &x, const Nodes &P, uint32_t *
         // only a component that spans at the end of the chunk can hold the first spanning site
         const bool spans = threadIdx.x < tn && wp.tot[comp] == (kFlagLo | kFlagHi);
         uint32_t st = kEmptySlot;
-        if (__syncthreads_or(spans)) {
-            const uint32_t nlist = replay_list(x, wp, spans);
-            if (spans && comp == threadIdx.x) {
-                const uint32_t t = replay_component<true>(wp, threadIdx.x, nlist, C, status);
-                if (t != kEmptySlot) atomicMin(&x.span_t, t);
-            }
-            __syncthreads();
-            st = x.span_t;
-        }
+        if (__syncthreads_or(spans)) st = first_span_site(wp, tn);
         if (threadIdx.x == 0) cyc_back += static_cast<unsigned long long>(clock64() - t0);
         for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey[h] = kEmptySlot;
         if (st != kEmptySlot) return b + st + 1u;
