@@ -2081,6 +2081,13 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool
 
 using namespace perc;
 
+// Workspace of a launch: the header and one slot per sample in flight -- per CTA, or per group of
+// `members` CTAs for the cooperative group kernel (its CTAs share their group's slot).
+static size_t cfg_ws_bytes(const LaunchCfg &cfg)
+{
+    return sizeof(WsHeader) + size_t(cfg.grid / cfg.members) * cfg.slot_bytes;
+}
+
 extern "C" size_t perc_workspace_bytes(int op, uint32_t max_L, uint32_t num)
 {
     if (op == PERC_OP_RANK) {
@@ -2090,10 +2097,9 @@ extern "C" size_t perc_workspace_bytes(int op, uint32_t max_L, uint32_t num)
     if (op != PERC_OP_NSTAR && op != PERC_OP_MASS && op != PERC_OP_SMAX) return 0;
     LaunchCfg cfg;
     if (launch_cfg(op, max_L, num, cfg) != PERC_OK) return 0;
-    size_t bytes = sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes;
+    size_t bytes = cfg_ws_bytes(cfg);
     LaunchCfg sw;  // perc_nstar may run either method: room for both
-    if (op == PERC_OP_NSTAR && launch_cfg(kOpSweep, max_L, num, sw) == PERC_OK)
-        bytes = std::max(bytes, sizeof(WsHeader) + size_t(sw.grid) * sw.slot_bytes);
+    if (op == PERC_OP_NSTAR && launch_cfg(kOpSweep, max_L, num, sw) == PERC_OK) bytes = std::max(bytes, cfg_ws_bytes(sw));
     return bytes;
 }
 
@@ -2121,14 +2127,14 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
     if (method < 0) return method;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (method == 2) {
-        if (ws_bytes < sizeof(WsHeader) + size_t(sw.grid) * sw.slot_bytes) return PERC_EWORKSPACE;
+        if (ws_bytes < cfg_ws_bytes(sw)) return PERC_EWORKSPACE;
         if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
         k_nstar_sweep<<<sw.grid, sw.threads, sw.smem, stream>>>(samples, num_samples, max_L, sw.smem_L, sw.node_cap,
                                                                 sw.edge_scap, bracket, nstar, passes, stats,
                                                                 static_cast<char *>(workspace), sw.slot_bytes);
         return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
     }
-    if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
+    if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
     if (cfg.members > 1) {
         // every group's barrier counters, abort flag and shared scalars start at zero
@@ -2163,7 +2169,7 @@ extern "C" int perc_mass(const perc_sample *samples, uint32_t num_samples, uint3
     LaunchCfg cfg;
     int rc = launch_cfg(PERC_OP_MASS, max_L, num_samples, cfg);
     if (rc != PERC_OK) return rc;
-    if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
+    if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
     k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap, cfg.edge_scap, n, mass,
@@ -2180,7 +2186,7 @@ extern "C" int perc_smax_window(const perc_sample *samples, uint32_t num_samples
     LaunchCfg cfg;
     int rc = launch_cfg(PERC_OP_SMAX, max_L, num_samples, cfg);
     if (rc != PERC_OK) return rc;
-    if (ws_bytes < sizeof(WsHeader) + size_t(cfg.grid) * cfg.slot_bytes) return PERC_EWORKSPACE;
+    if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
     k_smax<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap,

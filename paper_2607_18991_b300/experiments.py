@@ -11,6 +11,8 @@ Each run prints one JSON line:
   bracket (network trained at L = 8 and 16 only) and with the plain one;
 * ``L40``   -- sc(5)-1,...,7 at L = 40 (102.4M sites), seeds 1..8;
 * ``mixed`` -- 4096 samples with L uniform in {10..40} and random masks, plain and learned;
+* ``large`` -- the largest lattices: L = 48 (254.8M sites), all 127 neighborhoods, seeds 1..2, and
+  L = 64 (1.07G sites), sc(5)-1,...,7, seeds 1..4; samples/s with the plain bracket;
 * ``universality`` -- p_hat(k, L) = mean n*/L^5 for all 127 neighborhoods at L in {8, 12, 16, 20, 24},
   extrapolated per neighborhood to L -> infinity (p_hat = p_c + A L^(-1/nu)), compared with Table I,
   and the universality fits p_c = c/(z+b), p_c = zeta^(-g), p_c = a zeta^(-g) on those values and on
@@ -118,6 +120,17 @@ def run_mixed(params, quick: bool = False) -> dict:
 UNIV_SEEDS = {8: 512, 12: 256, 16: 128, 20: 64, 24: 32}
 
 
+def run_large(quick: bool = False) -> dict:
+    out = {"workload": "largest lattices, plain bracket, times with the ranking of every seed"}
+    for name, wl in (("L48_all127", workloads.samples(48, workloads.ALL_MASKS, range(1, 2 if quick else 3))),
+                     ("L64_z892", workloads.samples(64, [127], range(1, 2 if quick else 5)))):
+        (ns, passes), dt = _timed(lambda: driver.nstar(wl))
+        out[name] = {"samples": len(wl), "seconds": dt, "samples_per_s": len(wl) / dt,
+                     "mean_nstar_over_N": float(np.mean(ns / float(wl[0, 0]) ** 5)),
+                     "passes_per_sample": float(passes.mean())}
+    return out
+
+
 def _fits(z, zeta, pc) -> dict:
     (b, c), (eb, ec), rss = analysis.fit_rational_z(z, pc)
     (g,), (eg,), rss_g = analysis.fit_power_zeta(zeta, pc)
@@ -155,17 +168,19 @@ def run_universality(quick: bool = False) -> dict:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["mass", "L24", "L40", "mixed", "universality", "all"])
+    ap.add_argument("which", choices=["mass", "L24", "L40", "mixed", "universality", "large", "all"])
     ap.add_argument("--quick", action="store_true")
     args = ap.parse_args()
     torch.cuda.set_device(0)
-    params = None if args.which in ("mass", "universality") else trained_params(args.quick)
+    params = None if args.which in ("mass", "universality", "large") else trained_params(args.quick)
     todo = ["mass", "L24", "L40", "mixed"] if args.which == "all" else [args.which]
     for w in todo:
         if w == "mass":
             r = run_mass(args.quick)
         elif w == "universality":
             r = run_universality(args.quick)
+        elif w == "large":
+            r = run_large(args.quick)
         elif w == "L24":
             r = run_L24(params, args.quick)
         elif w == "L40":

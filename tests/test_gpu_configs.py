@@ -1,5 +1,8 @@
 """Parity on the other workloads: compact-neighborhood masses, L = 24 with the learned bracket,
-L = 40 (the largest lattice), the mixed-L batch, and the full L = 16 benchmark launch (sampled)."""
+L = 40, the mixed-L batch, the full L = 16 benchmark launch (sampled), and lattices of 254.8M and
+1.07G sites (L = 48, 64) against n* the oracle stored in tests/golden/nstar_large.txt."""
+import os
+
 import numpy as np
 import pytest
 
@@ -81,3 +84,27 @@ def test_full_size_L16_launch_sampled(method):
     assert np.array_equal(ns[sel], orc_nstar(step.workload[sel]))
     if method == "bisection":
         assert passes.max() <= 2 * 20 + 1  # a fallback costs one failed check plus the plain bisection
+
+
+def _stored_large(L):
+    path = os.path.join(os.path.dirname(__file__), "golden", "nstar_large.txt")
+    rows = [tuple(int(v) for v in line.split()) for line in open(path) if line.strip() and not line.startswith("#")]
+    rows = [r for r in rows if r[0] == L]
+    return np.array([r[:3] for r in rows], dtype=np.int64), np.array([r[3] for r in rows], dtype=np.uint32)
+
+
+@pytest.mark.parametrize("L", [48, 64])
+def test_large_lattices_against_stored_oracle(L):
+    """A few samples on the largest lattices, both n* methods: the automatic one (cooperative CTA
+    groups running the bisection, for so few samples) and the sweep on one CTA a sample."""
+    from paper_2607_18991_b300 import driver, perc
+    w, want = _stored_large(L)
+    assert len(w) > 0
+    ns, _ = driver.nstar(w)
+    assert np.array_equal(ns, want)
+    perc.set_launch_option(perc.OPT_METHOD, perc.METHOD_SWEEP)
+    try:
+        ns_sweep, _ = driver.nstar(w)
+    finally:
+        perc.set_launch_option(perc.OPT_METHOD, perc.METHOD_AUTO)
+    assert np.array_equal(ns_sweep, want)
