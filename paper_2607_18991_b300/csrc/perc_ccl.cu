@@ -1355,7 +1355,6 @@ __device__ __forceinline__ void window_scan(const Ctl &c, const uint32_t *bm, co
 
 struct SmaxShared {
     uint32_t run_max;  // S_max after the last site added
-    uint32_t span_t;   // first chunk site whose cluster spans (n* sweep)
     uint32_t red[32];
 };
 
@@ -1381,10 +1380,7 @@ __device__ __forceinline__ uint32_t chunk_front(Ctl &c, SmaxShared &x, const Nod
     wp.ev[threadIdx.x] = 0u;
     if (!kSpan) wp.lp[threadIdx.x] = kRootBit | 1u;
     for (uint32_t y = threadIdx.x; y < C + kRootHash; y += C) wp.cc[y] = y;
-    if (threadIdx.x == 0) {
-        c.ecount[0] = 0u;
-        x.span_t = kEmptySlot;
-    }
+    if (threadIdx.x == 0) c.ecount[0] = 0u;
     uint32_t site = 0u;
     if (threadIdx.x < count) {  // the chunk's sites join the bitmap
         site = __ldg(smp.perm + b + threadIdx.x);
@@ -1509,20 +1505,16 @@ __device__ __forceinline__ uint32_t replay_list(SmaxShared &x, const WinPtrs &wp
 
 // Replay of the component rooted at chunk site t0 (one thread): its sites in rank order (found in
 // the replay list), each merged with the clusters its records name (union by size on the local
-// slots; entries kRootBit | size, or kRootBit | size << 2 | flags for the sweep).  S_max windows:
-// ev[t] = the cluster size right after site t.  Sweep: returns the first site whose cluster carries
-// both border flags, or kEmptySlot.
-template <bool kSpan>
-__device__ __forceinline__ uint32_t replay_component(const WinPtrs &wp, uint32_t t0, uint32_t nlist, uint32_t C,
-                                                     int *status)
+// slots; entries kRootBit | size); ev[t] = the cluster size right after site t.
+__device__ __forceinline__ void replay_component(const WinPtrs &wp, uint32_t t0, uint32_t nlist, uint32_t C,
+                                                 int *status)
 {
     const uint32_t s_lp = smem_addr(wp.lp);
-    constexpr uint32_t kSz = kSpan ? 2u : 0u;  // shift of the size field
     for (uint32_t i = 0; i < nlist; ++i) {
         const uint32_t t = wp.gm[i];
         if (wp.memb[t] != t0) continue;
         const uint32_t k0 = wp.off[t], k1 = wp.off[t + 1u];
-        uint32_t ra = t, ea = lds_u32(s_lp + 4u * t);  // no earlier record names site t: a root
+        uint32_t ra = t, sa = lds_u32(s_lp + 4u * t) & ~kRootBit;  // no earlier record names site t: a root
         for (uint32_t k = k0; k < k1; ++k) {
             const uint32_t bs = wp.rec[k] & kRecSlot;
             if (bs >= C + kRootHash) {  // full hash (ruled out by the capacities)
@@ -1543,24 +1535,18 @@ __device__ __forceinline__ uint32_t replay_component(const WinPtrs &wp, uint32_t
                 v = lds_u32(s_lp + 4u * g);
             }
             if (xr == ra) continue;
-            const uint32_t sa = (ea & ~kRootBit) >> kSz, sb = (v & ~kRootBit) >> kSz;
-            const uint32_t e = kRootBit | ((sa + sb) << kSz) | (kSpan ? ((ea | v) & 3u) : 0u);
+            const uint32_t sb = v & ~kRootBit;
             if (sa >= sb) {
                 sts_u32(s_lp + 4u * xr, ra);
             } else {
                 sts_u32(s_lp + 4u * ra, xr);
                 ra = xr;
             }
-            ea = e;
-            sts_u32(s_lp + 4u * ra, ea);
+            sa += sb;
+            sts_u32(s_lp + 4u * ra, kRootBit | sa);
         }
-        if (kSpan) {
-            if ((ea & 3u) == (kFlagLo | kFlagHi)) return t;
-        } else {
-            wp.ev[t] = ea & ~kRootBit;
-        }
+        wp.ev[t] = sa;
     }
-    return kEmptySlot;
 }
 
 // One sample of k_smax (all threads).  Writes row[k] = S_max(n_lo + k) for n_lo + k <= n_end.
@@ -1608,7 +1594,7 @@ __device__ void smax_sample(Ctl &c, SmaxShared &x, const Nodes &P, const Nodes &
         const bool need = threadIdx.x < tn && wp.tot[comp] > run0;
         if (__syncthreads_or(need)) {
             const uint32_t nlist = replay_list(x, wp, need);
-            if (need && comp == threadIdx.x) replay_component<false>(wp, threadIdx.x, nlist, C, status);
+            if (need && comp == threadIdx.x) replay_component(wp, threadIdx.x, nlist, C, status);
             __syncthreads();
         }
         const uint32_t v = threadIdx.x < tn ? wp.ev[threadIdx.x] : 0u;

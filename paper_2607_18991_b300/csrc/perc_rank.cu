@@ -11,6 +11,7 @@
 //                  eight ballots), tile staged in shared memory in digit order, written in runs,
 // and the last scatter also writes rank[perm[r]] = r.  Seeds are sorted in chunks that fit the
 // workspace.
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 
@@ -53,7 +54,7 @@ static inline uint32_t rank_chunk(uint64_t N, uint32_t num_seeds)
 size_t rank_workspace_bytes(uint32_t L, uint32_t num_seeds)
 {
     const uint64_t N = num_sites(L);
-    return 256 + size_t(rank_chunk(N, num_seeds)) * rank_bytes_per_seed(N);
+    return 256 + 16 + size_t(rank_chunk(N, num_seeds)) * rank_bytes_per_seed(N);  // (+16: hist alignment)
 }
 
 // Element e of a tile is read by warp (e / 256), round ((e / 32) % 8), lane (e % 32): warp-major,
@@ -86,42 +87,55 @@ k_rank_hist(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ seeds
     if (threadIdx.x < 256) hist[(size_t(s) * 256 + threadIdx.x) * T + tile] = h[threadIdx.x];
 }
 
-// Exclusive scan of one seed's 256*T counters (digit-major), one block per seed.
+// Exclusive scan of one seed's 256*T counters (digit-major), one block per seed: rounds of
+// 4 * blockDim consecutive counters, each thread reading four neighbours at once (coalesced 16-byte
+// loads; the row starts 1024-byte aligned), a block scan of the threads' sums and a running carry.
 __global__ void __launch_bounds__(1024) k_rank_scan(uint32_t T, uint32_t *__restrict__ hist)
 {
     __shared__ uint32_t warp_sum[32];
+    __shared__ uint32_t carry_s;
     uint32_t *h = hist + size_t(blockIdx.x) * 256 * T;
-    const uint32_t n = 256u * T;
-    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
-    const uint32_t b = threadIdx.x * per;
-    const uint32_t e = min(n, b + per);
-    uint32_t local = 0;
-    for (uint32_t i = b; i < e; ++i) local += h[i];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        uint32_t w = lane < nw ? warp_sum[lane] : 0u;
+    const uint32_t n = 256u * T;  // a multiple of 4
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < n; base += 4u * blockDim.x) {
+        const uint32_t i = base + 4u * threadIdx.x;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (i < n) v = *reinterpret_cast<const uint4 *>(h + i);
+        const uint32_t local = v.x + v.y + v.z + v.w;
+        uint32_t x = local;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        if (lane < nw) warp_sum[lane] = w;  // inclusive
-    }
-    __syncthreads();
-    uint32_t run = x - local + (warp > 0 ? warp_sum[warp - 1] : 0u);
-    for (uint32_t i = b; i < e; ++i) {
-        const uint32_t c = h[i];
-        h[i] = run;
-        run += c;
+        if (lane == 31) warp_sum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = lane < nw ? warp_sum[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < nw) warp_sum[lane] = w;  // inclusive
+            if (lane == nw - 1) carry_s = carry + w;
+        }
+        __syncthreads();
+        if (i < n) {
+            uint32_t run = carry + x - local + (warp > 0 ? warp_sum[warp - 1] : 0u);
+            uint4 o;
+            o.x = run;
+            run += v.x;
+            o.y = run;
+            run += v.y;
+            o.z = run;
+            run += v.z;
+            o.w = run;
+            *reinterpret_cast<uint4 *>(h + i) = o;
+        }
+        carry = carry_s;
+        __syncthreads();  // warp_sum and carry_s are rewritten by the next round
     }
 }
 
@@ -461,7 +475,9 @@ extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, 
     char *ws = static_cast<char *>(workspace) + 256;
     uint32_t *a_keys = reinterpret_cast<uint32_t *>(ws);
     uint32_t *a_vals = a_keys + size_t(chunk) * N;
-    uint32_t *hist = a_vals + size_t(chunk) * N;
+    // the histograms start 16-byte aligned: k_rank_scan reads and writes them four at a time
+    uint32_t *hist = reinterpret_cast<uint32_t *>((reinterpret_cast<uintptr_t>(a_vals + size_t(chunk) * N) + 15) &
+                                                  ~uintptr_t(15));
 
     static bool attr_set = false;
     static uint32_t tma_ctas = 0;
