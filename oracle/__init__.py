@@ -13,8 +13,10 @@ Contents and the passages they follow:
   SC'11) and ordered by (key, site index).
 * ``nz`` -- the sequential Newman--Ziff sweep: n* (first n with a cluster touching x1 = 0 and
   x1 = L-1) and S_max(n) (eq. Pmax).
+* ``nstar_span`` -- the same sweep's n* under another spanning rule: both borders of axis a
+  (x_{a+1} = 0 and x_{a+1} = L-1, a = 0..4) or of any axis (``SPAN_ANY``), with ten border flags.
 * ``bfs`` and ``minimax_nstar`` -- independent brute-force cross-checks (flood fill at fixed n;
-  bottleneck-path identity) used only to pin ``nz``.
+  bottleneck-path identity) used only to pin ``nz`` and ``nstar_span``.
 * ``smax_prefix`` -- the same sweep stopped after n_stop sites: S_max(n) for n = 0..n_stop.
 * ``binomial_weights`` / ``binomial_convolve`` / ``pmax`` -- S_max(n) -> S_max(p) (Methods,
   "Computational methods") and P_max(p) = S_max(p) / L^5 (eq. Pmax).
@@ -31,6 +33,7 @@ import subprocess
 import numpy as np
 
 NEVER = 0xFFFFFFFF
+SPAN_ANY = 5  # spanning rule: both borders of some axis
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "perc_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
@@ -67,8 +70,14 @@ def lib():
         L.orc_nz.restype = i32
         L.orc_bfs.argtypes = [u32, u32, P(u32), u64, P(i32), P(i64)]
         L.orc_bfs.restype = i32
+        L.orc_bfs_span.argtypes = [u32, u32, u32, P(u32), u64, P(i32), P(i64)]
+        L.orc_bfs_span.restype = i32
         L.orc_minimax_nstar.argtypes = [u32, u32, P(u32)]
         L.orc_minimax_nstar.restype = u32
+        L.orc_minimax_nstar_axis.argtypes = [u32, u32, u32, P(u32)]
+        L.orc_minimax_nstar_axis.restype = u32
+        L.orc_nstar_span.argtypes = [u32, u32, u32, P(u32), P(u32), P(u32)]
+        L.orc_nstar_span.restype = i32
         L.orc_smax_prefix.argtypes = [u32, u32, P(u32), P(u32), u64, P(i64)]
         L.orc_smax_prefix.restype = i32
         L.orc_binomial_weights.argtypes = [u64, ctypes.c_double, P(ctypes.c_double)]
@@ -161,20 +170,34 @@ def smax_prefix(L: int, mask: int, perm: np.ndarray, rk: np.ndarray, n_stop: int
     return out
 
 
-def bfs(L: int, mask: int, rk: np.ndarray, n: int) -> tuple[bool, int]:
-    """Flood fill of the sites with rank < n: (some cluster spans x1, S_max)."""
+def nstar_span(L: int, mask: int, span: int, perm: np.ndarray, rk: np.ndarray) -> int:
+    """n* of the sweep under spanning rule ``span``: 0..4 = both borders of axis x_{span+1},
+    SPAN_ANY = both borders of some axis."""
+    out = ctypes.c_uint32()
+    perm = np.ascontiguousarray(perm, dtype=np.uint32)
+    rk = np.ascontiguousarray(rk, dtype=np.uint32)
+    if lib().orc_nstar_span(L, mask, span, _ptr(perm, ctypes.c_uint32), _ptr(rk, ctypes.c_uint32),
+                            ctypes.byref(out)) != 0:
+        raise ValueError(f"orc_nstar_span failed for L={L} mask={mask} span={span}")
+    return out.value
+
+
+def bfs(L: int, mask: int, rk: np.ndarray, n: int, span: int = 0) -> tuple[bool, int]:
+    """Flood fill of the sites with rank < n: (some cluster spans under rule ``span``, S_max)."""
     sp = ctypes.c_int()
     sm = ctypes.c_int64()
     rk = np.ascontiguousarray(rk, dtype=np.uint32)
-    if lib().orc_bfs(L, mask, _ptr(rk, ctypes.c_uint32), n, ctypes.byref(sp), ctypes.byref(sm)) != 0:
-        raise ValueError("orc_bfs failed")
+    if lib().orc_bfs_span(L, mask, span, _ptr(rk, ctypes.c_uint32), n, ctypes.byref(sp),
+                          ctypes.byref(sm)) != 0:
+        raise ValueError("orc_bfs_span failed")
     return bool(sp.value), sm.value
 
 
-def minimax_nstar(L: int, mask: int, rk: np.ndarray) -> int:
-    """n* from the bottleneck-path identity (Dijkstra with max as path cost)."""
+def minimax_nstar(L: int, mask: int, rk: np.ndarray, axis: int = 0) -> int:
+    """n* from the bottleneck-path identity between the faces x_{axis+1} = 0 and = L-1
+    (Dijkstra with max as path cost)."""
     rk = np.ascontiguousarray(rk, dtype=np.uint32)
-    return int(lib().orc_minimax_nstar(L, mask, _ptr(rk, ctypes.c_uint32)))
+    return int(lib().orc_minimax_nstar_axis(L, mask, axis, _ptr(rk, ctypes.c_uint32)))
 
 
 def binomial_convolve(q_of_n: np.ndarray, p: float) -> float:
@@ -198,11 +221,12 @@ def pmax(smax_all: np.ndarray, L: int, p: float) -> float:
     return binomial_convolve(np.asarray(smax_all, dtype=np.float64), p) / N
 
 
-def nstar_batch(L: int, seeds, masks) -> np.ndarray:
-    """n*[len(masks), len(seeds)] by one ranking per seed and one sweep per (mask, seed)."""
+def nstar_batch(L: int, seeds, masks, span: int = 0) -> np.ndarray:
+    """n*[len(masks), len(seeds)] by one ranking per seed and one sweep per (mask, seed), under
+    spanning rule ``span`` (0 = the x1 axis)."""
     out = np.zeros((len(masks), len(seeds)), dtype=np.uint32)
     for s_i, seed in enumerate(seeds):
         perm, rk = rank(L, int(seed))
         for m_i, m in enumerate(masks):
-            out[m_i, s_i] = nz(L, int(m), perm, rk)[0]
+            out[m_i, s_i] = nz(L, int(m), perm, rk)[0] if span == 0 else nstar_span(L, int(m), span, perm, rk)
     return out

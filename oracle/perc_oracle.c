@@ -12,7 +12,9 @@
  *     Philox4x32-10 counter-based generator (Salmon et al., SC'11) and ordered by (key, index);
  *   - the Newman--Ziff sweep: add the sites one at a time in that order and merge clusters with
  *     union-find, which gives, for every n, the largest cluster S_max(n) (eq. Pmax) and the first
- *     n at which a cluster touches both borders x1 = 0 and x1 = L-1 (the spanning cluster);
+ *     n at which a cluster touches both borders x1 = 0 and x1 = L-1 (the spanning cluster), or,
+ *     as a variant of the spanning rule, both borders x_a = 0 and x_a = L-1 of another axis a, or
+ *     of any axis;
  *   - independent cross-checks used only to pin the sweep: a breadth-first flood fill at a fixed
  *     n, and the bottleneck (minimax) path identity for the first spanning n;
  *   - the binomial convolution that turns S_max(n) into S_max(p).
@@ -183,12 +185,30 @@ static int64_t orc_neighbor(uint32_t L, const int x[5], const int8_t *v)
 /* ------------------------------------------------------------------------------------------ */
 /* Newman--Ziff sweep (Methods, "Computational methods").  Sites are added in rank order; each   */
 /* new site is merged with every already occupied neighbor by union-find (union by size, path   */
-/* compression).  A cluster carries two border flags: LO (has a site with x1 = 0) and HI (has a  */
-/* site with x1 = L-1).  Adding one site can only make its own cluster spanning, so the first n  */
-/* at which the new site's cluster carries LO|HI is n*.  S_max is tracked after every addition.  */
+/* compression).  A cluster carries ten border flags: bit 2a (has a site with x_{a+1} = 0) and  */
+/* bit 2a+1 (has a site with x_{a+1} = L-1), a = 0..4.  The spanning rule `span` is an axis     */
+/* 0..4 (x1..x5: the cluster carries both flags of that axis) or ORC_SPAN_ANY (both flags of     */
+/* some axis).  Adding one site can only make its own cluster spanning, so the first n at which  */
+/* the new site's cluster spans is n*.  S_max is tracked after every addition.                   */
 /* ------------------------------------------------------------------------------------------ */
-#define ORC_LO 1u
-#define ORC_HI 2u
+#define ORC_SPAN_ANY 5u
+
+static uint16_t orc_site_flags(uint32_t L, const int x[5])
+{
+    uint16_t f = 0;
+    for (int a = 0; a < 5; ++a) {
+        if (x[a] == 0) f |= (uint16_t)(1u << (2 * a));
+        if (x[a] == (int)L - 1) f |= (uint16_t)(1u << (2 * a + 1));
+    }
+    return f;
+}
+
+static int orc_spans(uint16_t f, uint32_t span)
+{
+    for (uint32_t a = 0; a < 5; ++a)
+        if ((span == ORC_SPAN_ANY || span == a) && ((f >> (2 * a)) & 3u) == 3u) return 1;
+    return 0;
+}
 
 static uint32_t orc_find(uint32_t *parent, uint32_t a)
 {
@@ -205,17 +225,18 @@ static uint32_t orc_find(uint32_t *parent, uint32_t a)
 /*
  * Runs the sweep for one (L, mask) on a given order over the first n_limit sites (n_limit <= N).
  * Outputs:
- *   *nstar_out            first spanning n <= n_limit (ORC_NEVER if none);
+ *   *nstar_out            first spanning n <= n_limit under the rule `span` (ORC_NEVER if none);
  *   smax_at[q]            S_max after nq[q] sites (nq[q] in [0, n_limit]); nq may be NULL when nnq = 0;
  *   smax_all (optional)   S_max(n) for n = 0..n_limit (n_limit+1 entries), NULL to skip.
  * Returns 0, or -1 on bad input / no memory.
  */
-static int orc_sweep(uint32_t L, uint32_t mask, const uint32_t *perm, const uint32_t *rank,
+static int orc_sweep(uint32_t L, uint32_t mask, uint32_t span, const uint32_t *perm, const uint32_t *rank,
                      const uint64_t *nq, uint32_t nnq, int64_t *smax_at, uint32_t *nstar_out,
                      int64_t *smax_all, uint64_t n_limit)
 {
     uint64_t N = orc_num_sites(L);
-    if (L == 0 || N >= 0xFFFFFFFFull || mask < 1 || mask > 127 || n_limit > N) return -1;
+    if (L == 0 || N >= 0xFFFFFFFFull || mask < 1 || mask > 127 || span > ORC_SPAN_ANY || n_limit > N)
+        return -1;
     for (uint32_t q = 0; q < nnq; ++q)
         if (nq[q] > n_limit) return -1;
 
@@ -224,7 +245,7 @@ static int orc_sweep(uint32_t L, uint32_t mask, const uint32_t *perm, const uint
 
     uint32_t *parent = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
     uint32_t *size = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
-    uint8_t *flags = (uint8_t *)malloc((size_t)N);
+    uint16_t *flags = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)N);
     if (!parent || !size || !flags) {
         free(parent); free(size); free(flags);
         return -1;
@@ -245,7 +266,7 @@ static int orc_sweep(uint32_t L, uint32_t mask, const uint32_t *perm, const uint
         orc_coords(L, i, x);
         parent[i] = i;
         size[i] = 1;
-        flags[i] = (uint8_t)((x[0] == 0 ? ORC_LO : 0u) | (x[0] == (int)L - 1 ? ORC_HI : 0u));
+        flags[i] = orc_site_flags(L, x);
         for (int v = 0; v < z; ++v) {
             int64_t j = orc_neighbor(L, x, offs + 5 * v);
             if (j < 0 || rank[j] >= r) continue; /* empty neighbor */
@@ -259,7 +280,7 @@ static int orc_sweep(uint32_t L, uint32_t mask, const uint32_t *perm, const uint
         uint32_t root = orc_find(parent, i);
         if (size[root] > smax) smax = size[root];
         uint64_t n = r + 1;
-        if (nstar == ORC_NEVER && flags[root] == (ORC_LO | ORC_HI)) nstar = (uint32_t)n;
+        if (nstar == ORC_NEVER && orc_spans(flags[root], span)) nstar = (uint32_t)n;
         for (uint32_t q = 0; q < nnq; ++q)
             if (nq[q] == n) smax_at[q] = smax;
         if (smax_all) smax_all[n] = smax;
@@ -275,7 +296,14 @@ int orc_nz(uint32_t L, uint32_t mask, const uint32_t *perm, const uint32_t *rank
            const uint64_t *nq, uint32_t nnq, int64_t *smax_at, uint32_t *nstar_out,
            int64_t *smax_all)
 {
-    return orc_sweep(L, mask, perm, rank, nq, nnq, smax_at, nstar_out, smax_all, orc_num_sites(L));
+    return orc_sweep(L, mask, 0, perm, rank, nq, nnq, smax_at, nstar_out, smax_all, orc_num_sites(L));
+}
+
+/* n* alone under the spanning rule `span` (0..4: axis x_{span+1}; ORC_SPAN_ANY: any axis). */
+int orc_nstar_span(uint32_t L, uint32_t mask, uint32_t span, const uint32_t *perm, const uint32_t *rank,
+                   uint32_t *nstar_out)
+{
+    return orc_sweep(L, mask, span, perm, rank, NULL, 0, NULL, nstar_out, NULL, orc_num_sites(L));
 }
 
 /* S_max(n) for n = 0..n_stop (n_stop + 1 entries): the sweep stopped after n_stop sites. */
@@ -284,18 +312,20 @@ int orc_smax_prefix(uint32_t L, uint32_t mask, const uint32_t *perm, const uint3
 {
     uint32_t nstar;
     if (!smax_prefix) return -1;
-    return orc_sweep(L, mask, perm, rank, NULL, 0, NULL, &nstar, smax_prefix, n_stop);
+    return orc_sweep(L, mask, 0, perm, rank, NULL, 0, NULL, &nstar, smax_prefix, n_stop);
 }
 
 /* ------------------------------------------------------------------------------------------ */
 /* Brute force at a fixed n: occupy the sites with rank < n and flood-fill every cluster.        */
-/* Independent of the sweep (no union-find); used only to pin it on tiny lattices.               */
+/* Independent of the sweep (no union-find, no border flags); used only to pin it on tiny        */
+/* lattices.  A cluster spans axis a when it holds a site with x_{a+1} = 0 and one with          */
+/* x_{a+1} = L-1; `span` as for the sweep.                                                       */
 /* ------------------------------------------------------------------------------------------ */
-int orc_bfs(uint32_t L, uint32_t mask, const uint32_t *rank, uint64_t n,
-            int *spans, int64_t *smax)
+int orc_bfs_span(uint32_t L, uint32_t mask, uint32_t span, const uint32_t *rank, uint64_t n,
+                 int *spans, int64_t *smax)
 {
     uint64_t N = orc_num_sites(L);
-    if (L == 0 || N >= 0xFFFFFFFFull || mask < 1 || mask > 127 || n > N) return -1;
+    if (L == 0 || N >= 0xFFFFFFFFull || mask < 1 || mask > 127 || span > ORC_SPAN_ANY || n > N) return -1;
     int8_t offs[892 * 5];
     int z = orc_mask_offsets((int)mask, offs);
     uint8_t *seen = (uint8_t *)calloc((size_t)N, 1);
@@ -309,7 +339,7 @@ int orc_bfs(uint32_t L, uint32_t mask, const uint32_t *rank, uint64_t n,
     for (uint64_t s = 0; s < N; ++s) {
         if (rank[s] >= n || seen[s]) continue;
         int64_t count = 0;
-        int lo = 0, hi = 0;
+        int lo[5] = {0, 0, 0, 0, 0}, hi[5] = {0, 0, 0, 0, 0};
         uint64_t top = 0;
         stack[top++] = (uint32_t)s;
         seen[s] = 1;
@@ -318,8 +348,10 @@ int orc_bfs(uint32_t L, uint32_t mask, const uint32_t *rank, uint64_t n,
             int x[5];
             orc_coords(L, u, x);
             ++count;
-            if (x[0] == 0) lo = 1;
-            if (x[0] == (int)L - 1) hi = 1;
+            for (int a = 0; a < 5; ++a) {
+                if (x[a] == 0) lo[a] = 1;
+                if (x[a] == (int)L - 1) hi[a] = 1;
+            }
             for (int v = 0; v < z; ++v) {
                 int64_t j = orc_neighbor(L, x, offs + 5 * v);
                 if (j < 0 || rank[j] >= n || seen[j]) continue;
@@ -327,7 +359,8 @@ int orc_bfs(uint32_t L, uint32_t mask, const uint32_t *rank, uint64_t n,
                 stack[top++] = (uint32_t)j;
             }
         }
-        if (lo && hi) sp_any = 1;
+        for (uint32_t a = 0; a < 5; ++a)
+            if ((span == ORC_SPAN_ANY || span == a) && lo[a] && hi[a]) sp_any = 1;
         if (count > best) best = count;
     }
     *spans = sp_any;
@@ -336,9 +369,14 @@ int orc_bfs(uint32_t L, uint32_t mask, const uint32_t *rank, uint64_t n,
     return 0;
 }
 
+int orc_bfs(uint32_t L, uint32_t mask, const uint32_t *rank, uint64_t n, int *spans, int64_t *smax)
+{
+    return orc_bfs_span(L, mask, 0, rank, n, spans, smax);
+}
+
 /* ------------------------------------------------------------------------------------------ */
-/* Bottleneck-path identity: n* = 1 + min over paths from the face x1 = 0 to the face           */
-/* x1 = L-1 of the largest rank on the path.  Computed by Dijkstra's algorithm with the path     */
+/* Bottleneck-path identity: n* = 1 + min over paths from the face x_a = 0 to the face          */
+/* x_a = L-1 (a = axis + 1) of the largest rank on the path.  Computed by Dijkstra's algorithm with the path     */
 /* cost "max" instead of "+", on a binary heap.  Independent of the sweep and of the flood fill. */
 /* ------------------------------------------------------------------------------------------ */
 typedef struct { uint32_t cost, site; } orc_he;
@@ -371,10 +409,10 @@ static orc_he orc_heap_pop(orc_he *h, uint64_t *len)
     return top;
 }
 
-uint32_t orc_minimax_nstar(uint32_t L, uint32_t mask, const uint32_t *rank)
+uint32_t orc_minimax_nstar_axis(uint32_t L, uint32_t mask, uint32_t axis, const uint32_t *rank)
 {
     uint64_t N = orc_num_sites(L);
-    if (L == 0 || N >= 0xFFFFFFFFull || mask < 1 || mask > 127) return ORC_NEVER;
+    if (L == 0 || N >= 0xFFFFFFFFull || mask < 1 || mask > 127 || axis > 4) return ORC_NEVER;
     int8_t offs[892 * 5];
     int z = orc_mask_offsets((int)mask, offs);
     uint32_t *best = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
@@ -386,9 +424,11 @@ uint32_t orc_minimax_nstar(uint32_t L, uint32_t mask, const uint32_t *rank)
         free(best); free(done); free(heap);
         return ORC_NEVER;
     }
-    uint64_t face = N / L; /* sites with x1 = 0 are indices [0, L^4) */
     for (uint64_t i = 0; i < N; ++i) best[i] = ORC_NEVER;
-    for (uint64_t i = 0; i < face; ++i) {
+    for (uint64_t i = 0; i < N; ++i) {
+        int x[5];
+        orc_coords(L, (uint32_t)i, x);
+        if (x[axis] != 0) continue; /* sources: the face x_a = 0 */
         best[i] = rank[i];
         orc_heap_push(heap, &len, (orc_he){rank[i], (uint32_t)i});
     }
@@ -399,7 +439,7 @@ uint32_t orc_minimax_nstar(uint32_t L, uint32_t mask, const uint32_t *rank)
         done[e.site] = 1;
         int x[5];
         orc_coords(L, e.site, x);
-        if (x[0] == (int)L - 1) { /* first target settled carries the minimum bottleneck */
+        if (x[axis] == (int)L - 1) { /* first target settled carries the minimum bottleneck */
             answer = e.cost;
             break;
         }
@@ -421,6 +461,11 @@ uint32_t orc_minimax_nstar(uint32_t L, uint32_t mask, const uint32_t *rank)
     }
     free(best); free(done); free(heap);
     return answer == ORC_NEVER ? ORC_NEVER : answer + 1;
+}
+
+uint32_t orc_minimax_nstar(uint32_t L, uint32_t mask, const uint32_t *rank)
+{
+    return orc_minimax_nstar_axis(L, mask, 0, rank);
 }
 
 /* ------------------------------------------------------------------------------------------ */
