@@ -16,6 +16,10 @@ rank 0 prints one JSON line.  `--impl reference` times the CPU oracle on the sam
 binomial weights of 16 probabilities per neighborhood (p_c of Table I, +-2%), S_max(n) over the
 window of n outside which each binomial has less than 1e-16 on either side, and the convolution to
 P_max(p) (eq. Pmax).
+
+`--workload any` measures n* for spanning along any of the five axes: the same step with five
+samples per (mask, seed) (spanning axis x1..x5, each with its own verified bracket) in the n*
+launch, then perc_nstar_min_axes; a sample of the metric is one (mask, seed) pair.
 """
 from __future__ import annotations
 
@@ -37,6 +41,8 @@ L = 16
 NUM_SEEDS = 256
 MASKS = list(range(1, 128))
 METRIC = "samples/sec (exact n*) at L=16 over 127 neighborhoods, learned vs plain bracket"
+ANY_METRIC = ("samples/sec (exact n* for spanning along any of the 5 axes) at L=16 over 127 neighborhoods, "
+              "learned vs plain bracket")
 PMAX_METRIC = ("samples/sec of P_max(p) curves (exact S_max(n) over the windows of n holding all but 1e-16 of "
                "each binomial, convolution at 16 p per neighborhood) at L=16 over 127 neighborhoods")
 
@@ -62,6 +68,14 @@ def _oracle_seed(seed: int) -> int:
     perm, rk = oracle.rank(L, seed)
     for m in MASKS:
         oracle.nz(L, m, perm, rk)
+    return len(MASKS)
+
+
+def _oracle_any_seed(seed: int) -> int:
+    import oracle
+    perm, rk = oracle.rank(L, seed)
+    for m in MASKS:
+        oracle.nstar_span(L, m, oracle.SPAN_ANY, perm, rk)
     return len(MASKS)
 
 
@@ -201,6 +215,7 @@ def run_ours(args):
     ws = perc.Workspace(dev)
     seeds, wl = workload_for(rank, args.num_seeds)
     num = len(wl)
+    axes = 5 if args.workload == "any" else 1
 
     # ---- bracket network: trained on plain n* of held-out seeds at L = 8 (zone 1) and L = 16
     t_train = time.perf_counter()
@@ -216,8 +231,9 @@ def run_ours(args):
     # ---- resident inputs: one preallocated step (seeds, orders, sample table, brackets, outputs)
     from paper_2607_18991_b300 import autotune
     N = L ** 5
-    step_obj = driver.NstarStep(L, MASKS, seeds, params=params, margin=args.margin)
+    step_obj = driver.NstarStep(L, MASKS, seeds, params=params, margin=args.margin, axes=axes)
     samples, br, ns, ps = step_obj.samples, step_obj.bracket, step_obj.nstar, step_obj.passes
+    nl = step_obj.launch_num  # samples of the n* launch (num x axes)
     perm, rk, ws_buf = step_obj.perm, step_obj.rank, step_obj.ws
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     lib = perc.lib()
@@ -228,11 +244,11 @@ def run_ours(args):
     if not args.no_tune:
         step_obj.run_rank()
         step_obj.run_bracket()
-        few = np.arange(min(4, len(seeds)) * len(MASKS))
+        few = np.arange(min(4, len(seeds)) * len(MASKS) * axes)
         sub = samples[torch.as_tensor(few, device=dev)]
         tuned = autotune.tune(sub, L, bracket=br[torch.as_tensor(few, device=dev)])
         torch.cuda.synchronize()
-        nb = max(perc.workspace_bytes(perc.OP_RANK, L, len(seeds)), perc.workspace_bytes(perc.OP_NSTAR, L, num))
+        nb = max(perc.workspace_bytes(perc.OP_RANK, L, len(seeds)), perc.workspace_bytes(perc.OP_NSTAR, L, nl))
         if nb > ws_buf.numel():
             step_obj.ws = ws_buf = torch.empty(nb, dtype=torch.uint8, device=dev)
 
@@ -351,11 +367,14 @@ def run_ours(args):
         params_d2.copy_(params_host, non_blocking=True)
         perc._ok(lib.perc_rank(L, seeds_d2.data_ptr(), len(seeds), perm.data_ptr(), rk.data_ptr(),
                                ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_rank")
-        perc._ok(lib.perc_bracket(params_d2.data_ptr(), samples_d2.data_ptr(), num, args.margin, br.data_ptr(), sp),
+        perc._ok(lib.perc_bracket(params_d2.data_ptr(), samples_d2.data_ptr(), nl, args.margin, br.data_ptr(), sp),
                  "perc_bracket")
-        perc._ok(lib.perc_nstar(samples_d2.data_ptr(), num, L, br.data_ptr(), ns.data_ptr(), None, None,
+        perc._ok(lib.perc_nstar(samples_d2.data_ptr(), nl, L, br.data_ptr(), ns.data_ptr(), None, None,
                                 ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_nstar")
-        ns_host.copy_(ns, non_blocking=True)
+        if axes > 1:
+            perc._ok(lib.perc_nstar_min_axes(ns.data_ptr(), num, axes, step_obj.nstar_any.data_ptr(), sp),
+                     "perc_nstar_min_axes")
+        ns_host.copy_(step_obj.nstar_any if axes > 1 else ns, non_blocking=True)
 
     for _ in range(args.warmup):
         e2e_step()
@@ -393,7 +412,7 @@ def run_ours(args):
     # reaches n* (each site and label once), per sample
     sweep = st_learned["chunks"] > 0
     if sweep:
-        alg_bytes = num * (N / 8 * 2 + 8 * L ** 4) + 12 * st_learned["new_sites"] + 8 * st_learned["hooks"]
+        alg_bytes = nl * (N / 8 * 2 + 8 * L ** 4) + 12 * st_learned["new_sites"] + 8 * st_learned["hooks"]
     else:
         alg_bytes = (st_learned["passes"] * (N / 8 * 2 + 8 * L ** 4) + 12 * st_learned["probe_sites"]
                      + 8 * st_learned["hooks"])
@@ -404,26 +423,33 @@ def run_ours(args):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     achieved = alg_bytes / (ms_nstar_learned * 1e-3) / 1e9
-    traffic = measured_traffic(("sweep_" if sweep else "") + "learned_bytes_per_launch")
+    traffic = measured_traffic(("any_" if axes > 1 else "") + ("sweep_" if sweep else "") + "learned_bytes_per_launch")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n_seeds_cpu = cpu_workers * args.cpu_seeds_per_worker
-        rate, done, dt = oracle_rate(range(1, n_seeds_cpu + 1), cpu_workers)
+        rate, done, dt = oracle_rate(range(1, n_seeds_cpu + 1), cpu_workers,
+                                     _oracle_any_seed if axes > 1 else _oracle_seed)
         cpu = {"value": rate, "unit": "samples/s", "cores": cpu_workers, "kind": "oracle",
                "sample": f"L=16, seeds 1..{n_seeds_cpu} x 127 masks ({done} samples) in {dt:.1f} s, "
-                         f"one ranking per seed, {cpu_workers} spawned workers"}
+                         f"one ranking per seed, {cpu_workers} spawned workers"
+                         + (", one any-axis sweep (ten border flags) per sample" if axes > 1 else "")}
 
-    gpu_launches = (math.ceil(len(seeds) / 64) * 13) + 2  # rank passes + bracket + nstar per step
+    # rank passes + bracket + nstar (+ the minimum over axes) per step
+    gpu_launches = (math.ceil(len(seeds) / 64) * 13) + 2 + (1 if axes > 1 else 0)
     value = world * num / (ms_learned * 1e-3)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "metric": ANY_METRIC if axes > 1 else METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic (Philox-keyed site orders, seeds per rank)",
             "config": {"workload": "all 127 neighborhoods, L=16 (1,048,576 sites), seeds 1..256 per rank, "
-                                   "32,512 samples/rank, one persistent launch",
+                                   "32,512 samples/rank, one persistent launch"
+                                   + (" of 5 spanning axes per sample (162,560 sweeps), then the minimum over "
+                                      "axes" if axes > 1 else ""),
                        "L": L, "masks": 127, "seeds_per_rank": int(len(seeds)), "samples_per_rank": num,
+                       "spanning": "any of x1..x5" if axes > 1 else "x1",
                        "bracket": "learned", "margin": args.margin,
                        "method": "sweep (chunked Newman-Ziff replay)" if sweep else "bisection",
                        "l2": "flushed (256 MiB write) between timed steps; site orders 2 GiB > L2",
@@ -680,7 +706,7 @@ def run_reference(args):
     workers = max(1, min(host_cores(), 32))
     per_step = workers  # one seed (127 samples) per worker per step
     pmax = args.workload == "pmax"
-    fn = _oracle_pmax_seed if pmax else _oracle_seed
+    fn = {"pmax": _oracle_pmax_seed, "any": _oracle_any_seed}.get(args.workload, _oracle_seed)
     for w in range(args.warmup):
         oracle_rate(range(1, min(per_step, 4) + 1), min(workers, 4), fn)
     rates, total_dt, total_done = [], 0.0, 0
@@ -692,12 +718,14 @@ def run_reference(args):
         total_done += done
     value = total_done / total_dt
     line = {
-        "impl": "reference", "metric": PMAX_METRIC if pmax else METRIC, "value": value, "unit": "samples/s",
+        "impl": "reference", "metric": {"pmax": PMAX_METRIC, "any": ANY_METRIC}.get(args.workload, METRIC),
+        "value": value, "unit": "samples/s",
         "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (Philox-keyed site orders)",
         "config": {"workload": ("P_max(p) curves (16 p at Table I p_c +- 2%), " if pmax else "") +
+                               ("n* for spanning along any axis, " if args.workload == "any" else "") +
                                "all 127 neighborhoods, L=16 (1,048,576 sites); each step a bounded sample of "
                                f"{per_step} seeds x 127 masks", "L": L, "masks": 127},
         "cpu_baseline": {"value": value, "unit": "samples/s", "cores": workers, "kind": "oracle",
@@ -722,8 +750,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
     ap.add_argument("--no-graph", dest="graph", action="store_false", help="do not time CUDA-graph replays")
-    ap.add_argument("--workload", default="nstar", choices=["nstar", "pmax"],
-                    help="nstar: the n* samples/s line (default); pmax: the P_max(p) path")
+    ap.add_argument("--workload", default="nstar", choices=["nstar", "pmax", "any"],
+                    help="nstar: the n* samples/s line (default); pmax: the P_max(p) path; any: n* for "
+                         "spanning along any of the five axes")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one learned and one plain step inside a profiler range and exit")
     args = ap.parse_args()

@@ -7,7 +7,9 @@
  * eq. Pmax; Introduction):
  *   - a sample is a lattice side L, a zone mask and a random site-addition order;
  *   - n* is the smallest number n of occupied sites (the first n in that order) for which one
- *     cluster touches both borders x1 = 0 and x1 = L-1 (open boundaries);
+ *     cluster touches both borders x1 = 0 and x1 = L-1 (open boundaries); a sample may name
+ *     another spanning axis a instead (borders x_{a+1} = 0 and x_{a+1} = L-1), and
+ *     perc_nstar_min_axes turns the five per-axis values into n* for spanning along any axis;
  *   - S_max(n) is the size of the largest cluster with the first n sites occupied.
  * The order of a sample with seed s sorts the sites ascending by (key_i, i), where key_i is word 0
  * of Philox4x32-10 with counter (i, 0, 0, 0) and key (s mod 2^32, s >> 32), and
@@ -55,11 +57,20 @@ typedef enum {
 #define PERC_OP_MASS 3
 #define PERC_OP_SMAX 4
 
+/* zone_mask word of a sample: bits 0..6 select coordination zones 1..7 (at least one); bits 8..10
+ * hold the spanning axis a = 0..4 that perc_nstar tests (borders x_{a+1} = 0 and x_{a+1} = L-1;
+ * 0, the x1 axis, is the default); every other bit is zero.  The neighborhoods are invariant under
+ * exchanging coordinates, so n* along every axis has the same distribution; perc_bracket reads the
+ * zone bits only, and perc_mass / perc_smax_window ignore the axis. */
+#define PERC_ZONE_BITS 0x7Fu
+#define PERC_AXIS_SHIFT 8u
+#define PERC_ZONE_WORD(zones, axis) ((uint32_t)(zones) | ((uint32_t)(axis) << PERC_AXIS_SHIFT))
+
 /* One sample.  perm/rank are this sample's site order (as written by perc_rank); samples that
  * share a seed point at the same arrays.  Layout: 24 bytes, 8-byte aligned. */
 typedef struct {
     uint32_t L;           /* lattice side, 1 <= L <= max_L given to the call */
-    uint32_t zone_mask;   /* bit (i-1) selects coordination zone i; 1..127 */
+    uint32_t zone_mask;   /* PERC_ZONE_WORD(zones 1..127, spanning axis 0..4) */
     const uint32_t *perm; /* device [L^5]: perm[r] = site added r-th */
     const uint32_t *rank; /* device [L^5]: rank[perm[r]] = r */
 } perc_sample;
@@ -132,6 +143,19 @@ int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, uint32_t *p
 int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
                const uint32_t *bracket, uint32_t *nstar, uint32_t *passes, perc_stats *stats,
                void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * perc_nstar_min_axes -- n* for spanning along any axis (a cluster touching both borders of some
+ * axis; the paper names no direction, Introduction) from per-axis n*: spanning along one axis is
+ * monotone in n, so out[k] = min over a < axes of nstar[k * axes + a].  The caller runs perc_nstar
+ * on `axes` samples per (order, neighborhood) that differ only in the spanning axis, stored
+ * consecutively.
+ *   nstar  device uint32[num][axes] (per-axis n*, PERC_NEVER where an axis never spans)
+ *   axes   1..5
+ *   out    device uint32[num] (output; PERC_NEVER when no axis spans)
+ * Errors: PERC_EINVAL (null pointer, num 0, axes outside 1..5), PERC_ECUDA.
+ */
+int perc_nstar_min_axes(const uint32_t *nstar, uint32_t num, uint32_t axes, uint32_t *out, void *stream);
 
 /*
  * perc_mass -- largest-cluster size S_max(n) of each sample with its first n[k] sites occupied

@@ -62,6 +62,7 @@ struct Ctl {
     uint32_t z;       // offsets of the sample's neighborhood
     uint32_t R;       // row entries of the sample's neighborhood
     uint32_t NP;      // plane entries (L = 16 path)
+    uint32_t axis;    // spanning axis of the sample: its borders are x_{axis+1} = 0 and = L-1
     uint32_t ecount[2];  // edge-list fill of the current and the next chunk
     unsigned long long hooks, new_sites, sites, unions, cyc_scan, cyc_link;
 };
@@ -374,11 +375,19 @@ struct SiteGeo {
     uint32_t allowed;  // row path: 25-bit in-lattice mask of (d1..d5); plane path: (d1..d3) part
     uint32_t a5;       // in-lattice d5 values
     uint32_t sm0, sm1, sm2, sh, wbase;  // plane path only
-    bool low, high;    // on the x1 = 0 / x1 = L-1 border
+    bool low, high;    // on the low / high border of the spanning axis (x_{axis+1} = 0 / L-1)
 };
 
+// A sample's zone_mask word: bits 0..6 the coordination zones, bits 8..10 the spanning axis 0..4,
+// every other bit zero.
+constexpr uint32_t kZoneBits = 0x7Fu, kAxisShift = 8u;
+__device__ __forceinline__ bool valid_zone_word(uint32_t w)
+{
+    return (w & kZoneBits) != 0u && (w & ~(kZoneBits | (7u << kAxisShift))) == 0u && (w >> kAxisShift) < 5u;
+}
+
 template <bool kPlanes>
-__device__ __forceinline__ SiteGeo site_geo(uint32_t i, uint32_t L, const FastDiv &fd)
+__device__ __forceinline__ SiteGeo site_geo(uint32_t i, uint32_t L, const FastDiv &fd, uint32_t axis)
 {
     SiteGeo s;
     s.i = i;
@@ -392,16 +401,18 @@ __device__ __forceinline__ SiteGeo site_geo(uint32_t i, uint32_t L, const FastDi
         s.sm2 = (a4 & 16u) ? s.a5 : 0u;
         s.sh = (i + 30u) & 31u;
         s.wbase = (i + 30u) >> 5;
-        s.low = x1 == 0u;
-        s.high = x1 == kPlaneL - 1u;
+        const uint32_t xa = (i >> (16u - 4u * axis)) & 15u;  // x_{axis+1}
+        s.low = xa == 0u;
+        s.high = xa == kPlaneL - 1u;
     } else {
         uint32_t x[5];
         site_coords(i, fd, x);
         s.allowed = site_allowed(x, L);
         s.a5 = s.allowed >> 20;
         s.sm0 = s.sm1 = s.sm2 = s.sh = s.wbase = 0u;
-        s.low = x[0] == 0u;
-        s.high = x[0] == L - 1u;
+        const uint32_t xa = axis == 0u ? x[0] : axis == 1u ? x[1] : axis == 2u ? x[2] : axis == 3u ? x[3] : x[4];
+        s.low = xa == 0u;
+        s.high = xa == L - 1u;
     }
     return s;
 }
@@ -466,7 +477,7 @@ __device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *log
         // ---- scan
         const uint32_t r = base + grp;
         if (r < r1) {
-            const SiteGeo g = site_geo<kPlanes>(__ldg(perm + r), L, fd);
+            const SiteGeo g = site_geo<kPlanes>(__ldg(perm + r), L, fd, c.axis);
             const uint32_t node = r + 2u;
             if (gl == 0u) {
                 ++sites;
@@ -679,8 +690,8 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
         const uint32_t s = c.sample;
         if (s >= num) break;
         const perc_sample smp = samples[s];
-        const uint32_t L = smp.L, mask = smp.zone_mask;
-        if (L < 1u || L > max_L || mask < 1u || mask > 127u || !smp.perm || !smp.rank) {
+        const uint32_t L = smp.L, mask = smp.zone_mask & kZoneBits, axis = smp.zone_mask >> kAxisShift;
+        if (L < 1u || L > max_L || !valid_zone_word(smp.zone_mask) || !smp.perm || !smp.rank) {
             if (threadIdx.x == 0) {
                 nstar_out[s] = PERC_NEVER;
                 if (passes_out) passes_out[s] = 0;
@@ -699,6 +710,7 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
         if (threadIdx.x == 0) {
             nd_st(P, 0u, 0u);
             nd_st(P, 1u, 1u);
+            c.axis = axis;
         }
         const FastDiv fd = make_fastdiv(L);
         __syncthreads();
@@ -905,8 +917,8 @@ k_nstar_group(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
         if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;  // all have read it
         if (s >= num) break;
         const perc_sample smp = samples[s];
-        const uint32_t L = smp.L, mask = smp.zone_mask;
-        if (L < 1u || L > max_L || mask < 1u || mask > 127u || !smp.perm || !smp.rank) {
+        const uint32_t L = smp.L, mask = smp.zone_mask & kZoneBits, axis = smp.zone_mask >> kAxisShift;
+        if (L < 1u || L > max_L || !valid_zone_word(smp.zone_mask) || !smp.perm || !smp.rank) {
             if (leader && threadIdx.x == 0) {
                 nstar_out[s] = PERC_NEVER;
                 if (passes_out) passes_out[s] = 0;
@@ -922,6 +934,7 @@ k_nstar_group(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
             nd_st(P, 0u, 0u);
             nd_st(P, 1u, 1u);
         }
+        if (threadIdx.x == 0) c.axis = axis;  // every member CTA's own copy
         const FastDiv fd = make_fastdiv(L);
         if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;
         clk.setup += clock64() - t_setup;
@@ -1073,9 +1086,9 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         const uint32_t s = c.sample;
         if (s >= num) break;
         const perc_sample smp = samples[s];
-        const uint32_t L = smp.L, mask = smp.zone_mask;
+        const uint32_t L = smp.L, mask = smp.zone_mask & kZoneBits, axis = smp.zone_mask >> kAxisShift;
         const uint64_t n64 = n_in[s];
-        if (L < 1u || L > max_L || mask < 1u || mask > 127u || !smp.perm || !smp.rank ||
+        if (L < 1u || L > max_L || !valid_zone_word(smp.zone_mask) || !smp.perm || !smp.rank ||
             n64 > num_sites(L)) {
             if (threadIdx.x == 0) {
                 mass_out[s] = -1;
@@ -1096,6 +1109,7 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
             c.logn = 0;
             c.stop = 0;
             c.ecount[0] = 0;
+            c.axis = axis;
         }
         const FastDiv fd = make_fastdiv(L);
         __syncthreads();
@@ -1329,7 +1343,7 @@ __device__ __forceinline__ void window_scan(const Ctl &c, const uint32_t *bm, co
     const uint32_t gshift = lanes_shift(count, R);
     const uint32_t gsize = 1u << gshift, gl = threadIdx.x & (gsize - 1u), t = threadIdx.x >> gshift;
     if (t >= count) return;
-    const SiteGeo g = site_geo<kPlanes>(gshift ? __ldg(perm + b + t) : site, L, fd);
+    const SiteGeo g = site_geo<kPlanes>(gshift ? __ldg(perm + b + t) : site, L, fd, c.axis);
     if (fl && gl == 0u) {
         const uint32_t f = (g.low ? kFlagLo : 0u) | (g.high ? kFlagHi : 0u);
         fl[t] = f;
@@ -1704,9 +1718,9 @@ k_smax(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         const uint32_t s = c.sample;
         if (s >= num) break;
         const perc_sample smp = samples[s];
-        const uint32_t L = smp.L, mask = smp.zone_mask;
+        const uint32_t L = smp.L, mask = smp.zone_mask & kZoneBits, axis = smp.zone_mask >> kAxisShift;
         uint32_t *row = out + size_t(s) * window;
-        if (L < 1u || L > max_L || mask < 1u || mask > 127u || !smp.perm || !smp.rank) {
+        if (L < 1u || L > max_L || !valid_zone_word(smp.zone_mask) || !smp.perm || !smp.rank) {
             for (uint32_t k = threadIdx.x; k < window; k += C) row[k] = kEmptySlot;
             if (threadIdx.x == 0) set_status(&hdr->status, PERC_EDEVICE);
             __syncthreads();
@@ -1733,6 +1747,7 @@ k_smax(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
             c.logn = 0;
             c.stop = 0;
             c.ecount[0] = 0;
+            c.axis = axis;  // S_max does not use borders; kept defined for the shared scan
         }
         __syncthreads();
         if (smem_bm && L == kPlaneL)
@@ -1790,8 +1805,8 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
         const uint32_t s = c.sample;
         if (s >= num) break;
         const perc_sample smp = samples[s];
-        const uint32_t L = smp.L, mask = smp.zone_mask;
-        if (L < 1u || L > max_L || mask < 1u || mask > 127u || !smp.perm || !smp.rank) {
+        const uint32_t L = smp.L, mask = smp.zone_mask & kZoneBits, axis = smp.zone_mask >> kAxisShift;
+        if (L < 1u || L > max_L || !valid_zone_word(smp.zone_mask) || !smp.perm || !smp.rank) {
             if (threadIdx.x == 0) {
                 nstar_out[s] = PERC_NEVER;
                 if (passes_out) passes_out[s] = 0;
@@ -1812,6 +1827,7 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
             nd_st(PA, 1u, 1u);
             nd_st(P, 0u, 0u);  // for the sweep (the same words when node_cap > 1)
             nd_st(P, 1u, 1u);
+            c.axis = axis;
             c.stop = 0;
             c.logn = 0;
             c.ecount[0] = 0;
@@ -2145,6 +2161,31 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
     k_nstar<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap, cfg.edge_scap, bracket,
                                                          nstar, passes, stats, static_cast<char *>(workspace),
                                                          cfg.slot_bytes);
+    return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
+}
+
+// n* under the any-axis spanning rule from the per-axis values: spanning along one axis is
+// monotone in n, so the first n at which some axis spans is the smallest of the per-axis n*
+// (PERC_NEVER, the largest uint32, drops out of the minimum unless every axis is PERC_NEVER).
+namespace perc {
+__global__ void __launch_bounds__(256) k_nstar_min_axes(const uint32_t *__restrict__ nstar, uint32_t num,
+                                                        uint32_t axes, uint32_t *__restrict__ out)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= num) return;
+    const uint32_t *row = nstar + size_t(k) * axes;
+    uint32_t m = PERC_NEVER;
+    for (uint32_t a = 0; a < axes; ++a) m = min(m, __ldg(row + a));
+    out[k] = m;
+}
+}  // namespace perc
+
+extern "C" int perc_nstar_min_axes(const uint32_t *nstar, uint32_t num, uint32_t axes, uint32_t *out,
+                                   void *stream_)
+{
+    if (!nstar || !out || num == 0 || axes == 0 || axes > 5) return PERC_EINVAL;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    k_nstar_min_axes<<<(num + 255u) / 256u, 256, 0, stream>>>(nstar, num, axes, out);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }
 

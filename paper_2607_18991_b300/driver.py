@@ -1,7 +1,8 @@
 """Batched driver over the C ABI: rank the seeds of a workload, build the sample table, and run
 perc_nstar (plain or learned bracket) or perc_mass on it.
 
-A workload is an int64 array [num, 3] of (L, zone mask, seed).  Samples are processed in chunks
+A workload is an int64 array [num, 3] of (L, zone word, seed); the zone word is a zone mask
+1..127, with the spanning axis in bits 8..10 for n* along x2..x5 (``perc.zone_word``).  Samples are processed in chunks
 whose site orders fit a device-memory budget; within a chunk every distinct (L, seed) is ranked
 once and shared by all masks that use it, and all the chunk's samples (mixed L allowed) go to one
 persistent launch, ordered largest lattice first so the long samples start early.
@@ -58,6 +59,13 @@ class Prepared:
             perm_ptr[sel] = perm_t.data_ptr() + row.astype(np.uint64) * np.uint64(N * 4)
             rank_ptr[sel] = rank_t.data_ptr() + row.astype(np.uint64) * np.uint64(N * 4)
         self.samples = perc.make_samples(sub[:, 0], sub[:, 1], perm_ptr, rank_ptr)
+        self._table = (sub[:, 0], sub[:, 1] & 0x7F, perm_ptr, rank_ptr)
+
+    def axis_samples(self, axes: int = perc.NUM_AXES) -> torch.Tensor:
+        """The chunk's samples with `axes` consecutive rows each, spanning axes 0..axes-1 (same
+        order, same neighborhood), for n* along any axis."""
+        Ls, masks, pp, rp = (np.repeat(a, axes) for a in self._table)
+        return perc.make_samples(Ls, perc.zone_word(masks, np.tile(np.arange(axes), len(self.idx))), pp, rp)
 
 
 def prepare(workload, budget: int = DEFAULT_BUDGET, ws: perc.Workspace | None = None, stream=None):
@@ -97,6 +105,37 @@ def nstar(workload, params: torch.Tensor | None = None, margin: float = 0.0, sta
     """Exact n* for every (L, mask, seed) row of `workload`; returns (nstar, passes)."""
     workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
     return run_nstar(iter_prepared(workload, budget), len(workload), params, margin, stats)
+
+
+def run_nstar_any(preps, num: int, params: torch.Tensor | None = None, margin: float = 0.0,
+                  ws: perc.Workspace | None = None, stream=None):
+    """n* for spanning along any axis and the per-axis n* (numpy uint32 [num], [num, 5]) for
+    prepared chunks: perc_nstar over five samples per row (axes x1..x5, each with its own
+    verified bracket), then perc_nstar_min_axes."""
+    ws = ws or perc.default_workspace()
+    A = perc.NUM_AXES
+    out = np.zeros(num, dtype=np.uint32)
+    per_axis = np.zeros((num, A), dtype=np.uint32)
+    for p in preps:
+        smp = p.axis_samples(A)
+        br = perc.bracket(params, smp, margin, stream=stream) if params is not None else None
+        ns, _ = perc.nstar(smp, p.max_L, bracket=br, ws=ws, stream=stream, want_passes=False)
+        anyn = perc.nstar_min_axes(ns, A, stream=stream)
+        out[p.idx] = perc.u32(anyn)
+        per_axis[p.idx] = perc.u32(ns).reshape(-1, A)
+        rc = perc.check(ws, stream)
+        if rc != 0:
+            raise perc.PercError(rc, "perc_nstar device status")
+        del p
+    return out, per_axis
+
+
+def nstar_any(workload, params: torch.Tensor | None = None, margin: float = 0.0,
+              budget: int = DEFAULT_BUDGET):
+    """Exact n* for spanning along any axis for every (L, mask, seed) row of `workload`;
+    returns (nstar_any, nstar per axis [num, 5])."""
+    workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
+    return run_nstar_any(iter_prepared(workload, budget), len(workload), params, margin)
 
 
 def mass(workload, n, budget: int = DEFAULT_BUDGET):
@@ -241,11 +280,15 @@ class NstarStep:
     """Rank the seeds, propose brackets and find n* for all (mask, seed) pairs at one L.
 
     Every device buffer is allocated here, so ``run`` only enqueues library calls on the stream and
-    can be captured in a CUDA graph (``capture``).  Samples are seed-major.
+    can be captured in a CUDA graph (``capture``).  Samples are seed-major.  With ``axes`` > 1 every
+    (mask, seed) pair becomes that many consecutive samples spanning along x1, x2, ... and the n*
+    phase ends with perc_nstar_min_axes: ``nstar_any`` holds n* for spanning along any of them.
     """
 
-    def __init__(self, L: int, masks, seeds, params: torch.Tensor | None = None, margin: float = 0.0):
+    def __init__(self, L: int, masks, seeds, params: torch.Tensor | None = None, margin: float = 0.0,
+                 axes: int = 1):
         self.L = int(L)
+        self.axes = int(axes)
         self.masks = np.asarray(list(masks), dtype=np.int64)
         self.seeds = np.asarray(list(seeds), dtype=np.int64)
         self.params = params
@@ -257,12 +300,17 @@ class NstarStep:
         self.seeds_dev = torch.as_tensor(self.seeds, device="cuda")
         self.perm = torch.empty((S, N), dtype=torch.int32, device="cuda")
         self.rank = torch.empty((S, N), dtype=torch.int32, device="cuda")
-        rows = np.repeat(np.arange(S), len(self.masks))
-        self.samples = perc.samples_for(self.L, np.tile(self.masks, S), rows, self.perm, self.rank)
-        self.bracket = torch.empty((self.num, 2), dtype=torch.int32, device="cuda")
-        self.nstar = torch.empty(self.num, dtype=torch.int32, device="cuda")
-        self.passes = torch.empty(self.num, dtype=torch.int32, device="cuda")
-        nb = max(perc.workspace_bytes(perc.OP_RANK, self.L, S), perc.workspace_bytes(perc.OP_NSTAR, self.L, self.num))
+        A = self.axes
+        self.launch_num = self.num * A  # samples of the perc_nstar launch
+        rows = np.repeat(np.arange(S), len(self.masks) * A)
+        words = perc.zone_word(np.repeat(np.tile(self.masks, S), A), np.tile(np.arange(A), self.num))
+        self.samples = perc.samples_for(self.L, words, rows, self.perm, self.rank)
+        self.bracket = torch.empty((self.launch_num, 2), dtype=torch.int32, device="cuda")
+        self.nstar = torch.empty(self.launch_num, dtype=torch.int32, device="cuda")
+        self.passes = torch.empty(self.launch_num, dtype=torch.int32, device="cuda")
+        self.nstar_any = torch.empty(self.num, dtype=torch.int32, device="cuda") if A > 1 else None
+        nb = max(perc.workspace_bytes(perc.OP_RANK, self.L, S),
+                 perc.workspace_bytes(perc.OP_NSTAR, self.L, self.launch_num))
         self.ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
         self.lib = perc.lib()
 
@@ -272,14 +320,18 @@ class NstarStep:
                                     self.rank.data_ptr(), self.ws.data_ptr(), self.ws.numel(), sp), "perc_rank")
 
     def run_bracket(self, stream=None):
-        perc._ok(self.lib.perc_bracket(self.params.data_ptr(), self.samples.data_ptr(), self.num, self.margin,
-                                       self.bracket.data_ptr(), perc._stream(stream)), "perc_bracket")
+        perc._ok(self.lib.perc_bracket(self.params.data_ptr(), self.samples.data_ptr(), self.launch_num,
+                                       self.margin, self.bracket.data_ptr(), perc._stream(stream)), "perc_bracket")
 
     def run_nstar(self, learned: bool, stats: torch.Tensor | None = None, stream=None):
         br = self.bracket.data_ptr() if learned else None
-        perc._ok(self.lib.perc_nstar(self.samples.data_ptr(), self.num, self.L, br, self.nstar.data_ptr(),
+        perc._ok(self.lib.perc_nstar(self.samples.data_ptr(), self.launch_num, self.L, br, self.nstar.data_ptr(),
                                      self.passes.data_ptr(), perc._ptr(stats), self.ws.data_ptr(), self.ws.numel(),
                                      perc._stream(stream)), "perc_nstar")
+        if self.axes > 1:
+            perc._ok(self.lib.perc_nstar_min_axes(self.nstar.data_ptr(), self.num, self.axes,
+                                                  self.nstar_any.data_ptr(), perc._stream(stream)),
+                     "perc_nstar_min_axes")
 
     def run(self, learned: bool = True, stats: torch.Tensor | None = None, stream=None):
         self.run_rank(stream)
@@ -301,6 +353,8 @@ class NstarStep:
         rc = self.lib.perc_check(self.ws.data_ptr(), perc._stream())
         if rc != 0:
             raise perc.PercError(rc, "perc_nstar device status")
+        if self.axes > 1:  # n* along any axis; passes summed over the axes of each pair
+            return perc.u32(self.nstar_any), perc.u32(self.passes).reshape(-1, self.axes).sum(axis=1)
         return perc.u32(self.nstar), perc.u32(self.passes)
 
 

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libperc.so")
 NEVER = 0xFFFFFFFF
 MAX_L = 73
 OP_RANK, OP_NSTAR, OP_MASS, OP_SMAX = 1, 2, 3, 4
+AXIS_SHIFT, NUM_AXES = 8, 5  # zone word: spanning axis in bits 8..10; axes x1..x5
 OPT_THREADS, OPT_SMEM_NODES, OPT_MAX_CTAS, OPT_GROUP, OPT_METHOD = 1, 2, 3, 4, 5
 METHOD_AUTO, METHOD_BISECTION, METHOD_SWEEP = 0, 1, 2
 MLP_NPARAM = 4931
@@ -49,6 +50,7 @@ def lib() -> ctypes.CDLL:
         "perc_rank": (i32, [u32, vp, u32, vp, vp, vp, sz, vp]),
         "perc_nstar": (i32, [vp, u32, u32, vp, vp, vp, vp, vp, sz, vp]),
         "perc_nstar_noalloc": (i32, [vp, u32, u32, vp, vp, vp, vp, vp]),
+        "perc_nstar_min_axes": (i32, [vp, u32, u32, vp, vp]),
         "perc_mass": (i32, [vp, u32, u32, vp, vp, vp, sz, vp]),
         "perc_smax_window": (i32, [vp, u32, u32, vp, vp, u32, vp, vp, sz, vp]),
         "perc_binomial_weights": (i32, [vp, vp, vp, u32, u32, vp, u32, vp, vp]),
@@ -71,7 +73,7 @@ def lib() -> ctypes.CDLL:
 
 
 def exported_symbols() -> list[str]:
-    return ["perc_workspace_bytes", "perc_rank", "perc_nstar", "perc_nstar_noalloc", "perc_mass",
+    return ["perc_workspace_bytes", "perc_rank", "perc_nstar", "perc_nstar_noalloc", "perc_nstar_min_axes", "perc_mass",
             "perc_smax_window", "perc_binomial_weights", "perc_pmax", "perc_check",
             "perc_mlp_forward", "perc_mlp_grad", "perc_adam", "perc_mlp_train", "perc_bracket",
             "perc_status_string", "perc_set_launch_option"]
@@ -151,8 +153,14 @@ def rank(L: int, seeds, ws: Workspace | None = None, stream=None, out=None):
     return perm, rk
 
 
+def zone_word(masks, axes=0):
+    """perc_sample.zone_mask: zone bits 0..6 and the spanning axis (0..4) in bits 8..10."""
+    return np.asarray(masks, dtype=np.int64) | (np.asarray(axes, dtype=np.int64) << AXIS_SHIFT)
+
+
 def make_samples(Ls, masks, perm_ptrs, rank_ptrs) -> torch.Tensor:
-    """Device array of perc_sample {uint32 L, uint32 mask, perm*, rank*} as int64 [num, 3]."""
+    """Device array of perc_sample {uint32 L, uint32 zone word, perm*, rank*} as int64 [num, 3];
+    `masks` are zone words (a plain zone mask 1..127 spans along x1)."""
     Ls = np.asarray(Ls, dtype=np.int64)
     masks = np.asarray(masks, dtype=np.int64)
     arr = np.zeros((len(Ls), 3), dtype=np.int64)
@@ -194,6 +202,16 @@ def nstar(samples: torch.Tensor, max_L: int, bracket: torch.Tensor | None = None
     _ok(lib().perc_nstar(samples.data_ptr(), num, max_L, _ptr(bracket), ns.data_ptr(), _ptr(ps),
                          _ptr(stats), buf.data_ptr(), buf.numel(), _stream(stream)), "perc_nstar")
     return ns, ps
+
+
+def nstar_min_axes(nstar_axes: torch.Tensor, axes: int = NUM_AXES, out=None, stream=None) -> torch.Tensor:
+    """perc_nstar_min_axes: n* for spanning along any axis from per-axis n* stored [num][axes]
+    (int32 tensors holding uint32; PERC_NEVER = -1)."""
+    num = nstar_axes.numel() // axes
+    o = out if out is not None else torch.empty(num, dtype=torch.int32, device="cuda")
+    _ok(lib().perc_nstar_min_axes(nstar_axes.data_ptr(), num, axes, o.data_ptr(), _stream(stream)),
+        "perc_nstar_min_axes")
+    return o
 
 
 def nstar_noalloc(samples: torch.Tensor, max_L: int, bracket: torch.Tensor | None = None,

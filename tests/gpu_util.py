@@ -25,3 +25,14 @@ def orc_mass(workload, n) -> np.ndarray:
         perm, rk = orc_order(int(L), int(s))
         out[k] = oracle.nz(int(L), int(m), perm, rk, [int(n[k])])[1][0]
     return out
+
+
+def orc_nstar_rule(workload, span=None) -> np.ndarray:
+    """Oracle n* for rows (L, zone word, seed) under the word's own spanning axis (bits 8..10), or
+    under rule `span` (0..4 an axis, oracle.SPAN_ANY any axis) when given."""
+    out = np.zeros(len(workload), dtype=np.uint32)
+    for k, (L, w, s) in enumerate(np.asarray(workload, dtype=np.int64)):
+        perm, rk = orc_order(int(L), int(s))
+        rule = int(w) >> 8 if span is None else span
+        out[k] = oracle.nstar_span(int(L), int(w) & 0x7F, rule, perm, rk)
+    return out
