@@ -62,6 +62,8 @@ struct Ctl {
     uint32_t z;       // offsets of the sample's neighborhood
     uint32_t R;       // row entries of the sample's neighborhood
     uint32_t NP;      // plane entries (L = 16 path)
+    uint32_t Rhalf;   // row entries up to the centre row (d1..d4 = 0), which come first
+    uint32_t NPhalf;  // plane entries up to the centre plane (d1..d3 = 0)
     uint32_t axis;    // spanning axis of the sample: its borders are x_{axis+1} = 0 and = L-1
     uint32_t ecount[2];  // edge-list fill of the current and the next chunk
     unsigned long long hooks, new_sites, sites, unions, cyc_scan, cyc_link;
@@ -169,6 +171,12 @@ struct __align__(16) RowEntry {
     uint32_t pad;
 };
 constexpr int kRowCand = 625;  // (d1..d4) in {-2..2}^4
+// Rows are stored in ascending base-5 code of (d1+2, .., d4+2), i.e. in lexicographic order of
+// (d1..d4).  The site index orders coordinates with x1 most significant, so an in-lattice neighbor
+// has a smaller index than the site exactly when its offset's first non-zero component is
+// negative: the rows before the centre row (code 312) hold only such neighbors, the centre row
+// those with d5 < 0, and the rows after it none.
+constexpr uint32_t kRowCentre = 312;
 
 // Builds the row table of `mask` for side L (all threads; ends with a barrier); returns the count
 // of rows and writes the number of offsets to *z.
@@ -197,11 +205,12 @@ __device__ uint32_t build_rows(uint32_t mask, uint32_t L, RowEntry *rows, uint32
     __syncthreads();
     if (threadIdx.x < 32) {
         const uint32_t lane = threadIdx.x;
-        uint32_t count = 0;
+        uint32_t count = 0, half = 0;
         for (uint32_t base = 0; base < static_cast<uint32_t>(kRowCand); base += 32) {
             const uint32_t key = base + lane;
             const uint32_t m = key < static_cast<uint32_t>(kRowCand) ? scratch[key] : 0u;
             const uint32_t bal = __ballot_sync(0xffffffffu, m != 0u);
+            half += __popc(__ballot_sync(0xffffffffu, m != 0u && key <= kRowCentre));
             if (m) {
                 RowEntry e;
                 uint32_t kk = key, onehot = 0;
@@ -225,6 +234,7 @@ __device__ uint32_t build_rows(uint32_t mask, uint32_t L, RowEntry *rows, uint32
         }
         if (lane == 0) {
             c.R = count;
+            c.Rhalf = half;
             c.z = z;
         }
     }
@@ -315,7 +325,8 @@ __device__ __forceinline__ uint32_t lanes_shift(uint32_t count, uint32_t R)
 // i + delta - 34 + 32F + t.
 // ------------------------------------------------------------------------------------------------
 constexpr uint32_t kPlaneL = 16;
-constexpr int kPlaneCand = 125;  // (d1, d2, d3) in {-2..2}^3
+constexpr int kPlaneCand = 125;  // (d1, d2, d3) in {-2..2}^3, stored in ascending base-5 code
+constexpr uint32_t kPlaneCentre = 62;  // code of (0, 0, 0)
 
 struct __align__(16) PlaneEntry {
     int32_t dword;   // plane offset / 32 (= ((d1*16 + d2)*16 + d3) * 8)
@@ -343,7 +354,7 @@ __device__ uint32_t build_planes16(const RowEntry *rows, uint32_t R, PlaneEntry 
     __syncthreads();
     if (threadIdx.x < 32) {
         const uint32_t lane = threadIdx.x;
-        uint32_t count = 0;
+        uint32_t count = 0, half = 0;
         for (uint32_t base = 0; base < static_cast<uint32_t>(kPlaneCand); base += 32) {
             const uint32_t key = base + lane;
             uint32_t f[5] = {0u, 0u, 0u, 0u, 0u};
@@ -351,6 +362,7 @@ __device__ uint32_t build_planes16(const RowEntry *rows, uint32_t R, PlaneEntry 
                 for (int q = 0; q < 5; ++q) f[q] = scratch[key * 5 + q];
             const bool any = (f[0] | f[1] | f[2] | f[3] | f[4]) != 0u;
             const uint32_t bal = __ballot_sync(0xffffffffu, any);
+            half += __popc(__ballot_sync(0xffffffffu, any && key <= kPlaneCentre));
             if (any) {
                 const int d1 = static_cast<int>(key / 25u) - 2, d2 = static_cast<int>((key / 5u) % 5u) - 2,
                           d3 = static_cast<int>(key % 5u) - 2;
@@ -363,7 +375,10 @@ __device__ uint32_t build_planes16(const RowEntry *rows, uint32_t R, PlaneEntry 
             }
             count += __popc(bal);
         }
-        if (lane == 0) c.NP = count;
+        if (lane == 0) {
+            c.NP = count;
+            c.NPhalf = half;
+        }
     }
     __syncthreads();
     return c.NP;
@@ -453,7 +468,17 @@ __device__ __forceinline__ uint32_t read_flag(const uint32_t *f)
     return kGroup ? __ldcg(f) : *reinterpret_cast<const volatile uint32_t *>(f);
 }
 
-template <bool kSmemBm, bool kFaces, bool kPlanes, bool kGroup = false>
+// Bits t of a 32-bit hit mask whose neighbor index base + t lies below the site: t < lim.
+__device__ __forceinline__ uint32_t below_mask(int32_t lim)
+{
+    return lim <= 0 ? 0u : lim >= 32 ? 0xFFFFFFFFu : (1u << lim) - 1u;
+}
+
+// kHalf: the pass covers every occupied site (r0 = 0 and the bitmap holds exactly the sites of rank
+// below r1), so each edge is taken once, from its end with the larger site index: only the table
+// entries up to the centre entry are scanned, their hits are cut to neighbors below the site, and
+// every edge is merged (no rank-order rule).
+template <bool kSmemBm, bool kFaces, bool kPlanes, bool kGroup = false, bool kHalf = false>
 __device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *logb, const uint32_t *bm,
                                            const RowEntry *rows, const PlaneEntry *planes, const EdgeList &E,
                                            const uint32_t *perm, const uint32_t *rank, uint32_t L,
@@ -461,7 +486,7 @@ __device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *log
                                            uint32_t *stop_flag = nullptr, uint32_t *logn = nullptr,
                                            uint32_t member = 0, uint32_t members = 1)
 {
-    const uint32_t R = kPlanes ? c.NP : c.R;
+    const uint32_t R = kHalf ? (kPlanes ? c.NPhalf : c.Rhalf) : (kPlanes ? c.NP : c.R);
     const uint32_t gshift = lanes_shift(r1 - r0, R);
     const uint32_t gsize = 1u << gshift, gl = threadIdx.x & (gsize - 1u), grp = threadIdx.x >> gshift;
     const uint32_t chunk = blockDim.x >> gshift;
@@ -490,6 +515,12 @@ __device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *log
             for (uint32_t k = gl; k < R; k += gsize) {
                 uint32_t h[3];
                 const uint32_t jb = entry_hits<kSmemBm, kPlanes>(g, bm, rows, planes, k, h);
+                if (kHalf) {  // a no-op except on the centre entry
+                    const int32_t lim = static_cast<int32_t>(g.i - jb);
+                    h[0] &= below_mask(lim);
+                    h[1] &= below_mask(lim - 32);
+                    h[2] &= below_mask(lim - 64);
+                }
                 const uint32_t nh = __popc(h[0]) + __popc(h[1]) + __popc(h[2]);
                 if (nh == 0u) continue;
                 uint32_t slot = atomicAdd(ecount, nh);
@@ -524,7 +555,7 @@ __device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *log
             for (int q = 0; q < 4; ++q) {
                 const uint32_t e = e0 + q * blockDim.x;
                 if (e >= ne) continue;
-                if (!(ed[q].y & kNodeFlag) && other[q] >= ed[q].x) continue;  // the later site merges it
+                if (!kHalf && !(ed[q].y & kNodeFlag) && other[q] >= ed[q].x) continue;  // the later site merges it
                 ++unions;
                 hooks += uf_unite(P, ed[q].x, other[q], nold, logb, logn, stopp) ? 1u : 0u;
             }
@@ -1120,11 +1151,11 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         }
         __syncthreads();
         if (smem_bm && L == kPlaneL)
-            union_pass<true, false, true>(c, P, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+            union_pass<true, false, true, false, true>(c, P, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         else if (smem_bm)
-            union_pass<true, false, false>(c, P, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+            union_pass<true, false, false, false, true>(c, P, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         else
-            union_pass<false, false, false>(c, P, nullptr, bm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+            union_pass<false, false, false, false, true>(c, P, nullptr, bm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         __syncthreads();
         for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) atomicAdd(cnt + uf_find(P, r + 2u, 0u), 1u);
         __syncthreads();
@@ -1580,8 +1611,8 @@ __device__ void smax_sample(Ctl &c, SmaxShared &x, const Nodes &P, const Nodes &
     }
     __syncthreads();
     if (n0 > 0u)
-        union_pass<kSmemBm, false, kPlanes>(c, PA, nullptr, bm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u,
-                                            n0, 0u);
+        union_pass<kSmemBm, false, kPlanes, false, true>(c, PA, nullptr, bm, sm.rows, sm.planes, E, smp.perm, smp.rank,
+                                                         L, fd, 0u, n0, 0u);
     __syncthreads();
     for (uint32_t r = threadIdx.x; r < n0; r += C) atomicAdd(cnt + uf_find(PA, r + 2u, 0u), 1u);
     __syncthreads();
@@ -1855,14 +1886,14 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
             for (uint32_t r = threadIdx.x; r < n_s; r += C) nd_st(PA, r + 2u, r + 2u);
             __syncthreads();
             if (smem_bm && L == kPlaneL)
-                union_pass<true, true, true>(c, PA, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd,
-                                             0u, n_s, 0u);
+                union_pass<true, true, true, false, true>(c, PA, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm,
+                                                          smp.rank, L, fd, 0u, n_s, 0u);
             else if (smem_bm)
-                union_pass<true, true, false>(c, PA, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm, smp.rank, L,
-                                              fd, 0u, n_s, 0u);
+                union_pass<true, true, false, false, true>(c, PA, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm,
+                                                           smp.rank, L, fd, 0u, n_s, 0u);
             else
-                union_pass<false, true, false>(c, PA, nullptr, bm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd,
-                                               0u, n_s, 0u);
+                union_pass<false, true, false, false, true>(c, PA, nullptr, bm, sm.rows, sm.planes, E, smp.perm,
+                                                            smp.rank, L, fd, 0u, n_s, 0u);
             __syncthreads();
             ++npass;
             tot_probe += n_s;
