@@ -57,3 +57,20 @@ def test_host_side_argument_checks_without_gpu():
     assert lib.perc_workspace_bytes(7, 8, 1) == 0
     assert lib.perc_workspace_bytes(1, 0, 1) == 0
     assert lib.perc_workspace_bytes(1, 8, 1) > 8 * 8 ** 5
+    # perc_nstar_min_axes: null pointers, no rows, axes outside 1..5
+    assert lib.perc_nstar_min_axes(None, 4, 5, 1, None) == -1
+    assert lib.perc_nstar_min_axes(1, 4, 5, None, None) == -1
+    assert lib.perc_nstar_min_axes(1, 0, 5, 1, None) == -1
+    assert lib.perc_nstar_min_axes(1, 4, 0, 1, None) == -1
+    assert lib.perc_nstar_min_axes(1, 4, 6, 1, None) == -1
+
+
+def test_zone_word_layout():
+    # the zone word packs the zones in bits 0..6 and the spanning axis in bits 8..10, as the header
+    # defines it (PERC_ZONE_WORD)
+    from paper_2607_18991_b300 import perc
+    hdr = open(os.path.join(ROOT, "include", "perc.h")).read()
+    assert re.search(r"#define PERC_AXIS_SHIFT 8u", hdr) and re.search(r"#define PERC_ZONE_BITS 0x7Fu", hdr)
+    assert perc.AXIS_SHIFT == 8 and perc.NUM_AXES == 5
+    assert int(perc.zone_word(127, 4)) == 127 | (4 << 8)
+    assert list(perc.zone_word([1, 2], [0, 3])) == [1, 2 | (3 << 8)]
