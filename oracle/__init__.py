@@ -17,6 +17,9 @@ Contents and the passages they follow:
   (x_{a+1} = 0 and x_{a+1} = L-1, a = 0..4) or of any axis (``SPAN_ANY``), with ten border flags.
 * ``bfs`` and ``minimax_nstar`` -- independent brute-force cross-checks (flood fill at fixed n;
   bottleneck-path identity) used only to pin ``nz`` and ``nstar_span``.
+* ``nz_periodic`` / ``bfs_periodic`` -- the periodic-boundary variant (offsets wrap modulo L): the
+  first n at which a cluster wraps around the torus along one axis, and S_max(n); the sweep keeps
+  an unwrapped coordinate per cluster, the flood fill checks it without union-find.
 * ``smax_prefix`` -- the same sweep stopped after n_stop sites: S_max(n) for n = 0..n_stop.
 * ``binomial_weights`` / ``binomial_convolve`` / ``pmax`` -- S_max(n) -> S_max(p) (Methods,
   "Computational methods") and P_max(p) = S_max(p) / L^5 (eq. Pmax).
@@ -78,6 +81,10 @@ def lib():
         L.orc_minimax_nstar_axis.restype = u32
         L.orc_nstar_span.argtypes = [u32, u32, u32, P(u32), P(u32), P(u32)]
         L.orc_nstar_span.restype = i32
+        L.orc_nz_periodic.argtypes = [u32, u32, u32, P(u32), P(u32), P(u64), u32, P(i64), P(u32)]
+        L.orc_nz_periodic.restype = i32
+        L.orc_bfs_periodic.argtypes = [u32, u32, u32, P(u32), u64, P(i32), P(i64)]
+        L.orc_bfs_periodic.restype = i32
         L.orc_smax_prefix.argtypes = [u32, u32, P(u32), P(u32), u64, P(i64)]
         L.orc_smax_prefix.restype = i32
         L.orc_binomial_weights.argtypes = [u64, ctypes.c_double, P(ctypes.c_double)]
@@ -180,6 +187,32 @@ def nstar_span(L: int, mask: int, span: int, perm: np.ndarray, rk: np.ndarray) -
                             ctypes.byref(out)) != 0:
         raise ValueError(f"orc_nstar_span failed for L={L} mask={mask} span={span}")
     return out.value
+
+
+def nz_periodic(L: int, mask: int, perm: np.ndarray, rk: np.ndarray, nq=(), axis: int = 0):
+    """Sweep with periodic boundaries: (first n at which a cluster wraps along axis ``axis``,
+    S_max after nq[q] sites as int64[len(nq)])."""
+    nq = np.ascontiguousarray(np.asarray(nq, dtype=np.uint64).reshape(-1))
+    smax_at = np.zeros(len(nq), dtype=np.int64)
+    out = ctypes.c_uint32()
+    perm = np.ascontiguousarray(perm, dtype=np.uint32)
+    rk = np.ascontiguousarray(rk, dtype=np.uint32)
+    if lib().orc_nz_periodic(L, mask, axis, _ptr(perm, ctypes.c_uint32), _ptr(rk, ctypes.c_uint32),
+                             _ptr(nq, ctypes.c_uint64), len(nq), _ptr(smax_at, ctypes.c_int64),
+                             ctypes.byref(out)) != 0:
+        raise ValueError(f"orc_nz_periodic failed for L={L} mask={mask} axis={axis}")
+    return out.value, smax_at
+
+
+def bfs_periodic(L: int, mask: int, rk: np.ndarray, n: int, axis: int = 0) -> tuple[bool, int]:
+    """Flood fill of the sites with rank < n on the torus: (some cluster wraps along ``axis``, S_max)."""
+    w = ctypes.c_int()
+    sm = ctypes.c_int64()
+    rk = np.ascontiguousarray(rk, dtype=np.uint32)
+    if lib().orc_bfs_periodic(L, mask, axis, _ptr(rk, ctypes.c_uint32), n, ctypes.byref(w),
+                              ctypes.byref(sm)) != 0:
+        raise ValueError("orc_bfs_periodic failed")
+    return bool(w.value), sm.value
 
 
 def bfs(L: int, mask: int, rk: np.ndarray, n: int, span: int = 0) -> tuple[bool, int]:

@@ -17,6 +17,8 @@
  *     of any axis;
  *   - independent cross-checks used only to pin the sweep: a breadth-first flood fill at a fixed
  *     n, and the bottleneck (minimax) path identity for the first spanning n;
+ *   - the periodic-boundary variant: S_max(n) on the 5-torus and the first n at which a cluster
+ *     wraps around it along one axis, with its own flood-fill cross-check;
  *   - the binomial convolution that turns S_max(n) into S_max(p).
  *
  * Readings of what the paper leaves open (all are stated here so a reader can check them):
@@ -466,6 +468,170 @@ uint32_t orc_minimax_nstar_axis(uint32_t L, uint32_t mask, uint32_t axis, const 
 uint32_t orc_minimax_nstar(uint32_t L, uint32_t mask, const uint32_t *rank)
 {
     return orc_minimax_nstar_axis(L, mask, 0, rank);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Periodic boundaries (a variant; the paper does not state its boundary conditions): offsets    */
+/* wrap modulo L in every coordinate, so the lattice is a 5-torus and every site has all z       */
+/* neighbors (at small L several offsets may reach the same site, or the site itself).  No       */
+/* border exists; the spanning cluster becomes a wrapping one: a cluster wraps along axis a when */
+/* it holds a closed path whose steps' x_{a+1} components do not sum to zero.  The sweep keeps,  */
+/* beside each union-find parent, the displacement along axis a to it, so every cluster carries  */
+/* an unwrapped coordinate; an edge inside one cluster whose two ends disagree with the step     */
+/* closes such a path.                                                                           */
+/* ------------------------------------------------------------------------------------------ */
+static int64_t orc_neighbor_periodic(uint32_t L, const int x[5], const int8_t *v)
+{
+    int64_t j = 0;
+    for (int k = 0; k < 5; ++k) {
+        int y = ((x[k] + v[k]) % (int)L + (int)L) % (int)L;
+        j = j * L + y;
+    }
+    return j;
+}
+
+/* Root of a and the displacement pos(a) - pos(root) along the axis; compresses the path. */
+static uint32_t orc_find_disp(uint32_t *parent, int64_t *dpar, uint32_t a, int64_t *disp)
+{
+    uint32_t root = a;
+    int64_t d = 0;
+    while (parent[root] != root) {
+        d += dpar[root];
+        root = parent[root];
+    }
+    int64_t rem = d; /* displacement of x to the root */
+    uint32_t x = a;
+    while (x != root && parent[x] != root) {
+        uint32_t next = parent[x];
+        int64_t dx = dpar[x];
+        parent[x] = root;
+        dpar[x] = rem;
+        rem -= dx;
+        x = next;
+    }
+    *disp = d;
+    return root;
+}
+
+/*
+ * The sweep with periodic boundaries for one (L, mask) on a given order.  Outputs the first n at
+ * which a cluster wraps along axis `axis` (0..4; ORC_NEVER if none up to N) and S_max after nq[q]
+ * sites.  Returns 0, or -1 on bad input / no memory.
+ */
+int orc_nz_periodic(uint32_t L, uint32_t mask, uint32_t axis, const uint32_t *perm, const uint32_t *rank,
+                    const uint64_t *nq, uint32_t nnq, int64_t *smax_at, uint32_t *nwrap_out)
+{
+    uint64_t N = orc_num_sites(L);
+    if (L == 0 || N >= 0xFFFFFFFFull || mask < 1 || mask > 127 || axis > 4) return -1;
+    uint64_t last_query = 0;
+    for (uint32_t q = 0; q < nnq; ++q) {
+        if (nq[q] > N) return -1;
+        if (nq[q] == 0) smax_at[q] = 0;
+        if (nq[q] > last_query) last_query = nq[q];
+    }
+    int8_t offs[892 * 5];
+    int z = orc_mask_offsets((int)mask, offs);
+    uint32_t *parent = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+    uint32_t *size = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+    int64_t *dpar = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    if (!parent || !size || !dpar) {
+        free(parent); free(size); free(dpar);
+        return -1;
+    }
+    uint32_t nwrap = ORC_NEVER, smax = 0;
+    int wrapped = 0;
+    for (uint64_t r = 0; r < N; ++r) {
+        uint32_t i = perm[r];
+        int x[5];
+        orc_coords(L, i, x);
+        parent[i] = i;
+        size[i] = 1;
+        dpar[i] = 0;
+        for (int v = 0; v < z; ++v) {
+            const int8_t *off = offs + 5 * v;
+            uint32_t j = (uint32_t)orc_neighbor_periodic(L, x, off);
+            if (j != i && rank[j] >= r) continue; /* empty neighbor (j == i: a loop through i) */
+            int64_t da, db;
+            uint32_t ra = orc_find_disp(parent, dpar, i, &da), rb = orc_find_disp(parent, dpar, j, &db);
+            int64_t step = off[axis]; /* pos(j) = pos(i) + step */
+            if (ra == rb) {
+                if (da + step != db) wrapped = 1;
+                continue;
+            }
+            if (size[ra] >= size[rb]) {
+                parent[rb] = ra;
+                dpar[rb] = step + da - db; /* pos(rb) - pos(ra) */
+                size[ra] += size[rb];
+            } else {
+                parent[ra] = rb;
+                dpar[ra] = db - da - step; /* pos(ra) - pos(rb) */
+                size[rb] += size[ra];
+            }
+        }
+        int64_t d;
+        uint32_t root = orc_find_disp(parent, dpar, i, &d);
+        if (size[root] > smax) smax = size[root];
+        uint64_t n = r + 1;
+        if (wrapped && nwrap == ORC_NEVER) nwrap = (uint32_t)n;
+        for (uint32_t q = 0; q < nnq; ++q)
+            if (nq[q] == n) smax_at[q] = smax;
+        if (nwrap != ORC_NEVER && n >= last_query) break;
+    }
+    *nwrap_out = nwrap;
+    free(parent); free(size); free(dpar);
+    return 0;
+}
+
+/* Brute force at a fixed n with periodic boundaries: flood fill that gives every site of a      */
+/* cluster an unwrapped coordinate along the axis when first reached; a step to a reached site   */
+/* that disagrees with its coordinate closes a winding path.  No union-find; pins the sweep.    */
+int orc_bfs_periodic(uint32_t L, uint32_t mask, uint32_t axis, const uint32_t *rank, uint64_t n,
+                     int *wraps, int64_t *smax)
+{
+    uint64_t N = orc_num_sites(L);
+    if (L == 0 || N >= 0xFFFFFFFFull || mask < 1 || mask > 127 || axis > 4 || n > N) return -1;
+    int8_t offs[892 * 5];
+    int z = orc_mask_offsets((int)mask, offs);
+    uint8_t *seen = (uint8_t *)calloc((size_t)N, 1);
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    uint32_t *stack = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+    if (!seen || !pos || !stack) {
+        free(seen); free(pos); free(stack);
+        return -1;
+    }
+    int any = 0;
+    int64_t best = 0;
+    for (uint64_t s = 0; s < N; ++s) {
+        if (rank[s] >= n || seen[s]) continue;
+        int64_t count = 0;
+        uint64_t top = 0;
+        stack[top++] = (uint32_t)s;
+        seen[s] = 1;
+        pos[s] = 0;
+        while (top) {
+            uint32_t u = stack[--top];
+            int x[5];
+            orc_coords(L, u, x);
+            ++count;
+            for (int v = 0; v < z; ++v) {
+                const int8_t *off = offs + 5 * v;
+                uint32_t w = (uint32_t)orc_neighbor_periodic(L, x, off);
+                if (rank[w] >= n) continue;
+                if (!seen[w]) {
+                    seen[w] = 1;
+                    pos[w] = pos[u] + off[axis];
+                    stack[top++] = w;
+                } else if (pos[w] != pos[u] + off[axis]) {
+                    any = 1;
+                }
+            }
+        }
+        if (count > best) best = count;
+    }
+    *wraps = any;
+    *smax = best;
+    free(seen); free(pos); free(stack);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------------------------ */
