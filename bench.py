@@ -20,6 +20,10 @@ P_max(p) (eq. Pmax).
 `--workload any` measures n* for spanning along any of the five axes: the same step with five
 samples per (mask, seed) (spanning axis x1..x5, each with its own verified bracket) in the n*
 launch, then perc_nstar_min_axes; a sample of the metric is one (mask, seed) pair.
+
+`--workload wrap` measures the periodic-boundary variant: one step = perc_rank of the seeds and
+perc_nstar_wrap (the first n at which a cluster wraps around the torus along x1, by bisection) over
+all 127 neighborhoods; 32 seeds per rank unless --num-seeds says otherwise.
 """
 from __future__ import annotations
 
@@ -44,6 +48,9 @@ MASKS = list(range(1, 128))
 METRIC = "samples/sec (exact n*) at L=16 over 127 neighborhoods, learned vs plain bracket"
 ANY_METRIC = ("samples/sec (exact n* for spanning along any of the 5 axes) at L=16 over 127 neighborhoods, "
               "learned vs plain bracket")
+WRAP_METRIC = ("samples/sec (exact first wrapping n along x1, periodic boundaries) at L=16 over 127 "
+               "neighborhoods")
+WRAP_SEEDS = 32
 PMAX_METRIC = ("samples/sec of P_max(p) curves (exact S_max(n) over the windows of n holding all but 1e-16 of "
                "each binomial, convolution at 16 p per neighborhood) at L=16 over 127 neighborhoods")
 
@@ -77,6 +84,14 @@ def _oracle_any_seed(seed: int) -> int:
     perm, rk = oracle.rank(L, seed)
     for m in MASKS:
         oracle.nstar_span(L, m, oracle.SPAN_ANY, perm, rk)
+    return len(MASKS)
+
+
+def _oracle_wrap_seed(seed: int) -> int:
+    import oracle
+    perm, rk = oracle.rank(L, seed)
+    for m in MASKS:
+        oracle.nz_periodic(L, m, perm, rk, (), 0)
     return len(MASKS)
 
 
@@ -700,6 +715,137 @@ def run_pmax_ours(args):
 
 
 # ------------------------------------------------------------------------------------------------
+# our arm, periodic boundaries: first wrapping n
+# ------------------------------------------------------------------------------------------------
+def run_wrap_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    cpu_workers = max(1, min(host_cores(), 32))
+
+    from paper_2607_18991_b300 import build as pbuild
+    from paper_2607_18991_b300 import driver, perc
+
+    pbuild.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    lib = perc.lib()
+    num_seeds = WRAP_SEEDS if args.num_seeds == NUM_SEEDS else args.num_seeds
+    seeds, _ = workload_for(rank, num_seeds)
+    st = driver.NstarStep(L, MASKS, seeds)  # site orders and the sample table (axis x1)
+    num = st.num
+    out = torch.empty(num, dtype=torch.int32, device=dev)
+    wsp = torch.empty(perc.workspace_bytes(perc.OP_PERIODIC, L, num), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def run_wrap(samples_ptr):
+        perc._ok(lib.perc_nstar_wrap(samples_ptr, num, L, out.data_ptr(), wsp.data_ptr(), wsp.numel(), sp),
+                 "perc_nstar_wrap")
+
+    def step(ev=None):
+        st.run_rank()
+        if ev is not None:
+            ev.record(stream)
+        run_wrap(st.samples.data_ptr())
+
+    def timed(fn, K: int, W: int):
+        for _ in range(W):
+            fn()
+        torch.cuda.synchronize()
+        tot, t_rank = 0.0, 0.0
+        for _ in range(K):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            e[0].record(stream)
+            fn(e[1])
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            tot += e[0].elapsed_time(e[2])
+            t_rank += e[0].elapsed_time(e[1])
+        return tot / K, t_rank / K
+
+    gpu_index = torch.cuda.current_device()
+    phys = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    smi_index = int(phys[gpu_index]) if phys and phys[0].strip().isdigit() else gpu_index
+    with ClockSampler(smi_index) as clk:
+        ms_step, ms_rank = timed(step, args.steps, args.warmup)
+    clocks = clk.summary()
+    rc = lib.perc_check(wsp.data_ptr(), sp)
+    if rc != 0:
+        raise perc.PercError(rc, "perc_nstar_wrap device status")
+    ns = perc.u32(out)
+
+    # ---- e2e through the C ABI from pinned host buffers
+    seeds_host = torch.from_numpy(seeds.astype(np.int64)).pin_memory()
+    samples_host = st.samples.cpu().pin_memory()
+    ns_host = torch.empty(num, dtype=torch.int32).pin_memory()
+    seeds_d2 = torch.empty_like(st.seeds_dev)
+    samples_d2 = torch.empty_like(st.samples)
+
+    def e2e_step(ev=None):
+        seeds_d2.copy_(seeds_host, non_blocking=True)
+        samples_d2.copy_(samples_host, non_blocking=True)
+        perc._ok(lib.perc_rank(L, seeds_d2.data_ptr(), len(seeds), st.perm.data_ptr(), st.rank.data_ptr(),
+                               st.ws.data_ptr(), st.ws.numel(), sp), "perc_rank")
+        if ev is not None:
+            ev.record(stream)
+        run_wrap(samples_d2.data_ptr())
+        ns_host.copy_(out, non_blocking=True)
+
+    e2e_ms, _ = timed(e2e_step, args.steps, args.warmup)
+    assert np.array_equal(ns_host.numpy().view(np.uint32), ns), "e2e n* differs from the resident step's"
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms_step = max_over_ranks(ms_step)
+    e2e_ms = max_over_ranks(e2e_ms)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, done, dt = oracle_rate(range(1, cpu_workers + 1), cpu_workers, _oracle_wrap_seed)
+        cpu = {"value": rate, "unit": "samples/s", "cores": cpu_workers, "kind": "oracle",
+               "sample": f"L=16, seeds 1..{cpu_workers} x 127 masks ({done} samples) in {dt:.1f} s, one "
+                         f"displacement sweep per sample, {cpu_workers} spawned workers"}
+    value = world * num / (ms_step * 1e-3)
+    if rank == 0:
+        line = {
+            "metric": WRAP_METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic (Philox-keyed site orders, seeds per rank)",
+            "config": {"workload": f"periodic boundaries, all 127 neighborhoods, L=16 (1,048,576 sites), seeds "
+                                   f"1..{num_seeds} per rank, {num} samples/rank, wrapping along x1, bisection over n",
+                       "L": L, "masks": 127, "seeds_per_rank": int(len(seeds)), "samples_per_rank": num,
+                       "l2": "flushed (256 MiB write) between timed steps; site orders > L2",
+                       "parallelism": f"dp{world} (seed blocks, no collective)"},
+            "phases_ms": {"rank": ms_rank, "wrap": ms_step - ms_rank},
+            "mean_nstar_over_N": float(ns.astype(np.float64).mean() / L ** 5),
+            "e2e": {"value": world * num / (e2e_ms * 1e-3), "unit": "samples/s", "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": int(seeds_host.numel() * 8 + samples_host.numel() * 8),
+                    "d2h_bytes_per_step": int(ns_host.numel() * 4)},
+            "roofline": None,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": (math.ceil(len(seeds) / 64) * 13) + 1,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------------
 # reference arm: the CPU oracle on the same workload
 # ------------------------------------------------------------------------------------------------
 def run_reference(args):
@@ -709,7 +855,7 @@ def run_reference(args):
     workers = max(1, min(host_cores(), 32))
     per_step = workers  # one seed (127 samples) per worker per step
     pmax = args.workload == "pmax"
-    fn = {"pmax": _oracle_pmax_seed, "any": _oracle_any_seed}.get(args.workload, _oracle_seed)
+    fn = {"pmax": _oracle_pmax_seed, "any": _oracle_any_seed, "wrap": _oracle_wrap_seed}.get(args.workload, _oracle_seed)
     for w in range(args.warmup):
         oracle_rate(range(1, min(per_step, 4) + 1), min(workers, 4), fn)
     rates, total_dt, total_done = [], 0.0, 0
@@ -721,7 +867,7 @@ def run_reference(args):
         total_done += done
     value = total_done / total_dt
     line = {
-        "impl": "reference", "metric": {"pmax": PMAX_METRIC, "any": ANY_METRIC}.get(args.workload, METRIC),
+        "impl": "reference", "metric": {"pmax": PMAX_METRIC, "any": ANY_METRIC, "wrap": WRAP_METRIC}.get(args.workload, METRIC),
         "value": value, "unit": "samples/s",
         "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_dt / args.steps,
@@ -729,6 +875,7 @@ def run_reference(args):
         "data": "synthetic (Philox-keyed site orders)",
         "config": {"workload": ("P_max(p) curves (16 p at Table I p_c +- 2%), " if pmax else "") +
                                ("n* for spanning along any axis, " if args.workload == "any" else "") +
+                               ("first wrapping n, periodic boundaries, " if args.workload == "wrap" else "") +
                                "all 127 neighborhoods, L=16 (1,048,576 sites); each step a bounded sample of "
                                f"{per_step} seeds x 127 masks", "L": L, "masks": 127},
         "cpu_baseline": {"value": value, "unit": "samples/s", "cores": workers, "kind": "oracle",
@@ -753,9 +900,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
     ap.add_argument("--no-graph", dest="graph", action="store_false", help="do not time CUDA-graph replays")
-    ap.add_argument("--workload", default="nstar", choices=["nstar", "pmax", "any"],
+    ap.add_argument("--workload", default="nstar", choices=["nstar", "pmax", "any", "wrap"],
                     help="nstar: the n* samples/s line (default); pmax: the P_max(p) path; any: n* for "
-                         "spanning along any of the five axes")
+                         "spanning along any of the five axes; wrap: first wrapping n with periodic boundaries")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one learned and one plain step inside a profiler range and exit")
     args = ap.parse_args()
@@ -765,6 +912,8 @@ def main():
         run_reference(args)
     elif args.workload == "pmax":
         run_pmax_ours(args)
+    elif args.workload == "wrap":
+        run_wrap_ours(args)
     else:
         run_ours(args)
 

@@ -56,6 +56,7 @@ typedef enum {
 #define PERC_OP_NSTAR 2
 #define PERC_OP_MASS 3
 #define PERC_OP_SMAX 4
+#define PERC_OP_PERIODIC 5 /* perc_mass_periodic and perc_nstar_wrap */
 
 /* zone_mask word of a sample: bits 0..6 select coordination zones 1..7 (at least one); bits 8..10
  * hold the spanning axis a = 0..4 that perc_nstar tests (borders x_{a+1} = 0 and x_{a+1} = L-1;
@@ -156,6 +157,33 @@ int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
  * Errors: PERC_EINVAL (null pointer, num 0, axes outside 1..5), PERC_ECUDA.
  */
 int perc_nstar_min_axes(const uint32_t *nstar, uint32_t num, uint32_t axes, uint32_t *out, void *stream);
+
+/*
+ * Periodic boundaries (a variant; the paper does not state its boundary conditions): offsets wrap
+ * modulo L in every coordinate, so the lattice is a 5-torus with no border.  Lattice sides up to
+ * PERC_PERIODIC_MAX_L.  Workspace: perc_workspace_bytes(PERC_OP_PERIODIC, max_L, num_samples).
+ * Samples that fail the device check get mass -1 / n* PERC_NEVER and set PERC_EDEVICE; a
+ * union-find walk longer than the sample's node count (which a correct forest never needs) sets
+ * PERC_ETIMEOUT and gives the same outputs.
+ *
+ * perc_mass_periodic -- S_max(n) on the torus: the largest cluster of each sample with its first
+ * n[k] sites occupied (eq. Pmax).
+ *   n     device uint64[num_samples], 0 <= n[k] <= L^5 (larger n is a device-side error)
+ *   mass  device int64[num_samples] (output)
+ *
+ * perc_nstar_wrap -- the first n at which a cluster wraps around the torus along the sample's
+ * axis (zone word bits 8..10): it holds a closed path whose steps' x_{a+1} components do not sum
+ * to zero.  Found by bisection over n with one union-find pass per probe that carries, for every
+ * node, the displacement along the axis to its parent.  Every neighborhood wraps at n = L^5.
+ *   nstar device uint32[num_samples] (output)
+ * Errors: PERC_EINVAL (null pointer, num_samples 0, max_L outside 1..PERC_PERIODIC_MAX_L),
+ * PERC_EWORKSPACE, PERC_ECUDA.
+ */
+#define PERC_PERIODIC_MAX_L 40u
+int perc_mass_periodic(const perc_sample *samples, uint32_t num_samples, uint32_t max_L, const uint64_t *n,
+                       int64_t *mass, void *workspace, size_t ws_bytes, void *stream);
+int perc_nstar_wrap(const perc_sample *samples, uint32_t num_samples, uint32_t max_L, uint32_t *nstar,
+                    void *workspace, size_t ws_bytes, void *stream);
 
 /*
  * perc_mass -- largest-cluster size S_max(n) of each sample with its first n[k] sites occupied

@@ -2127,6 +2127,7 @@ extern "C" size_t perc_workspace_bytes(int op, uint32_t max_L, uint32_t num)
         if (max_L < 1 || max_L > PERC_MAX_L || num == 0) return 0;
         return rank_workspace_bytes(max_L, num);
     }
+    if (op == PERC_OP_PERIODIC) return periodic_workspace_bytes(max_L, num);
     if (op != PERC_OP_NSTAR && op != PERC_OP_MASS && op != PERC_OP_SMAX) return 0;
     LaunchCfg cfg;
     if (launch_cfg(op, max_L, num, cfg) != PERC_OK) return 0;

@@ -174,5 +174,7 @@ __host__ __device__ inline uint64_t num_sites(uint32_t L)
 
 // Workspace of perc_rank for num_seeds seeds of side L (defined in perc_rank.cu).
 size_t rank_workspace_bytes(uint32_t L, uint32_t num_seeds);
+// Workspace of the periodic-boundary calls (defined in perc_periodic.cu); 0 when not configurable.
+size_t periodic_workspace_bytes(uint32_t max_L, uint32_t num);
 
 }  // namespace perc

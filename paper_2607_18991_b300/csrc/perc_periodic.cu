@@ -1,0 +1,302 @@
+// perc_periodic.cu -- the periodic-boundary variants of the path: offsets wrap modulo L in every
+// coordinate (the lattice is a 5-torus), a variant of the boundary conditions, which the paper does
+// not state (Methods, "Computational methods").
+//
+//   perc_mass_periodic  S_max with the first n sites of the Newman--Ziff order occupied (eq. Pmax);
+//   perc_nstar_wrap     the first n at which a cluster wraps around the torus along the sample's
+//                       axis: it holds a closed path whose steps' x_{a+1} components do not sum to
+//                       zero (the torus's counterpart of the spanning cluster, Introduction).
+//
+// One CTA per sample (persistent queue).  A pass at n: the bitmap of the first n sites, one
+// union-find node per site in rank space, and every edge taken once, from its later site in rank
+// order.  Each node word holds its parent and the displacement along the axis to it, so every
+// cluster carries an unwrapped coordinate; an edge inside one cluster whose ends disagree with
+// its step closes a winding path.  S_max counts the roots; n* is found by bisection over n
+// (wrapping is monotone in n, and it holds at n = L^5: every zone has a step with a non-zero
+// component along every axis, and repeating it L times winds around the torus).
+#include <algorithm>
+
+#include "perc_common.cuh"
+
+namespace perc {
+namespace {
+
+__constant__ ZoneTable c_tzones = kZones;
+
+constexpr uint32_t kPerThreads = 512;
+constexpr uint32_t kPeriodicMaxL = PERC_PERIODIC_MAX_L;  // displacements stay below 2 L^5 < 2^31
+constexpr size_t kPeriodicBudget = size_t(16) << 30;  // bytes of per-CTA slots in one launch
+
+struct PerHeader {
+    int status;       // first device-side error (perc_check reads it)
+    uint32_t queue;   // next sample
+    uint32_t pad[62];
+};
+static_assert(sizeof(PerHeader) == 256, "header is 256 bytes");
+
+__host__ __device__ inline size_t per_align(size_t b) { return (b + 255) & ~size_t(255); }
+__host__ __device__ inline size_t per_bm_words(uint64_t N) { return size_t(N / 32 + 1); }
+
+// Per-CTA slot: bitmap (one bit per site), node words (parent << 32 | displacement) and counts.
+__host__ __device__ inline size_t per_slot_bytes(uint64_t N)
+{
+    return per_align(per_bm_words(N) * 4) + per_align(size_t(N) * 8) + per_align(size_t(N) * 4);
+}
+
+__device__ __forceinline__ unsigned long long node_word(uint32_t parent, int32_t disp)
+{
+    return (static_cast<unsigned long long>(parent) << 32) | static_cast<uint32_t>(disp);
+}
+__device__ __forceinline__ uint32_t word_parent(unsigned long long w) { return static_cast<uint32_t>(w >> 32); }
+__device__ __forceinline__ int32_t word_disp(unsigned long long w) { return static_cast<int32_t>(static_cast<uint32_t>(w)); }
+
+// Root of x and pos(x) - pos(root) along the axis, with path halving (a compare-and-swap that may
+// fail: every word read stays a true relative position, since positions inside a cluster never
+// change once joined).  More than `cap` steps would mean a cycle in the forest: *bad is set.
+__device__ uint32_t tfind(unsigned long long *nd, uint32_t x, int32_t &d, uint32_t cap, bool &bad)
+{
+    int32_t acc = 0;
+    for (uint32_t it = 0; it <= cap; ++it) {
+        const unsigned long long w = __ldcg(nd + x);
+        const uint32_t p = word_parent(w);
+        if (p == x) {
+            d = acc;
+            return x;
+        }
+        const unsigned long long w2 = __ldcg(nd + p);
+        const uint32_t g = word_parent(w2);
+        if (g == p) {
+            d = acc + word_disp(w);
+            return p;
+        }
+        const int32_t dxg = word_disp(w) + word_disp(w2);
+        atomicCAS(nd + x, w, node_word(g, dxg));
+        acc += dxg;
+        x = g;
+    }
+    bad = true;
+    d = acc;
+    return x;
+}
+
+// Joins the clusters of nodes a and b over a step with pos(b) = pos(a) + step (the larger root
+// goes under the smaller).  Returns true when a and b already were one cluster and the step
+// disagrees with their coordinates: the edge closes a winding path.
+__device__ bool tunite(unsigned long long *nd, uint32_t a, uint32_t b, int32_t step, uint32_t cap, bool &bad)
+{
+    for (uint32_t it = 0; it <= cap; ++it) {
+        int32_t da, db;
+        const uint32_t ra = tfind(nd, a, da, cap, bad);
+        const uint32_t rb = tfind(nd, b, db, cap, bad);
+        if (bad) return false;
+        if (ra == rb) return da + step != db;
+        if (ra < rb) {  // pos(rb) - pos(ra) = da + step - db
+            if (atomicCAS(nd + rb, node_word(rb, 0), node_word(ra, da + step - db)) == node_word(rb, 0)) return false;
+        } else {  // pos(ra) - pos(rb) = db - da - step
+            if (atomicCAS(nd + ra, node_word(ra, 0), node_word(rb, db - da - step)) == node_word(ra, 0)) return false;
+        }
+    }
+    bad = true;
+    return false;
+}
+
+struct PerShared {
+    uint32_t sample;
+    uint32_t z;
+    uint32_t flag;   // a winding path was found in the running pass
+    uint32_t bad;    // a union-find loop ran out
+    uint32_t best;   // largest cluster
+    uint32_t offs[kMaxOffsets];  // the neighborhood's packed offsets
+};
+
+// One pass at n: the forest of the first n sites.  kWrap: stop as soon as a winding path along
+// `axis` closes; returns whether one did.  Otherwise every cluster is complete on return.
+template <bool kWrap>
+__device__ bool torus_pass(PerShared &sh, uint32_t *bm, unsigned long long *nd, const uint32_t *perm,
+                           const uint32_t *rank, uint32_t L, uint32_t N, uint32_t n, uint32_t axis)
+{
+    const uint32_t words = static_cast<uint32_t>(per_bm_words(N));
+    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) __stcg(bm + w, 0u);
+    for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) __stcg(nd + r, node_word(r, 0));
+    if (threadIdx.x == 0) sh.flag = 0u;
+    __syncthreads();
+    for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) {
+        const uint32_t i = __ldg(perm + r);
+        atomicOr(bm + (i >> 5), 1u << (i & 31u));
+    }
+    __syncthreads();
+    const uint32_t z = sh.z;
+    bool bad = false;
+    for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) {
+        if (kWrap && *reinterpret_cast<volatile uint32_t *>(&sh.flag)) break;
+        const uint32_t i = __ldg(perm + r);
+        uint32_t x[5], rest = i;
+        for (int k = 4; k >= 0; --k) {
+            x[k] = rest % L;
+            rest /= L;
+        }
+        for (uint32_t v = 0; v < z; ++v) {
+            const uint32_t packed = sh.offs[v];
+            uint32_t j = 0;
+            for (int k = 0; k < 5; ++k) j = j * L + (x[k] + 2u * L + zone_component(packed, k)) % L;
+            if (!((__ldcg(bm + (j >> 5)) >> (j & 31u)) & 1u)) continue;
+            const uint32_t rj = j == i ? r : __ldg(rank + j);
+            if (rj > r || (!kWrap && rj == r)) continue;  // the later site takes the edge; loops only wind
+            const int32_t step = zone_component(packed, static_cast<int>(axis));
+            if (tunite(nd, r, rj, step, n, bad) && kWrap) {
+                *reinterpret_cast<volatile uint32_t *>(&sh.flag) = 1u;
+                break;
+            }
+            if (bad) break;
+        }
+        if (bad) break;
+    }
+    if (bad) atomicOr(&sh.bad, 1u);
+    __syncthreads();
+    const bool wrapped = sh.flag != 0u;
+    __syncthreads();  // every thread has read the flag before the next pass clears it
+    return wrapped;
+}
+
+template <bool kWrap>
+__global__ void __launch_bounds__(kPerThreads) k_torus(const perc_sample *__restrict__ samples, uint32_t num,
+                                                       uint32_t max_L, const uint64_t *__restrict__ n_in,
+                                                       int64_t *__restrict__ mass_out, uint32_t *__restrict__ nstar_out,
+                                                       char *ws, size_t slot_bytes)
+{
+    __shared__ PerShared sh;
+    PerHeader *hdr = reinterpret_cast<PerHeader *>(ws);
+    char *slot = ws + sizeof(PerHeader) + size_t(blockIdx.x) * slot_bytes;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            sh.sample = atomicAdd(&hdr->queue, 1u);
+            sh.bad = 0u;
+        }
+        __syncthreads();
+        const uint32_t s = sh.sample;
+        if (s >= num) break;
+        const perc_sample smp = samples[s];
+        const uint32_t L = smp.L, word = smp.zone_mask, mask = word & 0x7Fu, axis = word >> 8;
+        const bool ok_word = mask != 0u && (word & ~0x77Fu) == 0u && axis < 5u;
+        const bool ok = L >= 1u && L <= max_L && ok_word && smp.perm && smp.rank &&
+                        (kWrap || n_in[s] <= num_sites(L));
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                if (kWrap)
+                    nstar_out[s] = PERC_NEVER;
+                else
+                    mass_out[s] = -1;
+                set_status(&hdr->status, PERC_EDEVICE);
+            }
+            __syncthreads();
+            continue;
+        }
+        const uint32_t N = static_cast<uint32_t>(num_sites(L));
+        uint32_t *bm = reinterpret_cast<uint32_t *>(slot);
+        unsigned long long *nd = reinterpret_cast<unsigned long long *>(slot + per_align(per_bm_words(N) * 4));
+        uint32_t *cnt = reinterpret_cast<uint32_t *>(slot + per_align(per_bm_words(N) * 4) + per_align(size_t(N) * 8));
+        if (threadIdx.x == 0) {  // the neighborhood's offsets, zone by zone
+            uint32_t z = 0;
+            for (int zone = 0; zone < kZoneCount; ++zone) {
+                if (!(mask & (1u << zone))) continue;
+                for (uint32_t k = c_tzones.start[zone]; k < c_tzones.start[zone + 1]; ++k) sh.offs[z++] = c_tzones.vec[k];
+            }
+            sh.z = z;
+            sh.best = 0u;
+        }
+        __syncthreads();
+        if (kWrap) {
+            uint32_t lo = 1, hi = N;  // wrap(N) holds (see the top of the file)
+            while (lo < hi && !sh.bad) {
+                const uint32_t mid = lo + (hi - lo) / 2u;
+                if (torus_pass<true>(sh, bm, nd, smp.perm, smp.rank, L, N, mid, axis))
+                    hi = mid;
+                else
+                    lo = mid + 1u;
+            }
+            if (threadIdx.x == 0) {
+                nstar_out[s] = sh.bad ? PERC_NEVER : lo;
+                if (sh.bad) set_status(&hdr->status, PERC_ETIMEOUT);
+            }
+        } else {
+            const uint32_t n = static_cast<uint32_t>(n_in[s]);
+            for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) __stcg(cnt + r, 0u);
+            torus_pass<false>(sh, bm, nd, smp.perm, smp.rank, L, N, n, axis);
+            bool bad = sh.bad != 0u;
+            for (uint32_t r = threadIdx.x; r < n && !bad; r += blockDim.x) {
+                int32_t d;
+                atomicAdd(cnt + tfind(nd, r, d, n, bad), 1u);
+            }
+            if (bad) atomicOr(&sh.bad, 1u);
+            __syncthreads();
+            uint32_t best = 0;
+            for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) best = max(best, __ldcg(cnt + r));
+            best = __reduce_max_sync(0xffffffffu, best);
+            if ((threadIdx.x & 31u) == 0u) atomicMax(&sh.best, best);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                mass_out[s] = sh.bad ? -1 : static_cast<int64_t>(sh.best);
+                if (sh.bad) set_status(&hdr->status, PERC_ETIMEOUT);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Launch shape shared by the workspace query and the launch: CTAs = min(samples, 2 per SM, what
+// the slot budget allows).
+int torus_cfg(uint32_t max_L, uint32_t num, uint32_t &grid, size_t &slot)
+{
+    if (max_L < 1 || max_L > kPeriodicMaxL || num == 0) return PERC_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PERC_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PERC_ECUDA;
+    slot = per_slot_bytes(num_sites(max_L));
+    const size_t by_budget = std::max<size_t>(1, kPeriodicBudget / slot);
+    grid = static_cast<uint32_t>(std::min<size_t>({size_t(num), size_t(2 * sms), by_budget}));
+    return PERC_OK;
+}
+
+template <bool kWrap>
+int torus_launch(const perc_sample *samples, uint32_t num, uint32_t max_L, const uint64_t *n, int64_t *mass,
+                 uint32_t *nstar, void *workspace, size_t ws_bytes, void *stream_)
+{
+    uint32_t grid = 0;
+    size_t slot = 0;
+    const int rc = torus_cfg(max_L, num, grid, slot);
+    if (rc != PERC_OK) return rc;
+    if (ws_bytes < sizeof(PerHeader) + size_t(grid) * slot) return PERC_EWORKSPACE;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (cudaMemsetAsync(workspace, 0, sizeof(PerHeader), stream) != cudaSuccess) return PERC_ECUDA;
+    k_torus<kWrap><<<grid, kPerThreads, 0, stream>>>(samples, num, max_L, n, mass, nstar,
+                                                     static_cast<char *>(workspace), slot);
+    return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
+}
+
+}  // namespace
+
+size_t periodic_workspace_bytes(uint32_t max_L, uint32_t num)
+{
+    uint32_t grid = 0;
+    size_t slot = 0;
+    if (torus_cfg(max_L, num, grid, slot) != PERC_OK) return 0;
+    return sizeof(PerHeader) + size_t(grid) * slot;
+}
+
+}  // namespace perc
+
+using namespace perc;
+
+extern "C" int perc_mass_periodic(const perc_sample *samples, uint32_t num_samples, uint32_t max_L, const uint64_t *n,
+                                  int64_t *mass, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!samples || !n || !mass || !workspace || num_samples == 0) return PERC_EINVAL;
+    return torus_launch<false>(samples, num_samples, max_L, n, mass, nullptr, workspace, ws_bytes, stream);
+}
+
+extern "C" int perc_nstar_wrap(const perc_sample *samples, uint32_t num_samples, uint32_t max_L, uint32_t *nstar,
+                               void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!samples || !nstar || !workspace || num_samples == 0) return PERC_EINVAL;
+    return torus_launch<true>(samples, num_samples, max_L, nullptr, nullptr, nstar, workspace, ws_bytes, stream);
+}

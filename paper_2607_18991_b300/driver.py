@@ -138,6 +138,38 @@ def nstar_any(workload, params: torch.Tensor | None = None, margin: float = 0.0,
     return run_nstar_any(iter_prepared(workload, budget), len(workload), params, margin)
 
 
+def nstar_wrap(workload, budget: int = DEFAULT_BUDGET):
+    """First n at which a cluster wraps around the torus (periodic boundaries) along each row's
+    axis, for every (L, zone word, seed) row of `workload` (uint32 numpy)."""
+    workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
+    ws = perc.default_workspace()
+    out = np.zeros(len(workload), dtype=np.uint32)
+    for p in iter_prepared(workload, budget, ws):
+        ns = perc.nstar_wrap(p.samples, p.max_L, ws=ws)
+        out[p.idx] = perc.u32(ns)
+        rc = perc.check(ws)
+        if rc != 0:
+            raise perc.PercError(rc, "perc_nstar_wrap device status")
+        del p
+    return out
+
+
+def mass_periodic(workload, n, budget: int = DEFAULT_BUDGET):
+    """S_max(n[k]) on the torus (periodic boundaries) for every row of `workload` (int64 numpy)."""
+    workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
+    n = np.asarray(n, dtype=np.int64).reshape(-1)
+    ws = perc.default_workspace()
+    out = np.zeros(len(workload), dtype=np.int64)
+    for p in iter_prepared(workload, budget, ws):
+        m = perc.mass_periodic(p.samples, p.max_L, torch.as_tensor(n[p.idx]), ws=ws)
+        out[p.idx] = m.cpu().numpy()
+        rc = perc.check(ws)
+        if rc != 0:
+            raise perc.PercError(rc, "perc_mass_periodic device status")
+        del p
+    return out
+
+
 def mass(workload, n, budget: int = DEFAULT_BUDGET):
     """S_max(n[k]) for every (L, mask, seed) row of `workload` (int64 numpy)."""
     workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)

@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libperc.so")
 NEVER = 0xFFFFFFFF
 MAX_L = 73
-OP_RANK, OP_NSTAR, OP_MASS, OP_SMAX = 1, 2, 3, 4
+OP_RANK, OP_NSTAR, OP_MASS, OP_SMAX, OP_PERIODIC = 1, 2, 3, 4, 5
+PERIODIC_MAX_L = 40
 AXIS_SHIFT, NUM_AXES = 8, 5  # zone word: spanning axis in bits 8..10; axes x1..x5
 OPT_THREADS, OPT_SMEM_NODES, OPT_MAX_CTAS, OPT_GROUP, OPT_METHOD = 1, 2, 3, 4, 5
 METHOD_AUTO, METHOD_BISECTION, METHOD_SWEEP = 0, 1, 2
@@ -51,6 +52,8 @@ def lib() -> ctypes.CDLL:
         "perc_nstar": (i32, [vp, u32, u32, vp, vp, vp, vp, vp, sz, vp]),
         "perc_nstar_noalloc": (i32, [vp, u32, u32, vp, vp, vp, vp, vp]),
         "perc_nstar_min_axes": (i32, [vp, u32, u32, vp, vp]),
+        "perc_mass_periodic": (i32, [vp, u32, u32, vp, vp, vp, sz, vp]),
+        "perc_nstar_wrap": (i32, [vp, u32, u32, vp, vp, sz, vp]),
         "perc_mass": (i32, [vp, u32, u32, vp, vp, vp, sz, vp]),
         "perc_smax_window": (i32, [vp, u32, u32, vp, vp, u32, vp, vp, sz, vp]),
         "perc_binomial_weights": (i32, [vp, vp, vp, u32, u32, vp, u32, vp, vp]),
@@ -74,6 +77,7 @@ def lib() -> ctypes.CDLL:
 
 def exported_symbols() -> list[str]:
     return ["perc_workspace_bytes", "perc_rank", "perc_nstar", "perc_nstar_noalloc", "perc_nstar_min_axes", "perc_mass",
+            "perc_mass_periodic", "perc_nstar_wrap",
             "perc_smax_window", "perc_binomial_weights", "perc_pmax", "perc_check",
             "perc_mlp_forward", "perc_mlp_grad", "perc_adam", "perc_mlp_train", "perc_bracket",
             "perc_status_string", "perc_set_launch_option"]
@@ -212,6 +216,31 @@ def nstar_min_axes(nstar_axes: torch.Tensor, axes: int = NUM_AXES, out=None, str
     _ok(lib().perc_nstar_min_axes(nstar_axes.data_ptr(), num, axes, o.data_ptr(), _stream(stream)),
         "perc_nstar_min_axes")
     return o
+
+
+def mass_periodic(samples: torch.Tensor, max_L: int, n: torch.Tensor, ws: Workspace | None = None,
+                  stream=None, out=None):
+    """perc_mass_periodic: S_max(n) on the torus (offsets wrap modulo L), int64 tensor [num]."""
+    num = samples.shape[0]
+    m = out if out is not None else torch.empty(num, dtype=torch.int64, device="cuda")
+    n = n.to(device="cuda", dtype=torch.int64).contiguous()
+    ws = ws or default_workspace()
+    buf = ws.get(workspace_bytes(OP_PERIODIC, max_L, num))
+    _ok(lib().perc_mass_periodic(samples.data_ptr(), num, max_L, n.data_ptr(), m.data_ptr(), buf.data_ptr(),
+                                 buf.numel(), _stream(stream)), "perc_mass_periodic")
+    return m
+
+
+def nstar_wrap(samples: torch.Tensor, max_L: int, ws: Workspace | None = None, stream=None, out=None):
+    """perc_nstar_wrap: first n at which a cluster wraps around the torus along each sample's axis,
+    int32 tensor [num] of uint32 values."""
+    num = samples.shape[0]
+    ns = out if out is not None else torch.empty(num, dtype=torch.int32, device="cuda")
+    ws = ws or default_workspace()
+    buf = ws.get(workspace_bytes(OP_PERIODIC, max_L, num))
+    _ok(lib().perc_nstar_wrap(samples.data_ptr(), num, max_L, ns.data_ptr(), buf.data_ptr(), buf.numel(),
+                              _stream(stream)), "perc_nstar_wrap")
+    return ns
 
 
 def nstar_noalloc(samples: torch.Tensor, max_L: int, bracket: torch.Tensor | None = None,

@@ -36,3 +36,18 @@ def orc_nstar_rule(workload, span=None) -> np.ndarray:
         rule = int(w) >> 8 if span is None else span
         out[k] = oracle.nstar_span(int(L), int(w) & 0x7F, rule, perm, rk)
     return out
+
+
+def orc_periodic(workload, n=None):
+    """Oracle on the torus for rows (L, zone word, seed): the first wrapping n along the word's
+    axis, and S_max(n[k]) when n is given."""
+    nw = np.zeros(len(workload), dtype=np.uint32)
+    sm = np.zeros(len(workload), dtype=np.int64)
+    for k, (L, w, s) in enumerate(np.asarray(workload, dtype=np.int64)):
+        perm, rk = orc_order(int(L), int(s))
+        q = [] if n is None else [int(n[k])]
+        a, b = oracle.nz_periodic(int(L), int(w) & 0x7F, perm, rk, q, int(w) >> 8)
+        nw[k] = a
+        if n is not None:
+            sm[k] = b[0]
+    return nw, sm
