@@ -7,13 +7,14 @@
 //                       axis: it holds a closed path whose steps' x_{a+1} components do not sum to
 //                       zero (the torus's counterpart of the spanning cluster, Introduction).
 //
-// One CTA per sample (persistent queue).  A pass at n: the bitmap of the first n sites, one
-// union-find node per site in rank space, and every edge taken once, from its later site in rank
-// order.  Each node word holds its parent and the displacement along the axis to it, so every
+// One CTA per sample (persistent queue).  The forest of the first n sites: the bitmap of those
+// sites, one union-find node per site in rank space, and every edge taken once, from its later site
+// in rank order.  Each node word holds its parent and the displacement along the axis to it, so every
 // cluster carries an unwrapped coordinate; an edge inside one cluster whose ends disagree with
 // its step closes a winding path.  S_max counts the roots; n* is found by bisection over n
 // (wrapping is monotone in n, and it holds at n = L^5: every zone has a step with a non-zero
-// component along every axis, and repeating it L times winds around the torus).
+// component along every axis, and repeating it L times winds around the torus), each probe
+// extending the forest of the largest n known not to wrap.
 #include <algorithm>
 
 #include "perc_common.cuh"
@@ -37,10 +38,11 @@ static_assert(sizeof(PerHeader) == 256, "header is 256 bytes");
 __host__ __device__ inline size_t per_align(size_t b) { return (b + 255) & ~size_t(255); }
 __host__ __device__ inline size_t per_bm_words(uint64_t N) { return size_t(N / 32 + 1); }
 
-// Per-CTA slot: bitmap (one bit per site), node words (parent << 32 | displacement) and counts.
+// Per-CTA slot: bitmap (one bit per site), two forests of node words (parent << 32 | displacement:
+// the committed one and the probe's) and cluster counts.
 __host__ __device__ inline size_t per_slot_bytes(uint64_t N)
 {
-    return per_align(per_bm_words(N) * 4) + per_align(size_t(N) * 8) + per_align(size_t(N) * 4);
+    return per_align(per_bm_words(N) * 4) + 2 * per_align(size_t(N) * 8) + per_align(size_t(N) * 4);
 }
 
 __device__ __forceinline__ unsigned long long node_word(uint32_t parent, int32_t disp)
@@ -109,41 +111,50 @@ struct PerShared {
     uint32_t offs[kMaxOffsets];  // the neighborhood's packed offsets
 };
 
-// One pass at n: the forest of the first n sites.  kWrap: stop as soon as a winding path along
-// `axis` closes; returns whether one did.  Otherwise every cluster is complete on return.
-template <bool kWrap>
-__device__ bool torus_pass(PerShared &sh, uint32_t *bm, unsigned long long *nd, const uint32_t *perm,
-                           const uint32_t *rank, uint32_t L, uint32_t N, uint32_t n, uint32_t axis)
+// Bitmap bits and singleton nodes of the sites of rank r0 .. r1-1.
+__device__ void torus_add(uint32_t *bm, unsigned long long *nd, const uint32_t *perm, uint32_t r0, uint32_t r1)
 {
-    const uint32_t words = static_cast<uint32_t>(per_bm_words(N));
-    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) __stcg(bm + w, 0u);
-    for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) __stcg(nd + r, node_word(r, 0));
-    if (threadIdx.x == 0) sh.flag = 0u;
-    __syncthreads();
-    for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) {
+    for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        __stcg(nd + r, node_word(r, 0));
         const uint32_t i = __ldg(perm + r);
         atomicOr(bm + (i >> 5), 1u << (i & 31u));
     }
-    __syncthreads();
+}
+
+// The sites of rank r0 .. r1-1 join the forest `nd` of the first r0 sites (the bitmap holds the
+// first r1 sites, their nodes are set).  Every edge is taken by its later site in rank order, so
+// the new sites' edges to each other and to the earlier sites are all seen.  kWrap: stop as soon as
+// a winding path along `axis` closes (sh.flag).  Ends with a barrier.
+template <bool kWrap>
+__device__ void torus_link(PerShared &sh, const uint32_t *bm, unsigned long long *nd, const uint32_t *perm,
+                           const uint32_t *rank, uint32_t L, uint32_t r0, uint32_t r1, uint32_t axis)
+{
     const uint32_t z = sh.z;
     bool bad = false;
-    for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) {
+    for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
         if (kWrap && *reinterpret_cast<volatile uint32_t *>(&sh.flag)) break;
         const uint32_t i = __ldg(perm + r);
-        uint32_t x[5], rest = i;
+        // per axis k, the wrapped coordinates (x_k + d) mod L for d = -2..2, six bits each
+        uint32_t wk[5], rest = i;
+#pragma unroll
         for (int k = 4; k >= 0; --k) {
-            x[k] = rest % L;
+            const uint32_t xk = rest % L;
             rest /= L;
+            uint32_t w = 0;
+#pragma unroll
+            for (uint32_t f = 0; f < 5u; ++f) w |= ((xk + 2u * L + f - 2u) % L) << (6u * f);
+            wk[k] = w;
         }
         for (uint32_t v = 0; v < z; ++v) {
             const uint32_t packed = sh.offs[v];
             uint32_t j = 0;
-            for (int k = 0; k < 5; ++k) j = j * L + (x[k] + 2u * L + zone_component(packed, k)) % L;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) j = j * L + ((wk[k] >> (6u * ((packed >> (3 * k)) & 7u))) & 63u);
             if (!((__ldcg(bm + (j >> 5)) >> (j & 31u)) & 1u)) continue;
             const uint32_t rj = j == i ? r : __ldg(rank + j);
             if (rj > r || (!kWrap && rj == r)) continue;  // the later site takes the edge; loops only wind
             const int32_t step = zone_component(packed, static_cast<int>(axis));
-            if (tunite(nd, r, rj, step, n, bad) && kWrap) {
+            if (tunite(nd, r, rj, step, r1, bad) && kWrap) {
                 *reinterpret_cast<volatile uint32_t *>(&sh.flag) = 1u;
                 break;
             }
@@ -153,9 +164,6 @@ __device__ bool torus_pass(PerShared &sh, uint32_t *bm, unsigned long long *nd, 
     }
     if (bad) atomicOr(&sh.bad, 1u);
     __syncthreads();
-    const bool wrapped = sh.flag != 0u;
-    __syncthreads();  // every thread has read the flag before the next pass clears it
-    return wrapped;
 }
 
 template <bool kWrap>
@@ -193,8 +201,12 @@ __global__ void __launch_bounds__(kPerThreads) k_torus(const perc_sample *__rest
         }
         const uint32_t N = static_cast<uint32_t>(num_sites(L));
         uint32_t *bm = reinterpret_cast<uint32_t *>(slot);
-        unsigned long long *nd = reinterpret_cast<unsigned long long *>(slot + per_align(per_bm_words(N) * 4));
-        uint32_t *cnt = reinterpret_cast<uint32_t *>(slot + per_align(per_bm_words(N) * 4) + per_align(size_t(N) * 8));
+        const size_t bm_bytes = per_align(per_bm_words(N) * 4), nd_bytes = per_align(size_t(N) * 8);
+        unsigned long long *ndc = reinterpret_cast<unsigned long long *>(slot + bm_bytes);  // committed forest
+        unsigned long long *ndw = reinterpret_cast<unsigned long long *>(slot + bm_bytes + nd_bytes);
+        uint32_t *cnt = reinterpret_cast<uint32_t *>(slot + bm_bytes + 2 * nd_bytes);
+        const uint32_t words = static_cast<uint32_t>(per_bm_words(N));
+        for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) __stcg(bm + w, 0u);
         if (threadIdx.x == 0) {  // the neighborhood's offsets, zone by zone
             uint32_t z = 0;
             for (int zone = 0; zone < kZoneCount; ++zone) {
@@ -206,13 +218,33 @@ __global__ void __launch_bounds__(kPerThreads) k_torus(const perc_sample *__rest
         }
         __syncthreads();
         if (kWrap) {
-            uint32_t lo = 1, hi = N;  // wrap(N) holds (see the top of the file)
+            // bisection over n with the forest of the largest n known not to wrap (nc = lo - 1)
+            // kept: a probe copies it and adds only the sites from nc up to the probe, and a probe
+            // that wraps is dropped again (its bitmap bits cleared)
+            uint32_t lo = 1, hi = N, nc = 0;  // wrap(N) holds (see the top of the file)
             while (lo < hi && !sh.bad) {
-                const uint32_t mid = lo + (hi - lo) / 2u;
-                if (torus_pass<true>(sh, bm, nd, smp.perm, smp.rank, L, N, mid, axis))
+                const uint32_t mid = lo + (hi - lo) / 2u;  // > nc
+                for (uint32_t r = threadIdx.x; r < nc; r += blockDim.x) __stcg(ndw + r, __ldcg(ndc + r));
+                torus_add(bm, ndw, smp.perm, nc, mid);
+                if (threadIdx.x == 0) sh.flag = 0u;
+                __syncthreads();
+                torus_link<true>(sh, bm, ndw, smp.perm, smp.rank, L, nc, mid, axis);
+                const bool wrapped = sh.flag != 0u;
+                __syncthreads();  // every thread has read the flag before the next probe clears it
+                if (wrapped) {
                     hi = mid;
-                else
+                    for (uint32_t r = nc + threadIdx.x; r < mid; r += blockDim.x) {
+                        const uint32_t i = __ldg(smp.perm + r);
+                        atomicAnd(bm + (i >> 5), ~(1u << (i & 31u)));
+                    }
+                    __syncthreads();  // cleared before the next probe sets bits again
+                } else {
                     lo = mid + 1u;
+                    unsigned long long *tmp = ndc;
+                    ndc = ndw;
+                    ndw = tmp;
+                    nc = mid;
+                }
             }
             if (threadIdx.x == 0) {
                 nstar_out[s] = sh.bad ? PERC_NEVER : lo;
@@ -221,11 +253,13 @@ __global__ void __launch_bounds__(kPerThreads) k_torus(const perc_sample *__rest
         } else {
             const uint32_t n = static_cast<uint32_t>(n_in[s]);
             for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) __stcg(cnt + r, 0u);
-            torus_pass<false>(sh, bm, nd, smp.perm, smp.rank, L, N, n, axis);
+            torus_add(bm, ndc, smp.perm, 0u, n);
+            __syncthreads();
+            torus_link<false>(sh, bm, ndc, smp.perm, smp.rank, L, 0u, n, axis);
             bool bad = sh.bad != 0u;
             for (uint32_t r = threadIdx.x; r < n && !bad; r += blockDim.x) {
                 int32_t d;
-                atomicAdd(cnt + tfind(nd, r, d, n, bad), 1u);
+                atomicAdd(cnt + tfind(ndc, r, d, n, bad), 1u);
             }
             if (bad) atomicOr(&sh.bad, 1u);
             __syncthreads();
