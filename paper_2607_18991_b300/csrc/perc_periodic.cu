@@ -24,7 +24,8 @@ namespace {
 
 __constant__ ZoneTable c_tzones = kZones;
 
-constexpr uint32_t kPerThreads = 512;
+constexpr uint32_t kPerThreads = 1024;
+constexpr uint32_t kTorusSmemMaxL = 16;  // up to L = 16 the bitmap (128 KiB) lives in shared memory
 constexpr uint32_t kPeriodicMaxL = PERC_PERIODIC_MAX_L;  // displacements stay below 2 L^5 < 2^31
 constexpr size_t kPeriodicBudget = size_t(16) << 30;  // bytes of per-CTA slots in one launch
 
@@ -126,8 +127,9 @@ __device__ void torus_add(uint32_t *bm, unsigned long long *nd, const uint32_t *
 // the new sites' edges to each other and to the earlier sites are all seen.  kWrap: stop as soon as
 // a winding path along `axis` closes (sh.flag).  Ends with a barrier.
 template <bool kWrap>
-__device__ void torus_link(PerShared &sh, const uint32_t *bm, unsigned long long *nd, const uint32_t *perm,
-                           const uint32_t *rank, uint32_t L, uint32_t r0, uint32_t r1, uint32_t axis)
+__device__ void torus_link(PerShared &sh, const uint32_t *bm, bool smem_bm, unsigned long long *nd,
+                           const uint32_t *perm, const uint32_t *rank, uint32_t L, uint32_t r0, uint32_t r1,
+                           uint32_t axis)
 {
     const uint32_t z = sh.z;
     bool bad = false;
@@ -150,7 +152,8 @@ __device__ void torus_link(PerShared &sh, const uint32_t *bm, unsigned long long
             uint32_t j = 0;
 #pragma unroll
             for (int k = 0; k < 5; ++k) j = j * L + ((wk[k] >> (6u * ((packed >> (3 * k)) & 7u))) & 63u);
-            if (!((__ldcg(bm + (j >> 5)) >> (j & 31u)) & 1u)) continue;
+            const uint32_t word = smem_bm ? bm[j >> 5] : __ldcg(bm + (j >> 5));
+            if (!((word >> (j & 31u)) & 1u)) continue;
             const uint32_t rj = j == i ? r : __ldg(rank + j);
             if (rj > r || (!kWrap && rj == r)) continue;  // the later site takes the edge; loops only wind
             const int32_t step = zone_component(packed, static_cast<int>(axis));
@@ -166,13 +169,16 @@ __device__ void torus_link(PerShared &sh, const uint32_t *bm, unsigned long long
     __syncthreads();
 }
 
+// smem_L: samples with L <= smem_L keep the bitmap in the dynamic shared memory (0: none do).
 template <bool kWrap>
-__global__ void __launch_bounds__(kPerThreads) k_torus(const perc_sample *__restrict__ samples, uint32_t num,
-                                                       uint32_t max_L, const uint64_t *__restrict__ n_in,
-                                                       int64_t *__restrict__ mass_out, uint32_t *__restrict__ nstar_out,
-                                                       char *ws, size_t slot_bytes)
+__global__ void __launch_bounds__(kPerThreads, 1) k_torus(const perc_sample *__restrict__ samples, uint32_t num,
+                                                          uint32_t max_L, uint32_t smem_L,
+                                                          const uint64_t *__restrict__ n_in,
+                                                          int64_t *__restrict__ mass_out,
+                                                          uint32_t *__restrict__ nstar_out, char *ws, size_t slot_bytes)
 {
     __shared__ PerShared sh;
+    extern __shared__ uint32_t sbm[];
     PerHeader *hdr = reinterpret_cast<PerHeader *>(ws);
     char *slot = ws + sizeof(PerHeader) + size_t(blockIdx.x) * slot_bytes;
     for (;;) {
@@ -200,13 +206,19 @@ __global__ void __launch_bounds__(kPerThreads) k_torus(const perc_sample *__rest
             continue;
         }
         const uint32_t N = static_cast<uint32_t>(num_sites(L));
-        uint32_t *bm = reinterpret_cast<uint32_t *>(slot);
+        const bool smem_bm = L <= smem_L;
+        uint32_t *bm = smem_bm ? sbm : reinterpret_cast<uint32_t *>(slot);
         const size_t bm_bytes = per_align(per_bm_words(N) * 4), nd_bytes = per_align(size_t(N) * 8);
         unsigned long long *ndc = reinterpret_cast<unsigned long long *>(slot + bm_bytes);  // committed forest
         unsigned long long *ndw = reinterpret_cast<unsigned long long *>(slot + bm_bytes + nd_bytes);
         uint32_t *cnt = reinterpret_cast<uint32_t *>(slot + bm_bytes + 2 * nd_bytes);
         const uint32_t words = static_cast<uint32_t>(per_bm_words(N));
-        for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) __stcg(bm + w, 0u);
+        for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) {
+            if (smem_bm)
+                bm[w] = 0u;
+            else
+                __stcg(bm + w, 0u);
+        }
         if (threadIdx.x == 0) {  // the neighborhood's offsets, zone by zone
             uint32_t z = 0;
             for (int zone = 0; zone < kZoneCount; ++zone) {
@@ -228,7 +240,7 @@ __global__ void __launch_bounds__(kPerThreads) k_torus(const perc_sample *__rest
                 torus_add(bm, ndw, smp.perm, nc, mid);
                 if (threadIdx.x == 0) sh.flag = 0u;
                 __syncthreads();
-                torus_link<true>(sh, bm, ndw, smp.perm, smp.rank, L, nc, mid, axis);
+                torus_link<true>(sh, bm, smem_bm, ndw, smp.perm, smp.rank, L, nc, mid, axis);
                 const bool wrapped = sh.flag != 0u;
                 __syncthreads();  // every thread has read the flag before the next probe clears it
                 if (wrapped) {
@@ -255,7 +267,7 @@ __global__ void __launch_bounds__(kPerThreads) k_torus(const perc_sample *__rest
             for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) __stcg(cnt + r, 0u);
             torus_add(bm, ndc, smp.perm, 0u, n);
             __syncthreads();
-            torus_link<false>(sh, bm, ndc, smp.perm, smp.rank, L, 0u, n, axis);
+            torus_link<false>(sh, bm, smem_bm, ndc, smp.perm, smp.rank, L, 0u, n, axis);
             bool bad = sh.bad != 0u;
             for (uint32_t r = threadIdx.x; r < n && !bad; r += blockDim.x) {
                 int32_t d;
@@ -277,9 +289,9 @@ __global__ void __launch_bounds__(kPerThreads) k_torus(const perc_sample *__rest
     }
 }
 
-// Launch shape shared by the workspace query and the launch: CTAs = min(samples, 2 per SM, what
-// the slot budget allows).
-int torus_cfg(uint32_t max_L, uint32_t num, uint32_t &grid, size_t &slot)
+// Launch shape shared by the workspace query and the launch: one CTA per SM (1024 threads), at most
+// one per sample and what the slot budget allows; the bitmap in shared memory when max_L <= 16.
+int torus_cfg(uint32_t max_L, uint32_t num, uint32_t &grid, size_t &slot, size_t &smem)
 {
     if (max_L < 1 || max_L > kPeriodicMaxL || num == 0) return PERC_EINVAL;
     int dev = 0, sms = 0;
@@ -287,7 +299,8 @@ int torus_cfg(uint32_t max_L, uint32_t num, uint32_t &grid, size_t &slot)
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PERC_ECUDA;
     slot = per_slot_bytes(num_sites(max_L));
     const size_t by_budget = std::max<size_t>(1, kPeriodicBudget / slot);
-    grid = static_cast<uint32_t>(std::min<size_t>({size_t(num), size_t(2 * sms), by_budget}));
+    grid = static_cast<uint32_t>(std::min<size_t>({size_t(num), size_t(sms), by_budget}));
+    smem = max_L <= kTorusSmemMaxL ? per_bm_words(num_sites(max_L)) * 4 : 0;
     return PERC_OK;
 }
 
@@ -296,14 +309,21 @@ int torus_launch(const perc_sample *samples, uint32_t num, uint32_t max_L, const
                  uint32_t *nstar, void *workspace, size_t ws_bytes, void *stream_)
 {
     uint32_t grid = 0;
-    size_t slot = 0;
-    const int rc = torus_cfg(max_L, num, grid, slot);
+    size_t slot = 0, smem = 0;
+    const int rc = torus_cfg(max_L, num, grid, slot, smem);
     if (rc != PERC_OK) return rc;
     if (ws_bytes < sizeof(PerHeader) + size_t(grid) * slot) return PERC_EWORKSPACE;
+    static size_t attr_smem = 0;  // largest dynamic shared memory this instance was allowed so far
+    if (smem > attr_smem) {
+        if (cudaFuncSetAttribute(k_torus<kWrap>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+            return PERC_ECUDA;
+        attr_smem = smem;
+    }
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(PerHeader), stream) != cudaSuccess) return PERC_ECUDA;
-    k_torus<kWrap><<<grid, kPerThreads, 0, stream>>>(samples, num, max_L, n, mass, nstar,
-                                                     static_cast<char *>(workspace), slot);
+    const uint32_t smem_L = smem ? max_L : 0u;
+    k_torus<kWrap><<<grid, kPerThreads, smem, stream>>>(samples, num, max_L, smem_L, n, mass, nstar,
+                                                        static_cast<char *>(workspace), slot);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }
 
@@ -312,8 +332,8 @@ int torus_launch(const perc_sample *samples, uint32_t num, uint32_t max_L, const
 size_t periodic_workspace_bytes(uint32_t max_L, uint32_t num)
 {
     uint32_t grid = 0;
-    size_t slot = 0;
-    if (torus_cfg(max_L, num, grid, slot) != PERC_OK) return 0;
+    size_t slot = 0, smem = 0;
+    if (torus_cfg(max_L, num, grid, slot, smem) != PERC_OK) return 0;
     return sizeof(PerHeader) + size_t(grid) * slot;
 }
 

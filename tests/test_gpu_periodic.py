@@ -74,3 +74,14 @@ def test_invalid_samples_and_arguments():
     assert int(m.cpu()[0]) == -1 and perc.check() == -5
     with pytest.raises(perc.PercError):
         perc.nstar_wrap(s, 41)  # above the periodic calls' largest side
+
+
+def test_global_bitmap_path_above_16():
+    # a launch whose largest side is above 16 keeps every sample's bitmap in global memory
+    from paper_2607_18991_b300 import driver
+    w = np.concatenate([rows(20, (1, 64, 127), (1,), (0, 2)), rows(9, (3, 100), (2,), (1,))])
+    N = w[:, 0] ** 5
+    n = (N * np.array([0.1, 0.02, 0.3, 0.15, 0.01, 0.5, 0.2, 0.05])).astype(np.int64)
+    want_w, want_m = orc_periodic(w, n)
+    assert np.array_equal(driver.nstar_wrap(w), want_w)
+    assert np.array_equal(driver.mass_periodic(w, n), want_m)
