@@ -27,7 +27,7 @@ def _chunks(workload: np.ndarray, budget: int):
         L, _, seed = (int(v) for v in workload[idx])
         key = (L, seed)
         cost = 0 if key in seen else 8 * L ** 5
-        if chunk and used + cost > budget:
+        if chunk and cost and used + cost > budget:  # a sample whose order is already here joins
             yield np.array(chunk)
             chunk, seen, used = [], set(), 0
             cost = 8 * L ** 5

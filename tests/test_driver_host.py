@@ -1,0 +1,47 @@
+"""Host logic of the batched driver, without a GPU: the split of a workload into chunks whose
+distinct site orders (perm + rank, 8 bytes a site) fit a device-memory budget."""
+import numpy as np
+
+from paper_2607_18991_b300 import driver, workloads
+
+
+def order_bytes(rows):
+    return sum(8 * L ** 5 for L, s in {(int(r[0]), int(r[2])) for r in rows})
+
+
+def check_chunks(w, budget):
+    chunks = list(driver._chunks(w, budget))
+    idx = np.concatenate(chunks)
+    assert np.array_equal(np.sort(idx), np.arange(len(w)))  # every sample exactly once
+    for c in chunks:
+        rows = w[c]
+        # a chunk's orders fit, unless one order alone is larger than the budget
+        assert order_bytes(rows) <= budget or len({(int(r[0]), int(r[2])) for r in rows}) == 1
+        assert np.all(np.diff(rows[:, 0]) <= 0)  # largest lattices first
+    return chunks
+
+
+def test_one_chunk_when_everything_fits():
+    w = workloads.samples(8, range(1, 128), range(1, 5))
+    chunks = check_chunks(w, driver.DEFAULT_BUDGET)
+    assert len(chunks) == 1
+
+
+def test_split_keeps_orders_shared_by_their_masks():
+    # four seeds of L = 16 (8 MiB of orders each) under a 20 MiB budget: two seeds a chunk, and
+    # every mask of a seed lands in the chunk that holds its order
+    w = workloads.samples(16, range(1, 128), range(1, 5))
+    chunks = check_chunks(w, 20 << 20)
+    assert len(chunks) == 2
+    for c in chunks:
+        seeds = set(w[c, 2].tolist())
+        assert len(seeds) == 2 and len(c) == 2 * 127
+
+
+def test_mixed_sides_and_oversized_orders():
+    w = workloads.mixed4096(300)
+    check_chunks(w, 64 << 20)
+    # an order larger than the budget still forms a chunk of its own
+    big = workloads.samples(24, [1, 127], [1, 2])  # 8 * 24^5 bytes = 61 MiB per order
+    chunks = check_chunks(big, 16 << 20)
+    assert len(chunks) == 2 and all(len(c) == 2 for c in chunks)
