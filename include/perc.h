@@ -262,8 +262,9 @@ int perc_pmax(const uint32_t *smax, const uint32_t *group, uint32_t num_samples,
  *   call allocates nothing.  The first call on a device looks the array's address up and should
  *   come before any stream capture.  Calls share the array: calls that may overlap on the GPU race
  *   and must be serialised by the caller.  The launch uses as many CTAs as slots of its size fit
- *   in the array (a slot is about 15 MiB at L = 16), so it is slower than perc_nstar; a max_L
- *   whose single slot does not fit (L above 20) returns PERC_EWORKSPACE.  Device-side sample
+ *   in the array (a slot is about 15 MiB at L = 16, 57 MiB at L = 23, one CTA from L = 21),
+ *   so it is slower than perc_nstar; a max_L whose single slot does not fit (L above 23) returns
+ *   PERC_EWORKSPACE.  Device-side sample
  *   errors give n* = PERC_NEVER; the status word is not exposed.
  */
 int perc_nstar_noalloc(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
@@ -284,6 +285,13 @@ int perc_nstar_noalloc(const perc_sample *samples, uint32_t num_samples, uint32_
  *                        2..64 = that many
  *   PERC_OPT_METHOD      perc_nstar's method: 0 = automatic (the sweep, unless the bisection would
  *                        run cooperative groups), 1 = bisection, 2 = sweep
+ *   PERC_OPT_SPIN_LIMIT  polls a bounded device-side wait makes before it gives up with
+ *                        PERC_ETIMEOUT (the cooperative groups' barriers in perc_nstar, the tile
+ *                        copies of perc_rank); 0 = the default, 2^26.  A small value makes those
+ *                        waits run out on purpose, so that the timeout path can be tested: the
+ *                        kernels then return early, the call's outputs are undefined, and
+ *                        perc_check reports PERC_ETIMEOUT.  After a timeout in perc_rank each CTA
+ *                        still waits (default limit) for the tile copies it has in flight.
  * Returns PERC_EINVAL for an unknown option or value.  Environment variables PERC_GROUP and
  * PERC_METHOD override PERC_OPT_GROUP and PERC_OPT_METHOD.
  */
@@ -292,6 +300,7 @@ int perc_nstar_noalloc(const perc_sample *samples, uint32_t num_samples, uint32_
 #define PERC_OPT_MAX_CTAS 3
 #define PERC_OPT_GROUP 4
 #define PERC_OPT_METHOD 5
+#define PERC_OPT_SPIN_LIMIT 6
 int perc_set_launch_option(int option, int value);
 
 /*

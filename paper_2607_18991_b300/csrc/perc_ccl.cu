@@ -850,10 +850,10 @@ k_nstar(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, u
 // whose bitmap lives in global memory and batches too small to give every SM a sample of its own
 // (e.g. L = 40).  The group's union-find, undo log and bitmap are in its global slot; the CTAs
 // split the bitmap update, the chunks of new sites and the commit, and meet at group barriers.
-// Every wait is bounded: a barrier that is not reached within ~kSpinLimit polls sets
-// PERC_ETIMEOUT and an abort flag, and every CTA of the group returns.
+// Every wait is bounded: a barrier that is not reached within `spin_limit` polls (kSpinLimit unless
+// PERC_OPT_SPIN_LIMIT sets another) sets PERC_ETIMEOUT and an abort flag, and every CTA of the
+// group returns.
 // ------------------------------------------------------------------------------------------------
-constexpr uint32_t kSpinLimit = 1u << 26;
 
 struct GroupState {  // at the start of a group's slot (256 bytes)
     uint32_t bar_count, bar_gen, abort, sample;
@@ -862,7 +862,8 @@ struct GroupState {  // at the start of a group's slot (256 bytes)
 static_assert(sizeof(GroupState) == 256, "group state is 256 bytes");
 
 // Returns false if the group aborted (a wait ran out); all threads of the CTA agree.
-__device__ __forceinline__ bool group_sync(GroupState *gs, uint32_t members, int *status, uint32_t *ok_s)
+__device__ __forceinline__ bool group_sync(GroupState *gs, uint32_t members, int *status, uint32_t *ok_s,
+                                           uint32_t spin_limit)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -880,7 +881,7 @@ __device__ __forceinline__ bool group_sync(GroupState *gs, uint32_t members, int
                     ok = 0u;
                     break;
                 }
-                if (++it > kSpinLimit) {
+                if (++it >= spin_limit) {
                     set_status(status, PERC_ETIMEOUT);
                     atomicExch(&gs->abort, 1u);
                     ok = 0u;
@@ -905,7 +906,8 @@ __host__ __device__ inline size_t group_slot_bytes(uint64_t Ncap, uint32_t threa
 __global__ void __launch_bounds__(1024, 1)
 k_nstar_group(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t members,
               uint32_t edge_scap, const uint32_t *__restrict__ bracket, uint32_t *__restrict__ nstar_out,
-              uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes)
+              uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes,
+              uint32_t spin_limit)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     // shared memory: [row table][plane table (unused)][edge list]
@@ -942,10 +944,10 @@ k_nstar_group(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
             c.cyc_link = 0;
             if (leader) atomicExch(&gs->sample, atomicAdd(&hdr->queue, 1u));
         }
-        if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;
+        if (!(alive = group_sync(gs, members, &hdr->status, &ok_s, spin_limit))) break;
         const long long t_setup = clock64();
         const uint32_t s = __ldcg(&gs->sample);
-        if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;  // all have read it
+        if (!(alive = group_sync(gs, members, &hdr->status, &ok_s, spin_limit))) break;  // all have read it
         if (s >= num) break;
         const perc_sample smp = samples[s];
         const uint32_t L = smp.L, mask = smp.zone_mask & kZoneBits, axis = smp.zone_mask >> kAxisShift;
@@ -967,7 +969,7 @@ k_nstar_group(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
         }
         if (threadIdx.x == 0) c.axis = axis;  // every member CTA's own copy
         const FastDiv fd = make_fastdiv(L);
-        if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;
+        if (!(alive = group_sync(gs, members, &hdr->status, &ok_s, spin_limit))) break;
         clk.setup += clock64() - t_setup;
 
         const uint32_t n_top = (L <= 2u) ? N + 1u : N;
@@ -1005,7 +1007,7 @@ k_nstar_group(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
                     atomicExch(&gs->logn, 0u);
                 }
             }
-            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;
+            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s, spin_limit))) break;
             const long long t0 = clock64();
             // bitmap of the first mid sites and fresh nodes for the new ones, split over the group
             if (mid > bm_n) {
@@ -1020,21 +1022,21 @@ k_nstar_group(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
                 }
             }
             for (uint32_t r = nb + gtid; r < mid; r += gthreads) nd_st(P, r + 2u, r + 2u);
-            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;
+            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s, spin_limit))) break;
             const long long t1 = clock64();
             union_pass<false, true, false, true>(c, P, logb, bm, rows, nullptr, E, smp.perm, smp.rank, L, fd, nb, mid,
                                                  nb + 2u, &gs->stop, &gs->logn, member, members);
-            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;
+            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s, spin_limit))) break;
             const long long t2 = clock64();
             const uint32_t span = nd_ld(P, 1u) != 1u;
             const uint32_t logn = __ldcg(&gs->logn);
             const bool stopped = __ldcg(&gs->stop) != 0u;
-            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;  // all have read span
+            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s, spin_limit))) break;  // all have read span
             for (uint32_t k = gtid; k < logn; k += gthreads) {
                 const uint32_t b = __ldcg(logb + k);
                 nd_st(P, b, span ? b : (nd_ld(P, b) & ~kTag));
             }
-            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s))) break;
+            if (!(alive = group_sync(gs, members, &hdr->status, &ok_s, spin_limit))) break;
             clk.update += t1 - t0;
             clk.unite += t2 - t1;
             clk.commit += clock64() - t2;
@@ -1968,17 +1970,56 @@ static int env_int(const char *name, int dflt)
     return v ? atoi(v) : dflt;
 }
 
+constexpr int kCfgDevices = 64;
+static std::mutex g_attr_mutex;
+static size_t g_attr_bytes[kAttrSlots][kCfgDevices];
+static uint32_t g_attr_ctas[kAttrSlots][kCfgDevices];
+
+int ensure_smem_attr(AttrSlot slot, const void *fn, size_t bytes)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kCfgDevices) return PERC_ECUDA;
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (g_attr_bytes[slot][dev] >= bytes) return PERC_OK;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) != cudaSuccess)
+        return PERC_ECUDA;
+    g_attr_bytes[slot][dev] = bytes;
+    return PERC_OK;
+}
+
+int resident_ctas(AttrSlot slot, const void *fn, int threads, size_t smem, uint32_t &ctas)
+{
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kCfgDevices) return PERC_ECUDA;
+    {
+        std::lock_guard<std::mutex> lock(g_attr_mutex);
+        if (g_attr_ctas[slot][dev]) {
+            ctas = g_attr_ctas[slot][dev];
+            return PERC_OK;
+        }
+    }
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess)
+        return PERC_ECUDA;
+    ctas = static_cast<uint32_t>(sms * (occ > 0 ? occ : 1));
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    g_attr_ctas[slot][dev] = ctas;
+    return PERC_OK;
+}
+
 struct CfgCache {
     int threads = 0, occ = 0;
     size_t smem = 0, attr_smem = 0;
     bool valid = false;
 };
-constexpr int kCfgDevices = 64;
 static CfgCache g_cfg_cache[4][kCfgDevices];
 static std::mutex g_cfg_mutex;
 
 // Launch options set through perc_set_launch_option (0 = automatic).
 static int g_opt_threads = 0, g_opt_smem_nodes = -1, g_opt_max_ctas = 0, g_opt_group = 0, g_opt_method = 0;
+static uint32_t g_opt_spin_limit = 0;  // polls of a bounded device wait; 0 = kSpinLimit
+
+uint32_t spin_limit() { return g_opt_spin_limit ? g_opt_spin_limit : kSpinLimit; }
 constexpr int kOpSweep = 100;  // launch configuration of k_nstar_sweep (perc_nstar, sweep method)
 static CfgCache g_group_cache[kCfgDevices];
 
@@ -2187,7 +2228,7 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
         lc.numAttrs = 1;
         const cudaError_t e = cudaLaunchKernelEx(&lc, k_nstar_group, samples, num_samples, max_L, cfg.members,
                                                  cfg.edge_scap, bracket, nstar, passes, stats,
-                                                 static_cast<char *>(workspace), cfg.slot_bytes);
+                                                 static_cast<char *>(workspace), cfg.slot_bytes, spin_limit());
         return e == cudaSuccess ? PERC_OK : PERC_ECUDA;
     }
     k_nstar<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap, cfg.edge_scap, bracket,
@@ -2276,6 +2317,10 @@ extern "C" int perc_set_launch_option(int option, int value)
     case PERC_OPT_METHOD:
         if (value < 0 || value > 2) return PERC_EINVAL;
         g_opt_method = value;
+        return PERC_OK;
+    case PERC_OPT_SPIN_LIMIT:
+        if (value < 0) return PERC_EINVAL;
+        g_opt_spin_limit = static_cast<uint32_t>(value);
         return PERC_OK;
     default:
         return PERC_EINVAL;

@@ -172,6 +172,21 @@ __host__ __device__ inline uint64_t num_sites(uint32_t L)
     return l * l * l * l * l;
 }
 
+// Polls a bounded device-side wait makes before it gives up with PERC_ETIMEOUT: kSpinLimit, or
+// the value of PERC_OPT_SPIN_LIMIT (defined in perc_ccl.cu).  A wait that drains copies still in
+// flight after a timeout always uses kSpinLimit.
+constexpr uint32_t kSpinLimit = 1u << 26;
+uint32_t spin_limit();
+
+// Host-side per-device launch state (defined in perc_ccl.cu; thread-safe).  Kernel attributes such
+// as the dynamic shared-memory limit are set per device, so each is set once on every device that
+// launches the kernel.  Returns PERC_OK or PERC_ECUDA.
+enum AttrSlot { kAttrMlpGrad, kAttrRankScatter, kAttrRankScatterTma, kAttrTorusMass, kAttrTorusWrap, kAttrSlots };
+int ensure_smem_attr(AttrSlot slot, const void *fn, size_t bytes);
+// Resident CTAs of `fn` (threads, dynamic shared memory) times the SM count of the current device,
+// cached per (slot, device).
+int resident_ctas(AttrSlot slot, const void *fn, int threads, size_t smem, uint32_t &ctas);
+
 // Workspace of perc_rank for num_seeds seeds of side L (defined in perc_rank.cu).
 size_t rank_workspace_bytes(uint32_t L, uint32_t num_seeds);
 // Workspace of the periodic-boundary calls (defined in perc_periodic.cu); 0 when not configurable.

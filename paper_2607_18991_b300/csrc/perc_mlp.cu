@@ -220,13 +220,9 @@ static size_t grad_smem_bytes()
 static int launch_grad(const float *params, const float *X, const float *y, uint32_t B, float *grad,
                        float *loss, cudaStream_t stream)
 {
-    static bool attr_set = false;
     const size_t smem = grad_smem_bytes();
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
-            return PERC_ECUDA;
-        attr_set = true;
-    }
+    if (ensure_smem_attr(kAttrMlpGrad, reinterpret_cast<const void *>(k_mlp_grad), smem) != PERC_OK)
+        return PERC_ECUDA;  // (set once per device)
     if (cudaMemsetAsync(grad, 0, sizeof(float) * kNParam, stream) != cudaSuccess) return PERC_ECUDA;
     if (loss && cudaMemsetAsync(loss, 0, sizeof(float), stream) != cudaSuccess) return PERC_ECUDA;
     k_mlp_grad<<<(B + kRows - 1) / kRows, kRows, smem, stream>>>(params, X, y, B, grad, loss);

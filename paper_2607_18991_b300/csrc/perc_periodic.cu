@@ -313,12 +313,10 @@ int torus_launch(const perc_sample *samples, uint32_t num, uint32_t max_L, const
     const int rc = torus_cfg(max_L, num, grid, slot, smem);
     if (rc != PERC_OK) return rc;
     if (ws_bytes < sizeof(PerHeader) + size_t(grid) * slot) return PERC_EWORKSPACE;
-    static size_t attr_smem = 0;  // largest dynamic shared memory this instance was allowed so far
-    if (smem > attr_smem) {
-        if (cudaFuncSetAttribute(k_torus<kWrap>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
-            return PERC_ECUDA;
-        attr_smem = smem;
-    }
+    // the dynamic shared-memory limit is per device: raised once per device to the largest asked for
+    if (smem && ensure_smem_attr(kWrap ? kAttrTorusWrap : kAttrTorusMass, reinterpret_cast<const void *>(k_torus<kWrap>),
+                                 smem) != PERC_OK)
+        return PERC_ECUDA;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(PerHeader), stream) != cudaSuccess) return PERC_ECUDA;
     const uint32_t smem_L = smem ? max_L : 0u;

@@ -269,10 +269,11 @@ k_rank_scatter(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ se
 // mbarrier) already brings the next tile's keys and values into the other shared buffer.  The
 // buffer just ranked also serves as the staging area of the digit-ordered tile.  Needs 16-byte
 // aligned rows (L^5 a multiple of 4); otherwise k_rank_scatter is used.  Waits are bounded: a copy
-// that does not land within kTmaSpinLimit polls sets PERC_ETIMEOUT in the workspace status word
-// and the CTA stops.
+// that does not land within `spin_limit` polls (kSpinLimit unless PERC_OPT_SPIN_LIMIT sets another)
+// sets PERC_ETIMEOUT in the workspace status word and the CTA stops, after waiting (up to
+// kSpinLimit polls each) for the copies it still has in flight, so that none of them lands in
+// shared memory a later CTA owns.  The launch's outputs are then undefined.
 // ------------------------------------------------------------------------------------------------
-constexpr uint32_t kTmaSpinLimit = 1u << 26;
 
 struct TmaScatterSmem {
     uint32_t key[2][kRankTile];
@@ -304,9 +305,9 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, uint32_t limit)
 {
-    for (uint32_t it = 0; it < kTmaSpinLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -321,7 +322,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
 __global__ void __launch_bounds__(kRankThreads, 2)
 k_rank_scatter_tma(int pass, uint32_t N, uint32_t T, uint32_t S, const uint32_t *__restrict__ kin,
                    const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                   uint32_t *__restrict__ rank_out, const uint32_t *__restrict__ hist, int *status)
+                   uint32_t *__restrict__ rank_out, const uint32_t *__restrict__ hist, int *status,
+                   uint32_t spin_limit)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TmaScatterSmem &S_ = *reinterpret_cast<TmaScatterSmem *>(smem_raw);
@@ -361,18 +363,24 @@ k_rank_scatter_tma(int pass, uint32_t N, uint32_t T, uint32_t S, const uint32_t 
         // the other buffer was released by the barrier that ended the previous iteration
         const bool next = w + gridDim.x < total;
         if (threadIdx.x == 0 && next) issue(w + gridDim.x, b ^ 1);
-        if (!mbar_wait(&S_.bar[b], use[b] & 1u)) {
+        if (!mbar_wait(&S_.bar[b], use[b] & 1u, spin_limit)) {
             set_status(status, PERC_ETIMEOUT);
             S_.stop = 1u;
         }
-        ++use[b];
         __syncthreads();
         if (S_.stop) {
-            // let the copy already issued into the other buffer land before the CTA goes away
-            if (threadIdx.x == 0 && next) mbar_wait(&S_.bar[b ^ 1], use[b ^ 1] & 1u);
+            // drain: the copy into this buffer (whose wait gave up) and the one already issued into
+            // the other must land before the CTA goes away.  If a drain wait runs out as well, the
+            // status word keeps PERC_ETIMEOUT (the first error) and the launch's results are void.
+            if (threadIdx.x == 0) {
+                bool ok = mbar_wait(&S_.bar[b], use[b] & 1u, kSpinLimit);
+                if (next) ok = mbar_wait(&S_.bar[b ^ 1], use[b ^ 1] & 1u, kSpinLimit) && ok;
+                if (!ok) set_status(status, PERC_ETIMEOUT);
+            }
             __syncthreads();
             break;
         }
+        ++use[b];
         uint32_t key[kRankItems], val[kRankItems], pos[kRankItems], dig[kRankItems];
 #pragma unroll
         for (int k = 0; k < kRankItems; ++k) {
@@ -479,24 +487,15 @@ extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, 
     uint32_t *hist = reinterpret_cast<uint32_t *>((reinterpret_cast<uintptr_t>(a_vals + size_t(chunk) * N) + 15) &
                                                   ~uintptr_t(15));
 
-    static bool attr_set = false;
-    static uint32_t tma_ctas = 0;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(k_rank_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(sizeof(ScatterSmem))) != cudaSuccess)
-            return PERC_ECUDA;
-        if (cudaFuncSetAttribute(k_rank_scatter_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(sizeof(TmaScatterSmem))) != cudaSuccess)
-            return PERC_ECUDA;
-        int dev = 0, sms = 0, occ = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rank_scatter_tma, kRankThreads,
-                                                          sizeof(TmaScatterSmem)) != cudaSuccess)
-            return PERC_ECUDA;
-        tma_ctas = static_cast<uint32_t>(sms * (occ > 0 ? occ : 1));
-        attr_set = true;
-    }
+    // attributes and the resident CTA count are per device (set and cached once per device)
+    uint32_t tma_ctas = 0;
+    if (ensure_smem_attr(kAttrRankScatter, reinterpret_cast<const void *>(k_rank_scatter), sizeof(ScatterSmem)) !=
+            PERC_OK ||
+        ensure_smem_attr(kAttrRankScatterTma, reinterpret_cast<const void *>(k_rank_scatter_tma),
+                         sizeof(TmaScatterSmem)) != PERC_OK ||
+        resident_ctas(kAttrRankScatterTma, reinterpret_cast<const void *>(k_rank_scatter_tma), kRankThreads,
+                      sizeof(TmaScatterSmem), tma_ctas) != PERC_OK)
+        return PERC_ECUDA;
     // bulk-async tile loads need 16-byte aligned rows; the status word is the workspace header
     const bool use_tma = (N % 4u) == 0u && env_int_rank("PERC_RANK_TMA", 1) != 0;
     int *status = static_cast<int *>(workspace);
@@ -519,7 +518,7 @@ extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, 
                 const uint32_t work = T * S;
                 const uint32_t g = work < tma_ctas ? work : tma_ctas;
                 k_rank_scatter_tma<<<g, kRankThreads, sizeof(TmaScatterSmem), stream>>>(
-                    pass, uint32_t(N), T, S, kin, vin, kout, vout, b_keys, hist, status);
+                    pass, uint32_t(N), T, S, kin, vin, kout, vout, b_keys, hist, status, spin_limit());
             } else {
                 k_rank_scatter<<<grid, kRankThreads, sizeof(ScatterSmem), stream>>>(pass, uint32_t(N), T, sd, kin, vin,
                                                                                     kout, vout, b_keys, hist);

@@ -20,7 +20,7 @@ MAX_L = 73
 OP_RANK, OP_NSTAR, OP_MASS, OP_SMAX, OP_PERIODIC = 1, 2, 3, 4, 5
 PERIODIC_MAX_L = 40
 AXIS_SHIFT, NUM_AXES = 8, 5  # zone word: spanning axis in bits 8..10; axes x1..x5
-OPT_THREADS, OPT_SMEM_NODES, OPT_MAX_CTAS, OPT_GROUP, OPT_METHOD = 1, 2, 3, 4, 5
+OPT_THREADS, OPT_SMEM_NODES, OPT_MAX_CTAS, OPT_GROUP, OPT_METHOD, OPT_SPIN_LIMIT = 1, 2, 3, 4, 5, 6
 METHOD_AUTO, METHOD_BISECTION, METHOD_SWEEP = 0, 1, 2
 MLP_NPARAM = 4931
 STATS_FIELDS = ("passes", "new_sites", "probe_sites", "hooks", "early_exits", "fallbacks",

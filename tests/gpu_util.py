@@ -1,5 +1,7 @@
 """Helpers for the GPU parity tests: oracle answers for workloads (CPU) and caching."""
 import functools
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -51,3 +53,29 @@ def orc_periodic(workload, n=None):
         if n is not None:
             sm[k] = b[0]
     return nw, sm
+
+
+def _orc_group(L: int, seed: int, masks):
+    perm, rk = oracle.rank(L, seed)
+    return [oracle.nz(L, int(m), perm, rk)[0] for m in masks]
+
+
+def orc_nstar_threads(workload, threads: int | None = None) -> np.ndarray:
+    """Oracle n* for rows (L, mask, seed), one ranking per distinct (L, seed), the groups spread over
+    host threads (the oracle's C calls release the interpreter lock).  Nothing is cached, so large
+    lattices hold their site orders only while their group runs."""
+    workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
+    oracle.lib()  # load the library once before the threads start
+    groups = {}
+    for k, (L, m, s) in enumerate(workload.tolist()):
+        groups.setdefault((L, s), []).append((k, m))
+    # the largest lattices first, so the longest groups start early
+    keys = sorted(groups, key=lambda g: -g[0])
+    threads = threads or max(1, min(8, os.cpu_count() or 1))
+    out = np.zeros(len(workload), dtype=np.uint32)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        futs = {g: ex.submit(_orc_group, g[0], g[1], [m for _, m in groups[g]]) for g in keys}
+        for g, f in futs.items():
+            for (k, _), v in zip(groups[g], f.result()):
+                out[k] = v
+    return out

@@ -1,12 +1,14 @@
 """Parity on the other workloads: compact-neighborhood masses, L = 24 with the learned bracket,
-L = 40, the mixed-L batch, the full L = 16 benchmark launch (sampled), and lattices of 254.8M and
-1.07G sites (L = 48, 64) against n* the oracle stored in tests/golden/nstar_large.txt."""
+L = 40 (plain and learned bracket), the whole mixed-L batch of 4096 samples (sampled across
+L = 10..40), the full L = 16 benchmark launch (every 16th seed), and lattices of 254.8M and 1.07G
+sites (L = 48, 64) against n* the oracle stored in tests/golden/nstar_large.txt."""
+import functools
 import os
 
 import numpy as np
 import pytest
 
-from gpu_util import orc_mass, orc_nstar
+from gpu_util import orc_mass, orc_nstar, orc_nstar_threads
 
 pytestmark = pytest.mark.gpu
 
@@ -15,6 +17,7 @@ PC_COMPACT = {1: 0.14079633, 3: 0.033794, 7: 0.013190, 15: 0.007850, 31: 0.00515
               127: 0.001934}
 
 
+@functools.lru_cache(maxsize=1)
 def quick_params():
     from paper_2607_18991_b300 import bracket, driver
     wl = np.concatenate([np.array([(8, 1, s) for s in range(500001, 500201)]),
@@ -50,20 +53,52 @@ def test_L24_learned_and_plain():
 
 
 def test_L40_all_zones():
+    """Zones 1-7 at L = 40 (102.4M sites), plain and learned bracket.  The network is trained at
+    L = 8 and 16 only, so at L = 40 its bracket is wide (or fails verification and falls back)."""
     from paper_2607_18991_b300 import driver, workloads
     w = workloads.z892_L40(1)
+    want = orc_nstar(w)
     ns, passes = driver.nstar(w)
-    assert np.array_equal(ns, orc_nstar(w))
+    assert np.array_equal(ns, want)
     assert passes[0] in (26, 27)  # floor / ceil of log2(40^5)
+    ns_l, _ = driver.nstar(w, params=quick_params(), margin=0.05)
+    assert np.array_equal(ns_l, want)
+
+
+def mixed_rows(w, per_band=((10, 20, 16), (21, 30, 12), (31, 40, 6)), seed=7):
+    """Rows of the mixed batch drawn across its whole range of L: `count` rows from each band
+    [lo, hi] of sides (a fixed draw), so every kernel path of the batch meets the oracle."""
+    rng = np.random.default_rng(seed)
+    pick = []
+    for lo, hi, count in per_band:
+        band = np.nonzero((w[:, 0] >= lo) & (w[:, 0] <= hi))[0]
+        pick.extend(rng.choice(band, size=count, replace=False).tolist())
+    return np.array(sorted(pick))
 
 
 def test_mixed_batch_sampled():
+    """The whole mixed batch (4096 samples, L uniform in 10..40, random masks) in the launches the
+    benchmark runs, with the learned bracket; 34 rows drawn across L = 10..40 (6 above L = 30) are
+    compared with the oracle."""
     from paper_2607_18991_b300 import driver, workloads
     w = workloads.mixed4096()
-    pick = np.nonzero(w[:, 0] <= 20)[0][:48]
-    sub = w[pick]
-    ns, _ = driver.nstar(sub, params=quick_params(), margin=0.05)
-    assert np.array_equal(ns, orc_nstar(sub))
+    pick = mixed_rows(w)
+    assert (w[pick, 0] > 30).sum() >= 4 and w[pick, 0].min() <= 12
+    want = orc_nstar_threads(w[pick])
+    ns, _ = driver.nstar(w, params=quick_params(), margin=0.05)
+    assert np.array_equal(ns[pick], want)
+
+
+FULL_SIZE_SEEDS = list(range(1, 257, 16))  # every 16th seed of 1..256
+
+
+_full_size_cache = {}
+
+
+def full_size_want(key, rows):
+    if key not in _full_size_cache:
+        _full_size_cache[key] = orc_nstar_threads(rows)
+    return _full_size_cache[key]
 
 
 @pytest.mark.parametrize("method", ["bisection", "sweep"])
@@ -80,8 +115,9 @@ def test_full_size_L16_launch_sampled(method):
         ns, passes = step.result()
     finally:
         perc.set_launch_option(perc.OPT_METHOD, perc.METHOD_AUTO)
-    sel = np.nonzero(np.isin(step.workload[:, 2], [1, 128, 256]))[0]
-    assert np.array_equal(ns[sel], orc_nstar(step.workload[sel]))
+    sel = np.nonzero(np.isin(step.workload[:, 2], FULL_SIZE_SEEDS))[0]
+    assert len(sel) == 16 * 127
+    assert np.array_equal(ns[sel], full_size_want(tuple(sel.tolist()), step.workload[sel]))
     if method == "bisection":
         assert passes.max() <= 2 * 20 + 1  # a fallback costs one failed check plus the plain bisection
 

@@ -4,10 +4,13 @@ Such callers (for example code that runs inside a framework which owns every dev
 or that has to stay within a memory budget fixed in advance) cannot hand the library a workspace.
 perc_nstar_noalloc uses a fixed array that the library itself keeps in device memory instead.  These
 tests call it through the C ABI and check that two calls in a row return exactly what perc_nstar
-returns on the same samples; this file is named so that pytest collects it last.
+returns on the same samples and what the oracle's Newman--Ziff sweep gives; this file is named so
+that pytest collects it last.
 """
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -42,12 +45,24 @@ def test_noalloc_matches_workspace_entry_point_twice(L, masks, seeds):
         ns_b, _ = perc.nstar_noalloc(smp, L, bracket=exact)
         assert np.array_equal(perc.u32(ns_b), want_ns)
     assert np.all(want_ns <= N)
+    orc = [oracle.nz(L, m, *oracle.rank(L, s))[0] for s in seeds for m in masks]
+    assert np.array_equal(want_ns, np.array(orc, dtype=np.uint32))
     torch.cuda.synchronize()
+
+
+def test_noalloc_largest_lattice_that_fits():
+    """L = 23 is the largest side whose one CTA slot (about 57 MiB) fits in the 64 MiB scratch."""
+    from paper_2607_18991_b300 import perc
+    smp, keep = _samples(23, [127], [1])
+    for _ in range(2):
+        ns, _ = perc.nstar_noalloc(smp, 23)
+        assert perc.u32(ns)[0] == oracle.nz(23, 127, *oracle.rank(23, 1))[0]
 
 
 def test_noalloc_rejects_lattices_beyond_its_scratch():
     from paper_2607_18991_b300 import perc
     smp, keep = _samples(4, [1], [1])
-    with pytest.raises(perc.PercError) as err:
-        perc.nstar_noalloc(smp, 40)  # one CTA slot for L = 40 is far larger than 64 MiB
-    assert err.value.rc == -2
+    for max_L in (24, 40):  # one CTA slot: about 69 MiB at L = 24, far more at L = 40
+        with pytest.raises(perc.PercError) as err:
+            perc.nstar_noalloc(smp, max_L)
+        assert err.value.rc == -2
