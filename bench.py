@@ -55,6 +55,13 @@ PMAX_METRIC = ("samples/sec of P_max(p) curves (exact S_max(n) over the windows 
                "each binomial, convolution at 16 p per neighborhood) at L=16 over 127 neighborhoods")
 
 
+def rank_launches(L: int, num_seeds: int) -> int:
+    """Kernels perc_rank launches: per chunk of up to 64 seeds, the bucket path's count, scan, place
+    and sort (L^5 <= 8,388,608) or the radix path's four histogram, scan and scatter passes."""
+    per_chunk = 4 if L ** 5 <= 8_388_608 else 12
+    return math.ceil(num_seeds / 64) * per_chunk
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -454,7 +461,7 @@ def run_ours(args):
                          + (", one any-axis sweep (ten border flags) per sample" if axes > 1 else "")}
 
     # rank passes + bracket + nstar (+ the minimum over axes) per step
-    gpu_launches = (math.ceil(len(seeds) / 64) * 13) + 2 + (1 if axes > 1 else 0)
+    gpu_launches = rank_launches(L, len(seeds)) + 2 + (1 if axes > 1 else 0)
     value = world * num / (ms_learned * 1e-3)
     if rank == 0:
         line = {
@@ -681,7 +688,7 @@ def run_pmax_ours(args):
                "sample": f"L=16, seeds 1..{n_seeds_cpu} x 127 masks ({done} samples, 16 p each) in {dt:.1f} s, "
                          f"one ranking per seed, {cpu_workers} spawned workers"}
 
-    gpu_launches = (math.ceil(len(seeds) / 64) * 13) + 3  # rank passes + weights + S_max + P_max
+    gpu_launches = rank_launches(L, len(seeds)) + 3  # rank + weights + S_max + P_max
     value = world * num / (ms_step * 1e-3)
     if rank == 0:
         line = {
@@ -837,7 +844,7 @@ def run_wrap_ours(args):
             "roofline": None,
             "cpu_baseline": cpu,
             "clocks": clocks,
-            "gpu_launches": (math.ceil(len(seeds) / 64) * 13) + 1,
+            "gpu_launches": rank_launches(L, len(seeds)) + 1,
         }
         print(json.dumps(line))
     if world > 1:

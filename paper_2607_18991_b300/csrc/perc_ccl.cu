@@ -38,8 +38,11 @@ namespace perc {
 
 constexpr uint32_t kTag = 0x80000000u;
 constexpr uint32_t kSmemBitmapMaxL = 17;
+constexpr uint32_t kSumMixL = 32;             // above this side a batch's region is that of side 16
+constexpr size_t kSumReserve = size_t(16) << 10;  // shared memory kept for nodes and edges
 constexpr size_t kSmemNodes = 16384;  // most union-find nodes a CTA keeps in shared memory
-constexpr size_t kSlotCapBytes = size_t(32) << 30;  // total per-CTA slot memory aimed at
+// Total per-CTA slot memory a launch aims at: a quarter of the device's memory (68 GiB on a B300).
+constexpr uint32_t kSlotCapShare = 4;
 
 __constant__ ZoneTable c_zones = kZones;
 
@@ -64,6 +67,8 @@ struct Ctl {
     uint32_t NP;      // plane entries (L = 16 path)
     uint32_t Rhalf;   // row entries up to the centre row (d1..d4 = 0), which come first
     uint32_t NPhalf;  // plane entries up to the centre plane (d1..d3 = 0)
+    uint32_t G;       // summary-group entries of the sample's neighborhood
+    uint32_t Ghalf;   // summary-table entries up to the centre entry
     uint32_t axis;    // spanning axis of the sample: its borders are x_{axis+1} = 0 and = L-1
     uint32_t ecount[2];  // edge-list fill of the current and the next chunk
     unsigned long long hooks, new_sites, sites, unions, cyc_scan, cyc_link;
@@ -384,11 +389,125 @@ __device__ uint32_t build_planes16(const RowEntry *rows, uint32_t R, PlaneEntry 
     return c.NP;
 }
 
+// ------------------------------------------------------------------------------------------------
+// How a site's neighborhood is scanned (template parameter of the passes):
+//   kScanRows    one funnel-shifted bitmap window per (d1..d4) row entry (any L);
+//   kScanPlanes  L = 16: one 80-bit bitmap block per (d1, d2, d3) plane entry;
+//   kScanGroups  with the occupancy summary in shared memory: per (d1, d2, d3) group entry one
+//                5-bit summary window names the rows (d4) that may hold a neighbor, and only those
+//                rows are read from the bitmap (any L);
+//   kScanGroupsG the same with the summary in the CTA's global slot (lattices whose summary does
+//                not fit in shared memory).
+// The summary has one bit per lattice row (the L sites sharing x1..x4): bit kSumGuard + r is set
+// once a site of row r = i / L is occupied.  It only ever gains bits, so the passes that use it are
+// those whose occupancy only grows (the sweep, S_max windows, the mass pass).  It serves lattices
+// whose bitmap lives in global memory (L above 17): near the threshold the occupancy is sparse
+// (p_c z is of order one), so most summary windows are empty, and a site's scan reads 81 summary
+// windows on chip instead of 297 bitmap rows through L2 (all seven zones).  While the whole bitmap
+// sits in shared memory the row and plane tests are cheaper than the summary's data-dependent
+// candidate loop, whose trip count differs from lane to lane.
+// ------------------------------------------------------------------------------------------------
+enum ScanMode : int { kScanRows = 0, kScanPlanes = 1, kScanGroups = 2, kScanGroupsG = 3 };
+__host__ __device__ constexpr bool uses_sum(int m) { return m >= kScanGroups; }
+
+constexpr uint32_t kSumGuard = 64;  // zero bits before the summary's row 0 (and 128 after the last row)
+__host__ __device__ inline uint32_t sum_words(uint32_t L)
+{
+    const uint64_t rows = uint64_t(L) * L * L * L;
+    return static_cast<uint32_t>((rows + kSumGuard + 128) / 32 + 1);
+}
+__host__ __device__ inline size_t sum_bytes(uint32_t L) { return (size_t(sum_words(L)) * 4 + 15) & ~size_t(15); }
+
+// Group entry (kScanGroups): one (d1, d2, d3) triple of the neighborhood.
+struct __align__(16) GroupEntry {
+    int32_t rdelta;  // row offset of (d1, d2, d3, d4 = -2): ((d1*L + d2)*L + d3)*L - 2
+    uint32_t oh;     // one-hot of d1, d2, d3: bit 5k + d_k + 2, k = 0..2
+    uint32_t cm;     // bit d4 + 2 for every d4 whose row (d1..d4) is in the neighborhood
+    uint32_t code;   // base-5 code of (d1, d2, d3, d4 = -2): index of its row in the d5 table
+};
+
+constexpr uint32_t kGroupCentre = 62;  // code of (0, 0, 0)
+constexpr size_t kSumTabBytes = sizeof(GroupEntry) * 125;
+constexpr size_t kD5Bytes = 640;                            // d5 masks of the 625 (d1..d4) rows
+
+// Tables of the summary scan, pointers into shared memory (the summary may be global).
+struct ScanTabs {
+    const RowEntry *rows;
+    const PlaneEntry *planes;
+    const GroupEntry *tab;
+    const uint8_t *d5m;    // d5 mask (bit d5 + 2) of every (d1..d4) row, by base-5 code
+    uint32_t *sum;         // occupancy summary
+};
+
+// Builds the summary tables of `mask` for side L (all threads; ends with a barrier): the d5 mask of
+// every (d1..d4) row, and the group entries in ascending code, those up to the centre entry first.
+// scratch holds kRowCand words.
+__device__ void build_sum_tabs(uint32_t mask, uint32_t L, GroupEntry *tab, uint8_t *d5m, uint32_t *scratch, Ctl &c)
+{
+    for (uint32_t t = threadIdx.x; t < kRowCand; t += blockDim.x) scratch[t] = 0u;
+    __syncthreads();
+    uint32_t z = 0;
+    for (int zone = 0; zone < kZoneCount; ++zone)
+        if (mask & (1u << zone)) z += c_zones.start[zone + 1] - c_zones.start[zone];
+    for (uint32_t v = threadIdx.x; v < z; v += blockDim.x) {
+        uint32_t k = v, packed = 0;
+        for (int zone = 0; zone < kZoneCount; ++zone) {
+            if (!(mask & (1u << zone))) continue;
+            const uint32_t cnt = c_zones.start[zone + 1] - c_zones.start[zone];
+            if (k < cnt) {
+                packed = c_zones.vec[c_zones.start[zone] + k];
+                break;
+            }
+            k -= cnt;
+        }
+        uint32_t key = 0;
+        for (int d = 0; d < 4; ++d) key = key * 5u + static_cast<uint32_t>(zone_component(packed, d) + 2);
+        atomicOr(scratch + key, 1u << (zone_component(packed, 4) + 2));
+    }
+    __syncthreads();
+    uint8_t *d5w = d5m;
+    for (uint32_t t = threadIdx.x; t < kRowCand; t += blockDim.x) d5w[t] = static_cast<uint8_t>(scratch[t]);
+    if (threadIdx.x < 32) {
+        const uint32_t lane = threadIdx.x;
+        uint32_t count = 0, half = 0;
+        const int32_t Li = static_cast<int32_t>(L);
+        {  // one lane per (d1, d2, d3) triple
+            for (uint32_t base = 0; base < 125u; base += 32) {
+                const uint32_t key = base + lane;
+                uint32_t cm = 0;
+                if (key < 125u)
+                    for (uint32_t u = 0; u < 5; ++u) cm |= (scratch[key * 5u + u] ? 1u : 0u) << u;
+                const uint32_t bal = __ballot_sync(0xffffffffu, cm != 0u);
+                half += __popc(__ballot_sync(0xffffffffu, cm != 0u && key <= kGroupCentre));
+                if (cm) {
+                    const int32_t d1 = static_cast<int32_t>(key / 25u) - 2, d2 = static_cast<int32_t>((key / 5u) % 5u) - 2,
+                                  d3 = static_cast<int32_t>(key % 5u) - 2;
+                    GroupEntry e;
+                    e.rdelta = ((d1 * Li + d2) * Li + d3) * Li - 2;
+                    e.oh = (1u << (d1 + 2)) | (1u << (5 + d2 + 2)) | (1u << (10 + d3 + 2));
+                    e.cm = cm;
+                    e.code = key * 5u;
+                    tab[count + __popc(bal & ((1u << lane) - 1u))] = e;
+                }
+                count += __popc(bal);
+            }
+        }
+        if (lane == 0) {
+            c.G = count;
+            c.Ghalf = half;
+            c.z = z;
+        }
+    }
+    __syncthreads();
+}
+
 // Site geometry for the scan phase.
 struct SiteGeo {
     uint32_t i;        // site index
-    uint32_t allowed;  // row path: 25-bit in-lattice mask of (d1..d5); plane path: (d1..d3) part
+    uint32_t allowed;  // rows / summary paths: 25-bit in-lattice mask of (d1..d5); plane path: (d1..d3) part
     uint32_t a5;       // in-lattice d5 values
+    uint32_t a4;       // in-lattice d4 values (summary paths)
+    uint32_t r0;       // row index i / L (summary group path)
     uint32_t sm0, sm1, sm2, sh, wbase;  // plane path only
     bool low, high;    // on the low / high border of the spanning axis (x_{axis+1} = 0 / L-1)
 };
@@ -401,12 +520,13 @@ __device__ __forceinline__ bool valid_zone_word(uint32_t w)
     return (w & kZoneBits) != 0u && (w & ~(kZoneBits | (7u << kAxisShift))) == 0u && (w >> kAxisShift) < 5u;
 }
 
-template <bool kPlanes>
+template <int kMode>
 __device__ __forceinline__ SiteGeo site_geo(uint32_t i, uint32_t L, const FastDiv &fd, uint32_t axis)
 {
     SiteGeo s;
     s.i = i;
-    if (kPlanes) {  // L = 16: coordinates are 4-bit fields of the index
+    s.a4 = s.r0 = 0u;
+    if (kMode == kScanPlanes) {  // L = 16: coordinates are 4-bit fields of the index
         const uint32_t x1 = i >> 16, x2 = (i >> 12) & 15u, x3 = (i >> 8) & 15u, x4 = (i >> 4) & 15u, x5 = i & 15u;
         s.allowed = allowed_bits(x1, kPlaneL) | (allowed_bits(x2, kPlaneL) << 5) | (allowed_bits(x3, kPlaneL) << 10);
         const uint32_t a4 = allowed_bits(x4, kPlaneL);
@@ -424,6 +544,8 @@ __device__ __forceinline__ SiteGeo site_geo(uint32_t i, uint32_t L, const FastDi
         site_coords(i, fd, x);
         s.allowed = site_allowed(x, L);
         s.a5 = s.allowed >> 20;
+        s.a4 = (s.allowed >> 15) & 31u;
+        s.r0 = uses_sum(kMode) ? fdiv(i, fd) : 0u;
         s.sm0 = s.sm1 = s.sm2 = s.sh = s.wbase = 0u;
         const uint32_t xa = axis == 0u ? x[0] : axis == 1u ? x[1] : axis == 2u ? x[2] : axis == 3u ? x[3] : x[4];
         s.low = xa == 0u;
@@ -459,6 +581,46 @@ __device__ __forceinline__ uint32_t entry_hits(const SiteGeo &g, const uint32_t 
     }
 }
 
+template <int kMode>
+__device__ __forceinline__ uint32_t sum_word(const uint32_t *sum, uint32_t k)
+{
+    return kMode == kScanGroupsG ? ld_cg(sum + k) : sum[k];
+}
+
+// Bits t of a 32-bit hit mask whose neighbor index base + t lies below the site: t < lim.
+__device__ __forceinline__ uint32_t below_mask(int32_t lim)
+{
+    return lim <= 0 ? 0u : lim >= 32 ? 0xFFFFFFFFu : (1u << lim) - 1u;
+}
+
+// Summary scan of group k of a site: for every row of the group that the summary marks occupied,
+// the row's 5-bit window of the bitmap (d5 = -2..2) masked by the neighborhood's d5 values and the
+// lattice; emit(jb, h) for every non-empty one (bit t of h is the neighbor site jb + t).  kHalf keeps
+// only neighbors below the site's index.
+template <bool kSmemBm, int kMode, bool kHalf, class Emit>
+__device__ __forceinline__ void sum_entry_hits(const SiteGeo &g, const uint32_t *bm, const ScanTabs &T, uint32_t L,
+                                               uint32_t k, Emit &emit)
+{
+    {
+        const GroupEntry e = T.tab[k];
+        if ((e.oh & ~g.allowed & 0x7FFFu) != 0u) return;
+        const uint32_t sb = g.r0 + kSumGuard + static_cast<uint32_t>(e.rdelta);
+        uint32_t cand = __funnelshift_r(sum_word<kMode>(T.sum, sb >> 5), sum_word<kMode>(T.sum, (sb >> 5) + 1u), sb & 31u) &
+                        e.cm & g.a4;
+        while (cand) {
+            const uint32_t u = __ffs(cand) - 1u;
+            cand &= cand - 1u;
+            const uint32_t m5 = T.d5m[e.code + u] & g.a5;
+            const uint32_t jb = g.i + static_cast<uint32_t>(e.rdelta + static_cast<int32_t>(u)) * L - 2u;
+            const uint32_t bb = jb + kBmGuard;
+            uint32_t h =
+                __funnelshift_r(bm_word<kSmemBm>(bm, bb >> 5), bm_word<kSmemBm>(bm, (bb >> 5) + 1u), bb & 31u) & m5;
+            if (kHalf) h &= below_mask(static_cast<int32_t>(g.i - jb));
+            if (h) emit(jb, h);
+        }
+    }
+}
+
 // The early-exit flag and the undo-log length live in shared memory for a one-CTA sample and in
 // global memory (read L2-coherently) when a group of CTAs works on one sample; CTA `member` of a
 // group of `members` takes every members-th chunk of the new sites.
@@ -468,25 +630,21 @@ __device__ __forceinline__ uint32_t read_flag(const uint32_t *f)
     return kGroup ? __ldcg(f) : *reinterpret_cast<const volatile uint32_t *>(f);
 }
 
-// Bits t of a 32-bit hit mask whose neighbor index base + t lies below the site: t < lim.
-__device__ __forceinline__ uint32_t below_mask(int32_t lim)
-{
-    return lim <= 0 ? 0u : lim >= 32 ? 0xFFFFFFFFu : (1u << lim) - 1u;
-}
-
 // kHalf: the pass covers every occupied site (r0 = 0 and the bitmap holds exactly the sites of rank
 // below r1), so each edge is taken once, from its end with the larger site index: only the table
 // entries up to the centre entry are scanned, their hits are cut to neighbors below the site, and
 // every edge is merged (no rank-order rule).
-template <bool kSmemBm, bool kFaces, bool kPlanes, bool kGroup = false, bool kHalf = false>
+template <bool kSmemBm, bool kFaces, int kMode, bool kGroup = false, bool kHalf = false>
 __device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *logb, const uint32_t *bm,
-                                           const RowEntry *rows, const PlaneEntry *planes, const EdgeList &E,
+                                           const ScanTabs &T, const EdgeList &E,
                                            const uint32_t *perm, const uint32_t *rank, uint32_t L,
                                            const FastDiv &fd, uint32_t r0, uint32_t r1, uint32_t nold,
                                            uint32_t *stop_flag = nullptr, uint32_t *logn = nullptr,
                                            uint32_t member = 0, uint32_t members = 1)
 {
-    const uint32_t R = kHalf ? (kPlanes ? c.NPhalf : c.Rhalf) : (kPlanes ? c.NP : c.R);
+    constexpr bool kPlanes = kMode == kScanPlanes;
+    const uint32_t R = uses_sum(kMode) ? (kHalf ? c.Ghalf : c.G)
+                                       : kHalf ? (kPlanes ? c.NPhalf : c.Rhalf) : (kPlanes ? c.NP : c.R);
     const uint32_t gshift = lanes_shift(r1 - r0, R);
     const uint32_t gsize = 1u << gshift, gl = threadIdx.x & (gsize - 1u), grp = threadIdx.x >> gshift;
     const uint32_t chunk = blockDim.x >> gshift;
@@ -502,7 +660,7 @@ __device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *log
         // ---- scan
         const uint32_t r = base + grp;
         if (r < r1) {
-            const SiteGeo g = site_geo<kPlanes>(__ldg(perm + r), L, fd, c.axis);
+            const SiteGeo g = site_geo<kMode>(__ldg(perm + r), L, fd, c.axis);
             const uint32_t node = r + 2u;
             if (gl == 0u) {
                 ++sites;
@@ -512,9 +670,19 @@ __device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *log
                     if (g.high) edge_put(E, k, make_uint2(node, kNodeFlag | 1u));
                 }
             }
-            for (uint32_t k = gl; k < R; k += gsize) {
+            if constexpr (uses_sum(kMode)) {
+                auto emit = [&](uint32_t jb, uint32_t h) {
+                    uint32_t slot = atomicAdd(ecount, static_cast<uint32_t>(__popc(h)));
+                    while (h) {
+                        const uint32_t t = __ffs(h) - 1;
+                        h &= h - 1u;
+                        edge_put(E, slot++, make_uint2(node, jb + t));
+                    }
+                };
+                for (uint32_t k = gl; k < R; k += gsize) sum_entry_hits<kSmemBm, kMode, kHalf>(g, bm, T, L, k, emit);
+            } else for (uint32_t k = gl; k < R; k += gsize) {
                 uint32_t h[3];
-                const uint32_t jb = entry_hits<kSmemBm, kPlanes>(g, bm, rows, planes, k, h);
+                const uint32_t jb = entry_hits<kSmemBm, kPlanes>(g, bm, T.rows, T.planes, k, h);
                 if (kHalf) {  // a no-op except on the centre entry
                     const int32_t lim = static_cast<int32_t>(g.i - jb);
                     h[0] &= below_mask(lim);
@@ -592,31 +760,42 @@ __host__ __device__ inline size_t slot_edge_entries(uint32_t threads) { return s
 struct SlotPtrs {
     uint32_t *P, *logb, *gbm;
     uint2 *gedges;
+    uint32_t *gsum;  // occupancy summary of lattices whose summary does not fit in shared memory
 };
 
 __host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-__host__ __device__ inline size_t slot_bytes_for(uint64_t Ncap, bool gbm, uint32_t threads)
+// gsum_L: side whose occupancy summary the slot holds (0: none); log: the slot holds a second
+// node-sized array (the bisection's undo log, the cluster counts of S_max and the mass pass; the
+// sweep has none).
+__host__ __device__ inline size_t slot_bytes_for(uint64_t Ncap, bool gbm, uint32_t threads, uint32_t gsum_L = 0,
+                                                 bool log = true)
 {
-    return 2 * align256((Ncap + 2) * 4) + (gbm ? align256(size_t(bm_words(Ncap)) * 4) : 0) +
-           align256(slot_edge_entries(threads) * sizeof(uint2));
+    return (log ? 2 : 1) * align256((Ncap + 2) * 4) + (gbm ? align256(size_t(bm_words(Ncap)) * 4) : 0) +
+           align256(slot_edge_entries(threads) * sizeof(uint2)) + (gsum_L ? align256(sum_bytes(gsum_L)) : 0);
 }
 
-__device__ __forceinline__ SlotPtrs slot_ptrs(char *ws, size_t slot_bytes, uint64_t Ncap, bool gbm)
+__device__ __forceinline__ SlotPtrs slot_ptrs(char *ws, size_t slot_bytes, uint64_t Ncap, bool gbm, bool gsum = false,
+                                              bool log = true)
 {
     char *base = ws + sizeof(WsHeader) + size_t(blockIdx.x) * slot_bytes;
-    const size_t nodes = align256((Ncap + 2) * 4);
+    const size_t nodes = align256((Ncap + 2) * 4), arrays = (log ? 2 : 1) * nodes;
     const size_t bmb = gbm ? align256(size_t(bm_words(Ncap)) * 4) : 0;
     SlotPtrs s;
     s.P = reinterpret_cast<uint32_t *>(base);
-    s.logb = reinterpret_cast<uint32_t *>(base + nodes);
-    s.gbm = gbm ? reinterpret_cast<uint32_t *>(base + 2 * nodes) : nullptr;
-    s.gedges = reinterpret_cast<uint2 *>(base + 2 * nodes + bmb);
+    s.logb = log ? reinterpret_cast<uint32_t *>(base + nodes) : nullptr;
+    s.gbm = gbm ? reinterpret_cast<uint32_t *>(base + arrays) : nullptr;
+    s.gedges = reinterpret_cast<uint2 *>(base + arrays + bmb);
+    s.gsum = gsum ? reinterpret_cast<uint32_t *>(base + arrays + bmb +
+                                                 align256(slot_edge_entries(blockDim.x) * sizeof(uint2)))
+                  : nullptr;
     return s;
 }
 
 // Shared-memory carve-up: [row table][plane table][bitmap of side smem_L][node_cap union-find
-// nodes][edge list (the rest)]; the table-building scratch uses the start of the edge list.
+// nodes][edge list (the rest)]; the table-building scratch uses the start of the edge list.  The
+// summary kernels use [summary tables][d5 masks][region][nodes][extra][edge list] instead
+// (smem_ptrs_sum), with rows and planes null.
 struct SmemPtrs {
     RowEntry *rows;
     PlaneEntry *planes;
@@ -624,6 +803,8 @@ struct SmemPtrs {
     uint32_t *nodes;
     uint2 *edges;
     uint32_t *scratch;
+    GroupEntry *tab;
+    uint8_t *d5m;
 };
 
 __host__ __device__ inline size_t smem_tables_bytes() { return sizeof(RowEntry) * kRowCand + sizeof(PlaneEntry) * kPlaneCand; }
@@ -647,7 +828,76 @@ __device__ __forceinline__ SmemPtrs smem_ptrs(unsigned char *dyn, uint32_t smem_
     p.nodes = reinterpret_cast<uint32_t *>(dyn + nodes_at);
     p.edges = reinterpret_cast<uint2 *>(dyn + nodes_at + smem_nodes_bytes(node_cap) + extra);
     p.scratch = reinterpret_cast<uint32_t *>(p.edges);
+    p.tab = nullptr;
+    p.d5m = nullptr;
     return p;
+}
+
+// Region of the summary kernels: a sample with L <= smem_L keeps its bitmap there, one with
+// smem_L < L <= sum_L its occupancy summary (its bitmap is in the slot), a bigger one neither (both
+// in the slot).
+__host__ __device__ inline size_t region_bm_bytes(uint32_t L) { return L ? smem_bitmap_bytes(L) : 0; }
+
+__host__ __device__ inline size_t smem_sum_tables_bytes() { return kSumTabBytes + kD5Bytes; }
+
+// Shared memory of the summary kernels: [row table][plane table][group table][d5 masks][region]
+// [node_cap nodes][extra][edge list].
+__device__ __forceinline__ SmemPtrs smem_ptrs_sum(unsigned char *dyn, size_t region, uint32_t node_cap, size_t extra = 0)
+{
+    SmemPtrs p;
+    p.rows = reinterpret_cast<RowEntry *>(dyn);
+    p.planes = reinterpret_cast<PlaneEntry *>(dyn + sizeof(RowEntry) * kRowCand);
+    p.tab = reinterpret_cast<GroupEntry *>(dyn + smem_tables_bytes());
+    p.d5m = dyn + smem_tables_bytes() + kSumTabBytes;
+    p.sbm = reinterpret_cast<uint32_t *>(dyn + smem_tables_bytes() + smem_sum_tables_bytes());
+    const size_t nodes_at = smem_tables_bytes() + smem_sum_tables_bytes() + region;
+    p.nodes = reinterpret_cast<uint32_t *>(dyn + nodes_at);
+    p.edges = reinterpret_cast<uint2 *>(dyn + nodes_at + smem_nodes_bytes(node_cap) + extra);
+    p.scratch = reinterpret_cast<uint32_t *>(p.edges);
+    return p;
+}
+
+// This sample's bitmap and summary (see smem_ptrs_sum); sum is null while the bitmap is on chip.
+__device__ __forceinline__ void sample_bm_sum(const SmemPtrs &sm, const SlotPtrs &sp, uint32_t L, uint32_t smem_L,
+                                              uint32_t sum_L, uint32_t *&bm, uint32_t *&sum)
+{
+    if (L <= smem_L) {
+        bm = sm.sbm;
+        sum = nullptr;
+    } else {
+        bm = sp.gbm;
+        sum = L <= sum_L ? sm.sbm : sp.gsum;
+    }
+}
+
+// Per-sample setup of the summary kernels (all threads; ends with a barrier): bitmap (and summary)
+// cleared, and the scan tables of the sample's path: rows (and planes at L = 16) while the bitmap is
+// on chip, the summary groups otherwise.
+__device__ __forceinline__ void sample_tables(Ctl &c, const SmemPtrs &sm, uint32_t *bm, uint32_t *sum, uint32_t L,
+                                              uint32_t mask, bool smem_bm)
+{
+    const uint32_t words = bm_words(num_sites(L));
+    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
+    if (smem_bm) {
+        build_rows(mask, L, sm.rows, sm.scratch, c);
+        if (L == kPlaneL) build_planes16(sm.rows, c.R, sm.planes, sm.scratch, c);
+    } else {
+        const uint32_t swords = sum_words(L);
+        for (uint32_t w = threadIdx.x; w < swords; w += blockDim.x) sum[w] = 0u;
+        build_sum_tabs(mask, L, sm.tab, sm.d5m, sm.scratch, c);
+    }
+}
+
+// Bitmap and summary gain the sites of rank [n0, n1).
+__device__ __forceinline__ void bitmap_add_sum(uint32_t *bm, uint32_t *sum, const uint32_t *perm, uint32_t n0,
+                                               uint32_t n1, const FastDiv &fd)
+{
+    for (uint32_t r = n0 + threadIdx.x; r < n1; r += blockDim.x) {
+        const uint32_t site = __ldg(perm + r), i = site + kBmGuard;
+        atomicOr(bm + (i >> 5), 1u << (i & 31u));
+        const uint32_t row = fdiv(site, fd) + kSumGuard;
+        atomicOr(sum + (row >> 5), 1u << (row & 31u));
+    }
 }
 
 struct PhaseClock {
@@ -668,10 +918,11 @@ __device__ __forceinline__ uint32_t probe(Ctl &c, const Nodes &P, uint32_t *logb
     __syncthreads();
     const long long t1 = clock64();
     // (the chunk loop of the union pass ends with a block barrier, mid > nb gives at least one chunk)
+    const ScanTabs T{sm.rows, sm.planes, nullptr, nullptr, nullptr};
     if (kSmemBm && L == kPlaneL)
-        union_pass<true, true, true>(c, P, logb, sm.sbm, sm.rows, sm.planes, E, perm, rank, L, fd, nb, mid, nb + 2u);
+        union_pass<true, true, kScanPlanes>(c, P, logb, sm.sbm, T, E, perm, rank, L, fd, nb, mid, nb + 2u);
     else
-        union_pass<kSmemBm, true, false>(c, P, logb, bm, sm.rows, sm.planes, E, perm, rank, L, fd, nb, mid, nb + 2u);
+        union_pass<kSmemBm, true, kScanRows>(c, P, logb, bm, T, E, perm, rank, L, fd, nb, mid, nb + 2u);
     const long long t2 = clock64();
     clk.update += t1 - t0;
     clk.unite += t2 - t1;
@@ -1024,7 +1275,8 @@ k_nstar_group(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
             for (uint32_t r = nb + gtid; r < mid; r += gthreads) nd_st(P, r + 2u, r + 2u);
             if (!(alive = group_sync(gs, members, &hdr->status, &ok_s, spin_limit))) break;
             const long long t1 = clock64();
-            union_pass<false, true, false, true>(c, P, logb, bm, rows, nullptr, E, smp.perm, smp.rank, L, fd, nb, mid,
+            const ScanTabs T{rows, nullptr, nullptr, nullptr, nullptr};
+            union_pass<false, true, kScanRows, true>(c, P, logb, bm, T, E, smp.perm, smp.rank, L, fd, nb, mid,
                                                  nb + 2u, &gs->stop, &gs->logn, member, members);
             if (!(alive = group_sync(gs, members, &hdr->status, &ok_s, spin_limit))) break;
             const long long t2 = clock64();
@@ -1098,17 +1350,17 @@ k_nstar_group(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
 
 // S_max(n) per sample: one full pass over the first n sites, then cluster sizes by root counting.
 __global__ void __launch_bounds__(1024, 1)
-k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t node_cap,
-        uint32_t edge_scap,
+k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t sum_L,
+       size_t region, uint32_t node_cap, uint32_t edge_scap,
        const uint64_t *__restrict__ n_in, int64_t *__restrict__ mass_out, char *ws, size_t slot_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
-    const SmemPtrs sm = smem_ptrs(dyn, smem_L, node_cap);
+    const SmemPtrs sm = smem_ptrs_sum(dyn, region, node_cap);
     __shared__ Ctl c;
     __shared__ uint32_t red[32];
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
-    const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
+    const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L, max_L > sum_L);
     const EdgeList E{sm.edges, edge_scap, sp.gedges};
     const Nodes P{sp.P, static_cast<uint32_t>(__cvta_generic_to_shared(sm.nodes)), node_cap};
     uint32_t *cnt = sp.logb;
@@ -1133,11 +1385,9 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         const uint32_t N = static_cast<uint32_t>(num_sites(L));
         const uint32_t n = static_cast<uint32_t>(n64);
         const bool smem_bm = L <= smem_L;
-        uint32_t *bm = smem_bm ? sm.sbm : sp.gbm;
-        const uint32_t words = bm_words(N);
-        for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
-        build_rows(mask, L, sm.rows, sm.scratch, c);
-        if (smem_bm && L == kPlaneL) build_planes16(sm.rows, c.R, sm.planes, sm.scratch, c);
+        uint32_t *bm, *sum;
+        sample_bm_sum(sm, sp, L, smem_L, sum_L, bm, sum);
+        sample_tables(c, sm, bm, sum, L, mask, smem_bm);
         if (threadIdx.x == 0) {
             c.logn = 0;
             c.stop = 0;
@@ -1146,18 +1396,24 @@ k_mass(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         }
         const FastDiv fd = make_fastdiv(L);
         __syncthreads();
-        bitmap_update(bm, smp.perm, 0u, n);
+        if (smem_bm)
+            bitmap_update(bm, smp.perm, 0u, n);
+        else
+            bitmap_add_sum(bm, sum, smp.perm, 0u, n, fd);
         for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) {
             nd_st(P, r + 2u, r + 2u);
             __stcg(cnt + r + 2u, 0u);
         }
         __syncthreads();
+        const ScanTabs T{sm.rows, sm.planes, sm.tab, sm.d5m, sum};
         if (smem_bm && L == kPlaneL)
-            union_pass<true, false, true, false, true>(c, P, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+            union_pass<true, false, kScanPlanes, false, true>(c, P, nullptr, sm.sbm, T, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         else if (smem_bm)
-            union_pass<true, false, false, false, true>(c, P, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+            union_pass<true, false, kScanRows, false, true>(c, P, nullptr, sm.sbm, T, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+        else if (L <= sum_L)
+            union_pass<false, false, kScanGroups, false, true>(c, P, nullptr, bm, T, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         else
-            union_pass<false, false, false, false, true>(c, P, nullptr, bm, sm.rows, sm.planes, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
+            union_pass<false, false, kScanGroupsG, false, true>(c, P, nullptr, bm, T, E, smp.perm, smp.rank, L, fd, 0u, n, 0u);
         __syncthreads();
         for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) atomicAdd(cnt + uf_find(P, r + 2u, 0u), 1u);
         __syncthreads();
@@ -1207,19 +1463,23 @@ static_assert(kRecCap > kMaxOffsets && kRecCap < kRootHash && (kRootHash & (kRoo
 constexpr uint32_t kRecSlot = 0xFFFFu;  // a record is (chunk site << 16) | local slot
 constexpr uint32_t kFlagLo = 1u, kFlagHi = 2u;  // a cluster touches x1 = 0 / x1 = L-1
 
+// The window arrays, at fixed offsets from one base (computed where they are used, so that a kernel
+// keeps one pointer live instead of twelve).
 struct WinPtrs {
-    uint32_t *deg;   // [C] kept edges per chunk site
-    uint32_t *ev;    // [C] cluster size right after each chunk site is added (replayed components)
-    uint32_t *lp;    // [C + kRootHash] local union-find in time order: parent slot, or kRootBit | entry
-    uint32_t *hkey;  // [kRootHash] forest node of local slot C + h (kEmptySlot: free)
-    uint32_t *rec;   // [kRecCap] kept edges in site order: (chunk site << 16) | earlier end's local slot
-    uint32_t *off;   // [C + 1] first record of each chunk site
-    uint32_t *cc;    // [C + kRootHash] components of the chunk's records (union-find, smallest root)
-    uint32_t *memb;  // [C] component of each chunk site
-    uint32_t *fl;    // [C] border flags of each chunk site (n* sweep)
-    uint32_t *gm;    // [C] smallest forest node of each component, then the replay list
-    uint32_t *cur;   // [C] placement cursor of each chunk site's records
-    uint32_t *tot;   // [C] per-component totals: border flags (n* sweep) or cluster size
+    uint32_t *u;  // start of the window arrays
+    uint32_t C;   // chunk capacity (blockDim.x)
+    __device__ __forceinline__ uint32_t *deg() const { return u; }           // [C] kept edges per chunk site
+    __device__ __forceinline__ uint32_t *ev() const { return u + C; }        // [C] cluster size (or flags) per site
+    __device__ __forceinline__ uint32_t *lp() const { return u + 2 * C; }    // [C + kRootHash] local union-find in time order: parent slot, or kRootBit | entry
+    __device__ __forceinline__ uint32_t *hkey() const { return u + 3 * C + kRootHash; }  // [kRootHash] forest node of local slot C + h (kEmptySlot: free)
+    __device__ __forceinline__ uint32_t *rec() const { return u + 3 * C + 2 * kRootHash; }  // [kRecCap] kept edges in site order: (chunk site << 16) | local slot
+    __device__ __forceinline__ uint32_t *off() const { return u + 3 * C + 2 * kRootHash + kRecCap; }  // [C + 1] first record of each chunk site
+    __device__ __forceinline__ uint32_t *cc() const { return u + 4 * C + 1 + 2 * kRootHash + kRecCap; }  // [C + kRootHash] components of the chunk's records
+    __device__ __forceinline__ uint32_t *memb() const { return u + 5 * C + 1 + 3 * kRootHash + kRecCap; }  // [C] component of each chunk site
+    __device__ __forceinline__ uint32_t *fl() const { return u + 6 * C + 1 + 3 * kRootHash + kRecCap; }  // [C] border flags of each chunk site (n* sweep)
+    __device__ __forceinline__ uint32_t *gm() const { return u + 7 * C + 1 + 3 * kRootHash + kRecCap; }  // [C] smallest forest node of each component, then the replay list
+    __device__ __forceinline__ uint32_t *cur() const { return u + 8 * C + 1 + 3 * kRootHash + kRecCap; }  // [C] placement cursor of each chunk site's records
+    __device__ __forceinline__ uint32_t *tot() const { return u + 9 * C + 1 + 3 * kRootHash + kRecCap; }  // [C] per-component totals: border flags or cluster size
 };
 
 __host__ __device__ inline size_t smem_window_bytes(uint32_t threads)
@@ -1229,21 +1489,7 @@ __host__ __device__ inline size_t smem_window_bytes(uint32_t threads)
 
 __device__ __forceinline__ WinPtrs win_ptrs(unsigned char *at, uint32_t C)
 {
-    WinPtrs w;
-    uint32_t *u = reinterpret_cast<uint32_t *>(at);
-    w.deg = u;
-    w.ev = u + C;
-    w.lp = u + 2 * C;
-    w.hkey = w.lp + C + kRootHash;
-    w.rec = w.hkey + kRootHash;
-    w.off = w.rec + kRecCap;
-    w.cc = w.off + C + 1;
-    w.memb = w.cc + C + kRootHash;
-    w.fl = w.memb + C;
-    w.gm = w.fl + C;
-    w.cur = w.gm + C;
-    w.tot = w.cur + C;
-    return w;
+    return WinPtrs{reinterpret_cast<uint32_t *>(at), C};
 }
 
 // The first pass of a sample keeps the nodes below PA.cap (its own nodes plus the window arrays'
@@ -1351,9 +1597,9 @@ __device__ __forceinline__ uint32_t root_slot(const WinPtrs &wp, const uint32_t 
     uint32_t h = (g * 2654435761u) >> (32 - 11);
     static_assert(kRootHash == 2048u, "hash width");
     for (uint32_t probe = 0; probe < kRootHash; ++probe) {
-        const uint32_t prev = atomicCAS(wp.hkey + h, kEmptySlot, g);
+        const uint32_t prev = atomicCAS(wp.hkey() + h, kEmptySlot, g);
         if (prev == kEmptySlot) {
-            wp.lp[C + h] = kSpan ? (kRootBit | 4u | (g == 0u ? kFlagLo : g == 1u ? kFlagHi : 0u))
+            wp.lp()[C + h] = kSpan ? (kRootBit | 4u | (g == 0u ? kFlagLo : g == 1u ? kFlagHi : 0u))
                                  : (kRootBit | __ldcg(cnt + g));
             return C + h;
         }
@@ -1366,35 +1612,48 @@ __device__ __forceinline__ uint32_t root_slot(const WinPtrs &wp, const uint32_t 
 // Scan of the window chunk [b, b + count): edges (local index of the site, occupied neighbor).  With
 // one site per thread, `site` is the thread's site (loaded by the caller); with fl, each site's
 // border flags go to fl and, for the n* sweep, its local union-find entry to lp.
-template <bool kSmemBm, bool kPlanes>
-__device__ __forceinline__ void window_scan(const Ctl &c, const uint32_t *bm, const RowEntry *rows,
-                                            const PlaneEntry *planes, const EdgeList &E, const uint32_t *perm,
-                                            uint32_t L, const FastDiv &fd, uint32_t b, uint32_t count,
-                                            uint32_t site, uint32_t *ecount, uint32_t *fl, uint32_t *lp)
+template <bool kSmemBm, int kMode>
+__device__ __forceinline__ void window_scan(const Ctl &c, const uint32_t *bm, const ScanTabs &T, const EdgeList &E,
+                                            const uint32_t *perm, uint32_t L, const FastDiv &fd, uint32_t b,
+                                            uint32_t count, uint32_t site, uint32_t *ecount, uint32_t *fl,
+                                            uint32_t *lp)
 {
-    const uint32_t R = kPlanes ? c.NP : c.R;
+    constexpr bool kPlanes = kMode == kScanPlanes;
+    const uint32_t R = uses_sum(kMode) ? c.G : kPlanes ? c.NP : c.R;
     const uint32_t gshift = lanes_shift(count, R);
     const uint32_t gsize = 1u << gshift, gl = threadIdx.x & (gsize - 1u), t = threadIdx.x >> gshift;
     if (t >= count) return;
-    const SiteGeo g = site_geo<kPlanes>(gshift ? __ldg(perm + b + t) : site, L, fd, c.axis);
+    const SiteGeo g = site_geo<kMode>(gshift ? __ldg(perm + b + t) : site, L, fd, c.axis);
     if (fl && gl == 0u) {
         const uint32_t f = (g.low ? kFlagLo : 0u) | (g.high ? kFlagHi : 0u);
         fl[t] = f;
         lp[t] = kRootBit | 4u | f;
     }
-    for (uint32_t k = gl; k < R; k += gsize) {
-        uint32_t h[3];
-        const uint32_t jb = entry_hits<kSmemBm, kPlanes>(g, bm, rows, planes, k, h);
-        const uint32_t nh = __popc(h[0]) + __popc(h[1]) + __popc(h[2]);
-        if (nh == 0u) continue;
-        uint32_t slot = atomicAdd(ecount, nh);
+    if constexpr (uses_sum(kMode)) {
+        auto emit = [&](uint32_t jb, uint32_t h) {
+            uint32_t slot = atomicAdd(ecount, static_cast<uint32_t>(__popc(h)));
+            while (h) {
+                const uint32_t bit = __ffs(h) - 1;
+                h &= h - 1u;
+                edge_put(E, slot++, make_uint2(t, jb + bit));
+            }
+        };
+        for (uint32_t k = gl; k < R; k += gsize) sum_entry_hits<kSmemBm, kMode, false>(g, bm, T, L, k, emit);
+    } else {
+        for (uint32_t k = gl; k < R; k += gsize) {
+            uint32_t h[3];
+            const uint32_t jb = entry_hits<kSmemBm, kPlanes>(g, bm, T.rows, T.planes, k, h);
+            const uint32_t nh = __popc(h[0]) + __popc(h[1]) + __popc(h[2]);
+            if (nh == 0u) continue;
+            uint32_t slot = atomicAdd(ecount, nh);
 #pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            uint32_t hf = h[f];
-            while (hf) {
-                const uint32_t bit = __ffs(hf) - 1;
-                hf &= hf - 1u;
-                edge_put(E, slot++, make_uint2(t, jb + 32u * f + bit));
+            for (int f = 0; f < 3; ++f) {
+                uint32_t hf = h[f];
+                while (hf) {
+                    const uint32_t bit = __ffs(hf) - 1;
+                    hf &= hf - 1u;
+                    edge_put(E, slot++, make_uint2(t, jb + 32u * f + bit));
+                }
             }
         }
     }
@@ -1411,32 +1670,36 @@ struct SmaxShared {
 // Returns the number of sites taken (>= 1); `comp` gets the component (its smallest site) of the
 // thread's site (< tn).  The previous chunk must have ended with a block barrier after its last
 // reader of the per-site arrays.
-template <bool kSmemBm, bool kPlanes, bool kSpan>
+template <bool kSmemBm, int kMode, bool kSpan>
 __device__ __forceinline__ uint32_t chunk_front(Ctl &c, SmaxShared &x, const Nodes &P, const uint32_t *cnt,
-                                                uint32_t *bm, const SmemPtrs &sm, const WinPtrs &wp,
+                                                uint32_t *bm, const ScanTabs &T, const WinPtrs &wp,
                                                 const EdgeList &E, const perc_sample &smp, const FastDiv &fd,
                                                 uint32_t b, uint32_t n_end, uint32_t &comp)
 {
     const uint32_t C = blockDim.x;
     const uint32_t count = min(C, n_end - b);
     const long long t0 = clock64();
-    wp.deg[threadIdx.x] = 0u;
-    wp.cur[threadIdx.x] = 0u;
-    wp.tot[threadIdx.x] = 0u;
-    wp.gm[threadIdx.x] = kEmptySlot;
-    wp.ev[threadIdx.x] = 0u;
-    if (!kSpan) wp.lp[threadIdx.x] = kRootBit | 1u;
-    for (uint32_t y = threadIdx.x; y < C + kRootHash; y += C) wp.cc[y] = y;
+    wp.deg()[threadIdx.x] = 0u;
+    wp.cur()[threadIdx.x] = 0u;
+    wp.tot()[threadIdx.x] = 0u;
+    wp.gm()[threadIdx.x] = kEmptySlot;
+    wp.ev()[threadIdx.x] = 0u;
+    if (!kSpan) wp.lp()[threadIdx.x] = kRootBit | 1u;
+    for (uint32_t y = threadIdx.x; y < C + kRootHash; y += C) wp.cc()[y] = y;
     if (threadIdx.x == 0) c.ecount[0] = 0u;
     uint32_t site = 0u;
-    if (threadIdx.x < count) {  // the chunk's sites join the bitmap
+    if (threadIdx.x < count) {  // the chunk's sites join the bitmap (and the summary)
         site = __ldg(smp.perm + b + threadIdx.x);
         const uint32_t i = site + kBmGuard;
         atomicOr(bm + (i >> 5), 1u << (i & 31u));
+        if (uses_sum(kMode)) {
+            const uint32_t row = fdiv(site, fd) + kSumGuard;
+            atomicOr(T.sum + (row >> 5), 1u << (row & 31u));
+        }
     }
     __syncthreads();
-    window_scan<kSmemBm, kPlanes>(c, bm, sm.rows, sm.planes, E, smp.perm, smp.L, fd, b, count, site, &c.ecount[0],
-                                  kSpan ? wp.fl : nullptr, wp.lp);
+    window_scan<kSmemBm, kMode>(c, bm, T, E, smp.perm, smp.L, fd, b, count, site, &c.ecount[0],
+                                kSpan ? wp.fl() : nullptr, wp.lp());
     __syncthreads();
     const long long t1 = clock64();
     const uint32_t ne = c.ecount[0];
@@ -1445,33 +1708,33 @@ __device__ __forceinline__ uint32_t chunk_front(Ctl &c, SmaxShared &x, const Nod
         const uint2 ed = edge_get(E, e);
         const uint32_t rj = __ldg(smp.rank + ed.y);
         const bool keep = rj < b + ed.x;
-        if (keep) atomicAdd(wp.deg + ed.x, 1u);
+        if (keep) atomicAdd(wp.deg() + ed.x, 1u);
         edge_put(E, e, make_uint2(keep ? ed.x : kEmptySlot, rj));
     }
     __syncthreads();
-    const uint32_t d = wp.deg[threadIdx.x];
+    const uint32_t d = wp.deg()[threadIdx.x];
     uint32_t total;
     const uint32_t excl = block_exclusive_sum(d, x.red, total);
-    wp.off[threadIdx.x] = excl;
-    if (threadIdx.x == C - 1u) wp.off[C] = total;
+    wp.off()[threadIdx.x] = excl;
+    if (threadIdx.x == C - 1u) wp.off()[C] = total;
     const uint32_t tn = __syncthreads_count(threadIdx.x < count && excl + d <= kRecCap);
     // resolve: earlier neighbors to local slots, records in site order
     for (uint32_t e = threadIdx.x; e < ne; e += C) {
         const uint2 ed = edge_get(E, e);
         if (ed.x >= tn) continue;  // dropped, or past the cut
-        const uint32_t pos = wp.off[ed.x] + atomicAdd(wp.cur + ed.x, 1u);
+        const uint32_t pos = wp.off()[ed.x] + atomicAdd(wp.cur() + ed.x, 1u);
         const uint32_t slot = ed.y >= b ? ed.y - b : root_slot<kSpan>(wp, cnt, uf_find(P, ed.y + 2u, 0u), C);
-        wp.rec[pos] = (ed.x << 16) | (slot & kRecSlot);
+        wp.rec()[pos] = (ed.x << 16) | (slot & kRecSlot);
     }
-    const uint32_t nrec = wp.off[tn];
+    const uint32_t nrec = wp.off()[tn];
     __syncthreads();
     // the clusters a chunk builds only interact inside a component of its records
     for (uint32_t k = threadIdx.x; k < nrec; k += C) {
-        const uint32_t r = wp.rec[k], s2 = r & kRecSlot;
-        if (s2 < C + kRootHash) cc_unite(wp.cc, r >> 16, s2);
+        const uint32_t r = wp.rec()[k], s2 = r & kRecSlot;
+        if (s2 < C + kRootHash) cc_unite(wp.cc(), r >> 16, s2);
     }
     __syncthreads();
-    comp = threadIdx.x < tn ? cc_find(wp.cc, threadIdx.x) : 0u;
+    comp = threadIdx.x < tn ? cc_find(wp.cc(), threadIdx.x) : 0u;
     if (threadIdx.x == 0) {
         c.cyc_scan += static_cast<unsigned long long>(t1 - t0);
         c.cyc_link += static_cast<unsigned long long>(clock64() - t1);
@@ -1496,56 +1759,56 @@ __device__ __forceinline__ void chunk_components(const Nodes &P, uint32_t *cnt, 
 {
     const uint32_t C = blockDim.x;
     if (threadIdx.x < tn) {
-        wp.memb[threadIdx.x] = comp;
+        wp.memb()[threadIdx.x] = comp;
         if (kSpan)
-            atomicOr(wp.tot + comp, wp.fl[threadIdx.x]);
+            atomicOr(wp.tot() + comp, wp.fl()[threadIdx.x]);
         else
-            atomicAdd(wp.tot + comp, 1u);
-        atomicMin(wp.gm + comp, b + threadIdx.x + 2u);
+            atomicAdd(wp.tot() + comp, 1u);
+        atomicMin(wp.gm() + comp, b + threadIdx.x + 2u);
     }
     for (uint32_t h = threadIdx.x; h < kRootHash; h += C) {
-        const uint32_t g = wp.hkey[h];
+        const uint32_t g = wp.hkey()[h];
         if (g == kEmptySlot) continue;
-        const uint32_t ch = cc_find(wp.cc, C + h);
+        const uint32_t ch = cc_find(wp.cc(), C + h);
         if (kSpan)
-            atomicOr(wp.tot + ch, g == 0u ? kFlagLo : g == 1u ? kFlagHi : 0u);
+            atomicOr(wp.tot() + ch, g == 0u ? kFlagLo : g == 1u ? kFlagHi : 0u);
         else
-            atomicAdd(wp.tot + ch, wp.lp[C + h] & ~kRootBit);
-        atomicMin(wp.gm + ch, g);
+            atomicAdd(wp.tot() + ch, wp.lp()[C + h] & ~kRootBit);
+        atomicMin(wp.gm() + ch, g);
     }
     __syncthreads();
     auto root_of = [&](uint32_t cp) {
         if (kSpan) {
-            const uint32_t f = wp.tot[cp];
+            const uint32_t f = wp.tot()[cp];
             if (f & kFlagLo) return 0u;
             if (f & kFlagHi) return 1u;
         }
-        return wp.gm[cp];
+        return wp.gm()[cp];
     };
     if (threadIdx.x < tn) {
         const uint32_t node = b + threadIdx.x + 2u, r = root_of(comp);
         nd_st(P, node, r);
-        if (!kSpan && r == node) __stcg(cnt + node, wp.tot[comp]);
+        if (!kSpan && r == node) __stcg(cnt + node, wp.tot()[comp]);
     }
     for (uint32_t h = threadIdx.x; h < kRootHash; h += C) {
-        const uint32_t g = wp.hkey[h];
+        const uint32_t g = wp.hkey()[h];
         if (g == kEmptySlot) continue;
-        const uint32_t ch = cc_find(wp.cc, C + h), r = root_of(ch);
+        const uint32_t ch = cc_find(wp.cc(), C + h), r = root_of(ch);
         if (r != g)
             nd_st(P, g, r);
         else if (!kSpan)
-            __stcg(cnt + g, wp.tot[ch]);
+            __stcg(cnt + g, wp.tot()[ch]);
     }
 }
 
 // The sites of the components to replay (need = this thread's site belongs to one), in rank order,
-// compacted into wp.gm (free after the write-back); returns their number.  All threads; contains
+// compacted into wp.gm() (free after the write-back); returns their number.  All threads; contains
 // block barriers.
 __device__ __forceinline__ uint32_t replay_list(SmaxShared &x, const WinPtrs &wp, bool need)
 {
     uint32_t tot;
     const uint32_t at = block_exclusive_sum(need ? 1u : 0u, x.red, tot);
-    if (need) wp.gm[at] = threadIdx.x;
+    if (need) wp.gm()[at] = threadIdx.x;
     __syncthreads();
     return tot;
 }
@@ -1556,14 +1819,14 @@ __device__ __forceinline__ uint32_t replay_list(SmaxShared &x, const WinPtrs &wp
 __device__ __forceinline__ void replay_component(const WinPtrs &wp, uint32_t t0, uint32_t nlist, uint32_t C,
                                                  int *status)
 {
-    const uint32_t s_lp = smem_addr(wp.lp);
+    const uint32_t s_lp = smem_addr(wp.lp());
     for (uint32_t i = 0; i < nlist; ++i) {
-        const uint32_t t = wp.gm[i];
-        if (wp.memb[t] != t0) continue;
-        const uint32_t k0 = wp.off[t], k1 = wp.off[t + 1u];
+        const uint32_t t = wp.gm()[i];
+        if (wp.memb()[t] != t0) continue;
+        const uint32_t k0 = wp.off()[t], k1 = wp.off()[t + 1u];
         uint32_t ra = t, sa = lds_u32(s_lp + 4u * t) & ~kRootBit;  // no earlier record names site t: a root
         for (uint32_t k = k0; k < k1; ++k) {
-            const uint32_t bs = wp.rec[k] & kRecSlot;
+            const uint32_t bs = wp.rec()[k] & kRecSlot;
             if (bs >= C + kRootHash) {  // full hash (ruled out by the capacities)
                 set_status(status, PERC_EDEVICE);
                 continue;
@@ -1592,29 +1855,33 @@ __device__ __forceinline__ void replay_component(const WinPtrs &wp, uint32_t t0,
             sa += sb;
             sts_u32(s_lp + 4u * ra, kRootBit | sa);
         }
-        wp.ev[t] = sa;
+        wp.ev()[t] = sa;
     }
 }
 
 // One sample of k_smax (all threads).  Writes row[k] = S_max(n_lo + k) for n_lo + k <= n_end.
-template <bool kSmemBm, bool kPlanes>
-__device__ void smax_sample(Ctl &c, SmaxShared &x, const Nodes &P, const Nodes &PA, uint32_t *cnt, uint32_t *bm,
-                            const SmemPtrs &sm, const WinPtrs &wp, const EdgeList &E, const perc_sample &smp,
-                            uint32_t n0, uint32_t n_end, uint64_t nlo, uint32_t window, uint32_t *row, int *status)
+template <bool kSmemBm, int kMode>
+__device__ __forceinline__ void smax_sample(Ctl &c, SmaxShared &x, const Nodes &P, const Nodes &PA, uint32_t *cnt, uint32_t *bm,
+                            const SmemPtrs &sm, const ScanTabs &T, const WinPtrs &wp, const EdgeList &E,
+                            const perc_sample &smp, uint32_t n0, uint32_t n_end, uint64_t nlo, uint32_t window,
+                            uint32_t *row, int *status)
 {
     const uint32_t C = blockDim.x, L = smp.L;
     if (kSmemBm) bm = sm.sbm;
     const FastDiv fd = make_fastdiv(L);
     // ---- the forest of the first n0 sites (nodes PA), the cluster sizes and S_max(n0)
-    bitmap_update(bm, smp.perm, 0u, n0);
+    if constexpr (uses_sum(kMode))
+        bitmap_add_sum(bm, T.sum, smp.perm, 0u, n0, fd);
+    else
+        bitmap_update(bm, smp.perm, 0u, n0);
     for (uint32_t r = threadIdx.x; r < n0; r += C) {
         nd_st(PA, r + 2u, r + 2u);
         __stcg(cnt + r + 2u, 0u);
     }
     __syncthreads();
     if (n0 > 0u)
-        union_pass<kSmemBm, false, kPlanes, false, true>(c, PA, nullptr, bm, sm.rows, sm.planes, E, smp.perm, smp.rank,
-                                                         L, fd, 0u, n0, 0u);
+        union_pass<kSmemBm, false, kMode, false, true>(c, PA, nullptr, bm, T, E, smp.perm, smp.rank, L, fd, 0u, n0,
+                                                       0u);
     __syncthreads();
     for (uint32_t r = threadIdx.x; r < n0; r += C) atomicAdd(cnt + uf_find(PA, r + 2u, 0u), 1u);
     __syncthreads();
@@ -1623,7 +1890,7 @@ __device__ void smax_sample(Ctl &c, SmaxShared &x, const Nodes &P, const Nodes &
     best = __reduce_max_sync(0xffffffffu, best);
     if ((threadIdx.x & 31u) == 0u) x.red[threadIdx.x >> 5] = best;
     lend_back(P, PA, n0 + 2u);
-    for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey[h] = kEmptySlot;
+    for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey()[h] = kEmptySlot;
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t bmax = 0;
@@ -1634,65 +1901,118 @@ __device__ void smax_sample(Ctl &c, SmaxShared &x, const Nodes &P, const Nodes &
     // ---- the window's sites, a chunk at a time
     for (uint32_t b = n0; b < n_end;) {
         uint32_t comp;
-        const uint32_t tn = chunk_front<kSmemBm, kPlanes, false>(c, x, P, cnt, bm, sm, wp, E, smp, fd, b, n_end, comp);
+        const uint32_t tn = chunk_front<kSmemBm, kMode, false>(c, x, P, cnt, bm, T, wp, E, smp, fd, b, n_end, comp);
         const uint32_t run0 = x.run_max;
         chunk_components<false>(P, cnt, wp, b, tn, comp);
         // a component can raise S_max only if its final size passes the running maximum: replay those
-        const bool need = threadIdx.x < tn && wp.tot[comp] > run0;
+        const bool need = threadIdx.x < tn && wp.tot()[comp] > run0;
         if (__syncthreads_or(need)) {
             const uint32_t nlist = replay_list(x, wp, need);
             if (need && comp == threadIdx.x) replay_component(wp, threadIdx.x, nlist, C, status);
             __syncthreads();
         }
-        const uint32_t v = threadIdx.x < tn ? wp.ev[threadIdx.x] : 0u;
+        const uint32_t v = threadIdx.x < tn ? wp.ev()[threadIdx.x] : 0u;
         const uint32_t run = max(block_inclusive_max(v, x.red), run0);
         if (threadIdx.x < tn) {
             const uint64_t k = uint64_t(b) + threadIdx.x + 1u - nlo;
             if (k < window) row[k] = run;
         }
         if (threadIdx.x == tn - 1u) x.run_max = run;
-        for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey[h] = kEmptySlot;
+        for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey()[h] = kEmptySlot;
         b += tn;
         __syncthreads();  // the per-site arrays, the hash and run_max are read again by the next chunk
     }
 }
 
+// Union-find of the first-spanning-site search: entries that a probe hooks carry kProbeTag until the
+// probe is committed, and path halving never shortcuts a tagged edge, so that undoing a probe (its
+// hooked roots reset) leaves a valid committed forest.
+constexpr uint32_t kProbeTag = 0x80000000u;
+
+__device__ __forceinline__ uint32_t pcc_find(uint32_t *cc, uint32_t x)
+{
+    volatile uint32_t *v = cc;
+    for (;;) {
+        const uint32_t p = v[x], pu = p & ~kProbeTag;
+        if (pu == x) return x;
+        const uint32_t g = v[pu], gu = g & ~kProbeTag;
+        if (gu == pu) return pu;
+        if (((p | g) & kProbeTag) == 0u) v[x] = gu;  // both edges committed
+        x = gu;
+    }
+}
+
+__device__ __forceinline__ void pcc_unite(uint32_t *cc, uint32_t a, uint32_t b, uint32_t *log, uint32_t *logn)
+{
+    for (;;) {
+        a = pcc_find(cc, a);
+        b = pcc_find(cc, b);
+        if (a == b) return;
+        if (a > b) {
+            const uint32_t t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(cc + b, b, a | kProbeTag) == b) {
+            log[atomicAdd(logn, 1u)] = b;
+            return;
+        }
+    }
+}
+
 // The first site of a spanning chunk whose cluster carries both border flags (all threads; the chunk
 // spans once all its tn sites are added).  Bisection over m, the number of the chunk's sites added:
-// the records of sites < m (stored in site order, the first off[m] of them) are united into local
-// components (shared-memory union-find, smallest slot as root, so every component of a site has a
-// site as root), each root ORs the border flags of its sites and of the earlier clusters it reaches
-// (forest root 0: x1 = 0, root 1: x1 = L-1), and m spans when a root carries both.  span(0) is
-// false (the earlier clusters do not span) and span(tn) true; the answer is the largest m that does
-// not span.  About log2(tn) rounds of four block barriers, instead of one thread replaying the
-// component site by site.
-__device__ uint32_t first_span_site(const WinPtrs &wp, uint32_t tn)
+// the records of sites < m (stored in site order, the first off[m] of them) unite sites and earlier
+// clusters' slots into local components (shared-memory union-find, smallest slot as root, so every
+// component of a site has a site as root), each root ORs the border flags of its sites and of the
+// earlier clusters it reaches (forest root 0: x1 = 0, root 1: x1 = L-1), and m spans when a root
+// carries both.  span(0) is false (the earlier clusters do not span) and span(tn) true; the answer
+// is the largest m that does not span.  The union-find of the largest non-spanning m found so far
+// is kept: a probe only adds the records of the sites between it and the probe, and a probe that
+// spans is undone from its log of hooked roots (in lp, which the sweep does not use), so the
+// records are united about twice in all instead of once per round.  sh: four words of shared
+// scratch.
+__device__ uint32_t first_span_site(const WinPtrs &wp, uint32_t tn, uint32_t *sh)
 {
     const uint32_t C = blockDim.x;
-    uint32_t lo = 0, hi = tn;
+    uint32_t *cc = wp.cc(), *ev = wp.ev(), *log = wp.lp();
+    for (uint32_t y = threadIdx.x; y < C + kRootHash; y += C) cc[y] = y;
+    if (threadIdx.x < 4) sh[threadIdx.x] = threadIdx.x < 2 ? 0u : kEmptySlot;
+    __syncthreads();
+    for (uint32_t h = threadIdx.x; h < kRootHash; h += C) {  // the local slots of the border roots
+        const uint32_t g = wp.hkey()[h];
+        if (g <= 1u) sh[2 + g] = C + h;
+    }
+    uint32_t lo = 0, hi = tn, round = 0;
     while (hi - lo > 1u) {
         const uint32_t m = (lo + hi) >> 1;
-        for (uint32_t y = threadIdx.x; y < C + kRootHash; y += C) wp.cc[y] = y;
-        wp.ev[threadIdx.x] = 0u;
-        __syncthreads();
-        const uint32_t nr = wp.off[m];
-        for (uint32_t k = threadIdx.x; k < nr; k += C) {
-            const uint32_t r = wp.rec[k], s2 = r & kRecSlot;
-            if (s2 < C + kRootHash) cc_unite(wp.cc, r >> 16, s2);
+        uint32_t *logn = sh + (round & 1u);
+        ev[threadIdx.x] = 0u;
+        const uint32_t r1 = wp.off()[m];
+        for (uint32_t k = wp.off()[lo] + threadIdx.x; k < r1; k += C) {
+            const uint32_t r = wp.rec()[k], s2 = r & kRecSlot;
+            if (s2 < C + kRootHash) pcc_unite(cc, r >> 16, s2, log, logn);
         }
         __syncthreads();
-        if (threadIdx.x < m) atomicOr(wp.ev + cc_find(wp.cc, threadIdx.x), wp.fl[threadIdx.x]);
-        for (uint32_t h = threadIdx.x; h < kRootHash; h += C) {
-            const uint32_t g = wp.hkey[h];
-            if (g > 1u) continue;  // free slot (kEmptySlot) or a root that touches no border
-            const uint32_t rt = cc_find(wp.cc, C + h);
-            if (rt < C) atomicOr(wp.ev + rt, g == 0u ? kFlagLo : kFlagHi);  // reached by a site below m
+        if (threadIdx.x < m) atomicOr(ev + pcc_find(cc, threadIdx.x), wp.fl()[threadIdx.x]);
+        if (threadIdx.x < 2u && sh[2 + threadIdx.x] != kEmptySlot) {
+            const uint32_t rt = pcc_find(cc, sh[2 + threadIdx.x]);
+            if (rt < C) atomicOr(ev + rt, threadIdx.x == 0u ? kFlagLo : kFlagHi);  // reached by a site below m
         }
         __syncthreads();
-        if (__syncthreads_or(threadIdx.x < m && wp.ev[threadIdx.x] == (kFlagLo | kFlagHi)))
+        const bool span = __syncthreads_or(threadIdx.x < m && ev[threadIdx.x] == (kFlagLo | kFlagHi));
+        const uint32_t nlog = *logn;
+        for (uint32_t k = threadIdx.x; k < nlog; k += C) {
+            const uint32_t b = log[k];
+            cc[b] = span ? b : (cc[b] & ~kProbeTag);  // undo the probe, or commit its hooks
+        }
+        if (threadIdx.x == 0) sh[(round & 1u) ^ 1u] = 0u;  // the next round's log count
+        __syncthreads();
+        if (span)
             hi = m;
         else
             lo = m;
+        ++round;
     }
     return hi - 1u;
 }
@@ -1700,26 +2020,31 @@ __device__ uint32_t first_span_site(const WinPtrs &wp, uint32_t tn)
 // The n* sweep of one sample from n_s (all threads; the sites of rank < n_s are merged and do not
 // span).  Returns n*, or PERC_NEVER if no n <= N spans; `chunks` counts the chunks taken.  Only a
 // chunk whose components touch both borders at its end is searched for the first spanning site.
-template <bool kSmemBm, bool kPlanes>
-__device__ uint32_t span_sweep(Ctl &c, SmaxShared &x, const Nodes &P, uint32_t *bm, const SmemPtrs &sm,
-                               const WinPtrs &wp, const EdgeList &E, const perc_sample &smp, const FastDiv &fd,
-                               uint32_t N, uint32_t n_s, uint32_t &chunks, unsigned long long &cyc_back, int *status)
+template <bool kSmemBm, int kMode>
+__device__ __forceinline__ uint32_t span_sweep(Ctl &c, SmaxShared &x, const Nodes &P, uint32_t *bm, const SmemPtrs &sm,
+                               const ScanTabs &T, const WinPtrs &wp, const EdgeList &E, const perc_sample &smp,
+                               const FastDiv &fd, uint32_t N, uint32_t n_s, uint32_t &chunks,
+                               unsigned long long &cyc_back, unsigned long long &cyc_span, int *status)
 {
     const uint32_t C = blockDim.x;
     if (kSmemBm) bm = sm.sbm;
-    for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey[h] = kEmptySlot;
+    for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey()[h] = kEmptySlot;
     for (uint32_t b = n_s; b < N;) {
         ++chunks;
         uint32_t comp;
-        const uint32_t tn = chunk_front<kSmemBm, kPlanes, true>(c, x, P, nullptr, bm, sm, wp, E, smp, fd, b, N, comp);
+        const uint32_t tn = chunk_front<kSmemBm, kMode, true>(c, x, P, nullptr, bm, T, wp, E, smp, fd, b, N, comp);
         const long long t0 = clock64();
         chunk_components<true>(P, nullptr, wp, b, tn, comp);
         // only a component that spans at the end of the chunk can hold the first spanning site
-        const bool spans = threadIdx.x < tn && wp.tot[comp] == (kFlagLo | kFlagHi);
+        const bool spans = threadIdx.x < tn && wp.tot()[comp] == (kFlagLo | kFlagHi);
         uint32_t st = kEmptySlot;
-        if (__syncthreads_or(spans)) st = first_span_site(wp, tn);
+        if (__syncthreads_or(spans)) {
+            const long long t1 = clock64();
+            st = first_span_site(wp, tn, x.red);
+            if (threadIdx.x == 0) cyc_span += static_cast<unsigned long long>(clock64() - t1);
+        }
         if (threadIdx.x == 0) cyc_back += static_cast<unsigned long long>(clock64() - t0);
-        for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey[h] = kEmptySlot;
+        for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey()[h] = kEmptySlot;
         if (st != kEmptySlot) return b + st + 1u;
         b += tn;
         __syncthreads();  // the per-site arrays and the hash are reset by the next chunk
@@ -1728,19 +2053,19 @@ __device__ uint32_t span_sweep(Ctl &c, SmaxShared &x, const Nodes &P, uint32_t *
 }
 
 __global__ void __launch_bounds__(1024, 1)
-k_smax(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t node_cap,
-       uint32_t edge_scap, const uint64_t *__restrict__ n_lo, const uint32_t *__restrict__ count, uint32_t window,
-       uint32_t *__restrict__ out, char *ws, size_t slot_bytes)
+k_smax(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L, uint32_t sum_L,
+       size_t region, uint32_t node_cap, uint32_t edge_scap, const uint64_t *__restrict__ n_lo,
+       const uint32_t *__restrict__ count, uint32_t window, uint32_t *__restrict__ out, char *ws, size_t slot_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     const uint32_t C = blockDim.x;
-    const SmemPtrs sm = smem_ptrs(dyn, smem_L, node_cap, smem_window_bytes(C));
+    const SmemPtrs sm = smem_ptrs_sum(dyn, region, node_cap, smem_window_bytes(C));
     const WinPtrs wp = win_ptrs(reinterpret_cast<unsigned char *>(sm.nodes) + smem_nodes_bytes(node_cap), C);
     __shared__ Ctl c;
     __shared__ SmaxShared x;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
-    const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
+    const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L, max_L > sum_L);
     const EdgeList E{sm.edges, edge_scap, sp.gedges};
     const Nodes P{sp.P, static_cast<uint32_t>(__cvta_generic_to_shared(sm.nodes)), node_cap};
     const Nodes PA{sp.P, P.sbase, node_cap + static_cast<uint32_t>(smem_window_bytes(C) / 4)};  // first pass
@@ -1771,11 +2096,9 @@ k_smax(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
         const uint64_t last = nlo + len - 1u;  // the last n computed
         const uint32_t n0 = static_cast<uint32_t>(nlo), n_end = last < N ? static_cast<uint32_t>(last) : N;
         const bool smem_bm = L <= smem_L;
-        uint32_t *bm = smem_bm ? sm.sbm : sp.gbm;
-        const uint32_t words = bm_words(N);
-        for (uint32_t w = threadIdx.x; w < words; w += C) bm[w] = 0u;
-        build_rows(mask, L, sm.rows, sm.scratch, c);
-        if (smem_bm && L == kPlaneL) build_planes16(sm.rows, c.R, sm.planes, sm.scratch, c);
+        uint32_t *bm, *sum;
+        sample_bm_sum(sm, sp, L, smem_L, sum_L, bm, sum);
+        sample_tables(c, sm, bm, sum, L, mask, smem_bm);
         if (threadIdx.x == 0) {
             c.logn = 0;
             c.stop = 0;
@@ -1783,12 +2106,19 @@ k_smax(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
             c.axis = axis;  // S_max does not use borders; kept defined for the shared scan
         }
         __syncthreads();
+        const ScanTabs T{sm.rows, sm.planes, sm.tab, sm.d5m, sum};
         if (smem_bm && L == kPlaneL)
-            smax_sample<true, true>(c, x, P, PA, sp.logb, bm, sm, wp, E, smp, n0, n_end, nlo, window, row, &hdr->status);
+            smax_sample<true, kScanPlanes>(c, x, P, PA, sp.logb, bm, sm, T, wp, E, smp, n0, n_end, nlo, window, row,
+                                           &hdr->status);
         else if (smem_bm)
-            smax_sample<true, false>(c, x, P, PA, sp.logb, bm, sm, wp, E, smp, n0, n_end, nlo, window, row, &hdr->status);
+            smax_sample<true, kScanRows>(c, x, P, PA, sp.logb, bm, sm, T, wp, E, smp, n0, n_end, nlo, window, row,
+                                         &hdr->status);
+        else if (L <= sum_L)
+            smax_sample<false, kScanGroups>(c, x, P, PA, sp.logb, bm, sm, T, wp, E, smp, n0, n_end, nlo, window, row,
+                                            &hdr->status);
         else
-            smax_sample<false, false>(c, x, P, PA, sp.logb, bm, sm, wp, E, smp, n0, n_end, nlo, window, row, &hdr->status);
+            smax_sample<false, kScanGroupsG>(c, x, P, PA, sp.logb, bm, sm, T, wp, E, smp, n0, n_end, nlo, window, row,
+                                             &hdr->status);
         __syncthreads();
     }
 }
@@ -1804,24 +2134,26 @@ k_smax(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, ui
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024, 1)
 k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L,
-              uint32_t node_cap, uint32_t edge_scap, const uint32_t *__restrict__ bracket,
-              uint32_t *__restrict__ nstar_out, uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws,
-              size_t slot_bytes)
+              uint32_t sum_L, size_t region, uint32_t node_cap, uint32_t edge_scap,
+              const uint32_t *__restrict__ bracket, uint32_t *__restrict__ nstar_out,
+              uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     const uint32_t C = blockDim.x;
-    const SmemPtrs sm = smem_ptrs(dyn, smem_L, node_cap, smem_window_bytes(C));
+    const SmemPtrs sm = smem_ptrs_sum(dyn, region, node_cap, smem_window_bytes(C));
     const WinPtrs wp = win_ptrs(reinterpret_cast<unsigned char *>(sm.nodes) + smem_nodes_bytes(node_cap), C);
     __shared__ Ctl c;
     __shared__ SmaxShared x;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
-    const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L);
+    const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L, max_L > sum_L, false);
     const EdgeList E{sm.edges, edge_scap, sp.gedges};
     const Nodes P{sp.P, static_cast<uint32_t>(__cvta_generic_to_shared(sm.nodes)), node_cap};
     const Nodes PA{sp.P, P.sbase, node_cap + static_cast<uint32_t>(smem_window_bytes(C) / 4)};  // first pass
-    unsigned long long tot_passes = 0, tot_probe = 0, tot_fb = 0, tot_ok = 0, tot_chunks = 0;
-    unsigned long long cyc_setup = 0, cyc_first = 0, cyc_back = 0;
+    // per-CTA counters, kept in shared memory (thread 0 updates them) rather than in registers
+    __shared__ unsigned long long tot_passes, tot_probe, tot_fb, tot_ok, tot_chunks;
+    __shared__ unsigned long long cyc_setup, cyc_first, cyc_back, cyc_span;
+    if (threadIdx.x == 0) tot_passes = tot_probe = tot_fb = tot_ok = tot_chunks = cyc_setup = cyc_first = cyc_back = cyc_span = 0;
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1850,11 +2182,12 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
         }
         const uint32_t N = static_cast<uint32_t>(num_sites(L));
         const bool smem_bm = L <= smem_L;
-        uint32_t *bm = smem_bm ? sm.sbm : sp.gbm;
-        const uint32_t words = bm_words(N);
-        for (uint32_t w = threadIdx.x; w < words; w += C) bm[w] = 0u;
-        build_rows(mask, L, sm.rows, sm.scratch, c);
-        if (smem_bm && L == kPlaneL) build_planes16(sm.rows, c.R, sm.planes, sm.scratch, c);
+        uint32_t *bm, *sum;
+        sample_bm_sum(sm, sp, L, smem_L, sum_L, bm, sum);
+        sample_tables(c, sm, bm, sum, L, mask, smem_bm);
+        // scan tables of the on-chip bitmap paths and of the summary paths
+        const ScanTabs Tb{sm.rows, sm.planes, nullptr, nullptr, nullptr};
+        const ScanTabs Ts{nullptr, nullptr, sm.tab, sm.d5m, sum};
         if (threadIdx.x == 0) {
             nd_st(PA, 0u, 0u);  // for the first pass
             nd_st(PA, 1u, 1u);
@@ -1868,7 +2201,7 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
         const FastDiv fd = make_fastdiv(L);
         __syncthreads();
         const long long t_first = clock64();
-        cyc_setup += static_cast<unsigned long long>(t_first - t_setup);
+        if (threadIdx.x == 0) cyc_setup += static_cast<unsigned long long>(t_first - t_setup);
 
         // the start: the bracket's lower end minus one, which must not span
         uint32_t n_s = 0, blo = 0, bhi = 0, npass = 0;
@@ -1879,30 +2212,36 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
             if (blo >= 1u && blo <= bhi && bhi <= N) {
                 n_s = blo - 1u;
                 have_br = true;
-            } else {
+            } else if (threadIdx.x == 0) {
                 ++tot_fb;
             }
         }
         if (n_s > 0u) {
-            bitmap_update(bm, smp.perm, 0u, n_s);
+            if (smem_bm)
+                bitmap_update(bm, smp.perm, 0u, n_s);
+            else
+                bitmap_add_sum(bm, sum, smp.perm, 0u, n_s, fd);
             for (uint32_t r = threadIdx.x; r < n_s; r += C) nd_st(PA, r + 2u, r + 2u);
             __syncthreads();
             if (smem_bm && L == kPlaneL)
-                union_pass<true, true, true, false, true>(c, PA, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm,
-                                                          smp.rank, L, fd, 0u, n_s, 0u);
+                union_pass<true, true, kScanPlanes, false, true>(c, PA, nullptr, sm.sbm, Tb, E, smp.perm, smp.rank, L,
+                                                                 fd, 0u, n_s, 0u);
             else if (smem_bm)
-                union_pass<true, true, false, false, true>(c, PA, nullptr, sm.sbm, sm.rows, sm.planes, E, smp.perm,
-                                                           smp.rank, L, fd, 0u, n_s, 0u);
+                union_pass<true, true, kScanRows, false, true>(c, PA, nullptr, sm.sbm, Tb, E, smp.perm, smp.rank, L, fd,
+                                                               0u, n_s, 0u);
+            else if (L <= sum_L)
+                union_pass<false, true, kScanGroups, false, true>(c, PA, nullptr, bm, Ts, E, smp.perm, smp.rank, L, fd,
+                                                                  0u, n_s, 0u);
             else
-                union_pass<false, true, false, false, true>(c, PA, nullptr, bm, sm.rows, sm.planes, E, smp.perm,
-                                                            smp.rank, L, fd, 0u, n_s, 0u);
+                union_pass<false, true, kScanGroupsG, false, true>(c, PA, nullptr, bm, Ts, E, smp.perm, smp.rank, L, fd,
+                                                                   0u, n_s, 0u);
             __syncthreads();
             ++npass;
-            tot_probe += n_s;
+            if (threadIdx.x == 0) tot_probe += n_s;
             const bool span = nd_ld(PA, 1u) != 1u;
             lend_back(P, PA, n_s + 2u);  // (a barrier: every thread has read node 1)
             if (span) {                  // n* < the bracket's lower end: sweep from the start
-                ++tot_fb;
+                if (threadIdx.x == 0) ++tot_fb;
                 have_br = false;
                 n_s = 0u;
                 if (threadIdx.x == 0) {
@@ -1913,16 +2252,24 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
             }
         }
         uint32_t chunks = 0, ns;
-        cyc_first += static_cast<unsigned long long>(clock64() - t_first);
+        if (threadIdx.x == 0) cyc_first += static_cast<unsigned long long>(clock64() - t_first);
         if (smem_bm && L == kPlaneL)
-            ns = span_sweep<true, true>(c, x, P, bm, sm, wp, E, smp, fd, N, n_s, chunks, cyc_back, &hdr->status);
+            ns = span_sweep<true, kScanPlanes>(c, x, P, bm, sm, Tb, wp, E, smp, fd, N, n_s, chunks, cyc_back, cyc_span,
+                                               &hdr->status);
         else if (smem_bm)
-            ns = span_sweep<true, false>(c, x, P, bm, sm, wp, E, smp, fd, N, n_s, chunks, cyc_back, &hdr->status);
+            ns = span_sweep<true, kScanRows>(c, x, P, bm, sm, Tb, wp, E, smp, fd, N, n_s, chunks, cyc_back, cyc_span,
+                                             &hdr->status);
+        else if (L <= sum_L)
+            ns = span_sweep<false, kScanGroups>(c, x, P, bm, sm, Ts, wp, E, smp, fd, N, n_s, chunks, cyc_back, cyc_span,
+                                                &hdr->status);
         else
-            ns = span_sweep<false, false>(c, x, P, bm, sm, wp, E, smp, fd, N, n_s, chunks, cyc_back, &hdr->status);
+            ns = span_sweep<false, kScanGroupsG>(c, x, P, bm, sm, Ts, wp, E, smp, fd, N, n_s, chunks, cyc_back, cyc_span,
+                                                 &hdr->status);
         npass += chunks;
-        tot_chunks += chunks;
-        if (have_br && ns >= blo && ns <= bhi) ++tot_ok;
+        if (threadIdx.x == 0) {
+            tot_chunks += chunks;
+            if (have_br && ns >= blo && ns <= bhi) ++tot_ok;
+        }
         if (threadIdx.x == 0) {
             nstar_out[s] = ns;
             if (passes_out) passes_out[s] = npass;
@@ -1947,6 +2294,7 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
         atomicAdd(&stats->cyc_setup, cyc_setup);
         atomicAdd(&stats->cyc_update, cyc_first);
         atomicAdd(&stats->cyc_commit, cyc_back);
+        atomicAdd(&stats->cyc_union, cyc_span);
     }
 }
 
@@ -1957,6 +2305,8 @@ struct LaunchCfg {
     int threads = 0;
     size_t smem = 0;
     uint32_t smem_L = 0;
+    uint32_t sum_L = 0;   // summary kernels: largest side whose occupancy summary is in shared memory
+    size_t region = 0;    // summary kernels: bytes of the shared bitmap / summary region
     uint32_t node_cap = 0;
     uint32_t edge_scap = 0;
     uint32_t grid = 0;
@@ -1984,6 +2334,24 @@ int ensure_smem_attr(AttrSlot slot, const void *fn, size_t bytes)
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) != cudaSuccess)
         return PERC_ECUDA;
     g_attr_bytes[slot][dev] = bytes;
+    return PERC_OK;
+}
+
+static size_t g_dev_total[kCfgDevices];
+
+// Slot memory a launch on the current device may take (a fixed share of its memory, cached per
+// device so that the workspace query and the launch agree).
+static int slot_cap_bytes(size_t &cap)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kCfgDevices) return PERC_ECUDA;
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (!g_dev_total[dev]) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || total_b == 0) return PERC_ECUDA;
+        g_dev_total[dev] = total_b;
+    }
+    cap = g_dev_total[dev] / kSlotCapShare;
     return PERC_OK;
 }
 
@@ -2042,15 +2410,37 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool
     // goes to union-find nodes (up to kSmemNodes, keeping room for 512 edges) and then to the
     // shared part of the edge list.
     const size_t extra = (op == PERC_OP_SMAX || op == kOpSweep) ? smem_window_bytes(cfg.threads) : 0;
-    size_t base = smem_tables_bytes() + smem_bitmap_bytes(cfg.smem_L) + extra;
+    // The sweep, S_max windows and the mass pass keep one shared region for the bitmap of lattices
+    // up to smem_L or the occupancy summary of lattices up to sum_L (whose bitmap is global).  A
+    // batch whose largest side is above kSmemBitmapMaxL gives the region to summaries (and the rest
+    // to union-find nodes), unless it also reaches past kSumMixL (mixed batches), where the region of
+    // a side-16 bitmap also holds the summaries up to side 32.
+    const bool sum_op = op == PERC_OP_MASS || op == PERC_OP_SMAX || op == kOpSweep;
+    if (sum_op) cfg.smem_L = max_L <= kSmemBitmapMaxL ? max_L : (max_L > kSumMixL ? kPlaneL : 0u);
+    auto base_for = [&](uint32_t sL) {
+        return sum_op ? smem_tables_bytes() + smem_sum_tables_bytes() + region_bm_bytes(sL) + extra
+                      : smem_tables_bytes() + smem_bitmap_bytes(sL) + extra;
+    };
+    size_t base = base_for(cfg.smem_L);
     const size_t min_edges = size_t(kRowCand) * sizeof(uint32_t);  // table-building scratch
     int ctas = (65536 / (cfg.threads * 64)) > 0 ? 65536 / (cfg.threads * 64) : 1;
     while (ctas > 1 && size_t(optin) / ctas - 1024 < base + min_edges) --ctas;  // fewer, larger CTAs
     const size_t share = size_t(optin) / ctas - 1024;  // room for the static shared variables
     // a lattice whose bitmap does not fit beside the op's own arrays keeps it in global memory
-    while (cfg.smem_L > 1 && base + min_edges > share)
-        base = smem_tables_bytes() + smem_bitmap_bytes(--cfg.smem_L) + extra;
+    while (cfg.smem_L > (sum_op ? 0u : 1u) && base + min_edges > share) base = base_for(--cfg.smem_L);
     if (base + min_edges > share) return PERC_EINVAL;
+    cfg.sum_L = max_L;
+    if (sum_op) {
+        // summaries of lattices above smem_L: as large as fits beside a reserve for nodes and edges
+        cfg.region = region_bm_bytes(cfg.smem_L);
+        const size_t fixed = smem_tables_bytes() + smem_sum_tables_bytes() + extra + min_edges + kSumReserve;
+        const size_t room = std::max(cfg.region, share > fixed ? share - fixed : size_t(0));
+        cfg.sum_L = cfg.smem_L;
+        while (cfg.sum_L < max_L && sum_bytes(cfg.sum_L + 1) <= room) ++cfg.sum_L;
+        cfg.region = std::max(cfg.region, sum_bytes(cfg.sum_L));
+        base = smem_tables_bytes() + smem_sum_tables_bytes() + cfg.region + extra;
+        if (base + min_edges > share) return PERC_EINVAL;
+    }
     size_t room = share - base;
     size_t nodes = room > 512 * sizeof(uint2) ? (room - 512 * sizeof(uint2)) / 4 : 0;
     if (nodes > kSmemNodes) nodes = kSmemNodes;
@@ -2088,7 +2478,7 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool
         }
     }
     if (occ < 1) return PERC_EINVAL;
-    cfg.slot_bytes = slot_bytes_for(Ncap, max_L > cfg.smem_L, cfg.threads);
+    cfg.slot_bytes = slot_bytes_for(Ncap, max_L > cfg.smem_L, cfg.threads, max_L > cfg.sum_L ? max_L : 0u, op != kOpSweep);
     uint64_t grid = uint64_t(sms) * occ;
     const int cta_cap = env_int("PERC_MAX_CTAS", g_opt_max_ctas);
     if (cta_cap > 0 && uint64_t(cta_cap) < grid) grid = cta_cap;
@@ -2138,14 +2528,18 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool
             if (groups < 1) return PERC_EINVAL;
             if (groups > num) groups = num;
             cfg.slot_bytes = group_slot_bytes(Ncap, cfg.threads, cfg.members);
-            const uint64_t mem_groups = kSlotCapBytes / cfg.slot_bytes;
+            size_t cap_b = 0;
+            if (slot_cap_bytes(cap_b) != PERC_OK) return PERC_ECUDA;
+            const uint64_t mem_groups = cap_b / cfg.slot_bytes;
             if (groups > mem_groups) groups = mem_groups > 0 ? mem_groups : 1;
             cfg.grid = static_cast<uint32_t>(groups * members);
             return PERC_OK;
         }
     }
     if (grid > num) grid = num;
-    const uint64_t mem_cap = kSlotCapBytes / cfg.slot_bytes;
+    size_t cap_b = 0;
+    if (slot_cap_bytes(cap_b) != PERC_OK) return PERC_ECUDA;
+    const uint64_t mem_cap = cap_b / cfg.slot_bytes;
     if (grid > mem_cap) grid = mem_cap > 0 ? mem_cap : 1;
     cfg.grid = static_cast<uint32_t>(grid);
     return PERC_OK;
@@ -2204,9 +2598,10 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
     if (method == 2) {
         if (ws_bytes < cfg_ws_bytes(sw)) return PERC_EWORKSPACE;
         if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
-        k_nstar_sweep<<<sw.grid, sw.threads, sw.smem, stream>>>(samples, num_samples, max_L, sw.smem_L, sw.node_cap,
-                                                                sw.edge_scap, bracket, nstar, passes, stats,
-                                                                static_cast<char *>(workspace), sw.slot_bytes);
+        k_nstar_sweep<<<sw.grid, sw.threads, sw.smem, stream>>>(samples, num_samples, max_L, sw.smem_L, sw.sum_L,
+                                                                sw.region, sw.node_cap, sw.edge_scap, bracket, nstar,
+                                                                passes, stats, static_cast<char *>(workspace),
+                                                                sw.slot_bytes);
         return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
     }
     if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
@@ -2272,7 +2667,8 @@ extern "C" int perc_mass(const perc_sample *samples, uint32_t num_samples, uint3
     if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
-    k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap, cfg.edge_scap, n, mass,
+    k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.sum_L, cfg.region,
+                                                        cfg.node_cap, cfg.edge_scap, n, mass,
                                                         static_cast<char *>(workspace), cfg.slot_bytes);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }
@@ -2289,8 +2685,8 @@ extern "C" int perc_smax_window(const perc_sample *samples, uint32_t num_samples
     if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
-    k_smax<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap,
-                                                        cfg.edge_scap, n_lo, count, window, smax,
+    k_smax<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.sum_L, cfg.region,
+                                                        cfg.node_cap, cfg.edge_scap, n_lo, count, window, smax,
                                                         static_cast<char *>(workspace), cfg.slot_bytes);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }

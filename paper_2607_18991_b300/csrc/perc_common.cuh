@@ -181,7 +181,16 @@ uint32_t spin_limit();
 // Host-side per-device launch state (defined in perc_ccl.cu; thread-safe).  Kernel attributes such
 // as the dynamic shared-memory limit are set per device, so each is set once on every device that
 // launches the kernel.  Returns PERC_OK or PERC_ECUDA.
-enum AttrSlot { kAttrMlpGrad, kAttrRankScatter, kAttrRankScatterTma, kAttrTorusMass, kAttrTorusWrap, kAttrSlots };
+enum AttrSlot {
+    kAttrMlpGrad,
+    kAttrRankScatter,
+    kAttrRankScatterTma,
+    kAttrRankBCount,
+    kAttrRankBPlace,
+    kAttrTorusMass,
+    kAttrTorusWrap,
+    kAttrSlots
+};
 int ensure_smem_attr(AttrSlot slot, const void *fn, size_t bytes);
 // Resident CTAs of `fn` (threads, dynamic shared memory) times the SM count of the current device,
 // cached per (slot, device).

@@ -87,15 +87,17 @@ k_rank_hist(int pass, uint32_t N, uint32_t T, const uint64_t *__restrict__ seeds
     if (threadIdx.x < 256) hist[(size_t(s) * 256 + threadIdx.x) * T + tile] = h[threadIdx.x];
 }
 
-// Exclusive scan of one seed's 256*T counters (digit-major), one block per seed: rounds of
+// Exclusive scan of one seed's n counters (n a multiple of 4; the digit-major 256*T tile counts of
+// the radix passes, or the bucket counts of the bucket path), one block per seed: rounds of
 // 4 * blockDim consecutive counters, each thread reading four neighbours at once (coalesced 16-byte
-// loads; the row starts 1024-byte aligned), a block scan of the threads' sums and a running carry.
-__global__ void __launch_bounds__(1024) k_rank_scan(uint32_t T, uint32_t *__restrict__ hist)
+// loads; rows start 16-byte aligned), a block scan of the threads' sums and a running carry.  With
+// `copy`, the scanned row is also written there.
+__global__ void __launch_bounds__(1024) k_rank_scan(uint32_t n, uint32_t *__restrict__ hist, uint32_t *__restrict__ copy)
 {
     __shared__ uint32_t warp_sum[32];
     __shared__ uint32_t carry_s;
-    uint32_t *h = hist + size_t(blockIdx.x) * 256 * T;
-    const uint32_t n = 256u * T;  // a multiple of 4
+    uint32_t *h = hist + size_t(blockIdx.x) * n;
+    uint32_t *cp = copy ? copy + size_t(blockIdx.x) * n : nullptr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     uint32_t carry = 0;
     for (uint32_t base = 0; base < n; base += 4u * blockDim.x) {
@@ -133,6 +135,7 @@ __global__ void __launch_bounds__(1024) k_rank_scan(uint32_t T, uint32_t *__rest
             run += v.z;
             o.w = run;
             *reinterpret_cast<uint4 *>(h + i) = o;
+            if (cp) *reinterpret_cast<uint4 *>(cp + i) = o;
         }
         carry = carry_s;
         __syncthreads();  // warp_sum and carry_s are rewritten by the next round
@@ -305,15 +308,27 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  : "memory");
 }
 
+// Waits for the phase `parity` of the mbarrier, at most `limit` polls.  With the default limit a
+// poll is try_wait (the thread may be suspended until the phase completes or a hardware time limit
+// passes); a smaller limit (PERC_OPT_SPIN_LIMIT) polls with test_wait, which never suspends, so that
+// the wait can run out before a copy lands.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, uint32_t limit)
 {
+    const bool suspend = limit >= kSpinLimit;
     for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
+        if (suspend)
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(smem_u32(bar)), "r"(parity)
+                : "memory");
+        else
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(smem_u32(bar)), "r"(parity)
+                : "memory");
         if (done) return true;
     }
     return false;
@@ -466,6 +481,194 @@ k_rank_scatter_tma(int pass, uint32_t N, uint32_t T, uint32_t S, const uint32_t 
     // every copy a CTA issues is for a work item it consumes, so none is in flight at exit
 }
 
+// ------------------------------------------------------------------------------------------------
+// Bucket path (L^5 <= kBucketMaxN, which covers L <= 24).  The keys are uniform 32-bit values, so
+// their top B bits split a seed's sites into 2^B buckets of about 512 sites each; every bucket is
+// then sorted on its own, in shared memory:
+//   k_rank_bcount  per tile of kBTile sites: keys drawn, a shared-memory histogram of their buckets,
+//                  added into the seed's bucket counts (one global atomic per bucket and tile);
+//   k_rank_scan    exclusive scan of each seed's counts -> bucket starts (copied into the cursors);
+//   k_rank_bplace  per tile: keys drawn and kept in shared memory, each bucket's share of the tile
+//                  reserved with one atomicAdd on its cursor, every (key, site) record written into
+//                  its bucket;
+//   k_rank_bsort   per bucket: its records into shared memory, a counting sort on the next
+//                  kSubBits key bits (about half a record per sub-bucket), an insertion sort by
+//                  (key, site) inside each sub-bucket, then perm and rank written.
+// Records reach a bucket in no fixed order; the bucket sort orders them completely by (key, site),
+// so the result is the same order as the radix path's.  A bucket larger than kBCap (never seen:
+// about 512 sites are expected, and a Poisson count that exceeds 2048 has probability far below
+// 1e-100) is ordered by counting, for each record, the records before it: slow, exact at any size.
+// ------------------------------------------------------------------------------------------------
+constexpr uint32_t kBTileItems = 32;
+constexpr uint32_t kBTile = kRankThreads * kBTileItems;  // 16384 sites per tile
+constexpr uint32_t kBucketMaxBits = 14;
+constexpr uint64_t kBucketMaxN = uint64_t(512) << kBucketMaxBits;  // 8,388,608 sites
+constexpr uint32_t kBCap = 2048;
+constexpr uint32_t kSubBits = 10;
+constexpr uint32_t kSub = 1u << kSubBits;
+constexpr uint32_t kBSortThreads = 256;
+
+// Bucket bits B: the smallest with N / 2^B <= 512 (at most kBucketMaxBits).
+__host__ __device__ inline uint32_t bucket_bits(uint64_t N)
+{
+    uint32_t b = 0;
+    while (b < kBucketMaxBits && (N >> b) > 512u) ++b;
+    return b;
+}
+// Counters per seed: 2^B rounded up to a multiple of 4 (the scan reads four at a time).
+__host__ __device__ inline uint32_t bucket_row(uint32_t B) { return (1u << B) < 4u ? 4u : (1u << B); }
+
+__device__ __forceinline__ uint32_t bucket_of(uint32_t key, uint32_t B) { return B ? key >> (32u - B) : 0u; }
+
+__global__ void __launch_bounds__(kRankThreads)
+k_rank_bcount(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32_t *__restrict__ counts)
+{
+    extern __shared__ uint32_t bh[];  // [2^B]
+    const uint32_t s = blockIdx.y, nb = 1u << B;
+    for (uint32_t b = threadIdx.x; b < nb; b += kRankThreads) bh[b] = 0u;
+    __syncthreads();
+    const uint64_t seed = seeds[s];
+    const uint32_t e0 = blockIdx.x * kBTile;
+#pragma unroll 4
+    for (uint32_t k = 0; k < kBTileItems; ++k) {
+        const uint32_t e = e0 + k * kRankThreads + threadIdx.x;
+        if (e < N) atomicAdd(&bh[bucket_of(site_key(seed, e), B)], 1u);
+    }
+    __syncthreads();
+    uint32_t *row = counts + size_t(s) * bucket_row(B);
+    for (uint32_t b = threadIdx.x; b < nb; b += kRankThreads)
+        if (bh[b]) atomicAdd(row + b, bh[b]);
+}
+
+__global__ void __launch_bounds__(kRankThreads)
+k_rank_bplace(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32_t *__restrict__ cursors,
+              uint2 *__restrict__ recs)
+{
+    extern __shared__ uint32_t bh[];  // [2^B] counts, then this tile's places; then the tile's keys
+    uint32_t *keys = bh + (1u << B);
+    const uint32_t s = blockIdx.y, nb = 1u << B;
+    for (uint32_t b = threadIdx.x; b < nb; b += kRankThreads) bh[b] = 0u;
+    __syncthreads();
+    const uint64_t seed = seeds[s];
+    const uint32_t e0 = blockIdx.x * kBTile;
+#pragma unroll 4
+    for (uint32_t k = 0; k < kBTileItems; ++k) {
+        const uint32_t j = k * kRankThreads + threadIdx.x, e = e0 + j;
+        if (e < N) {
+            const uint32_t key = site_key(seed, e);
+            keys[j] = key;
+            atomicAdd(&bh[bucket_of(key, B)], 1u);
+        }
+    }
+    __syncthreads();
+    uint32_t *cur = cursors + size_t(s) * bucket_row(B);
+    for (uint32_t b = threadIdx.x; b < nb; b += kRankThreads)
+        if (bh[b]) bh[b] = atomicAdd(cur + b, bh[b]);  // this tile's first place in bucket b
+    __syncthreads();
+    uint2 *row = recs + size_t(s) * N;
+#pragma unroll 4
+    for (uint32_t k = 0; k < kBTileItems; ++k) {
+        const uint32_t j = k * kRankThreads + threadIdx.x, e = e0 + j;
+        if (e < N) {
+            const uint32_t key = keys[j];
+            row[atomicAdd(&bh[bucket_of(key, B)], 1u)] = make_uint2(key, e);
+        }
+    }
+}
+
+// (key, site) order of two records
+__device__ __forceinline__ bool rec_less(uint2 a, uint2 b) { return a.x < b.x || (a.x == b.x && a.y < b.y); }
+
+struct BSortSmem {
+    uint2 in[kBCap];
+    uint2 out[kBCap];
+    uint32_t start[kSub + 1];  // sub-bucket starts (exclusive scan of the counts), start[kSub] = size
+    uint32_t cur[kSub];
+    uint32_t wsum[kBSortThreads / 32];
+};
+
+__global__ void __launch_bounds__(kBSortThreads)
+k_rank_bsort(uint32_t N, uint32_t B, const uint32_t *__restrict__ starts, const uint2 *__restrict__ recs,
+             uint32_t *__restrict__ perm, uint32_t *__restrict__ rank_out)
+{
+    __shared__ BSortSmem S_;
+    const uint32_t s = blockIdx.y, b = blockIdx.x, nb = 1u << B;
+    const uint32_t *st = starts + size_t(s) * bucket_row(B);
+    const uint32_t lo = st[b], hi = b + 1u < nb ? st[b + 1u] : N, n = hi - lo;
+    const uint2 *in = recs + size_t(s) * N + lo;
+    uint32_t *po = perm + size_t(s) * N;
+    uint32_t *ro = rank_out + size_t(s) * N;
+    if (n > kBCap) {  // exact at any size: each record's place is the number of records before it
+        for (uint32_t j = threadIdx.x; j < n; j += kBSortThreads) {
+            const uint2 r = in[j];
+            uint32_t before = 0;
+            for (uint32_t i = 0; i < n; ++i) before += rec_less(in[i], r) ? 1u : 0u;
+            po[lo + before] = r.y;
+            ro[r.y] = lo + before;
+        }
+        return;
+    }
+    const uint32_t shift = 32u - B - kSubBits;
+    for (uint32_t q = threadIdx.x; q < kSub; q += kBSortThreads) S_.cur[q] = 0u;
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < n; j += kBSortThreads) {
+        const uint2 r = in[j];
+        S_.in[j] = r;
+        atomicAdd(&S_.cur[(r.x >> shift) & (kSub - 1u)], 1u);
+    }
+    __syncthreads();
+    // exclusive scan of the kSub counts: four consecutive per thread, then a block scan of the sums
+    constexpr uint32_t per = kSub / kBSortThreads;
+    uint32_t v[per], sum = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < per; ++q) {
+        v[q] = S_.cur[threadIdx.x * per + q];
+        sum += v[q];
+    }
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= static_cast<uint32_t>(o)) x += y;
+    }
+    if (lane == 31u) S_.wsum[warp] = x;
+    __syncthreads();
+    uint32_t run = x - sum;
+    for (uint32_t w = 0; w < warp; ++w) run += S_.wsum[w];
+#pragma unroll
+    for (uint32_t q = 0; q < per; ++q) {
+        S_.start[threadIdx.x * per + q] = run;
+        S_.cur[threadIdx.x * per + q] = run;
+        run += v[q];
+    }
+    if (threadIdx.x == 0) S_.start[kSub] = n;
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < n; j += kBSortThreads) {
+        const uint2 r = S_.in[j];
+        S_.out[atomicAdd(&S_.cur[(r.x >> shift) & (kSub - 1u)], 1u)] = r;
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < kSub; q += kBSortThreads) {  // insertion sort of each sub-bucket
+        const uint32_t a = S_.start[q], z = S_.start[q + 1u];
+        for (uint32_t j = a + 1u; j < z; ++j) {
+            const uint2 r = S_.out[j];
+            uint32_t i = j;
+            while (i > a && rec_less(r, S_.out[i - 1u])) {
+                S_.out[i] = S_.out[i - 1u];
+                --i;
+            }
+            S_.out[i] = r;
+        }
+    }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < n; j += kBSortThreads) {
+        const uint32_t site = S_.out[j].y;
+        po[lo + j] = site;
+        ro[site] = lo + j;
+    }
+}
+
 }  // namespace perc
 
 using namespace perc;
@@ -500,6 +703,28 @@ extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, 
     const bool use_tma = (N % 4u) == 0u && env_int_rank("PERC_RANK_TMA", 1) != 0;
     int *status = static_cast<int *>(workspace);
     if (cudaMemsetAsync(workspace, 0, 256, stream) != cudaSuccess) return PERC_ECUDA;
+    if (N <= kBucketMaxN && env_int_rank("PERC_RANK_BUCKET", 1) != 0) {
+        // bucket path: the records (8 bytes a site) take the radix path's key and value buffers, the
+        // bucket counts and cursors its histogram area
+        const uint32_t Bb = bucket_bits(N), nb = 1u << Bb, row = bucket_row(Bb);
+        const uint32_t Tb = static_cast<uint32_t>((N + kBTile - 1) / kBTile);
+        const size_t smem_count = size_t(nb) * 4, smem_place = size_t(nb) * 4 + size_t(kBTile) * 4;
+        if (ensure_smem_attr(kAttrRankBCount, reinterpret_cast<const void *>(k_rank_bcount), smem_count) != PERC_OK ||
+            ensure_smem_attr(kAttrRankBPlace, reinterpret_cast<const void *>(k_rank_bplace), smem_place) != PERC_OK)
+            return PERC_ECUDA;
+        uint2 *recs = reinterpret_cast<uint2 *>(a_keys);  // a_keys then a_vals: chunk * N * 8 bytes
+        for (uint32_t s0 = 0; s0 < num_seeds; s0 += chunk) {
+            const uint32_t S = min(chunk, num_seeds - s0);
+            uint32_t *counts = hist, *cursors = hist + size_t(S) * row;
+            if (cudaMemsetAsync(counts, 0, size_t(S) * row * 4, stream) != cudaSuccess) return PERC_ECUDA;
+            k_rank_bcount<<<dim3(Tb, S), kRankThreads, smem_count, stream>>>(uint32_t(N), Bb, seeds + s0, counts);
+            k_rank_scan<<<S, 1024, 0, stream>>>(row, counts, cursors);
+            k_rank_bplace<<<dim3(Tb, S), kRankThreads, smem_place, stream>>>(uint32_t(N), Bb, seeds + s0, cursors, recs);
+            k_rank_bsort<<<dim3(nb, S), kBSortThreads, 0, stream>>>(uint32_t(N), Bb, counts, recs, perm + size_t(s0) * N,
+                                                                   rank + size_t(s0) * N);
+        }
+        return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
+    }
     for (uint32_t s0 = 0; s0 < num_seeds; s0 += chunk) {
         const uint32_t S = min(chunk, num_seeds - s0);
         const uint64_t *sd = seeds + s0;
@@ -513,7 +738,7 @@ extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, 
             uint32_t *kout = (pass == 0 || pass == 2) ? a_keys : b_keys;
             uint32_t *vout = (pass == 0 || pass == 2) ? a_vals : b_vals;
             k_rank_hist<<<grid, kRankThreads, 0, stream>>>(pass, uint32_t(N), T, sd, kin, hist);
-            k_rank_scan<<<S, 1024, 0, stream>>>(T, hist);
+            k_rank_scan<<<S, 1024, 0, stream>>>(256u * T, hist, nullptr);
             if (pass > 0 && use_tma) {
                 const uint32_t work = T * S;
                 const uint32_t g = work < tma_ctas ? work : tma_ctas;

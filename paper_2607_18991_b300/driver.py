@@ -14,11 +14,22 @@ import torch
 
 from . import perc
 
-DEFAULT_BUDGET = 24 << 30  # bytes of perm + rank per chunk
+def default_budget() -> int:
+    """Bytes of perm + rank per chunk: a quarter of the device's memory, at most 64 GiB (the
+    launch's per-CTA slots take up to another quarter)."""
+    try:
+        total = torch.cuda.get_device_properties(torch.cuda.current_device()).total_memory
+    except Exception:
+        return 24 << 30
+    return int(min(64 << 30, total // 4))
 
 
-def _chunks(workload: np.ndarray, budget: int):
+DEFAULT_BUDGET = None  # resolved by default_budget() on first use
+
+
+def _chunks(workload: np.ndarray, budget: int | None):
     """Split sample indices so that the distinct (L, seed) orders of a chunk fit in `budget`."""
+    budget = budget or default_budget()
     # largest L first, then seed-major: the CTAs running at the same time share one site order,
     # which then stays in L2 while all its masks are processed
     order = np.lexsort((workload[:, 1], workload[:, 2], -workload[:, 0]))

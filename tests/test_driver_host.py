@@ -23,7 +23,7 @@ def check_chunks(w, budget):
 
 def test_one_chunk_when_everything_fits():
     w = workloads.samples(8, range(1, 128), range(1, 5))
-    chunks = check_chunks(w, driver.DEFAULT_BUDGET)
+    chunks = check_chunks(w, driver.default_budget())
     assert len(chunks) == 1
 
 

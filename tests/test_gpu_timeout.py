@@ -43,7 +43,7 @@ def test_group_barrier_wait_runs_out_then_exact():
 
 def test_rank_copy_wait_runs_out_then_exact():
     from paper_2607_18991_b300 import perc
-    L, seeds = 16, [3, 4, 5, 6]
+    L, seeds = 26, [3, 4]  # above L = 24 perc_rank takes the radix path with the tile copies
     ws = perc.Workspace()
     _limit(1)
     try:
