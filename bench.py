@@ -51,6 +51,10 @@ ANY_METRIC = ("samples/sec (exact n* for spanning along any of the 5 axes) at L=
 WRAP_METRIC = ("samples/sec (exact first wrapping n along x1, periodic boundaries) at L=16 over 127 "
                "neighborhoods")
 WRAP_SEEDS = 32
+L24_SEEDS = 128
+METRIC_L24 = "samples/sec (exact n*) at L=24 over 127 neighborhoods, learned vs plain bracket"
+MIXED_METRIC = ("samples/sec (exact n*) over a mixed batch of 4096 samples, L uniform in 10..40, random "
+                "neighborhoods, learned bracket, as one CUDA graph")
 PMAX_METRIC = ("samples/sec of P_max(p) curves (exact S_max(n) over the windows of n holding all but 1e-16 of "
                "each binomial, convolution at 16 p per neighborhood) at L=16 over 127 neighborhoods")
 
@@ -60,6 +64,23 @@ def rank_launches(L: int, num_seeds: int) -> int:
     and sort (L^5 <= 8,388,608) or the radix path's four histogram, scan and scatter passes."""
     per_chunk = 4 if L ** 5 <= 8_388_608 else 12
     return math.ceil(num_seeds / 64) * per_chunk
+
+
+def train_bracket(args):
+    """The bracket network, trained on plain n* of held-out seeds (1,000,001..) at the shapes of the
+    first two workloads: zone 1 at L = 8 and all 127 neighborhoods at L = 16."""
+    import torch
+
+    from paper_2607_18991_b300 import bracket as pbracket
+    from paper_2607_18991_b300 import driver
+    train_seeds = np.arange(1, args.train_seeds + 1) + 1_000_000
+    wl_train = np.concatenate([np.array([(8, 1, s) for s in range(1_000_001, 1_001_001)]),
+                               np.array([(16, m, int(s)) for m in MASKS for s in train_seeds])])
+    ns_train, _ = driver.nstar(wl_train)
+    params, losses = pbracket.train(wl_train[:, 0], wl_train[:, 1], ns_train, steps=args.train_steps,
+                                    lr=args.lr, seed=0)
+    torch.cuda.synchronize()
+    return params, losses
 
 
 def dist_env():
@@ -78,35 +99,39 @@ def workload_for(rank: int, num_seeds: int = NUM_SEEDS):
 # ------------------------------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline); workers are spawned, never forked
 # ------------------------------------------------------------------------------------------------
-def _oracle_seed(seed: int) -> int:
+def _oracle_seed(job) -> int:
     import oracle
+    L, seed = job
     perm, rk = oracle.rank(L, seed)
     for m in MASKS:
         oracle.nz(L, m, perm, rk)
     return len(MASKS)
 
 
-def _oracle_any_seed(seed: int) -> int:
+def _oracle_any_seed(job) -> int:
     import oracle
+    L, seed = job
     perm, rk = oracle.rank(L, seed)
     for m in MASKS:
         oracle.nstar_span(L, m, oracle.SPAN_ANY, perm, rk)
     return len(MASKS)
 
 
-def _oracle_wrap_seed(seed: int) -> int:
+def _oracle_wrap_seed(job) -> int:
     import oracle
+    L, seed = job
     perm, rk = oracle.rank(L, seed)
     for m in MASKS:
         oracle.nz_periodic(L, m, perm, rk, (), 0)
     return len(MASKS)
 
 
-def _oracle_pmax_seed(seed: int) -> int:
+def _oracle_pmax_seed(job) -> int:
     """P_max(p) of every neighborhood for one seed with the oracle: its sweep stopped at the end of
     the GPU's window of n, its binomial weights over all n, and their product."""
     import oracle
     from paper_2607_18991_b300 import workloads
+    L, seed = job
     N = L ** 5
     perm, rk = oracle.rank(L, seed)
     for m in MASKS:
@@ -120,14 +145,45 @@ def _oracle_pmax_seed(seed: int) -> int:
     return len(MASKS)
 
 
-def oracle_rate(seeds, workers: int, fn=_oracle_seed):
+def _oracle_row(job) -> int:
+    """One (L, mask, seed) row of a mixed batch with the oracle: its ranking and its sweep."""
+    import oracle
+    L, m, seed = job
+    perm, rk = oracle.rank(L, seed)
+    oracle.nz(L, m, perm, rk)
+    return 1
+
+
+def oracle_rate(seeds, workers: int, fn=_oracle_seed, L_=None):
+    """Samples/s of the oracle on the host cores: fn over jobs (L, seed) for each seed (or over the
+    given jobs when L_ is "rows"), in `workers` spawned processes."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
+    jobs = list(seeds) if L_ == "rows" else [(L if L_ is None else L_, int(s)) for s in seeds]
     t0 = time.perf_counter()
     with ctx.Pool(workers) as pool:
-        done = sum(pool.map(fn, list(seeds)))
+        done = sum(pool.map(fn, jobs))
     dt = time.perf_counter() - t0
     return done / dt, done, dt
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(jobs, workers: int, fn, what: str, rows: bool = False) -> dict:
+    """The oracle timed on the host cores (spawned workers), and on one core over the first job."""
+    rate, done, dt = oracle_rate(jobs, workers, fn, "rows" if rows else None)
+    one, done1, dt1 = oracle_rate(list(jobs)[:1], 1, fn, "rows" if rows else None)
+    return {"value": rate, "unit": "samples/s", "cores": workers, "kind": "oracle",
+            "cpu_model": cpu_model(), "single_core": {"value": one, "samples": done1, "s": dt1},
+            "sample": f"{what} ({done} samples) in {dt:.1f} s, {workers} spawned workers"}
 
 
 def source_sha256() -> str:
@@ -244,13 +300,7 @@ def run_ours(args):
 
     # ---- bracket network: trained on plain n* of held-out seeds at L = 8 (zone 1) and L = 16
     t_train = time.perf_counter()
-    train_seeds = np.arange(1, args.train_seeds + 1) + 1_000_000
-    wl_train = np.concatenate([np.array([(8, 1, s) for s in range(1_000_001, 1_001_001)]),
-                               np.array([(L, m, int(s)) for m in MASKS for s in train_seeds])])
-    ns_train, _ = driver.nstar(wl_train)
-    params, losses = pbracket.train(wl_train[:, 0], wl_train[:, 1], ns_train, steps=args.train_steps,
-                                    lr=args.lr, seed=0)
-    torch.cuda.synchronize()
+    params, losses = train_bracket(args)
     t_train = time.perf_counter() - t_train
 
     # ---- resident inputs: one preallocated step (seeds, orders, sample table, brackets, outputs)
@@ -275,7 +325,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         nb = max(perc.workspace_bytes(perc.OP_RANK, L, len(seeds)), perc.workspace_bytes(perc.OP_NSTAR, L, nl))
         if nb > ws_buf.numel():
-            step_obj.ws = ws_buf = torch.empty(nb, dtype=torch.uint8, device=dev)
+            step_obj.ws = ws_buf = perc.new_workspace(nb, dev)
 
     def step(learned: bool, ev=None):
         step_obj.run_rank()
@@ -452,32 +502,30 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        n_seeds_cpu = cpu_workers * args.cpu_seeds_per_worker
-        rate, done, dt = oracle_rate(range(1, n_seeds_cpu + 1), cpu_workers,
-                                     _oracle_any_seed if axes > 1 else _oracle_seed)
-        cpu = {"value": rate, "unit": "samples/s", "cores": cpu_workers, "kind": "oracle",
-               "sample": f"L=16, seeds 1..{n_seeds_cpu} x 127 masks ({done} samples) in {dt:.1f} s, "
-                         f"one ranking per seed, {cpu_workers} spawned workers"
-                         + (", one any-axis sweep (ten border flags) per sample" if axes > 1 else "")}
+        n_seeds_cpu = cpu_workers * (args.cpu_seeds_per_worker if L <= 16 else 1)
+        cpu = cpu_baseline(range(1, n_seeds_cpu + 1), cpu_workers, _oracle_any_seed if axes > 1 else _oracle_seed,
+                           f"L={L}, seeds 1..{n_seeds_cpu} x 127 masks, one ranking per seed"
+                           + (", one any-axis sweep (ten border flags) per sample" if axes > 1 else ""))
 
     # rank passes + bracket + nstar (+ the minimum over axes) per step
     gpu_launches = rank_launches(L, len(seeds)) + 2 + (1 if axes > 1 else 0)
     value = world * num / (ms_learned * 1e-3)
     if rank == 0:
         line = {
-            "metric": ANY_METRIC if axes > 1 else METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
-            "steps": args.steps,
+            "metric": ANY_METRIC if axes > 1 else (METRIC_L24 if L == 24 else METRIC), "value": value,
+            "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic (Philox-keyed site orders, seeds per rank)",
-            "config": {"workload": "all 127 neighborhoods, L=16 (1,048,576 sites), seeds 1..256 per rank, "
-                                   "32,512 samples/rank, one persistent launch"
+            "config": {"workload": f"all 127 neighborhoods, L={L} ({N:,} sites), seeds 1..{len(seeds)} per rank, "
+                                   f"{num:,} samples/rank, one persistent launch"
                                    + (" of 5 spanning axes per sample (162,560 sweeps), then the minimum over "
                                       "axes" if axes > 1 else ""),
                        "L": L, "masks": 127, "seeds_per_rank": int(len(seeds)), "samples_per_rank": num,
                        "spanning": "any of x1..x5" if axes > 1 else "x1",
                        "bracket": "learned", "margin": args.margin,
                        "method": "sweep (chunked Newman-Ziff replay)" if sweep else "bisection",
-                       "l2": "flushed (256 MiB write) between timed steps; site orders 2 GiB > L2",
+                       "l2": f"flushed (256 MiB write) between timed steps; site orders {8 * N * len(seeds) / 2**30:.1f} "
+                             "GiB > L2",
                        "parallelism": f"dp{world} (seed blocks, no collective)"},
             "plain": {"value": world * num / (ms_plain * 1e-3), "unit": "samples/s", "ms_per_step": ms_plain,
                       "ms_per_step_eager": ms_plain_eager, "ms_per_step_graph": ms_graph.get(False),
@@ -683,10 +731,8 @@ def run_pmax_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n_seeds_cpu = cpu_workers
-        rate, done, dt = oracle_rate(range(1, n_seeds_cpu + 1), cpu_workers, _oracle_pmax_seed)
-        cpu = {"value": rate, "unit": "samples/s", "cores": cpu_workers, "kind": "oracle",
-               "sample": f"L=16, seeds 1..{n_seeds_cpu} x 127 masks ({done} samples, 16 p each) in {dt:.1f} s, "
-                         f"one ranking per seed, {cpu_workers} spawned workers"}
+        cpu = cpu_baseline(range(1, n_seeds_cpu + 1), cpu_workers, _oracle_pmax_seed,
+                           f"L=16, seeds 1..{n_seeds_cpu} x 127 masks, 16 p each, one ranking per seed")
 
     gpu_launches = rank_launches(L, len(seeds)) + 3  # rank + weights + S_max + P_max
     value = world * num / (ms_step * 1e-3)
@@ -701,7 +747,8 @@ def run_pmax_ours(args):
                        "L": L, "masks": 127, "seeds_per_rank": int(len(seeds)), "samples_per_rank": num,
                        "p_per_sample": int(st.np), "window_max": int(st.window),
                        "window_mean": float(st.count[st.group].mean()),
-                       "l2": "flushed (256 MiB write) between timed steps; site orders 2 GiB > L2",
+                       "l2": f"flushed (256 MiB write) between timed steps; site orders {8 * N * len(seeds) / 2**30:.1f} "
+                             "GiB > L2",
                        "parallelism": f"dp{world} (seed blocks, no collective)"},
             "phases_ms": {"rank": ms_rank, "weights": ms_weights, "smax": ms_smax, "pmax": ms_pmax,
                           "step_eager": ms_eager, "step_graph": ms_graph},
@@ -747,7 +794,7 @@ def run_wrap_ours(args):
     st = driver.NstarStep(L, MASKS, seeds)  # site orders and the sample table (axis x1)
     num = st.num
     out = torch.empty(num, dtype=torch.int32, device=dev)
-    wsp = torch.empty(perc.workspace_bytes(perc.OP_PERIODIC, L, num), dtype=torch.uint8, device=dev)
+    wsp = perc.new_workspace(perc.workspace_bytes(perc.OP_PERIODIC, L, num), dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def run_wrap(samples_ptr):
@@ -821,10 +868,8 @@ def run_wrap_ours(args):
     e2e_ms = max_over_ranks(e2e_ms)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, done, dt = oracle_rate(range(1, cpu_workers + 1), cpu_workers, _oracle_wrap_seed)
-        cpu = {"value": rate, "unit": "samples/s", "cores": cpu_workers, "kind": "oracle",
-               "sample": f"L=16, seeds 1..{cpu_workers} x 127 masks ({done} samples) in {dt:.1f} s, one "
-                         f"displacement sweep per sample, {cpu_workers} spawned workers"}
+        cpu = cpu_baseline(range(1, cpu_workers + 1), cpu_workers, _oracle_wrap_seed,
+                           f"L=16, seeds 1..{cpu_workers} x 127 masks, one displacement sweep per sample")
     value = world * num / (ms_step * 1e-3)
     if rank == 0:
         line = {
@@ -853,6 +898,218 @@ def run_wrap_ours(args):
 
 
 # ------------------------------------------------------------------------------------------------
+# our arm, the mixed batch (4096 samples, L uniform in 10..40, random neighborhoods)
+# ------------------------------------------------------------------------------------------------
+MIXED_CPU_ROWS = 16  # oracle rows per step of the CPU baseline / reference arm (a bounded sample)
+
+
+def mixed_workload(rank: int):
+    from paper_2607_18991_b300 import workloads
+    wl = workloads.mixed4096().copy()
+    wl[:, 2] += rank * len(wl)  # every rank its own seeds (weak scaling)
+    return wl
+
+
+def run_mixed_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2607_18991_b300 import autotune
+    from paper_2607_18991_b300 import build as pbuild
+    from paper_2607_18991_b300 import driver, perc
+
+    pbuild.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    params, losses = train_bracket(args)
+    wl = mixed_workload(rank)
+    num = len(wl)
+    step = driver.BatchStep(wl, params=params, margin=args.margin)
+    tuned = None if args.no_tune else autotune.tune_batch(step, learned=True)
+    for learned in (True, False):
+        step.run(learned)
+    torch.cuda.synchronize()
+    graphs = {learned: step.capture(learned) for learned in (True, False)} if args.graph else {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(learned: bool, K: int, W: int) -> float:
+        go = graphs[learned].replay if learned in graphs else (lambda: step.run(learned))
+        for _ in range(W):
+            go()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(K):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            a.record(stream)
+            go()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / K
+
+    gpu_index = torch.cuda.current_device()
+    phys = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    smi_index = int(phys[gpu_index]) if phys and phys[0].strip().isdigit() else gpu_index
+    with ClockSampler(smi_index) as clk:
+        ms_learned = timed(True, args.steps, args.warmup)
+        ms_plain = timed(False, args.steps, args.warmup)
+    clocks = clk.summary()
+
+    # n* launches alone (eager, per chunk, with counters) for the roofline, and the results
+    out, alg_bytes, ms_nstar = {}, 0.0, 0.0
+    for learned in (True, False):
+        for k, ch in enumerate(step.chunks):
+            step.run_rank(k)
+            st = perc.new_stats()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step.run_nstar(k, learned, stats=st)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if learned:
+                d = perc.stats_dict(st)
+                Ls = wl[ch["idx"], 0].astype(np.float64)
+                if d["chunks"] > 0 or d["passes"] == 0:  # the sweep: one pass to n* per sample
+                    alg_bytes += float(np.sum(Ls ** 5 / 4 + 8 * Ls ** 4)) + 12 * d["new_sites"] + 8 * d["hooks"]
+                else:  # the bisection: every probe a pass
+                    mean_pass = float(np.mean(Ls ** 5 / 4 + 8 * Ls ** 4))
+                    alg_bytes += d["passes"] * mean_pass + 12 * d["probe_sites"] + 8 * d["hooks"]
+                ms_nstar += a.elapsed_time(b)
+        out[learned] = step.result()
+    assert np.array_equal(out[True][0], out[False][0]), "learned and plain n* differ"
+
+    # e2e: each step copies every chunk's sample table and seeds from pinned host memory, replays the
+    # learned graph and reads every chunk's n* back
+    host_in = [(ch["samples"].cpu().pin_memory(), [g["seeds"].cpu().pin_memory() for g in ch["groups"]])
+               for ch in step.chunks]
+    host_out = [torch.empty(ch["n"], dtype=torch.int32).pin_memory() for ch in step.chunks]
+    go = graphs[True].replay if True in graphs else (lambda: step.run(True))
+
+    def e2e_step():
+        for ch, (smp_h, seeds_h) in zip(step.chunks, host_in):
+            ch["samples"].copy_(smp_h, non_blocking=True)
+            for g, sh in zip(ch["groups"], seeds_h):
+                g["seeds"].copy_(sh, non_blocking=True)
+        go()
+        for ch, ho in zip(step.chunks, host_out):
+            ho.copy_(ch["nstar"], non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    e2e_ms /= args.steps
+    h2d = sum(smp.numel() * 8 + sum(x.numel() * 8 for x in sh) for smp, sh in host_in)
+    d2h = sum(ho.numel() * 4 for ho in host_out)
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms_learned, ms_plain, e2e_ms = max_over_ranks(ms_learned), max_over_ranks(ms_plain), max_over_ranks(e2e_ms)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    achieved = alg_bytes / (ms_nstar * 1e-3) / 1e9
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rows = [tuple(int(v) for v in r) for r in wl[:MIXED_CPU_ROWS]]
+        cpu = cpu_baseline(rows, max(1, min(host_cores(), MIXED_CPU_ROWS)), _oracle_row,
+                           f"the first {MIXED_CPU_ROWS} rows of the mixed batch, one ranking and one sweep each",
+                           rows=True)
+    n_launch = sum(rank_launches(g["L"], g["S"]) for ch in step.chunks for g in ch["groups"]) + 2 * len(step.chunks)
+    if rank == 0:
+        line = {
+            "metric": MIXED_METRIC, "value": world * num / (ms_learned * 1e-3), "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (Philox-keyed site orders, seeds per rank)",
+            "config": {"workload": "mixed batch of 4096 samples: L uniform in 10..40, zone masks uniform in 1..127, "
+                                   "seed j+1 (numpy PCG64, seed 4096), one CUDA graph over all chunks",
+                       "samples_per_rank": num, "chunks": len(step.chunks), "bracket": "learned",
+                       "margin": args.margin, "l2": "flushed (256 MiB write) between timed steps; orders > L2",
+                       "parallelism": f"dp{world} (seed blocks, no collective)"},
+            "plain": {"value": world * num / (ms_plain * 1e-3), "unit": "samples/s", "ms_per_step": ms_plain},
+            "learned": {"ms_per_step": ms_learned, "nstar_ms": ms_nstar,
+                        "passes_per_sample": float(out[True][1].astype(np.float64).mean())},
+            "e2e": {"value": world * num / (e2e_ms * 1e-3), "unit": "samples/s", "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "roofline": {"kernel": "k_nstar_sweep / k_nstar_group (learned, all chunks)", "bound": "hbm",
+                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": None, "algorithmic_bytes_per_launch": alg_bytes,
+                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+            "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": n_launch,
+            "autotune": None if tuned is None else [{k: c[k] for k in ("method", "group", "ms")} for c in tuned],
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------------
+# on-chip peaks (python bench.py --peaks): L2 and shared-memory bandwidth, shared and L2 atomics
+# ------------------------------------------------------------------------------------------------
+def run_peaks(args):
+    import torch
+
+    from paper_2607_18991_b300 import build as pbuild
+    from paper_2607_18991_b300 import perc
+
+    pbuild.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    probes = [("l2_read", perc.MB_L2_READ, 64 << 20, 20, 1e9, "GB/s"),
+              ("smem_read", perc.MB_SMEM_READ, 1 << 20, 400, 1e9, "GB/s"),
+              ("smem_atomic_add", perc.MB_SMEM_ATOMIC, 1 << 20, 2000, 1e9, "Gop/s"),
+              ("smem_atomic_cas", perc.MB_SMEM_CAS, 1 << 20, 2000, 1e9, "Gop/s"),
+              ("l2_atomic_add", perc.MB_L2_ATOMIC, 16 << 20, 200, 1e9, "Gop/s")]
+    out = {}
+    gpu = torch.cuda.current_device()
+    with ClockSampler(gpu) as clk:
+        for name, which, nbytes, iters, scale, unit in probes:
+            buf = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+            perc.microbench(which, buf, iters)  # warm-up (and brings buf into L2)
+            best = None
+            for _ in range(5):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                units = perc.microbench(which, buf, iters)
+                b.record(stream)
+                torch.cuda.synchronize()
+                rate = units / (a.elapsed_time(b) * 1e-3) / scale
+                best = rate if best is None else max(best, rate)
+            out[name] = {"value": best, "unit": unit, "buffer_bytes": nbytes, "iters": iters}
+    out["clocks"] = clk.summary()
+    out["device"] = torch.cuda.get_device_name()
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------------------------------------
 # reference arm: the CPU oracle on the same workload
 # ------------------------------------------------------------------------------------------------
 def run_reference(args):
@@ -862,31 +1119,47 @@ def run_reference(args):
     workers = max(1, min(host_cores(), 32))
     per_step = workers  # one seed (127 samples) per worker per step
     pmax = args.workload == "pmax"
-    fn = {"pmax": _oracle_pmax_seed, "any": _oracle_any_seed, "wrap": _oracle_wrap_seed}.get(args.workload, _oracle_seed)
+    mixed = args.workload == "mixed"
+    fn = {"pmax": _oracle_pmax_seed, "any": _oracle_any_seed, "wrap": _oracle_wrap_seed,
+          "mixed": _oracle_row}.get(args.workload, _oracle_seed)
+    if mixed:  # each step a bounded sample: the next MIXED_CPU_ROWS rows of the batch
+        wl = mixed_workload(0)
+        per_step = MIXED_CPU_ROWS
+        workers = max(1, min(workers, per_step))
+        jobs = lambda k: [tuple(int(v) for v in r) for r in wl[k * per_step:(k + 1) * per_step]]
+    else:
+        jobs = lambda k: range(1 + k * per_step, 1 + (k + 1) * per_step)
     for w in range(args.warmup):
-        oracle_rate(range(1, min(per_step, 4) + 1), min(workers, 4), fn)
+        oracle_rate(list(jobs(0))[:min(per_step, 4)], min(workers, 4), fn, "rows" if mixed else None)
     rates, total_dt, total_done = [], 0.0, 0
     for k in range(args.steps):
-        s0 = 1 + k * per_step
-        rate, done, dt = oracle_rate(range(s0, s0 + per_step), workers, fn)
+        rate, done, dt = oracle_rate(jobs(k), workers, fn, "rows" if mixed else None)
         rates.append(rate)
         total_dt += dt
         total_done += done
     value = total_done / total_dt
+    metric = {"pmax": PMAX_METRIC, "any": ANY_METRIC, "wrap": WRAP_METRIC, "L24": METRIC_L24,
+              "mixed": MIXED_METRIC}.get(args.workload, METRIC)
+    if mixed:
+        what = (f"mixed batch of 4096 samples (L uniform in 10..40, random neighborhoods); each step a bounded "
+                f"sample of {per_step} of its rows, one ranking and one sweep each")
+    else:
+        what = (("P_max(p) curves (16 p at Table I p_c +- 2%), " if pmax else "") +
+                ("n* for spanning along any axis, " if args.workload == "any" else "") +
+                ("first wrapping n, periodic boundaries, " if args.workload == "wrap" else "") +
+                f"all 127 neighborhoods, L={L} ({L ** 5:,} sites); each step a bounded sample of "
+                f"{per_step} seeds x 127 masks")
     line = {
-        "impl": "reference", "metric": {"pmax": PMAX_METRIC, "any": ANY_METRIC, "wrap": WRAP_METRIC}.get(args.workload, METRIC),
+        "impl": "reference", "metric": metric,
         "value": value, "unit": "samples/s",
         "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (Philox-keyed site orders)",
-        "config": {"workload": ("P_max(p) curves (16 p at Table I p_c +- 2%), " if pmax else "") +
-                               ("n* for spanning along any axis, " if args.workload == "any" else "") +
-                               ("first wrapping n, periodic boundaries, " if args.workload == "wrap" else "") +
-                               "all 127 neighborhoods, L=16 (1,048,576 sites); each step a bounded sample of "
-                               f"{per_step} seeds x 127 masks", "L": L, "masks": 127},
+        "config": {"workload": what} if mixed else {"workload": what, "L": L, "masks": 127},
         "cpu_baseline": {"value": value, "unit": "samples/s", "cores": workers, "kind": "oracle",
-                         "sample": f"{args.steps} steps x {per_step} seeds x 127 masks at L=16"},
+                         "cpu_model": cpu_model(),
+                         "sample": f"{args.steps} steps x {per_step} " + ("rows" if mixed else f"seeds x 127 masks at L={L}")},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -907,20 +1180,32 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
     ap.add_argument("--no-graph", dest="graph", action="store_false", help="do not time CUDA-graph replays")
-    ap.add_argument("--workload", default="nstar", choices=["nstar", "pmax", "any", "wrap"],
-                    help="nstar: the n* samples/s line (default); pmax: the P_max(p) path; any: n* for "
+    ap.add_argument("--workload", default="nstar", choices=["nstar", "L24", "mixed", "pmax", "any", "wrap"],
+                    help="nstar: the n* samples/s line (default); L24: the same at L = 24 (128 seeds); mixed: "
+                         "4096 samples with L in 10..40 as one CUDA graph; pmax: the P_max(p) path; any: n* for "
                          "spanning along any of the five axes; wrap: first wrapping n with periodic boundaries")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the on-chip peaks (L2 and shared-memory bandwidth, atomics) and exit")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one learned and one plain step inside a profiler range and exit")
     args = ap.parse_args()
+    global L
+    if args.workload == "L24":
+        L = 24
+        if args.num_seeds == NUM_SEEDS:
+            args.num_seeds = L24_SEEDS
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.peaks:
+        run_peaks(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "pmax":
         run_pmax_ours(args)
     elif args.workload == "wrap":
         run_wrap_ours(args)
+    elif args.workload == "mixed":
+        run_mixed_ours(args)
     else:
         run_ours(args)
 

@@ -18,12 +18,15 @@
  * Conventions for every entry point:
  *   - Pointers marked "device" are caller-owned device memory; "host" pointers are read during
  *     the call only.  The library never allocates device memory: the caller sizes the workspace
- *     with perc_workspace_bytes() and passes it in.
+ *     with perc_workspace_bytes() and passes it in.  The first 256 bytes of a workspace are its
+ *     header (the status word and a work queue): the caller zeroes them once after allocating it.
  *   - Every call that takes a stream only enqueues work on it and returns; it is capturable in a
  *     CUDA graph.  Arguments that the host can check are checked before any launch
  *     (PERC_EINVAL / PERC_EWORKSPACE).  Errors found on the device (a sample with an invalid L or
- *     mask, a bounded wait that ran out) are written to a status word in the workspace;
- *     perc_check() synchronises the stream and returns it.
+ *     mask, a bounded wait that ran out) are written to the status word in the workspace, which
+ *     keeps the first such error of all the calls made since the last perc_check() (so a batch of
+ *     calls can be checked once at its end); perc_check() synchronises the stream, returns the
+ *     status and clears it.
  *   - Returns PERC_OK (0) or a negative perc_status.
  */
 #ifndef PERC_H
@@ -338,6 +341,30 @@ int perc_mlp_train(float *params, float *m, float *v, float *grad, const float *
  * N = L^5, clamped to 1 <= lo <= hi <= N. */
 int perc_bracket(const float *params, const perc_sample *samples, uint32_t num_samples,
                  float margin, uint32_t *bracket, void *stream);
+
+/*
+ * perc_microbench -- on-chip throughput probes (not in the paper): the peaks that the n* kernels,
+ * which keep their data in shared memory and L2 rather than HBM, are measured against.  One launch
+ * of one probe over every SM on `stream`; the caller times it (CUDA events) and divides *units by
+ * the time.
+ *   which  PERC_MB_L2_READ      16-byte L2-only loads streaming `iters` times over buf (choose
+ *                               `bytes` well below the L2 size, after one warm-up launch); units
+ *                               = bytes read
+ *          PERC_MB_SMEM_READ    conflict-free 16-byte shared-memory loads; units = bytes read
+ *          PERC_MB_SMEM_ATOMIC  shared-memory atomicAdd, one word per lane; units = operations
+ *          PERC_MB_SMEM_CAS     shared-memory atomicCAS, one word per lane; units = operations
+ *          PERC_MB_L2_ATOMIC    atomicAdd on distinct words spread over buf; units = operations
+ *   buf    device scratch of `bytes` bytes (>= 4096; its contents are overwritten)
+ *   iters  passes / operations per thread (>= 1)
+ *   units  host double (output)
+ * Errors: PERC_EINVAL (unknown probe, null pointer, bytes < 4096, iters 0), PERC_ECUDA.
+ */
+#define PERC_MB_L2_READ 1
+#define PERC_MB_SMEM_READ 2
+#define PERC_MB_SMEM_ATOMIC 3
+#define PERC_MB_SMEM_CAS 4
+#define PERC_MB_L2_ATOMIC 5
+int perc_microbench(int which, void *buf, size_t bytes, uint32_t iters, double *units, void *stream);
 
 /* Human-readable name of a perc_status value. */
 const char *perc_status_string(int status);

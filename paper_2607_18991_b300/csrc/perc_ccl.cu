@@ -28,6 +28,7 @@
 //     an old node, so the committed forest stays valid;
 //   * a spanning probe stops as soon as node 1 is hooked (early exit), since span is decided.
 #include <algorithm>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <mutex>
@@ -2549,6 +2550,13 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool
 
 using namespace perc;
 
+// A launch resets its work queue; the status word keeps the first device-side error since the last
+// perc_check (the caller zeroes the header once when it allocates the workspace).
+static cudaError_t reset_queue(void *workspace, cudaStream_t stream)
+{
+    return cudaMemsetAsync(static_cast<char *>(workspace) + offsetof(WsHeader, queue), 0, sizeof(uint32_t), stream);
+}
+
 // Workspace of a launch: the header and one slot per sample in flight -- per CTA, or per group of
 // `members` CTAs for the cooperative group kernel (its CTAs share their group's slot).
 static size_t cfg_ws_bytes(const LaunchCfg &cfg)
@@ -2597,7 +2605,7 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     if (method == 2) {
         if (ws_bytes < cfg_ws_bytes(sw)) return PERC_EWORKSPACE;
-        if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
+        if (reset_queue(workspace, stream) != cudaSuccess) return PERC_ECUDA;
         k_nstar_sweep<<<sw.grid, sw.threads, sw.smem, stream>>>(samples, num_samples, max_L, sw.smem_L, sw.sum_L,
                                                                 sw.region, sw.node_cap, sw.edge_scap, bracket, nstar,
                                                                 passes, stats, static_cast<char *>(workspace),
@@ -2605,7 +2613,7 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
         return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
     }
     if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
-    if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
+    if (reset_queue(workspace, stream) != cudaSuccess) return PERC_ECUDA;
     if (cfg.members > 1) {
         // every group's barrier counters, abort flag and shared scalars start at zero
         if (cudaMemset2DAsync(static_cast<char *>(workspace) + sizeof(WsHeader), cfg.slot_bytes, 0, sizeof(GroupState),
@@ -2666,7 +2674,7 @@ extern "C" int perc_mass(const perc_sample *samples, uint32_t num_samples, uint3
     if (rc != PERC_OK) return rc;
     if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
-    if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
+    if (reset_queue(workspace, stream) != cudaSuccess) return PERC_ECUDA;
     k_mass<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.sum_L, cfg.region,
                                                         cfg.node_cap, cfg.edge_scap, n, mass,
                                                         static_cast<char *>(workspace), cfg.slot_bytes);
@@ -2684,7 +2692,7 @@ extern "C" int perc_smax_window(const perc_sample *samples, uint32_t num_samples
     if (rc != PERC_OK) return rc;
     if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
-    if (cudaMemsetAsync(workspace, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
+    if (reset_queue(workspace, stream) != cudaSuccess) return PERC_ECUDA;
     k_smax<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.sum_L, cfg.region,
                                                         cfg.node_cap, cfg.edge_scap, n_lo, count, window, smax,
                                                         static_cast<char *>(workspace), cfg.slot_bytes);
@@ -2787,6 +2795,7 @@ extern "C" int perc_nstar_noalloc(const perc_sample *samples, uint32_t num_sampl
         if (!g_noalloc_ptr[dev]) {
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PERC_ECUDA;
+            if (cudaMemset(p, 0, sizeof(WsHeader)) != cudaSuccess) return PERC_ECUDA;  // status and queue
             g_noalloc_ptr[dev] = p;
         }
         ws = g_noalloc_ptr[dev];
@@ -2795,7 +2804,7 @@ extern "C" int perc_nstar_noalloc(const perc_sample *samples, uint32_t num_sampl
     if (slots == 0) return PERC_EWORKSPACE;  // max_L too large for the static scratch
     const uint32_t grid = cfg.grid < slots ? cfg.grid : static_cast<uint32_t>(slots);
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
-    if (cudaMemsetAsync(ws, 0, sizeof(WsHeader), stream) != cudaSuccess) return PERC_ECUDA;
+    if (reset_queue(ws, stream) != cudaSuccess) return PERC_ECUDA;
     k_nstar<<<grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.node_cap,
                                                      cfg.edge_scap, bracket, nstar, passes, stats,
                                                      static_cast<char *>(ws), cfg.slot_bytes);

@@ -189,6 +189,7 @@ enum AttrSlot {
     kAttrRankBPlace,
     kAttrTorusMass,
     kAttrTorusWrap,
+    kAttrMicrobench,
     kAttrSlots
 };
 int ensure_smem_attr(AttrSlot slot, const void *fn, size_t bytes);

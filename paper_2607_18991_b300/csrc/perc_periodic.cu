@@ -17,6 +17,8 @@
 // extending the forest of the largest n known not to wrap.
 #include <algorithm>
 
+#include <cstddef>
+
 #include "perc_common.cuh"
 
 namespace perc {
@@ -318,7 +320,10 @@ int torus_launch(const perc_sample *samples, uint32_t num, uint32_t max_L, const
                                  smem) != PERC_OK)
         return PERC_ECUDA;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
-    if (cudaMemsetAsync(workspace, 0, sizeof(PerHeader), stream) != cudaSuccess) return PERC_ECUDA;
+    // the queue starts again; the status word keeps the first error since the last perc_check
+    if (cudaMemsetAsync(static_cast<char *>(workspace) + offsetof(PerHeader, queue), 0, sizeof(uint32_t), stream) !=
+        cudaSuccess)
+        return PERC_ECUDA;
     const uint32_t smem_L = smem ? max_L : 0u;
     k_torus<kWrap><<<grid, kPerThreads, smem, stream>>>(samples, num, max_L, smem_L, n, mass, nstar,
                                                         static_cast<char *>(workspace), slot);

@@ -488,23 +488,23 @@ k_rank_scatter_tma(int pass, uint32_t N, uint32_t T, uint32_t S, const uint32_t 
 //   k_rank_bcount  per tile of kBTile sites: keys drawn, a shared-memory histogram of their buckets,
 //                  added into the seed's bucket counts (one global atomic per bucket and tile);
 //   k_rank_scan    exclusive scan of each seed's counts -> bucket starts (copied into the cursors);
-//   k_rank_bplace  per tile: keys drawn and kept in shared memory, each bucket's share of the tile
-//                  reserved with one atomicAdd on its cursor, every (key, site) record written into
-//                  its bucket;
+//   k_rank_bplace  per tile: keys drawn and kept in shared memory with their offsets among the
+//                  tile's keys of the same bucket, each bucket's share of the tile reserved with one
+//                  atomicAdd on its cursor, every (key, site) record written into its bucket;
 //   k_rank_bsort   per bucket: its records into shared memory, a counting sort on the next
-//                  kSubBits key bits (about half a record per sub-bucket), an insertion sort by
+//                  kSubBits key bits (about one record per sub-bucket), an insertion sort by
 //                  (key, site) inside each sub-bucket, then perm and rank written.
 // Records reach a bucket in no fixed order; the bucket sort orders them completely by (key, site),
 // so the result is the same order as the radix path's.  A bucket larger than kBCap (never seen:
-// about 512 sites are expected, and a Poisson count that exceeds 2048 has probability far below
+// about 512 sites are expected, and a Poisson count that exceeds 1536 has probability far below
 // 1e-100) is ordered by counting, for each record, the records before it: slow, exact at any size.
 // ------------------------------------------------------------------------------------------------
 constexpr uint32_t kBTileItems = 32;
 constexpr uint32_t kBTile = kRankThreads * kBTileItems;  // 16384 sites per tile
 constexpr uint32_t kBucketMaxBits = 14;
 constexpr uint64_t kBucketMaxN = uint64_t(512) << kBucketMaxBits;  // 8,388,608 sites
-constexpr uint32_t kBCap = 2048;
-constexpr uint32_t kSubBits = 10;
+constexpr uint32_t kBCap = 1536;
+constexpr uint32_t kSubBits = 9;
 constexpr uint32_t kSub = 1u << kSubBits;
 constexpr uint32_t kBSortThreads = 256;
 
@@ -544,8 +544,11 @@ __global__ void __launch_bounds__(kRankThreads)
 k_rank_bplace(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32_t *__restrict__ cursors,
               uint2 *__restrict__ recs)
 {
-    extern __shared__ uint32_t bh[];  // [2^B] counts, then this tile's places; then the tile's keys
+    // shared: [2^B] bucket counts of the tile, then the tile's first place in each bucket; the tile's
+    // keys; each key's offset among the tile's keys of its bucket (one shared atomic a key)
+    extern __shared__ uint32_t bh[];
     uint32_t *keys = bh + (1u << B);
+    uint16_t *loc = reinterpret_cast<uint16_t *>(keys + kBTile);
     const uint32_t s = blockIdx.y, nb = 1u << B;
     for (uint32_t b = threadIdx.x; b < nb; b += kRankThreads) bh[b] = 0u;
     __syncthreads();
@@ -557,7 +560,7 @@ k_rank_bplace(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32
         if (e < N) {
             const uint32_t key = site_key(seed, e);
             keys[j] = key;
-            atomicAdd(&bh[bucket_of(key, B)], 1u);
+            loc[j] = static_cast<uint16_t>(atomicAdd(&bh[bucket_of(key, B)], 1u));
         }
     }
     __syncthreads();
@@ -571,7 +574,7 @@ k_rank_bplace(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32
         const uint32_t j = k * kRankThreads + threadIdx.x, e = e0 + j;
         if (e < N) {
             const uint32_t key = keys[j];
-            row[atomicAdd(&bh[bucket_of(key, B)], 1u)] = make_uint2(key, e);
+            row[bh[bucket_of(key, B)] + loc[j]] = make_uint2(key, e);
         }
     }
 }
@@ -699,16 +702,18 @@ extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, 
         resident_ctas(kAttrRankScatterTma, reinterpret_cast<const void *>(k_rank_scatter_tma), kRankThreads,
                       sizeof(TmaScatterSmem), tma_ctas) != PERC_OK)
         return PERC_ECUDA;
-    // bulk-async tile loads need 16-byte aligned rows; the status word is the workspace header
-    const bool use_tma = (N % 4u) == 0u && env_int_rank("PERC_RANK_TMA", 1) != 0;
-    int *status = static_cast<int *>(workspace);
-    if (cudaMemsetAsync(workspace, 0, 256, stream) != cudaSuccess) return PERC_ECUDA;
+    // bulk-async tile loads need 16-byte aligned sources: rows of a multiple of 4 keys, and perm and
+    // rank (which passes 2 and 3 read) starting on 16-byte boundaries; otherwise the plain scatter
+    const bool aligned = ((reinterpret_cast<uintptr_t>(perm) | reinterpret_cast<uintptr_t>(rank) |
+                           reinterpret_cast<uintptr_t>(workspace)) & 15u) == 0u;
+    const bool use_tma = (N % 4u) == 0u && aligned && env_int_rank("PERC_RANK_TMA", 1) != 0;
+    int *status = static_cast<int *>(workspace);  // keeps the first error since the last perc_check
     if (N <= kBucketMaxN && env_int_rank("PERC_RANK_BUCKET", 1) != 0) {
         // bucket path: the records (8 bytes a site) take the radix path's key and value buffers, the
         // bucket counts and cursors its histogram area
         const uint32_t Bb = bucket_bits(N), nb = 1u << Bb, row = bucket_row(Bb);
         const uint32_t Tb = static_cast<uint32_t>((N + kBTile - 1) / kBTile);
-        const size_t smem_count = size_t(nb) * 4, smem_place = size_t(nb) * 4 + size_t(kBTile) * 4;
+        const size_t smem_count = size_t(nb) * 4, smem_place = size_t(nb) * 4 + size_t(kBTile) * 6;
         if (ensure_smem_attr(kAttrRankBCount, reinterpret_cast<const void *>(k_rank_bcount), smem_count) != PERC_OK ||
             ensure_smem_attr(kAttrRankBPlace, reinterpret_cast<const void *>(k_rank_bplace), smem_place) != PERC_OK)
             return PERC_ECUDA;

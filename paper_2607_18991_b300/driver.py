@@ -354,7 +354,7 @@ class NstarStep:
         self.nstar_any = torch.empty(self.num, dtype=torch.int32, device="cuda") if A > 1 else None
         nb = max(perc.workspace_bytes(perc.OP_RANK, self.L, S),
                  perc.workspace_bytes(perc.OP_NSTAR, self.L, self.launch_num))
-        self.ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        self.ws = perc.new_workspace(nb)
         self.lib = perc.lib()
 
     def run_rank(self, stream=None):
@@ -401,6 +401,147 @@ class NstarStep:
         return perc.u32(self.nstar), perc.u32(self.passes)
 
 
+def _align256(b: int) -> int:
+    return (b + 255) & ~255
+
+
+def chunk_layout(sub: np.ndarray):
+    """Where the site orders of one chunk's rows (L, zone word, seed) go in a shared order buffer:
+    per distinct side L (largest first) its distinct seeds, a perm block [S][L^5] at byte `off` and a
+    rank block at `roff`, each 256-byte aligned (the ranking's tile copies read 16-byte aligned
+    rows).  Returns (groups, perm offset of each row, rank offset of each row, bytes used)."""
+    off = 0
+    perm_rel = np.zeros(len(sub), dtype=np.uint64)
+    rank_rel = np.zeros(len(sub), dtype=np.uint64)
+    groups = []
+    for L in sorted(set(int(x) for x in sub[:, 0]), reverse=True):
+        sel = np.nonzero(sub[:, 0] == L)[0]
+        seeds = np.unique(sub[sel, 2])
+        N, S = L ** 5, len(seeds)
+        row = np.searchsorted(seeds, sub[sel, 2]).astype(np.uint64)
+        roff = _align256(off + 4 * N * S)
+        perm_rel[sel] = np.uint64(off) + row * np.uint64(4 * N)
+        rank_rel[sel] = np.uint64(roff) + row * np.uint64(4 * N)
+        groups.append({"L": L, "S": S, "off": off, "roff": roff, "seeds": seeds})
+        off = _align256(roff + 4 * N * S)
+    return groups, perm_rel, rank_rel, off
+
+
+class BatchStep:
+    """n* for an arbitrary batch of (L, zone word, seed) rows -- mixed L allowed -- as one
+    fixed-shape step.
+
+    The batch is split into chunks whose site orders fit the memory budget (largest lattices
+    first, every (L, seed) order ranked once per chunk).  Every device buffer is allocated here:
+    one order buffer that every chunk reuses, each chunk's seeds, sample table, brackets and
+    outputs, and one workspace.  ``run`` therefore only enqueues library calls -- per chunk
+    perc_rank of its orders, perc_bracket and perc_nstar -- with no host synchronisation between
+    chunks, and ``capture`` records the whole batch as one CUDA graph.  ``options`` holds per-chunk
+    launch options ({"method": METHOD_*, "group": CTAs per sample}), as picked by
+    ``autotune.tune_batch``; they are set before each chunk's perc_nstar and restored after.
+    """
+
+    def __init__(self, workload, params: torch.Tensor | None = None, margin: float = 0.0,
+                 budget: int | None = None, options=None):
+        self.workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
+        self.num = len(self.workload)
+        self.params = params
+        self.margin = float(margin)
+        self.lib = perc.lib()
+        self.chunks = []
+        order_bytes = 0
+        for idx in _chunks(self.workload, budget):
+            groups, perm_rel, rank_rel, nbytes = chunk_layout(self.workload[idx])
+            for g in groups:
+                g["seeds"] = torch.as_tensor(g["seeds"].astype(np.int64), device="cuda")
+            sub = self.workload[idx]
+            self.chunks.append({"idx": idx, "max_L": int(sub[:, 0].max()), "n": len(idx), "groups": groups,
+                                "rel": (sub[:, 0], sub[:, 1], perm_rel, rank_rel)})
+            order_bytes = max(order_bytes, nbytes)
+        self.orders = torch.empty(max(order_bytes, 16) // 4 + 4, dtype=torch.int32, device="cuda")
+        base = np.uint64(self.orders.data_ptr())
+        for ch in self.chunks:
+            Ls, words, pp, rp = ch.pop("rel")
+            ch["samples"] = perc.make_samples(Ls, words, pp + base, rp + base)
+            ch["bracket"] = torch.empty((ch["n"], 2), dtype=torch.int32, device="cuda")
+            ch["nstar"] = torch.empty(ch["n"], dtype=torch.int32, device="cuda")
+            ch["passes"] = torch.empty(ch["n"], dtype=torch.int32, device="cuda")
+        self.options = list(options) if options is not None else [None] * len(self.chunks)
+        self.ws = None
+        self._size_workspace()
+
+    def _apply(self, opt):
+        perc.set_launch_option(perc.OPT_METHOD, opt["method"] if opt else perc.METHOD_AUTO)
+        perc.set_launch_option(perc.OPT_GROUP, opt["group"] if opt else 0)
+
+    def _size_workspace(self):
+        nb = 16
+        for ch, opt in zip(self.chunks, self.options):
+            for g in ch["groups"]:
+                nb = max(nb, perc.workspace_bytes(perc.OP_RANK, g["L"], g["S"]))
+            self._apply(opt)
+            try:
+                nb = max(nb, perc.workspace_bytes(perc.OP_NSTAR, ch["max_L"], ch["n"]))
+            finally:
+                self._apply(None)
+        if self.ws is None or self.ws.numel() < nb:
+            self.ws = None
+            self.ws = perc.new_workspace(nb)
+
+    def set_options(self, options):
+        self.options = list(options)
+        self._size_workspace()
+
+    def run_rank(self, k: int, stream=None):
+        ch, sp = self.chunks[k], perc._stream(stream)
+        base = self.orders.data_ptr()
+        for g in ch["groups"]:
+            N = g["L"] ** 5
+            perc._ok(self.lib.perc_rank(g["L"], g["seeds"].data_ptr(), g["S"], base + g["off"], base + g["roff"],
+                                        self.ws.data_ptr(), self.ws.numel(), sp), "perc_rank")
+
+    def run_nstar(self, k: int, learned: bool, stats: torch.Tensor | None = None, stream=None):
+        ch, sp = self.chunks[k], perc._stream(stream)
+        if learned:
+            perc._ok(self.lib.perc_bracket(self.params.data_ptr(), ch["samples"].data_ptr(), ch["n"], self.margin,
+                                           ch["bracket"].data_ptr(), sp), "perc_bracket")
+        self._apply(self.options[k])
+        try:
+            perc._ok(self.lib.perc_nstar(ch["samples"].data_ptr(), ch["n"], ch["max_L"],
+                                         ch["bracket"].data_ptr() if learned else None, ch["nstar"].data_ptr(),
+                                         ch["passes"].data_ptr(), perc._ptr(stats), self.ws.data_ptr(),
+                                         self.ws.numel(), sp), "perc_nstar")
+        finally:
+            self._apply(None)
+
+    def run(self, learned: bool = True, stats: torch.Tensor | None = None, stream=None):
+        for k in range(len(self.chunks)):
+            self.run_rank(k, stream)
+            self.run_nstar(k, learned, stats, stream)
+
+    def capture(self, learned: bool = True) -> torch.cuda.CUDAGraph:
+        """CUDA graph of the whole batch (warm the library up with ``run`` first)."""
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(g, stream=s):
+            self.run(learned)
+        torch.cuda.current_stream().wait_stream(s)
+        return g
+
+    def result(self):
+        """(n*, passes) as numpy uint32 in workload order (synchronises; raises on a device error)."""
+        rc = self.lib.perc_check(self.ws.data_ptr(), perc._stream())
+        if rc != 0:
+            raise perc.PercError(rc, "perc_nstar device status")
+        nstar = np.zeros(self.num, dtype=np.uint32)
+        passes = np.zeros(self.num, dtype=np.uint32)
+        for ch in self.chunks:
+            nstar[ch["idx"]] = perc.u32(ch["nstar"])
+            passes[ch["idx"]] = perc.u32(ch["passes"])
+        return nstar, passes
+
+
 class PmaxStep:
     """Rank the seeds, build the binomial weights and compute P_max(p) for all (mask, seed) pairs at
     one L, each mask with its own row of probabilities (eq. Pmax with the binomial convolution).
@@ -437,7 +578,7 @@ class PmaxStep:
         self.smax = torch.empty((self.num, self.window), dtype=torch.int32, device="cuda")
         self.pmax = torch.empty((self.num, self.np), dtype=torch.float64, device="cuda")
         nb = max(perc.workspace_bytes(perc.OP_RANK, self.L, S), perc.workspace_bytes(perc.OP_SMAX, self.L, self.num))
-        self.ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        self.ws = perc.new_workspace(nb)
         self.lib = perc.lib()
 
     def run_rank(self, stream=None):

@@ -23,6 +23,7 @@ AXIS_SHIFT, NUM_AXES = 8, 5  # zone word: spanning axis in bits 8..10; axes x1..
 OPT_THREADS, OPT_SMEM_NODES, OPT_MAX_CTAS, OPT_GROUP, OPT_METHOD, OPT_SPIN_LIMIT = 1, 2, 3, 4, 5, 6
 METHOD_AUTO, METHOD_BISECTION, METHOD_SWEEP = 0, 1, 2
 MLP_NPARAM = 4931
+MB_L2_READ, MB_SMEM_READ, MB_SMEM_ATOMIC, MB_SMEM_CAS, MB_L2_ATOMIC = 1, 2, 3, 4, 5
 STATS_FIELDS = ("passes", "new_sites", "probe_sites", "hooks", "early_exits", "fallbacks",
                 "verified", "sites_merged", "unions", "cyc_setup", "cyc_update", "cyc_union",
                 "cyc_commit", "cyc_scan", "cyc_link", "chunks")
@@ -66,6 +67,7 @@ def lib() -> ctypes.CDLL:
         "perc_mlp_train": (i32, [vp, vp, vp, vp, vp, vp, u32, u32, u32, f32, vp, vp]),
         "perc_bracket": (i32, [vp, vp, u32, f32, vp, vp]),
         "perc_status_string": (ctypes.c_char_p, [i32]),
+        "perc_microbench": (i32, [i32, vp, sz, u32, ctypes.POINTER(ctypes.c_double), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -77,7 +79,7 @@ def lib() -> ctypes.CDLL:
 
 def exported_symbols() -> list[str]:
     return ["perc_workspace_bytes", "perc_rank", "perc_nstar", "perc_nstar_noalloc", "perc_nstar_min_axes", "perc_mass",
-            "perc_mass_periodic", "perc_nstar_wrap",
+            "perc_mass_periodic", "perc_nstar_wrap", "perc_microbench",
             "perc_smax_window", "perc_binomial_weights", "perc_pmax", "perc_check",
             "perc_mlp_forward", "perc_mlp_grad", "perc_adam", "perc_mlp_train", "perc_bracket",
             "perc_status_string", "perc_set_launch_option"]
@@ -109,6 +111,13 @@ def workspace_bytes(op: int, max_L: int, num: int) -> int:
     return int(lib().perc_workspace_bytes(op, max_L, num))
 
 
+def new_workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    """A workspace buffer of nbytes with its 256-byte header (status word, work queue) zeroed."""
+    buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    buf[:256].zero_()
+    return buf
+
+
 class Workspace:
     """Caller-owned scratch for the library, grown on demand (a torch uint8 tensor)."""
 
@@ -121,7 +130,7 @@ class Workspace:
             raise PercError(-1, "workspace size query")
         if self.buf is None or self.buf.numel() < nbytes:
             self.buf = None
-            self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.buf = new_workspace(nbytes, self.device)
         return self.buf
 
 
@@ -371,3 +380,12 @@ def bracket(params: torch.Tensor, samples: torch.Tensor, margin: float = 0.0, st
     _ok(lib().perc_bracket(params.data_ptr(), samples.data_ptr(), num, margin, br.data_ptr(),
                            _stream(stream)), "perc_bracket")
     return br
+
+
+def microbench(which: int, buf: torch.Tensor, iters: int, stream=None) -> float:
+    """perc_microbench: enqueue one on-chip throughput probe over buf; returns its units (bytes or
+    operations) -- the caller times the launch."""
+    units = ctypes.c_double()
+    _ok(lib().perc_microbench(which, buf.data_ptr(), buf.numel() * buf.element_size(), iters, ctypes.byref(units),
+                              _stream(stream)), "perc_microbench")
+    return units.value

@@ -63,6 +63,13 @@ def test_host_side_argument_checks_without_gpu():
     assert lib.perc_nstar_min_axes(1, 0, 5, 1, None) == -1
     assert lib.perc_nstar_min_axes(1, 4, 0, 1, None) == -1
     assert lib.perc_nstar_min_axes(1, 4, 6, 1, None) == -1
+    # perc_microbench: unknown probe, null buffer, too small, no iterations
+    import ctypes
+    u = ctypes.c_double()
+    assert lib.perc_microbench(9, 1, 1 << 20, 1, ctypes.byref(u), None) == -1
+    assert lib.perc_microbench(1, None, 1 << 20, 1, ctypes.byref(u), None) == -1
+    assert lib.perc_microbench(1, 1, 100, 1, ctypes.byref(u), None) == -1
+    assert lib.perc_microbench(1, 1, 1 << 20, 0, ctypes.byref(u), None) == -1
 
 
 def test_zone_word_layout():

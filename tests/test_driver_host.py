@@ -45,3 +45,24 @@ def test_mixed_sides_and_oversized_orders():
     big = workloads.samples(24, [1, 127], [1, 2])  # 8 * 24^5 bytes = 61 MiB per order
     chunks = check_chunks(big, 16 << 20)
     assert len(chunks) == 2 and all(len(c) == 2 for c in chunks)
+
+
+def test_batch_layout_aligned_and_disjoint():
+    """The shared order buffer of a captured batch: every perm and rank block starts on a 256-byte
+    boundary (the ranking's tile copies read 16-byte aligned rows, also after a side with odd L^5),
+    blocks do not overlap, and each row's pointers fall inside its own block."""
+    w = workloads.mixed4096()
+    for idx in driver._chunks(w, 4 << 30):
+        sub = w[idx]
+        groups, perm_rel, rank_rel, nbytes = driver.chunk_layout(sub)
+        spans = []
+        for g in groups:
+            N, S = g["L"] ** 5, g["S"]
+            assert g["off"] % 256 == 0 and g["roff"] % 256 == 0
+            spans += [(g["off"], g["off"] + 4 * N * S), (g["roff"], g["roff"] + 4 * N * S)]
+            sel = sub[:, 0] == g["L"]
+            rows = np.searchsorted(g["seeds"], sub[sel, 2])
+            assert np.array_equal(perm_rel[sel], g["off"] + 4 * N * rows)
+            assert np.array_equal(rank_rel[sel], g["roff"] + 4 * N * rows)
+        spans.sort()
+        assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:])) and spans[-1][1] <= nbytes

@@ -142,6 +142,7 @@ def test_automatic_groups_for_few_big_lattices():
 
 def test_groups_on_a_dirty_workspace():
     # the group barriers live in the workspace: a reused workspace full of stale bytes must not matter
+    # (except its 256-byte header, the status word and queue, which the caller zeroes once)
     import torch
 
     from paper_2607_18991_b300 import driver, perc
@@ -152,7 +153,9 @@ def test_groups_on_a_dirty_workspace():
         perc.set_launch_option(perc.OPT_GROUP, 2)
         for fill in (0xFF, 0x01, 0x00):
             p = driver.prepare(w, ws=ws)[0]
-            ws.get(perc.workspace_bytes(perc.OP_NSTAR, p.max_L, len(p.idx))).fill_(fill)
+            buf = ws.get(perc.workspace_bytes(perc.OP_NSTAR, p.max_L, len(p.idx)))
+            buf.fill_(fill)
+            buf[:256].zero_()
             ns, _ = perc.nstar(p.samples, p.max_L, ws=ws)
             assert np.array_equal(perc.u32(ns), want[p.idx]), fill
             assert perc.check(ws) == 0

@@ -76,17 +76,67 @@ def mixed_rows(w, per_band=((10, 20, 16), (21, 30, 12), (31, 40, 6)), seed=7):
     return np.array(sorted(pick))
 
 
-def test_mixed_batch_sampled():
-    """The whole mixed batch (4096 samples, L uniform in 10..40, random masks) in the launches the
-    benchmark runs, with the learned bracket; 34 rows drawn across L = 10..40 (6 above L = 30) are
-    compared with the oracle."""
-    from paper_2607_18991_b300 import driver, workloads
+@functools.lru_cache(maxsize=1)
+def mixed_want():
+    from paper_2607_18991_b300 import workloads
     w = workloads.mixed4096()
     pick = mixed_rows(w)
+    return pick, orc_nstar_threads(w[pick])
+
+
+def test_mixed_batch_sampled():
+    """The whole mixed batch (4096 samples, L uniform in 10..40, random masks) eagerly, chunk by
+    chunk, with the learned bracket; 34 rows drawn across L = 10..40 (6 above L = 30) are compared
+    with the oracle."""
+    from paper_2607_18991_b300 import driver, workloads
+    w = workloads.mixed4096()
+    pick, want = mixed_want()
     assert (w[pick, 0] > 30).sum() >= 4 and w[pick, 0].min() <= 12
-    want = orc_nstar_threads(w[pick])
     ns, _ = driver.nstar(w, params=quick_params(), margin=0.05)
     assert np.array_equal(ns[pick], want)
+
+
+def test_mixed_batch_graph_replay():
+    """The whole mixed batch as one CUDA graph: driver.BatchStep captures every chunk's ranking,
+    bracket and n* launch with no host synchronisation between chunks; the replay (outputs cleared
+    first) equals the eager run and the oracle on the sampled rows."""
+    import torch
+
+    from paper_2607_18991_b300 import driver, workloads
+    w = workloads.mixed4096()
+    pick, want = mixed_want()
+    step = driver.BatchStep(w, params=quick_params(), margin=0.05)
+    assert len(step.chunks) > 1
+    step.run(True)
+    torch.cuda.synchronize()
+    eager, _ = step.result()
+    g = step.capture(True)
+    for ch in step.chunks:
+        ch["nstar"].fill_(-1)
+    g.replay()
+    torch.cuda.synchronize()
+    replay, _ = step.result()
+    assert np.array_equal(replay, eager)
+    assert np.array_equal(replay[pick], want)
+
+
+def test_batch_tuner_picks_exact_options():
+    """The per-chunk tuner (n* method and CTAs per sample) on big lattices in small chunks: every
+    candidate gives the same n*, and the chosen options reproduce the oracle."""
+    import torch
+
+    from paper_2607_18991_b300 import autotune, driver, workloads
+    w = workloads.mixed4096()
+    rows = np.nonzero(w[:, 0] >= 30)[0][:12]
+    sub = w[rows]
+    step = driver.BatchStep(sub, params=quick_params(), margin=0.05, budget=3 << 30)
+    chosen = autotune.tune_batch(step, learned=True, use_cache=False)
+    assert len(chosen) == len(step.chunks) > 1
+    assert any(len(c["table"]) > 1 for c in chosen)  # some chunk had several candidates
+    step.run(True)
+    torch.cuda.synchronize()
+    ns, _ = step.result()
+    assert np.array_equal(ns, orc_nstar_threads(sub))
 
 
 FULL_SIZE_SEEDS = list(range(1, 257, 16))  # every 16th seed of 1..256
