@@ -17,9 +17,9 @@ binomial weights of 16 probabilities per neighborhood (p_c of Table I, +-2%), S_
 window of n outside which each binomial has less than 1e-16 on either side, and the convolution to
 P_max(p) (eq. Pmax).
 
-`--workload any` measures n* for spanning along any of the five axes: the same step with five
-samples per (mask, seed) (spanning axis x1..x5, each with its own verified bracket) in the n*
-launch, then perc_nstar_min_axes; a sample of the metric is one (mask, seed) pair.
+`--workload any` measures n* for spanning along any of the five axes: the same step with one
+perc_nstar_any sweep per (mask, seed), whose clusters carry ten face flags (two per axis), and a
+bracket network trained on the any-axis n* of held-out seeds.
 
 `--workload wrap` measures the periodic-boundary variant: one step = perc_rank of the seeds and
 perc_nstar_wrap (the first n at which a cluster wraps around the torus along x1, by bisection) over
@@ -66,9 +66,10 @@ def rank_launches(L: int, num_seeds: int) -> int:
     return math.ceil(num_seeds / 64) * per_chunk
 
 
-def train_bracket(args):
+def train_bracket(args, any_axis: bool = False):
     """The bracket network, trained on plain n* of held-out seeds (1,000,001..) at the shapes of the
-    first two workloads: zone 1 at L = 8 and all 127 neighborhoods at L = 16."""
+    first two workloads: zone 1 at L = 8 and all 127 neighborhoods at L = 16 (the any-axis n* of the
+    same rows for the any-axis workload)."""
     import torch
 
     from paper_2607_18991_b300 import bracket as pbracket
@@ -76,7 +77,7 @@ def train_bracket(args):
     train_seeds = np.arange(1, args.train_seeds + 1) + 1_000_000
     wl_train = np.concatenate([np.array([(8, 1, s) for s in range(1_000_001, 1_001_001)]),
                                np.array([(16, m, int(s)) for m in MASKS for s in train_seeds])])
-    ns_train, _ = driver.nstar(wl_train)
+    ns_train, _ = driver.nstar_any_sweep(wl_train) if any_axis else driver.nstar(wl_train)
     params, losses = pbracket.train(wl_train[:, 0], wl_train[:, 1], ns_train, steps=args.train_steps,
                                     lr=args.lr, seed=0)
     torch.cuda.synchronize()
@@ -296,17 +297,18 @@ def run_ours(args):
     ws = perc.Workspace(dev)
     seeds, wl = workload_for(rank, args.num_seeds)
     num = len(wl)
-    axes = 5 if args.workload == "any" else 1
+    any_axis = args.workload == "any"
+    axes = 1
 
     # ---- bracket network: trained on plain n* of held-out seeds at L = 8 (zone 1) and L = 16
     t_train = time.perf_counter()
-    params, losses = train_bracket(args)
+    params, losses = train_bracket(args, any_axis=any_axis)
     t_train = time.perf_counter() - t_train
 
     # ---- resident inputs: one preallocated step (seeds, orders, sample table, brackets, outputs)
     from paper_2607_18991_b300 import autotune
     N = L ** 5
-    step_obj = driver.NstarStep(L, MASKS, seeds, params=params, margin=args.margin, axes=axes)
+    step_obj = driver.NstarStep(L, MASKS, seeds, params=params, margin=args.margin, any_axis=any_axis)
     samples, br, ns, ps = step_obj.samples, step_obj.bracket, step_obj.nstar, step_obj.passes
     nl = step_obj.launch_num  # samples of the n* launch (num x axes)
     perm, rk, ws_buf = step_obj.perm, step_obj.rank, step_obj.ws
@@ -323,7 +325,8 @@ def run_ours(args):
         sub = samples[torch.as_tensor(few, device=dev)]
         tuned = autotune.tune(sub, L, bracket=br[torch.as_tensor(few, device=dev)])
         torch.cuda.synchronize()
-        nb = max(perc.workspace_bytes(perc.OP_RANK, L, len(seeds)), perc.workspace_bytes(perc.OP_NSTAR, L, nl))
+        nb = max(perc.workspace_bytes(perc.OP_RANK, L, len(seeds)),
+                 perc.workspace_bytes(perc.OP_NSTAR_ANY if any_axis else perc.OP_NSTAR, L, nl))
         if nb > ws_buf.numel():
             step_obj.ws = ws_buf = perc.new_workspace(nb, dev)
 
@@ -444,8 +447,9 @@ def run_ours(args):
                                ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_rank")
         perc._ok(lib.perc_bracket(params_d2.data_ptr(), samples_d2.data_ptr(), nl, args.margin, br.data_ptr(), sp),
                  "perc_bracket")
-        perc._ok(lib.perc_nstar(samples_d2.data_ptr(), nl, L, br.data_ptr(), ns.data_ptr(), None, None,
-                                ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_nstar")
+        perc._ok((lib.perc_nstar_any if any_axis else lib.perc_nstar)(
+            samples_d2.data_ptr(), nl, L, br.data_ptr(), ns.data_ptr(), None, None, ws_buf.data_ptr(),
+            ws_buf.numel(), sp), "perc_nstar")
         if axes > 1:
             perc._ok(lib.perc_nstar_min_axes(ns.data_ptr(), num, axes, step_obj.nstar_any.data_ptr(), sp),
                      "perc_nstar_min_axes")
@@ -498,30 +502,29 @@ def run_ours(args):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     achieved = alg_bytes / (ms_nstar_learned * 1e-3) / 1e9
-    traffic = measured_traffic(("any_" if axes > 1 else "") + ("sweep_" if sweep else "") + "learned_bytes_per_launch")
+    traffic = measured_traffic(("any_" if any_axis else "") + ("sweep_" if sweep else "") + "learned_bytes_per_launch")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n_seeds_cpu = cpu_workers * (args.cpu_seeds_per_worker if L <= 16 else 1)
-        cpu = cpu_baseline(range(1, n_seeds_cpu + 1), cpu_workers, _oracle_any_seed if axes > 1 else _oracle_seed,
+        cpu = cpu_baseline(range(1, n_seeds_cpu + 1), cpu_workers, _oracle_any_seed if any_axis else _oracle_seed,
                            f"L={L}, seeds 1..{n_seeds_cpu} x 127 masks, one ranking per seed"
-                           + (", one any-axis sweep (ten border flags) per sample" if axes > 1 else ""))
+                           + (", one any-axis sweep (ten border flags) per sample" if any_axis else ""))
 
     # rank passes + bracket + nstar (+ the minimum over axes) per step
     gpu_launches = rank_launches(L, len(seeds)) + 2 + (1 if axes > 1 else 0)
     value = world * num / (ms_learned * 1e-3)
     if rank == 0:
         line = {
-            "metric": ANY_METRIC if axes > 1 else (METRIC_L24 if L == 24 else METRIC), "value": value,
+            "metric": ANY_METRIC if any_axis else (METRIC_L24 if L == 24 else METRIC), "value": value,
             "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic (Philox-keyed site orders, seeds per rank)",
             "config": {"workload": f"all 127 neighborhoods, L={L} ({N:,} sites), seeds 1..{len(seeds)} per rank, "
                                    f"{num:,} samples/rank, one persistent launch"
-                                   + (" of 5 spanning axes per sample (162,560 sweeps), then the minimum over "
-                                      "axes" if axes > 1 else ""),
+                                   + (", one sweep per sample with ten face flags (perc_nstar_any)" if any_axis else ""),
                        "L": L, "masks": 127, "seeds_per_rank": int(len(seeds)), "samples_per_rank": num,
-                       "spanning": "any of x1..x5" if axes > 1 else "x1",
+                       "spanning": "any of x1..x5" if any_axis else "x1",
                        "bracket": "learned", "margin": args.margin,
                        "method": "sweep (chunked Newman-Ziff replay)" if sweep else "bisection",
                        "l2": f"flushed (256 MiB write) between timed steps; site orders {8 * N * len(seeds) / 2**30:.1f} "

@@ -60,6 +60,7 @@ typedef enum {
 #define PERC_OP_MASS 3
 #define PERC_OP_SMAX 4
 #define PERC_OP_PERIODIC 5 /* perc_mass_periodic and perc_nstar_wrap */
+#define PERC_OP_NSTAR_ANY 6 /* perc_nstar_any */
 
 /* zone_mask word of a sample: bits 0..6 select coordination zones 1..7 (at least one); bits 8..10
  * hold the spanning axis a = 0..4 that perc_nstar tests (borders x_{a+1} = 0 and x_{a+1} = L-1;
@@ -160,6 +161,20 @@ int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
  * Errors: PERC_EINVAL (null pointer, num 0, axes outside 1..5), PERC_ECUDA.
  */
 int perc_nstar_min_axes(const uint32_t *nstar, uint32_t num, uint32_t axes, uint32_t *out, void *stream);
+
+/*
+ * perc_nstar_any -- n* for spanning along any axis (the paper names no direction, Introduction): the
+ * smallest n at which one cluster touches both borders x_{a+1} = 0 and x_{a+1} = L-1 of some axis a,
+ * found by ONE Newman--Ziff sweep per sample in which every cluster carries ten face flags (two per
+ * axis) -- the clusters do not depend on the axis, only the border flags do -- instead of five
+ * per-axis sweeps and perc_nstar_min_axes.  The sample's axis bits are ignored.  Arguments,
+ * bracket verification (the sweep starts at lo - 1 after checking that no cluster of the first
+ * lo - 1 sites spans along any axis; a bracket that fails falls back to the sweep from 0) and errors
+ * are those of perc_nstar; the workspace is perc_workspace_bytes(PERC_OP_NSTAR_ANY, max_L, num).
+ */
+int perc_nstar_any(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                   const uint32_t *bracket, uint32_t *nstar, uint32_t *passes, perc_stats *stats,
+                   void *workspace, size_t ws_bytes, void *stream);
 
 /*
  * Periodic boundaries (a variant; the paper does not state its boundary conditions): offsets wrap

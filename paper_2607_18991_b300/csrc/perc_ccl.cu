@@ -510,8 +510,16 @@ struct SiteGeo {
     uint32_t a4;       // in-lattice d4 values (summary paths)
     uint32_t r0;       // row index i / L (summary group path)
     uint32_t sm0, sm1, sm2, sh, wbase;  // plane path only
-    bool low, high;    // on the low / high border of the spanning axis (x_{axis+1} = 0 / L-1)
+    bool low, high;    // on the low / high border of the spanning axis (x_{axis+1} = 0 / L-1); false
+                       // when the sample spans along any axis (axis kAnyAxis)
+    uint32_t faces;    // bit 2k: x_{k+1} = 0, bit 2k + 1: x_{k+1} = L-1, k = 0..4
 };
+
+// Spanning along any axis (perc_nstar_any): the border flags of a cluster are the ten face bits of
+// SiteGeo::faces, and a cluster spans once it holds both faces of some axis.
+constexpr uint32_t kAnyAxis = 5u;
+constexpr uint32_t kFaceLoBits = 0x155u;  // bit 2k of each axis k
+__host__ __device__ inline bool spans_any(uint32_t f) { return (f & (f >> 1) & kFaceLoBits) != 0u; }
 
 // A sample's zone_mask word: bits 0..6 the coordination zones, bits 8..10 the spanning axis 0..4,
 // every other bit zero.
@@ -537,9 +545,13 @@ __device__ __forceinline__ SiteGeo site_geo(uint32_t i, uint32_t L, const FastDi
         s.sm2 = (a4 & 16u) ? s.a5 : 0u;
         s.sh = (i + 30u) & 31u;
         s.wbase = (i + 30u) >> 5;
-        const uint32_t xa = (i >> (16u - 4u * axis)) & 15u;  // x_{axis+1}
-        s.low = xa == 0u;
-        s.high = xa == kPlaneL - 1u;
+        s.faces = 0u;
+        const uint32_t xs[5] = {x1, x2, x3, x4, x5};
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            s.faces |= ((xs[k] == 0u) ? 1u : 0u) << (2 * k) | ((xs[k] == kPlaneL - 1u) ? 2u : 0u) << (2 * k);
+        s.low = axis < kAnyAxis && ((s.faces >> (2u * axis)) & 1u);
+        s.high = axis < kAnyAxis && ((s.faces >> (2u * axis + 1u)) & 1u);
     } else {
         uint32_t x[5];
         site_coords(i, fd, x);
@@ -548,9 +560,12 @@ __device__ __forceinline__ SiteGeo site_geo(uint32_t i, uint32_t L, const FastDi
         s.a4 = (s.allowed >> 15) & 31u;
         s.r0 = uses_sum(kMode) ? fdiv(i, fd) : 0u;
         s.sm0 = s.sm1 = s.sm2 = s.sh = s.wbase = 0u;
-        const uint32_t xa = axis == 0u ? x[0] : axis == 1u ? x[1] : axis == 2u ? x[2] : axis == 3u ? x[3] : x[4];
-        s.low = xa == 0u;
-        s.high = xa == L - 1u;
+        s.faces = 0u;
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            s.faces |= ((x[k] == 0u) ? 1u : 0u) << (2 * k) | ((x[k] == L - 1u) ? 2u : 0u) << (2 * k);
+        s.low = axis < kAnyAxis && ((s.faces >> (2u * axis)) & 1u);
+        s.high = axis < kAnyAxis && ((s.faces >> (2u * axis + 1u)) & 1u);
     }
     return s;
 }
@@ -1626,7 +1641,7 @@ __device__ __forceinline__ void window_scan(const Ctl &c, const uint32_t *bm, co
     if (t >= count) return;
     const SiteGeo g = site_geo<kMode>(gshift ? __ldg(perm + b + t) : site, L, fd, c.axis);
     if (fl && gl == 0u) {
-        const uint32_t f = (g.low ? kFlagLo : 0u) | (g.high ? kFlagHi : 0u);
+        const uint32_t f = c.axis == kAnyAxis ? g.faces : (g.low ? kFlagLo : 0u) | (g.high ? kFlagHi : 0u);
         fl[t] = f;
         lp[t] = kRootBit | 4u | f;
     }
@@ -1750,10 +1765,12 @@ __device__ __forceinline__ uint32_t smem_addr(const uint32_t *q)
 
 // After chunk_front (all threads): each component's total -- border flags (n* sweep) or cluster
 // size (S_max windows) -- and its smallest forest node, then (after one block barrier) the chunk
-// written back to the forest, every component under one node: for the sweep node 0 if the
-// component touches x1 = 0, node 1 if it touches x1 = L-1, else its smallest node (so a cluster
-// touching a border keeps that border's node as its root); for S_max windows its smallest node,
-// which takes the component's size.  The caller's next block barrier orders the write-back.
+// written back to the forest, every component under one node: for the sweep along one axis node 0
+// if the component touches x1 = 0, node 1 if it touches x1 = L-1, else its smallest node (so a
+// cluster touching a border keeps that border's node as its root); for S_max windows its smallest
+// node, which takes the component's size in cnt; for the sweep along any axis (cnt = the forest's
+// face words, read here for the earlier clusters) its smallest node, whose face word store_faces
+// writes later.  The caller's next block barrier orders the write-back.
 template <bool kSpan>
 __device__ __forceinline__ void chunk_components(const Nodes &P, uint32_t *cnt, const WinPtrs &wp, uint32_t b,
                                                  uint32_t tn, uint32_t comp)
@@ -1771,15 +1788,15 @@ __device__ __forceinline__ void chunk_components(const Nodes &P, uint32_t *cnt, 
         const uint32_t g = wp.hkey()[h];
         if (g == kEmptySlot) continue;
         const uint32_t ch = cc_find(wp.cc(), C + h);
-        if (kSpan)
-            atomicOr(wp.tot() + ch, g == 0u ? kFlagLo : g == 1u ? kFlagHi : 0u);
+        if (kSpan)  // the earlier cluster's border flags: its root's face word, or the border root it is
+            atomicOr(wp.tot() + ch, cnt ? __ldcg(cnt + g) : g == 0u ? kFlagLo : g == 1u ? kFlagHi : 0u);
         else
             atomicAdd(wp.tot() + ch, wp.lp()[C + h] & ~kRootBit);
         atomicMin(wp.gm() + ch, g);
     }
     __syncthreads();
     auto root_of = [&](uint32_t cp) {
-        if (kSpan) {
+        if (kSpan && !cnt) {
             const uint32_t f = wp.tot()[cp];
             if (f & kFlagLo) return 0u;
             if (f & kFlagHi) return 1u;
@@ -1799,6 +1816,22 @@ __device__ __forceinline__ void chunk_components(const Nodes &P, uint32_t *cnt, 
             nd_st(P, g, r);
         else if (!kSpan)
             __stcg(cnt + g, wp.tot()[ch]);
+    }
+}
+
+// Sweep along any axis, after a chunk that does not span: each component's face word goes to its
+// root (its smallest forest node).  Kept out of chunk_components because the first-spanning-site
+// search of a spanning chunk reads the earlier clusters' face words as they were before the chunk.
+__device__ __forceinline__ void store_faces(uint32_t *gflags, const WinPtrs &wp, uint32_t b, uint32_t tn,
+                                            uint32_t comp)
+{
+    const uint32_t C = blockDim.x;
+    if (threadIdx.x < tn && wp.gm()[comp] == b + threadIdx.x + 2u) __stcg(gflags + wp.gm()[comp], wp.tot()[comp]);
+    for (uint32_t h = threadIdx.x; h < kRootHash; h += C) {
+        const uint32_t g = wp.hkey()[h];
+        if (g == kEmptySlot) continue;
+        const uint32_t ch = cc_find(wp.cc(), C + h);
+        if (wp.gm()[ch] == g) __stcg(gflags + g, wp.tot()[ch]);
     }
 }
 
@@ -1972,18 +2005,23 @@ __device__ __forceinline__ void pcc_unite(uint32_t *cc, uint32_t a, uint32_t b, 
 // is kept: a probe only adds the records of the sites between it and the probe, and a probe that
 // spans is undone from its log of hooked roots (in lp, which the sweep does not use), so the
 // records are united about twice in all instead of once per round.  sh: four words of shared
-// scratch.
-__device__ uint32_t first_span_site(const WinPtrs &wp, uint32_t tn, uint32_t *sh)
+// scratch.  With gflags (spanning along any axis) the flags are face words, the earlier clusters'
+// flags come from the forest's face words, and m spans when a root holds both faces of an axis.
+__device__ uint32_t first_span_site(const WinPtrs &wp, uint32_t tn, uint32_t *sh, const uint32_t *gflags)
 {
     const uint32_t C = blockDim.x;
     uint32_t *cc = wp.cc(), *ev = wp.ev(), *log = wp.lp();
     for (uint32_t y = threadIdx.x; y < C + kRootHash; y += C) cc[y] = y;
     if (threadIdx.x < 4) sh[threadIdx.x] = threadIdx.x < 2 ? 0u : kEmptySlot;
     __syncthreads();
-    for (uint32_t h = threadIdx.x; h < kRootHash; h += C) {  // the local slots of the border roots
+    for (uint32_t h = threadIdx.x; h < kRootHash; h += C) {
         const uint32_t g = wp.hkey()[h];
-        if (g <= 1u) sh[2 + g] = C + h;
+        if (gflags)  // any axis: the slot keeps its cluster's face word from here on (0: none)
+            wp.hkey()[h] = g == kEmptySlot ? 0u : __ldcg(gflags + g);
+        else if (g <= 1u)  // one axis: the local slots of the border roots
+            sh[2 + g] = C + h;
     }
+    if (gflags) __syncthreads();
     uint32_t lo = 0, hi = tn, round = 0;
     while (hi - lo > 1u) {
         const uint32_t m = (lo + hi) >> 1;
@@ -1996,12 +2034,20 @@ __device__ uint32_t first_span_site(const WinPtrs &wp, uint32_t tn, uint32_t *sh
         }
         __syncthreads();
         if (threadIdx.x < m) atomicOr(ev + pcc_find(cc, threadIdx.x), wp.fl()[threadIdx.x]);
-        if (threadIdx.x < 2u && sh[2 + threadIdx.x] != kEmptySlot) {
+        if (gflags) {  // earlier clusters that touch faces, reached by a site below m
+            for (uint32_t h = threadIdx.x; h < kRootHash; h += C) {
+                const uint32_t f = wp.hkey()[h];
+                if (!f) continue;
+                const uint32_t rt = pcc_find(cc, C + h);
+                if (rt < C) atomicOr(ev + rt, f);
+            }
+        } else if (threadIdx.x < 2u && sh[2 + threadIdx.x] != kEmptySlot) {
             const uint32_t rt = pcc_find(cc, sh[2 + threadIdx.x]);
             if (rt < C) atomicOr(ev + rt, threadIdx.x == 0u ? kFlagLo : kFlagHi);  // reached by a site below m
         }
         __syncthreads();
-        const bool span = __syncthreads_or(threadIdx.x < m && ev[threadIdx.x] == (kFlagLo | kFlagHi));
+        const uint32_t fe = threadIdx.x < m ? ev[threadIdx.x] : 0u;
+        const bool span = __syncthreads_or(gflags ? spans_any(fe) : fe == (kFlagLo | kFlagHi));
         const uint32_t nlog = *logn;
         for (uint32_t k = threadIdx.x; k < nlog; k += C) {
             const uint32_t b = log[k];
@@ -2025,7 +2071,8 @@ template <bool kSmemBm, int kMode>
 __device__ __forceinline__ uint32_t span_sweep(Ctl &c, SmaxShared &x, const Nodes &P, uint32_t *bm, const SmemPtrs &sm,
                                const ScanTabs &T, const WinPtrs &wp, const EdgeList &E, const perc_sample &smp,
                                const FastDiv &fd, uint32_t N, uint32_t n_s, uint32_t &chunks,
-                               unsigned long long &cyc_back, unsigned long long &cyc_span, int *status)
+                               unsigned long long &cyc_back, unsigned long long &cyc_span, int *status,
+                               uint32_t *gflags)
 {
     const uint32_t C = blockDim.x;
     if (kSmemBm) bm = sm.sbm;
@@ -2033,16 +2080,19 @@ __device__ __forceinline__ uint32_t span_sweep(Ctl &c, SmaxShared &x, const Node
     for (uint32_t b = n_s; b < N;) {
         ++chunks;
         uint32_t comp;
-        const uint32_t tn = chunk_front<kSmemBm, kMode, true>(c, x, P, nullptr, bm, T, wp, E, smp, fd, b, N, comp);
+        const uint32_t tn = chunk_front<kSmemBm, kMode, true>(c, x, P, gflags, bm, T, wp, E, smp, fd, b, N, comp);
         const long long t0 = clock64();
-        chunk_components<true>(P, nullptr, wp, b, tn, comp);
+        chunk_components<true>(P, gflags, wp, b, tn, comp);
         // only a component that spans at the end of the chunk can hold the first spanning site
-        const bool spans = threadIdx.x < tn && wp.tot()[comp] == (kFlagLo | kFlagHi);
+        const uint32_t f = threadIdx.x < tn ? wp.tot()[comp] : 0u;
+        const bool spans = gflags ? spans_any(f) : f == (kFlagLo | kFlagHi);
         uint32_t st = kEmptySlot;
         if (__syncthreads_or(spans)) {
             const long long t1 = clock64();
-            st = first_span_site(wp, tn, x.red);
+            st = first_span_site(wp, tn, x.red, gflags);
             if (threadIdx.x == 0) cyc_span += static_cast<unsigned long long>(clock64() - t1);
+        } else if (gflags) {
+            store_faces(gflags, wp, b, tn, comp);
         }
         if (threadIdx.x == 0) cyc_back += static_cast<unsigned long long>(clock64() - t0);
         for (uint32_t h = threadIdx.x; h < kRootHash; h += C) wp.hkey()[h] = kEmptySlot;
@@ -2137,7 +2187,7 @@ __global__ void __launch_bounds__(1024, 1)
 k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L,
               uint32_t sum_L, size_t region, uint32_t node_cap, uint32_t edge_scap,
               const uint32_t *__restrict__ bracket, uint32_t *__restrict__ nstar_out,
-              uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes)
+              uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes, uint32_t any)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     const uint32_t C = blockDim.x;
@@ -2147,7 +2197,9 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
     __shared__ SmaxShared x;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const uint64_t Ncap = num_sites(max_L);
-    const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L, max_L > sum_L, false);
+    // spanning along any axis: the slot's second node-sized array holds each root's face word
+    const SlotPtrs sp = slot_ptrs(ws, slot_bytes, Ncap, max_L > smem_L, max_L > sum_L, any != 0u);
+    uint32_t *const gflags = any ? sp.logb : nullptr;
     const EdgeList E{sm.edges, edge_scap, sp.gedges};
     const Nodes P{sp.P, static_cast<uint32_t>(__cvta_generic_to_shared(sm.nodes)), node_cap};
     const Nodes PA{sp.P, P.sbase, node_cap + static_cast<uint32_t>(smem_window_bytes(C) / 4)};  // first pass
@@ -2194,7 +2246,7 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
             nd_st(PA, 1u, 1u);
             nd_st(P, 0u, 0u);  // for the sweep (the same words when node_cap > 1)
             nd_st(P, 1u, 1u);
-            c.axis = axis;
+            c.axis = gflags ? kAnyAxis : axis;
             c.stop = 0;
             c.logn = 0;
             c.ecount[0] = 0;
@@ -2222,7 +2274,10 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
                 bitmap_update(bm, smp.perm, 0u, n_s);
             else
                 bitmap_add_sum(bm, sum, smp.perm, 0u, n_s, fd);
-            for (uint32_t r = threadIdx.x; r < n_s; r += C) nd_st(PA, r + 2u, r + 2u);
+            for (uint32_t r = threadIdx.x; r < n_s; r += C) {
+                nd_st(PA, r + 2u, r + 2u);
+                if (gflags) __stcg(gflags + r + 2u, 0u);
+            }
             __syncthreads();
             if (smem_bm && L == kPlaneL)
                 union_pass<true, true, kScanPlanes, false, true>(c, PA, nullptr, sm.sbm, Tb, E, smp.perm, smp.rank, L,
@@ -2239,7 +2294,20 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
             __syncthreads();
             ++npass;
             if (threadIdx.x == 0) tot_probe += n_s;
-            const bool span = nd_ld(PA, 1u) != 1u;
+            bool span;
+            if (gflags) {  // the face words of the first pass's clusters, at their roots
+                for (uint32_t r = threadIdx.x; r < n_s; r += C) {
+                    const uint32_t f = site_geo<kScanRows>(__ldg(smp.perm + r), L, fd, kAnyAxis).faces;
+                    if (f) atomicOr(gflags + uf_find(PA, r + 2u, 0u), f);
+                }
+                __syncthreads();
+                bool any_span = false;
+                for (uint32_t r = threadIdx.x; r < n_s && !any_span; r += C)
+                    any_span = spans_any(__ldcg(gflags + uf_find(PA, r + 2u, 0u)));
+                span = __syncthreads_or(any_span);
+            } else {
+                span = nd_ld(PA, 1u) != 1u;
+            }
             lend_back(P, PA, n_s + 2u);  // (a barrier: every thread has read node 1)
             if (span) {                  // n* < the bracket's lower end: sweep from the start
                 if (threadIdx.x == 0) ++tot_fb;
@@ -2256,16 +2324,16 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
         if (threadIdx.x == 0) cyc_first += static_cast<unsigned long long>(clock64() - t_first);
         if (smem_bm && L == kPlaneL)
             ns = span_sweep<true, kScanPlanes>(c, x, P, bm, sm, Tb, wp, E, smp, fd, N, n_s, chunks, cyc_back, cyc_span,
-                                               &hdr->status);
+                                               &hdr->status, gflags);
         else if (smem_bm)
             ns = span_sweep<true, kScanRows>(c, x, P, bm, sm, Tb, wp, E, smp, fd, N, n_s, chunks, cyc_back, cyc_span,
-                                             &hdr->status);
+                                             &hdr->status, gflags);
         else if (L <= sum_L)
             ns = span_sweep<false, kScanGroups>(c, x, P, bm, sm, Ts, wp, E, smp, fd, N, n_s, chunks, cyc_back, cyc_span,
-                                                &hdr->status);
+                                                &hdr->status, gflags);
         else
             ns = span_sweep<false, kScanGroupsG>(c, x, P, bm, sm, Ts, wp, E, smp, fd, N, n_s, chunks, cyc_back, cyc_span,
-                                                 &hdr->status);
+                                                 &hdr->status, gflags);
         npass += chunks;
         if (threadIdx.x == 0) {
             tot_chunks += chunks;
@@ -2389,7 +2457,8 @@ static int g_opt_threads = 0, g_opt_smem_nodes = -1, g_opt_max_ctas = 0, g_opt_g
 static uint32_t g_opt_spin_limit = 0;  // polls of a bounded device wait; 0 = kSpinLimit
 
 uint32_t spin_limit() { return g_opt_spin_limit ? g_opt_spin_limit : kSpinLimit; }
-constexpr int kOpSweep = 100;  // launch configuration of k_nstar_sweep (perc_nstar, sweep method)
+constexpr int kOpSweep = 100;     // launch configuration of k_nstar_sweep (perc_nstar, sweep method)
+constexpr int kOpSweepAny = 101;  // k_nstar_sweep along any axis (perc_nstar_any): slots with face words
 static CfgCache g_group_cache[kCfgDevices];
 
 static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool allow_group = true)
@@ -2410,13 +2479,14 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool
     // registers a thread); each CTA takes an equal share.  What the tables and the bitmap leave
     // goes to union-find nodes (up to kSmemNodes, keeping room for 512 edges) and then to the
     // shared part of the edge list.
-    const size_t extra = (op == PERC_OP_SMAX || op == kOpSweep) ? smem_window_bytes(cfg.threads) : 0;
+    const bool sweep_op = op == kOpSweep || op == kOpSweepAny;
+    const size_t extra = (op == PERC_OP_SMAX || sweep_op) ? smem_window_bytes(cfg.threads) : 0;
     // The sweep, S_max windows and the mass pass keep one shared region for the bitmap of lattices
     // up to smem_L or the occupancy summary of lattices up to sum_L (whose bitmap is global).  A
     // batch whose largest side is above kSmemBitmapMaxL gives the region to summaries (and the rest
     // to union-find nodes), unless it also reaches past kSumMixL (mixed batches), where the region of
     // a side-16 bitmap also holds the summaries up to side 32.
-    const bool sum_op = op == PERC_OP_MASS || op == PERC_OP_SMAX || op == kOpSweep;
+    const bool sum_op = op == PERC_OP_MASS || op == PERC_OP_SMAX || sweep_op;
     if (sum_op) cfg.smem_L = max_L <= kSmemBitmapMaxL ? max_L : (max_L > kSumMixL ? kPlaneL : 0u);
     auto base_for = [&](uint32_t sL) {
         return sum_op ? smem_tables_bytes() + smem_sum_tables_bytes() + region_bm_bytes(sL) + extra
@@ -2454,7 +2524,7 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool
     cfg.smem = base + smem_nodes_bytes(cfg.node_cap) + size_t(cfg.edge_scap) * sizeof(uint2);
     // The attribute and the occupancy are queried once per (kernel, device, threads, shared memory)
     // and cached, so that a call made while a stream is being captured issues no such query.
-    const int k = op == PERC_OP_MASS ? 1 : op == PERC_OP_SMAX ? 2 : op == kOpSweep ? 3 : 0;
+    const int k = op == PERC_OP_MASS ? 1 : op == PERC_OP_SMAX ? 2 : sweep_op ? 3 : 0;
     const void *fn = k == 1   ? reinterpret_cast<const void *>(k_mass)
                      : k == 2 ? reinterpret_cast<const void *>(k_smax)
                      : k == 3 ? reinterpret_cast<const void *>(k_nstar_sweep)
@@ -2480,6 +2550,7 @@ static int launch_cfg(int op, uint32_t max_L, uint32_t num, LaunchCfg &cfg, bool
     }
     if (occ < 1) return PERC_EINVAL;
     cfg.slot_bytes = slot_bytes_for(Ncap, max_L > cfg.smem_L, cfg.threads, max_L > cfg.sum_L ? max_L : 0u, op != kOpSweep);
+    // (the any-axis sweep keeps its face words in the second node-sized array)
     uint64_t grid = uint64_t(sms) * occ;
     const int cta_cap = env_int("PERC_MAX_CTAS", g_opt_max_ctas);
     if (cta_cap > 0 && uint64_t(cta_cap) < grid) grid = cta_cap;
@@ -2571,6 +2642,10 @@ extern "C" size_t perc_workspace_bytes(int op, uint32_t max_L, uint32_t num)
         return rank_workspace_bytes(max_L, num);
     }
     if (op == PERC_OP_PERIODIC) return periodic_workspace_bytes(max_L, num);
+    if (op == PERC_OP_NSTAR_ANY) {
+        LaunchCfg any;
+        return launch_cfg(kOpSweepAny, max_L, num, any) == PERC_OK ? cfg_ws_bytes(any) : 0;
+    }
     if (op != PERC_OP_NSTAR && op != PERC_OP_MASS && op != PERC_OP_SMAX) return 0;
     LaunchCfg cfg;
     if (launch_cfg(op, max_L, num, cfg) != PERC_OK) return 0;
@@ -2609,7 +2684,7 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
         k_nstar_sweep<<<sw.grid, sw.threads, sw.smem, stream>>>(samples, num_samples, max_L, sw.smem_L, sw.sum_L,
                                                                 sw.region, sw.node_cap, sw.edge_scap, bracket, nstar,
                                                                 passes, stats, static_cast<char *>(workspace),
-                                                                sw.slot_bytes);
+                                                                sw.slot_bytes, 0u);
         return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
     }
     if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
@@ -2662,6 +2737,24 @@ extern "C" int perc_nstar_min_axes(const uint32_t *nstar, uint32_t num, uint32_t
     if (!nstar || !out || num == 0 || axes == 0 || axes > 5) return PERC_EINVAL;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     k_nstar_min_axes<<<(num + 255u) / 256u, 256, 0, stream>>>(nstar, num, axes, out);
+    return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
+}
+
+extern "C" int perc_nstar_any(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                              const uint32_t *bracket, uint32_t *nstar, uint32_t *passes, perc_stats *stats,
+                              void *workspace, size_t ws_bytes, void *stream_)
+{
+    if (!samples || !nstar || !workspace || num_samples == 0) return PERC_EINVAL;
+    LaunchCfg cfg;
+    const int rc = launch_cfg(kOpSweepAny, max_L, num_samples, cfg);
+    if (rc != PERC_OK) return rc;
+    if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (reset_queue(workspace, stream) != cudaSuccess) return PERC_ECUDA;
+    k_nstar_sweep<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.sum_L,
+                                                               cfg.region, cfg.node_cap, cfg.edge_scap, bracket, nstar,
+                                                               passes, stats, static_cast<char *>(workspace),
+                                                               cfg.slot_bytes, 1u);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }
 

@@ -149,6 +149,32 @@ def nstar_any(workload, params: torch.Tensor | None = None, margin: float = 0.0,
     return run_nstar_any(iter_prepared(workload, budget), len(workload), params, margin)
 
 
+def nstar_any_sweep(workload, params: torch.Tensor | None = None, margin: float = 0.0, bracket_rows=None,
+                    stats=None, budget: int = DEFAULT_BUDGET):
+    """Exact n* for spanning along any axis by one sweep per row (perc_nstar_any: every cluster
+    carries ten face flags), for every (L, mask, seed) row of `workload`; returns (nstar, passes).
+    The bracket comes from the network `params` or, row by row, from `bracket_rows` [num, 2]."""
+    workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
+    ws = perc.default_workspace()
+    nstar = np.zeros(len(workload), dtype=np.uint32)
+    passes = np.zeros(len(workload), dtype=np.uint32)
+    for p in iter_prepared(workload, budget, ws):
+        br = None
+        if params is not None:
+            br = perc.bracket(params, p.samples, margin)
+        elif bracket_rows is not None:
+            rows = np.asarray(bracket_rows, dtype=np.int64)[p.idx]
+            br = torch.as_tensor(rows.astype(np.uint32).view(np.int32), device="cuda").contiguous()
+        ns, ps = perc.nstar_any(p.samples, p.max_L, bracket=br, stats=stats, ws=ws)
+        nstar[p.idx] = perc.u32(ns)
+        passes[p.idx] = perc.u32(ps)
+        rc = perc.check(ws)
+        if rc != 0:
+            raise perc.PercError(rc, "perc_nstar_any device status")
+        del p
+    return nstar, passes
+
+
 def nstar_wrap(workload, budget: int = DEFAULT_BUDGET):
     """First n at which a cluster wraps around the torus (periodic boundaries) along each row's
     axis, for every (L, zone word, seed) row of `workload` (uint32 numpy)."""
@@ -326,12 +352,16 @@ class NstarStep:
     can be captured in a CUDA graph (``capture``).  Samples are seed-major.  With ``axes`` > 1 every
     (mask, seed) pair becomes that many consecutive samples spanning along x1, x2, ... and the n*
     phase ends with perc_nstar_min_axes: ``nstar_any`` holds n* for spanning along any of them.
+    With ``any_axis`` the n* phase is perc_nstar_any instead: one sweep per pair whose clusters
+    carry ten face flags gives n* for spanning along any axis directly.
     """
 
     def __init__(self, L: int, masks, seeds, params: torch.Tensor | None = None, margin: float = 0.0,
-                 axes: int = 1):
+                 axes: int = 1, any_axis: bool = False):
         self.L = int(L)
         self.axes = int(axes)
+        self.any_axis = bool(any_axis)
+        assert not (self.any_axis and self.axes > 1)
         self.masks = np.asarray(list(masks), dtype=np.int64)
         self.seeds = np.asarray(list(seeds), dtype=np.int64)
         self.params = params
@@ -353,7 +383,7 @@ class NstarStep:
         self.passes = torch.empty(self.launch_num, dtype=torch.int32, device="cuda")
         self.nstar_any = torch.empty(self.num, dtype=torch.int32, device="cuda") if A > 1 else None
         nb = max(perc.workspace_bytes(perc.OP_RANK, self.L, S),
-                 perc.workspace_bytes(perc.OP_NSTAR, self.L, self.launch_num))
+                 perc.workspace_bytes(perc.OP_NSTAR_ANY if self.any_axis else perc.OP_NSTAR, self.L, self.launch_num))
         self.ws = perc.new_workspace(nb)
         self.lib = perc.lib()
 
@@ -368,9 +398,10 @@ class NstarStep:
 
     def run_nstar(self, learned: bool, stats: torch.Tensor | None = None, stream=None):
         br = self.bracket.data_ptr() if learned else None
-        perc._ok(self.lib.perc_nstar(self.samples.data_ptr(), self.launch_num, self.L, br, self.nstar.data_ptr(),
-                                     self.passes.data_ptr(), perc._ptr(stats), self.ws.data_ptr(), self.ws.numel(),
-                                     perc._stream(stream)), "perc_nstar")
+        fn = self.lib.perc_nstar_any if self.any_axis else self.lib.perc_nstar
+        perc._ok(fn(self.samples.data_ptr(), self.launch_num, self.L, br, self.nstar.data_ptr(),
+                    self.passes.data_ptr(), perc._ptr(stats), self.ws.data_ptr(), self.ws.numel(),
+                    perc._stream(stream)), "perc_nstar_any" if self.any_axis else "perc_nstar")
         if self.axes > 1:
             perc._ok(self.lib.perc_nstar_min_axes(self.nstar.data_ptr(), self.num, self.axes,
                                                   self.nstar_any.data_ptr(), perc._stream(stream)),

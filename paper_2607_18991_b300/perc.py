@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libperc.so")
 NEVER = 0xFFFFFFFF
 MAX_L = 73
-OP_RANK, OP_NSTAR, OP_MASS, OP_SMAX, OP_PERIODIC = 1, 2, 3, 4, 5
+OP_RANK, OP_NSTAR, OP_MASS, OP_SMAX, OP_PERIODIC, OP_NSTAR_ANY = 1, 2, 3, 4, 5, 6
 PERIODIC_MAX_L = 40
 AXIS_SHIFT, NUM_AXES = 8, 5  # zone word: spanning axis in bits 8..10; axes x1..x5
 OPT_THREADS, OPT_SMEM_NODES, OPT_MAX_CTAS, OPT_GROUP, OPT_METHOD, OPT_SPIN_LIMIT = 1, 2, 3, 4, 5, 6
@@ -52,6 +52,7 @@ def lib() -> ctypes.CDLL:
         "perc_rank": (i32, [u32, vp, u32, vp, vp, vp, sz, vp]),
         "perc_nstar": (i32, [vp, u32, u32, vp, vp, vp, vp, vp, sz, vp]),
         "perc_nstar_noalloc": (i32, [vp, u32, u32, vp, vp, vp, vp, vp]),
+        "perc_nstar_any": (i32, [vp, u32, u32, vp, vp, vp, vp, vp, sz, vp]),
         "perc_nstar_min_axes": (i32, [vp, u32, u32, vp, vp]),
         "perc_mass_periodic": (i32, [vp, u32, u32, vp, vp, vp, sz, vp]),
         "perc_nstar_wrap": (i32, [vp, u32, u32, vp, vp, sz, vp]),
@@ -78,7 +79,8 @@ def lib() -> ctypes.CDLL:
 
 
 def exported_symbols() -> list[str]:
-    return ["perc_workspace_bytes", "perc_rank", "perc_nstar", "perc_nstar_noalloc", "perc_nstar_min_axes", "perc_mass",
+    return ["perc_workspace_bytes", "perc_rank", "perc_nstar", "perc_nstar_any", "perc_nstar_noalloc",
+            "perc_nstar_min_axes", "perc_mass",
             "perc_mass_periodic", "perc_nstar_wrap", "perc_microbench",
             "perc_smax_window", "perc_binomial_weights", "perc_pmax", "perc_check",
             "perc_mlp_forward", "perc_mlp_grad", "perc_adam", "perc_mlp_train", "perc_bracket",
@@ -214,6 +216,23 @@ def nstar(samples: torch.Tensor, max_L: int, bracket: torch.Tensor | None = None
     buf = ws.get(workspace_bytes(OP_NSTAR, max_L, num))
     _ok(lib().perc_nstar(samples.data_ptr(), num, max_L, _ptr(bracket), ns.data_ptr(), _ptr(ps),
                          _ptr(stats), buf.data_ptr(), buf.numel(), _stream(stream)), "perc_nstar")
+    return ns, ps
+
+
+def nstar_any(samples: torch.Tensor, max_L: int, bracket: torch.Tensor | None = None,
+              stats: torch.Tensor | None = None, ws: Workspace | None = None, stream=None, out=None,
+              want_passes: bool = True):
+    """perc_nstar_any: n* for spanning along any axis, one sweep per sample; (nstar, passes)."""
+    num = samples.shape[0]
+    if out is None:
+        ns = torch.empty(num, dtype=torch.int32, device="cuda")
+        ps = torch.empty(num, dtype=torch.int32, device="cuda") if want_passes else None
+    else:
+        ns, ps = out
+    ws = ws or default_workspace()
+    buf = ws.get(workspace_bytes(OP_NSTAR_ANY, max_L, num))
+    _ok(lib().perc_nstar_any(samples.data_ptr(), num, max_L, _ptr(bracket), ns.data_ptr(), _ptr(ps), _ptr(stats),
+                             buf.data_ptr(), buf.numel(), _stream(stream)), "perc_nstar_any")
     return ns, ps
 
 
