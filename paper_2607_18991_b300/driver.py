@@ -343,6 +343,61 @@ def merge_shards(num: int, parts) -> np.ndarray:
 
 
 # ------------------------------------------------------------------------------------------------
+# per-shard result files with resume: a long sharded run writes each finished chunk of its rows to
+# a file of its own, so that a restarted rank skips what is already done, and the files of all
+# ranks are merged once at the end
+# ------------------------------------------------------------------------------------------------
+def shard_file(out_dir: str, rank: int, k: int) -> str:
+    import os
+    return os.path.join(out_dir, f"shard{rank:04d}_chunk{k:05d}.npz")
+
+
+def _gpu_nstar_rows(rows, params=None, margin: float = 0.0):
+    return nstar(rows, params=params, margin=margin)
+
+
+def run_shard(workload, rank: int, world: int, out_dir: str, compute=None, params=None, margin: float = 0.0,
+              budget: int | None = None) -> dict:
+    """Rank `rank` of `world`: its rows of `workload` (``shard``), in the chunks ``_chunks`` makes of
+    them, each computed (``compute(rows) -> (nstar, passes)``; by default exact n* on the GPU) and
+    written to ``shard_file(out_dir, rank, k)`` as (workload indices, nstar, passes) -- through a
+    temporary name and a rename, so a file exists only complete.  A chunk whose file exists and holds
+    the same indices is skipped: rerunning after a crash resumes.  Returns {"done", "skipped"}."""
+    import os
+    workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
+    compute = compute or (lambda rows: _gpu_nstar_rows(rows, params, margin))
+    mine = shard(workload, rank, world)
+    os.makedirs(out_dir, exist_ok=True)
+    done = skipped = 0
+    for k, sub in enumerate(_chunks(workload[mine], budget)):
+        idx = mine[sub]
+        path = shard_file(out_dir, rank, k)
+        if os.path.exists(path):
+            with np.load(path) as f:
+                if np.array_equal(f["idx"], idx):
+                    skipped += 1
+                    continue
+        ns, ps = compute(workload[idx])
+        tmp = path + f".tmp{os.getpid()}.npz"
+        np.savez(tmp, idx=idx, nstar=np.asarray(ns, dtype=np.uint32), passes=np.asarray(ps, dtype=np.uint32))
+        os.replace(tmp, path)
+        done += 1
+    return {"done": done, "skipped": skipped}
+
+
+def merge_shard_files(out_dir: str, num: int):
+    """(nstar, passes) over all `num` rows from every shard file in out_dir (each row exactly once)."""
+    import glob
+    import os
+    parts_n, parts_p = [], []
+    for path in sorted(glob.glob(os.path.join(out_dir, "shard*_chunk*.npz"))):
+        with np.load(path) as f:
+            parts_n.append((f["idx"], f["nstar"]))
+            parts_p.append((f["idx"], f["passes"]))
+    return merge_shards(num, parts_n), merge_shards(num, parts_p)
+
+
+# ------------------------------------------------------------------------------------------------
 # a fixed-shape step with every buffer allocated up front (for timing and CUDA-graph capture)
 # ------------------------------------------------------------------------------------------------
 class NstarStep:
