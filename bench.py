@@ -61,8 +61,8 @@ PMAX_METRIC = ("samples/sec of P_max(p) curves (exact S_max(n) over the windows 
 
 def rank_launches(L: int, num_seeds: int) -> int:
     """Kernels perc_rank launches: per chunk of up to 64 seeds, the bucket path's count, scan, place
-    and sort (L^5 <= 8,388,608) or the radix path's four histogram, scan and scatter passes."""
-    per_chunk = 4 if L ** 5 <= 8_388_608 else 12
+    and sort (L^5 <= 104,857,600) or the radix path's four histogram, scan and scatter passes."""
+    per_chunk = 4 if L ** 5 <= 104_857_600 else 12
     return math.ceil(num_seeds / 64) * per_chunk
 
 

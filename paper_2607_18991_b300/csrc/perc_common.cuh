@@ -187,6 +187,7 @@ enum AttrSlot {
     kAttrRankScatterTma,
     kAttrRankBCount,
     kAttrRankBPlace,
+    kAttrRankBSortBig,
     kAttrTorusMass,
     kAttrTorusWrap,
     kAttrMicrobench,

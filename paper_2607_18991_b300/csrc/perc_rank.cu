@@ -482,9 +482,10 @@ k_rank_scatter_tma(int pass, uint32_t N, uint32_t T, uint32_t S, const uint32_t 
 }
 
 // ------------------------------------------------------------------------------------------------
-// Bucket path (L^5 <= kBucketMaxN, which covers L <= 24).  The keys are uniform 32-bit values, so
-// their top B bits split a seed's sites into 2^B buckets of about 512 sites each; every bucket is
-// then sorted on its own, in shared memory:
+// Bucket path (L^5 <= kBucketBigMaxN, which covers L <= 40).  The keys are uniform 32-bit values, so
+// their top B bits split a seed's sites into 2^B buckets -- of about 512 sites up to L = 24, and of
+// up to about 6,400 (B = 14) above, sorted by k_rank_bsort_big -- and every bucket is then sorted on
+// its own, in shared memory:
 //   k_rank_bcount  per tile of kBTile sites: keys drawn, a shared-memory histogram of their buckets,
 //                  added into the seed's bucket counts (one global atomic per bucket and tile);
 //   k_rank_scan    exclusive scan of each seed's counts -> bucket starts (copied into the cursors);
@@ -502,7 +503,8 @@ k_rank_scatter_tma(int pass, uint32_t N, uint32_t T, uint32_t S, const uint32_t 
 constexpr uint32_t kBTileItems = 32;
 constexpr uint32_t kBTile = kRankThreads * kBTileItems;  // 16384 sites per tile
 constexpr uint32_t kBucketMaxBits = 14;
-constexpr uint64_t kBucketMaxN = uint64_t(512) << kBucketMaxBits;  // 8,388,608 sites
+constexpr uint64_t kBucketMaxN = uint64_t(512) << kBucketMaxBits;  // 8,388,608 sites: small buckets
+constexpr uint64_t kBucketBigMaxN = uint64_t(6400) << kBucketMaxBits;  // 104,857,600 sites (L <= 40)
 constexpr uint32_t kBCap = 1536;
 constexpr uint32_t kSubBits = 9;
 constexpr uint32_t kSub = 1u << kSubBits;
@@ -672,6 +674,107 @@ k_rank_bsort(uint32_t N, uint32_t B, const uint32_t *__restrict__ starts, const 
     }
 }
 
+// Large buckets (kBucketMaxN < L^5 <= kBucketBigMaxN: 2^14 buckets of up to about 6,400 sites):
+// one CTA of 1024 threads a bucket, its records read twice from global memory (a counting pass on
+// the next sub_bits key bits, then a placing pass into shared memory), an insertion sort inside each
+// sub-bucket (about one record each), perm and rank written.  Shared memory (dynamic): cap records,
+// then 2^sub_bits + 1 sub-bucket starts and 2^sub_bits cursors.  A bucket over cap records is
+// ordered by counting the records before each (exact at any size).
+constexpr uint32_t kBSortBigThreads = 1024;
+
+__host__ __device__ inline void big_bucket_shape(uint64_t N, uint32_t B, uint32_t &sub_bits, uint32_t &cap)
+{
+    const uint64_t mean = (N + (uint64_t(1) << B) - 1) >> B;
+    sub_bits = 9;
+    while ((uint64_t(1) << sub_bits) < mean) ++sub_bits;  // about one record a sub-bucket
+    cap = (sub_bits <= 11 ? 4u : 2u) << sub_bits;            // 2.5 to 8 times the mean
+}
+
+__host__ __device__ inline size_t big_bucket_smem(uint32_t sub_bits, uint32_t cap)
+{
+    return size_t(cap) * sizeof(uint2) + (size_t(2) * (1u << sub_bits) + 1) * sizeof(uint32_t);
+}
+
+__global__ void __launch_bounds__(kBSortBigThreads)
+k_rank_bsort_big(uint32_t N, uint32_t B, uint32_t sub_bits, uint32_t cap, const uint32_t *__restrict__ starts,
+                 const uint2 *__restrict__ recs, uint32_t *__restrict__ perm, uint32_t *__restrict__ rank_out)
+{
+    extern __shared__ __align__(16) unsigned char bs_raw[];
+    uint2 *out = reinterpret_cast<uint2 *>(bs_raw);
+    const uint32_t S = 1u << sub_bits;
+    uint32_t *start = reinterpret_cast<uint32_t *>(out + cap);  // [S + 1]
+    uint32_t *cur = start + S + 1;                              // [S]
+    __shared__ uint32_t wsum[kBSortBigThreads / 32];
+    const uint32_t s = blockIdx.y, b = blockIdx.x, nb = 1u << B;
+    const uint32_t *st = starts + size_t(s) * bucket_row(B);
+    const uint32_t lo = st[b], hi = b + 1u < nb ? st[b + 1u] : N, n = hi - lo;
+    const uint2 *in = recs + size_t(s) * N + lo;
+    uint32_t *po = perm + size_t(s) * N;
+    uint32_t *ro = rank_out + size_t(s) * N;
+    if (n > cap) {
+        for (uint32_t j = threadIdx.x; j < n; j += kBSortBigThreads) {
+            const uint2 r = in[j];
+            uint32_t before = 0;
+            for (uint32_t i = 0; i < n; ++i) before += rec_less(in[i], r) ? 1u : 0u;
+            po[lo + before] = r.y;
+            ro[r.y] = lo + before;
+        }
+        return;
+    }
+    const uint32_t shift = 32u - B - sub_bits;
+    for (uint32_t q = threadIdx.x; q < S; q += kBSortBigThreads) cur[q] = 0u;
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < n; j += kBSortBigThreads) atomicAdd(&cur[(in[j].x >> shift) & (S - 1u)], 1u);
+    __syncthreads();
+    // exclusive scan of the S counts: a contiguous run per thread, then a block scan of the sums
+    const uint32_t per = (S + kBSortBigThreads - 1) / kBSortBigThreads;
+    const uint32_t q0 = min(S, threadIdx.x * per), q1 = min(S, q0 + per);
+    uint32_t sum = 0;
+    for (uint32_t q = q0; q < q1; ++q) sum += cur[q];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= static_cast<uint32_t>(o)) x += y;
+    }
+    if (lane == 31u) wsum[warp] = x;
+    __syncthreads();
+    uint32_t run = x - sum;
+    for (uint32_t w = 0; w < warp; ++w) run += wsum[w];
+    for (uint32_t q = q0; q < q1; ++q) {
+        const uint32_t c = cur[q];
+        start[q] = run;
+        cur[q] = run;
+        run += c;
+    }
+    if (threadIdx.x == 0) start[S] = n;
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < n; j += kBSortBigThreads) {
+        const uint2 r = in[j];
+        out[atomicAdd(&cur[(r.x >> shift) & (S - 1u)], 1u)] = r;
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < S; q += kBSortBigThreads) {  // insertion sort of each sub-bucket
+        const uint32_t a = start[q], z = start[q + 1u];
+        for (uint32_t j = a + 1u; j < z; ++j) {
+            const uint2 r = out[j];
+            uint32_t i = j;
+            while (i > a && rec_less(r, out[i - 1u])) {
+                out[i] = out[i - 1u];
+                --i;
+            }
+            out[i] = r;
+        }
+    }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < n; j += kBSortBigThreads) {
+        const uint32_t site = out[j].y;
+        po[lo + j] = site;
+        ro[site] = lo + j;
+    }
+}
+
 }  // namespace perc
 
 using namespace perc;
@@ -708,14 +811,20 @@ extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, 
                            reinterpret_cast<uintptr_t>(workspace)) & 15u) == 0u;
     const bool use_tma = (N % 4u) == 0u && aligned && env_int_rank("PERC_RANK_TMA", 1) != 0;
     int *status = static_cast<int *>(workspace);  // keeps the first error since the last perc_check
-    if (N <= kBucketMaxN && env_int_rank("PERC_RANK_BUCKET", 1) != 0) {
+    if (N <= kBucketBigMaxN && env_int_rank("PERC_RANK_BUCKET", 1) != 0) {
         // bucket path: the records (8 bytes a site) take the radix path's key and value buffers, the
         // bucket counts and cursors its histogram area
         const uint32_t Bb = bucket_bits(N), nb = 1u << Bb, row = bucket_row(Bb);
         const uint32_t Tb = static_cast<uint32_t>((N + kBTile - 1) / kBTile);
         const size_t smem_count = size_t(nb) * 4, smem_place = size_t(nb) * 4 + size_t(kBTile) * 6;
+        const bool big = N > kBucketMaxN;
+        uint32_t sub_bits = 0, cap = 0;
+        if (big) big_bucket_shape(N, Bb, sub_bits, cap);
+        const size_t smem_big = big ? big_bucket_smem(sub_bits, cap) : 0;
         if (ensure_smem_attr(kAttrRankBCount, reinterpret_cast<const void *>(k_rank_bcount), smem_count) != PERC_OK ||
-            ensure_smem_attr(kAttrRankBPlace, reinterpret_cast<const void *>(k_rank_bplace), smem_place) != PERC_OK)
+            ensure_smem_attr(kAttrRankBPlace, reinterpret_cast<const void *>(k_rank_bplace), smem_place) != PERC_OK ||
+            (big && ensure_smem_attr(kAttrRankBSortBig, reinterpret_cast<const void *>(k_rank_bsort_big), smem_big) !=
+                        PERC_OK))
             return PERC_ECUDA;
         uint2 *recs = reinterpret_cast<uint2 *>(a_keys);  // a_keys then a_vals: chunk * N * 8 bytes
         for (uint32_t s0 = 0; s0 < num_seeds; s0 += chunk) {
@@ -725,8 +834,12 @@ extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, 
             k_rank_bcount<<<dim3(Tb, S), kRankThreads, smem_count, stream>>>(uint32_t(N), Bb, seeds + s0, counts);
             k_rank_scan<<<S, 1024, 0, stream>>>(row, counts, cursors);
             k_rank_bplace<<<dim3(Tb, S), kRankThreads, smem_place, stream>>>(uint32_t(N), Bb, seeds + s0, cursors, recs);
-            k_rank_bsort<<<dim3(nb, S), kBSortThreads, 0, stream>>>(uint32_t(N), Bb, counts, recs, perm + size_t(s0) * N,
-                                                                   rank + size_t(s0) * N);
+            if (big)
+                k_rank_bsort_big<<<dim3(nb, S), kBSortBigThreads, smem_big, stream>>>(
+                    uint32_t(N), Bb, sub_bits, cap, counts, recs, perm + size_t(s0) * N, rank + size_t(s0) * N);
+            else
+                k_rank_bsort<<<dim3(nb, S), kBSortThreads, 0, stream>>>(uint32_t(N), Bb, counts, recs,
+                                                                       perm + size_t(s0) * N, rank + size_t(s0) * N);
         }
         return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
     }

@@ -1,5 +1,6 @@
-"""perc_rank against the oracle's order: bit-exact perm and rank, on both of its paths (the bucket
-sort up to L = 24, the radix sort above) and on the radix path at small L as well."""
+"""perc_rank against the oracle's order: bit-exact perm and rank, on all of its paths (the bucket
+sort with small buckets up to L = 24 and with large ones up to L = 40, the radix sort above) and on
+the radix path at small L as well."""
 import os
 
 import numpy as np
@@ -26,7 +27,7 @@ def test_rank_bit_exact(L):
 
 @pytest.mark.parametrize("L", [1, 3, 8, 16])
 def test_rank_radix_path_bit_exact(L):
-    """The radix path (taken above L = 24) forced at small L through PERC_RANK_BUCKET=0."""
+    """The radix path (taken above L = 40) forced at small L through PERC_RANK_BUCKET=0."""
     os.environ["PERC_RANK_BUCKET"] = "0"
     try:
         _check(L, [1, 2, (1 << 40) + 17])
@@ -43,5 +44,9 @@ def test_rank_L24_sampled():
     _check(24, [5])  # the largest side of the bucket path (16384 buckets)
 
 
-def test_rank_L25_radix_path():
-    _check(25, [7])  # the smallest side of the radix path
+def test_rank_L25_large_buckets():
+    _check(25, [7])  # the smallest side with large buckets (16384 of about 600 sites)
+
+
+def test_rank_L32_large_buckets():
+    _check(32, [3])  # buckets of about 2048 sites

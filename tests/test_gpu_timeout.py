@@ -42,18 +42,24 @@ def test_group_barrier_wait_runs_out_then_exact():
 
 
 def test_rank_copy_wait_runs_out_then_exact():
+    import os
+
     from paper_2607_18991_b300 import perc
-    L, seeds = 26, [3, 4]  # above L = 24 perc_rank takes the radix path with the tile copies
+    L, seeds = 16, [3, 4, 5, 6]
     ws = perc.Workspace()
-    _limit(1)
+    os.environ["PERC_RANK_BUCKET"] = "0"  # the radix path, whose scatter waits on tile copies
     try:
-        perc.rank(L, seeds, ws=ws)
-        rc = perc.check(ws)
+        _limit(1)
+        try:
+            perc.rank(L, seeds, ws=ws)
+            rc = perc.check(ws)
+        finally:
+            _limit(0)
+        assert rc == PERC_ETIMEOUT
+        perm, rk = perc.rank(L, seeds, ws=ws)
+        assert perc.check(ws) == 0
     finally:
-        _limit(0)
-    assert rc == PERC_ETIMEOUT
-    perm, rk = perc.rank(L, seeds, ws=ws)
-    assert perc.check(ws) == 0
+        del os.environ["PERC_RANK_BUCKET"]
     for row, seed in enumerate(seeds):
         po, ro = oracle.rank(L, seed)
         assert np.array_equal(perc.u32(perm[row]), po) and np.array_equal(perc.u32(rk[row]), ro)
