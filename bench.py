@@ -22,7 +22,7 @@ perc_nstar_any sweep per (mask, seed), whose clusters carry ten face flags (two 
 bracket network trained on the any-axis n* of held-out seeds.
 
 `--workload wrap` measures the periodic-boundary variant: one step = perc_rank of the seeds and
-perc_nstar_wrap (the first n at which a cluster wraps around the torus along x1, by bisection) over
+perc_nstar_wrap (the first n at which a cluster wraps around the torus along x1, by a chunked sweep) over
 all 127 neighborhoods; 32 seeds per rank unless --num-seeds says otherwise.
 """
 from __future__ import annotations
@@ -880,7 +880,7 @@ def run_wrap_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic (Philox-keyed site orders, seeds per rank)",
             "config": {"workload": f"periodic boundaries, all 127 neighborhoods, L=16 (1,048,576 sites), seeds "
-                                   f"1..{num_seeds} per rank, {num} samples/rank, wrapping along x1, bisection over n",
+                                   f"1..{num_seeds} per rank, {num} samples/rank, wrapping along x1, chunked sweep over n",
                        "L": L, "masks": 127, "seeds_per_rank": int(len(seeds)), "samples_per_rank": num,
                        "l2": "flushed (256 MiB write) between timed steps; site orders > L2",
                        "parallelism": f"dp{world} (seed blocks, no collective)"},

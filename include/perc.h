@@ -191,8 +191,10 @@ int perc_nstar_any(const perc_sample *samples, uint32_t num_samples, uint32_t ma
  *
  * perc_nstar_wrap -- the first n at which a cluster wraps around the torus along the sample's
  * axis (zone word bits 8..10): it holds a closed path whose steps' x_{a+1} components do not sum
- * to zero.  Found by bisection over n with one union-find pass per probe that carries, for every
- * node, the displacement along the axis to its parent.  Every neighborhood wraps at n = L^5.
+ * to zero.  Found by a Newman--Ziff sweep over the site order in chunks of 512 sites, with a
+ * union-find forest that carries, for every node, the displacement along the axis to its parent;
+ * the chunk that first closes a winding path is undone and bisected.  Every neighborhood wraps at
+ * n = L^5.
  *   nstar device uint32[num_samples] (output)
  * Errors: PERC_EINVAL (null pointer, num_samples 0, max_L outside 1..PERC_PERIODIC_MAX_L),
  * PERC_EWORKSPACE, PERC_ECUDA.

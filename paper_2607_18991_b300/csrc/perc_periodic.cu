@@ -11,12 +11,12 @@
 // sites, one union-find node per site in rank space, and every edge taken once, from its later site
 // in rank order.  Each node word holds its parent and the displacement along the axis to it, so every
 // cluster carries an unwrapped coordinate; an edge inside one cluster whose ends disagree with
-// its step closes a winding path.  S_max counts the roots; n* is found by bisection over n
-// (wrapping is monotone in n, and it holds at n = L^5: every zone has a step with a non-zero
-// component along every axis, and repeating it L times winds around the torus), each probe
-// extending the forest of the largest n known not to wrap.
+// its step closes a winding path.  S_max counts the roots.  n* is found by a Newman--Ziff sweep in
+// chunks of sites: the forest of the committed sites is kept, a chunk's hooks are tagged and logged,
+// and a chunk that closes a winding path is undone and bisected, each probe extending the committed
+// forest (wrapping is monotone in n, and it holds at n = L^5: every zone has a step with a non-zero
+// component along every axis, and repeating it L times winds around the torus).
 #include <algorithm>
-
 #include <cstddef>
 
 #include "perc_common.cuh"
@@ -30,6 +30,8 @@ constexpr uint32_t kPerThreads = 1024;
 constexpr uint32_t kTorusSmemMaxL = 16;  // up to L = 16 the bitmap (128 KiB) lives in shared memory
 constexpr uint32_t kPeriodicMaxL = PERC_PERIODIC_MAX_L;  // displacements stay below 2 L^5 < 2^31
 constexpr size_t kPeriodicBudget = size_t(16) << 30;  // bytes of per-CTA slots in one launch
+constexpr uint32_t kWrapChunk = 512;  // sites one step of the wrap sweep adds (fastest of 256..2048 at L = 16)
+constexpr unsigned long long kTag = 1ull << 63;  // node word bit: a hook of the running probe
 
 struct PerHeader {
     int status;       // first device-side error (perc_check reads it)
@@ -41,23 +43,26 @@ static_assert(sizeof(PerHeader) == 256, "header is 256 bytes");
 __host__ __device__ inline size_t per_align(size_t b) { return (b + 255) & ~size_t(255); }
 __host__ __device__ inline size_t per_bm_words(uint64_t N) { return size_t(N / 32 + 1); }
 
-// Per-CTA slot: bitmap (one bit per site), two forests of node words (parent << 32 | displacement:
-// the committed one and the probe's) and cluster counts.
+// Per-CTA slot: bitmap (one bit per site), the forest's node words (tag bit 63, parent at bits
+// 32..62, displacement at bits 0..31) and one word per node: cluster counts (S_max) or the log of
+// the running probe's hooks (n*).
 __host__ __device__ inline size_t per_slot_bytes(uint64_t N)
 {
-    return per_align(per_bm_words(N) * 4) + 2 * per_align(size_t(N) * 8) + per_align(size_t(N) * 4);
+    return per_align(per_bm_words(N) * 4) + per_align(size_t(N) * 8) + per_align(size_t(N) * 4);
 }
 
 __device__ __forceinline__ unsigned long long node_word(uint32_t parent, int32_t disp)
 {
     return (static_cast<unsigned long long>(parent) << 32) | static_cast<uint32_t>(disp);
 }
-__device__ __forceinline__ uint32_t word_parent(unsigned long long w) { return static_cast<uint32_t>(w >> 32); }
+__device__ __forceinline__ uint32_t word_parent(unsigned long long w) { return static_cast<uint32_t>(w >> 32) & 0x7FFFFFFFu; }
 __device__ __forceinline__ int32_t word_disp(unsigned long long w) { return static_cast<int32_t>(static_cast<uint32_t>(w)); }
 
-// Root of x and pos(x) - pos(root) along the axis, with path halving (a compare-and-swap that may
-// fail: every word read stays a true relative position, since positions inside a cluster never
-// change once joined).  More than `cap` steps would mean a cycle in the forest: *bad is set.
+// Root of x and pos(x) - pos(root) along the axis, with path halving by a compare-and-swap that
+// may fail: every word read stays a true relative position, since positions inside a cluster never
+// change once joined.  Halving shortcuts only untagged links, so a shortcut stays true when the
+// running probe's tagged hooks are undone.  More than `cap` steps would mean a cycle in the forest:
+// *bad is set.
 __device__ uint32_t tfind(unsigned long long *nd, uint32_t x, int32_t &d, uint32_t cap, bool &bad)
 {
     int32_t acc = 0;
@@ -75,7 +80,7 @@ __device__ uint32_t tfind(unsigned long long *nd, uint32_t x, int32_t &d, uint32
             return p;
         }
         const int32_t dxg = word_disp(w) + word_disp(w2);
-        atomicCAS(nd + x, w, node_word(g, dxg));
+        if (!((w | w2) & kTag)) atomicCAS(nd + x, w, node_word(g, dxg));
         acc += dxg;
         x = g;
     }
@@ -85,20 +90,24 @@ __device__ uint32_t tfind(unsigned long long *nd, uint32_t x, int32_t &d, uint32
 }
 
 // Joins the clusters of nodes a and b over a step with pos(b) = pos(a) + step (the larger root
-// goes under the smaller).  Returns true when a and b already were one cluster and the step
-// disagrees with their coordinates: the edge closes a winding path.
-__device__ bool tunite(unsigned long long *nd, uint32_t a, uint32_t b, int32_t step, uint32_t cap, bool &bad)
+// goes under the smaller).  With a log the hook is tagged and its node appended to the log.
+// Returns true when a and b already were one cluster and the step disagrees with their
+// coordinates: the edge closes a winding path.
+__device__ bool tunite(unsigned long long *nd, uint32_t *log, uint32_t *logn, uint32_t a, uint32_t b, int32_t step,
+                       uint32_t cap, bool &bad)
 {
+    const unsigned long long tag = log ? kTag : 0ull;
     for (uint32_t it = 0; it <= cap; ++it) {
         int32_t da, db;
         const uint32_t ra = tfind(nd, a, da, cap, bad);
         const uint32_t rb = tfind(nd, b, db, cap, bad);
         if (bad) return false;
         if (ra == rb) return da + step != db;
-        if (ra < rb) {  // pos(rb) - pos(ra) = da + step - db
-            if (atomicCAS(nd + rb, node_word(rb, 0), node_word(ra, da + step - db)) == node_word(rb, 0)) return false;
-        } else {  // pos(ra) - pos(rb) = db - da - step
-            if (atomicCAS(nd + ra, node_word(ra, 0), node_word(rb, db - da - step)) == node_word(ra, 0)) return false;
+        const uint32_t lo = min(ra, rb), hi = max(ra, rb);
+        const int32_t rel = ra < rb ? da + step - db : db - da - step;  // pos(hi) - pos(lo)
+        if (atomicCAS(nd + hi, node_word(hi, 0), node_word(lo, rel) | tag) == node_word(hi, 0)) {
+            if (log) __stcg(log + atomicAdd(logn, 1u), hi);
+            return false;
         }
     }
     bad = true;
@@ -111,7 +120,8 @@ struct PerShared {
     uint32_t flag;   // a winding path was found in the running pass
     uint32_t bad;    // a union-find loop ran out
     uint32_t best;   // largest cluster
-    uint32_t offs[kMaxOffsets];  // the neighborhood's packed offsets
+    uint32_t logn;   // hooks in the running probe's log
+    uint32_t offs[kMaxOffsets];  // per offset: shifts 6 (d_k + 2) at bits 5k, d_axis + 2 at bits 28..30
 };
 
 // Bitmap bits and singleton nodes of the sites of rank r0 .. r1-1.
@@ -124,69 +134,126 @@ __device__ void torus_add(uint32_t *bm, unsigned long long *nd, const uint32_t *
     }
 }
 
-// The sites of rank r0 .. r1-1 join the forest `nd` of the first r0 sites (the bitmap holds the
-// first r1 sites, their nodes are set).  Every edge is taken by its later site in rank order, so
-// the new sites' edges to each other and to the earlier sites are all seen.  kWrap: stop as soon as
-// a winding path along `axis` closes (sh.flag).  Ends with a barrier.
-template <bool kWrap>
-__device__ void torus_link(PerShared &sh, const uint32_t *bm, bool smem_bm, unsigned long long *nd,
-                           const uint32_t *perm, const uint32_t *rank, uint32_t L, uint32_t r0, uint32_t r1,
-                           uint32_t axis)
+// Clears the bitmap words of the sites of rank 0 .. r1-1 (every set bit belongs to one of them).
+__device__ void torus_clear(uint32_t *bm, bool smem_bm, const uint32_t *perm, uint32_t r1)
 {
-    const uint32_t z = sh.z;
-    bool bad = false;
-    for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        if (kWrap && *reinterpret_cast<volatile uint32_t *>(&sh.flag)) break;
+    for (uint32_t r = threadIdx.x; r < r1; r += blockDim.x) {
         const uint32_t i = __ldg(perm + r);
-        // per axis k, the wrapped coordinates (x_k + d) mod L for d = -2..2, six bits each
-        uint32_t wk[5], rest = i;
+        if (smem_bm)
+            bm[i >> 5] = 0u;
+        else
+            __stcg(bm + (i >> 5), 0u);
+    }
+}
+
+// The sites of rank a .. b-1 (bitmap bits and nodes set) join the forest `nd`: every edge is taken
+// by its later site in rank order, so the sites' edges to each other and to the sites before a are
+// all seen (the bitmap may hold later sites too; the rank test drops them).  With fewer sites than
+// threads, 2..32 threads share a site's offsets.  With a log (the wrap sweep) the hooks are tagged
+// and logged, and the pass stops once a winding path along the axis closes (sh.flag).  Ends with a
+// barrier.
+__device__ void torus_link(PerShared &sh, const uint32_t *bm, bool smem_bm, unsigned long long *nd, uint32_t *log,
+                           const uint32_t *perm, const uint32_t *rank, const FastDiv &fd, uint32_t a, uint32_t b)
+{
+    const uint32_t L = fd.L, m = b - a, z = sh.z;
+    const bool wrap = log != nullptr;
+    uint32_t tps = 1;  // threads per site
+    while (tps < 32u && 2u * tps * m <= blockDim.x) tps *= 2u;
+    const uint32_t sub = threadIdx.x & (tps - 1u), stride = blockDim.x / tps;
+    bool bad = false, stop = false;
+    for (uint32_t k = threadIdx.x / tps; k < m && !stop; k += stride) {
+        if (wrap && *reinterpret_cast<volatile uint32_t *>(&sh.flag)) break;
+        const uint32_t r = a + k, i = __ldg(perm + r);
+        // per axis q, the wrapped coordinates (x_q + d) mod L for d = -2..2, six bits each
+        uint32_t x[5], wk[5];
+        site_coords(i, fd, x);
 #pragma unroll
-        for (int k = 4; k >= 0; --k) {
-            const uint32_t xk = rest % L;
-            rest /= L;
+        for (int q = 0; q < 5; ++q) {
             uint32_t w = 0;
 #pragma unroll
-            for (uint32_t f = 0; f < 5u; ++f) w |= ((xk + 2u * L + f - 2u) % L) << (6u * f);
-            wk[k] = w;
+            for (uint32_t f = 0; f < 5u; ++f) {
+                uint32_t c;
+                if (L >= 3u) {
+                    const int32_t t = static_cast<int32_t>(x[q] + f) - 2;
+                    c = static_cast<uint32_t>(t < 0 ? t + static_cast<int32_t>(L)
+                                                    : (t >= static_cast<int32_t>(L) ? t - static_cast<int32_t>(L) : t));
+                } else {
+                    c = (x[q] + 2u * L + f - 2u) % L;
+                }
+                w |= c << (6u * f);
+            }
+            wk[q] = w;
         }
-        for (uint32_t v = 0; v < z; ++v) {
-            const uint32_t packed = sh.offs[v];
+        for (uint32_t v = sub; v < z; v += tps) {
+            const uint32_t o = sh.offs[v];
             uint32_t j = 0;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) j = j * L + ((wk[k] >> (6u * ((packed >> (3 * k)) & 7u))) & 63u);
+            for (int q = 0; q < 5; ++q) j = j * L + ((wk[q] >> ((o >> (5 * q)) & 31u)) & 63u);
             const uint32_t word = smem_bm ? bm[j >> 5] : __ldcg(bm + (j >> 5));
             if (!((word >> (j & 31u)) & 1u)) continue;
             const uint32_t rj = j == i ? r : __ldg(rank + j);
-            if (rj > r || (!kWrap && rj == r)) continue;  // the later site takes the edge; loops only wind
-            const int32_t step = zone_component(packed, static_cast<int>(axis));
-            if (tunite(nd, r, rj, step, r1, bad) && kWrap) {
+            if (rj > r || (!wrap && rj == r)) continue;  // the later site takes the edge; loops only wind
+            const int32_t step = static_cast<int32_t>((o >> 28) & 7u) - 2;
+            if (tunite(nd, log, &sh.logn, r, rj, step, b, bad) && wrap) {
                 *reinterpret_cast<volatile uint32_t *>(&sh.flag) = 1u;
+                stop = true;
                 break;
             }
-            if (bad) break;
+            if (bad) {
+                stop = true;
+                break;
+            }
         }
-        if (bad) break;
     }
     if (bad) atomicOr(&sh.bad, 1u);
     __syncthreads();
 }
 
+// Ends the running probe of the wrap sweep: its logged hooks are undone (turned back into roots)
+// or committed (their tags cleared).  Tagged words are never shortened by path halving, so each
+// logged word is still the hook itself.  Ends with a barrier.
+__device__ void torus_settle(const PerShared &sh, unsigned long long *nd, const uint32_t *log, bool undo)
+{
+    const uint32_t n = sh.logn;
+    for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
+        const uint32_t x = __ldcg(log + k);
+        __stcg(nd + x, undo ? node_word(x, 0) : (__ldcg(nd + x) & ~kTag));
+    }
+    __syncthreads();
+}
+
 // smem_L: samples with L <= smem_L keep the bitmap in the dynamic shared memory (0: none do).
+// chunk: sites one step of the wrap sweep adds.
 template <bool kWrap>
 __global__ void __launch_bounds__(kPerThreads, 1) k_torus(const perc_sample *__restrict__ samples, uint32_t num,
                                                           uint32_t max_L, uint32_t smem_L,
                                                           const uint64_t *__restrict__ n_in,
                                                           int64_t *__restrict__ mass_out,
-                                                          uint32_t *__restrict__ nstar_out, char *ws, size_t slot_bytes)
+                                                          uint32_t *__restrict__ nstar_out, char *ws, size_t slot_bytes,
+                                                          uint32_t chunk)
 {
     __shared__ PerShared sh;
     extern __shared__ uint32_t sbm[];
     PerHeader *hdr = reinterpret_cast<PerHeader *>(ws);
     char *slot = ws + sizeof(PerHeader) + size_t(blockIdx.x) * slot_bytes;
+    const uint32_t Nmax = static_cast<uint32_t>(num_sites(max_L));
+    const size_t bm_bytes = per_align(per_bm_words(Nmax) * 4), nd_bytes = per_align(size_t(Nmax) * 8);
+    unsigned long long *nd = reinterpret_cast<unsigned long long *>(slot + bm_bytes);
+    uint32_t *aux = reinterpret_cast<uint32_t *>(slot + bm_bytes + nd_bytes);  // counts or hook log
+    // the bitmaps start clear; each sample clears the words it set
+    if (smem_L) {
+        const uint32_t sw = static_cast<uint32_t>(per_bm_words(num_sites(smem_L)));
+        for (uint32_t w = threadIdx.x; w < sw; w += blockDim.x) sbm[w] = 0u;
+    } else {
+        const uint32_t gw = static_cast<uint32_t>(per_bm_words(Nmax));
+        uint32_t *gbm = reinterpret_cast<uint32_t *>(slot);
+        for (uint32_t w = threadIdx.x; w < gw; w += blockDim.x) __stcg(gbm + w, 0u);
+    }
     for (;;) {
         if (threadIdx.x == 0) {
             sh.sample = atomicAdd(&hdr->queue, 1u);
             sh.bad = 0u;
+            sh.best = 0u;
         }
         __syncthreads();
         const uint32_t s = sh.sample;
@@ -210,77 +277,96 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_torus(const perc_sample *__r
         const uint32_t N = static_cast<uint32_t>(num_sites(L));
         const bool smem_bm = L <= smem_L;
         uint32_t *bm = smem_bm ? sbm : reinterpret_cast<uint32_t *>(slot);
-        const size_t bm_bytes = per_align(per_bm_words(N) * 4), nd_bytes = per_align(size_t(N) * 8);
-        unsigned long long *ndc = reinterpret_cast<unsigned long long *>(slot + bm_bytes);  // committed forest
-        unsigned long long *ndw = reinterpret_cast<unsigned long long *>(slot + bm_bytes + nd_bytes);
-        uint32_t *cnt = reinterpret_cast<uint32_t *>(slot + bm_bytes + 2 * nd_bytes);
-        const uint32_t words = static_cast<uint32_t>(per_bm_words(N));
-        for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) {
-            if (smem_bm)
-                bm[w] = 0u;
-            else
-                __stcg(bm + w, 0u);
+        const FastDiv fd = make_fastdiv(L);
+        // the neighborhood's offsets, zone by zone, one thread per table entry
+        uint32_t z = 0;
+        for (int zone = 0; zone < kZoneCount; ++zone)
+            if (mask & (1u << zone)) z += c_tzones.start[zone + 1] - c_tzones.start[zone];
+        for (uint32_t t = threadIdx.x; t < uint32_t(kMaxOffsets); t += blockDim.x) {
+            int zone = 0;
+            while (t >= c_tzones.start[zone + 1]) ++zone;
+            if (!(mask & (1u << zone))) continue;
+            uint32_t pos = t;
+            for (int q = 0; q < zone; ++q)
+                if (!(mask & (1u << q))) pos -= c_tzones.start[q + 1] - c_tzones.start[q];
+            const uint32_t packed = c_tzones.vec[t];
+            uint32_t o = ((packed >> (3u * axis)) & 7u) << 28;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) o |= (6u * ((packed >> (3 * q)) & 7u)) << (5 * q);
+            sh.offs[pos] = o;
         }
-        if (threadIdx.x == 0) {  // the neighborhood's offsets, zone by zone
-            uint32_t z = 0;
-            for (int zone = 0; zone < kZoneCount; ++zone) {
-                if (!(mask & (1u << zone))) continue;
-                for (uint32_t k = c_tzones.start[zone]; k < c_tzones.start[zone + 1]; ++k) sh.offs[z++] = c_tzones.vec[k];
-            }
-            sh.z = z;
-            sh.best = 0u;
-        }
+        if (threadIdx.x == 0) sh.z = z;
         __syncthreads();
         if (kWrap) {
-            // bisection over n with the forest of the largest n known not to wrap (nc = lo - 1)
-            // kept: a probe copies it and adds only the sites from nc up to the probe, and a probe
-            // that wraps is dropped again (its bitmap bits cleared)
-            uint32_t lo = 1, hi = N, nc = 0;  // wrap(N) holds (see the top of the file)
-            while (lo < hi && !sh.bad) {
-                const uint32_t mid = lo + (hi - lo) / 2u;  // > nc
-                for (uint32_t r = threadIdx.x; r < nc; r += blockDim.x) __stcg(ndw + r, __ldcg(ndc + r));
-                torus_add(bm, ndw, smp.perm, nc, mid);
-                if (threadIdx.x == 0) sh.flag = 0u;
-                __syncthreads();
-                torus_link<true>(sh, bm, smem_bm, ndw, smp.perm, smp.rank, L, nc, mid, axis);
-                const bool wrapped = sh.flag != 0u;
-                __syncthreads();  // every thread has read the flag before the next probe clears it
-                if (wrapped) {
-                    hi = mid;
-                    for (uint32_t r = nc + threadIdx.x; r < mid; r += blockDim.x) {
-                        const uint32_t i = __ldg(smp.perm + r);
-                        atomicAnd(bm + (i >> 5), ~(1u << (i & 31u)));
-                    }
-                    __syncthreads();  // cleared before the next probe sets bits again
-                } else {
-                    lo = mid + 1u;
-                    unsigned long long *tmp = ndc;
-                    ndc = ndw;
-                    ndw = tmp;
-                    nc = mid;
+            // the sweep: c sites committed, top sites in the bitmap with nodes set
+            uint32_t c = 0, top = 0, res = 0;
+            while (res == 0u) {
+                uint32_t hi = min(N, c + chunk);
+                if (hi <= c) {  // wrap(N) holds, so only a broken forest gets here
+                    if (threadIdx.x == 0) sh.bad = 1u;
+                    __syncthreads();
+                    break;
                 }
+                torus_add(bm, nd, smp.perm, top, hi);
+                top = hi;
+                if (threadIdx.x == 0) {
+                    sh.flag = 0u;
+                    sh.logn = 0u;
+                }
+                __syncthreads();
+                torus_link(sh, bm, smem_bm, nd, aux, smp.perm, smp.rank, fd, c, hi);
+                if (sh.bad) break;
+                bool wrapped = sh.flag != 0u;
+                torus_settle(sh, nd, aux, wrapped);
+                if (!wrapped) {
+                    c = hi;
+                    continue;
+                }
+                // the first wrapping n lies in (c, hi]: bisection, each probe on the committed forest
+                uint32_t lo = c + 1u;
+                while (lo < hi) {
+                    const uint32_t mid = lo + (hi - lo) / 2u;
+                    if (threadIdx.x == 0) {
+                        sh.flag = 0u;
+                        sh.logn = 0u;
+                    }
+                    __syncthreads();
+                    torus_link(sh, bm, smem_bm, nd, aux, smp.perm, smp.rank, fd, c, mid);
+                    if (sh.bad) break;
+                    wrapped = sh.flag != 0u;
+                    torus_settle(sh, nd, aux, wrapped);
+                    if (wrapped) {
+                        hi = mid;
+                    } else {
+                        c = mid;
+                        lo = mid + 1u;
+                    }
+                }
+                res = lo;
             }
+            torus_clear(bm, smem_bm, smp.perm, top);
             if (threadIdx.x == 0) {
-                nstar_out[s] = sh.bad ? PERC_NEVER : lo;
+                nstar_out[s] = sh.bad ? PERC_NEVER : res;
                 if (sh.bad) set_status(&hdr->status, PERC_ETIMEOUT);
             }
         } else {
             const uint32_t n = static_cast<uint32_t>(n_in[s]);
-            for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) __stcg(cnt + r, 0u);
-            torus_add(bm, ndc, smp.perm, 0u, n);
+            for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) __stcg(aux + r, 0u);
+            torus_add(bm, nd, smp.perm, 0u, n);
             __syncthreads();
-            torus_link<false>(sh, bm, smem_bm, ndc, smp.perm, smp.rank, L, 0u, n, axis);
+            torus_link(sh, bm, smem_bm, nd, nullptr, smp.perm, smp.rank, fd, 0u, n);
             bool bad = sh.bad != 0u;
             for (uint32_t r = threadIdx.x; r < n && !bad; r += blockDim.x) {
                 int32_t d;
-                atomicAdd(cnt + tfind(ndc, r, d, n, bad), 1u);
+                atomicAdd(aux + tfind(nd, r, d, n, bad), 1u);
             }
             if (bad) atomicOr(&sh.bad, 1u);
             __syncthreads();
             uint32_t best = 0;
-            for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) best = max(best, __ldcg(cnt + r));
+            for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) best = max(best, __ldcg(aux + r));
             best = __reduce_max_sync(0xffffffffu, best);
             if ((threadIdx.x & 31u) == 0u) atomicMax(&sh.best, best);
+            torus_clear(bm, smem_bm, smp.perm, n);
             __syncthreads();
             if (threadIdx.x == 0) {
                 mass_out[s] = sh.bad ? -1 : static_cast<int64_t>(sh.best);
@@ -326,7 +412,7 @@ int torus_launch(const perc_sample *samples, uint32_t num, uint32_t max_L, const
         return PERC_ECUDA;
     const uint32_t smem_L = smem ? max_L : 0u;
     k_torus<kWrap><<<grid, kPerThreads, smem, stream>>>(samples, num, max_L, smem_L, n, mass, nstar,
-                                                        static_cast<char *>(workspace), slot);
+                                                        static_cast<char *>(workspace), slot, kWrapChunk);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }
 
