@@ -699,11 +699,14 @@ __device__ __forceinline__ void union_pass(Ctl &c, const Nodes &P, uint32_t *log
             } else for (uint32_t k = gl; k < R; k += gsize) {
                 uint32_t h[3];
                 const uint32_t jb = entry_hits<kSmemBm, kPlanes>(g, bm, T.rows, T.planes, k, h);
-                if (kHalf) {  // a no-op except on the centre entry
+                if ((h[0] | h[1] | h[2]) == 0u) continue;
+                if (kHalf) {  // only the centre entry reaches above the site (the same entry in every lane)
                     const int32_t lim = static_cast<int32_t>(g.i - jb);
-                    h[0] &= below_mask(lim);
-                    h[1] &= below_mask(lim - 32);
-                    h[2] &= below_mask(lim - 64);
+                    if (lim < 96) {
+                        h[0] &= below_mask(lim);
+                        h[1] &= below_mask(lim - 32);
+                        h[2] &= below_mask(lim - 64);
+                    }
                 }
                 const uint32_t nh = __popc(h[0]) + __popc(h[1]) + __popc(h[2]);
                 if (nh == 0u) continue;
@@ -1659,8 +1662,8 @@ __device__ __forceinline__ void window_scan(const Ctl &c, const uint32_t *bm, co
         for (uint32_t k = gl; k < R; k += gsize) {
             uint32_t h[3];
             const uint32_t jb = entry_hits<kSmemBm, kPlanes>(g, bm, T.rows, T.planes, k, h);
+            if ((h[0] | h[1] | h[2]) == 0u) continue;
             const uint32_t nh = __popc(h[0]) + __popc(h[1]) + __popc(h[2]);
-            if (nh == 0u) continue;
             uint32_t slot = atomicAdd(ecount, nh);
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
