@@ -829,6 +829,17 @@ def run_wrap_ours(args):
             t_rank += e[0].elapsed_time(e[1])
         return tot / K, t_rank / K
 
+    if args.ncu_case:
+        # one step inside the profiler range, nothing else (for ncu)
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"ncu_case": True, "workload": "wrap", "samples": num, "seeds": int(len(seeds))}))
+        return
+
     gpu_index = torch.cuda.current_device()
     phys = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
     smi_index = int(phys[gpu_index]) if phys and phys[0].strip().isdigit() else gpu_index

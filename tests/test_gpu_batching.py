@@ -91,25 +91,29 @@ def _learned_gain(method):
     times = {}
     out = {}
     for learned in (True, False):
-        stats = perc.new_stats()
         step.run_rank()
         if learned:
             step.run_bracket()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        step.run_nstar(learned, stats)
-        b.record()
-        torch.cuda.synchronize()
-        times[learned] = a.elapsed_time(b)
+        best = None
+        for _ in range(3):  # the fastest of three launches
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            step.run_nstar(learned, perc.new_stats())
+            b.record()
+            torch.cuda.synchronize()
+            best = a.elapsed_time(b) if best is None else min(best, a.elapsed_time(b))
+        times[learned] = best
         out[learned] = step.result()
     assert np.array_equal(out[True][0], out[False][0])
     if method == "bisection":
         assert out[True][1].mean() < out[False][1].mean() - 3   # fewer passes per sample
         assert times[True] < 0.5 * times[False], times           # and much less time
-    else:  # the sweep starts at the bracket's lower end instead of n = 0: fewer chunks (the time
-        # is not asserted: a chunk costs about as much as the share of the first pass it replaces)
+    else:  # the sweep starts at the bracket's lower end instead of n = 0: fewer chunks, and the
+        # first pass over the sites below it (half neighborhoods, no per-chunk barriers) costs about
+        # half as much a site as a chunk
         assert out[True][1].mean() < out[False][1].mean(), (out[True][1].mean(), out[False][1].mean())
+        assert times[True] < 0.95 * times[False], times
     sel = np.arange(0, step.num, 97)
     assert np.array_equal(out[True][0][sel], orc_nstar(step.workload[sel]))
 
