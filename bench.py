@@ -59,11 +59,13 @@ PMAX_METRIC = ("samples/sec of P_max(p) curves (exact S_max(n) over the windows 
                "each binomial, convolution at 16 p per neighborhood) at L=16 over 127 neighborhoods")
 
 
-def rank_launches(L: int, num_seeds: int) -> int:
+def rank_launches(L: int, num_seeds: int, prefix: bool = False) -> int:
     """Kernels perc_rank launches: per chunk of up to 64 seeds, the bucket path's count, scan, place
-    and sort (L^5 <= 104,857,600) or the radix path's four histogram, scan and scatter passes."""
-    per_chunk = 4 if L ** 5 <= 104_857_600 else 12
-    return math.ceil(num_seeds / 64) * per_chunk
+    and sort (L^5 <= 104,857,600) or the radix path's four histogram, scan and scatter passes; with
+    prefix (perc_prefix_share + perc_rank_prefix) one more a chunk (the bucket cut) and the share."""
+    bucket = L ** 5 <= 104_857_600
+    per_chunk = (5 if prefix else 4) if bucket else 12
+    return math.ceil(num_seeds / 64) * per_chunk + (1 if prefix else 0)
 
 
 def train_bracket(args, any_axis: bool = False):
@@ -308,7 +310,8 @@ def run_ours(args):
     # ---- resident inputs: one preallocated step (seeds, orders, sample table, brackets, outputs)
     from paper_2607_18991_b300 import autotune
     N = L ** 5
-    step_obj = driver.NstarStep(L, MASKS, seeds, params=params, margin=args.margin, any_axis=any_axis)
+    step_obj = driver.NstarStep(L, MASKS, seeds, params=params, margin=args.margin, any_axis=any_axis,
+                                prefix=not args.no_prefix)
     samples, br, ns, ps = step_obj.samples, step_obj.bracket, step_obj.nstar, step_obj.passes
     nl = step_obj.launch_num  # samples of the n* launch (num x axes)
     perm, rk, ws_buf = step_obj.perm, step_obj.rank, step_obj.ws
@@ -330,7 +333,21 @@ def run_ours(args):
         if nb > ws_buf.numel():
             step_obj.ws = ws_buf = perc.new_workspace(nb, dev)
 
+    fallbacks = {"steps": 0, "samples": 0}
+
     def step(learned: bool, ev=None):
+        if learned and step_obj.prefix:  # bracket first: the ranking covers its share of each order
+            step_obj.run_bracket()
+            step_obj.run_prefix_rank()
+            if ev is not None:
+                ev[0].record(stream)
+                ev[1].record(stream)
+            step_obj.run_prefix_nstar()
+            fallbacks["steps"] += 1
+            fallbacks["samples"] += step_obj.finish()
+            if ev is not None:
+                ev[2].record(stream)
+            return
         step_obj.run_rank()
         if ev is not None:
             ev[0].record(stream)
@@ -384,6 +401,9 @@ def run_ours(args):
                 dist.barrier()
             a.record(stream)
             g.replay()
+            if learned and step_obj.prefix:  # the rare samples past the ranked prefix, inside the step
+                fallbacks["steps"] += 1
+                fallbacks["samples"] += step_obj.finish()
             b.record(stream)
             torch.cuda.synchronize()
             tot += a.elapsed_time(b)
@@ -439,10 +459,32 @@ def run_ours(args):
     samples_d2 = torch.empty_like(samples)
     params_d2 = torch.empty_like(params)
 
+    share_d = torch.zeros(2, dtype=torch.int32, device=dev)  # [share, unresolved] of the e2e prefix step
+    unres_host = torch.zeros(1, dtype=torch.int32).pin_memory()
+
     def e2e_step():
         seeds_d2.copy_(seeds_host, non_blocking=True)
         samples_d2.copy_(samples_host, non_blocking=True)
         params_d2.copy_(params_host, non_blocking=True)
+        if step_obj.prefix:  # bracket, its share of each order ranked, the sweep on the prefix
+            perc._ok(lib.perc_bracket(params_d2.data_ptr(), samples_d2.data_ptr(), nl, args.margin, br.data_ptr(),
+                                      sp), "perc_bracket")
+            perc._ok(lib.perc_prefix_share(samples_d2.data_ptr(), nl, br.data_ptr(), share_d.data_ptr(), sp),
+                     "perc_prefix_share")
+            perc._ok(lib.perc_rank_prefix(L, seeds_d2.data_ptr(), len(seeds), share_d.data_ptr(), perm.data_ptr(),
+                                          rk.data_ptr(), ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_rank_prefix")
+            share_d[1:].zero_()
+            perc._ok(lib.perc_nstar_prefix(samples_d2.data_ptr(), nl, L, br.data_ptr(), share_d.data_ptr(),
+                                           share_d.data_ptr() + 4, ns.data_ptr(), None, None, ws_buf.data_ptr(),
+                                           ws_buf.numel(), sp), "perc_nstar_prefix")
+            ns_host.copy_(ns, non_blocking=True)
+            unres_host.copy_(share_d[1:], non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            if int(unres_host[0]) > 0:  # samples past the ranked prefix: full orders, perc_nstar
+                idx = np.nonzero(ns_host.numpy().view(np.uint32) == perc.NEVER)[0]
+                got, _ = driver.nstar(step_obj.workload[idx], params, args.margin)
+                ns_host.numpy()[idx] = got.view(np.int32)
+            return
         perc._ok(lib.perc_rank(L, seeds_d2.data_ptr(), len(seeds), perm.data_ptr(), rk.data_ptr(),
                                ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_rank")
         perc._ok(lib.perc_bracket(params_d2.data_ptr(), samples_d2.data_ptr(), nl, args.margin, br.data_ptr(), sp),
@@ -470,7 +512,8 @@ def run_ours(args):
         e2e_ms += a.elapsed_time(b)
     e2e_ms /= args.steps
     h2d = seeds_host.numel() * 8 + samples_host.numel() * 8 + params_host.numel() * 4
-    d2h = ns_host.numel() * 4
+    d2h = ns_host.numel() * 4 + (4 if step_obj.prefix else 0)
+    assert np.array_equal(ns_host.numpy().view(np.uint32), out[True][0]), "e2e n* differs from the resident step's"
 
     # ---- max over ranks
     def max_over_ranks(x: float) -> float:
@@ -512,7 +555,8 @@ def run_ours(args):
                            + (", one any-axis sweep (ten border flags) per sample" if any_axis else ""))
 
     # rank passes + bracket + nstar (+ the minimum over axes) per step
-    gpu_launches = rank_launches(L, len(seeds)) + 2 + (1 if axes > 1 else 0)
+    gpu_launches = rank_launches(L, len(seeds), step_obj.prefix) + 2 + (1 if axes > 1 else 0)
+    share_val = int(step_obj.share[0].item()) if step_obj.prefix else None
     value = world * num / (ms_learned * 1e-3)
     if rank == 0:
         line = {
@@ -526,6 +570,8 @@ def run_ours(args):
                        "L": L, "masks": 127, "seeds_per_rank": int(len(seeds)), "samples_per_rank": num,
                        "spanning": "any of x1..x5" if any_axis else "x1",
                        "bracket": "learned", "margin": args.margin,
+                       "ranking": ("prefix: the first PERC_PREFIX_SITES(L^5, share) sites of each order, share = "
+                                   "the largest upper bracket end over L^5" if step_obj.prefix else "full"),
                        "method": "sweep (chunked Newman-Ziff replay)" if sweep else "bisection",
                        "l2": f"flushed (256 MiB write) between timed steps; site orders {8 * N * len(seeds) / 2**30:.1f} "
                              "GiB > L2",
@@ -536,7 +582,11 @@ def run_ours(args):
             "learned": {"value": value, "ms_per_step": ms_learned, "nstar_ms": ms_nstar_learned,
                         "rank_ms": ms_rank, "passes_per_sample": passes_learned, "stats": st_learned,
                         "ms_per_step_eager": ms_learned_eager, "ms_per_step_graph": ms_graph.get(True),
-                        "train_s": t_train, "train_loss_last": float(losses[-1].item())},
+                        "train_s": t_train, "train_loss_last": float(losses[-1].item()),
+                        "prefix": None if share_val is None else {
+                            "share": share_val / 2 ** 24, "ranked_sites": perc.prefix_sites(N, share_val),
+                            "of_sites": N, "fallback_samples": fallbacks["samples"],
+                            "prefix_steps": fallbacks["steps"]}},
             "e2e": {"value": world * num / (e2e_ms * 1e-3), "unit": "samples/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "roofline": {"kernel": ("k_nstar_sweep" if sweep else "k_nstar") + " (learned)", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
@@ -942,8 +992,9 @@ def run_mixed_ours(args):
     params, losses = train_bracket(args)
     wl = mixed_workload(rank)
     num = len(wl)
-    step = driver.BatchStep(wl, params=params, margin=args.margin)
+    step = driver.BatchStep(wl, params=params, margin=args.margin, prefix=not args.no_prefix)
     tuned = None if args.no_tune else autotune.tune_batch(step, learned=True)
+    fallbacks = {"steps": 0, "samples": 0}
     for learned in (True, False):
         step.run(learned)
     torch.cuda.synchronize()
@@ -964,6 +1015,9 @@ def run_mixed_ours(args):
                 dist.barrier()
             a.record(stream)
             go()
+            if learned and step.prefix:  # the rare samples past a chunk's ranked prefix, inside the step
+                fallbacks["steps"] += 1
+                fallbacks["samples"] += step.finish()
             b.record(stream)
             torch.cuda.synchronize()
             tot += a.elapsed_time(b)
@@ -975,6 +1029,7 @@ def run_mixed_ours(args):
     with ClockSampler(smi_index) as clk:
         ms_learned = timed(True, args.steps, args.warmup)
         ms_plain = timed(False, args.steps, args.warmup)
+    shares = perc.u32(step.share[:, 0]) if step.prefix else None
     clocks = clk.summary()
 
     # n* launches alone (eager, per chunk, with counters) for the roofline, and the results
@@ -1013,6 +1068,8 @@ def run_mixed_ours(args):
             for g, sh in zip(ch["groups"], seeds_h):
                 g["seeds"].copy_(sh, non_blocking=True)
         go()
+        if step.prefix:  # reads each chunk's unresolved count (synchronises) and finishes those samples
+            step.finish()
         for ch, ho in zip(step.chunks, host_out):
             ho.copy_(ch["nstar"], non_blocking=True)
 
@@ -1031,7 +1088,7 @@ def run_mixed_ours(args):
         e2e_ms += a.elapsed_time(b)
     e2e_ms /= args.steps
     h2d = sum(smp.numel() * 8 + sum(x.numel() * 8 for x in sh) for smp, sh in host_in)
-    d2h = sum(ho.numel() * 4 for ho in host_out)
+    d2h = sum(ho.numel() * 4 for ho in host_out) + (4 * len(step.chunks) if step.prefix else 0)
 
     def max_over_ranks(x: float) -> float:
         if world == 1:
@@ -1054,7 +1111,8 @@ def run_mixed_ours(args):
         cpu = cpu_baseline(rows, max(1, min(host_cores(), MIXED_CPU_ROWS)), _oracle_row,
                            f"the first {MIXED_CPU_ROWS} rows of the mixed batch, one ranking and one sweep each",
                            rows=True)
-    n_launch = sum(rank_launches(g["L"], g["S"]) for ch in step.chunks for g in ch["groups"]) + 2 * len(step.chunks)
+    n_launch = (sum(rank_launches(g["L"], g["S"], step.prefix) - (1 if step.prefix else 0)
+                    for ch in step.chunks for g in ch["groups"]) + (3 if step.prefix else 2) * len(step.chunks))
     if rank == 0:
         line = {
             "metric": MIXED_METRIC, "value": world * num / (ms_learned * 1e-3), "unit": "samples/s", "n_gpus": world,
@@ -1068,7 +1126,13 @@ def run_mixed_ours(args):
                        "parallelism": f"dp{world} (seed blocks, no collective)"},
             "plain": {"value": world * num / (ms_plain * 1e-3), "unit": "samples/s", "ms_per_step": ms_plain},
             "learned": {"ms_per_step": ms_learned, "nstar_ms": ms_nstar,
-                        "passes_per_sample": float(out[True][1].astype(np.float64).mean())},
+                        "passes_per_sample": float(out[True][1].astype(np.float64).mean()),
+                        "prefix": None if shares is None else {
+                            "share_per_chunk": [round(float(x) / 2 ** 24, 4) for x in shares],
+                            "ranked_sites": int(sum(perc.prefix_sites(g["L"] ** 5, int(x)) * g["S"]
+                                                    for ch, x in zip(step.chunks, shares) for g in ch["groups"])),
+                            "of_sites": int(sum(g["L"] ** 5 * g["S"] for ch in step.chunks for g in ch["groups"])),
+                            "fallback_samples": fallbacks["samples"], "prefix_steps": fallbacks["steps"]}},
             "e2e": {"value": world * num / (e2e_ms * 1e-3), "unit": "samples/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "roofline": {"kernel": "k_nstar_sweep / k_nstar_group (learned, all chunks)", "bound": "hbm",
@@ -1193,6 +1257,8 @@ def main():
     ap.add_argument("--cpu-seeds-per-worker", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
+    ap.add_argument("--no-prefix", action="store_true",
+                    help="learned arm: rank every site of each order instead of the brackets' share")
     ap.add_argument("--no-graph", dest="graph", action="store_false", help="do not time CUDA-graph replays")
     ap.add_argument("--workload", default="nstar", choices=["nstar", "L24", "mixed", "pmax", "any", "wrap"],
                     help="nstar: the n* samples/s line (default); L24: the same at L = 24 (128 seeds); mixed: "

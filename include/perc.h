@@ -360,6 +360,48 @@ int perc_bracket(const float *params, const perc_sample *samples, uint32_t num_s
                  float margin, uint32_t *bracket, void *stream);
 
 /*
+ * Ranking only the start of each order (not in the paper; the Newman--Ziff sweep reads the order
+ * only up to n*, and a verified bracket bounds n* from above in all but rare samples).  Three
+ * calls, in this order on one stream:
+ *
+ * perc_prefix_share -- *share = the largest upper bracket end hi[k] / L_k^5 over the samples, in
+ *   units of 2^-24, rounded up (at most 2^24).  A bracket that perc_nstar would not use (lo < 1,
+ *   lo > hi, hi > L^5) or an invalid side counts as the whole lattice.
+ *     samples, bracket  device, as for perc_nstar (bracket as perc_bracket writes it)
+ *     share             device uint32 (output)
+ *
+ * perc_rank_prefix -- perc_rank for the first K = PERC_PREFIX_SITES(L^5, *share) sites of every
+ *   order (the share of the lattice plus an eighth and 64 sites, at most L^5): for each seed,
+ *   perm[s][0..P) holds the P >= K sites of smallest (key, index) in order and rank[s][site] is set
+ *   for those sites, P ending at a key-bucket boundary (the top bits of the key).  Every other entry
+ *   of perm and rank is left as it was.  For L^5 above 104,857,600 (the radix path) every site is
+ *   ranked.  Arguments and workspace as for perc_rank, plus
+ *     share  device uint32, as perc_prefix_share writes it (read on the device)
+ *
+ * perc_nstar_prefix -- perc_nstar's sweep on such orders: no site of rank >= K (K from *share and
+ *   the sample's L^5, as above) is read.  A sample whose sweep reaches K without spanning gets
+ *   nstar = PERC_NEVER and adds one to *unresolved; it needs its order in full (perc_rank) and
+ *   perc_nstar.  Arguments, workspace (PERC_OP_NSTAR) and errors as for perc_nstar (the sweep
+ *   method always), plus
+ *     share       device uint32, as for perc_rank_prefix (the same value)
+ *     unresolved  device uint32, incremented (the caller zeroes it)
+ */
+#define PERC_PREFIX_BASE_(N, share) \
+    (((uint64_t)(N) * ((share) < (1u << 24) ? (uint64_t)(share) : (uint64_t)(1u << 24))) >> 24)
+#define PERC_PREFIX_SITES(N, share)                                            \
+    (PERC_PREFIX_BASE_(N, share) * 9u / 8u + 64u < (uint64_t)(N)               \
+         ? PERC_PREFIX_BASE_(N, share) * 9u / 8u + 64u                         \
+         : (uint64_t)(N))
+int perc_prefix_share(const perc_sample *samples, uint32_t num_samples, const uint32_t *bracket,
+                      uint32_t *share, void *stream);
+int perc_rank_prefix(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, const uint32_t *share,
+                     uint32_t *perm, uint32_t *rank, void *workspace, size_t ws_bytes, void *stream);
+int perc_nstar_prefix(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                      const uint32_t *bracket, const uint32_t *share, uint32_t *unresolved,
+                      uint32_t *nstar, uint32_t *passes, perc_stats *stats, void *workspace,
+                      size_t ws_bytes, void *stream);
+
+/*
  * perc_microbench -- on-chip throughput probes (not in the paper): the peaks that the n* kernels,
  * which keep their data in shared memory and L2 rather than HBM, are measured against.  One launch
  * of one probe over every SM on `stream`; the caller times it (CUDA events) and divides *units by

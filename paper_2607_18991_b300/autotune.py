@@ -3,7 +3,8 @@
 ``tune`` times perc_nstar on a small sample of a workload (a few seeds, all requested masks) under
 each candidate (threads per CTA, union-find nodes kept in shared memory) and keeps the fastest.
 ``tune_batch`` picks, for every chunk of a ``driver.BatchStep`` (a band of lattice sides), the n*
-method and the CTAs per sample: the sweep with one CTA a sample, or the bisection with cooperative
+method and the CTAs per sample (a step that ranks only prefixes runs the sweep, so there is nothing to
+pick): the sweep with one CTA a sample, or the bisection with cooperative
 groups of 2..32 CTAs a sample (which pays off when a chunk of big lattices holds fewer samples than
 the GPU has SMs).  Results are cached in a JSON file -- ``PERC_TUNE_CACHE``, else
 ``_build/tune.json`` beside this module -- keyed by the device name, the SHA-256 of the library's
@@ -134,6 +135,10 @@ def tune_batch(step, learned: bool = True, reps: int = 1, use_cache: bool = True
     """Per-chunk launch options of a driver.BatchStep: each chunk's orders are ranked once, then its
     n* launch is timed under every candidate; the fastest is kept.  Sets step's options and returns
     [{"method", "group", "ms", "table"}] per chunk."""
+    if learned and getattr(step, "prefix", False):  # perc_nstar_prefix always runs the sweep
+        chosen = [{"method": perc.METHOD_SWEEP, "group": 1, "ms": None, "table": []} for _ in step.chunks]
+        step.set_options([{"method": c["method"], "group": c["group"]} for c in chosen])
+        return chosen
     cache = _load()
     chosen = []
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count

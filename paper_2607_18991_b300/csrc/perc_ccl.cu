@@ -2190,7 +2190,8 @@ __global__ void __launch_bounds__(1024, 1)
 k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t max_L, uint32_t smem_L,
               uint32_t sum_L, size_t region, uint32_t node_cap, uint32_t edge_scap,
               const uint32_t *__restrict__ bracket, uint32_t *__restrict__ nstar_out,
-              uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes, uint32_t any)
+              uint32_t *__restrict__ passes_out, perc_stats *stats, char *ws, size_t slot_bytes, uint32_t any,
+              const uint32_t *__restrict__ share, uint32_t *__restrict__ unresolved)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     const uint32_t C = blockDim.x;
@@ -2237,6 +2238,8 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
             continue;
         }
         const uint32_t N = static_cast<uint32_t>(num_sites(L));
+        // orders ranked only in part (perc_nstar_prefix): no site of rank >= lim is read
+        const uint32_t lim = share ? prefix_sites(N, *share) : N;
         const bool smem_bm = L <= smem_L;
         uint32_t *bm, *sum;
         sample_bm_sum(sm, sp, L, smem_L, sum_L, bm, sum);
@@ -2265,7 +2268,7 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
         if (bracket) {
             blo = bracket[2 * size_t(s)];
             bhi = bracket[2 * size_t(s) + 1];
-            if (blo >= 1u && blo <= bhi && bhi <= N) {
+            if (blo >= 1u && blo <= bhi && bhi <= N && blo <= lim) {
                 n_s = blo - 1u;
                 have_br = true;
             } else if (threadIdx.x == 0) {
@@ -2326,16 +2329,16 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
         uint32_t chunks = 0, ns;
         if (threadIdx.x == 0) cyc_first += static_cast<unsigned long long>(clock64() - t_first);
         if (smem_bm && L == kPlaneL)
-            ns = span_sweep<true, kScanPlanes>(c, x, P, bm, sm, Tb, wp, E, smp, fd, N, n_s, chunks, cyc_back, cyc_span,
+            ns = span_sweep<true, kScanPlanes>(c, x, P, bm, sm, Tb, wp, E, smp, fd, lim, n_s, chunks, cyc_back, cyc_span,
                                                &hdr->status, gflags);
         else if (smem_bm)
-            ns = span_sweep<true, kScanRows>(c, x, P, bm, sm, Tb, wp, E, smp, fd, N, n_s, chunks, cyc_back, cyc_span,
+            ns = span_sweep<true, kScanRows>(c, x, P, bm, sm, Tb, wp, E, smp, fd, lim, n_s, chunks, cyc_back, cyc_span,
                                              &hdr->status, gflags);
         else if (L <= sum_L)
-            ns = span_sweep<false, kScanGroups>(c, x, P, bm, sm, Ts, wp, E, smp, fd, N, n_s, chunks, cyc_back, cyc_span,
+            ns = span_sweep<false, kScanGroups>(c, x, P, bm, sm, Ts, wp, E, smp, fd, lim, n_s, chunks, cyc_back, cyc_span,
                                                 &hdr->status, gflags);
         else
-            ns = span_sweep<false, kScanGroupsG>(c, x, P, bm, sm, Ts, wp, E, smp, fd, N, n_s, chunks, cyc_back, cyc_span,
+            ns = span_sweep<false, kScanGroupsG>(c, x, P, bm, sm, Ts, wp, E, smp, fd, lim, n_s, chunks, cyc_back, cyc_span,
                                                  &hdr->status, gflags);
         npass += chunks;
         if (threadIdx.x == 0) {
@@ -2344,6 +2347,7 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
         }
         if (threadIdx.x == 0) {
             nstar_out[s] = ns;
+            if (ns == PERC_NEVER && lim < N && unresolved) atomicAdd(unresolved, 1u);  // past the prefix
             if (passes_out) passes_out[s] = npass;
             tot_passes += npass;
             if (stats) {
@@ -2687,7 +2691,7 @@ extern "C" int perc_nstar(const perc_sample *samples, uint32_t num_samples, uint
         k_nstar_sweep<<<sw.grid, sw.threads, sw.smem, stream>>>(samples, num_samples, max_L, sw.smem_L, sw.sum_L,
                                                                 sw.region, sw.node_cap, sw.edge_scap, bracket, nstar,
                                                                 passes, stats, static_cast<char *>(workspace),
-                                                                sw.slot_bytes, 0u);
+                                                                sw.slot_bytes, 0u, nullptr, nullptr);
         return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
     }
     if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
@@ -2757,7 +2761,26 @@ extern "C" int perc_nstar_any(const perc_sample *samples, uint32_t num_samples, 
     k_nstar_sweep<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.sum_L,
                                                                cfg.region, cfg.node_cap, cfg.edge_scap, bracket, nstar,
                                                                passes, stats, static_cast<char *>(workspace),
-                                                               cfg.slot_bytes, 1u);
+                                                               cfg.slot_bytes, 1u, nullptr, nullptr);
+    return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
+}
+
+extern "C" int perc_nstar_prefix(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                                 const uint32_t *bracket, const uint32_t *share, uint32_t *unresolved,
+                                 uint32_t *nstar, uint32_t *passes, perc_stats *stats, void *workspace,
+                                 size_t ws_bytes, void *stream_)
+{
+    if (!samples || !share || !unresolved || !nstar || !workspace || num_samples == 0) return PERC_EINVAL;
+    LaunchCfg cfg;
+    const int rc = launch_cfg(kOpSweep, max_L, num_samples, cfg);
+    if (rc != PERC_OK) return rc;
+    if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (reset_queue(workspace, stream) != cudaSuccess) return PERC_ECUDA;
+    k_nstar_sweep<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.sum_L,
+                                                               cfg.region, cfg.node_cap, cfg.edge_scap, bracket, nstar,
+                                                               passes, stats, static_cast<char *>(workspace),
+                                                               cfg.slot_bytes, 0u, share, unresolved);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }
 

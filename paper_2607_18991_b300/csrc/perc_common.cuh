@@ -172,6 +172,13 @@ __host__ __device__ inline uint64_t num_sites(uint32_t L)
     return l * l * l * l * l;
 }
 
+// Sites of each order that perc_rank_prefix ranks at least and perc_nstar_prefix may read, for a
+// lattice of N sites (PERC_PREFIX_SITES: the share of the lattice, an eighth more and 64 sites).
+__host__ __device__ inline uint32_t prefix_sites(uint64_t N, uint32_t share)
+{
+    return static_cast<uint32_t>(PERC_PREFIX_SITES(N, share));
+}
+
 // Polls a bounded device-side wait makes before it gives up with PERC_ETIMEOUT: kSpinLimit, or
 // the value of PERC_OPT_SPIN_LIMIT (defined in perc_ccl.cu).  A wait that drains copies still in
 // flight after a timeout always uses kSpinLimit.

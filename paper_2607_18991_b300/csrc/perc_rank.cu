@@ -542,9 +542,10 @@ k_rank_bcount(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32
         if (bh[b]) atomicAdd(row + b, bh[b]);
 }
 
+// cut (nullable): per seed the last bucket to place (perc_rank_prefix); later buckets are skipped.
 __global__ void __launch_bounds__(kRankThreads)
 k_rank_bplace(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32_t *__restrict__ cursors,
-              uint2 *__restrict__ recs)
+              uint2 *__restrict__ recs, const uint32_t *__restrict__ cut)
 {
     // shared: [2^B] bucket counts of the tile, then the tile's first place in each bucket; the tile's
     // keys; each key's offset among the tile's keys of its bucket (one shared atomic a key)
@@ -552,6 +553,7 @@ k_rank_bplace(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32
     uint32_t *keys = bh + (1u << B);
     uint16_t *loc = reinterpret_cast<uint16_t *>(keys + kBTile);
     const uint32_t s = blockIdx.y, nb = 1u << B;
+    const uint32_t last = cut ? cut[s] : nb - 1u;
     for (uint32_t b = threadIdx.x; b < nb; b += kRankThreads) bh[b] = 0u;
     __syncthreads();
     const uint64_t seed = seeds[s];
@@ -560,9 +562,9 @@ k_rank_bplace(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32
     for (uint32_t k = 0; k < kBTileItems; ++k) {
         const uint32_t j = k * kRankThreads + threadIdx.x, e = e0 + j;
         if (e < N) {
-            const uint32_t key = site_key(seed, e);
+            const uint32_t key = site_key(seed, e), b = bucket_of(key, B);
             keys[j] = key;
-            loc[j] = static_cast<uint16_t>(atomicAdd(&bh[bucket_of(key, B)], 1u));
+            if (b <= last) loc[j] = static_cast<uint16_t>(atomicAdd(&bh[b], 1u));
         }
     }
     __syncthreads();
@@ -575,9 +577,57 @@ k_rank_bplace(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32
     for (uint32_t k = 0; k < kBTileItems; ++k) {
         const uint32_t j = k * kRankThreads + threadIdx.x, e = e0 + j;
         if (e < N) {
-            const uint32_t key = keys[j];
-            row[bh[bucket_of(key, B)] + loc[j]] = make_uint2(key, e);
+            const uint32_t key = keys[j], b = bucket_of(key, B);
+            if (b <= last) row[bh[b] + loc[j]] = make_uint2(key, e);
         }
+    }
+}
+
+// perc_rank_prefix: per seed the first bucket whose end reaches prefix_sites(N, *share) sites (the
+// starts are the exclusive scan of the bucket counts), one thread a seed.
+__global__ void __launch_bounds__(256) k_bucket_cut(uint32_t N, uint32_t B, uint32_t S,
+                                                    const uint32_t *__restrict__ starts,
+                                                    const uint32_t *__restrict__ share, uint32_t *__restrict__ cut)
+{
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const uint32_t nb = 1u << B, K = prefix_sites(N, *share);
+    const uint32_t *st = starts + size_t(s) * bucket_row(B);
+    uint32_t lo = 0u, hi = nb - 1u;  // the last bucket ends at N >= K
+    while (lo < hi) {
+        const uint32_t m = lo + (hi - lo) / 2u;
+        const uint32_t end = m + 1u < nb ? st[m + 1u] : N;
+        if (end >= K)
+            hi = m;
+        else
+            lo = m + 1u;
+    }
+    cut[s] = lo;
+}
+
+// The largest upper bracket end as a share of its sample's lattice, in units of 2^-24 rounded up
+// (one block of 1024 threads).  A bracket that perc_nstar would not use (lo < 1, lo > hi, hi > N)
+// or an invalid side counts as the whole lattice.
+__global__ void __launch_bounds__(1024) k_prefix_share(const perc_sample *__restrict__ samples,
+                                                       const uint32_t *__restrict__ bracket, uint32_t num,
+                                                       uint32_t *__restrict__ share)
+{
+    __shared__ uint32_t wmax[32];
+    uint32_t m = 0u;
+    for (uint32_t k = threadIdx.x; k < num; k += blockDim.x) {
+        const uint32_t L = samples[k].L, lo = bracket[2 * size_t(k)], hi = bracket[2 * size_t(k) + 1];
+        const uint64_t N = (L >= 1u && L <= PERC_MAX_L) ? num_sites(L) : 0u;
+        uint32_t q = 1u << 24;
+        if (N && lo >= 1u && lo <= hi && hi <= N) q = static_cast<uint32_t>(((uint64_t(hi) << 24) + N - 1u) / N);
+        m = max(m, q);
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31u) == 0u) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32u) {
+        uint32_t v = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0u;
+        v = __reduce_max_sync(0xffffffffu, v);
+        if (threadIdx.x == 0u) *share = min(v, 1u << 24);
     }
 }
 
@@ -594,10 +644,11 @@ struct BSortSmem {
 
 __global__ void __launch_bounds__(kBSortThreads)
 k_rank_bsort(uint32_t N, uint32_t B, const uint32_t *__restrict__ starts, const uint2 *__restrict__ recs,
-             uint32_t *__restrict__ perm, uint32_t *__restrict__ rank_out)
+             uint32_t *__restrict__ perm, uint32_t *__restrict__ rank_out, const uint32_t *__restrict__ cut)
 {
     __shared__ BSortSmem S_;
     const uint32_t s = blockIdx.y, b = blockIdx.x, nb = 1u << B;
+    if (cut && b > cut[s]) return;  // past the prefix (perc_rank_prefix)
     const uint32_t *st = starts + size_t(s) * bucket_row(B);
     const uint32_t lo = st[b], hi = b + 1u < nb ? st[b + 1u] : N, n = hi - lo;
     const uint2 *in = recs + size_t(s) * N + lo;
@@ -697,8 +748,10 @@ __host__ __device__ inline size_t big_bucket_smem(uint32_t sub_bits, uint32_t ca
 
 __global__ void __launch_bounds__(kBSortBigThreads)
 k_rank_bsort_big(uint32_t N, uint32_t B, uint32_t sub_bits, uint32_t cap, const uint32_t *__restrict__ starts,
-                 const uint2 *__restrict__ recs, uint32_t *__restrict__ perm, uint32_t *__restrict__ rank_out)
+                 const uint2 *__restrict__ recs, uint32_t *__restrict__ perm, uint32_t *__restrict__ rank_out,
+                 const uint32_t *__restrict__ cut)
 {
+    if (cut && blockIdx.x > cut[blockIdx.y]) return;  // past the prefix (perc_rank_prefix)
     extern __shared__ __align__(16) unsigned char bs_raw[];
     uint2 *out = reinterpret_cast<uint2 *>(bs_raw);
     const uint32_t S = 1u << sub_bits;
@@ -779,8 +832,10 @@ k_rank_bsort_big(uint32_t N, uint32_t B, uint32_t sub_bits, uint32_t cap, const 
 
 using namespace perc;
 
-extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, uint32_t *perm,
-                         uint32_t *rank, void *workspace, size_t ws_bytes, void *stream_)
+// share (nullable): rank only the first buckets of each order, up to prefix_sites(N, *share) sites
+// (bucket path; the radix path ranks every site).
+static int rank_impl(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, const uint32_t *share, uint32_t *perm,
+                     uint32_t *rank, void *workspace, size_t ws_bytes, void *stream_)
 {
     if (L < 1 || L > PERC_MAX_L || num_seeds == 0 || !seeds || !perm || !rank || !workspace)
         return PERC_EINVAL;
@@ -827,19 +882,25 @@ extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, 
                         PERC_OK))
             return PERC_ECUDA;
         uint2 *recs = reinterpret_cast<uint2 *>(a_keys);  // a_keys then a_vals: chunk * N * 8 bytes
+        // counts, cursors and (prefix) the per-seed last bucket: within the radix histogram area
+        if (size_t(2) * chunk * row + chunk > size_t(256) * T * chunk) return PERC_EINVAL;
         for (uint32_t s0 = 0; s0 < num_seeds; s0 += chunk) {
             const uint32_t S = min(chunk, num_seeds - s0);
             uint32_t *counts = hist, *cursors = hist + size_t(S) * row;
+            uint32_t *cut = share ? cursors + size_t(S) * row : nullptr;
             if (cudaMemsetAsync(counts, 0, size_t(S) * row * 4, stream) != cudaSuccess) return PERC_ECUDA;
             k_rank_bcount<<<dim3(Tb, S), kRankThreads, smem_count, stream>>>(uint32_t(N), Bb, seeds + s0, counts);
             k_rank_scan<<<S, 1024, 0, stream>>>(row, counts, cursors);
-            k_rank_bplace<<<dim3(Tb, S), kRankThreads, smem_place, stream>>>(uint32_t(N), Bb, seeds + s0, cursors, recs);
+            if (cut) k_bucket_cut<<<(S + 255) / 256, 256, 0, stream>>>(uint32_t(N), Bb, S, counts, share, cut);
+            k_rank_bplace<<<dim3(Tb, S), kRankThreads, smem_place, stream>>>(uint32_t(N), Bb, seeds + s0, cursors, recs,
+                                                                             cut);
             if (big)
                 k_rank_bsort_big<<<dim3(nb, S), kBSortBigThreads, smem_big, stream>>>(
-                    uint32_t(N), Bb, sub_bits, cap, counts, recs, perm + size_t(s0) * N, rank + size_t(s0) * N);
+                    uint32_t(N), Bb, sub_bits, cap, counts, recs, perm + size_t(s0) * N, rank + size_t(s0) * N, cut);
             else
                 k_rank_bsort<<<dim3(nb, S), kBSortThreads, 0, stream>>>(uint32_t(N), Bb, counts, recs,
-                                                                       perm + size_t(s0) * N, rank + size_t(s0) * N);
+                                                                       perm + size_t(s0) * N, rank + size_t(s0) * N,
+                                                                       cut);
         }
         return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
     }
@@ -868,5 +929,26 @@ extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, 
             }
         }
     }
+    return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
+}
+
+extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, uint32_t *perm, uint32_t *rank,
+                         void *workspace, size_t ws_bytes, void *stream)
+{
+    return rank_impl(L, seeds, num_seeds, nullptr, perm, rank, workspace, ws_bytes, stream);
+}
+
+extern "C" int perc_rank_prefix(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, const uint32_t *share,
+                                uint32_t *perm, uint32_t *rank, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!share) return PERC_EINVAL;
+    return rank_impl(L, seeds, num_seeds, share, perm, rank, workspace, ws_bytes, stream);
+}
+
+extern "C" int perc_prefix_share(const perc_sample *samples, uint32_t num_samples, const uint32_t *bracket,
+                                 uint32_t *share, void *stream)
+{
+    if (!samples || !bracket || !share || num_samples == 0) return PERC_EINVAL;
+    k_prefix_share<<<1, 1024, 0, static_cast<cudaStream_t>(stream)>>>(samples, bracket, num_samples, share);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }

@@ -412,7 +412,7 @@ class NstarStep:
     """
 
     def __init__(self, L: int, masks, seeds, params: torch.Tensor | None = None, margin: float = 0.0,
-                 axes: int = 1, any_axis: bool = False):
+                 axes: int = 1, any_axis: bool = False, prefix: bool = False):
         self.L = int(L)
         self.axes = int(axes)
         self.any_axis = bool(any_axis)
@@ -441,6 +441,9 @@ class NstarStep:
                  perc.workspace_bytes(perc.OP_NSTAR_ANY if self.any_axis else perc.OP_NSTAR, self.L, self.launch_num))
         self.ws = perc.new_workspace(nb)
         self.lib = perc.lib()
+        # learned steps rank only the start of each order (perc_rank_prefix) when asked to
+        self.prefix = bool(prefix) and params is not None and A == 1 and not self.any_axis
+        self.share = torch.zeros(2, dtype=torch.int32, device="cuda")  # [share, unresolved]
 
     def run_rank(self, stream=None):
         sp = perc._stream(stream)
@@ -462,14 +465,56 @@ class NstarStep:
                                                   self.nstar_any.data_ptr(), perc._stream(stream)),
                      "perc_nstar_min_axes")
 
+    def run_prefix_rank(self, stream=None):
+        """perc_prefix_share of the brackets (run_bracket first), then perc_rank_prefix."""
+        sp = perc._stream(stream)
+        share = self.share.data_ptr()
+        perc._ok(self.lib.perc_prefix_share(self.samples.data_ptr(), self.launch_num, self.bracket.data_ptr(),
+                                            share, sp), "perc_prefix_share")
+        perc._ok(self.lib.perc_rank_prefix(self.L, self.seeds_dev.data_ptr(), len(self.seeds), share,
+                                           self.perm.data_ptr(), self.rank.data_ptr(), self.ws.data_ptr(),
+                                           self.ws.numel(), sp), "perc_rank_prefix")
+
+    def run_prefix_nstar(self, stats: torch.Tensor | None = None, stream=None):
+        """perc_nstar_prefix on the prefix orders (the unresolved count zeroed first)."""
+        sp = perc._stream(stream)
+        self.share[1:].zero_()
+        perc._ok(self.lib.perc_nstar_prefix(self.samples.data_ptr(), self.launch_num, self.L, self.bracket.data_ptr(),
+                                            self.share.data_ptr(), self.share.data_ptr() + 4, self.nstar.data_ptr(),
+                                            self.passes.data_ptr(), perc._ptr(stats), self.ws.data_ptr(),
+                                            self.ws.numel(), sp), "perc_nstar_prefix")
+
+    def run_prefix(self, stats: torch.Tensor | None = None, stream=None):
+        """The learned step on orders ranked only up to the brackets' share of the lattice (``finish``
+        handles the rare sample whose n* lies past the ranked prefix)."""
+        self.run_bracket(stream)
+        self.run_prefix_rank(stream)
+        self.run_prefix_nstar(stats, stream)
+
     def run(self, learned: bool = True, stats: torch.Tensor | None = None, stream=None):
+        if learned and self.prefix:
+            self.run_prefix(stats, stream)
+            return
         self.run_rank(stream)
         if learned:
             self.run_bracket(stream)
         self.run_nstar(learned, stats, stream)
 
+    def finish(self) -> int:
+        """After a prefix step (synchronises): the samples whose n* lies past the ranked prefix get
+        their orders in full and perc_nstar; returns how many there were."""
+        if not self.prefix or int(self.share[1].item()) == 0:
+            return 0
+        idx = np.nonzero(perc.u32(self.nstar) == perc.NEVER)[0]
+        if len(idx):
+            got, _ = nstar(self.workload[idx], self.params, self.margin)
+            self.nstar[torch.as_tensor(idx, device="cuda")] = torch.as_tensor(got.view(np.int32), device="cuda")
+        self.share[1:].zero_()
+        return len(idx)
+
     def capture(self, learned: bool = True) -> torch.cuda.CUDAGraph:
-        """CUDA graph of one step (warm the library up with ``run`` first)."""
+        """CUDA graph of one step (warm the library up with ``run`` first; after a replay of a
+        prefix step, ``finish`` completes it)."""
         g = torch.cuda.CUDAGraph()
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
@@ -479,6 +524,7 @@ class NstarStep:
         return g
 
     def result(self):
+        self.finish()
         rc = self.lib.perc_check(self.ws.data_ptr(), perc._stream())
         if rc != 0:
             raise perc.PercError(rc, "perc_nstar device status")
@@ -528,8 +574,10 @@ class BatchStep:
     """
 
     def __init__(self, workload, params: torch.Tensor | None = None, margin: float = 0.0,
-                 budget: int | None = None, options=None):
+                 budget: int | None = None, options=None, prefix: bool = False):
         self.workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
+        # learned steps rank only the start of each order (perc_rank_prefix) when asked to
+        self.prefix = bool(prefix) and params is not None
         self.num = len(self.workload)
         self.params = params
         self.margin = float(margin)
@@ -552,6 +600,8 @@ class BatchStep:
             ch["bracket"] = torch.empty((ch["n"], 2), dtype=torch.int32, device="cuda")
             ch["nstar"] = torch.empty(ch["n"], dtype=torch.int32, device="cuda")
             ch["passes"] = torch.empty(ch["n"], dtype=torch.int32, device="cuda")
+        # per chunk [share, unresolved] of the prefix steps
+        self.share = torch.zeros((len(self.chunks), 2), dtype=torch.int32, device="cuda")
         self.options = list(options) if options is not None else [None] * len(self.chunks)
         self.ws = None
         self._size_workspace()
@@ -600,10 +650,50 @@ class BatchStep:
         finally:
             self._apply(None)
 
+    def run_prefix(self, k: int, stats: torch.Tensor | None = None, stream=None):
+        """Chunk k's learned step on orders ranked only up to the bracket's share of the lattice
+        (perc_bracket, perc_prefix_share, perc_rank_prefix per side, perc_nstar_prefix)."""
+        ch, sp = self.chunks[k], perc._stream(stream)
+        share = self.share[k].data_ptr()
+        perc._ok(self.lib.perc_bracket(self.params.data_ptr(), ch["samples"].data_ptr(), ch["n"], self.margin,
+                                       ch["bracket"].data_ptr(), sp), "perc_bracket")
+        perc._ok(self.lib.perc_prefix_share(ch["samples"].data_ptr(), ch["n"], ch["bracket"].data_ptr(), share, sp),
+                 "perc_prefix_share")
+        base = self.orders.data_ptr()
+        for g in ch["groups"]:
+            perc._ok(self.lib.perc_rank_prefix(g["L"], g["seeds"].data_ptr(), g["S"], share, base + g["off"],
+                                               base + g["roff"], self.ws.data_ptr(), self.ws.numel(), sp),
+                     "perc_rank_prefix")
+        self.share[k, 1:].zero_()
+        perc._ok(self.lib.perc_nstar_prefix(ch["samples"].data_ptr(), ch["n"], ch["max_L"], ch["bracket"].data_ptr(),
+                                            share, share + 4, ch["nstar"].data_ptr(), ch["passes"].data_ptr(),
+                                            perc._ptr(stats), self.ws.data_ptr(), self.ws.numel(), sp),
+                 "perc_nstar_prefix")
+
     def run(self, learned: bool = True, stats: torch.Tensor | None = None, stream=None):
         for k in range(len(self.chunks)):
+            if learned and self.prefix:
+                self.run_prefix(k, stats, stream)
+                continue
             self.run_rank(k, stream)
             self.run_nstar(k, learned, stats, stream)
+
+    def finish(self) -> int:
+        """After a prefix step (synchronises): the samples whose n* lies past their chunk's ranked
+        prefix get their orders in full and perc_nstar; returns how many there were."""
+        if not self.prefix:
+            return 0
+        counts = perc.u32(self.share[:, 1])
+        done = 0
+        for k in np.nonzero(counts)[0]:
+            ch = self.chunks[k]
+            idx = np.nonzero(perc.u32(ch["nstar"]) == perc.NEVER)[0]
+            if len(idx):
+                got, _ = nstar(self.workload[ch["idx"][idx]], self.params, self.margin)
+                ch["nstar"][torch.as_tensor(idx, device="cuda")] = torch.as_tensor(got.view(np.int32), device="cuda")
+                done += len(idx)
+        self.share[:, 1:].zero_()
+        return done
 
     def capture(self, learned: bool = True) -> torch.cuda.CUDAGraph:
         """CUDA graph of the whole batch (warm the library up with ``run`` first)."""
@@ -617,6 +707,7 @@ class BatchStep:
 
     def result(self):
         """(n*, passes) as numpy uint32 in workload order (synchronises; raises on a device error)."""
+        self.finish()
         rc = self.lib.perc_check(self.ws.data_ptr(), perc._stream())
         if rc != 0:
             raise perc.PercError(rc, "perc_nstar device status")

@@ -69,6 +69,9 @@ def lib() -> ctypes.CDLL:
         "perc_bracket": (i32, [vp, vp, u32, f32, vp, vp]),
         "perc_status_string": (ctypes.c_char_p, [i32]),
         "perc_microbench": (i32, [i32, vp, sz, u32, ctypes.POINTER(ctypes.c_double), vp]),
+        "perc_prefix_share": (i32, [vp, u32, vp, vp, vp]),
+        "perc_rank_prefix": (i32, [u32, vp, u32, vp, vp, vp, vp, sz, vp]),
+        "perc_nstar_prefix": (i32, [vp, u32, u32, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -84,7 +87,8 @@ def exported_symbols() -> list[str]:
             "perc_mass_periodic", "perc_nstar_wrap", "perc_microbench",
             "perc_smax_window", "perc_binomial_weights", "perc_pmax", "perc_check",
             "perc_mlp_forward", "perc_mlp_grad", "perc_adam", "perc_mlp_train", "perc_bracket",
-            "perc_status_string", "perc_set_launch_option"]
+            "perc_status_string", "perc_set_launch_option", "perc_prefix_share", "perc_rank_prefix",
+            "perc_nstar_prefix"]
 
 
 def status_string(rc: int) -> str:
@@ -408,3 +412,9 @@ def microbench(which: int, buf: torch.Tensor, iters: int, stream=None) -> float:
     _ok(lib().perc_microbench(which, buf.data_ptr(), buf.numel() * buf.element_size(), iters, ctypes.byref(units),
                               _stream(stream)), "perc_microbench")
     return units.value
+
+
+def prefix_sites(N: int, share: int) -> int:
+    """PERC_PREFIX_SITES: sites of an order that perc_rank_prefix ranks at least for `share`."""
+    base = (int(N) * min(int(share), 1 << 24)) >> 24
+    return min(int(N), base * 9 // 8 + 64)
