@@ -1,8 +1,11 @@
 """Benchmark: samples/s of exact n* at L = 16 over all 127 neighborhoods (seeds 1..256 per rank),
 learned bracket vs plain bracket, on one B300 per rank.
 
-One step = the whole path for one batch: perc_rank of the 256 seeds, the bracket network on the
-32,512 samples (learned arm), and the persistent perc_nstar launch.  Inputs (seeds, sample table,
+One step = the whole path for one batch.  Learned arm: the bracket network on the 32,512 samples,
+the share of each order its upper ends need (perc_prefix_share), the ranking of that share of the
+256 seeds' orders (perc_rank_prefix) and the persistent n* launch on it (perc_nstar_prefix), plus
+the full order and perc_nstar for any sample whose n* lies past the ranked prefix (--no-prefix:
+every site ranked).  Plain arm: perc_rank of every site and perc_nstar.  Inputs (seeds, sample table,
 network parameters) are resident in HBM when the timed region starts; L2 is flushed between steps
 and the site orders (2 GiB) are larger than L2 anyway.  `e2e` repeats the step through the C ABI
 from pinned host buffers with the host<->device copies inside the timed region.
