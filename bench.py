@@ -15,7 +15,8 @@ from pinned host buffers with the host<->device copies inside the timed region.
 Under torchrun every rank runs its own seed block (weak scaling, no collective on the data path);
 rank 0 prints one JSON line.  `--impl reference` times the CPU oracle on the same workload.
 
-`--workload pmax` measures the P_max(p) path instead: one step = perc_rank of the seeds, the
+`--workload pmax` measures the P_max(p) path instead: one step = perc_rank_prefix of the seeds (the
+start of each order up to the largest window end), the
 binomial weights of 16 probabilities per neighborhood (p_c of Table I, +-2%), S_max(n) over the
 window of n outside which each binomial has less than 1e-16 on either side, and the convolution to
 P_max(p) (eq. Pmax).
@@ -477,15 +478,16 @@ def run_ours(args):
             perc._ok(lib.perc_rank_prefix(L, seeds_d2.data_ptr(), len(seeds), share_d.data_ptr(), perm.data_ptr(),
                                           rk.data_ptr(), ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_rank_prefix")
             share_d[1:].zero_()
-            perc._ok(lib.perc_nstar_prefix(samples_d2.data_ptr(), nl, L, br.data_ptr(), share_d.data_ptr(),
-                                           share_d.data_ptr() + 4, ns.data_ptr(), None, None, ws_buf.data_ptr(),
-                                           ws_buf.numel(), sp), "perc_nstar_prefix")
+            perc._ok((lib.perc_nstar_any_prefix if any_axis else lib.perc_nstar_prefix)(
+                samples_d2.data_ptr(), nl, L, br.data_ptr(), share_d.data_ptr(), share_d.data_ptr() + 4,
+                ns.data_ptr(), None, None, ws_buf.data_ptr(), ws_buf.numel(), sp), "perc_nstar_prefix")
             ns_host.copy_(ns, non_blocking=True)
             unres_host.copy_(share_d[1:], non_blocking=True)
             torch.cuda.current_stream().synchronize()
             if int(unres_host[0]) > 0:  # samples past the ranked prefix: full orders, perc_nstar
                 idx = np.nonzero(ns_host.numpy().view(np.uint32) == perc.NEVER)[0]
-                got, _ = driver.nstar(step_obj.workload[idx], params, args.margin)
+                got, _ = (driver.nstar_any_sweep if any_axis else driver.nstar)(step_obj.workload[idx], params,
+                                                                                  args.margin)
                 ns_host.numpy()[idx] = got.view(np.int32)
             return
         perc._ok(lib.perc_rank(L, seeds_d2.data_ptr(), len(seeds), perm.data_ptr(), rk.data_ptr(),
@@ -723,15 +725,16 @@ def run_pmax_ours(args):
 
     # ---- e2e through the C ABI from pinned host buffers
     host = {k: getattr(st, k).cpu().pin_memory() for k in ("seeds_dev", "samples", "n_lo", "cnt", "group_dev",
-                                                            "Ng_dev", "lo_dev", "pg_dev", "count_dev")}
+                                                            "Ng_dev", "lo_dev", "pg_dev", "count_dev", "share")}
     dev2 = {k: torch.empty_like(getattr(st, k)) for k in host}
     pm_host = torch.empty_like(st.pmax, device="cpu").pin_memory()
 
     def e2e_step():
         for k in host:
             dev2[k].copy_(host[k], non_blocking=True)
-        perc._ok(lib.perc_rank(L, dev2["seeds_dev"].data_ptr(), len(seeds), st.perm.data_ptr(), st.rank.data_ptr(),
-                               st.ws.data_ptr(), st.ws.numel(), sp), "perc_rank")
+        perc._ok(lib.perc_rank_prefix(L, dev2["seeds_dev"].data_ptr(), len(seeds), dev2["share"].data_ptr(),
+                                      st.perm.data_ptr(), st.rank.data_ptr(), st.ws.data_ptr(), st.ws.numel(), sp),
+                 "perc_rank_prefix")
         perc._ok(lib.perc_binomial_weights(dev2["Ng_dev"].data_ptr(), dev2["lo_dev"].data_ptr(),
                                            dev2["count_dev"].data_ptr(), st.G, st.window, dev2["pg_dev"].data_ptr(),
                                            st.np, st.w.data_ptr(), sp), "perc_binomial_weights")
@@ -790,7 +793,7 @@ def run_pmax_ours(args):
         cpu = cpu_baseline(range(1, n_seeds_cpu + 1), cpu_workers, _oracle_pmax_seed,
                            f"L=16, seeds 1..{n_seeds_cpu} x 127 masks, 16 p each, one ranking per seed")
 
-    gpu_launches = rank_launches(L, len(seeds)) + 3  # rank + weights + S_max + P_max
+    gpu_launches = rank_launches(L, len(seeds), True) - 1 + 3  # rank (prefix, share from the host) + weights + S_max + P_max
     value = world * num / (ms_step * 1e-3)
     if rank == 0:
         line = {

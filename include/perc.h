@@ -385,6 +385,9 @@ int perc_bracket(const float *params, const perc_sample *samples, uint32_t num_s
  *   method always), plus
  *     share       device uint32, as for perc_rank_prefix (the same value)
  *     unresolved  device uint32, incremented (the caller zeroes it)
+ *
+ * perc_nstar_any_prefix -- the same for perc_nstar_any (spanning along any axis; workspace
+ *   PERC_OP_NSTAR_ANY); its unresolved samples need perc_nstar_any on full orders.
  */
 #define PERC_PREFIX_BASE_(N, share) \
     (((uint64_t)(N) * ((share) < (1u << 24) ? (uint64_t)(share) : (uint64_t)(1u << 24))) >> 24)
@@ -400,6 +403,10 @@ int perc_nstar_prefix(const perc_sample *samples, uint32_t num_samples, uint32_t
                       const uint32_t *bracket, const uint32_t *share, uint32_t *unresolved,
                       uint32_t *nstar, uint32_t *passes, perc_stats *stats, void *workspace,
                       size_t ws_bytes, void *stream);
+int perc_nstar_any_prefix(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                          const uint32_t *bracket, const uint32_t *share, uint32_t *unresolved,
+                          uint32_t *nstar, uint32_t *passes, perc_stats *stats, void *workspace,
+                          size_t ws_bytes, void *stream);
 
 /*
  * perc_microbench -- on-chip throughput probes (not in the paper): the peaks that the n* kernels,

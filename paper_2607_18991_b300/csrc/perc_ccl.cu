@@ -2765,14 +2765,15 @@ extern "C" int perc_nstar_any(const perc_sample *samples, uint32_t num_samples, 
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }
 
-extern "C" int perc_nstar_prefix(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
-                                 const uint32_t *bracket, const uint32_t *share, uint32_t *unresolved,
-                                 uint32_t *nstar, uint32_t *passes, perc_stats *stats, void *workspace,
-                                 size_t ws_bytes, void *stream_)
+// The sweep on orders ranked only up to prefix_sites(L^5, *share) (perc_nstar_prefix along the
+// sample's axis, perc_nstar_any_prefix along any axis).
+static int nstar_prefix(bool any, const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                        const uint32_t *bracket, const uint32_t *share, uint32_t *unresolved, uint32_t *nstar,
+                        uint32_t *passes, perc_stats *stats, void *workspace, size_t ws_bytes, void *stream_)
 {
     if (!samples || !share || !unresolved || !nstar || !workspace || num_samples == 0) return PERC_EINVAL;
     LaunchCfg cfg;
-    const int rc = launch_cfg(kOpSweep, max_L, num_samples, cfg);
+    const int rc = launch_cfg(any ? kOpSweepAny : kOpSweep, max_L, num_samples, cfg);
     if (rc != PERC_OK) return rc;
     if (ws_bytes < cfg_ws_bytes(cfg)) return PERC_EWORKSPACE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
@@ -2780,8 +2781,26 @@ extern "C" int perc_nstar_prefix(const perc_sample *samples, uint32_t num_sample
     k_nstar_sweep<<<cfg.grid, cfg.threads, cfg.smem, stream>>>(samples, num_samples, max_L, cfg.smem_L, cfg.sum_L,
                                                                cfg.region, cfg.node_cap, cfg.edge_scap, bracket, nstar,
                                                                passes, stats, static_cast<char *>(workspace),
-                                                               cfg.slot_bytes, 0u, share, unresolved);
+                                                               cfg.slot_bytes, any ? 1u : 0u, share, unresolved);
     return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
+}
+
+extern "C" int perc_nstar_prefix(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                                 const uint32_t *bracket, const uint32_t *share, uint32_t *unresolved,
+                                 uint32_t *nstar, uint32_t *passes, perc_stats *stats, void *workspace,
+                                 size_t ws_bytes, void *stream)
+{
+    return nstar_prefix(false, samples, num_samples, max_L, bracket, share, unresolved, nstar, passes, stats,
+                        workspace, ws_bytes, stream);
+}
+
+extern "C" int perc_nstar_any_prefix(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
+                                     const uint32_t *bracket, const uint32_t *share, uint32_t *unresolved,
+                                     uint32_t *nstar, uint32_t *passes, perc_stats *stats, void *workspace,
+                                     size_t ws_bytes, void *stream)
+{
+    return nstar_prefix(true, samples, num_samples, max_L, bracket, share, unresolved, nstar, passes, stats,
+                        workspace, ws_bytes, stream);
 }
 
 extern "C" int perc_mass(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,

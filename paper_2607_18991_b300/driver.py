@@ -442,7 +442,7 @@ class NstarStep:
         self.ws = perc.new_workspace(nb)
         self.lib = perc.lib()
         # learned steps rank only the start of each order (perc_rank_prefix) when asked to
-        self.prefix = bool(prefix) and params is not None and A == 1 and not self.any_axis
+        self.prefix = bool(prefix) and params is not None and A == 1
         self.share = torch.zeros(2, dtype=torch.int32, device="cuda")  # [share, unresolved]
 
     def run_rank(self, stream=None):
@@ -476,13 +476,14 @@ class NstarStep:
                                            self.ws.numel(), sp), "perc_rank_prefix")
 
     def run_prefix_nstar(self, stats: torch.Tensor | None = None, stream=None):
-        """perc_nstar_prefix on the prefix orders (the unresolved count zeroed first)."""
+        """perc_nstar_prefix (perc_nstar_any_prefix) on the prefix orders (the unresolved count
+        zeroed first)."""
         sp = perc._stream(stream)
         self.share[1:].zero_()
-        perc._ok(self.lib.perc_nstar_prefix(self.samples.data_ptr(), self.launch_num, self.L, self.bracket.data_ptr(),
-                                            self.share.data_ptr(), self.share.data_ptr() + 4, self.nstar.data_ptr(),
-                                            self.passes.data_ptr(), perc._ptr(stats), self.ws.data_ptr(),
-                                            self.ws.numel(), sp), "perc_nstar_prefix")
+        fn = self.lib.perc_nstar_any_prefix if self.any_axis else self.lib.perc_nstar_prefix
+        perc._ok(fn(self.samples.data_ptr(), self.launch_num, self.L, self.bracket.data_ptr(), self.share.data_ptr(),
+                    self.share.data_ptr() + 4, self.nstar.data_ptr(), self.passes.data_ptr(), perc._ptr(stats),
+                    self.ws.data_ptr(), self.ws.numel(), sp), "perc_nstar_prefix")
 
     def run_prefix(self, stats: torch.Tensor | None = None, stream=None):
         """The learned step on orders ranked only up to the brackets' share of the lattice (``finish``
@@ -507,7 +508,8 @@ class NstarStep:
             return 0
         idx = np.nonzero(perc.u32(self.nstar) == perc.NEVER)[0]
         if len(idx):
-            got, _ = nstar(self.workload[idx], self.params, self.margin)
+            full = nstar_any_sweep if self.any_axis else nstar
+            got, _ = full(self.workload[idx], self.params, self.margin)
             self.nstar[torch.as_tensor(idx, device="cuda")] = torch.as_tensor(got.view(np.int32), device="cuda")
         self.share[1:].zero_()
         return len(idx)
@@ -757,11 +759,16 @@ class PmaxStep:
         nb = max(perc.workspace_bytes(perc.OP_RANK, self.L, S), perc.workspace_bytes(perc.OP_SMAX, self.L, self.num))
         self.ws = perc.new_workspace(nb)
         self.lib = perc.lib()
+        # S_max(n) is asked for n < lo + count only, so only that start of each order is ranked
+        # (perc_rank_prefix with the share that covers the largest window end)
+        need = int(min(N, int(np.max(self.lo[self.group] + self.count[self.group]))))
+        self.share = torch.tensor([min(1 << 24, -(-(need << 24) // N)), 0], dtype=torch.int32, device="cuda")
+        assert perc.prefix_sites(N, int(self.share[0].item())) >= need
 
     def run_rank(self, stream=None):
-        perc._ok(self.lib.perc_rank(self.L, self.seeds_dev.data_ptr(), len(self.seeds), self.perm.data_ptr(),
-                                    self.rank.data_ptr(), self.ws.data_ptr(), self.ws.numel(), perc._stream(stream)),
-                 "perc_rank")
+        perc._ok(self.lib.perc_rank_prefix(self.L, self.seeds_dev.data_ptr(), len(self.seeds), self.share.data_ptr(),
+                                           self.perm.data_ptr(), self.rank.data_ptr(), self.ws.data_ptr(),
+                                           self.ws.numel(), perc._stream(stream)), "perc_rank_prefix")
 
     def run_weights(self, stream=None):
         perc._ok(self.lib.perc_binomial_weights(self.Ng_dev.data_ptr(), self.lo_dev.data_ptr(),

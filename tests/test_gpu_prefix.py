@@ -159,3 +159,35 @@ def test_batch_prefix_mixed_sides_match_oracle():
     g.replay()
     got_g, _ = step.result()
     assert np.array_equal(got_g, want)
+
+
+
+def test_any_axis_prefix_step_matches_oracle():
+    import oracle
+    from gpu_util import orc_nstar_rule
+
+    from paper_2607_18991_b300 import bracket as pbracket
+    from paper_2607_18991_b300 import driver
+    train = np.array([(12, m, s) for m in range(1, 128, 2) for s in (9001, 9002)])
+    ns_train, _ = driver.nstar_any_sweep(train)
+    params, _ = pbracket.train(train[:, 0], train[:, 1], ns_train, steps=600, lr=3e-3, seed=0)
+    step = driver.NstarStep(12, range(1, 128, 9), (1, 2), params=params, margin=0.05, any_axis=True, prefix=True)
+    assert step.prefix
+    want = orc_nstar_rule(step.workload, oracle.SPAN_ANY)
+    step.run(True)
+    got, _ = step.result()
+    assert np.array_equal(got, want)
+
+
+def test_pmax_step_ranks_only_the_windows():
+    from paper_2607_18991_b300 import driver, perc, workloads
+    p_of_mask = {m: workloads.pmax_grid(m) for m in range(2, 128, 21)}  # zone 1 alone would need most sites
+    st = driver.PmaxStep(12, sorted(p_of_mask), (1, 2), p_of_mask)
+    share = int(st.share[0].item())
+    assert 0 < share < 1 << 24
+    st.run_rank()
+    torch.cuda.synchronize()
+    K = perc.prefix_sites(12 ** 5, share)
+    for s, seed in enumerate((1, 2)):
+        want_perm, _ = orc_order(12, seed)
+        assert np.array_equal(perc.u32(st.perm[s, :K]), want_perm[:K])
