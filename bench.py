@@ -998,7 +998,7 @@ def run_mixed_ours(args):
     params, losses = train_bracket(args)
     wl = mixed_workload(rank)
     num = len(wl)
-    step = driver.BatchStep(wl, params=params, margin=args.margin, prefix=not args.no_prefix)
+    step = driver.BatchStep(wl, params=params, margin=args.margin, prefix=not args.no_prefix, by_cost=True)
     tuned = None if args.no_tune else autotune.tune_batch(step, learned=True)
     fallbacks = {"steps": 0, "samples": 0}
     for learned in (True, False):
@@ -1127,7 +1127,8 @@ def run_mixed_ours(args):
             "data": "synthetic (Philox-keyed site orders, seeds per rank)",
             "config": {"workload": "mixed batch of 4096 samples: L uniform in 10..40, zone masks uniform in 1..127, "
                                    "seed j+1 (numpy PCG64, seed 4096), one CUDA graph over all chunks",
-                       "samples_per_rank": num, "chunks": len(step.chunks), "bracket": "learned",
+                       "samples_per_rank": num, "chunks": len(step.chunks), "chunking": "slowest samples first (driver.sample_cost)",
+                       "bracket": "learned",
                        "margin": args.margin, "l2": "flushed (256 MiB write) between timed steps; orders > L2",
                        "parallelism": f"dp{world} (seed blocks, no collective)"},
             "plain": {"value": world * num / (ms_plain * 1e-3), "unit": "samples/s", "ms_per_step": ms_plain},

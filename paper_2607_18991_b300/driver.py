@@ -27,12 +27,32 @@ def default_budget() -> int:
 DEFAULT_BUDGET = None  # resolved by default_budget() on first use
 
 
-def _chunks(workload: np.ndarray, budget: int | None):
-    """Split sample indices so that the distinct (L, seed) orders of a chunk fit in `budget`."""
+ZONE_SIZES = np.array([10, 40, 80, 90, 112, 240, 320])
+
+
+def sample_cost(workload: np.ndarray) -> np.ndarray:
+    """Relative cost of the n* sweep of each row (L, zone word, seed), for scheduling only: the sites
+    it adds up to n* (L^5 times the neighborhood's Table I p_c) times a per-site cost that grows with
+    the neighborhood's size z, about (363 + z) as measured at L = 32..40."""
+    from .workloads import TABLE1_PC
+    masks = workload[:, 1] & 0x7F
+    pc = np.array([TABLE1_PC.get(int(m), 0.01) for m in masks])
+    z = np.array([int(ZONE_SIZES[[(int(m) >> i) & 1 == 1 for i in range(7)]].sum()) for m in masks])
+    return workload[:, 0].astype(np.float64) ** 5 * pc * (363.0 + z)
+
+
+def _chunks(workload: np.ndarray, budget: int | None, by_cost: bool = False):
+    """Split sample indices so that the distinct (L, seed) orders of a chunk fit in `budget`.  By
+    default the largest L come first, then seed-major: the CTAs running at the same time share one
+    site order, which then stays in L2 while all its masks are processed.  With by_cost the rows
+    come in falling sample_cost order instead: a batch of one seed per sample shares no order, and
+    a chunk's launch lasts as long as its slowest sample, so the slow samples share chunks and
+    each chunk's queue hands out its slowest samples first."""
     budget = budget or default_budget()
-    # largest L first, then seed-major: the CTAs running at the same time share one site order,
-    # which then stays in L2 while all its masks are processed
-    order = np.lexsort((workload[:, 1], workload[:, 2], -workload[:, 0]))
+    if by_cost:
+        order = np.argsort(-sample_cost(workload), kind="stable")
+    else:
+        order = np.lexsort((workload[:, 1], workload[:, 2], -workload[:, 0]))
     chunk, seen, used = [], set(), 0
     for idx in order:
         L, _, seed = (int(v) for v in workload[idx])
@@ -566,7 +586,8 @@ class BatchStep:
     fixed-shape step.
 
     The batch is split into chunks whose site orders fit the memory budget (largest lattices
-    first, every (L, seed) order ranked once per chunk).  Every device buffer is allocated here:
+    first, or with ``by_cost`` the slowest samples first, every (L, seed) order ranked once per
+    chunk).  Every device buffer is allocated here:
     one order buffer that every chunk reuses, each chunk's seeds, sample table, brackets and
     outputs, and one workspace.  ``run`` therefore only enqueues library calls -- per chunk
     perc_rank of its orders, perc_bracket and perc_nstar -- with no host synchronisation between
@@ -576,7 +597,7 @@ class BatchStep:
     """
 
     def __init__(self, workload, params: torch.Tensor | None = None, margin: float = 0.0,
-                 budget: int | None = None, options=None, prefix: bool = False):
+                 budget: int | None = None, options=None, prefix: bool = False, by_cost: bool = False):
         self.workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
         # learned steps rank only the start of each order (perc_rank_prefix) when asked to
         self.prefix = bool(prefix) and params is not None
@@ -586,7 +607,7 @@ class BatchStep:
         self.lib = perc.lib()
         self.chunks = []
         order_bytes = 0
-        for idx in _chunks(self.workload, budget):
+        for idx in _chunks(self.workload, budget, by_cost):
             groups, perm_rel, rank_rel, nbytes = chunk_layout(self.workload[idx])
             for g in groups:
                 g["seeds"] = torch.as_tensor(g["seeds"].astype(np.int64), device="cuda")

@@ -47,6 +47,21 @@ def test_mixed_sides_and_oversized_orders():
     assert len(chunks) == 2 and all(len(c) == 2 for c in chunks)
 
 
+def test_cost_ordered_chunks():
+    # by_cost: every sample once, chunks within the budget, and the rows in falling cost order
+    # across and inside chunks; the cost grows with L and with the neighborhood's threshold
+    w = workloads.mixed4096(500)
+    chunks = list(driver._chunks(w, 256 << 20, by_cost=True))
+    idx = np.concatenate(chunks)
+    assert np.array_equal(np.sort(idx), np.arange(len(w)))
+    cost = driver.sample_cost(w)
+    assert np.all(np.diff(cost[idx]) <= 0)
+    for c in chunks:
+        assert order_bytes(w[c]) <= 256 << 20 or len(c) == 1
+    c = driver.sample_cost(np.array([(16, 1, 1), (16, 127, 1), (32, 127, 1)]))
+    assert c[0] > c[1] and c[2] > c[1]
+
+
 def test_batch_layout_aligned_and_disjoint():
     """The shared order buffer of a captured batch: every perm and rank block starts on a 256-byte
     boundary (the ranking's tile copies read 16-byte aligned rows, also after a side with odd L^5),

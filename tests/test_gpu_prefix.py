@@ -147,7 +147,7 @@ def test_batch_prefix_mixed_sides_match_oracle():
     train = np.array([(L, m, s) for L in (8, 16) for m in range(1, 128, 3) for s in (7001, 7002)])
     ns_train, _ = driver.nstar(train)
     params, _ = pbracket.train(train[:, 0], train[:, 1], ns_train, steps=600, lr=3e-3, seed=0)
-    step = driver.BatchStep(wl, params=params, margin=0.05, budget=64 << 20, prefix=True)
+    step = driver.BatchStep(wl, params=params, margin=0.05, budget=64 << 20, prefix=True, by_cost=True)
     assert len(step.chunks) > 1
     want = orc_nstar(wl)
     step.run(True)
