@@ -72,17 +72,23 @@ def rank_launches(L: int, num_seeds: int, prefix: bool = False) -> int:
     return math.ceil(num_seeds / 64) * per_chunk + (1 if prefix else 0)
 
 
-def train_bracket(args, any_axis: bool = False):
+def train_bracket(args, any_axis: bool = False, big: bool = False):
     """The bracket network, trained on plain n* of held-out seeds (1,000,001..) at the shapes of the
     first two workloads: zone 1 at L = 8 and all 127 neighborhoods at L = 16 (the any-axis n* of the
-    same rows for the any-axis workload)."""
+    same rows for the any-axis workload).  With big (the mixed batch, L up to 40) also all 127
+    neighborhoods at L = 24 (8 seeds) and L = 32 (4 seeds), so that ln L is learned across the
+    batch's range instead of extrapolated from 8 and 16."""
     import torch
 
     from paper_2607_18991_b300 import bracket as pbracket
     from paper_2607_18991_b300 import driver
     train_seeds = np.arange(1, args.train_seeds + 1) + 1_000_000
-    wl_train = np.concatenate([np.array([(8, 1, s) for s in range(1_000_001, 1_001_001)]),
-                               np.array([(16, m, int(s)) for m in MASKS for s in train_seeds])])
+    parts = [np.array([(8, 1, s) for s in range(1_000_001, 1_001_001)]),
+             np.array([(16, m, int(s)) for m in MASKS for s in train_seeds])]
+    if big:
+        parts += [np.array([(L, m, s) for m in MASKS for s in range(1_000_001, 1_000_001 + k)])
+                  for L, k in ((24, 8), (32, 4))]
+    wl_train = np.concatenate(parts)
     ns_train, _ = driver.nstar_any_sweep(wl_train) if any_axis else driver.nstar(wl_train)
     params, losses = pbracket.train(wl_train[:, 0], wl_train[:, 1], ns_train, steps=args.train_steps,
                                     lr=args.lr, seed=0)
@@ -995,7 +1001,7 @@ def run_mixed_ours(args):
     pbuild.build()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    params, losses = train_bracket(args)
+    params, losses = train_bracket(args, big=True)
     wl = mixed_workload(rank)
     num = len(wl)
     step = driver.BatchStep(wl, params=params, margin=args.margin, prefix=not args.no_prefix, by_cost=True)

@@ -2275,14 +2275,27 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
                 ++tot_fb;
             }
         }
+        // A start that spans (n* below the bracket's lower end) retreats to three quarters of
+        // itself, up to three times, then to 0: the half-neighborhood pass needs the bitmap to hold
+        // exactly the sites below its end, so the bits of the sites given up are cleared (the
+        // occupancy summary only ever over-reports, which costs a wasted row read, no error)
         if (n_s > 0u) {
             if (smem_bm)
                 bitmap_update(bm, smp.perm, 0u, n_s);
             else
                 bitmap_add_sum(bm, sum, smp.perm, 0u, n_s, fd);
+        }
+        for (uint32_t tries = 0; n_s > 0u; ++tries) {
             for (uint32_t r = threadIdx.x; r < n_s; r += C) {
                 nd_st(PA, r + 2u, r + 2u);
                 if (gflags) __stcg(gflags + r + 2u, 0u);
+            }
+            if (threadIdx.x == 0) {  // a pass starts with clear borders, no early exit, an empty edge list
+                nd_st(PA, 0u, 0u);
+                nd_st(PA, 1u, 1u);
+                c.stop = 0u;
+                c.ecount[0] = 0u;
+                c.ecount[1] = 0u;
             }
             __syncthreads();
             if (smem_bm && L == kPlaneL)
@@ -2315,16 +2328,17 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
                 span = nd_ld(PA, 1u) != 1u;
             }
             lend_back(P, PA, n_s + 2u);  // (a barrier: every thread has read node 1)
-            if (span) {                  // n* < the bracket's lower end: sweep from the start
-                if (threadIdx.x == 0) ++tot_fb;
-                have_br = false;
-                n_s = 0u;
-                if (threadIdx.x == 0) {
-                    nd_st(P, 0u, 0u);
-                    nd_st(P, 1u, 1u);
-                }
-                __syncthreads();
+            if (!span) break;
+            if (threadIdx.x == 0) ++tot_fb;  // n* < n_s
+            have_br = false;
+            const uint32_t prev = n_s;
+            n_s = (tries < 3u && prev >= 4096u) ? static_cast<uint32_t>(uint64_t(prev) * 3u / 4u) : 0u;
+            bitmap_update(bm, smp.perm, prev, n_s);  // clears the bits of ranks n_s .. prev-1
+            if (n_s == 0u && threadIdx.x == 0) {  // the sweep from the start
+                nd_st(P, 0u, 0u);
+                nd_st(P, 1u, 1u);
             }
+            __syncthreads();
         }
         uint32_t chunks = 0, ns;
         if (threadIdx.x == 0) cyc_first += static_cast<unsigned long long>(clock64() - t_first);

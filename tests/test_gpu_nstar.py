@@ -141,3 +141,45 @@ def test_mass_matches_oracle(L):
     n[3:] = np.where(rng.random(len(w) - 3) < 0.5, np.minimum(ns[3:], N), n[3:])
     got = driver.mass(w, n)
     assert np.array_equal(got, orc_mass(w, n))
+
+
+@pytest.mark.parametrize("L", [12, 16, 20, 24])
+def test_start_retreats_after_a_spanning_first_pass(L):
+    # lower bracket ends 1.01, 1.5 and 4 times n*: the sweep's first pass spans, its start retreats
+    # by quarters (bits of the sites given up cleared) and finally to 0; n* stays exact on every
+    # bitmap path (rows, planes, summary in shared memory, summary in global memory)
+    import torch
+
+    from paper_2607_18991_b300 import driver, perc
+    w = wl(L, [1, 2, 3, 6], [1, 2])
+    want = orc_nstar(w)
+    p = driver.prepare(w)[0]
+    sub = want[p.idx].astype(np.int64)
+    N = L ** 5
+    perc.set_launch_option(perc.OPT_METHOD, perc.METHOD_SWEEP)
+    try:
+        for k in (1.01, 1.5, 4.0):
+            lo = np.minimum(N, np.ceil(sub * k).astype(np.int64) + 1)
+            br = torch.from_numpy(np.stack([lo, np.full_like(lo, N)], axis=1).astype(np.uint32).view(np.int32)).cuda()
+            stats = perc.new_stats()
+            ns, _ = perc.nstar(p.samples, p.max_L, bracket=br, stats=stats)
+            assert np.array_equal(perc.u32(ns), want[p.idx]), k
+            assert perc.stats_dict(stats)["fallbacks"] >= len(p.idx), k
+    finally:
+        perc.set_launch_option(perc.OPT_METHOD, perc.METHOD_AUTO)
+
+
+def test_any_axis_start_retreats():
+    import torch
+
+    import oracle
+    from gpu_util import orc_nstar_rule
+
+    from paper_2607_18991_b300 import driver, perc
+    w = wl(12, [1, 3, 9], [4, 5])
+    want = orc_nstar_rule(w, oracle.SPAN_ANY)
+    p = driver.prepare(w)[0]
+    lo = np.minimum(12 ** 5, 2 * want[p.idx].astype(np.int64) + 1)
+    br = torch.from_numpy(np.stack([lo, np.full_like(lo, 12 ** 5)], axis=1).astype(np.uint32).view(np.int32)).cuda()
+    ns, _ = perc.nstar_any(p.samples, p.max_L, bracket=br)
+    assert np.array_equal(perc.u32(ns), want[p.idx])
