@@ -75,9 +75,9 @@ def rank_launches(L: int, num_seeds: int, prefix: bool = False) -> int:
 def train_bracket(args, any_axis: bool = False, big: bool = False):
     """The bracket network, trained on plain n* of held-out seeds (1,000,001..) at the shapes of the
     first two workloads: zone 1 at L = 8 and all 127 neighborhoods at L = 16 (the any-axis n* of the
-    same rows for the any-axis workload).  With big (the mixed batch, L up to 40) also all 127
-    neighborhoods at L = 24 (8 seeds) and L = 32 (4 seeds), so that ln L is learned across the
-    batch's range instead of extrapolated from 8 and 16."""
+    same rows for the any-axis workload).  With big (workloads above L = 16: L = 24 and the mixed
+    batch, L up to 40) also all 127 neighborhoods at L = 24 (8 seeds) and L = 32 (4 seeds), so that
+    ln L is learned across their range instead of extrapolated from 8 and 16."""
     import torch
 
     from paper_2607_18991_b300 import bracket as pbracket
@@ -314,7 +314,7 @@ def run_ours(args):
 
     # ---- bracket network: trained on plain n* of held-out seeds at L = 8 (zone 1) and L = 16
     t_train = time.perf_counter()
-    params, losses = train_bracket(args, any_axis=any_axis)
+    params, losses = train_bracket(args, any_axis=any_axis, big=L > 16)
     t_train = time.perf_counter() - t_train
 
     # ---- resident inputs: one preallocated step (seeds, orders, sample table, brackets, outputs)
