@@ -30,6 +30,8 @@ constexpr uint32_t kPerThreads = 1024;
 constexpr uint32_t kTorusSmemMaxL = 16;  // up to L = 16 the bitmap (128 KiB) lives in shared memory
 constexpr uint32_t kPeriodicMaxL = PERC_PERIODIC_MAX_L;  // displacements stay below 2 L^5 < 2^31
 constexpr size_t kPeriodicBudget = size_t(16) << 30;  // bytes of per-CTA slots in one launch
+constexpr uint32_t kTorusRowCand = 625;  // (d1..d4) in {-2..2}^4
+constexpr uint32_t kTorusRowMinL = 5, kTorusRowMaxL = 32;  // sides the row scan serves
 constexpr uint32_t kWrapChunk = 512;  // sites one step of the wrap sweep adds (fastest of 256..2048 at L = 16)
 constexpr unsigned long long kTag = 1ull << 63;  // node word bit: a hook of the running probe
 
@@ -121,7 +123,11 @@ struct PerShared {
     uint32_t bad;    // a union-find loop ran out
     uint32_t best;   // largest cluster
     uint32_t logn;   // hooks in the running probe's log
+    uint32_t nrows;  // row entries (row scan)
     uint32_t offs[kMaxOffsets];  // per offset: shifts 6 (d_k + 2) at bits 5k, d_axis + 2 at bits 28..30
+    // per (d1..d4) with some d5 in the neighborhood: shifts 6 (d_k + 2) at bits 5k (k = 0..3), the
+    // neighborhood's d5 values at bits 20..24 (bit d5 + 2), d_axis + 2 at bits 25..27 (axis < 4)
+    uint32_t rows[kTorusRowCand];
 };
 
 // Bitmap bits and singleton nodes of the sites of rank r0 .. r1-1.
@@ -153,7 +159,8 @@ __device__ void torus_clear(uint32_t *bm, bool smem_bm, const uint32_t *perm, ui
 // and logged, and the pass stops once a winding path along the axis closes (sh.flag).  Ends with a
 // barrier.
 __device__ void torus_link(PerShared &sh, const uint32_t *bm, bool smem_bm, unsigned long long *nd, uint32_t *log,
-                           const uint32_t *perm, const uint32_t *rank, const FastDiv &fd, uint32_t a, uint32_t b)
+                           const uint32_t *perm, const uint32_t *rank, const FastDiv &fd, uint32_t a, uint32_t b,
+                           bool rows, bool axis4)
 {
     const uint32_t L = fd.L, m = b - a, z = sh.z;
     const bool wrap = log != nullptr;
@@ -184,6 +191,44 @@ __device__ void torus_link(PerShared &sh, const uint32_t *bm, bool smem_bm, unsi
             }
             wk[q] = w;
         }
+        // one neighbor j reached by a step along the axis: false ends this site's scan
+        auto edge = [&](uint32_t j, int32_t step) -> bool {
+            const uint32_t rj = j == i ? r : __ldg(rank + j);
+            if (rj > r || (!wrap && rj == r)) return true;  // the later site takes the edge; loops only wind
+            if (tunite(nd, log, &sh.logn, r, rj, step, b, bad) && wrap) {
+                *reinterpret_cast<volatile uint32_t *>(&sh.flag) = 1u;
+                return false;
+            }
+            return !bad;
+        };
+        if (rows) {
+            // row scan: per (d1..d4) entry the x5 row of the wrapped (x1..x4) (L bits at bit row * L,
+            // two words funnel-shifted), doubled so that the five bits (x5 - 2 .. x5 + 2) mod L are
+            // contiguous, masked by the entry's d5 values
+            const uint32_t x5s = x[4] + L - 2u >= L ? x[4] - 2u : x[4] + L - 2u;  // (x5 - 2) mod L
+            const unsigned long long lmask = (1ull << L) - 1ull;
+            for (uint32_t v = sub; v < sh.nrows && !stop; v += tps) {
+                const uint32_t e = sh.rows[v];
+                uint32_t row = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) row = row * L + ((wk[q] >> ((e >> (5 * q)) & 31u)) & 63u);
+                const uint32_t bb = row * L, wi = bb >> 5;
+                const uint32_t w0 = smem_bm ? bm[wi] : __ldcg(bm + wi), w1 = smem_bm ? bm[wi + 1u] : __ldcg(bm + wi + 1u);
+                const unsigned long long bits = ((static_cast<unsigned long long>(w1) << 32 | w0) >> (bb & 31u)) & lmask;
+                uint32_t win = static_cast<uint32_t>((bits | (bits << L)) >> x5s) & ((e >> 20) & 31u);
+                while (win) {
+                    const uint32_t t = __ffs(win) - 1u;
+                    win &= win - 1u;
+                    const uint32_t x5n = x5s + t >= L ? x5s + t - L : x5s + t;
+                    const int32_t step = axis4 ? static_cast<int32_t>(t) - 2 : static_cast<int32_t>((e >> 25) & 7u) - 2;
+                    if (!edge(bb + x5n, step)) {
+                        stop = true;
+                        break;
+                    }
+                }
+            }
+            continue;
+        }
         for (uint32_t v = sub; v < z; v += tps) {
             const uint32_t o = sh.offs[v];
             uint32_t j = 0;
@@ -191,15 +236,7 @@ __device__ void torus_link(PerShared &sh, const uint32_t *bm, bool smem_bm, unsi
             for (int q = 0; q < 5; ++q) j = j * L + ((wk[q] >> ((o >> (5 * q)) & 31u)) & 63u);
             const uint32_t word = smem_bm ? bm[j >> 5] : __ldcg(bm + (j >> 5));
             if (!((word >> (j & 31u)) & 1u)) continue;
-            const uint32_t rj = j == i ? r : __ldg(rank + j);
-            if (rj > r || (!wrap && rj == r)) continue;  // the later site takes the edge; loops only wind
-            const int32_t step = static_cast<int32_t>((o >> 28) & 7u) - 2;
-            if (tunite(nd, log, &sh.logn, r, rj, step, b, bad) && wrap) {
-                *reinterpret_cast<volatile uint32_t *>(&sh.flag) = 1u;
-                stop = true;
-                break;
-            }
-            if (bad) {
+            if (!edge(j, static_cast<int32_t>((o >> 28) & 7u) - 2)) {
                 stop = true;
                 break;
             }
@@ -254,6 +291,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_torus(const perc_sample *__r
             sh.sample = atomicAdd(&hdr->queue, 1u);
             sh.bad = 0u;
             sh.best = 0u;
+            sh.nrows = 0u;
         }
         __syncthreads();
         const uint32_t s = sh.sample;
@@ -295,6 +333,27 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_torus(const perc_sample *__r
             for (int q = 0; q < 5; ++q) o |= (6u * ((packed >> (3 * q)) & 7u)) << (5 * q);
             sh.offs[pos] = o;
         }
+        const bool rows = L >= kTorusRowMinL && L <= kTorusRowMaxL, axis4 = axis == 4u;
+        if (rows) {  // the row entries: per (d1..d4) the d5 whose |v|^2 is one of the sample's zones
+            for (uint32_t t = threadIdx.x; t < kTorusRowCand; t += blockDim.x) {
+                uint32_t e = 0, s2 = 0, code = t;
+#pragma unroll
+                for (int q = 3; q >= 0; --q) {
+                    const uint32_t f = code % 5u;  // d_q + 2
+                    code /= 5u;
+                    s2 += (f - 2u) * (f - 2u);
+                    e |= (6u * f) << (5 * q);
+                    if (static_cast<uint32_t>(q) == axis) e |= f << 25;
+                }
+                uint32_t d5m = 0;
+#pragma unroll
+                for (uint32_t f5 = 0; f5 < 5u; ++f5) {
+                    const uint32_t r2 = s2 + (f5 - 2u) * (f5 - 2u);
+                    if (r2 >= 1u && r2 <= 7u && ((mask >> (r2 - 1u)) & 1u)) d5m |= 1u << f5;
+                }
+                if (d5m) sh.rows[atomicAdd(&sh.nrows, 1u)] = e | (d5m << 20);
+            }
+        }
         if (threadIdx.x == 0) sh.z = z;
         __syncthreads();
         if (kWrap) {
@@ -314,7 +373,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_torus(const perc_sample *__r
                     sh.logn = 0u;
                 }
                 __syncthreads();
-                torus_link(sh, bm, smem_bm, nd, aux, smp.perm, smp.rank, fd, c, hi);
+                torus_link(sh, bm, smem_bm, nd, aux, smp.perm, smp.rank, fd, c, hi, rows, axis4);
                 if (sh.bad) break;
                 bool wrapped = sh.flag != 0u;
                 torus_settle(sh, nd, aux, wrapped);
@@ -331,7 +390,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_torus(const perc_sample *__r
                         sh.logn = 0u;
                     }
                     __syncthreads();
-                    torus_link(sh, bm, smem_bm, nd, aux, smp.perm, smp.rank, fd, c, mid);
+                    torus_link(sh, bm, smem_bm, nd, aux, smp.perm, smp.rank, fd, c, mid, rows, axis4);
                     if (sh.bad) break;
                     wrapped = sh.flag != 0u;
                     torus_settle(sh, nd, aux, wrapped);
@@ -354,7 +413,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_torus(const perc_sample *__r
             for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) __stcg(aux + r, 0u);
             torus_add(bm, nd, smp.perm, 0u, n);
             __syncthreads();
-            torus_link(sh, bm, smem_bm, nd, nullptr, smp.perm, smp.rank, fd, 0u, n);
+            torus_link(sh, bm, smem_bm, nd, nullptr, smp.perm, smp.rank, fd, 0u, n, rows, axis4);
             bool bad = sh.bad != 0u;
             for (uint32_t r = threadIdx.x; r < n && !bad; r += blockDim.x) {
                 int32_t d;
