@@ -1041,7 +1041,13 @@ def run_mixed_ours(args):
     with ClockSampler(smi_index) as clk:
         ms_learned = timed(True, args.steps, args.warmup)
         ms_plain = timed(False, args.steps, args.warmup)
-    shares = perc.u32(step.share[:, 0]) if step.prefix else None
+    ranked = None
+    if step.prefix:  # sites ranked per step: each order up to its own share
+        ranked = 0
+        for ch in step.chunks:
+            sh = perc.u32(ch["shares"])
+            for g in ch["groups"]:
+                ranked += sum(perc.prefix_sites(g["L"] ** 5, int(x)) for x in sh[g["share_at"]:g["share_at"] + g["S"]])
     clocks = clk.summary()
 
     # n* launches alone (eager, per chunk, with counters) for the roofline, and the results
@@ -1123,8 +1129,9 @@ def run_mixed_ours(args):
         cpu = cpu_baseline(rows, max(1, min(host_cores(), MIXED_CPU_ROWS)), _oracle_row,
                            f"the first {MIXED_CPU_ROWS} rows of the mixed batch, one ranking and one sweep each",
                            rows=True)
-    n_launch = (sum(rank_launches(g["L"], g["S"], step.prefix) - (1 if step.prefix else 0)
-                    for ch in step.chunks for g in ch["groups"]) + (3 if step.prefix else 2) * len(step.chunks))
+    # per side: the shares (prefix) and the ranking; per chunk: the bracket and n*
+    n_launch = (sum(rank_launches(g["L"], g["S"], step.prefix) for ch in step.chunks for g in ch["groups"])
+                + 2 * len(step.chunks))
     if rank == 0:
         line = {
             "metric": MIXED_METRIC, "value": world * num / (ms_learned * 1e-3), "unit": "samples/s", "n_gpus": world,
@@ -1140,10 +1147,9 @@ def run_mixed_ours(args):
             "plain": {"value": world * num / (ms_plain * 1e-3), "unit": "samples/s", "ms_per_step": ms_plain},
             "learned": {"ms_per_step": ms_learned, "nstar_ms": ms_nstar,
                         "passes_per_sample": float(out[True][1].astype(np.float64).mean()),
-                        "prefix": None if shares is None else {
-                            "share_per_chunk": [round(float(x) / 2 ** 24, 4) for x in shares],
-                            "ranked_sites": int(sum(perc.prefix_sites(g["L"] ** 5, int(x)) * g["S"]
-                                                    for ch, x in zip(step.chunks, shares) for g in ch["groups"])),
+                        "prefix": None if ranked is None else {
+                            "shares": "per order: the largest bracket share of the samples that read it",
+                            "ranked_sites": int(ranked),
                             "of_sites": int(sum(g["L"] ** 5 * g["S"] for ch in step.chunks for g in ch["groups"])),
                             "fallback_samples": fallbacks["samples"], "prefix_steps": fallbacks["steps"]}},
             "e2e": {"value": world * num / (e2e_ms * 1e-3), "unit": "samples/s", "ms_per_step": e2e_ms,

@@ -383,8 +383,19 @@ int perc_bracket(const float *params, const perc_sample *samples, uint32_t num_s
  *   nstar = PERC_NEVER and adds one to *unresolved; it needs its order in full (perc_rank) and
  *   perc_nstar.  Arguments, workspace (PERC_OP_NSTAR) and errors as for perc_nstar (the sweep
  *   method always), plus
- *     share       device uint32, as for perc_rank_prefix (the same value)
+ *     share       device uint32, as for perc_rank_prefix (the same value); or NULL when the orders
+ *                 were ranked per seed (perc_rank_prefix_seeds): each sample then reads up to the
+ *                 K of its own bracket's share (bracket required)
  *     unresolved  device uint32, incremented (the caller zeroes it)
+ *
+ * Per seed, for batches whose seeds serve different neighborhoods or sides (one seed per sample):
+ * perc_prefix_shares -- for one order block (side L, num_seeds orders of L^5 sites from perm, laid
+ *   out as for perc_rank), shares[s] = the largest share (as perc_prefix_share) over the samples
+ *   whose perm points at order s of the block; samples of other blocks or sides are skipped.
+ *   shares: device uint32[num_seeds] (output, zeroed first; 0 for an order no sample reads).
+ * perc_rank_prefix_seeds -- perc_rank_prefix with shares[s] for seed s (device uint32[num_seeds]).
+ *   Every sample's own K is at most its seed's, so perc_nstar_prefix with share NULL reads only
+ *   ranked sites.
  *
  * perc_nstar_any_prefix -- the same for perc_nstar_any (spanning along any axis; workspace
  *   PERC_OP_NSTAR_ANY); its unresolved samples need perc_nstar_any on full orders.
@@ -403,6 +414,10 @@ int perc_nstar_prefix(const perc_sample *samples, uint32_t num_samples, uint32_t
                       const uint32_t *bracket, const uint32_t *share, uint32_t *unresolved,
                       uint32_t *nstar, uint32_t *passes, perc_stats *stats, void *workspace,
                       size_t ws_bytes, void *stream);
+int perc_prefix_shares(const perc_sample *samples, uint32_t num_samples, const uint32_t *bracket,
+                       const uint32_t *perm, uint32_t L, uint32_t num_seeds, uint32_t *shares, void *stream);
+int perc_rank_prefix_seeds(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, const uint32_t *shares,
+                           uint32_t *perm, uint32_t *rank, void *workspace, size_t ws_bytes, void *stream);
 int perc_nstar_any_prefix(const perc_sample *samples, uint32_t num_samples, uint32_t max_L,
                           const uint32_t *bracket, const uint32_t *share, uint32_t *unresolved,
                           uint32_t *nstar, uint32_t *passes, perc_stats *stats, void *workspace,

@@ -2238,8 +2238,13 @@ k_nstar_sweep(const perc_sample *__restrict__ samples, uint32_t num, uint32_t ma
             continue;
         }
         const uint32_t N = static_cast<uint32_t>(num_sites(L));
-        // orders ranked only in part (perc_nstar_prefix): no site of rank >= lim is read
-        const uint32_t lim = share ? prefix_sites(N, *share) : N;
+        // orders ranked only in part (perc_nstar_prefix): no site of rank >= lim is read; the share
+        // is one word for the launch, or (share null, unresolved set) the sample's own bracket's
+        uint32_t lim = N;
+        if (share)
+            lim = prefix_sites(N, *share);
+        else if (unresolved && bracket)
+            lim = prefix_sites(N, bracket_share(L, bracket[2 * size_t(s)], bracket[2 * size_t(s) + 1]));
         const bool smem_bm = L <= smem_L;
         uint32_t *bm, *sum;
         sample_bm_sum(sm, sp, L, smem_L, sum_L, bm, sum);
@@ -2785,7 +2790,8 @@ static int nstar_prefix(bool any, const perc_sample *samples, uint32_t num_sampl
                         const uint32_t *bracket, const uint32_t *share, uint32_t *unresolved, uint32_t *nstar,
                         uint32_t *passes, perc_stats *stats, void *workspace, size_t ws_bytes, void *stream_)
 {
-    if (!samples || !share || !unresolved || !nstar || !workspace || num_samples == 0) return PERC_EINVAL;
+    if (!samples || (!share && !bracket) || !unresolved || !nstar || !workspace || num_samples == 0)
+        return PERC_EINVAL;
     LaunchCfg cfg;
     const int rc = launch_cfg(any ? kOpSweepAny : kOpSweep, max_L, num_samples, cfg);
     if (rc != PERC_OK) return rc;

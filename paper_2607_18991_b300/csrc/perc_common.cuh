@@ -179,6 +179,16 @@ __host__ __device__ inline uint32_t prefix_sites(uint64_t N, uint32_t share)
     return static_cast<uint32_t>(PERC_PREFIX_SITES(N, share));
 }
 
+// A sample's bracket (lo, hi) as a share of its lattice of side L: hi / L^5 in units of 2^-24,
+// rounded up; a bracket that perc_nstar would not use (lo < 1, lo > hi, hi > L^5) or an invalid side
+// counts as the whole lattice (2^24).
+__host__ __device__ inline uint32_t bracket_share(uint32_t L, uint32_t lo, uint32_t hi)
+{
+    const uint64_t N = (L >= 1u && L <= PERC_MAX_L) ? num_sites(L) : 0u;
+    if (N == 0u || lo < 1u || lo > hi || hi > N) return 1u << 24;
+    return static_cast<uint32_t>(((uint64_t(hi) << 24) + N - 1u) / N);
+}
+
 // Polls a bounded device-side wait makes before it gives up with PERC_ETIMEOUT: kSpinLimit, or
 // the value of PERC_OPT_SPIN_LIMIT (defined in perc_ccl.cu).  A wait that drains copies still in
 // flight after a timeout always uses kSpinLimit.

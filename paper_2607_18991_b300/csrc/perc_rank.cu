@@ -583,15 +583,31 @@ k_rank_bplace(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32
     }
 }
 
+// Per seed of one order block (side L, num_seeds rows of L^5 sites from perm_base), the largest
+// share of the samples whose order is a row of that block (shares zeroed by the caller).
+__global__ void __launch_bounds__(256) k_prefix_shares(const perc_sample *__restrict__ samples, uint32_t num,
+                                                       const uint32_t *__restrict__ bracket, const uint32_t *perm_base,
+                                                       uint32_t L, uint32_t num_seeds, uint32_t *__restrict__ shares)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= num) return;
+    const perc_sample smp = samples[k];
+    if (smp.L != L || smp.perm < perm_base) return;
+    const uint64_t N = num_sites(L), off = static_cast<uint64_t>(smp.perm - perm_base);  // in sites
+    if (off % N != 0u || off / N >= num_seeds) return;
+    atomicMax(shares + off / N, bracket_share(L, bracket[2 * size_t(k)], bracket[2 * size_t(k) + 1]));
+}
+
 // perc_rank_prefix: per seed the first bucket whose end reaches prefix_sites(N, *share) sites (the
 // starts are the exclusive scan of the bucket counts), one thread a seed.
 __global__ void __launch_bounds__(256) k_bucket_cut(uint32_t N, uint32_t B, uint32_t S,
                                                     const uint32_t *__restrict__ starts,
-                                                    const uint32_t *__restrict__ share, uint32_t *__restrict__ cut)
+                                                    const uint32_t *__restrict__ share, uint32_t per_seed,
+                                                    uint32_t *__restrict__ cut)
 {
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
-    const uint32_t nb = 1u << B, K = prefix_sites(N, *share);
+    const uint32_t nb = 1u << B, K = prefix_sites(N, per_seed ? share[s] : share[0]);
     const uint32_t *st = starts + size_t(s) * bucket_row(B);
     uint32_t lo = 0u, hi = nb - 1u;  // the last bucket ends at N >= K
     while (lo < hi) {
@@ -614,13 +630,8 @@ __global__ void __launch_bounds__(1024) k_prefix_share(const perc_sample *__rest
 {
     __shared__ uint32_t wmax[32];
     uint32_t m = 0u;
-    for (uint32_t k = threadIdx.x; k < num; k += blockDim.x) {
-        const uint32_t L = samples[k].L, lo = bracket[2 * size_t(k)], hi = bracket[2 * size_t(k) + 1];
-        const uint64_t N = (L >= 1u && L <= PERC_MAX_L) ? num_sites(L) : 0u;
-        uint32_t q = 1u << 24;
-        if (N && lo >= 1u && lo <= hi && hi <= N) q = static_cast<uint32_t>(((uint64_t(hi) << 24) + N - 1u) / N);
-        m = max(m, q);
-    }
+    for (uint32_t k = threadIdx.x; k < num; k += blockDim.x)
+        m = max(m, bracket_share(samples[k].L, bracket[2 * size_t(k)], bracket[2 * size_t(k) + 1]));
     m = __reduce_max_sync(0xffffffffu, m);
     if ((threadIdx.x & 31u) == 0u) wmax[threadIdx.x >> 5] = m;
     __syncthreads();
@@ -834,8 +845,8 @@ using namespace perc;
 
 // share (nullable): rank only the first buckets of each order, up to prefix_sites(N, *share) sites
 // (bucket path; the radix path ranks every site).
-static int rank_impl(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, const uint32_t *share, uint32_t *perm,
-                     uint32_t *rank, void *workspace, size_t ws_bytes, void *stream_)
+static int rank_impl(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, const uint32_t *share, bool per_seed,
+                     uint32_t *perm, uint32_t *rank, void *workspace, size_t ws_bytes, void *stream_)
 {
     if (L < 1 || L > PERC_MAX_L || num_seeds == 0 || !seeds || !perm || !rank || !workspace)
         return PERC_EINVAL;
@@ -891,7 +902,10 @@ static int rank_impl(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, cons
             if (cudaMemsetAsync(counts, 0, size_t(S) * row * 4, stream) != cudaSuccess) return PERC_ECUDA;
             k_rank_bcount<<<dim3(Tb, S), kRankThreads, smem_count, stream>>>(uint32_t(N), Bb, seeds + s0, counts);
             k_rank_scan<<<S, 1024, 0, stream>>>(row, counts, cursors);
-            if (cut) k_bucket_cut<<<(S + 255) / 256, 256, 0, stream>>>(uint32_t(N), Bb, S, counts, share, cut);
+            if (cut)
+                k_bucket_cut<<<(S + 255) / 256, 256, 0, stream>>>(uint32_t(N), Bb, S, counts,
+                                                                 per_seed ? share + s0 : share, per_seed ? 1u : 0u,
+                                                                 cut);
             k_rank_bplace<<<dim3(Tb, S), kRankThreads, smem_place, stream>>>(uint32_t(N), Bb, seeds + s0, cursors, recs,
                                                                              cut);
             if (big)
@@ -935,14 +949,33 @@ static int rank_impl(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, cons
 extern "C" int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, uint32_t *perm, uint32_t *rank,
                          void *workspace, size_t ws_bytes, void *stream)
 {
-    return rank_impl(L, seeds, num_seeds, nullptr, perm, rank, workspace, ws_bytes, stream);
+    return rank_impl(L, seeds, num_seeds, nullptr, false, perm, rank, workspace, ws_bytes, stream);
 }
 
 extern "C" int perc_rank_prefix(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, const uint32_t *share,
                                 uint32_t *perm, uint32_t *rank, void *workspace, size_t ws_bytes, void *stream)
 {
     if (!share) return PERC_EINVAL;
-    return rank_impl(L, seeds, num_seeds, share, perm, rank, workspace, ws_bytes, stream);
+    return rank_impl(L, seeds, num_seeds, share, false, perm, rank, workspace, ws_bytes, stream);
+}
+
+extern "C" int perc_rank_prefix_seeds(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, const uint32_t *shares,
+                                      uint32_t *perm, uint32_t *rank, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!shares) return PERC_EINVAL;
+    return rank_impl(L, seeds, num_seeds, shares, true, perm, rank, workspace, ws_bytes, stream);
+}
+
+extern "C" int perc_prefix_shares(const perc_sample *samples, uint32_t num_samples, const uint32_t *bracket,
+                                  const uint32_t *perm, uint32_t L, uint32_t num_seeds, uint32_t *shares, void *stream_)
+{
+    if (!samples || !bracket || !perm || !shares || num_samples == 0 || num_seeds == 0 || L < 1 || L > PERC_MAX_L)
+        return PERC_EINVAL;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (cudaMemsetAsync(shares, 0, size_t(num_seeds) * sizeof(uint32_t), stream) != cudaSuccess) return PERC_ECUDA;
+    k_prefix_shares<<<(num_samples + 255) / 256, 256, 0, stream>>>(samples, num_samples, bracket, perm, L, num_seeds,
+                                                                   shares);
+    return cudaGetLastError() == cudaSuccess ? PERC_OK : PERC_ECUDA;
 }
 
 extern "C" int perc_prefix_share(const perc_sample *samples, uint32_t num_samples, const uint32_t *bracket,

@@ -623,7 +623,13 @@ class BatchStep:
             ch["bracket"] = torch.empty((ch["n"], 2), dtype=torch.int32, device="cuda")
             ch["nstar"] = torch.empty(ch["n"], dtype=torch.int32, device="cuda")
             ch["passes"] = torch.empty(ch["n"], dtype=torch.int32, device="cuda")
-        # per chunk [share, unresolved] of the prefix steps
+            # prefix steps: each order's share (per group, a slice per seed)
+            ch["shares"] = torch.zeros(sum(g["S"] for g in ch["groups"]), dtype=torch.int32, device="cuda")
+            at = 0
+            for g in ch["groups"]:
+                g["share_at"] = at
+                at += g["S"]
+        # per chunk [unused, unresolved] of the prefix steps
         self.share = torch.zeros((len(self.chunks), 2), dtype=torch.int32, device="cuda")
         self.options = list(options) if options is not None else [None] * len(self.chunks)
         self.ws = None
@@ -674,24 +680,26 @@ class BatchStep:
             self._apply(None)
 
     def run_prefix(self, k: int, stats: torch.Tensor | None = None, stream=None):
-        """Chunk k's learned step on orders ranked only up to the bracket's share of the lattice
-        (perc_bracket, perc_prefix_share, perc_rank_prefix per side, perc_nstar_prefix)."""
+        """Chunk k's learned step on orders ranked only up to their samples' bracket shares:
+        perc_bracket, then per side perc_prefix_shares (each order the largest share of the samples
+        that read it) and perc_rank_prefix_seeds, then perc_nstar_prefix with every sample capped at
+        its own share."""
         ch, sp = self.chunks[k], perc._stream(stream)
-        share = self.share[k].data_ptr()
         perc._ok(self.lib.perc_bracket(self.params.data_ptr(), ch["samples"].data_ptr(), ch["n"], self.margin,
                                        ch["bracket"].data_ptr(), sp), "perc_bracket")
-        perc._ok(self.lib.perc_prefix_share(ch["samples"].data_ptr(), ch["n"], ch["bracket"].data_ptr(), share, sp),
-                 "perc_prefix_share")
         base = self.orders.data_ptr()
         for g in ch["groups"]:
-            perc._ok(self.lib.perc_rank_prefix(g["L"], g["seeds"].data_ptr(), g["S"], share, base + g["off"],
-                                               base + g["roff"], self.ws.data_ptr(), self.ws.numel(), sp),
-                     "perc_rank_prefix")
+            shares = ch["shares"].data_ptr() + 4 * g["share_at"]
+            perc._ok(self.lib.perc_prefix_shares(ch["samples"].data_ptr(), ch["n"], ch["bracket"].data_ptr(),
+                                                 base + g["off"], g["L"], g["S"], shares, sp), "perc_prefix_shares")
+            perc._ok(self.lib.perc_rank_prefix_seeds(g["L"], g["seeds"].data_ptr(), g["S"], shares, base + g["off"],
+                                                     base + g["roff"], self.ws.data_ptr(), self.ws.numel(), sp),
+                     "perc_rank_prefix_seeds")
         self.share[k, 1:].zero_()
         perc._ok(self.lib.perc_nstar_prefix(ch["samples"].data_ptr(), ch["n"], ch["max_L"], ch["bracket"].data_ptr(),
-                                            share, share + 4, ch["nstar"].data_ptr(), ch["passes"].data_ptr(),
-                                            perc._ptr(stats), self.ws.data_ptr(), self.ws.numel(), sp),
-                 "perc_nstar_prefix")
+                                            None, self.share[k].data_ptr() + 4, ch["nstar"].data_ptr(),
+                                            ch["passes"].data_ptr(), perc._ptr(stats), self.ws.data_ptr(),
+                                            self.ws.numel(), sp), "perc_nstar_prefix")
 
     def run(self, learned: bool = True, stats: torch.Tensor | None = None, stream=None):
         for k in range(len(self.chunks)):

@@ -73,6 +73,8 @@ def lib() -> ctypes.CDLL:
         "perc_rank_prefix": (i32, [u32, vp, u32, vp, vp, vp, vp, sz, vp]),
         "perc_nstar_prefix": (i32, [vp, u32, u32, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
         "perc_nstar_any_prefix": (i32, [vp, u32, u32, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+        "perc_prefix_shares": (i32, [vp, u32, vp, vp, u32, u32, vp, vp]),
+        "perc_rank_prefix_seeds": (i32, [u32, vp, u32, vp, vp, vp, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -89,7 +91,7 @@ def exported_symbols() -> list[str]:
             "perc_smax_window", "perc_binomial_weights", "perc_pmax", "perc_check",
             "perc_mlp_forward", "perc_mlp_grad", "perc_adam", "perc_mlp_train", "perc_bracket",
             "perc_status_string", "perc_set_launch_option", "perc_prefix_share", "perc_rank_prefix",
-            "perc_nstar_prefix", "perc_nstar_any_prefix"]
+            "perc_nstar_prefix", "perc_nstar_any_prefix", "perc_prefix_shares", "perc_rank_prefix_seeds"]
 
 
 def status_string(rc: int) -> str:

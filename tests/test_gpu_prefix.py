@@ -191,3 +191,52 @@ def test_pmax_step_ranks_only_the_windows():
     for s, seed in enumerate((1, 2)):
         want_perm, _ = orc_order(12, seed)
         assert np.array_equal(perc.u32(st.perm[s, :K]), want_perm[:K])
+
+
+def test_prefix_shares_per_order_of_a_block():
+    from paper_2607_18991_b300 import perc
+    L, S = 12, 4
+    N = L ** 5
+    perm = torch.zeros((S, N), dtype=torch.int32, device="cuda")
+    other = torch.zeros((1, 8 ** 5), dtype=torch.int32, device="cuda")
+    rows = [0, 0, 2, 3, 0]  # order 1 is read by no sample; the last sample is of another side
+    Ls = [L, L, L, L, 8]
+    ptrs = [perm.data_ptr() + 4 * N * r for r in rows[:4]] + [other.data_ptr()]
+    samples = perc.make_samples(np.array(Ls), np.array([1, 2, 3, 4, 5]), np.array(ptrs, dtype=np.uint64),
+                                np.array(ptrs, dtype=np.uint64))
+    br = np.array([[5, 1000], [7, 30000], [1, 777], [9, 8], [1, 32768]], dtype=np.int64)  # 4th malformed
+    bracket = torch.as_tensor(br.astype(np.int32), device="cuda")
+    shares = torch.full((S,), 123, dtype=torch.int32, device="cuda")
+    perc._ok(perc.lib().perc_prefix_shares(samples.data_ptr(), 5, bracket.data_ptr(), perm.data_ptr(), L, S,
+                                           shares.data_ptr(), perc._stream()), "perc_prefix_shares")
+    got = perc.u32(shares)
+
+    def q(hi):
+        return -(-(int(hi) << 24) // N)
+
+    assert list(got) == [max(q(1000), q(30000)), 0, q(777), 1 << 24]
+
+
+def test_rank_prefix_per_seed_shares():
+    from paper_2607_18991_b300 import perc
+    L = 12
+    seeds = (3, 4, 5, 6)
+    shares_v = [0, 1 << 19, 1 << 22, 1 << 24]
+    N = L ** 5
+    perm = torch.full((4, N), -7, dtype=torch.int32, device="cuda")
+    rk = torch.full((4, N), -7, dtype=torch.int32, device="cuda")
+    sd = torch.as_tensor(np.asarray(seeds, dtype=np.int64), device="cuda")
+    shares = torch.as_tensor(np.array(shares_v, dtype=np.int32), device="cuda")
+    ws = perc.new_workspace(perc.workspace_bytes(perc.OP_RANK, L, 4))
+    perc._ok(perc.lib().perc_rank_prefix_seeds(L, sd.data_ptr(), 4, shares.data_ptr(), perm.data_ptr(),
+                                               rk.data_ptr(), ws.data_ptr(), ws.numel(), perc._stream()),
+             "perc_rank_prefix_seeds")
+    torch.cuda.synchronize()
+    p, r = perc.u32(perm), perc.u32(rk)
+    for s, (seed, q) in enumerate(zip(seeds, shares_v)):
+        K = perc.prefix_sites(N, q)
+        want, _ = orc_order(L, seed)
+        assert np.array_equal(p[s, :K], want[:K])
+        assert np.array_equal(r[s, want[:K]], np.arange(K, dtype=np.uint32))
+        if q < 1 << 22:  # a small share leaves most of the order unwritten
+            assert (p[s, K:] == np.uint32(-7 & 0xFFFFFFFF)).sum() > N // 2
