@@ -61,6 +61,7 @@ typedef enum {
 #define PERC_OP_SMAX 4
 #define PERC_OP_PERIODIC 5 /* perc_mass_periodic and perc_nstar_wrap */
 #define PERC_OP_NSTAR_ANY 6 /* perc_nstar_any */
+#define PERC_OP_MINIMAX 7   /* perc_nstar_minimax */
 
 /* zone_mask word of a sample: bits 0..6 select coordination zones 1..7 (at least one); bits 8..10
  * hold the spanning axis a = 0..4 that perc_nstar tests (borders x_{a+1} = 0 and x_{a+1} = L-1;
@@ -204,6 +205,25 @@ int perc_mass_periodic(const perc_sample *samples, uint32_t num_samples, uint32_
                        int64_t *mass, void *workspace, size_t ws_bytes, void *stream);
 int perc_nstar_wrap(const perc_sample *samples, uint32_t num_samples, uint32_t max_L, uint32_t *nstar,
                     void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * perc_nstar_minimax -- n* by a second, independent formulation (a check, not a fast path): the
+ * first n at which the first n sites hold a cluster touching both borders of the sample's axis is
+ * the smallest, over paths of neighboring sites joining the two borders, of the path's largest
+ * rank + 1 (a min-max path value).  Found by relaxing one label per site -- rank + 1 on the
+ * x_{a+1} = 0 border, then label(i) = max(rank(i) + 1, min over neighbors of label(j)) -- until no
+ * label changes (at most L^5 + 2 sweeps of z neighbor reads a site; PERC_ETIMEOUT past them, which
+ * a correct relaxation never reaches), and reading the smallest label on the x_{a+1} = L-1 border.
+ * Needs every site's rank (perc_rank, not perc_rank_prefix); perm is not read.  Lattice sides up to
+ * PERC_MINIMAX_MAX_L; workspace perc_workspace_bytes(PERC_OP_MINIMAX, max_L, num_samples) (one
+ * label per site of the largest lattice, per CTA).
+ *   nstar  device uint32[num_samples] (output)
+ * Errors: PERC_EINVAL, PERC_EWORKSPACE, PERC_ECUDA; samples that fail the device check get
+ * PERC_NEVER and set PERC_EDEVICE.
+ */
+#define PERC_MINIMAX_MAX_L 24u
+int perc_nstar_minimax(const perc_sample *samples, uint32_t num_samples, uint32_t max_L, uint32_t *nstar,
+                       void *workspace, size_t ws_bytes, void *stream);
 
 /*
  * perc_mass -- largest-cluster size S_max(n) of each sample with its first n[k] sites occupied

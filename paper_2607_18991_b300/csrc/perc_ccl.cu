@@ -2668,6 +2668,7 @@ extern "C" size_t perc_workspace_bytes(int op, uint32_t max_L, uint32_t num)
         return rank_workspace_bytes(max_L, num);
     }
     if (op == PERC_OP_PERIODIC) return periodic_workspace_bytes(max_L, num);
+    if (op == PERC_OP_MINIMAX) return minimax_workspace_bytes(max_L, num);
     if (op == PERC_OP_NSTAR_ANY) {
         LaunchCfg any;
         return launch_cfg(kOpSweepAny, max_L, num, any) == PERC_OK ? cfg_ws_bytes(any) : 0;

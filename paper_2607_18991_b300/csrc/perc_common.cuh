@@ -219,5 +219,7 @@ int resident_ctas(AttrSlot slot, const void *fn, int threads, size_t smem, uint3
 size_t rank_workspace_bytes(uint32_t L, uint32_t num_seeds);
 // Workspace of the periodic-boundary calls (defined in perc_periodic.cu); 0 when not configurable.
 size_t periodic_workspace_bytes(uint32_t max_L, uint32_t num);
+// Workspace of perc_nstar_minimax (defined in perc_minimax.cu); 0 when not configurable.
+size_t minimax_workspace_bytes(uint32_t max_L, uint32_t num);
 
 }  // namespace perc

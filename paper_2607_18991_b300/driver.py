@@ -169,6 +169,21 @@ def nstar_any(workload, params: torch.Tensor | None = None, margin: float = 0.0,
     return run_nstar_any(iter_prepared(workload, budget), len(workload), params, margin)
 
 
+def nstar_minimax(workload, budget: int = DEFAULT_BUDGET):
+    """n* of every (L, zone word, seed) row by min-max path labels (perc_nstar_minimax: a second,
+    independent formulation, for small lattices); uint32 numpy."""
+    workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
+    ws = perc.default_workspace()
+    out = np.zeros(len(workload), dtype=np.uint32)
+    for p in iter_prepared(workload, budget, ws):
+        out[p.idx] = perc.u32(perc.nstar_minimax(p.samples, p.max_L, ws=ws))
+        rc = perc.check(ws)
+        if rc != 0:
+            raise perc.PercError(rc, "perc_nstar_minimax device status")
+        del p
+    return out
+
+
 def nstar_any_sweep(workload, params: torch.Tensor | None = None, margin: float = 0.0, bracket_rows=None,
                     stats=None, budget: int = DEFAULT_BUDGET):
     """Exact n* for spanning along any axis by one sweep per row (perc_nstar_any: every cluster

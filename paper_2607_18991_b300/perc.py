@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libperc.so")
 NEVER = 0xFFFFFFFF
 MAX_L = 73
-OP_RANK, OP_NSTAR, OP_MASS, OP_SMAX, OP_PERIODIC, OP_NSTAR_ANY = 1, 2, 3, 4, 5, 6
+OP_RANK, OP_NSTAR, OP_MASS, OP_SMAX, OP_PERIODIC, OP_NSTAR_ANY, OP_MINIMAX = 1, 2, 3, 4, 5, 6, 7
 PERIODIC_MAX_L = 40
 AXIS_SHIFT, NUM_AXES = 8, 5  # zone word: spanning axis in bits 8..10; axes x1..x5
 OPT_THREADS, OPT_SMEM_NODES, OPT_MAX_CTAS, OPT_GROUP, OPT_METHOD, OPT_SPIN_LIMIT = 1, 2, 3, 4, 5, 6
@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
         "perc_nstar_any_prefix": (i32, [vp, u32, u32, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
         "perc_prefix_shares": (i32, [vp, u32, vp, vp, u32, u32, vp, vp]),
         "perc_rank_prefix_seeds": (i32, [u32, vp, u32, vp, vp, vp, vp, sz, vp]),
+        "perc_nstar_minimax": (i32, [vp, u32, u32, vp, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -91,7 +92,8 @@ def exported_symbols() -> list[str]:
             "perc_smax_window", "perc_binomial_weights", "perc_pmax", "perc_check",
             "perc_mlp_forward", "perc_mlp_grad", "perc_adam", "perc_mlp_train", "perc_bracket",
             "perc_status_string", "perc_set_launch_option", "perc_prefix_share", "perc_rank_prefix",
-            "perc_nstar_prefix", "perc_nstar_any_prefix", "perc_prefix_shares", "perc_rank_prefix_seeds"]
+            "perc_nstar_prefix", "perc_nstar_any_prefix", "perc_prefix_shares", "perc_rank_prefix_seeds",
+            "perc_nstar_minimax"]
 
 
 def status_string(rc: int) -> str:
@@ -421,3 +423,14 @@ def prefix_sites(N: int, share: int) -> int:
     """PERC_PREFIX_SITES: sites of an order that perc_rank_prefix ranks at least for `share`."""
     base = (int(N) * min(int(share), 1 << 24)) >> 24
     return min(int(N), base * 9 // 8 + 64)
+
+
+def nstar_minimax(samples: torch.Tensor, max_L: int, ws: Workspace | None = None, stream=None) -> torch.Tensor:
+    """perc_nstar_minimax: n* as a min-max path value (int32 tensor [num], uint32 values)."""
+    num = samples.shape[0]
+    out = torch.empty(num, dtype=torch.int32, device=samples.device)
+    ws = ws or default_workspace()
+    buf = ws.get(workspace_bytes(OP_MINIMAX, max_L, num))
+    _ok(lib().perc_nstar_minimax(samples.data_ptr(), num, max_L, out.data_ptr(), buf.data_ptr(), buf.numel(),
+                                 _stream(stream)), "perc_nstar_minimax")
+    return out
