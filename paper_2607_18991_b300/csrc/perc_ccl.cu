@@ -578,14 +578,16 @@ __device__ __forceinline__ uint32_t entry_hits(const SiteGeo &g, const uint32_t 
 {
     h[0] = h[1] = h[2] = 0u;
     if (kPlanes) {
+        // branch-free: a plane outside the lattice reads words 0..3 and is masked out, so that the
+        // loads of successive entries need not wait on a divergent exit
         const PlaneEntry e = planes[k];
-        if ((e.oh & 0x7FFFu & ~g.allowed) != 0u) return 0u;
-        const uint32_t *w = bm + (g.wbase + static_cast<uint32_t>(e.dword));
+        const uint32_t ok = (e.oh & 0x7FFFu & ~g.allowed) == 0u ? 0xFFFFFFFFu : 0u;
+        const uint32_t *w = bm + ((g.wbase + static_cast<uint32_t>(e.dword)) & ok);
         // the fourth word only matters when the 69-bit block starts past bit 27
         const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = g.sh > 27u ? w[3] : 0u;
-        h[0] = __funnelshift_r(w0, w1, g.sh) & e.pm0 & g.sm0;
-        h[1] = __funnelshift_r(w1, w2, g.sh) & e.pm1 & g.sm1;
-        h[2] = __funnelshift_r(w2, w3, g.sh) & (e.oh >> 16) & g.sm2;
+        h[0] = __funnelshift_r(w0, w1, g.sh) & e.pm0 & g.sm0 & ok;
+        h[1] = __funnelshift_r(w1, w2, g.sh) & e.pm1 & g.sm1 & ok;
+        h[2] = __funnelshift_r(w2, w3, g.sh) & (e.oh >> 16) & g.sm2 & ok;
         return g.i + static_cast<uint32_t>(e.dword) * 32u - 34u;
     } else {
         const RowEntry e = rows[k];
