@@ -1004,7 +1004,8 @@ def run_mixed_ours(args):
     params, losses = train_bracket(args, big=True)
     wl = mixed_workload(rank)
     num = len(wl)
-    step = driver.BatchStep(wl, params=params, margin=args.margin, prefix=not args.no_prefix, by_cost=True)
+    step = driver.BatchStep(wl, params=params, margin=args.margin, prefix=not args.no_prefix, by_cost=True,
+                            streams=args.batch_streams)
     tuned = None if args.no_tune else autotune.tune_batch(step, learned=True)
     fallbacks = {"steps": 0, "samples": 0}
     for learned in (True, False):
@@ -1140,7 +1141,7 @@ def run_mixed_ours(args):
             "data": "synthetic (Philox-keyed site orders, seeds per rank)",
             "config": {"workload": "mixed batch of 4096 samples: L uniform in 10..40, zone masks uniform in 1..127, "
                                    "seed j+1 (numpy PCG64, seed 4096), one CUDA graph over all chunks",
-                       "samples_per_rank": num, "chunks": len(step.chunks), "chunking": "slowest samples first (driver.sample_cost)",
+                       "samples_per_rank": num, "chunks": len(step.chunks), "chunking": "slowest samples first (driver.sample_cost)", "streams": args.batch_streams,
                        "bracket": "learned",
                        "margin": args.margin, "l2": "flushed (256 MiB write) between timed steps; orders > L2",
                        "parallelism": f"dp{world} (seed blocks, no collective)"},
@@ -1276,6 +1277,8 @@ def main():
     ap.add_argument("--cpu-seeds-per-worker", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
+    ap.add_argument("--batch-streams", type=int, default=4,
+                    help="mixed batch: chunks alternate over this many streams (each its own order buffer)")
     ap.add_argument("--no-prefix", action="store_true",
                     help="learned arm: rank every site of each order instead of the brackets' share")
     ap.add_argument("--no-graph", dest="graph", action="store_false", help="do not time CUDA-graph replays")

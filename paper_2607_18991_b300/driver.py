@@ -609,11 +609,19 @@ class BatchStep:
     chunks, and ``capture`` records the whole batch as one CUDA graph.  ``options`` holds per-chunk
     launch options ({"method": METHOD_*, "group": CTAs per sample}), as picked by
     ``autotune.tune_batch``; they are set before each chunk's perc_nstar and restored after.
+
+    With ``streams`` = 2 the chunks alternate between two streams, each with its own order buffer
+    (half the budget each) and workspace, so that a chunk whose launch waits on a few slow samples
+    leaves its idle SMs to the next chunk instead of holding up the whole batch; the graph then
+    forks into the two streams and joins them at its end.  A chunk never runs beside one of its own
+    stream's, and the cooperative CTA groups (which need the whole GPU) are not used then.
     """
 
     def __init__(self, workload, params: torch.Tensor | None = None, margin: float = 0.0,
-                 budget: int | None = None, options=None, prefix: bool = False, by_cost: bool = False):
+                 budget: int | None = None, options=None, prefix: bool = False, by_cost: bool = False,
+                 streams: int = 1):
         self.workload = np.asarray(workload, dtype=np.int64).reshape(-1, 3)
+        self.nbuf = max(1, int(streams))
         # learned steps rank only the start of each order (perc_rank_prefix) when asked to
         self.prefix = bool(prefix) and params is not None
         self.num = len(self.workload)
@@ -622,7 +630,7 @@ class BatchStep:
         self.lib = perc.lib()
         self.chunks = []
         order_bytes = 0
-        for idx in _chunks(self.workload, budget, by_cost):
+        for idx in _chunks(self.workload, (budget or default_budget()) // self.nbuf, by_cost):
             groups, perm_rel, rank_rel, nbytes = chunk_layout(self.workload[idx])
             for g in groups:
                 g["seeds"] = torch.as_tensor(g["seeds"].astype(np.int64), device="cuda")
@@ -630,9 +638,12 @@ class BatchStep:
             self.chunks.append({"idx": idx, "max_L": int(sub[:, 0].max()), "n": len(idx), "groups": groups,
                                 "rel": (sub[:, 0], sub[:, 1], perm_rel, rank_rel)})
             order_bytes = max(order_bytes, nbytes)
-        self.orders = torch.empty(max(order_bytes, 16) // 4 + 4, dtype=torch.int32, device="cuda")
-        base = np.uint64(self.orders.data_ptr())
-        for ch in self.chunks:
+        self.orders = [torch.empty(max(order_bytes, 16) // 4 + 4, dtype=torch.int32, device="cuda")
+                       for _ in range(self.nbuf)]
+        self.streams = [torch.cuda.Stream() for _ in range(self.nbuf)] if self.nbuf > 1 else None
+        for k, ch in enumerate(self.chunks):
+            ch["buf"] = k % self.nbuf
+            base = np.uint64(self.orders[ch["buf"]].data_ptr())
             Ls, words, pp, rp = ch.pop("rel")
             ch["samples"] = perc.make_samples(Ls, words, pp + base, rp + base)
             ch["bracket"] = torch.empty((ch["n"], 2), dtype=torch.int32, device="cuda")
@@ -647,8 +658,12 @@ class BatchStep:
         # per chunk [unused, unresolved] of the prefix steps
         self.share = torch.zeros((len(self.chunks), 2), dtype=torch.int32, device="cuda")
         self.options = list(options) if options is not None else [None] * len(self.chunks)
-        self.ws = None
+        self.wss = [None] * self.nbuf
         self._size_workspace()
+
+    @property
+    def ws(self):
+        return self.wss[0]
 
     def _apply(self, opt):
         perc.set_launch_option(perc.OPT_METHOD, opt["method"] if opt else perc.METHOD_AUTO)
@@ -664,9 +679,14 @@ class BatchStep:
                 nb = max(nb, perc.workspace_bytes(perc.OP_NSTAR, ch["max_L"], ch["n"]))
             finally:
                 self._apply(None)
-        if self.ws is None or self.ws.numel() < nb:
-            self.ws = None
-            self.ws = perc.new_workspace(nb)
+        for b in range(self.nbuf):
+            if self.wss[b] is None or self.wss[b].numel() < nb:
+                self.wss[b] = None
+                self.wss[b] = perc.new_workspace(nb)
+
+    def _base_ws(self, k: int):
+        ch = self.chunks[k]
+        return self.orders[ch["buf"]].data_ptr(), self.wss[ch["buf"]]
 
     def set_options(self, options):
         self.options = list(options)
@@ -674,23 +694,26 @@ class BatchStep:
 
     def run_rank(self, k: int, stream=None):
         ch, sp = self.chunks[k], perc._stream(stream)
-        base = self.orders.data_ptr()
+        base, ws = self._base_ws(k)
         for g in ch["groups"]:
-            N = g["L"] ** 5
             perc._ok(self.lib.perc_rank(g["L"], g["seeds"].data_ptr(), g["S"], base + g["off"], base + g["roff"],
-                                        self.ws.data_ptr(), self.ws.numel(), sp), "perc_rank")
+                                        ws.data_ptr(), ws.numel(), sp), "perc_rank")
 
     def run_nstar(self, k: int, learned: bool, stats: torch.Tensor | None = None, stream=None):
         ch, sp = self.chunks[k], perc._stream(stream)
         if learned:
             perc._ok(self.lib.perc_bracket(self.params.data_ptr(), ch["samples"].data_ptr(), ch["n"], self.margin,
                                            ch["bracket"].data_ptr(), sp), "perc_bracket")
-        self._apply(self.options[k])
+        _, ws = self._base_ws(k)
+        opt = self.options[k]
+        if self.nbuf > 1:  # no cooperative groups beside another stream's launch
+            opt = {"method": opt["method"] if opt else perc.METHOD_SWEEP, "group": 1}
+        self._apply(opt)
         try:
             perc._ok(self.lib.perc_nstar(ch["samples"].data_ptr(), ch["n"], ch["max_L"],
                                          ch["bracket"].data_ptr() if learned else None, ch["nstar"].data_ptr(),
-                                         ch["passes"].data_ptr(), perc._ptr(stats), self.ws.data_ptr(),
-                                         self.ws.numel(), sp), "perc_nstar")
+                                         ch["passes"].data_ptr(), perc._ptr(stats), ws.data_ptr(),
+                                         ws.numel(), sp), "perc_nstar")
         finally:
             self._apply(None)
 
@@ -702,27 +725,40 @@ class BatchStep:
         ch, sp = self.chunks[k], perc._stream(stream)
         perc._ok(self.lib.perc_bracket(self.params.data_ptr(), ch["samples"].data_ptr(), ch["n"], self.margin,
                                        ch["bracket"].data_ptr(), sp), "perc_bracket")
-        base = self.orders.data_ptr()
+        base, ws = self._base_ws(k)
         for g in ch["groups"]:
             shares = ch["shares"].data_ptr() + 4 * g["share_at"]
             perc._ok(self.lib.perc_prefix_shares(ch["samples"].data_ptr(), ch["n"], ch["bracket"].data_ptr(),
                                                  base + g["off"], g["L"], g["S"], shares, sp), "perc_prefix_shares")
             perc._ok(self.lib.perc_rank_prefix_seeds(g["L"], g["seeds"].data_ptr(), g["S"], shares, base + g["off"],
-                                                     base + g["roff"], self.ws.data_ptr(), self.ws.numel(), sp),
+                                                     base + g["roff"], ws.data_ptr(), ws.numel(), sp),
                      "perc_rank_prefix_seeds")
         self.share[k, 1:].zero_()
         perc._ok(self.lib.perc_nstar_prefix(ch["samples"].data_ptr(), ch["n"], ch["max_L"], ch["bracket"].data_ptr(),
                                             None, self.share[k].data_ptr() + 4, ch["nstar"].data_ptr(),
-                                            ch["passes"].data_ptr(), perc._ptr(stats), self.ws.data_ptr(),
-                                            self.ws.numel(), sp), "perc_nstar_prefix")
+                                            ch["passes"].data_ptr(), perc._ptr(stats), ws.data_ptr(),
+                                            ws.numel(), sp), "perc_nstar_prefix")
 
     def run(self, learned: bool = True, stats: torch.Tensor | None = None, stream=None):
-        for k in range(len(self.chunks)):
-            if learned and self.prefix:
-                self.run_prefix(k, stats, stream)
-                continue
-            self.run_rank(k, stream)
-            self.run_nstar(k, learned, stats, stream)
+        main = stream if stream is not None else torch.cuda.current_stream()
+        if self.nbuf > 1:  # fork: every chunk stream starts after the work already on `main`
+            start = torch.cuda.Event()
+            start.record(main)
+            for s in self.streams:
+                s.wait_event(start)
+        for k, ch in enumerate(self.chunks):
+            s = self.streams[ch["buf"]] if self.nbuf > 1 else main
+            with torch.cuda.stream(s):  # (the torch ops of the step, e.g. zeroing a counter, too)
+                if learned and self.prefix:
+                    self.run_prefix(k, stats, s)
+                    continue
+                self.run_rank(k, s)
+                self.run_nstar(k, learned, stats, s)
+        if self.nbuf > 1:  # join
+            for s in self.streams:
+                done = torch.cuda.Event()
+                done.record(s)
+                main.wait_event(done)
 
     def finish(self) -> int:
         """After a prefix step (synchronises): the samples whose n* lies past their chunk's ranked
@@ -754,9 +790,10 @@ class BatchStep:
     def result(self):
         """(n*, passes) as numpy uint32 in workload order (synchronises; raises on a device error)."""
         self.finish()
-        rc = self.lib.perc_check(self.ws.data_ptr(), perc._stream())
-        if rc != 0:
-            raise perc.PercError(rc, "perc_nstar device status")
+        for ws in self.wss:
+            rc = self.lib.perc_check(ws.data_ptr(), perc._stream())
+            if rc != 0:
+                raise perc.PercError(rc, "perc_nstar device status")
         nstar = np.zeros(self.num, dtype=np.uint32)
         passes = np.zeros(self.num, dtype=np.uint32)
         for ch in self.chunks:
