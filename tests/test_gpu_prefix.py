@@ -240,3 +240,32 @@ def test_rank_prefix_per_seed_shares():
         assert np.array_equal(r[s, want[:K]], np.arange(K, dtype=np.uint32))
         if q < 1 << 22:  # a small share leaves most of the order unwritten
             assert (p[s, K:] == np.uint32(-7 & 0xFFFFFFFF)).sum() > N // 2
+
+
+@pytest.mark.parametrize("streams", [2, 3])
+def test_batch_over_several_streams_matches_oracle(streams):
+    # chunks alternate over streams with their own order buffers and workspaces; eager and graph,
+    # learned (prefix-ranked) and plain steps all give the oracle's n*
+    from paper_2607_18991_b300 import bracket as pbracket
+    from paper_2607_18991_b300 import driver
+    rng = np.random.default_rng(5)
+    wl = np.array([(int(L), int(m), 900 + j) for j, (L, m) in
+                   enumerate(zip(rng.integers(5, 21, 60), rng.integers(1, 128, 60)))])
+    train = np.array([(L, m, s) for L in (8, 16) for m in range(1, 128, 3) for s in (7001, 7002)])
+    ns_train, _ = driver.nstar(train)
+    params, _ = pbracket.train(train[:, 0], train[:, 1], ns_train, steps=600, lr=3e-3, seed=0)
+    want = orc_nstar(wl)
+    for prefix in (False, True):
+        step = driver.BatchStep(wl, params=params, margin=0.05, budget=128 << 20, prefix=prefix, by_cost=True,
+                                streams=streams)
+        assert len(step.chunks) > streams
+        for learned in (True, False):
+            step.run(learned)
+            got, _ = step.result()
+            assert np.array_equal(got, want), (prefix, learned)
+        g = step.capture(True)
+        for ch in step.chunks:
+            ch["nstar"].fill_(0)
+        g.replay()
+        got, _ = step.result()
+        assert np.array_equal(got, want), ("graph", prefix)
