@@ -212,8 +212,11 @@ int perc_nstar_wrap(const perc_sample *samples, uint32_t num_samples, uint32_t m
  * the smallest, over paths of neighboring sites joining the two borders, of the path's largest
  * rank + 1 (a min-max path value).  Found by relaxing one label per site -- rank + 1 on the
  * x_{a+1} = 0 border, then label(i) = max(rank(i) + 1, min over neighbors of label(j)) -- until no
- * label changes (at most L^5 + 2 sweeps of z neighbor reads a site; PERC_ETIMEOUT past them, which
- * a correct relaxation never reaches), and reading the smallest label on the x_{a+1} = L-1 border.
+ * label changes (at most L^5 + 2 sweeps; PERC_ETIMEOUT past them, which a correct relaxation
+ * never reaches), and reading the smallest label on the x_{a+1} = L-1 border.  A sweep visits the
+ * lattice in tiles of 4^5 sites: each tile's labels and a radius-2 halo are brought into shared
+ * memory by one TMA tensor copy and relaxed there.  A tile copy that does not land within the
+ * polls of PERC_OPT_SPIN_LIMIT ends the CTA's work with PERC_ETIMEOUT (outputs then undefined).
  * Needs every site's rank (perc_rank, not perc_rank_prefix); perm is not read.  Lattice sides up to
  * PERC_MINIMAX_MAX_L; workspace perc_workspace_bytes(PERC_OP_MINIMAX, max_L, num_samples) (one
  * label per site of the largest lattice, per CTA).
@@ -327,7 +330,7 @@ int perc_nstar_noalloc(const perc_sample *samples, uint32_t num_samples, uint32_
  *                        run cooperative groups), 1 = bisection, 2 = sweep
  *   PERC_OPT_SPIN_LIMIT  polls a bounded device-side wait makes before it gives up with
  *                        PERC_ETIMEOUT (the cooperative groups' barriers in perc_nstar, the tile
- *                        copies of perc_rank); 0 = the default, 2^26.  A small value makes those
+ *                        copies of perc_rank and of perc_nstar_minimax); 0 = the default, 2^26.  A small value makes those
  *                        waits run out on purpose, so that the timeout path can be tested: the
  *                        kernels then return early, the call's outputs are undefined, and
  *                        perc_check reports PERC_ETIMEOUT.  After a timeout in perc_rank each CTA

@@ -208,6 +208,7 @@ enum AttrSlot {
     kAttrTorusMass,
     kAttrTorusWrap,
     kAttrMicrobench,
+    kAttrMinimax,
     kAttrSlots
 };
 int ensure_smem_attr(AttrSlot slot, const void *fn, size_t bytes);

@@ -46,3 +46,29 @@ def test_minimax_rejects_large_sides_and_bad_samples():
     ws = perc.Workspace()
     got = perc.u32(perc.nstar_minimax(s, 4, ws=ws))
     assert got[1] == perc.NEVER and perc.check(ws) == -5  # PERC_EDEVICE
+
+
+def test_minimax_tiles_at_L16_match_union_find():
+    # several 4^5 tiles a side, each visit a TMA tensor copy of the tile and its halo
+    from paper_2607_18991_b300 import driver, perc
+    w = np.array([(16, m, s) for m in (1, 7, 42, 127) for s in (1, 2)] +
+                 [(12, int(perc.zone_word(3, 4)), 5), (10, int(perc.zone_word(64, 2)), 6)], dtype=np.int64)
+    assert np.array_equal(driver.nstar_minimax(w), driver.nstar(w)[0])
+
+
+def test_minimax_copy_wait_runs_out():
+    # a limit of one poll on the tile copy's barrier: the kernel reports PERC_ETIMEOUT, lets its
+    # copy land, and returns; the next call with the default limit is exact
+    from paper_2607_18991_b300 import driver, perc
+    w = np.array([(8, m, s) for m in (1, 127) for s in (1, 2)], dtype=np.int64)
+    p = driver.prepare(w)[0]
+    ws = perc.Workspace()
+    perc.set_launch_option(perc.OPT_SPIN_LIMIT, 1)
+    try:
+        perc.nstar_minimax(p.samples, p.max_L, ws=ws)
+        assert perc.check(ws) == -4  # PERC_ETIMEOUT
+    finally:
+        perc.set_launch_option(perc.OPT_SPIN_LIMIT, 0)
+    got = perc.u32(perc.nstar_minimax(p.samples, p.max_L, ws=ws))
+    assert perc.check(ws) == 0
+    assert np.array_equal(got, orc_nstar(w[p.idx]))
