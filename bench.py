@@ -973,6 +973,43 @@ def run_wrap_ours(args):
         dist.destroy_process_group()
 
 
+def run_minimax_case(args):
+    """The min-max labeling check path (perc_nstar_minimax) on 8 samples at L = 12 (masks 1 and 127,
+    seeds 1..4): CUDA-event time of one launch and its n* against the union-find sweep's; with
+    --ncu-case, one launch inside a profiler range after one untimed launch."""
+    import torch
+
+    from paper_2607_18991_b300 import build as pbuild
+    from paper_2607_18991_b300 import driver, perc
+
+    pbuild.build()
+    w = np.array([(12, m, s) for m in (1, 127) for s in range(1, 5)], dtype=np.int64)
+    p = driver.prepare(w)[0]
+    ws = perc.Workspace()
+    perc.nstar_minimax(p.samples, p.max_L, ws=ws)
+    torch.cuda.synchronize()
+    if args.ncu_case:
+        torch.cuda.profiler.start()
+    times = []
+    for _ in range(1 if args.ncu_case else max(1, args.steps)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = perc.nstar_minimax(p.samples, p.max_L, ws=ws)
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    if args.ncu_case:
+        torch.cuda.profiler.stop()
+    if perc.check(ws) != 0:
+        raise perc.PercError(perc.check(ws), "perc_nstar_minimax device status")
+    got = perc.u32(out)
+    want, _ = driver.nstar(w[p.idx])
+    if not np.array_equal(got, want):
+        raise SystemExit("min-max labeling n* differs from the union-find sweep's")
+    print(json.dumps({"workload": "minimax", "ncu_case": bool(args.ncu_case), "L": 12, "samples": len(w),
+                      "ms_per_launch": float(np.median(times)), "nstar": got.tolist()}))
+
+
 # ------------------------------------------------------------------------------------------------
 # our arm, the mixed batch (4096 samples, L uniform in 10..40, random neighborhoods)
 # ------------------------------------------------------------------------------------------------
@@ -1282,10 +1319,11 @@ def main():
     ap.add_argument("--no-prefix", action="store_true",
                     help="learned arm: rank every site of each order instead of the brackets' share")
     ap.add_argument("--no-graph", dest="graph", action="store_false", help="do not time CUDA-graph replays")
-    ap.add_argument("--workload", default="nstar", choices=["nstar", "L24", "mixed", "pmax", "any", "wrap"],
+    ap.add_argument("--workload", default="nstar", choices=["nstar", "L24", "mixed", "pmax", "any", "wrap", "minimax"],
                     help="nstar: the n* samples/s line (default); L24: the same at L = 24 (128 seeds); mixed: "
                          "4096 samples with L in 10..40 as one CUDA graph; pmax: the P_max(p) path; any: n* for "
-                         "spanning along any of the five axes; wrap: first wrapping n with periodic boundaries")
+                         "spanning along any of the five axes; wrap: first wrapping n with periodic boundaries; "
+                         "minimax: the min-max labeling check path on 8 samples at L = 12 (no bench line)")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the on-chip peaks (L2 and shared-memory bandwidth, atomics) and exit")
     ap.add_argument("--ncu-case", action="store_true",
@@ -1306,6 +1344,8 @@ def main():
         run_pmax_ours(args)
     elif args.workload == "wrap":
         run_wrap_ours(args)
+    elif args.workload == "minimax":
+        run_minimax_case(args)
     elif args.workload == "mixed":
         run_mixed_ours(args)
     else:

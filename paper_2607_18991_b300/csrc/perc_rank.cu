@@ -495,6 +495,13 @@ k_rank_scatter_tma(int pass, uint32_t N, uint32_t T, uint32_t S, const uint32_t 
 //   k_rank_bsort   per bucket: its records into shared memory, a counting sort on the next
 //                  kSubBits key bits (about one record per sub-bucket), an insertion sort by
 //                  (key, site) inside each sub-bucket, then perm and rank written.
+// Ranking only a prefix (perc_rank_prefix) places and sorts only the buckets up to the cut, the
+// first bucket whose end reaches the K sites asked for.  While counting, k_rank_bcount also lists
+// the sites of the buckets up to stage_last -- where about K + 8 sqrt(K) + 64 keys are expected to
+// end -- at the end of the seed's record row, so that k_rank_bplace draws the keys of those sites
+// only instead of every key of the order a second time.  The exact counts decide
+// the cut; a cut past the staged buckets, or staged records that would not fit in half a row, sends
+// k_rank_bplace back to drawing the keys (same result).
 // Records reach a bucket in no fixed order; the bucket sort orders them completely by (key, site),
 // so the result is the same order as the radix path's.  A bucket larger than kBCap (never seen:
 // about 512 sites are expected, and a Poisson count that exceeds 1536 has probability far below
@@ -522,30 +529,106 @@ __host__ __device__ inline uint32_t bucket_row(uint32_t B) { return (1u << B) < 
 
 __device__ __forceinline__ uint32_t bucket_of(uint32_t key, uint32_t B) { return B ? key >> (32u - B) : 0u; }
 
+// Staging of the prefix ranking: up to N / 2 site indices (32-bit) at the end of a seed's record
+// row (the placed records of a staged seed, at most as many, end before them).
+constexpr uint32_t kNoStage = 0xFFFFFFFFu;
+static_assert(kBTileItems == 32, "k_rank_bcount keeps round k's ballot in lane k");
+__host__ __device__ inline uint32_t stage_cap(uint32_t N) { return N / 2u; }
+
+// Last bucket staged for a prefix of K sites: the one where K + 8 sqrt(K) + 64 keys are expected to
+// end (a shorter count than K there has probability below 1e-15), or kNoStage when that many
+// records would not fit the staging half of the row.
+__device__ __forceinline__ uint32_t stage_last(uint32_t N, uint32_t B, uint32_t K)
+{
+    const uint64_t t = uint64_t(K) + 8u * static_cast<uint64_t>(sqrtf(static_cast<float>(K))) + 64u;
+    if (t > stage_cap(N)) return kNoStage;
+    const uint64_t b = (t << B) / N;
+    return static_cast<uint32_t>(b < (1u << B) - 1u ? b : (1u << B) - 1u);
+}
+
+__device__ __forceinline__ uint32_t *stage_row(uint2 *recs, uint32_t N, uint32_t s)
+{
+    return reinterpret_cast<uint32_t *>(recs + size_t(s) * N) + (2u * N - stage_cap(N));
+}
+
+// Bucket counts of every key; with share (perc_rank_prefix) also the list of the sites whose keys
+// fall in the buckets up to stage_last, at stage_row(recs, N, s), their number in stage_n[s].
 __global__ void __launch_bounds__(kRankThreads)
-k_rank_bcount(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32_t *__restrict__ counts)
+k_rank_bcount(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32_t *__restrict__ counts,
+              const uint32_t *__restrict__ share, uint32_t per_seed, uint2 *__restrict__ recs,
+              uint32_t *__restrict__ stage_n)
 {
     extern __shared__ uint32_t bh[];  // [2^B]
+    __shared__ uint32_t wbase[kRankWarps];
+    __shared__ uint32_t tile_base, tile_tot;
     const uint32_t s = blockIdx.y, nb = 1u << B;
+    const uint32_t last = share ? stage_last(N, B, prefix_sites(N, per_seed ? share[s] : share[0])) : kNoStage;
+    const bool stage = last != kNoStage;  // the same for the whole block
     for (uint32_t b = threadIdx.x; b < nb; b += kRankThreads) bh[b] = 0u;
     __syncthreads();
     const uint64_t seed = seeds[s];
     const uint32_t e0 = blockIdx.x * kBTile;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t mine = 0u;  // lane k: which lanes of the warp stage their key of round k
 #pragma unroll 4
     for (uint32_t k = 0; k < kBTileItems; ++k) {
         const uint32_t e = e0 + k * kRankThreads + threadIdx.x;
-        if (e < N) atomicAdd(&bh[bucket_of(site_key(seed, e), B)], 1u);
+        bool keep = false;
+        if (e < N) {
+            const uint32_t b = bucket_of(site_key(seed, e), B);
+            atomicAdd(&bh[b], 1u);
+            keep = b <= last;
+        }
+        if (stage) {
+            const uint32_t m = __ballot_sync(0xffffffffu, keep);
+            if (lane == k) mine = m;
+        }
     }
     __syncthreads();
     uint32_t *row = counts + size_t(s) * bucket_row(B);
     for (uint32_t b = threadIdx.x; b < nb; b += kRankThreads)
         if (bh[b]) atomicAdd(row + b, bh[b]);
+    if (!stage) return;
+    // the tile's staged sites: warp-major, then round, then lane; one reservation a tile
+    const uint32_t c = __popc(mine);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= static_cast<uint32_t>(o)) incl += y;
+    }
+    if (lane == 31u) wbase[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kRankWarps; ++w) {
+            const uint32_t v = wbase[w];
+            wbase[w] = t;
+            t += v;
+        }
+        tile_tot = t;
+        tile_base = t ? atomicAdd(stage_n + s, t) : 0u;
+    }
+    __syncthreads();
+    const uint32_t cap = stage_cap(N);
+    if (tile_tot == 0u || tile_base + tile_tot > cap) return;  // nothing, or past the staging area
+    uint32_t *stg = stage_row(recs, N, s);
+    const uint32_t wb = tile_base + wbase[warp], excl = incl - c;
+#pragma unroll 4
+    for (uint32_t k = 0; k < kBTileItems; ++k) {
+        const uint32_t m = __shfl_sync(0xffffffffu, mine, k), off = __shfl_sync(0xffffffffu, excl, k);
+        if ((m >> lane) & 1u) stg[wb + off + __popc(m & ((1u << lane) - 1u))] = e0 + k * kRankThreads + threadIdx.x;
+    }
 }
 
 // cut (nullable): per seed the last bucket to place (perc_rank_prefix); later buckets are skipped.
+// stage_n (nullable, with cut and share): a seed whose cut lies within its staged buckets, and
+// whose staged sites all fit, draws the keys of its staged sites only; any other draws every key.
+// Tiles are taken in steps of gridDim.x.
 __global__ void __launch_bounds__(kRankThreads)
 k_rank_bplace(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32_t *__restrict__ cursors,
-              uint2 *__restrict__ recs, const uint32_t *__restrict__ cut)
+              uint2 *__restrict__ recs, const uint32_t *__restrict__ cut, const uint32_t *__restrict__ share,
+              uint32_t per_seed, const uint32_t *__restrict__ stage_n)
 {
     // shared: [2^B] bucket counts of the tile, then the tile's first place in each bucket; the tile's
     // keys; each key's offset among the tile's keys of its bucket (one shared atomic a key)
@@ -554,32 +637,67 @@ k_rank_bplace(uint32_t N, uint32_t B, const uint64_t *__restrict__ seeds, uint32
     uint16_t *loc = reinterpret_cast<uint16_t *>(keys + kBTile);
     const uint32_t s = blockIdx.y, nb = 1u << B;
     const uint32_t last = cut ? cut[s] : nb - 1u;
-    for (uint32_t b = threadIdx.x; b < nb; b += kRankThreads) bh[b] = 0u;
-    __syncthreads();
-    const uint64_t seed = seeds[s];
-    const uint32_t e0 = blockIdx.x * kBTile;
-#pragma unroll 4
-    for (uint32_t k = 0; k < kBTileItems; ++k) {
-        const uint32_t j = k * kRankThreads + threadIdx.x, e = e0 + j;
-        if (e < N) {
-            const uint32_t key = site_key(seed, e), b = bucket_of(key, B);
-            keys[j] = key;
-            if (b <= last) loc[j] = static_cast<uint16_t>(atomicAdd(&bh[b], 1u));
-        }
+    bool staged = false;
+    uint32_t M = 0u;
+    if (stage_n && cut && share) {
+        const uint32_t sl = stage_last(N, B, prefix_sites(N, per_seed ? share[s] : share[0]));
+        M = stage_n[s];
+        staged = sl != kNoStage && last <= sl && M <= stage_cap(N);
     }
-    __syncthreads();
-    uint32_t *cur = cursors + size_t(s) * bucket_row(B);
-    for (uint32_t b = threadIdx.x; b < nb; b += kRankThreads)
-        if (bh[b]) bh[b] = atomicAdd(cur + b, bh[b]);  // this tile's first place in bucket b
-    __syncthreads();
+    const uint32_t tiles = ((staged ? M : N) + kBTile - 1u) / kBTile;
+    const uint32_t *stg = stage_row(recs, N, s);
     uint2 *row = recs + size_t(s) * N;
+    const uint64_t seed = seeds[s];
+    uint32_t *cur = cursors + size_t(s) * bucket_row(B);
+    for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        for (uint32_t b = threadIdx.x; b < nb; b += kRankThreads) bh[b] = 0u;
+        __syncthreads();
+        const uint32_t e0 = tile * kBTile;
+        if (staged) {
 #pragma unroll 4
-    for (uint32_t k = 0; k < kBTileItems; ++k) {
-        const uint32_t j = k * kRankThreads + threadIdx.x, e = e0 + j;
-        if (e < N) {
-            const uint32_t key = keys[j], b = bucket_of(key, B);
-            if (b <= last) row[bh[b] + loc[j]] = make_uint2(key, e);
+            for (uint32_t k = 0; k < kBTileItems; ++k) {
+                const uint32_t j = k * kRankThreads + threadIdx.x, e = e0 + j;
+                if (e < M) {
+                    const uint32_t key = site_key(seed, __ldg(stg + e)), b = bucket_of(key, B);
+                    keys[j] = key;
+                    if (b <= last) loc[j] = static_cast<uint16_t>(atomicAdd(&bh[b], 1u));
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (uint32_t k = 0; k < kBTileItems; ++k) {
+                const uint32_t j = k * kRankThreads + threadIdx.x, e = e0 + j;
+                if (e < N) {
+                    const uint32_t key = site_key(seed, e), b = bucket_of(key, B);
+                    keys[j] = key;
+                    if (b <= last) loc[j] = static_cast<uint16_t>(atomicAdd(&bh[b], 1u));
+                }
+            }
         }
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < nb; b += kRankThreads)
+            if (bh[b]) bh[b] = atomicAdd(cur + b, bh[b]);  // this tile's first place in bucket b
+        __syncthreads();
+        if (staged) {
+#pragma unroll 4
+            for (uint32_t k = 0; k < kBTileItems; ++k) {
+                const uint32_t j = k * kRankThreads + threadIdx.x, e = e0 + j;
+                if (e < M) {
+                    const uint32_t key = keys[j], b = bucket_of(key, B);
+                    if (b <= last) row[bh[b] + loc[j]] = make_uint2(key, __ldg(stg + e));
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (uint32_t k = 0; k < kBTileItems; ++k) {
+                const uint32_t j = k * kRankThreads + threadIdx.x, e = e0 + j;
+                if (e < N) {
+                    const uint32_t key = keys[j], b = bucket_of(key, B);
+                    if (b <= last) row[bh[b] + loc[j]] = make_uint2(key, e);
+                }
+            }
+        }
+        __syncthreads();  // bh is reset for the next tile
     }
 }
 
@@ -893,21 +1011,33 @@ static int rank_impl(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, cons
                         PERC_OK))
             return PERC_ECUDA;
         uint2 *recs = reinterpret_cast<uint2 *>(a_keys);  // a_keys then a_vals: chunk * N * 8 bytes
-        // counts, cursors and (prefix) the per-seed last bucket: within the radix histogram area
-        if (size_t(2) * chunk * row + chunk > size_t(256) * T * chunk) return PERC_EINVAL;
+        // counts, staged record counts (prefix; padded to 16 bytes), cursors and (prefix) the per-seed
+        // last bucket: within the radix histogram area
+        const size_t pad = (size_t(chunk) + 3u) & ~size_t(3);
+        if (size_t(2) * chunk * row + pad + chunk > size_t(256) * T * chunk) return PERC_EINVAL;
+        // prefix: records staged while counting (PERC_RANK_STAGE=0 turns it off), and a grid of about
+        // eight CTAs an SM over the chunk's seeds that takes the staged tiles in steps
+        const bool stage = share && env_int_rank("PERC_RANK_STAGE", 1) != 0;
+        int dev = 0, sms = 0;
+        if (share && (cudaGetDevice(&dev) != cudaSuccess ||
+                      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess))
+            return PERC_ECUDA;
         for (uint32_t s0 = 0; s0 < num_seeds; s0 += chunk) {
             const uint32_t S = min(chunk, num_seeds - s0);
-            uint32_t *counts = hist, *cursors = hist + size_t(S) * row;
+            const size_t padS = (size_t(S) + 3u) & ~size_t(3);
+            uint32_t *counts = hist, *stage_n = hist + size_t(S) * row, *cursors = stage_n + padS;
             uint32_t *cut = share ? cursors + size_t(S) * row : nullptr;
-            if (cudaMemsetAsync(counts, 0, size_t(S) * row * 4, stream) != cudaSuccess) return PERC_ECUDA;
-            k_rank_bcount<<<dim3(Tb, S), kRankThreads, smem_count, stream>>>(uint32_t(N), Bb, seeds + s0, counts);
+            const uint32_t *sh = share ? (per_seed ? share + s0 : share) : nullptr;
+            if (cudaMemsetAsync(counts, 0, (size_t(S) * row + padS) * 4, stream) != cudaSuccess) return PERC_ECUDA;
+            k_rank_bcount<<<dim3(Tb, S), kRankThreads, smem_count, stream>>>(
+                uint32_t(N), Bb, seeds + s0, counts, stage ? sh : nullptr, per_seed ? 1u : 0u, recs, stage_n);
             k_rank_scan<<<S, 1024, 0, stream>>>(row, counts, cursors);
             if (cut)
-                k_bucket_cut<<<(S + 255) / 256, 256, 0, stream>>>(uint32_t(N), Bb, S, counts,
-                                                                 per_seed ? share + s0 : share, per_seed ? 1u : 0u,
+                k_bucket_cut<<<(S + 255) / 256, 256, 0, stream>>>(uint32_t(N), Bb, S, counts, sh, per_seed ? 1u : 0u,
                                                                  cut);
-            k_rank_bplace<<<dim3(Tb, S), kRankThreads, smem_place, stream>>>(uint32_t(N), Bb, seeds + s0, cursors, recs,
-                                                                             cut);
+            const uint32_t gx = share ? min(Tb, max(1u, (8u * uint32_t(sms) + S - 1u) / S)) : Tb;
+            k_rank_bplace<<<dim3(gx, S), kRankThreads, smem_place, stream>>>(
+                uint32_t(N), Bb, seeds + s0, cursors, recs, cut, sh, per_seed ? 1u : 0u, stage ? stage_n : nullptr);
             if (big)
                 k_rank_bsort_big<<<dim3(nb, S), kBSortBigThreads, smem_big, stream>>>(
                     uint32_t(N), Bb, sub_bits, cap, counts, recs, perm + size_t(s0) * N, rank + size_t(s0) * N, cut);

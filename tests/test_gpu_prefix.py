@@ -242,6 +242,57 @@ def test_rank_prefix_per_seed_shares():
             assert (p[s, K:] == np.uint32(-7 & 0xFFFFFFFF)).sum() > N // 2
 
 
+def _rank_prefix_seeds(L, seeds, shares_v):
+    from paper_2607_18991_b300 import perc
+    N, S = L ** 5, len(seeds)
+    perm = torch.full((S, N), -7, dtype=torch.int32, device="cuda")
+    rk = torch.full((S, N), -7, dtype=torch.int32, device="cuda")
+    sd = torch.as_tensor(np.asarray(seeds, dtype=np.int64), device="cuda")
+    shares = torch.as_tensor(np.array(shares_v, dtype=np.int64).astype(np.int32), device="cuda")
+    ws = perc.new_workspace(perc.workspace_bytes(perc.OP_RANK, L, S))
+    perc._ok(perc.lib().perc_rank_prefix_seeds(L, sd.data_ptr(), S, shares.data_ptr(), perm.data_ptr(),
+                                               rk.data_ptr(), ws.data_ptr(), ws.numel(), perc._stream()),
+             "perc_rank_prefix_seeds")
+    torch.cuda.synchronize()
+    return perc.u32(perm), perc.u32(rk)
+
+
+def test_rank_prefix_staged_and_drawn_again_agree(monkeypatch):
+    # small shares place the records staged while counting; a share whose records would not fit half
+    # an order (from about 44 % of the lattice) draws the keys again, as does PERC_RANK_STAGE=0
+    L = 12
+    N = L ** 5
+    seeds = (11, 12, 13, 14, 15, 16, 2 ** 33 + 1)
+    shares_v = [0, 1 << 19, 6 << 20, 7 << 20, 8 << 20, 1 << 24, 3 << 20]
+    from paper_2607_18991_b300 import perc
+    got = {}
+    for stage in ("1", "0"):
+        monkeypatch.setenv("PERC_RANK_STAGE", stage)
+        got[stage] = _rank_prefix_seeds(L, seeds, shares_v)
+    for s, (seed, q) in enumerate(zip(seeds, shares_v)):
+        K = perc.prefix_sites(N, q)
+        want, _ = orc_order(L, seed)
+        for stage in ("1", "0"):
+            p, r = got[stage]
+            assert np.array_equal(p[s, :K], want[:K]), (stage, q)
+            assert np.array_equal(r[s, want[:K]], np.arange(K, dtype=np.uint32)), (stage, q)
+    # both write the same prefix, through the same last bucket
+    assert np.array_equal(got["1"][0], got["0"][0])
+    assert np.array_equal(got["1"][1], got["0"][1])
+
+
+def test_rank_prefix_staged_at_L40_equals_full_ranking():
+    from paper_2607_18991_b300 import perc
+    L, seed, share = 40, 7, 1 << 18  # K = 1.8 % of 102,400,000 sites
+    p, r = _rank_prefix_seeds(L, [seed], [share])
+    fp, fr = perc.rank(L, [seed])
+    fp, fr = perc.u32(fp)[0], perc.u32(fr)[0]
+    K = perc.prefix_sites(L ** 5, share)
+    assert np.array_equal(p[0, :K], fp[:K])
+    assert np.array_equal(r[0, fp[:K]], np.arange(K, dtype=np.uint32))
+    assert (p[0, K:] == np.uint32(-7 & 0xFFFFFFFF)).sum() > L ** 5 // 2
+
+
 @pytest.mark.parametrize("streams", [2, 3])
 def test_batch_over_several_streams_matches_oracle(streams):
     # chunks alternate over streams with their own order buffers and workspaces; eager and graph,
