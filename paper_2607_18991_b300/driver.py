@@ -41,6 +41,15 @@ def sample_cost(workload: np.ndarray) -> np.ndarray:
     return workload[:, 0].astype(np.float64) ** 5 * pc * (363.0 + z)
 
 
+def tail_by_cost(workload: np.ndarray, per_seed: int, tail_seeds: int) -> np.ndarray:
+    """Queue order of seed-major rows (per_seed rows a seed): unchanged, except the rows of the last
+    tail_seeds seeds, which follow in falling sample_cost order (ties in their order)."""
+    n = len(workload)
+    t = max(0, min(n, int(tail_seeds) * int(per_seed)))
+    tail = np.arange(n - t, n)
+    return np.concatenate([np.arange(n - t), tail[np.argsort(-sample_cost(workload[tail]), kind="stable")]])
+
+
 def _chunks(workload: np.ndarray, budget: int | None, by_cost: bool = False):
     """Split sample indices so that the distinct (L, seed) orders of a chunk fit in `budget`.  By
     default the largest L come first, then seed-major: the CTAs running at the same time share one
@@ -439,7 +448,10 @@ class NstarStep:
     """Rank the seeds, propose brackets and find n* for all (mask, seed) pairs at one L.
 
     Every device buffer is allocated here, so ``run`` only enqueues library calls on the stream and
-    can be captured in a CUDA graph (``capture``).  Samples are seed-major.  With ``axes`` > 1 every
+    can be captured in a CUDA graph (``capture``).  Samples are seed-major, except that the samples of
+    the last ``tail_seeds`` seeds (default: an eighth of them) are queued by falling sample_cost, so
+    that the launch ends on its cheapest samples instead of waiting on a slow one dequeued last;
+    ``workload`` lists the samples in queue order.  With ``axes`` > 1 every
     (mask, seed) pair becomes that many consecutive samples spanning along x1, x2, ... and the n*
     phase ends with perc_nstar_min_axes: ``nstar_any`` holds n* for spanning along any of them.
     With ``any_axis`` the n* phase is perc_nstar_any instead: one sweep per pair whose clusters
@@ -447,7 +459,7 @@ class NstarStep:
     """
 
     def __init__(self, L: int, masks, seeds, params: torch.Tensor | None = None, margin: float = 0.0,
-                 axes: int = 1, any_axis: bool = False, prefix: bool = False):
+                 axes: int = 1, any_axis: bool = False, prefix: bool = False, tail_seeds: int | None = None):
         self.L = int(L)
         self.axes = int(axes)
         self.any_axis = bool(any_axis)
@@ -458,15 +470,19 @@ class NstarStep:
         self.margin = float(margin)
         N = self.L ** 5
         S = len(self.seeds)
-        self.workload = np.array([(self.L, m, s) for s in self.seeds for m in self.masks], dtype=np.int64)
+        wl = np.array([(self.L, m, s) for s in self.seeds for m in self.masks], dtype=np.int64).reshape(-1, 3)
+        seed_row = np.repeat(np.arange(S), len(self.masks))
+        order = tail_by_cost(wl, len(self.masks), S // 8 if tail_seeds is None else int(tail_seeds))
+        wl, seed_row = wl[order], seed_row[order]
+        self.workload = wl
         self.num = len(self.workload)
         self.seeds_dev = torch.as_tensor(self.seeds, device="cuda")
         self.perm = torch.empty((S, N), dtype=torch.int32, device="cuda")
         self.rank = torch.empty((S, N), dtype=torch.int32, device="cuda")
         A = self.axes
         self.launch_num = self.num * A  # samples of the perc_nstar launch
-        rows = np.repeat(np.arange(S), len(self.masks) * A)
-        words = perc.zone_word(np.repeat(np.tile(self.masks, S), A), np.tile(np.arange(A), self.num))
+        rows = np.repeat(seed_row, A)
+        words = perc.zone_word(np.repeat(wl[:, 1], A), np.tile(np.arange(A), self.num))
         self.samples = perc.samples_for(self.L, words, rows, self.perm, self.rank)
         self.bracket = torch.empty((self.launch_num, 2), dtype=torch.int32, device="cuda")
         self.nstar = torch.empty(self.launch_num, dtype=torch.int32, device="cuda")

@@ -81,3 +81,19 @@ def test_batch_layout_aligned_and_disjoint():
             assert np.array_equal(rank_rel[sel], g["roff"] + 4 * N * rows)
         spans.sort()
         assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:])) and spans[-1][1] <= nbytes
+
+
+def test_tail_by_cost_orders_only_the_last_seeds():
+    from paper_2607_18991_b300 import driver
+    masks, seeds = np.arange(1, 128), np.arange(1, 17)
+    wl = np.array([(16, m, s) for s in seeds for m in masks])
+    order = driver.tail_by_cost(wl, len(masks), 2)
+    assert np.array_equal(np.sort(order), np.arange(len(wl)))  # a permutation
+    head = len(wl) - 2 * len(masks)
+    assert np.array_equal(order[:head], np.arange(head))  # the first 14 seeds as they were
+    tail = wl[order[head:]]
+    assert set(tail[:, 2]) == {15, 16}
+    cost = driver.sample_cost(tail)
+    assert np.all(np.diff(cost) <= 0)  # the last two seeds by falling cost: zone 1 first
+    assert tail[0, 1] == 1 and tail[1, 1] == 1
+    assert np.array_equal(driver.tail_by_cost(wl, len(masks), 0), np.arange(len(wl)))
