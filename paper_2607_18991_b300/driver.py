@@ -50,6 +50,28 @@ def tail_by_cost(workload: np.ndarray, per_seed: int, tail_seeds: int) -> np.nda
     return np.concatenate([np.arange(n - t), tail[np.argsort(-sample_cost(workload[tail]), kind="stable")]])
 
 
+def chunk_estimate(sub: np.ndarray, sms: int = 148) -> float:
+    """Rough duration in ms of one chunk of rows (L, zone word, seed) run alone, for assigning chunks
+    to streams only: its ranking (about 50 ms per 10^9 sites of the distinct orders, keys drawn once
+    each) plus its n* launch, which lasts as long as its slowest sample or its total cost spread over
+    the SMs (about 120 ms per 10^9 of sample_cost), as measured on the mixed batch."""
+    sites = sum(int(L) ** 5 for L, _ in {(int(r[0]), int(r[2])) for r in sub})
+    cost = sample_cost(sub)
+    return 50e-9 * sites + 120e-9 * max(float(cost.max()), float(cost.sum()) / sms)
+
+
+def assign_streams(estimates, streams: int):
+    """Stream of each chunk, in chunk order: the one with the least estimated work so far (ties to
+    the lowest index), so that a slow chunk's stream takes fewer of the others."""
+    load = [0.0] * max(1, int(streams))
+    out = []
+    for e in estimates:
+        b = min(range(len(load)), key=lambda i: (load[i], i))
+        out.append(b)
+        load[b] += float(e)
+    return out
+
+
 def _chunks(workload: np.ndarray, budget: int | None, by_cost: bool = False):
     """Split sample indices so that the distinct (L, seed) orders of a chunk fit in `budget`.  By
     default the largest L come first, then seed-major: the CTAs running at the same time share one
@@ -626,10 +648,11 @@ class BatchStep:
     launch options ({"method": METHOD_*, "group": CTAs per sample}), as picked by
     ``autotune.tune_batch``; they are set before each chunk's perc_nstar and restored after.
 
-    With ``streams`` = 2 the chunks alternate between two streams, each with its own order buffer
+    With ``streams`` = 2 the chunks are spread over two streams, each with its own order buffer
     (half the budget each) and workspace, so that a chunk whose launch waits on a few slow samples
-    leaves its idle SMs to the next chunk instead of holding up the whole batch; the graph then
-    forks into the two streams and joins them at its end.  A chunk never runs beside one of its own
+    leaves its idle SMs to the next chunk instead of holding up the whole batch; each chunk goes to
+    the stream with the least estimated work so far (``assign_streams``); the graph then forks into
+    the two streams and joins them at its end.  A chunk never runs beside one of its own
     stream's, and the cooperative CTA groups (which need the whole GPU) are not used then.
     """
 
@@ -657,8 +680,10 @@ class BatchStep:
         self.orders = [torch.empty(max(order_bytes, 16) // 4 + 4, dtype=torch.int32, device="cuda")
                        for _ in range(self.nbuf)]
         self.streams = [torch.cuda.Stream() for _ in range(self.nbuf)] if self.nbuf > 1 else None
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        bufs = assign_streams([chunk_estimate(self.workload[ch["idx"]], sms) for ch in self.chunks], self.nbuf)
         for k, ch in enumerate(self.chunks):
-            ch["buf"] = k % self.nbuf
+            ch["buf"] = bufs[k]
             base = np.uint64(self.orders[ch["buf"]].data_ptr())
             Ls, words, pp, rp = ch.pop("rel")
             ch["samples"] = perc.make_samples(Ls, words, pp + base, rp + base)

@@ -97,3 +97,22 @@ def test_tail_by_cost_orders_only_the_last_seeds():
     assert np.all(np.diff(cost) <= 0)  # the last two seeds by falling cost: zone 1 first
     assert tail[0, 1] == 1 and tail[1, 1] == 1
     assert np.array_equal(driver.tail_by_cost(wl, len(masks), 0), np.arange(len(wl)))
+
+
+def test_chunks_go_to_the_least_loaded_stream():
+    from paper_2607_18991_b300 import driver
+    assert driver.assign_streams([10, 1, 1, 1, 1, 1, 1], 3) == [0, 1, 2, 1, 2, 1, 2]
+    assert driver.assign_streams([1, 1, 1], 1) == [0, 0, 0]
+    # the slow first chunk of a cost-ordered mixed batch keeps its stream to itself for a while
+    rng = np.random.default_rng(4096)
+    L = rng.integers(10, 41, 512)
+    w = np.stack([L, rng.integers(1, 128, 512), np.arange(1, 513)], axis=1)
+    chunks = list(driver._chunks(w, 1 << 30, by_cost=True))
+    est = [driver.chunk_estimate(w[c]) for c in chunks]
+    assert est[0] == max(est)
+    bufs = driver.assign_streams(est, 4)
+    assert bufs[:4] == [0, 1, 2, 3]
+    load = np.zeros(4)
+    for b, e in zip(bufs, est):
+        load[b] += e
+    assert load.max() - load.min() <= max(est)
