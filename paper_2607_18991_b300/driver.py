@@ -651,8 +651,9 @@ class BatchStep:
     With ``streams`` = 2 the chunks are spread over two streams, each with its own order buffer
     (half the budget each) and workspace, so that a chunk whose launch waits on a few slow samples
     leaves its idle SMs to the next chunk instead of holding up the whole batch; each chunk goes to
-    the stream with the least estimated work so far (``assign_streams``); the graph then forks into
-    the two streams and joins them at its end.  A chunk never runs beside one of its own
+    the stream with the least estimated work so far (``assign_streams``), and the stream of the first
+    chunk (the slowest samples) has the higher priority; the graph then forks into the two streams
+    and joins them at its end.  A chunk never runs beside one of its own
     stream's, and the cooperative CTA groups (which need the whole GPU) are not used then.
     """
 
@@ -679,9 +680,13 @@ class BatchStep:
             order_bytes = max(order_bytes, nbytes)
         self.orders = [torch.empty(max(order_bytes, 16) // 4 + 4, dtype=torch.int32, device="cuda")
                        for _ in range(self.nbuf)]
-        self.streams = [torch.cuda.Stream() for _ in range(self.nbuf)] if self.nbuf > 1 else None
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-        bufs = assign_streams([chunk_estimate(self.workload[ch["idx"]], sms) for ch in self.chunks], self.nbuf)
+        est = [chunk_estimate(self.workload[ch["idx"]], sms) for ch in self.chunks]
+        bufs = assign_streams(est, self.nbuf)
+        # the stream of the first (slowest) chunk runs at a higher priority: its launches take SMs as
+        # they free up before the other streams' waiting CTAs, so the longest path starts first
+        self.streams = ([torch.cuda.Stream(priority=-1 if b == bufs[0] else 0) for b in range(self.nbuf)]
+                        if self.nbuf > 1 else None)
         for k, ch in enumerate(self.chunks):
             ch["buf"] = bufs[k]
             base = np.uint64(self.orders[ch["buf"]].data_ptr())
