@@ -398,7 +398,11 @@ int perc_bracket(const float *params, const perc_sample *samples, uint32_t num_s
  *   perm[s][0..P) holds the P >= K sites of smallest (key, index) in order and rank[s][site] is set
  *   for those sites, P ending at a key-bucket boundary (the top bits of the key).  Every other entry
  *   of perm and rank is left as it was.  For L^5 above 104,857,600 (the radix path) every site is
- *   ranked.  Arguments and workspace as for perc_rank, plus
+ *   ranked.  The keys are drawn once for every site (bucket counts) and once more only for the
+ *   sites whose keys fall in the buckets where about K + 8 sqrt(K) + 64 keys are expected to end,
+ *   listed in the workspace while counting; a seed whose cut lies past them, or whose list would
+ *   pass half its order, draws all its keys again (the same result; PERC_RANK_STAGE=0 in the
+ *   environment always does).  Arguments and workspace as for perc_rank, plus
  *     share  device uint32, as perc_prefix_share writes it (read on the device)
  *
  * perc_nstar_prefix -- perc_nstar's sweep on such orders: no site of rank >= K (K from *share and
