@@ -853,15 +853,20 @@ class PmaxStep:
     one L, each mask with its own row of probabilities (eq. Pmax with the binomial convolution).
 
     Every device buffer is allocated here, so ``run`` only enqueues library calls on the stream.
-    Samples are seed-major; the weight groups are the masks (one row of p per mask)."""
+    Samples are seed-major except the last ``tail_seeds`` seeds (default: an eighth), queued by
+    falling sample_cost as in NstarStep; ``workload`` lists them in queue order.  The weight groups
+    are the masks (one row of p per mask)."""
 
-    def __init__(self, L: int, masks, seeds, p_of_mask: dict, tail: float = 1e-16):
+    def __init__(self, L: int, masks, seeds, p_of_mask: dict, tail: float = 1e-16, tail_seeds: int | None = None):
         self.L = int(L)
         self.masks = np.asarray(list(masks), dtype=np.int64)
         self.seeds = np.asarray(list(seeds), dtype=np.int64)
         N = self.L ** 5
         S = len(self.seeds)
-        self.workload = np.array([(self.L, m, s) for s in self.seeds for m in self.masks], dtype=np.int64)
+        wl = np.array([(self.L, m, s) for s in self.seeds for m in self.masks], dtype=np.int64).reshape(-1, 3)
+        seed_row = np.repeat(np.arange(S), len(self.masks))
+        order = tail_by_cost(wl, len(self.masks), S // 8 if tail_seeds is None else int(tail_seeds))
+        self.workload, seed_row = wl[order], seed_row[order]
         self.num = len(self.workload)
         p = np.array([p_of_mask[int(m)] for m in self.workload[:, 1]], dtype=np.float64)
         self.group, self.Ng, self.lo, self.count, self.pg, self.window = pmax_windows(
@@ -871,8 +876,7 @@ class PmaxStep:
         self.seeds_dev = torch.as_tensor(self.seeds, device="cuda")
         self.perm = torch.empty((S, N), dtype=torch.int32, device="cuda")
         self.rank = torch.empty((S, N), dtype=torch.int32, device="cuda")
-        rows = np.repeat(np.arange(S), len(self.masks))
-        self.samples = perc.samples_for(self.L, np.tile(self.masks, S), rows, self.perm, self.rank)
+        self.samples = perc.samples_for(self.L, self.workload[:, 1], seed_row, self.perm, self.rank)
         self.n_lo = torch.as_tensor(self.lo[self.group], device="cuda")
         self.cnt = torch.as_tensor(self.count[self.group].astype(np.int32), device="cuda")
         self.group_dev = torch.as_tensor(self.group.astype(np.int32), device="cuda")

@@ -186,3 +186,28 @@ def test_pmax_full_size_L16_sampled():
         pre = oracle.smax_prefix(16, m, perm, rk, hi).astype(np.float64)
         want = [float(np.dot(w[: hi + 1], pre)) / N for w in w_all]
         assert np.allclose(pm[k], want, rtol=1e-9, atol=1e-15), m
+
+
+def test_pmax_step_queue_order_matches_rows():
+    """The step queues its last seeds by cost; its rows (``workload``), windows and P_max must still
+    belong together: the same P_max as the unbatched call on the step's rows, and, for a few rows,
+    the oracle's."""
+    import torch
+
+    from paper_2607_18991_b300 import driver
+    masks = (1, 3, 7, 64, 127)
+    grid = {m: PC[m] * np.linspace(0.95, 1.05, 4) for m in masks}
+    st = driver.PmaxStep(8, masks, range(1, 17), grid)
+    assert not np.array_equal(st.workload[:, 2], np.repeat(np.arange(1, 17), len(masks)))  # reordered tail
+    st.run()
+    torch.cuda.synchronize()
+    got = st.pmax.cpu().numpy()
+    p = np.array([grid[int(m)] for m in st.workload[:, 1]])
+    want, _ = driver.pmax(st.workload, p)
+    assert np.allclose(got, want, rtol=1e-12, atol=0.0)
+    for k in (0, len(st.workload) - 1, len(st.workload) - 7):
+        _, m, s = (int(v) for v in st.workload[k])
+        perm, rk = orc_order(8, s)
+        sall = oracle.nz(8, m, perm, rk, smax_all=True)[2]
+        ref = np.array([oracle.pmax(sall, 8, float(q)) for q in p[k]])
+        assert np.allclose(got[k], ref, rtol=1e-9, atol=1e-15), (m, s)
