@@ -106,6 +106,7 @@ def dist_env():
 def workload_for(rank: int, num_seeds: int = NUM_SEEDS):
     seeds = np.arange(1, num_seeds + 1) + rank * num_seeds
     # seed-major: the 127 masks of a seed are adjacent, so CTAs running together share one site order
+    # (NstarStep then queues the last eighth of the seeds by cost)
     return seeds, np.array([(L, m, int(s)) for s in seeds for m in MASKS], dtype=np.int64)
 
 
@@ -1315,7 +1316,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
     ap.add_argument("--batch-streams", type=int, default=4,
-                    help="mixed batch: chunks alternate over this many streams (each its own order buffer)")
+                    help="mixed batch: chunks spread over this many streams, each to the least loaded "
+                         "(each stream its own order buffer)")
     ap.add_argument("--no-prefix", action="store_true",
                     help="learned arm: rank every site of each order instead of the brackets' share")
     ap.add_argument("--no-graph", dest="graph", action="store_false", help="do not time CUDA-graph replays")
