@@ -119,6 +119,10 @@ size_t perc_workspace_bytes(int op, uint32_t max_L, uint32_t num);
  *   L          lattice side, 1..PERC_MAX_L
  *   seeds      device uint64[num_seeds]
  *   perm, rank device uint32[num_seeds][L^5] (outputs, row s for seed s)
+ * Up to L^5 = 104,857,600 (L <= 40) a bucket sort on the keys' top bits, above it an LSD radix
+ * sort; both give the same order.  Environment variables (for comparisons; results unchanged):
+ * PERC_RANK_BUCKET=0 takes the radix sort at any L, PERC_RANK_TMA=0 its plain scatter instead of
+ * the one fed by bulk copies.
  * Errors: PERC_EINVAL (L out of range, num_seeds 0, null pointer), PERC_EWORKSPACE.
  */
 int perc_rank(uint32_t L, const uint64_t *seeds, uint32_t num_seeds, uint32_t *perm,
